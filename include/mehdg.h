@@ -1,0 +1,209 @@
+/*
+ * mehdg.h - C ABI of the GB300 (sm_103a) macro-element HDG trace solver.
+ *
+ * Implements the data-parallel hot path of the macro-element hybridized DG
+ * method of Badrkhani, Hiemstra, Mika and Schillinger, "A matrix-free
+ * macro-element variant of the hybridized discontinuous Galerkin method"
+ * (arXiv 2302.10917), for the 2D steady advection-diffusion problem
+ *     -kappa Lap u + beta . grad u = f  on (0,1)^2,   u = g_D on the boundary
+ * (Eq. C21 with a constant velocity a = beta, first-order form Eq. C22).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Mesh (Sec. 5.1, d = 2): n x n squares, each split by its "/" diagonal into
+ *   t = 0 (lower-right): v0 = (x_{i+1}, y_j), v1 = (x_{i+1}, y_{j+1}), v2 = (x_i, y_j)
+ *   t = 1 (upper-left) : v0 = (x_i, y_{j+1}), v1 = (x_i, y_j),         v2 = (x_{i+1}, y_{j+1})
+ *   element id e = 2 (j n + i) + t, N = 2 n^2. Local edge k is opposite v_k
+ *   and runs from v_{k+1} to v_{k+2}.
+ * Macro-element spaces (Sec. 3.2): C0 piecewise P_p on the uniform m-fold
+ *   subdivision of each macro-triangle; P = m p; Q = (P+1)(P+2)/2 lattice
+ *   nodes (a/P, b/P), a + b <= P, in reference coordinates of the affine map
+ *   x = v0 + xi (v1 - v0) + eta (v2 - v0), numbered b-major, a fastest:
+ *   node(a, b) = b (P+1) - b (b-1)/2 + a.
+ * Trace (Sec. 3.2): C0 piecewise P_p on each macro-edge, P + 1 dofs per edge
+ *   at equispaced points, oriented from the lower to the higher global vertex
+ *   id (vertex (i, j) has id j (n+1) + i). Trace unknowns live on the
+ *   n^2 + 2 n (n-1) interior edges (all four sides are Dirichlet):
+ *     diagonal   D(i,j)        -> j n + i
+ *     horizontal H(i,j), 1<=j<n -> n^2 + (j-1) n + i
+ *     vertical   V(i,j), 1<=i<n -> n^2 + n (n-1) + j (n-1) + (i-1)
+ *   global trace dof = edge (P + 1) + s; N_tr = (#interior edges)(P + 1).
+ *   Boundary edges: bottom H(i,0) -> i, top H(i,n) -> n + i,
+ *   left V(0,j) -> 2n + j, right V(n,j) -> 3n + j.
+ * Source quadrature (element formation, Sec. 6.1): on every sub-triangle
+ *   (upright ones (si,sj), si+sj<=m-1, with corners (si,sj),(si+1,sj),(si,sj+1)
+ *   in units of 1/m, then inverted ones (si,sj), si+sj<=m-2, with corners
+ *   (si+1,sj+1),(si,sj+1),(si+1,sj); sj outer, si inner) the collapsed
+ *   Gauss rule with ng = p + 2 points per direction: local point
+ *   (u_i (1 - u_j), u_j), index j ng + i, u_* the Gauss-Legendre nodes on
+ *   [0,1]. n_qp = m^2 ng^2 points per element.
+ * Dirichlet data: on each boundary edge, m sub-edges x (p + 2) Gauss points
+ *   along its orientation; g_D is L2-projected onto the trace space (Sec. 2.3).
+ * Stabilisation (Sec. 3.1, value not given in the paper):
+ *   tau_e = kappa_e / tau_len + |beta| on all edges of element e.
+ *
+ * Memory, streams and errors
+ * --------------------------
+ * Pointers named *_dev are CUDA device pointers owned by the caller; *_host
+ * pointers are host memory owned by the caller. The context owns every
+ * internal buffer (Schur blocks, factors, Krylov basis). All device work is
+ * enqueued on the stream given to hdg_create; entry points that return data
+ * to the host (hdg_info, hdg_solve's report, hdg_run_host) synchronise that
+ * stream. A failing call returns a status other than HDG_OK and records a
+ * message that hdg_last_error returns; the context stays usable unless the
+ * status is HDG_ERR_CUDA. Call order: hdg_create -> hdg_set_source ->
+ * hdg_condense -> {hdg_rhs, hdg_apply, hdg_solve} -> hdg_recover; a call out
+ * of order returns HDG_ERR_STATE. Only nrhs = 1 is accepted by this version.
+ * Nothing here falls back to the CPU: without a usable sm_103a device every
+ * entry point that launches work returns HDG_ERR_CUDA.
+ */
+#ifndef MEHDG_H
+#define MEHDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, unsupported option) */
+  HDG_ERR_STATE = 2,     /* call made out of the documented order */
+  HDG_ERR_CUDA = 3,      /* CUDA runtime error (message holds the CUDA error string) */
+  HDG_ERR_OOM = 4,       /* device allocation failed */
+  HDG_ERR_SINGULAR = 5,  /* a local matrix had a zero pivot (element index in the message) */
+  HDG_ERR_NOCONV = 6,    /* GMRES stopped at maxit; x holds the last iterate */
+  HDG_ERR_TIMEOUT = 7    /* a bounded device wait gave up */
+} hdg_status;
+
+typedef struct {
+  int n;                 /* macro squares per side (N = 2 n^2 macro-triangles), n >= 1 */
+  int m;                 /* sub-edges per macro-edge (m^2 sub-triangles), 1 <= m <= 16 */
+  int p;                 /* polynomial degree, 1 <= p <= 4 */
+  double beta[2];        /* constant advection velocity a */
+  double kappa0;         /* diffusivity used when kappa == NULL; >= 0 (0 = pure advection) */
+  const double* kappa;   /* host pointer, N per-element diffusivities >= 0, or NULL */
+  double tau_len;        /* length scale of tau_e = kappa_e / tau_len + |beta|; > 0 */
+  int bc[4];             /* boundary type per side (bottom, top, left, right); 0 = Dirichlet (only value accepted) */
+} hdg_mesh_desc;
+
+typedef struct {
+  int64_t N;             /* macro-elements */
+  int64_t Q;             /* lattice nodes per element */
+  int64_t n_t;           /* trace dofs per element, 3 (P + 1) */
+  int64_t N_tr;          /* global trace unknowns */
+  int64_t n_int_edges;   /* interior edges */
+  int64_t n_bnd_edges;   /* boundary edges, 4 n */
+  int64_t n_qp;          /* source points per element */
+  int64_t n_bqp;         /* Dirichlet-data points per boundary edge */
+  size_t device_bytes;   /* device memory currently held by the context */
+} hdg_info_t;
+
+/* Solve options. mode: 0 = FP64 GMRES on FP64 Schur blocks; 1 = FP32 Schur
+ * blocks inside FP64 iterative refinement (requires HDG_STORE_FP32). */
+typedef struct {
+  double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
+  int maxit;             /* maximum number of operator applications inside GMRES */
+  int restart;           /* GMRES restart length, 1 <= restart <= 128 */
+  int mode;
+} hdg_solve_opts;
+
+typedef struct {
+  int iterations;        /* Arnoldi steps (preconditioned operator applications) */
+  int restarts;          /* GMRES cycles */
+  int outer;             /* iterative-refinement sweeps (mode 1), else 0 */
+  int converged;         /* 1 if rel_residual <= tol */
+  double rel_residual;   /* true relative residual at exit, computed with FP64 S */
+} hdg_solve_report;
+
+/* hdg_condense flags */
+#define HDG_STORE_FP32 1u      /* also keep an FP32 copy of the preconditioned blocks */
+#define HDG_KEEP_FACTORS 2u    /* keep the factored local systems for hdg_recover (else recover refactors) */
+
+/* Build the structured macro mesh, the reference-lattice tables of level m
+ * (mass, derivative, boundary and trace matrices, quadrature) and the device
+ * copies of those tables. Sec. 5.1 (mesh), Sec. 3.2 (spaces), Sec. 6.1
+ * (element formation). stream: a cudaStream_t (NULL = legacy default
+ * stream). *out receives a new context; free it with hdg_destroy.
+ * Errors: HDG_ERR_ARG for an invalid descriptor, HDG_ERR_CUDA/OOM. */
+hdg_status hdg_create(const hdg_mesh_desc* desc, void* stream, hdg_ctx** out);
+
+/* Sizes of the problem and the context's device memory (host struct). */
+hdg_status hdg_info(const hdg_ctx* ctx, hdg_info_t* out);
+
+/* Physical coordinates of the source quadrature points, [N][n_qp][2] FP64
+ * device array (layout in the header comment). The caller evaluates f there. */
+hdg_status hdg_quad_points(const hdg_ctx* ctx, double* xy_dev);
+
+/* Physical coordinates of the Dirichlet-data points, [4 n][n_bqp][2] FP64. */
+hdg_status hdg_bnd_quad_points(const hdg_ctx* ctx, double* xy_dev);
+
+/* Record the source f at the quadrature points ([N][n_qp] FP64, device) and
+ * the Dirichlet data g_D at the boundary points ([4 n][n_bqp] FP64, device,
+ * or NULL for g_D = 0). The arrays are read by hdg_condense and
+ * hdg_recover and must stay valid until then. Eq. (weak_form): l(V), with
+ * u^ = v^ + g^ (Sec. 3.1) and g^ the L2 projection of g_D (Sec. 2.3). */
+hdg_status hdg_set_source(hdg_ctx* ctx, const double* f_qp_dev, const double* gD_qp_dev, int nrhs);
+
+/* Static condensation of every macro-element, Eqs. (global_problem) and
+ * (local_problem) with the block system Eq. (D) and the forms of Eq.
+ * (weak_form): forms A_e, B_e, C_e, D_e and the load of each element,
+ * eliminates q and u with partial-pivoting LU in FP64, and stores the Schur
+ * block S_e = D_e - C_e A_e^-1 B_e, its face-preconditioned form
+ * (Sec. 6.1, D_f^-1 applied row-block-wise) and the element right-hand
+ * side -C_e A_e^-1 R_e - S_e g^_e. flags: HDG_STORE_FP32, HDG_KEEP_FACTORS.
+ * Errors: HDG_ERR_SINGULAR if a pivot is exactly zero (first such element
+ * in the message), HDG_ERR_OOM, HDG_ERR_STATE before hdg_set_source. */
+hdg_status hdg_condense(hdg_ctx* ctx, unsigned flags);
+
+/* Assembled condensed right-hand side g = R_u^ - C A^-1 R_u (Eq.
+ * global_problem) including the Dirichlet lift; [N_tr] FP64 device. */
+hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
+
+/* Matrix-free trace-operator apply (Sec. 3.3.2, steps 1-4):
+ *   precond = 0: y = S x, S = sum_e L_e^T (D_e - C_e A_e^-1 B_e) L_e;
+ *   precond = 1: y = D^-1 S x, the left-preconditioned operator of Sec. 6.1.
+ * x, y: [N_tr] device arrays, FP64 (prec = 64) or FP32 (prec = 32, uses the
+ * FP32 blocks; precond must be 1). x and y must not overlap. */
+hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int prec, int precond);
+
+/* Solve S x = g (Eq. global_problem) with restarted GMRES, left-
+ * preconditioned by D^-1 (Sec. 6.1). x_dev holds the initial guess on entry
+ * and the solution on exit ([N_tr] FP64). report may be NULL.
+ * Returns HDG_ERR_NOCONV (with x = last iterate and the report filled) if
+ * maxit is reached first. */
+hdg_status hdg_solve(hdg_ctx* ctx, const double* g_dev, double* x_dev, int nrhs,
+                     const hdg_solve_opts* opts, hdg_solve_report* report);
+
+/* Local back-solve Eq. (local_matrix_problem): A_e U_e = R_e - B_e u^_e for
+ * every element, u^_e gathered from x (interior edges) and g^ (boundary).
+ * u_dev: [N][Q] FP64, q_dev: [N][2][Q] FP64 (q = -grad u), lattice order. */
+hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double* q_dev, int nrhs);
+
+/* Copy the FP64 Schur blocks S_e of elements e0 .. e0+count-1 into S_dev as
+ * row-major [count][n_t][n_t] (element-local trace order: local edge k,
+ * then position along the edge from v_{k+1} to v_{k+2}). */
+hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
+
+/* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to
+ * the device, condenses, assembles g, solves from x = 0, recovers u and q
+ * and copies x, u, q back (each output may be NULL to skip its copy).
+ * Synchronous. Same layouts as above. */
+hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_qp_host,
+                        const hdg_solve_opts* opts, double* x_host, double* u_host,
+                        double* q_host, hdg_solve_report* report);
+
+/* Last error message of the context (never NULL; "" if none). */
+const char* hdg_last_error(const hdg_ctx* ctx);
+
+/* Release every resource of the context (NULL is allowed). */
+void hdg_destroy(hdg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MEHDG_H */

@@ -1,0 +1,225 @@
+"""GB300 (sm_103a) macro-element HDG trace solver: thin Python binding.
+
+Argument marshalling only: every step of the hot path (element formation,
+batched static condensation, trace-operator apply, GMRES, back-solve) runs in
+the CUDA library ``libmehdg.so`` behind the C ABI of ``include/mehdg.h``.
+PyTorch supplies device memory and the CUDA stream. There is no CPU fallback:
+if the library or a GPU is missing, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmehdg.so")
+
+HDG_OK, HDG_ERR_ARG, HDG_ERR_STATE, HDG_ERR_CUDA, HDG_ERR_OOM = 0, 1, 2, 3, 4
+HDG_ERR_SINGULAR, HDG_ERR_NOCONV, HDG_ERR_TIMEOUT = 5, 6, 7
+HDG_STORE_FP32, HDG_KEEP_FACTORS = 1, 2
+STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_CUDA", 4: "HDG_ERR_OOM",
+                5: "HDG_ERR_SINGULAR", 6: "HDG_ERR_NOCONV", 7: "HDG_ERR_TIMEOUT"}
+
+EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", "hdg_set_source",
+            "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
+            "hdg_run_host", "hdg_last_error", "hdg_destroy"]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
+                ("beta", ctypes.c_double * 2), ("kappa0", ctypes.c_double),
+                ("kappa", ctypes.POINTER(ctypes.c_double)), ("tau_len", ctypes.c_double),
+                ("bc", ctypes.c_int * 4)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("Q", ctypes.c_int64), ("n_t", ctypes.c_int64),
+                ("N_tr", ctypes.c_int64), ("n_int_edges", ctypes.c_int64),
+                ("n_bnd_edges", ctypes.c_int64), ("n_qp", ctypes.c_int64), ("n_bqp", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
+                ("mode", ctypes.c_int)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HDGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmehdg.so and declare the C signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(path)
+    vp, dp, i64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64
+    lib.hdg_create.argtypes = [ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)]
+    lib.hdg_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.hdg_quad_points.argtypes = [vp, dp]
+    lib.hdg_bnd_quad_points.argtypes = [vp, dp]
+    lib.hdg_set_source.argtypes = [vp, dp, dp, ctypes.c_int]
+    lib.hdg_condense.argtypes = [vp, ctypes.c_uint]
+    lib.hdg_rhs.argtypes = [vp, dp]
+    lib.hdg_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.hdg_solve.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)]
+    lib.hdg_recover.argtypes = [vp, dp, dp, dp, ctypes.c_int]
+    lib.hdg_get_schur.argtypes = [vp, i64, i64, dp]
+    lib.hdg_run_host.argtypes = [vp, dp, dp, ctypes.POINTER(SolveOpts), dp, dp, dp, ctypes.POINTER(SolveReport)]
+    lib.hdg_last_error.argtypes = [vp]
+    lib.hdg_last_error.restype = ctypes.c_char_p
+    lib.hdg_destroy.argtypes = [vp]
+    lib.hdg_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("hdg_last_error", "hdg_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Problem:
+    """One macro-element HDG problem on the structured unit-square mesh (one GPU)."""
+
+    def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, device="cuda:0", stream=None):
+        self.lib = load_library()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        d = MeshDesc()
+        d.n, d.m, d.p = n, m, p
+        d.beta[0], d.beta[1] = float(beta[0]), float(beta[1])
+        d.tau_len = float(tau_len)
+        self._kappa_host = None
+        if isinstance(kappa, (int, float)):
+            d.kappa0 = float(kappa)
+            d.kappa = ctypes.POINTER(ctypes.c_double)()
+        else:
+            k = torch.as_tensor(kappa, dtype=torch.float64).contiguous().cpu()
+            self._kappa_host = k
+            d.kappa0 = 1.0
+            d.kappa = ctypes.cast(ctypes.c_void_p(k.data_ptr()), ctypes.POINTER(ctypes.c_double))
+        for s in range(4):
+            d.bc[s] = 0
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.hdg_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        self.h = h
+        if st != HDG_OK:
+            msg = self.lib.hdg_last_error(h).decode() if h.value else ""
+            if h.value:
+                self.lib.hdg_destroy(h)
+            self.h = ctypes.c_void_p()
+            raise HDGError(st, msg or "hdg_create failed")
+        info = Info()
+        self._check(self.lib.hdg_info(self.h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in Info._fields_}
+        self.n, self.m, self.p = n, m, p
+        self._src = None
+
+    # ------------------------------------------------------------------ utils
+    def _check(self, st):
+        if st != HDG_OK:
+            raise HDGError(st, self.lib.hdg_last_error(self.h).decode())
+
+    def _f64(self, *shape):
+        return torch.empty(*shape, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.hdg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------- API
+    def quad_points(self):
+        xy = self._f64(self.info["N"], self.info["n_qp"], 2)
+        self._check(self.lib.hdg_quad_points(self.h, _ptr(xy)))
+        return xy
+
+    def bnd_quad_points(self):
+        xy = self._f64(self.info["n_bnd_edges"], self.info["n_bqp"], 2)
+        self._check(self.lib.hdg_bnd_quad_points(self.h, _ptr(xy)))
+        return xy
+
+    def set_source(self, f_qp, gD_qp=None):
+        f_qp = f_qp.to(self.device, torch.float64).contiguous()
+        gD_qp = None if gD_qp is None else gD_qp.to(self.device, torch.float64).contiguous()
+        self._src = (f_qp, gD_qp)       # keep alive until condense / recover
+        self._check(self.lib.hdg_set_source(self.h, _ptr(f_qp), _ptr(gD_qp), 1))
+
+    def condense(self, store_fp32=False, keep_factors=True):
+        flags = (HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
+        self._check(self.lib.hdg_condense(self.h, flags))
+
+    def rhs(self):
+        g = self._f64(self.info["N_tr"])
+        self._check(self.lib.hdg_rhs(self.h, _ptr(g)))
+        return g
+
+    def apply(self, x, precond=False, prec=64, out=None):
+        dt = torch.float64 if prec == 64 else torch.float32
+        x = x.to(self.device, dt).contiguous()
+        y = out if out is not None else torch.empty_like(x)
+        self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), 1, prec, 1 if precond else 0))
+        return y
+
+    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True):
+        g = g.to(self.device, torch.float64).contiguous()
+        x = torch.zeros_like(g) if x0 is None else x0.to(self.device, torch.float64).clone()
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode)
+        r = SolveReport()
+        st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), 1, ctypes.byref(o), ctypes.byref(r))
+        if check and st not in (HDG_OK, HDG_ERR_NOCONV):
+            self._check(st)
+        return x, r.as_dict(), st
+
+    def recover(self, x):
+        x = x.to(self.device, torch.float64).contiguous()
+        u = self._f64(self.info["N"], self.info["Q"])
+        q = self._f64(self.info["N"], 2, self.info["Q"])
+        self._check(self.lib.hdg_recover(self.h, _ptr(x), _ptr(u), _ptr(q), 1))
+        return u, q
+
+    def schur(self, e0=0, count=None):
+        count = self.info["N"] - e0 if count is None else count
+        S = self._f64(count, self.info["n_t"], self.info["n_t"])
+        self._check(self.lib.hdg_get_schur(self.h, e0, count, _ptr(S)))
+        return S
+
+    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True):
+        """End-to-end call on host (ideally pinned) tensors; returns (x, u, q, report)."""
+        N, Q, N_tr = self.info["N"], self.info["Q"], self.info["N_tr"]
+        x = torch.empty(N_tr, dtype=torch.float64, pin_memory=True) if outputs else None
+        u = torch.empty(N, Q, dtype=torch.float64, pin_memory=True) if outputs else None
+        q = torch.empty(N, 2, Q, dtype=torch.float64, pin_memory=True) if outputs else None
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=0)
+        r = SolveReport()
+        st = self.lib.hdg_run_host(self.h, _ptr(f_host), _ptr(gD_host), ctypes.byref(o), _ptr(x), _ptr(u),
+                                   _ptr(q), ctypes.byref(r))
+        if st not in (HDG_OK, HDG_ERR_NOCONV):
+            self._check(st)
+        return x, u, q, r.as_dict()

@@ -1,0 +1,405 @@
+// C ABI of the macro-element HDG library (declarations and the paper passages
+// each entry point follows are in include/mehdg.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include "launch.h"
+
+using namespace mehdg;
+
+namespace {
+
+hdg_status set_err(hdg_ctx* c, hdg_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+hdg_status cuda_err(hdg_ctx* c, cudaError_t e, const char* where) {
+  return set_err(c, e == cudaErrorMemoryAllocation ? HDG_ERR_OOM : HDG_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t dev_alloc(hdg_ctx* c, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) c->bytes += count * sizeof(T);
+  return e;
+}
+
+template <typename T>
+void dev_free(hdg_ctx* c, T*& p, size_t count) {
+  if (p) {
+    cudaFree((void*)p);
+    c->bytes -= std::min(c->bytes, count * sizeof(T));
+  }
+  p = nullptr;
+}
+
+// Physical source points, [N][n_qp][2].
+__global__ void quad_points_kernel(Params P, DevTables dt, double* xy) {
+  const int64_t total = (int64_t)P.N * P.n_qp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(idx / P.n_qp);
+    const int r = (int)(idx - (int64_t)e * P.n_qp);
+    const int s = r / P.nqs, q = r - s * P.nqs;
+    const int qj = q / P.ng, qi = q - qj * P.ng;
+    const double xh = dt.uq[qi] * (1.0 - dt.uq[qj]), eh = dt.uq[qj];
+    const int* c = dt.subtri + 6 * s;
+    const double xi = (c[0] + xh * (c[2] - c[0]) + eh * (c[4] - c[0])) / P.m;
+    const double eta = (c[1] + xh * (c[3] - c[1]) + eh * (c[5] - c[1])) / P.m;
+    double v[3][2];
+    elem_vertices(e, P.n, v);
+    xy[2 * idx + 0] = v[0][0] + xi * (v[1][0] - v[0][0]) + eta * (v[2][0] - v[0][0]);
+    xy[2 * idx + 1] = v[0][1] + xi * (v[1][1] - v[0][1]) + eta * (v[2][1] - v[0][1]);
+  }
+}
+
+// Dirichlet-data points, [4n][m * ngb][2].
+__global__ void bnd_points_kernel(Params P, DevTables dt, double* xy) {
+  const int64_t total = (int64_t)P.n_bnd * P.n_bqp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / P.n_bqp);
+    const int r = (int)(idx - (int64_t)b * P.n_bqp);
+    const int s = r / P.ngb, q = r - s * P.ngb;
+    const int side = b / P.n, k = b - side * P.n;
+    const double h = 1.0 / P.n;
+    double a0[2], a1[2];
+    if (side == 0) { a0[0] = k * h; a0[1] = 0.0; a1[0] = (k + 1) * h; a1[1] = 0.0; }
+    else if (side == 1) { a0[0] = k * h; a0[1] = 1.0; a1[0] = (k + 1) * h; a1[1] = 1.0; }
+    else if (side == 2) { a0[0] = 0.0; a0[1] = k * h; a1[0] = 0.0; a1[1] = (k + 1) * h; }
+    else { a0[0] = 1.0; a0[1] = k * h; a1[0] = 1.0; a1[1] = (k + 1) * h; }
+    const double th = (s + dt.bu[q]) / P.m;
+    xy[2 * idx + 0] = a0[0] + th * (a1[0] - a0[0]);
+    xy[2 * idx + 1] = a0[1] + th * (a1[1] - a0[1]);
+  }
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Copy the host tables into one device allocation.
+cudaError_t upload_tables(hdg_ctx* c) {
+  const RefTables& T = c->ref;
+  struct Item { const void* src; size_t bytes; void** dst; };
+  DevTables& d = c->dt;
+  std::vector<Item> items = {
+      {T.Dxi.data(), T.Dxi.size() * 8, (void**)&d.Dxi},   {T.Deta.data(), T.Deta.size() * 8, (void**)&d.Deta},
+      {T.Kxx.data(), T.Kxx.size() * 8, (void**)&d.Kxx},   {T.Kyy.data(), T.Kyy.size() * 8, (void**)&d.Kyy},
+      {T.Ksym.data(), T.Ksym.size() * 8, (void**)&d.Ksym}, {T.Xxi.data(), T.Xxi.size() * 8, (void**)&d.Xxi},
+      {T.Xeta.data(), T.Xeta.size() * 8, (void**)&d.Xeta}, {T.Fh.data(), T.Fh.size() * 8, (void**)&d.Fh},
+      {T.Pxi.data(), T.Pxi.size() * 8, (void**)&d.Pxi},   {T.Peta.data(), T.Peta.size() * 8, (void**)&d.Peta},
+      {T.Yh.data(), T.Yh.size() * 8, (void**)&d.Yh},      {T.Hh.data(), T.Hh.size() * 8, (void**)&d.Hh},
+      {T.Gh.data(), T.Gh.size() * 8, (void**)&d.Gh},      {T.Ghinv.data(), T.Ghinv.size() * 8, (void**)&d.Ghinv},
+      {T.phiq.data(), T.phiq.size() * 8, (void**)&d.phiq}, {T.wq.data(), T.wq.size() * 8, (void**)&d.wq},
+      {T.uq.data(), T.uq.size() * 8, (void**)&d.uq},      {T.bpsi.data(), T.bpsi.size() * 8, (void**)&d.bpsi},
+      {T.bw.data(), T.bw.size() * 8, (void**)&d.bw},      {T.bu.data(), T.bu.size() * 8, (void**)&d.bu},
+      {T.enode.data(), T.enode.size() * 4, (void**)&d.enode}, {T.subtri.data(), T.subtri.size() * 4, (void**)&d.subtri},
+      {T.subnode.data(), T.subnode.size() * 4, (void**)&d.subnode},
+      {T.ns_ptr.data(), T.ns_ptr.size() * 4, (void**)&d.ns_ptr}, {T.ns_idx.data(), T.ns_idx.size() * 4, (void**)&d.ns_idx},
+  };
+  size_t total = 0;
+  for (auto& it : items) total += round_up(it.bytes, 256);
+  cudaError_t e = cudaMalloc(&c->d_tables, total);
+  if (e != cudaSuccess) return e;
+  c->bytes += total;
+  std::vector<unsigned char> host(total, 0);
+  size_t off = 0;
+  for (auto& it : items) {
+    std::memcpy(host.data() + off, it.src, it.bytes);
+    *it.dst = (unsigned char*)c->d_tables + off;
+    off += round_up(it.bytes, 256);
+  }
+  e = cudaMemcpyAsync(c->d_tables, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
+  if (!out) return HDG_ERR_ARG;
+  *out = nullptr;
+  if (!d) return HDG_ERR_ARG;
+  if (d->n < 1 || d->n > 1448 || d->m < 1 || d->m > 16 || d->p < 1 || d->p > 4) return HDG_ERR_ARG;
+  if (!(d->tau_len > 0.0) || !std::isfinite(d->beta[0]) || !std::isfinite(d->beta[1])) return HDG_ERR_ARG;
+  for (int s = 0; s < 4; ++s)
+    if (d->bc[s] != 0) return HDG_ERR_ARG;
+  const int64_t N = 2LL * d->n * d->n;
+  if (!d->kappa && !(d->kappa0 >= 0.0 && std::isfinite(d->kappa0))) return HDG_ERR_ARG;
+  if (d->kappa)
+    for (int64_t e = 0; e < N; ++e)
+      if (!(d->kappa[e] >= 0.0) || !std::isfinite(d->kappa[e])) return HDG_ERR_ARG;
+  const int P_ = d->m * d->p;
+  const int64_t n_int = (int64_t)d->n * d->n + 2LL * d->n * (d->n - 1);
+  if (n_int * (P_ + 1) > 0x7fffffffLL) return HDG_ERR_ARG;
+
+  hdg_ctx* c = new (std::nothrow) hdg_ctx();
+  if (!c) return HDG_ERR_OOM;
+  c->stream = (cudaStream_t)stream;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    *out = c;
+    return set_err(c, HDG_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+  }
+  try {
+    build_reference_tables(d->m, d->p, c->ref);
+  } catch (const std::exception& ex) {
+    *out = c;
+    return set_err(c, HDG_ERR_ARG, ex.what());
+  }
+  const RefTables& T = c->ref;
+  Params& P = c->prm;
+  P.n = d->n; P.m = d->m; P.p = d->p; P.P = T.P; P.P1 = T.P1; P.Q = T.Q; P.n_t = T.n_t;
+  P.N = (int)N;
+  P.n_int = (int)n_int;
+  P.n_bnd = 4 * d->n;
+  P.N_tr = (int)(n_int * T.P1);
+  P.ng = T.ng; P.nqs = T.nqs; P.nloc = T.nloc; P.nsub = T.nsub; P.n_qp = T.nsub * T.nqs;
+  P.ngb = T.ngb; P.n_bqp = d->m * T.ngb;
+  P.bx = d->beta[0]; P.by = d->beta[1]; P.babs = std::hypot(d->beta[0], d->beta[1]);
+  P.kappa0 = d->kappa0; P.tau_len = d->tau_len;
+  P.R = T.Q + T.n_t;
+  P.Cc = T.Q + T.n_t + 1;
+  P.ld = (int)round_up(P.Cc, 4);
+  *out = c;
+  if ((e = upload_tables(c)) != cudaSuccess) return cuda_err(c, e, "uploading reference tables");
+  std::vector<double> kap(N, d->kappa0);
+  if (d->kappa) std::copy(d->kappa, d->kappa + N, kap.begin());
+  if ((e = dev_alloc(c, &c->d_kappa, N)) != cudaSuccess) return cuda_err(c, e, "kappa");
+  if ((e = cudaMemcpyAsync(c->d_kappa, kap.data(), N * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    return cuda_err(c, e, "kappa upload");
+  if ((e = dev_alloc(c, &c->d_escale, P.n_int)) != cudaSuccess) return cuda_err(c, e, "face scales");
+  if ((e = launch_face_scale(P, c->d_kappa, c->d_escale, c->stream)) != cudaSuccess) return cuda_err(c, e, "face scales");
+  if ((e = dev_alloc(c, &c->d_ghat, (size_t)P.n_bnd * P.P1)) != cudaSuccess) return cuda_err(c, e, "ghat");
+  if ((e = cudaMemsetAsync(c->d_ghat, 0, (size_t)P.n_bnd * P.P1 * 8, c->stream)) != cudaSuccess)
+    return cuda_err(c, e, "ghat");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_err(c, e, "create");
+  return HDG_OK;
+}
+
+hdg_status hdg_info(const hdg_ctx* c, hdg_info_t* out) {
+  if (!c || !out) return HDG_ERR_ARG;
+  const Params& P = c->prm;
+  out->N = P.N; out->Q = P.Q; out->n_t = P.n_t; out->N_tr = P.N_tr;
+  out->n_int_edges = P.n_int; out->n_bnd_edges = P.n_bnd; out->n_qp = P.n_qp; out->n_bqp = P.n_bqp;
+  out->device_bytes = c->bytes;
+  return HDG_OK;
+}
+
+hdg_status hdg_quad_points(const hdg_ctx* cc, double* xy) {
+  hdg_ctx* c = const_cast<hdg_ctx*>(cc);
+  if (!c || !xy) return HDG_ERR_ARG;
+  if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  quad_points_kernel<<<1024, 256, 0, c->stream>>>(c->prm, c->dt, xy);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_quad_points");
+}
+
+hdg_status hdg_bnd_quad_points(const hdg_ctx* cc, double* xy) {
+  hdg_ctx* c = const_cast<hdg_ctx*>(cc);
+  if (!c || !xy) return HDG_ERR_ARG;
+  if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  bnd_points_kernel<<<64, 256, 0, c->stream>>>(c->prm, c->dt, xy);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_bnd_quad_points");
+}
+
+hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, int nrhs) {
+  if (!c) return HDG_ERR_ARG;
+  if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  if (!f_qp || nrhs != 1) return set_err(c, HDG_ERR_ARG, "f_qp must be a device pointer and nrhs must be 1");
+  c->f_qp = f_qp;
+  c->gD_qp = gD_qp;
+  cudaError_t e;
+  if (gD_qp) e = launch_project_dirichlet(c->prm, c->dt, gD_qp, c->d_ghat, c->stream);
+  else e = cudaMemsetAsync(c->d_ghat, 0, (size_t)c->prm.n_bnd * c->prm.P1 * 8, c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "hdg_set_source");
+  c->state = 1;
+  return HDG_OK;
+}
+
+hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
+  if (!c) return HDG_ERR_ARG;
+  if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
+  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS)) return set_err(c, HDG_ERR_ARG, "unknown flags");
+  const Params& P = c->prm;
+  cudaError_t e;
+  const size_t sblk = (size_t)P.N * 3 * P.n_t * P.P1;
+  if (!c->d_S && (e = dev_alloc(c, &c->d_S, sblk)) != cudaSuccess) return cuda_err(c, e, "S blocks");
+  if (!c->d_St && (e = dev_alloc(c, &c->d_St, sblk)) != cudaSuccess) return cuda_err(c, e, "preconditioned S blocks");
+  if ((flags & HDG_STORE_FP32) && !c->d_St32 && (e = dev_alloc(c, &c->d_St32, sblk)) != cudaSuccess)
+    return cuda_err(c, e, "FP32 S blocks");
+  if (!(flags & HDG_STORE_FP32)) dev_free(c, c->d_St32, sblk);
+  if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
+  if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
+  if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
+  const size_t slot = (size_t)P.R * P.ld;
+  const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, 4096);
+  if (c->ws_slots != want) {
+    dev_free(c, c->d_ws, (size_t)c->ws_slots * slot);
+    c->ws_slots = 0;
+    if ((e = dev_alloc(c, &c->d_ws, (size_t)want * slot)) != cudaSuccess) return cuda_err(c, e, "local workspace");
+    c->ws_slots = want;
+  }
+  const int keep = (flags & HDG_KEEP_FACTORS) ? 1 : 0;
+  const double* gh = c->gD_qp ? c->d_ghat : nullptr;
+  for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
+    const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
+    e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, keep, 1, c->d_S, c->d_St,
+                        (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
+  }
+  if ((e = launch_assemble_rhs(P, c->d_gel, c->d_g, c->stream)) != cudaSuccess) return cuda_err(c, e, "rhs");
+  std::vector<int> info(P.N);
+  if ((e = cudaMemcpyAsync(info.data(), c->d_info, (size_t)P.N * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_err(c, e, "info");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_err(c, e, "condense");
+  c->flags = flags;
+  for (int64_t i = 0; i < P.N; ++i)
+    if (info[i]) {
+      c->state = 1;
+      return set_err(c, HDG_ERR_SINGULAR, "zero pivot in column " + std::to_string(info[i] - 1) + " of element " +
+                                                std::to_string(i));
+    }
+  c->state = 2;
+  return HDG_OK;
+}
+
+hdg_status hdg_rhs(hdg_ctx* c, double* g) {
+  if (!c || !g) return HDG_ERR_ARG;
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_rhs before hdg_condense");
+  cudaError_t e = cudaMemcpyAsync(g, c->d_g, (size_t)c->prm.N_tr * 8, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_rhs");
+}
+
+hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int precond) {
+  if (!c) return HDG_ERR_ARG;
+  if (!x || !y || x == y || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad x/y or nrhs");
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
+  cudaError_t e;
+  if (prec == 64) {
+    e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream)
+                : launch_apply64(c->prm, c->d_S, (const double*)x, (double*)y, nullptr, nullptr, c->stream);
+  } else if (prec == 32) {
+    if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
+    e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, c->d_escale, nullptr, c->stream);
+  } else {
+    return set_err(c, HDG_ERR_ARG, "prec must be 64 or 32");
+  }
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
+}
+
+hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg_solve_opts* o,
+                     hdg_solve_report* rep) {
+  if (!c) return HDG_ERR_ARG;
+  if (!g || !x || !o || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
+  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode != 0)
+    return set_err(c, HDG_ERR_ARG, "bad solve options");
+  hdg_solve_report r{};
+  const hdg_status s = gmres_solve(c, g, x, *o, r);
+  if (rep) *rep = r;
+  return s;
+}
+
+hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nrhs) {
+  if (!c) return HDG_ERR_ARG;
+  if (!x || !u || !q || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_recover before hdg_condense");
+  const Params& P = c->prm;
+  const double* gh = c->gD_qp ? c->d_ghat : nullptr;
+  cudaError_t e;
+  if (c->flags & HDG_KEEP_FACTORS) {
+    e = launch_recover(P, c->dt, c->d_ws, 0, P.N, 1, x, gh, u, q, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "recover");
+  } else {
+    for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
+      const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
+      e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, 0, 0, nullptr, nullptr, nullptr,
+                          nullptr, nullptr, c->stream);
+      if (e != cudaSuccess) return cuda_err(c, e, "refactor");
+      e = launch_recover(P, c->dt, c->d_ws, e0, cnt, 0, x, gh, u, q, c->stream);
+      if (e != cudaSuccess) return cuda_err(c, e, "recover");
+    }
+  }
+  return HDG_OK;
+}
+
+hdg_status hdg_get_schur(hdg_ctx* c, int64_t e0, int64_t count, double* S) {
+  if (!c) return HDG_ERR_ARG;
+  if (!S || e0 < 0 || count < 1 || e0 + count > c->prm.N) return set_err(c, HDG_ERR_ARG, "bad element range");
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_get_schur before hdg_condense");
+  cudaError_t e = launch_get_schur(c->prm, c->d_S, e0, count, S, c->stream);
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_get_schur");
+}
+
+hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host, const hdg_solve_opts* o,
+                        double* x_host, double* u_host, double* q_host, hdg_solve_report* rep) {
+  if (!c) return HDG_ERR_ARG;
+  if (!f_host || !o) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  const Params& P = c->prm;
+  const size_t nf = (size_t)P.N * P.n_qp, ng = (size_t)P.n_bnd * P.n_bqp;
+  const size_t nu = (size_t)P.N * P.Q;
+  double *df = nullptr, *dg = nullptr, *dx = nullptr, *du = nullptr, *dq = nullptr, *dgv = nullptr;
+  cudaError_t e = cudaSuccess;
+  hdg_status s = HDG_OK;
+  auto cleanup = [&]() {
+    cudaFree(df); cudaFree(dg); cudaFree(dx); cudaFree(du); cudaFree(dq); cudaFree(dgv);
+  };
+  if ((e = cudaMalloc(&df, nf * 8)) != cudaSuccess || (gD_host && (e = cudaMalloc(&dg, ng * 8)) != cudaSuccess) ||
+      (e = cudaMalloc(&dx, (size_t)P.N_tr * 8)) != cudaSuccess || (e = cudaMalloc(&dgv, (size_t)P.N_tr * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&du, nu * 8)) != cudaSuccess || (e = cudaMalloc(&dq, 2 * nu * 8)) != cudaSuccess) {
+    cleanup();
+    return cuda_err(c, e, "hdg_run_host buffers");
+  }
+  if ((e = cudaMemcpyAsync(df, f_host, nf * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (gD_host && (e = cudaMemcpyAsync(dg, gD_host, ng * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(dx, 0, (size_t)P.N_tr * 8, c->stream)) != cudaSuccess) {
+    cleanup();
+    return cuda_err(c, e, "hdg_run_host upload");
+  }
+  if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, HDG_KEEP_FACTORS)) == HDG_OK &&
+      (s = hdg_rhs(c, dgv)) == HDG_OK) {
+    s = hdg_solve(c, dgv, dx, 1, o, rep);
+    if (s == HDG_OK || s == HDG_ERR_NOCONV) {
+      const hdg_status s2 = hdg_recover(c, dx, du, dq, 1);
+      if (s2 != HDG_OK) s = s2;
+    }
+  }
+  if (s == HDG_OK || s == HDG_ERR_NOCONV) {
+    if ((x_host && (e = cudaMemcpyAsync(x_host, dx, (size_t)P.N_tr * 8, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) ||
+        (u_host && (e = cudaMemcpyAsync(u_host, du, nu * 8, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) ||
+        (q_host && (e = cudaMemcpyAsync(q_host, dq, 2 * nu * 8, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+      s = cuda_err(c, e, "hdg_run_host download");
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  // the staged source buffers are released: a new hdg_set_source is required
+  c->f_qp = nullptr;
+  c->gD_qp = nullptr;
+  c->state = 0;
+  cleanup();
+  return s;
+}
+
+const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void hdg_destroy(hdg_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
+  cudaFree(c->d_St32); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
+  cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
+  cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_x32);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Matrix-free trace-operator apply (Sec. 3.3.2, steps 1-4) over stored Schur
+// blocks, edge-centric so that step 4 (the face reduction) needs no second
+// pass and no atomics.
+//
+// Steps 1-3 of the paper, v^_e = C_e A_e^-1 B_e u^_e, are folded into the
+// stored S_e = D_e - C_e A_e^-1 B_e (Eq. global_problem); step 4 sums the two
+// element sides of every interior face in a fixed order (deterministic):
+//   y_f = (S_{e+} x_{e+})|_f + (S_{e-} x_{e-})|_f .
+// With the D^-1 preconditioner of Sec. 6.1, D_f = -(tau+ + tau-) L_f Gh (the
+// advective parts cancel across a face), so D_f^-1 = scale_f Gh^-1; Gh^-1 is
+// folded into the stored row-blocks at condensation and step 4 reduces to a
+// per-face scale.
+//
+// One thread per (interior edge, trace position); a CTA covers EPB whole
+// edges, stages the two element trace vectors of each edge in shared memory
+// (gathered with orientation flips, Dirichlet edges contribute 0) and streams
+// the matching row-blocks S[e][k][j][t] (contiguous in t) from HBM.
+#include "internal.h"
+
+namespace mehdg {
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restrict__ S, const T* __restrict__ x,
+                                                    T* __restrict__ y, const double* __restrict__ escale,
+                                                    int epb, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ unsigned char sraw[];
+  Acc* xs = reinterpret_cast<Acc*>(sraw);   // [epb][2][n_t]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  const int f0 = blockIdx.x * epb;
+  const int tid = threadIdx.x;
+
+  // gather the element trace vectors of both sides of every edge of the CTA
+  for (int idx = tid; idx < epb * 2 * nt; idx += blockDim.x) {
+    const int le = idx / (2 * nt);
+    const int rem = idx - le * 2 * nt;
+    const int sd = rem / nt, c = rem - sd * nt;
+    const int f = f0 + le;
+    Acc v = Acc(0);
+    if (f < P.n_int) {
+      int e[2], k[2], fl[2];
+      double len;
+      edge_sides(f, P.n, e, k, fl, &len);
+      int code[3], flip[3];
+      elem_edges(e[sd], P.n, code, flip);
+      const int kk = c / P1, t = c - kk * P1;
+      if (code[kk] >= 0) v = Acc(x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)]);
+    }
+    xs[idx] = v;
+  }
+  __syncthreads();
+
+  const int le = tid / P1, s = tid - le * P1;
+  const int f = f0 + le;
+  if (le >= epb || f >= P.n_int) return;
+  int e[2], k[2], fl[2];
+  double len;
+  edge_sides(f, P.n, e, k, fl, &len);
+  Acc acc0 = Acc(0), acc1 = Acc(0);
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int t = fl[sd] ? PP - s : s;
+    const T* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + t;
+    const Acc* xv = xs + (le * 2 + sd) * nt;
+    int j = 0;
+    for (; j + 4 <= nt; j += 4) {
+      const Acc s0 = Acc(base[(size_t)(j + 0) * P1]);
+      const Acc s1 = Acc(base[(size_t)(j + 1) * P1]);
+      const Acc s2 = Acc(base[(size_t)(j + 2) * P1]);
+      const Acc s3 = Acc(base[(size_t)(j + 3) * P1]);
+      acc0 += s0 * xv[j + 0];
+      acc1 += s1 * xv[j + 1];
+      acc0 += s2 * xv[j + 2];
+      acc1 += s3 * xv[j + 3];
+    }
+    for (; j < nt; ++j) acc0 += Acc(base[(size_t)j * P1]) * xv[j];
+  }
+  Acc r = acc0 + acc1;
+  if (escale) r *= Acc(escale[f]);
+  y[(size_t)f * P1 + s] = T(r);
+}
+
+int apply_edges_per_block(const Params& P) {
+  int epb = 256 / P.P1;
+  return epb < 1 ? 1 : epb;
+}
+
+cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
+                           const int* stop, cudaStream_t st) {
+  const int epb = apply_edges_per_block(P);
+  const int grid = (P.n_int + epb - 1) / epb;
+  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(double);
+  apply_kernel<double, double><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply32(const Params& P, const float* S, const float* x, float* y, const double* escale,
+                           const int* stop, cudaStream_t st) {
+  const int epb = apply_edges_per_block(P);
+  const int grid = (P.n_int + epb - 1) / epb;
+  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float);
+  apply_kernel<float, float><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
+}
+
+// Assembled right-hand side: g_f = gel_{e+}|_f + gel_{e-}|_f (fixed order).
+__global__ void assemble_rhs_kernel(Params P, const double* gel, double* g) {
+  const int64_t total = (int64_t)P.n_int * P.P1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / P.P1), s = (int)(idx - (int64_t)f * P.P1);
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    double acc = 0.0;
+    for (int sd = 0; sd < 2; ++sd) {
+      const int t = fl[sd] ? P.P - s : s;
+      acc += gel[(size_t)e[sd] * P.n_t + k[sd] * P.P1 + t];
+    }
+    g[idx] = acc;
+  }
+}
+
+// Face preconditioner on a vector: z_f = scale_f Gh^-1 y_f (Sec. 6.1).
+__global__ void face_dinv_kernel(Params P, const double* Ghinv, const double* escale, const double* y, double* z) {
+  const int64_t total = (int64_t)P.n_int * P.P1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / P.P1), s = (int)(idx - (int64_t)f * P.P1);
+    const double* yf = y + (size_t)f * P.P1;
+    double acc = 0.0;
+    for (int t = 0; t < P.P1; ++t) acc += Ghinv[s * P.P1 + t] * yf[t];
+    z[idx] = escale[f] * acc;
+  }
+}
+
+// Per-face scale -1 / ((tau+ + tau-) L_f) of D_f^-1.
+__global__ void face_scale_kernel(Params P, const double* kappa, double* escale) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < P.n_int; f += gridDim.x * blockDim.x) {
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    const double tsum = kappa[e[0]] / P.tau_len + kappa[e[1]] / P.tau_len + 2.0 * P.babs;
+    escale[f] = -1.0 / (tsum * len);
+  }
+}
+
+cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st) {
+  assemble_rhs_kernel<<<1024, 256, 0, st>>>(P, gel, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
+                             cudaStream_t st) {
+  face_dinv_kernel<<<1024, 256, 0, st>>>(P, Ghinv, escale, y, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_scale(const Params& P, const double* kappa, double* escale, cudaStream_t st) {
+  face_scale_kernel<<<256, 256, 0, st>>>(P, kappa, escale);
+  return cudaGetLastError();
+}
+
+}  // namespace mehdg

@@ -1,0 +1,472 @@
+// Batched static condensation of every macro-element (Eqs. global_problem and
+// local_problem; block system Eq. D; element formation Sec. 6.1; LU remark of
+// Sec. 3.3.2). One CTA per macro-element.
+//
+// Each CTA forms its element's bordered system in FP64
+//
+//          [ A_u  B_u  F ]     rows 0 .. Q-1      : u-equations after eliminating q
+//      W = [ C_u  D_u  0 ]     rows Q .. Q+n_t-1  : trace equations
+//
+// where (q eliminated exactly through q_x = M^-1 (Dx u - Fx u^), q_y alike)
+//   A_u = kappa (Dx^T M^-1 Dx + Dy^T M^-1 Dy) - (beta_x Dx + beta_y Dy) + tau E
+//   B_u = Fa - tau F - kappa (Dx^T M^-1 Fx + Dy^T M^-1 Fy)
+//   C_u = kappa (Fx^T M^-1 Dx + Fy^T M^-1 Dy) + tau F^T
+//   D_u = Ga - tau G - kappa (Fx^T M^-1 Fx + Fy^T M^-1 Fy)
+// and eliminates the first Q columns with partial pivoting restricted to the
+// u-rows (blocked right-looking LU, panel width NB). The trailing block then
+// holds [S_e | -C A^-1 R] with S_e = D_e - C_e A_e^-1 B_e, and rows 0..Q-1
+// hold U, L^-1 P B_u and L^-1 P F for the back-solve.
+#include "internal.h"
+
+namespace mehdg {
+
+constexpr int NB = 16;        // panel width
+constexpr int LDP = NB + 1;   // padded panel row stride (bank spread for column scans)
+constexpr int RT = 8;         // rows per trailing-update work item
+
+struct CondArgs {
+  Params prm;
+  DevTables dt;
+  const double* kappa;
+  const double* f_qp;
+  const double* ghat;
+  double* ws;
+  int64_t e0;
+  int slot_is_element;    // 1: workspace slot = element id; 0: slot = blockIdx.x
+  int write_outputs;
+  double* S;
+  double* St;
+  float* St32;
+  double* gel;
+  int* info;
+};
+
+__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, off);
+    const int oi = __shfl_down_sync(0xffffffffu, i, off);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+
+__global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
+  const Params& P = a.prm;
+  const int e = (int)(a.e0 + blockIdx.x);
+  if (e >= P.N) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, Cc = P.Cc, ld = P.ld;
+  double* W = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)R * ld;
+
+  extern __shared__ double smem[];
+  double* Ls = smem;                       // [R][LDP]
+  double* Us = smem + (size_t)R * LDP;     // [NB][ld]
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int piv_s[NB];
+
+  // ---------------------------------------------------------- element data
+  ElemGeom g;
+  elem_geom(e, P.n, g);
+  const double kap = a.kappa[e];
+  const double tau = kap / P.tau_len + P.babs;
+  const double gxx = g.gxi[0] * g.gxi[0] + g.gxi[1] * g.gxi[1];
+  const double gxy = g.gxi[0] * g.geta[0] + g.gxi[1] * g.geta[1];
+  const double gyy = g.geta[0] * g.geta[0] + g.geta[1] * g.geta[1];
+  const double bxi = P.bx * g.gxi[0] + P.by * g.gxi[1];
+  const double beta_ = P.bx * g.geta[0] + P.by * g.geta[1];
+  double nxi[3], neta[3], bn[3];
+  for (int k = 0; k < 3; ++k) {
+    nxi[k] = g.nrm[k][0] * g.gxi[0] + g.nrm[k][1] * g.gxi[1];
+    neta[k] = g.nrm[k][0] * g.geta[0] + g.nrm[k][1] * g.geta[1];
+    bn[k] = P.bx * g.nrm[k][0] + P.by * g.nrm[k][1];
+  }
+  const double cK = kap * g.detJ;
+
+  // source: per sub-triangle projections into Ls (free before the LU starts)
+  double* proj = Ls;
+  {
+    const double* fe = a.f_qp + (size_t)e * P.n_qp;
+    for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
+      const int s = idx / P.nloc, b = idx - s * P.nloc;
+      double acc = 0.0;
+      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
+      proj[idx] = acc;
+    }
+  }
+  __syncthreads();
+
+  // --------------------------------------------------- form the bordered system
+  for (int i = 0; i < R; ++i) {
+    double* row = W + (size_t)i * ld;
+    if (i < Q) {
+      const size_t qi = (size_t)i * Q;
+      for (int j = tid; j < ld; j += nthr) {
+        double v;
+        if (j < Q) {
+          v = cK * (gxx * a.dt.Kxx[qi + j] + gxy * a.dt.Ksym[qi + j] + gyy * a.dt.Kyy[qi + j])
+              - g.detJ * (bxi * a.dt.Dxi[qi + j] + beta_ * a.dt.Deta[qi + j]);
+        } else if (j < Q + nt) {
+          const int c = j - Q, k = c / P1;
+          const size_t ic = (size_t)i * nt + c;
+          v = g.L[k] * ((bn[k] - tau) * a.dt.Fh[ic] - kap * (nxi[k] * a.dt.Pxi[ic] + neta[k] * a.dt.Peta[ic]));
+        } else if (j == Q + nt) {
+          double acc = 0.0;
+          for (int q = a.dt.ns_ptr[i]; q < a.dt.ns_ptr[i + 1]; ++q) acc += proj[a.dt.ns_idx[q]];
+          v = acc * g.detJ / (double)(P.m * P.m);
+        } else {
+          v = 0.0;
+        }
+        row[j] = v;
+      }
+    } else {
+      const int r = i - Q, k = r / P1, t = r - k * P1;
+      for (int j = tid; j < ld; j += nthr) {
+        double v;
+        if (j < Q) {
+          const size_t jr = (size_t)j * nt + r;
+          v = g.L[k] * (kap * (nxi[k] * a.dt.Pxi[jr] + neta[k] * a.dt.Peta[jr]) + tau * a.dt.Fh[jr]);
+        } else if (j < Q + nt) {
+          const int c = j - Q, l = c / P1, t2 = c - l * P1;
+          const double nn = g.nrm[k][0] * g.nrm[l][0] + g.nrm[k][1] * g.nrm[l][1];
+          v = -kap * g.L[k] * g.L[l] * nn / g.detJ * a.dt.Hh[(size_t)r * nt + c];
+          if (l == k) v += g.L[k] * (bn[k] - tau) * a.dt.Gh[t * P1 + t2];
+        } else {
+          v = 0.0;
+        }
+        row[j] = v;
+      }
+    }
+  }
+  __syncthreads();
+  // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
+  for (int k = 0; k < 3; ++k) {
+    for (int idx = tid; idx < P1 * P1; idx += nthr) {
+      const int t = idx / P1, t2 = idx - t * P1;
+      const int ni = a.dt.enode[k * P1 + t], nj = a.dt.enode[k * P1 + t2];
+      W[(size_t)ni * ld + nj] += tau * g.L[k] * a.dt.Gh[idx];
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------- blocked LU, Q pivots
+  int singular_col = -1;
+  for (int j0 = 0; j0 < Q; j0 += NB) {
+    const int nb = min(NB, Q - j0);
+    const int rows = R - j0;
+    for (int idx = tid; idx < rows * NB; idx += nthr) {
+      const int r = idx / NB, c = idx - r * NB;
+      Ls[r * LDP + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+      // pivot: largest |a| among u-rows j0+c .. Q-1 (first one on ties)
+      double best = -1.0;
+      int bi = c;
+      for (int r = c + tid; r < Q - j0; r += nthr) {
+        const double v = fabs(Ls[r * LDP + c]);
+        if (v > best) { best = v; bi = r; }
+      }
+      warp_argmax(best, bi);
+      if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid < 32) {
+        const int nw = nthr >> 5;
+        double v = tid < nw ? red_v[tid] : -1.0;
+        int ii = tid < nw ? red_i[tid] : 0x7fffffff;
+        warp_argmax(v, ii);
+        if (tid == 0) piv_s[c] = ii;
+      }
+      __syncthreads();
+      const int pr = piv_s[c];
+      if (pr != c) {
+        for (int cc = tid; cc < nb; cc += nthr) {
+          const double t0 = Ls[c * LDP + cc];
+          Ls[c * LDP + cc] = Ls[pr * LDP + cc];
+          Ls[pr * LDP + cc] = t0;
+        }
+        __syncthreads();
+      }
+      const double d = Ls[c * LDP + c];
+      if (d == 0.0 && singular_col < 0) singular_col = j0 + c;
+      const double inv = (d != 0.0) ? 1.0 / d : 0.0;
+      for (int r = c + 1 + tid; r < rows; r += nthr) Ls[r * LDP + c] *= inv;
+      __syncthreads();
+      const int nrem = nb - c - 1;
+      if (nrem > 0) {
+        const int nr = rows - c - 1;
+        for (int idx = tid; idx < nr * nrem; idx += nthr) {
+          const int r = c + 1 + idx / nrem, cc = c + 1 + idx % nrem;
+          Ls[r * LDP + cc] -= Ls[r * LDP + c] * Ls[c * LDP + cc];
+        }
+        __syncthreads();
+      }
+    }
+    for (int idx = tid; idx < rows * nb; idx += nthr) {
+      const int r = idx / nb, c = idx - r * nb;
+      W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDP + c];
+    }
+    const int jb = j0 + nb, ncol = Cc - jb;
+    if (ncol > 0) {
+      // row interchanges and U12 = L11^-1 A12, one column per thread
+      for (int j = jb + tid; j < Cc; j += nthr) {
+        double u[NB];
+        for (int c = 0; c < nb; ++c) {
+          const int pr = piv_s[c];
+          if (pr != c) {
+            double* x0 = W + (size_t)(j0 + c) * ld + j;
+            double* x1 = W + (size_t)(j0 + pr) * ld + j;
+            const double t0 = *x0;
+            *x0 = *x1;
+            *x1 = t0;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : 0.0;
+#pragma unroll
+        for (int c = 1; c < NB; ++c) {
+          if (c < nb) {
+            double s = u[c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) s -= Ls[c * LDP + t] * u[t];
+            u[c] = s;
+          }
+        }
+        for (int c = 0; c < nb; ++c) {
+          W[(size_t)(j0 + c) * ld + j] = u[c];
+          Us[c * ld + j] = u[c];
+        }
+      }
+      __syncthreads();
+      // trailing update A22 -= L21 U12 (rows jb..R-1, columns jb..Cc-1)
+      const int nrow = R - jb;
+      const int ntile = (nrow + RT - 1) / RT;
+      for (int item = tid; item < ntile * ncol; item += nthr) {
+        const int rt = item / ncol, j = jb + (item - rt * ncol);
+        double u[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? Us[c * ld + j] : 0.0;
+        const int r0 = jb + rt * RT;
+        const int r1 = min(r0 + RT, R);
+        for (int r = r0; r < r1; ++r) {
+          double* wp = W + (size_t)r * ld + j;
+          const double* l = Ls + (r - j0) * LDP;
+          double acc = *wp;
+#pragma unroll
+          for (int c = 0; c < NB; ++c) acc -= l[c] * u[c];
+          *wp = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && a.info) a.info[e] = singular_col >= 0 ? singular_col + 1 : 0;
+  if (!a.write_outputs) return;
+
+  // ------------------------------------------------------------- outputs
+  // S_e row-blocks per local edge: S[e][k][j][t] = S_e(k P1 + t, j)
+  const size_t sb = (size_t)e * 3 * nt * P1;
+  for (int idx = tid; idx < nt * nt; idx += nthr) {
+    const int j = idx / nt, r = idx - j * nt;
+    const int k = r / P1, t = r - k * P1;
+    a.S[sb + ((size_t)k * nt + j) * P1 + t] = W[(size_t)(Q + r) * ld + Q + j];
+  }
+  // preconditioned rows: Gh^-1 applied to each edge block of rows
+  for (int idx = tid; idx < nt * nt; idx += nthr) {
+    const int j = idx / nt, r = idx - j * nt;
+    const int k = r / P1, t = r - k * P1;
+    double acc = 0.0;
+    for (int t2 = 0; t2 < P1; ++t2) acc += a.dt.Ghinv[t * P1 + t2] * W[(size_t)(Q + k * P1 + t2) * ld + Q + j];
+    const size_t o = sb + ((size_t)k * nt + j) * P1 + t;
+    a.St[o] = acc;
+    if (a.St32) a.St32[o] = (float)acc;
+  }
+  // element right-hand side -C A^-1 R - S_e g^_e
+  int code[3], flip[3];
+  elem_edges(e, P.n, code, flip);
+  for (int r = tid; r < nt; r += nthr) {
+    double acc = W[(size_t)(Q + r) * ld + Q + nt];
+    if (a.ghat) {
+      for (int k = 0; k < 3; ++k) {
+        if (code[k] >= 0) continue;
+        const double* gb = a.ghat + (size_t)(-1 - code[k]) * P1;
+        for (int t = 0; t < P1; ++t)
+          acc -= W[(size_t)(Q + r) * ld + Q + k * P1 + t] * gb[flip[k] ? P.P - t : t];
+      }
+    }
+    a.gel[(size_t)e * nt + r] = acc;
+  }
+}
+
+// Back-solve Eq. (local_matrix_problem) on the factored bordered system:
+// U u = L^-1 P (F - B_u u^_e), then q = M^-1 (D u - F u^) per component.
+struct RecArgs {
+  Params prm;
+  DevTables dt;
+  const double* ws;
+  int64_t e0;
+  int slot_is_element;
+  const double* x;
+  const double* ghat;
+  double* u;
+  double* q;
+};
+
+__global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
+  const Params& P = a.prm;
+  const int e = (int)(a.e0 + blockIdx.x);
+  if (e >= P.N) return;
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, ld = P.ld;
+  const double* W = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)P.R * ld;
+  extern __shared__ double sm[];
+  double* xe = sm;             // n_t
+  double* rhs = xe + nt;       // Q
+  double* uu = rhs + Q;        // Q
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+
+  int code[3], flip[3];
+  elem_edges(e, P.n, code, flip);
+  for (int c = tid; c < nt; c += blockDim.x) {
+    const int k = c / P1, t = c - k * P1;
+    const int s = flip[k] ? P.P - t : t;
+    double v = 0.0;
+    if (code[k] >= 0) v = a.x[(size_t)code[k] * P1 + s];
+    else if (a.ghat) v = a.ghat[(size_t)(-1 - code[k]) * P1 + s];
+    xe[c] = v;
+  }
+  __syncthreads();
+  // rhs = c - W x_e, one warp per row
+  for (int i = warp; i < Q; i += nw) {
+    const double* row = W + (size_t)i * ld + Q;
+    double acc = 0.0;
+    for (int c = lane; c < nt; c += 32) acc += row[c] * xe[c];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) rhs[i] = row[nt] - acc;
+  }
+  __syncthreads();
+  // back substitution by warp 0
+  if (warp == 0) {
+    for (int i = Q - 1; i >= 0; --i) {
+      const double* row = W + (size_t)i * ld;
+      double acc = 0.0;
+      for (int j = i + 1 + lane; j < Q; j += 32) acc += row[j] * uu[j];
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) uu[i] = (rhs[i] - acc) / row[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  ElemGeom g;
+  elem_geom(e, P.n, g);
+  double* ue = a.u + (size_t)e * Q;
+  double* qe = a.q + (size_t)e * 2 * Q;
+  for (int i = warp; i < Q; i += nw) {
+    const double* xr = a.dt.Xxi + (size_t)i * Q;
+    const double* yr = a.dt.Xeta + (size_t)i * Q;
+    double sx = 0.0, sy = 0.0;
+    for (int j = lane; j < Q; j += 32) {
+      sx += xr[j] * uu[j];
+      sy += yr[j] * uu[j];
+    }
+    const double* fr = a.dt.Yh + (size_t)i * nt;
+    double cx = 0.0, cy = 0.0;
+    for (int c = lane; c < nt; c += 32) {
+      const int k = c / P1;
+      const double v = fr[c] * xe[c] * g.L[k];
+      cx += g.nrm[k][0] * v;
+      cy += g.nrm[k][1] * v;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      sx += __shfl_down_sync(0xffffffffu, sx, off);
+      sy += __shfl_down_sync(0xffffffffu, sy, off);
+      cx += __shfl_down_sync(0xffffffffu, cx, off);
+      cy += __shfl_down_sync(0xffffffffu, cy, off);
+    }
+    if (lane == 0) {
+      // grad_x = gxi_x d_xi + geta_x d_eta, and M^-1 = Mh^-1 / detJ
+      qe[i] = g.gxi[0] * sx + g.geta[0] * sy - cx / g.detJ;
+      qe[Q + i] = g.gxi[1] * sx + g.geta[1] * sy - cy / g.detJ;
+      ue[i] = uu[i];
+    }
+  }
+}
+
+// Dirichlet data: g^ = L2 projection of g_D on every boundary edge (Sec. 2.3).
+__global__ void project_dirichlet_kernel(Params P, DevTables dt, const double* gD, double* ghat) {
+  const int b = blockIdx.x;
+  if (b >= P.n_bnd) return;
+  extern __shared__ double rhs[];
+  for (int t = threadIdx.x; t < P.P1; t += blockDim.x) rhs[t] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* gb = gD + (size_t)b * P.n_bqp;
+    for (int s = 0; s < P.m; ++s)
+      for (int q = 0; q < P.ngb; ++q) {
+        const double w = dt.bw[q] / P.m * gb[s * P.ngb + q];
+        for (int r = 0; r <= P.p; ++r) rhs[s * P.p + r] += w * dt.bpsi[q * (P.p + 1) + r];
+      }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P.P1; t += blockDim.x) {
+    double acc = 0.0;
+    for (int t2 = 0; t2 < P.P1; ++t2) acc += dt.Ghinv[t * P.P1 + t2] * rhs[t2];
+    ghat[(size_t)b * P.P1 + t] = acc;
+  }
+}
+
+// Gather S_e from the row-block layout into row-major [count][n_t][n_t].
+__global__ void get_schur_kernel(Params P, const double* S, int64_t e0, int64_t count, double* out) {
+  const int64_t total = count * P.n_t * P.n_t;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t el = idx / (P.n_t * P.n_t);
+    const int rc = (int)(idx - el * P.n_t * P.n_t);
+    const int r = rc / P.n_t, c = rc - r * P.n_t;
+    const int k = r / P.P1, t = r - k * P.P1;
+    out[idx] = S[(size_t)(e0 + el) * 3 * P.n_t * P.P1 + ((size_t)k * P.n_t + c) * P.P1 + t];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+size_t condense_smem_bytes(const Params& P) {
+  return ((size_t)P.R * LDP + (size_t)NB * P.ld) * sizeof(double);
+}
+
+cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
+                            const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
+                            int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
+                            cudaStream_t st) {
+  CondArgs a;
+  a.prm = P; a.dt = dt; a.kappa = kappa; a.f_qp = f_qp; a.ghat = ghat; a.ws = ws; a.e0 = e0;
+  a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
+  a.S = S; a.St = St; a.St32 = St32; a.gel = gel; a.info = info;
+  const size_t sm = condense_smem_bytes(P);
+  cudaError_t err = cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (err != cudaSuccess) return err;
+  condense_kernel<<<(unsigned)count, 256, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
+                           int slot_is_element, const double* x, const double* ghat, double* u, double* q,
+                           cudaStream_t st) {
+  RecArgs a;
+  a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element;
+  a.x = x; a.ghat = ghat; a.u = u; a.q = q;
+  const size_t sm = (size_t)(P.n_t + 2 * P.Q) * sizeof(double);
+  recover_kernel<<<(unsigned)count, 128, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_dirichlet(const Params& P, const DevTables& dt, const double* gD, double* ghat,
+                                     cudaStream_t st) {
+  project_dirichlet_kernel<<<P.n_bnd, 64, P.P1 * sizeof(double), st>>>(P, dt, gD, ghat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64_t count, double* out,
+                             cudaStream_t st) {
+  get_schur_kernel<<<1024, 256, 0, st>>>(P, S, e0, count, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mehdg

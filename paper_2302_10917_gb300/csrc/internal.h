@@ -1,0 +1,190 @@
+// Internal declarations of the macro-element HDG library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/mehdg.h"
+
+namespace mehdg {
+
+// ---------------------------------------------------------------------------
+// Reference tables of one refinement level (m, p), computed once on the host
+// (reference.cpp) and copied to the device. All matrices are row-major FP64.
+//   Mh          Q x Q     int phi_j phi_i              (reference triangle)
+//   Dxi, Deta   Q x Q     int phi_j d_xi phi_i, ...    (row = differentiated test fn)
+//   Kxx, Kyy    Q x Q     Dxi^T Mh^-1 Dxi, Deta^T Mh^-1 Deta
+//   Ksym        Q x Q     Dxi^T Mh^-1 Deta + Deta^T Mh^-1 Dxi
+//   Xxi, Xeta   Q x Q     Mh^-1 Dxi, Mh^-1 Deta        (recovery of q)
+//   Fh          Q x 3P1   int_0^1 psi_t phi_i ds on reference edge k (block k)
+//   Pxi, Peta   Q x 3P1   Dxi^T Mh^-1 Fh, Deta^T Mh^-1 Fh
+//   Yh          Q x 3P1   Mh^-1 Fh
+//   Hh          3P1 x 3P1 Fh^T Mh^-1 Fh
+//   Gh, Ghinv   P1 x P1   1D C0 trace mass on [0,1] (m sub-intervals) and inverse
+//   enode       3 x P1    lattice node of position t along reference edge k
+//   phiq        nqs x nloc  P_p basis of a sub-triangle at its source points
+//   wq          nqs        source weights on the unit triangle (sum 1/2)
+//   subnode     nsub x nloc lattice node of each local basis function
+//   node_sub    CSR over lattice nodes -> (sub-triangle, local index)
+//   bpsi        ngb x (p+1) 1D basis at the boundary Gauss points, bw weights
+// ---------------------------------------------------------------------------
+struct RefTables {
+  int m = 0, p = 0, P = 0, P1 = 0, Q = 0, n_t = 0;
+  int ng = 0, nqs = 0, nloc = 0, nsub = 0, ngb = 0;
+  std::vector<double> Mh, Dxi, Deta, Kxx, Kyy, Ksym, Xxi, Xeta;
+  std::vector<double> Fh, Pxi, Peta, Yh, Hh, Gh, Ghinv;
+  std::vector<int> enode;
+  std::vector<double> phiq, wq, uq;     // uq: Gauss nodes on [0,1] (ng)
+  std::vector<int> subtri;              // nsub x 6 corners (a,b) in units of 1/m
+  std::vector<int> subnode;
+  std::vector<int> ns_ptr, ns_idx;      // CSR: node -> entries s * nloc + a
+  std::vector<double> bpsi, bw, bu;     // boundary rule: nodes bu, weights bw (ngb)
+};
+
+// Builds the tables of level (m, p). Throws std::runtime_error on failure.
+void build_reference_tables(int m, int p, RefTables& T);
+
+// Device copies of the reference tables (pointers into one allocation).
+struct DevTables {
+  double *Dxi, *Deta, *Kxx, *Kyy, *Ksym, *Xxi, *Xeta;
+  double *Fh, *Pxi, *Peta, *Yh, *Hh, *Gh, *Ghinv;
+  int* enode;
+  double *phiq, *wq, *uq;
+  int *subtri, *subnode, *ns_ptr, *ns_idx;
+  double *bpsi, *bw, *bu;
+};
+
+// Scalar problem parameters passed by value to kernels.
+struct Params {
+  int n, m, p, P, P1, Q, n_t;
+  int N, n_int, n_bnd, N_tr;
+  int ng, nqs, nloc, nsub, n_qp, ngb, n_bqp;
+  double bx, by, babs, kappa0, tau_len;
+  int R, Cc, ld;         // bordered local system: rows, used columns, leading dimension
+};
+
+// ---------------------------------------------------------------------------
+// Structured-mesh geometry (closed form, host and device).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void elem_vertices(int e, int n, double v[3][2]) {
+  const int sq = e >> 1, t = e & 1;
+  const int j = sq / n, i = sq - j * n;
+  const double h = 1.0 / n;
+  const double x0 = i * h, x1 = (i + 1) * h, y0 = j * h, y1 = (j + 1) * h;
+  if (t == 0) {
+    v[0][0] = x1; v[0][1] = y0; v[1][0] = x1; v[1][1] = y1; v[2][0] = x0; v[2][1] = y0;
+  } else {
+    v[0][0] = x0; v[0][1] = y1; v[1][0] = x0; v[1][1] = y0; v[2][0] = x1; v[2][1] = y1;
+  }
+}
+
+// Local edge k of element e -> code (>= 0: interior edge id; < 0: -1 - boundary id), flip.
+__host__ __device__ inline void elem_edges(int e, int n, int code[3], int flip[3]) {
+  const int sq = e >> 1, t = e & 1;
+  const int j = sq / n, i = sq - j * n;
+  const int nn = n * n;
+  auto horiz = [&](int ii, int jj) -> int {
+    if (jj == 0) return -1 - ii;
+    if (jj == n) return -1 - (n + ii);
+    return nn + (jj - 1) * n + ii;
+  };
+  auto vert = [&](int ii, int jj) -> int {
+    if (ii == 0) return -1 - (2 * n + jj);
+    if (ii == n) return -1 - (3 * n + jj);
+    return nn + n * (n - 1) + jj * (n - 1) + (ii - 1);
+  };
+  code[0] = j * n + i;
+  if (t == 0) {
+    flip[0] = 1; code[1] = horiz(i, j); flip[1] = 0; code[2] = vert(i + 1, j); flip[2] = 0;
+  } else {
+    flip[0] = 0; code[1] = horiz(i, j + 1); flip[1] = 1; code[2] = vert(i, j); flip[2] = 1;
+  }
+}
+
+// The two sides (element, local edge, flip) of interior edge f; also its length.
+__host__ __device__ inline void edge_sides(int f, int n, int e[2], int k[2], int fl[2], double* len) {
+  const int nn = n * n;
+  const double h = 1.0 / n;
+  if (f < nn) {
+    const int j = f / n, i = f - j * n;
+    e[0] = 2 * (j * n + i); k[0] = 0; fl[0] = 1;
+    e[1] = 2 * (j * n + i) + 1; k[1] = 0; fl[1] = 0;
+    *len = h * 1.4142135623730951;
+  } else if (f < nn + n * (n - 1)) {
+    const int r = f - nn, j = 1 + r / n, i = r % n;
+    e[0] = 2 * ((j - 1) * n + i) + 1; k[0] = 1; fl[0] = 1;   // square below, upper-left
+    e[1] = 2 * (j * n + i); k[1] = 1; fl[1] = 0;             // square above, lower-right
+    *len = h;
+  } else {
+    const int r = f - nn - n * (n - 1), j = r / (n - 1), i = 1 + r % (n - 1);
+    e[0] = 2 * (j * n + (i - 1)); k[0] = 2; fl[0] = 0;       // square left, lower-right
+    e[1] = 2 * (j * n + i) + 1; k[1] = 2; fl[1] = 1;         // square right, upper-left
+    *len = h;
+  }
+}
+
+// Affine map data of element e: det J, reference gradients, edge lengths and
+// outward normals (edge k from v_{k+1} to v_{k+2}).
+struct ElemGeom {
+  double detJ;
+  double gxi[2], geta[2];   // grad xi, grad eta (rows of J^-1)
+  double L[3], nrm[3][2];
+};
+
+__host__ __device__ inline void elem_geom(int e, int n, ElemGeom& g) {
+  double v[3][2];
+  elem_vertices(e, n, v);
+  const double J00 = v[1][0] - v[0][0], J10 = v[1][1] - v[0][1];
+  const double J01 = v[2][0] - v[0][0], J11 = v[2][1] - v[0][1];
+  g.detJ = J00 * J11 - J01 * J10;
+  const double id = 1.0 / g.detJ;
+  g.gxi[0] = J11 * id;  g.gxi[1] = -J01 * id;
+  g.geta[0] = -J10 * id; g.geta[1] = J00 * id;
+  for (int k = 0; k < 3; ++k) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    const double tx = v[b][0] - v[a][0], ty = v[b][1] - v[a][1];
+    const double L = sqrt(tx * tx + ty * ty);
+    g.L[k] = L;
+    g.nrm[k][0] = ty / L;
+    g.nrm[k][1] = -tx / L;
+  }
+}
+
+}  // namespace mehdg
+
+// ---------------------------------------------------------------------------
+// Context (opaque to callers).
+// ---------------------------------------------------------------------------
+struct hdg_ctx {
+  mehdg::Params prm;
+  mehdg::RefTables ref;
+  mehdg::DevTables dt;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int state = 0;            // 0 created, 1 source set, 2 condensed
+  unsigned flags = 0;
+  void* d_tables = nullptr;
+  double* d_kappa = nullptr;      // [N]
+  const double* f_qp = nullptr;   // caller-owned
+  const double* gD_qp = nullptr;  // caller-owned or null
+  double* d_ghat = nullptr;       // [n_bnd][P1]
+  double* d_S = nullptr;          // [N][3][n_t][P1]  S_e, row-blocks per edge
+  double* d_St = nullptr;         // [N][3][n_t][P1]  Gh^-1 S_e (preconditioned rows)
+  float* d_St32 = nullptr;        // FP32 copy of d_St
+  double* d_gel = nullptr;        // [N][n_t] element right-hand sides
+  double* d_g = nullptr;          // [N_tr] assembled right-hand side
+  double* d_ws = nullptr;         // factored bordered systems [slots][R][ld]
+  int64_t ws_slots = 0;
+  int* d_info = nullptr;          // [N] zero-pivot column + 1, or 0
+  double* d_escale = nullptr;     // [n_int] -1 / ((tau+ + tau-) L_f)
+  // Krylov workspace
+  double* d_V = nullptr;          // [restart + 1][N_tr]
+  double* d_w = nullptr;          // [N_tr]
+  double* d_r = nullptr;          // [N_tr]
+  double* d_part = nullptr;       // reduction partials
+  double* d_small = nullptr;      // Hessenberg, Givens, scalars
+  int* d_flag = nullptr;
+  float* d_x32 = nullptr;         // FP32 vectors for mode 1
+  int krylov_restart = 0;
+  size_t bytes = 0;
+};

@@ -1,0 +1,32 @@
+// Kernel launchers shared between the translation units of the library.
+#pragma once
+#include "internal.h"
+
+namespace mehdg {
+
+size_t condense_smem_bytes(const Params& P);
+cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
+                            const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
+                            int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
+                            cudaStream_t st);
+cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
+                           int slot_is_element, const double* x, const double* ghat, double* u, double* q,
+                           cudaStream_t st);
+cudaError_t launch_project_dirichlet(const Params& P, const DevTables& dt, const double* gD, double* ghat,
+                                     cudaStream_t st);
+cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64_t count, double* out,
+                             cudaStream_t st);
+
+cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
+                           const int* stop, cudaStream_t st);
+cudaError_t launch_apply32(const Params& P, const float* S, const float* x, float* y, const double* escale,
+                           const int* stop, cudaStream_t st);
+cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
+cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
+                             cudaStream_t st);
+cudaError_t launch_face_scale(const Params& P, const double* kappa, double* escale, cudaStream_t st);
+
+// Restarted GMRES on the condensed system (krylov.cu).
+hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep);
+
+}  // namespace mehdg

@@ -1,0 +1,301 @@
+// Reference-lattice tables of one refinement level (host set-up, run once per
+// context). Sec. 3.2: W(K), V(K) are C0 piecewise P_p on the uniform m-fold
+// subdivision of the reference triangle; M(F) is C0 piecewise P_p on the m
+// sub-edges of a macro-edge. Every element matrix of the affine macro-element
+// is a linear combination of the tables built here (element formation,
+// Sec. 6.1), with coefficients from the element's Jacobian, kappa, tau and beta.
+//
+// The tables that involve Mh^-1 come from eliminating q = -grad u inside each
+// macro-element: the q-rows of A_e read M q_x - Dx u + Fx u^ = 0, so
+// q_x = M^-1 (Dx u - Fx u^); M^-1 D and M^-1 F scale with the affine map, so
+// Dx^T M^-1 Dx etc. are fixed reference matrices times element scalars.
+#include <cmath>
+#include <stdexcept>
+#include "internal.h"
+
+namespace mehdg {
+namespace {
+
+// Gauss-Legendre nodes and weights on [0,1] by Newton iteration on P_n.
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p0 = 1.0; p1 = z; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    // roots come out in decreasing order of z; store ascending on [0,1]
+    x[n - 1 - i] = 0.5 * (1.0 + z);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// P_p Lagrange basis of one triangle at barycentric point lam, multi-indices al.
+// val[b], dl[b][k] = d phi_b / d lambda_k.
+void lagrange_tri(int p, const std::vector<int>& al, int nloc, const double lam[3],
+                  double* val, double (*dl)[3]) {
+  for (int b = 0; b < nloc; ++b) {
+    double f[3], df[3];
+    for (int k = 0; k < 3; ++k) {
+      double v = 1.0, d = 0.0;
+      for (int j = 0; j < al[3 * b + k]; ++j) {
+        const double g = (p * lam[k] - j) / (j + 1.0);
+        d = d * g + v * (p / (j + 1.0));
+        v *= g;
+      }
+      f[k] = v;
+      df[k] = d;
+    }
+    val[b] = f[0] * f[1] * f[2];
+    dl[b][0] = df[0] * f[1] * f[2];
+    dl[b][1] = f[0] * df[1] * f[2];
+    dl[b][2] = f[0] * f[1] * df[2];
+  }
+}
+
+// 1D P_p Lagrange basis on [0,1] with equispaced nodes.
+void lagrange_1d(int p, double s, double* out) {
+  for (int k = 0; k <= p; ++k) {
+    double v = 1.0;
+    for (int j = 0; j <= p; ++j)
+      if (j != k) v *= (s - double(j) / p) / (double(k - j) / p);
+    out[k] = v;
+  }
+}
+
+// In-place Cholesky A = L L^T (row-major n x n, lower triangle kept).
+void cholesky(std::vector<double>& A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    if (!(d > 0.0)) throw std::runtime_error("reference mass matrix is not positive definite");
+    d = std::sqrt(d);
+    A[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = s / d;
+    }
+  }
+}
+
+// X = A^-1 B for the Cholesky factor L of A (n x n), B row-major n x c.
+std::vector<double> chol_solve(const std::vector<double>& L, int n, const std::vector<double>& B, int c) {
+  std::vector<double> X(B);
+  for (int col = 0; col < c; ++col) {
+    for (int i = 0; i < n; ++i) {
+      double s = X[(size_t)i * c + col];
+      for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * X[(size_t)k * c + col];
+      X[(size_t)i * c + col] = s / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = X[(size_t)i * c + col];
+      for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * X[(size_t)k * c + col];
+      X[(size_t)i * c + col] = s / L[(size_t)i * n + i];
+    }
+  }
+  return X;
+}
+
+// C = A^T B with A (r x a), B (r x b), row-major.
+std::vector<double> atb(const std::vector<double>& A, int r, int a, const std::vector<double>& B, int b) {
+  std::vector<double> C((size_t)a * b, 0.0);
+  for (int k = 0; k < r; ++k)
+    for (int i = 0; i < a; ++i) {
+      const double aki = A[(size_t)k * a + i];
+      if (aki == 0.0) continue;
+      const double* brow = &B[(size_t)k * b];
+      double* crow = &C[(size_t)i * b];
+      for (int j = 0; j < b; ++j) crow[j] += aki * brow[j];
+    }
+  return C;
+}
+
+}  // namespace
+
+void build_reference_tables(int m, int p, RefTables& T) {
+  if (m < 1 || p < 1) throw std::runtime_error("m and p must be >= 1");
+  T.m = m;
+  T.p = p;
+  T.P = m * p;
+  T.P1 = T.P + 1;
+  T.Q = (T.P + 1) * (T.P + 2) / 2;
+  T.n_t = 3 * T.P1;
+  const int P = T.P, P1 = T.P1, Q = T.Q, nt = T.n_t;
+  auto node = [P](int a, int b) { return b * (P + 1) - b * (b - 1) / 2 + a; };
+
+  // sub-triangles (published order) and their local P_p nodes
+  T.subtri.clear();
+  for (int sj = 0; sj < m; ++sj)
+    for (int si = 0; si + sj <= m - 1; ++si) {
+      int c[6] = {si, sj, si + 1, sj, si, sj + 1};
+      T.subtri.insert(T.subtri.end(), c, c + 6);
+    }
+  for (int sj = 0; sj < m - 1; ++sj)
+    for (int si = 0; si + sj <= m - 2; ++si) {
+      int c[6] = {si + 1, sj + 1, si, sj + 1, si + 1, sj};
+      T.subtri.insert(T.subtri.end(), c, c + 6);
+    }
+  T.nsub = (int)T.subtri.size() / 6;
+  T.nloc = (p + 1) * (p + 2) / 2;
+  std::vector<int> al;   // local multi-indices (A, B, C)
+  for (int aC = 0; aC <= p; ++aC)
+    for (int aB = 0; aB + aC <= p; ++aB) {
+      al.push_back(p - aB - aC);
+      al.push_back(aB);
+      al.push_back(aC);
+    }
+  T.subnode.assign((size_t)T.nsub * T.nloc, 0);
+  for (int s = 0; s < T.nsub; ++s) {
+    const int* c = &T.subtri[6 * s];
+    for (int b = 0; b < T.nloc; ++b) {
+      const int a = al[3 * b] * c[0] + al[3 * b + 1] * c[2] + al[3 * b + 2] * c[4];
+      const int bb = al[3 * b] * c[1] + al[3 * b + 1] * c[3] + al[3 * b + 2] * c[5];
+      T.subnode[(size_t)s * T.nloc + b] = node(a, bb);
+    }
+  }
+  // node -> (sub-triangle, local index) lists
+  T.ns_ptr.assign(Q + 1, 0);
+  for (int v : T.subnode) T.ns_ptr[v + 1]++;
+  for (int i = 0; i < Q; ++i) T.ns_ptr[i + 1] += T.ns_ptr[i];
+  T.ns_idx.assign(T.ns_ptr[Q], 0);
+  {
+    std::vector<int> fill(T.ns_ptr.begin(), T.ns_ptr.end() - 1);
+    for (int s = 0; s < T.nsub; ++s)
+      for (int b = 0; b < T.nloc; ++b) T.ns_idx[fill[T.subnode[(size_t)s * T.nloc + b]]++] = s * T.nloc + b;
+  }
+
+  // source / element rule on the unit triangle (collapsed Gauss, ng = p + 2)
+  T.ng = p + 2;
+  std::vector<double> gx, gw;
+  gauss01(T.ng, gx, gw);
+  T.uq = gx;
+  T.nqs = T.ng * T.ng;
+  T.wq.assign(T.nqs, 0.0);
+  T.phiq.assign((size_t)T.nqs * T.nloc, 0.0);
+  std::vector<double> dphi((size_t)T.nqs * T.nloc * 2);   // reference-sub-triangle gradients wrt (xi^, eta^)
+  {
+    std::vector<double> val(T.nloc);
+    std::vector<double[3]> dl(T.nloc);
+    for (int j = 0; j < T.ng; ++j)
+      for (int i = 0; i < T.ng; ++i) {
+        const int q = j * T.ng + i;
+        const double xh = gx[i] * (1.0 - gx[j]), eh = gx[j];
+        T.wq[q] = gw[i] * gw[j] * (1.0 - gx[j]);
+        const double lam[3] = {1.0 - xh - eh, xh, eh};
+        lagrange_tri(p, al, T.nloc, lam, val.data(), dl.data());
+        for (int b = 0; b < T.nloc; ++b) {
+          T.phiq[(size_t)q * T.nloc + b] = val[b];
+          dphi[((size_t)q * T.nloc + b) * 2 + 0] = dl[b][1] - dl[b][0];   // d/dxi^ (lambda_B = xi^)
+          dphi[((size_t)q * T.nloc + b) * 2 + 1] = dl[b][2] - dl[b][0];   // d/deta^ (lambda_C = eta^)
+        }
+      }
+  }
+
+  // mass and derivative matrices of the macro reference triangle
+  T.Mh.assign((size_t)Q * Q, 0.0);
+  T.Dxi.assign((size_t)Q * Q, 0.0);
+  T.Deta.assign((size_t)Q * Q, 0.0);
+  for (int s = 0; s < T.nsub; ++s) {
+    const int* c = &T.subtri[6 * s];
+    // sub-triangle map (xi, eta) = A + xi^ (B - A) + eta^ (C - A), all / m
+    const double j00 = double(c[2] - c[0]) / m, j10 = double(c[3] - c[1]) / m;
+    const double j01 = double(c[4] - c[0]) / m, j11 = double(c[5] - c[1]) / m;
+    const double det = j00 * j11 - j01 * j10;
+    // d(xi^, eta^)/d(xi, eta) = J_s^-1
+    const double i00 = j11 / det, i01 = -j01 / det, i10 = -j10 / det, i11 = j00 / det;
+    const int* nd = &T.subnode[(size_t)s * T.nloc];
+    for (int q = 0; q < T.nqs; ++q) {
+      const double w = T.wq[q] * std::fabs(det);
+      for (int a = 0; a < T.nloc; ++a) {
+        const double* da = &dphi[((size_t)q * T.nloc + a) * 2];
+        const double dxi_a = da[0] * i00 + da[1] * i10;    // d phi / d xi
+        const double deta_a = da[0] * i01 + da[1] * i11;   // d phi / d eta
+        const double pa = T.phiq[(size_t)q * T.nloc + a];
+        for (int b = 0; b < T.nloc; ++b) {
+          const double pb = T.phiq[(size_t)q * T.nloc + b];
+          const size_t ij = (size_t)nd[a] * Q + nd[b];
+          T.Mh[ij] += w * pa * pb;
+          T.Dxi[ij] += w * pb * dxi_a;
+          T.Deta[ij] += w * pb * deta_a;
+        }
+      }
+    }
+  }
+
+  // 1D trace mass Gh on [0,1] with m sub-intervals; boundary-data rule
+  T.ngb = p + 2;
+  gauss01(T.ngb, T.bu, T.bw);
+  T.bpsi.assign((size_t)T.ngb * (p + 1), 0.0);
+  for (int q = 0; q < T.ngb; ++q) lagrange_1d(p, T.bu[q], &T.bpsi[(size_t)q * (p + 1)]);
+  T.Gh.assign((size_t)P1 * P1, 0.0);
+  for (int s = 0; s < m; ++s)
+    for (int q = 0; q < T.ngb; ++q)
+      for (int r = 0; r <= p; ++r)
+        for (int r2 = 0; r2 <= p; ++r2)
+          T.Gh[(size_t)(s * p + r) * P1 + s * p + r2] +=
+              T.bw[q] / m * T.bpsi[(size_t)q * (p + 1) + r] * T.bpsi[(size_t)q * (p + 1) + r2];
+  {
+    std::vector<double> L(T.Gh);
+    cholesky(L, P1);
+    std::vector<double> I((size_t)P1 * P1, 0.0);
+    for (int i = 0; i < P1; ++i) I[(size_t)i * P1 + i] = 1.0;
+    T.Ghinv = chol_solve(L, P1, I, P1);
+  }
+
+  // reference edge k runs from vertex k+1 to vertex k+2: lattice nodes along it
+  T.enode.assign(3 * P1, 0);
+  for (int t = 0; t <= P; ++t) {
+    T.enode[0 * P1 + t] = node(P - t, t);   // (1,0) -> (0,1)
+    T.enode[1 * P1 + t] = node(0, P - t);   // (0,1) -> (0,0)
+    T.enode[2 * P1 + t] = node(t, 0);       // (0,0) -> (1,0)
+  }
+  // the restriction of the lattice basis to an edge is the trace basis, so
+  // int_0^1 psi_t phi_i ds = Gh[t'][t] for i = enode[k][t'] (0 elsewhere)
+  T.Fh.assign((size_t)Q * nt, 0.0);
+  for (int k = 0; k < 3; ++k)
+    for (int t2 = 0; t2 < P1; ++t2)
+      for (int t = 0; t < P1; ++t)
+        T.Fh[(size_t)T.enode[k * P1 + t2] * nt + k * P1 + t] = T.Gh[(size_t)t2 * P1 + t];
+
+  // products through Mh^-1
+  std::vector<double> L(T.Mh);
+  cholesky(L, Q);
+  T.Xxi = chol_solve(L, Q, T.Dxi, Q);
+  T.Xeta = chol_solve(L, Q, T.Deta, Q);
+  T.Yh = chol_solve(L, Q, T.Fh, nt);
+  T.Kxx = atb(T.Dxi, Q, Q, T.Xxi, Q);
+  T.Kyy = atb(T.Deta, Q, Q, T.Xeta, Q);
+  {
+    std::vector<double> a = atb(T.Dxi, Q, Q, T.Xeta, Q);
+    std::vector<double> b = atb(T.Deta, Q, Q, T.Xxi, Q);
+    T.Ksym.resize(a.size());
+    for (size_t i = 0; i < a.size(); ++i) T.Ksym[i] = a[i] + b[i];
+  }
+  T.Pxi = atb(T.Dxi, Q, Q, T.Yh, nt);
+  T.Peta = atb(T.Deta, Q, Q, T.Yh, nt);
+  T.Hh = atb(T.Fh, Q, nt, T.Yh, nt);
+}
+
+}  // namespace mehdg

@@ -1,0 +1,46 @@
+"""Seeded synthetic workloads (inputs only; none of the method's arithmetic).
+
+The paper's benchmarks are analytic (Sec. 4.1) and its timing runs use 3D
+adaptive meshes that are not available, so every workload is synthetic:
+structured unit-square macro meshes with the manufactured solution
+u = sin(pi x) sin(pi y) (source f = -kappa Lap u + beta . grad u, g_D = 0),
+plus seeded random fields for parity tests.
+"""
+import math
+
+import numpy as np
+import torch
+
+MASTER_SEED = 0x230210917
+
+# Workloads (n macro squares per side, m sub-edges per macro-edge, degree p).
+CONFIGS = {
+    "c0": dict(n=4, m=2, p=2, beta=(1.0, 1.0), kappa=1.0),
+    "c1": dict(n=128, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
+    "c2": dict(n=256, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
+    "c4": dict(n=256, m=4, p=2, beta=(1.0, 0.5), kappa=1.0),
+}
+
+
+def sin_sin_source(xy, kappa, beta):
+    """f = 2 kappa pi^2 sin(pi x) sin(pi y) + beta . grad(sin(pi x) sin(pi y)) at points xy[..., 2]."""
+    x, y = xy[..., 0], xy[..., 1]
+    pi = math.pi
+    sx, sy = torch.sin(pi * x), torch.sin(pi * y)
+    cx, cy = torch.cos(pi * x), torch.cos(pi * y)
+    return 2.0 * kappa * pi * pi * sx * sy + beta[0] * pi * cx * sy + beta[1] * pi * sx * cy
+
+
+def sin_sin_exact(xy):
+    return torch.sin(math.pi * xy[..., 0]) * torch.sin(math.pi * xy[..., 1])
+
+
+def random_kappa(N, seed, lo=0.5, hi=2.0):
+    """Per-element diffusivities, log-uniform in [lo, hi]."""
+    g = np.random.default_rng([MASTER_SEED, 17, int(seed)])
+    return np.exp(g.uniform(np.log(lo), np.log(hi), size=N))
+
+
+def random_vector(n, seed):
+    g = np.random.default_rng([MASTER_SEED, 29, int(seed)])
+    return g.standard_normal(n)

@@ -1,0 +1,118 @@
+"""The large workload (n = 128, m = 8, p = 3, beta = 50 (cos 0.3, sin 0.3), 32,768
+macro-elements, 1,222,400 trace unknowns) through the same calls bench.py times.
+
+The oracle cannot condense 32,768 elements in seconds, so it checks sampled
+outputs one by one (Schur blocks of sampled elements, apply rows of sampled
+edges from the oracle's own blocks of the two adjacent elements) and the
+solution is checked by properties that hold at any size: the reported
+residual, and closeness to the manufactured solution u = sin(pi x) sin(pi y).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.hdg import HDGProblem
+from paper_2302_10917_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+CFG = wl.CONFIGS["c1"]
+
+
+@pytest.fixture(scope="module")
+def big():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_10917_gb300 import Problem
+    gpu = Problem(CFG["n"], CFG["m"], CFG["p"], beta=CFG["beta"], kappa=CFG["kappa"])
+    xy = gpu.quad_points()
+    gpu.set_source(wl.sin_sin_source(xy, CFG["kappa"], CFG["beta"]))
+    gpu.condense(keep_factors=True)
+    ora = HDGProblem(CFG["n"], CFG["m"], CFG["p"], beta=CFG["beta"], kappa=CFG["kappa"])
+    yield gpu, ora
+    gpu.close()
+
+
+def _sample(N, k, seed):
+    return np.random.default_rng([wl.MASTER_SEED, seed]).choice(N, size=k, replace=False)
+
+
+def test_sampled_schur_blocks(big):
+    gpu, ora = big
+    N = ora.mesh.N
+    els = sorted(set(_sample(N, 4, 1).tolist() + [0, 1, N - 1]))
+    for e in els:
+        S_o, _ = ora.condense_element(int(e))
+        S_g = gpu.schur(int(e), 1)[0].cpu().numpy()
+        assert np.abs(S_g - S_o).max() / np.abs(S_o).max() < 1e-12, e
+
+
+def test_sampled_apply_rows(big):
+    gpu, ora = big
+    msh = ora.mesh
+    x = wl.random_vector(msh.N_tr, seed=7)
+    y = gpu.apply(torch.from_numpy(x)).cpu().numpy()
+    zero_bnd = np.zeros((msh.n_bnd_edges, msh.P1))
+    scale = np.abs(y).max()
+    edges = _sample(msh.n_int_edges, 6, 2).tolist() + [0, msh.n_int_edges - 1]
+    cache = {}
+    for f in edges:
+        # the two elements of edge f (oracle numbering)
+        sides = []
+        for cand in _elements_of_edge(msh, f):
+            if cand not in cache:
+                cache[cand] = ora.condense_element(cand)[0]
+            sides.append(cand)
+        out = np.zeros(msh.N_tr)
+        for e in sides:
+            ora.scatter(e, cache[e] @ ora.element_trace(e, x, zero_bnd), out)
+        sl = slice(f * msh.P1, (f + 1) * msh.P1)
+        assert np.abs(y[sl] - out[sl]).max() / scale < 1e-12, f
+
+
+def _elements_of_edge(msh, f):
+    n = msh.n
+    cands = []
+    if f < n * n:
+        j, i = divmod(f, n)
+        cands = [2 * (j * n + i), 2 * (j * n + i) + 1]
+    elif f < n * n + n * (n - 1):
+        r = f - n * n
+        j, i = 1 + r // n, r % n
+        cands = [2 * ((j - 1) * n + i) + 1, 2 * (j * n + i)]
+    else:
+        r = f - n * n - n * (n - 1)
+        j, i = r // (n - 1), 1 + r % (n - 1)
+        cands = [2 * (j * n + i - 1), 2 * (j * n + i) + 1]
+    for e in cands:     # consistency with the oracle's own edge tables
+        assert any(kind == "int" and idx == f for kind, idx, _ in msh.element_edges(e))
+    return cands
+
+
+def test_solve_to_1e10_and_solution_accuracy(big):
+    gpu, ora = big
+    g = gpu.rhs()
+    x, rep, st = gpu.solve(g, tol=1e-10, restart=50, maxit=20000)
+    assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10
+    u, q = gpu.recover(x)
+    msh = ora.mesh
+    ref = msh.lattice_ref()
+    N = msh.N
+    e = np.arange(N)
+    sq, t = e // 2, e % 2
+    j, i = sq // msh.n, sq % msh.n
+    h = 1.0 / msh.n
+    x0, x1, y0, y1 = i * h, (i + 1) * h, j * h, (j + 1) * h
+    v0 = np.where(t[:, None] == 0, np.stack([x1, y0], 1), np.stack([x0, y1], 1))
+    v1 = np.where(t[:, None] == 0, np.stack([x1, y1], 1), np.stack([x0, y0], 1))
+    v2 = np.where(t[:, None] == 0, np.stack([x0, y0], 1), np.stack([x1, y1], 1))
+    X = v0[:, None, :] + ref[None, :, 0:1] * (v1 - v0)[:, None, :] + ref[None, :, 1:2] * (v2 - v0)[:, None, :]
+    u_ex = np.sin(math.pi * X[..., 0]) * np.sin(math.pi * X[..., 1])
+    err = np.abs(u.cpu().numpy() - u_ex).max()
+    # p = 3 on sub-triangles of size 1/1024: discretization error ~1e-10; the
+    # algebraic error of a 1e-10 residual is amplified by cond(S)
+    assert err < 1e-6, err
+    qx = -math.pi * np.cos(math.pi * X[..., 0]) * np.sin(math.pi * X[..., 1])
+    assert np.abs(q[:, 0].cpu().numpy() - qx).max() < 1e-4
