@@ -101,6 +101,7 @@ typedef struct {
   int64_t n_qp;          /* source points per element */
   int64_t n_bqp;         /* Dirichlet-data points per boundary edge */
   size_t device_bytes;   /* device memory currently held by the context */
+  int64_t launches;      /* CUDA kernels this context has enqueued since hdg_create */
 } hdg_info_t;
 
 /* Solve options. mode: 0 = FP64 GMRES on FP64 Schur blocks; 1 = FP32 Schur
@@ -196,6 +197,26 @@ hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev)
 hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_qp_host,
                         const hdg_solve_opts* opts, double* x_host, double* u_host,
                         double* q_host, hdg_solve_report* report);
+
+/* Per-phase device timing (tracing). Phases: */
+#define HDG_PROF_CONDENSE 0   /* condensation kernel launches (element build + LU + Schur) */
+#define HDG_PROF_APPLY 1      /* FP64 trace-operator apply launches (hdg_apply and inside hdg_solve) */
+#define HDG_PROF_ORTHO 2      /* GMRES vector work of one Arnoldi step (CGS2, norm, Givens, scaling) */
+#define HDG_PROF_RECOVER 3    /* back-solve kernel launches */
+#define HDG_PROF_APPLY32 4    /* FP32 trace-operator apply launches */
+#define HDG_PROF_NPHASES 5
+typedef struct {
+  int64_t count[HDG_PROF_NPHASES];   /* timed launches (or Arnoldi steps for ORTHO) */
+  double ms[HDG_PROF_NPHASES];       /* summed CUDA-event time on the context stream */
+} hdg_profile_t;
+
+/* Start (enable != 0) or stop per-phase timing; starting clears the totals.
+ * While enabled, every timed launch is bracketed by a CUDA event pair on the
+ * context stream. */
+hdg_status hdg_profile(hdg_ctx* ctx, int enable);
+
+/* Synchronise the stream and return the totals since the last start. */
+hdg_status hdg_profile_read(hdg_ctx* ctx, hdg_profile_t* out);
 
 /* Last error message of the context (never NULL; "" if none). */
 const char* hdg_last_error(const hdg_ctx* ctx);

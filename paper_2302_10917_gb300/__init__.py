@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_C
 
 EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", "hdg_set_source",
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
-            "hdg_run_host", "hdg_last_error", "hdg_destroy"]
+            "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_last_error", "hdg_destroy"]
+PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -36,7 +37,7 @@ class Info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("Q", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("N_tr", ctypes.c_int64), ("n_int_edges", ctypes.c_int64),
                 ("n_bnd_edges", ctypes.c_int64), ("n_qp", ctypes.c_int64), ("n_bqp", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int64)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -50,6 +51,10 @@ class SolveReport(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5)]
 
 
 class HDGError(RuntimeError):
@@ -82,6 +87,8 @@ def load_library(path=LIB_PATH):
     lib.hdg_recover.argtypes = [vp, dp, dp, dp, ctypes.c_int]
     lib.hdg_get_schur.argtypes = [vp, i64, i64, dp]
     lib.hdg_run_host.argtypes = [vp, dp, dp, ctypes.POINTER(SolveOpts), dp, dp, dp, ctypes.POINTER(SolveReport)]
+    lib.hdg_profile.argtypes = [vp, ctypes.c_int]
+    lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
     lib.hdg_last_error.restype = ctypes.c_char_p
     lib.hdg_destroy.argtypes = [vp]
@@ -134,6 +141,22 @@ class Problem:
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
         self.n, self.m, self.p = n, m, p
         self._src = None
+
+    def launches(self):
+        """Kernels this context has enqueued so far (counted by the library)."""
+        info = Info()
+        self._check(self.lib.hdg_info(self.h, ctypes.byref(info)))
+        return info.launches
+
+    def profile(self, enable=True):
+        """Start (clears totals) or stop per-phase CUDA-event timing in the library."""
+        self._check(self.lib.hdg_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{phase: (timed launches, total ms)} since the last start."""
+        pr = Profile()
+        self._check(self.lib.hdg_profile_read(self.h, ctypes.byref(pr)))
+        return {name: (pr.count[i], pr.ms[i]) for i, name in enumerate(PROF_PHASES)}
 
     # ------------------------------------------------------------------ utils
     def _check(self, st):

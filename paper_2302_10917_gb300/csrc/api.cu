@@ -120,6 +120,23 @@ cudaError_t upload_tables(hdg_ctx* c) {
 
 }  // namespace
 
+namespace mehdg {
+// Fold the recorded event pairs into the per-phase totals and recycle them.
+void profile_collect(hdg_ctx* c) {
+  if (c->prof_ev.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& it : c->prof_ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) {
+      c->prof_ms[it.first] += ms;
+      c->prof_count[it.first] += 1;
+    }
+    c->prof_pool.push_back(it.second);
+  }
+  c->prof_ev.clear();
+}
+}  // namespace mehdg
+
 extern "C" {
 
 hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
@@ -176,6 +193,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if ((e = cudaMemcpyAsync(c->d_kappa, kap.data(), N * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
     return cuda_err(c, e, "kappa upload");
   if ((e = dev_alloc(c, &c->d_escale, P.n_int)) != cudaSuccess) return cuda_err(c, e, "face scales");
+  c->launches += 1;
   if ((e = launch_face_scale(P, c->d_kappa, c->d_escale, c->stream)) != cudaSuccess) return cuda_err(c, e, "face scales");
   if ((e = dev_alloc(c, &c->d_ghat, (size_t)P.n_bnd * P.P1)) != cudaSuccess) return cuda_err(c, e, "ghat");
   if ((e = cudaMemsetAsync(c->d_ghat, 0, (size_t)P.n_bnd * P.P1 * 8, c->stream)) != cudaSuccess)
@@ -190,6 +208,7 @@ hdg_status hdg_info(const hdg_ctx* c, hdg_info_t* out) {
   out->N = P.N; out->Q = P.Q; out->n_t = P.n_t; out->N_tr = P.N_tr;
   out->n_int_edges = P.n_int; out->n_bnd_edges = P.n_bnd; out->n_qp = P.n_qp; out->n_bqp = P.n_bqp;
   out->device_bytes = c->bytes;
+  out->launches = c->launches;
   return HDG_OK;
 }
 
@@ -198,6 +217,7 @@ hdg_status hdg_quad_points(const hdg_ctx* cc, double* xy) {
   if (!c || !xy) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
   quad_points_kernel<<<1024, 256, 0, c->stream>>>(c->prm, c->dt, xy);
+  c->launches += 1;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_quad_points");
 }
@@ -207,6 +227,7 @@ hdg_status hdg_bnd_quad_points(const hdg_ctx* cc, double* xy) {
   if (!c || !xy) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
   bnd_points_kernel<<<64, 256, 0, c->stream>>>(c->prm, c->dt, xy);
+  c->launches += 1;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_bnd_quad_points");
 }
@@ -218,8 +239,13 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
   c->f_qp = f_qp;
   c->gD_qp = gD_qp;
   cudaError_t e;
-  if (gD_qp) e = launch_project_dirichlet(c->prm, c->dt, gD_qp, c->d_ghat, c->stream);
-  else e = cudaMemsetAsync(c->d_ghat, 0, (size_t)c->prm.n_bnd * c->prm.P1 * 8, c->stream);
+  if (gD_qp) {
+    e = launch_project_dirichlet(c->prm, c->dt, gD_qp, c->d_ghat, c->stream);
+    c->launches += 1;
+  }
+  else {
+    e = cudaMemsetAsync(c->d_ghat, 0, (size_t)c->prm.n_bnd * c->prm.P1 * 8, c->stream);
+  }
   if (e != cudaSuccess) return cuda_err(c, e, "hdg_set_source");
   c->state = 1;
   return HDG_OK;
@@ -252,10 +278,15 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   const double* gh = c->gD_qp ? c->d_ghat : nullptr;
   for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
     const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
-    e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, keep, 1, c->d_S, c->d_St,
-                        (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream);
+    {
+      ProfScope ps(c, HDG_PROF_CONDENSE);
+      e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, keep, 1, c->d_S, c->d_St,
+                          (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream);
+    }
+    c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
   }
+  c->launches += 1;
   if ((e = launch_assemble_rhs(P, c->d_gel, c->d_g, c->stream)) != cudaSuccess) return cuda_err(c, e, "rhs");
   std::vector<int> info(P.N);
   if ((e = cudaMemcpyAsync(info.data(), c->d_info, (size_t)P.N * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
@@ -284,6 +315,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   if (!x || !y || x == y || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad x/y or nrhs");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
   cudaError_t e;
+  ProfScope ps(c, prec == 32 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY);
   if (prec == 64) {
     e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream)
                 : launch_apply64(c->prm, c->d_S, (const double*)x, (double*)y, nullptr, nullptr, c->stream);
@@ -293,6 +325,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   } else {
     return set_err(c, HDG_ERR_ARG, "prec must be 64 or 32");
   }
+  c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
 }
 
@@ -317,7 +350,9 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
   const double* gh = c->gD_qp ? c->d_ghat : nullptr;
   cudaError_t e;
   if (c->flags & HDG_KEEP_FACTORS) {
+    ProfScope ps(c, HDG_PROF_RECOVER);
     e = launch_recover(P, c->dt, c->d_ws, 0, P.N, 1, x, gh, u, q, c->stream);
+    c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "recover");
   } else {
     for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
@@ -326,6 +361,7 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
                           nullptr, nullptr, c->stream);
       if (e != cudaSuccess) return cuda_err(c, e, "refactor");
       e = launch_recover(P, c->dt, c->d_ws, e0, cnt, 0, x, gh, u, q, c->stream);
+      c->launches += 2;
       if (e != cudaSuccess) return cuda_err(c, e, "recover");
     }
   }
@@ -337,6 +373,7 @@ hdg_status hdg_get_schur(hdg_ctx* c, int64_t e0, int64_t count, double* S) {
   if (!S || e0 < 0 || count < 1 || e0 + count > c->prm.N) return set_err(c, HDG_ERR_ARG, "bad element range");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_get_schur before hdg_condense");
   cudaError_t e = launch_get_schur(c->prm, c->d_S, e0, count, S, c->stream);
+  c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_get_schur");
 }
 
@@ -390,11 +427,30 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
   return s;
 }
 
+hdg_status hdg_profile(hdg_ctx* c, int enable) {
+  if (!c) return HDG_ERR_ARG;
+  profile_collect(c);
+  if (enable) {
+    for (int i = 0; i < HDG_PROF_NPHASES; ++i) { c->prof_count[i] = 0; c->prof_ms[i] = 0.0; }
+  }
+  c->prof_on = enable != 0;
+  return HDG_OK;
+}
+
+hdg_status hdg_profile_read(hdg_ctx* c, hdg_profile_t* out) {
+  if (!c || !out) return HDG_ERR_ARG;
+  profile_collect(c);
+  for (int i = 0; i < HDG_PROF_NPHASES; ++i) { out->count[i] = c->prof_count[i]; out->ms[i] = c->prof_ms[i]; }
+  return HDG_OK;
+}
+
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void hdg_destroy(hdg_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  profile_collect(c);
+  for (auto& pr : c->prof_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
   cudaFree(c->d_St32); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);

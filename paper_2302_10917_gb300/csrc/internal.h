@@ -187,4 +187,38 @@ struct hdg_ctx {
   float* d_x32 = nullptr;         // FP32 vectors for mode 1
   int krylov_restart = 0;
   size_t bytes = 0;
+  int64_t launches = 0;     // kernels enqueued (reported by hdg_info)
+  // per-phase event timing
+  bool prof_on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;
+  int64_t prof_count[HDG_PROF_NPHASES] = {0};
+  double prof_ms[HDG_PROF_NPHASES] = {0};
 };
+
+namespace mehdg {
+// Event pair around a launch when profiling is on (no-op otherwise).
+struct ProfScope {
+  hdg_ctx* c;
+  int phase;
+  cudaEvent_t b = nullptr, e = nullptr;
+  ProfScope(hdg_ctx* ctx, int ph) : c(ctx), phase(ph) {
+    if (!c->prof_on) return;
+    if (!c->prof_pool.empty()) {
+      b = c->prof_pool.back().first;
+      e = c->prof_pool.back().second;
+      c->prof_pool.pop_back();
+    } else {
+      cudaEventCreate(&b);
+      cudaEventCreate(&e);
+    }
+    cudaEventRecord(b, c->stream);
+  }
+  ~ProfScope() {
+    if (!b) return;
+    cudaEventRecord(e, c->stream);
+    c->prof_ev.push_back({phase, {b, e}});
+  }
+};
+void profile_collect(hdg_ctx* c);
+}  // namespace mehdg

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 #include "launch.h"
 
 namespace mehdg {
@@ -273,6 +274,8 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
   return v;
 }
 
+#define LAUNCHED(k) (c->launches += (k))
+
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
   const Params& P = c->prm;
   const int K = o.restart;
@@ -293,10 +296,12 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   // ||g||, D^-1 g, ||D^-1 g||
   axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, 0.0, g, rr, n, part);
   sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
+  LAUNCHED(2);
   const double gnorm = std::sqrt(read_scalar(c, sm + L.sc + 5, cu));
   cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, g, bt, st));
   axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, bt, 0.0, bt, rr, n, part);
   sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
+  LAUNCHED(3);
   const double btnorm = std::sqrt(read_scalar(c, sm + L.sc + 5, cu));
   if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
   if (gnorm == 0.0) {
@@ -312,15 +317,25 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     // r0 = D^-1 g - D^-1 S x ; V0 = r0 / beta
     double tgt = target;
     cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &tgt, sizeof(double), cudaMemcpyHostToDevice, st));
-    cu.ok(launch_apply64(P, c->d_St, x, w, c->d_escale, nullptr, st));
+    {
+      ProfScope ps(c, HDG_PROF_APPLY);
+      cu.ok(launch_apply64(P, c->d_St, x, w, c->d_escale, nullptr, st));
+    }
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, bt, -1.0, w, rr, n, part);
     cycle_init_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG);
     scale_kernel<<<KG, KT, 0, st>>>(rr, sm, L.sc + 4, V, n, fl);
+    LAUNCHED(4);
     const int jmax = std::min(K, o.maxit - its);
+    std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
     for (int j = 0; j < jmax; ++j) {
+      mark[j] = c->prof_ev.size();
       double* Vj = V + (size_t)j * n;
       double* Hcol = sm + L.H + (size_t)j * (K + 1);
-      cu.ok(launch_apply64(P, c->d_St, Vj, w, c->d_escale, fl, st));
+      {
+        ProfScope ps(c, HDG_PROF_APPLY);
+        cu.ok(launch_apply64(P, c->d_St, Vj, w, c->d_escale, fl, st));
+      }
+      ProfScope po(c, HDG_PROF_ORTHO);
       mdot_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, w, part, fl);
       mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, j + 1, Hcol, sm + L.htmp, 0, fl);
       update_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, sm + L.htmp, -1.0, w, nullptr, fl);
@@ -329,6 +344,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       update_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, sm + L.htmp, -1.0, w, part, fl);
       givens_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG, j);
       scale_kernel<<<KG, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * n, n, fl);
+      LAUNCHED(9);
     }
     cu.ok(cudaGetLastError());
     int hflags[2] = {0, 0};
@@ -336,17 +352,27 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     cu.ok(cudaStreamSynchronize(st));
     if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
     const int jused = hflags[F_JUSED];
+    if (c->prof_on && jused < jmax) {
+      // steps after the stop flag was raised were enqueued but returned at once: not timed work
+      for (size_t i = mark[jused]; i < c->prof_ev.size(); ++i) c->prof_pool.push_back(c->prof_ev[i].second);
+      c->prof_ev.resize(mark[jused]);
+    }
     const double est = read_scalar(c, sm + L.sc + 1, cu);
     its += jused;
     rep.restarts += 1;
     if (jused > 0) {
       lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
       update_kernel<<<KG, KT, 0, st>>>(V, n, jused, sm + L.y, 1.0, x, nullptr, nullptr);
+      LAUNCHED(2);
     }
     // true residual with the unpreconditioned FP64 operator
-    cu.ok(launch_apply64(P, c->d_S, x, w, nullptr, nullptr, st));
+    {
+      ProfScope ps(c, HDG_PROF_APPLY);
+      cu.ok(launch_apply64(P, c->d_S, x, w, nullptr, nullptr, st));
+    }
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, -1.0, w, rr, n, part);
     sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
+    LAUNCHED(3);
     rel = std::sqrt(read_scalar(c, sm + L.sc + 5, cu)) / gnorm;
     if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
     rep.iterations = its;
