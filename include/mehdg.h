@@ -104,8 +104,11 @@ typedef struct {
   int64_t launches;      /* CUDA kernels this context has enqueued since hdg_create */
 } hdg_info_t;
 
-/* Solve options. mode: 0 = FP64 GMRES on FP64 Schur blocks; 1 = FP32 Schur
- * blocks inside FP64 iterative refinement (requires HDG_STORE_FP32). */
+/* Solve options. mode: 0 = FP64 GMRES, FP64 preconditioned apply;
+ * 1 = FP32 Schur blocks inside FP64 iterative refinement (requires
+ * HDG_STORE_FP32); 2 = FP64 GMRES whose preconditioned apply runs in split
+ * FP32 ("double-float", 48-bit significand) arithmetic on the FP32 pipe
+ * (requires HDG_STORE_DF64). The stopping test always uses the FP64 S. */
 typedef struct {
   double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
   int maxit;             /* maximum number of operator applications inside GMRES */
@@ -124,6 +127,7 @@ typedef struct {
 /* hdg_condense flags */
 #define HDG_STORE_FP32 1u      /* also keep an FP32 copy of the preconditioned blocks */
 #define HDG_KEEP_FACTORS 2u    /* keep the factored local systems for hdg_recover (else recover refactors) */
+#define HDG_STORE_DF64 4u      /* also keep the preconditioned blocks as FP32 hi/lo pairs (8 bytes per entry) */
 
 /* Build the structured macro mesh, the reference-lattice tables of level m
  * (mass, derivative, boundary and trace matrices, quadrature) and the device

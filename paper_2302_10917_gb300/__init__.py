@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libmehdg.so")
 
 HDG_OK, HDG_ERR_ARG, HDG_ERR_STATE, HDG_ERR_CUDA, HDG_ERR_OOM = 0, 1, 2, 3, 4
 HDG_ERR_SINGULAR, HDG_ERR_NOCONV, HDG_ERR_TIMEOUT = 5, 6, 7
-HDG_STORE_FP32, HDG_KEEP_FACTORS = 1, 2
+HDG_STORE_FP32, HDG_KEEP_FACTORS, HDG_STORE_DF64 = 1, 2, 4
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_CUDA", 4: "HDG_ERR_OOM",
                 5: "HDG_ERR_SINGULAR", 6: "HDG_ERR_NOCONV", 7: "HDG_ERR_TIMEOUT"}
 
@@ -194,8 +194,9 @@ class Problem:
         self._src = (f_qp, gD_qp)       # keep alive until condense / recover
         self._check(self.lib.hdg_set_source(self.h, _ptr(f_qp), _ptr(gD_qp), 1))
 
-    def condense(self, store_fp32=False, keep_factors=True):
-        flags = (HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
+    def condense(self, store_fp32=False, keep_factors=True, store_df64=False):
+        flags = ((HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
+                 | (HDG_STORE_DF64 if store_df64 else 0))
         self._check(self.lib.hdg_condense(self.h, flags))
 
     def rhs(self):
@@ -204,7 +205,7 @@ class Problem:
         return g
 
     def apply(self, x, precond=False, prec=64, out=None):
-        dt = torch.float64 if prec == 64 else torch.float32
+        dt = torch.float32 if prec == 32 else torch.float64
         x = x.to(self.device, dt).contiguous()
         y = out if out is not None else torch.empty_like(x)
         self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), 1, prec, 1 if precond else 0))

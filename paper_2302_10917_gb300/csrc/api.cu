@@ -254,7 +254,7 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
 hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
-  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS)) return set_err(c, HDG_ERR_ARG, "unknown flags");
+  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64)) return set_err(c, HDG_ERR_ARG, "unknown flags");
   const Params& P = c->prm;
   cudaError_t e;
   const size_t sblk = (size_t)P.N * 3 * P.n_t * P.P1;
@@ -263,11 +263,14 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if ((flags & HDG_STORE_FP32) && !c->d_St32 && (e = dev_alloc(c, &c->d_St32, sblk)) != cudaSuccess)
     return cuda_err(c, e, "FP32 S blocks");
   if (!(flags & HDG_STORE_FP32)) dev_free(c, c->d_St32, sblk);
+  if ((flags & HDG_STORE_DF64) && !c->d_Stdf && (e = dev_alloc(c, &c->d_Stdf, sblk)) != cudaSuccess)
+    return cuda_err(c, e, "split-FP32 S blocks");
+  if (!(flags & HDG_STORE_DF64)) dev_free(c, c->d_Stdf, sblk);
   if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
   if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
   if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
   const size_t slot = (size_t)P.R * P.ld;
-  const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, 4096);
+  const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, 2048);
   if (c->ws_slots != want) {
     dev_free(c, c->d_ws, (size_t)c->ws_slots * slot);
     c->ws_slots = 0;
@@ -285,6 +288,11 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     }
     c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
+  }
+  if (flags & HDG_STORE_DF64) {
+    c->launches += 1;
+    if ((e = launch_split_df(c->d_St, c->d_Stdf, (int64_t)sblk, c->stream)) != cudaSuccess)
+      return cuda_err(c, e, "split");
   }
   c->launches += 1;
   if ((e = launch_assemble_rhs(P, c->d_gel, c->d_g, c->stream)) != cudaSuccess) return cuda_err(c, e, "rhs");
@@ -319,11 +327,14 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   if (prec == 64) {
     e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream)
                 : launch_apply64(c->prm, c->d_S, (const double*)x, (double*)y, nullptr, nullptr, c->stream);
+  } else if (prec == 48) {
+    if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
+    e = launch_apply_df(c->prm, c->d_Stdf, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream);
   } else if (prec == 32) {
     if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
     e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, c->d_escale, nullptr, c->stream);
   } else {
-    return set_err(c, HDG_ERR_ARG, "prec must be 64 or 32");
+    return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
   }
   c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
@@ -334,8 +345,11 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!c) return HDG_ERR_ARG;
   if (!g || !x || !o || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
-  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode != 0)
+  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
+  if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
+  // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)
+  if (o->mode == 2 && !c->d_Stdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
   hdg_solve_report r{};
   const hdg_status s = gmres_solve(c, g, x, *o, r);
   if (rep) *rep = r;
@@ -452,7 +466,7 @@ void hdg_destroy(hdg_ctx* c) {
   profile_collect(c);
   for (auto& pr : c->prof_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
-  cudaFree(c->d_St32); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
+  cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_x32);
   delete c;

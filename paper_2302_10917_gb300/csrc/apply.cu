@@ -19,9 +19,9 @@
 
 namespace mehdg {
 
-template <typename T, typename Acc>
-__global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restrict__ S, const T* __restrict__ x,
-                                                    T* __restrict__ y, const double* __restrict__ escale,
+template <typename T, typename TX, typename Acc>
+__global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restrict__ S, const TX* __restrict__ x,
+                                                    TX* __restrict__ y, const double* __restrict__ escale,
                                                     int epb, const int* __restrict__ stop) {
   if (stop && *stop) return;
   extern __shared__ unsigned char sraw[];
@@ -63,21 +63,114 @@ __global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restric
     const T* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + t;
     const Acc* xv = xs + (le * 2 + sd) * nt;
     int j = 0;
-    for (; j + 4 <= nt; j += 4) {
-      const Acc s0 = Acc(base[(size_t)(j + 0) * P1]);
-      const Acc s1 = Acc(base[(size_t)(j + 1) * P1]);
-      const Acc s2 = Acc(base[(size_t)(j + 2) * P1]);
-      const Acc s3 = Acc(base[(size_t)(j + 3) * P1]);
-      acc0 += s0 * xv[j + 0];
-      acc1 += s1 * xv[j + 1];
-      acc0 += s2 * xv[j + 2];
-      acc1 += s3 * xv[j + 3];
+    for (; j + 8 <= nt; j += 8) {
+      T sv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        acc0 += Acc(sv[u]) * xv[j + u];
+        acc1 += Acc(sv[u + 1]) * xv[j + u + 1];
+      }
     }
     for (; j < nt; ++j) acc0 += Acc(base[(size_t)j * P1]) * xv[j];
   }
   Acc r = acc0 + acc1;
   if (escale) r *= Acc(escale[f]);
-  y[(size_t)f * P1 + s] = T(r);
+  y[(size_t)f * P1 + s] = TX(r);
+}
+
+// ---------------------------------------------------------------------------
+// Split-FP32 ("double-float") variant. GB300 issues FP64 FMAs at 1/63 of the
+// FP32 rate, so the FP64 apply above is bound by the FP64 pipe, not by HBM.
+// Here each block entry is stored as an unevaluated sum hi + lo of two FP32
+// numbers (hi = fl32(s), lo = fl32(s - hi); 48 significant bits, same 8 bytes
+// per entry), x is split the same way on the fly, and every product is
+// accumulated with error-free transformations (Dekker's product via FMA,
+// Knuth's two-sum) on the FP32 pipe; the two FP32 words are combined in FP64
+// once per output.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_fma(float& ah, float& al, float sh, float sl, float xh, float xl) {
+  const float p = sh * xh;
+  const float e = fmaf(sh, xh, -p);          // sh*xh = p + e exactly
+  const float t = ah + p;                    // two-sum(ah, p) = t + err
+  const float bp = t - ah;
+  const float err = (ah - (t - bp)) + (p - bp);
+  ah = t;
+  al = fmaf(sh, xl, al);
+  al = fmaf(sl, xh, al);
+  al += e + err;
+}
+
+__global__ void __launch_bounds__(256) apply_df_kernel(Params P, const float2* __restrict__ S,
+                                                       const double* __restrict__ x, double* __restrict__ y,
+                                                       const double* __restrict__ escale, int epb,
+                                                       const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ unsigned char sraw[];
+  float2* xs = reinterpret_cast<float2*>(sraw);   // [epb][2][n_t] (hi, lo)
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  const int f0 = blockIdx.x * epb;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < epb * 2 * nt; idx += blockDim.x) {
+    const int le = idx / (2 * nt);
+    const int rem = idx - le * 2 * nt;
+    const int sd = rem / nt, c = rem - sd * nt;
+    const int f = f0 + le;
+    double v = 0.0;
+    if (f < P.n_int) {
+      int e[2], k[2], fl[2];
+      double len;
+      edge_sides(f, P.n, e, k, fl, &len);
+      int code[3], flip[3];
+      elem_edges(e[sd], P.n, code, flip);
+      const int kk = c / P1, t = c - kk * P1;
+      if (code[kk] >= 0) v = x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+    }
+    const float hi = (float)v;
+    xs[idx] = make_float2(hi, (float)(v - (double)hi));
+  }
+  __syncthreads();
+  const int le = tid / P1, s = tid - le * P1;
+  const int f = f0 + le;
+  if (le >= epb || f >= P.n_int) return;
+  int e[2], k[2], fl[2];
+  double len;
+  edge_sides(f, P.n, e, k, fl, &len);
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int t = fl[sd] ? PP - s : s;
+    const float2* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + t;
+    const float2* xv = xs + (le * 2 + sd) * nt;
+    int j = 0;
+    for (; j + 8 <= nt; j += 8) {
+      float2 sv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        df_fma(h0, l0, sv[u].x, sv[u].y, xv[j + u].x, xv[j + u].y);
+        df_fma(h1, l1, sv[u + 1].x, sv[u + 1].y, xv[j + u + 1].x, xv[j + u + 1].y);
+      }
+    }
+    for (; j < nt; ++j) {
+      const float2 sv = base[(size_t)j * P1];
+      df_fma(h0, l0, sv.x, sv.y, xv[j].x, xv[j].y);
+    }
+  }
+  double r = ((double)h0 + (double)h1) + ((double)l0 + (double)l1);
+  if (escale) r *= escale[f];
+  y[(size_t)f * P1 + s] = r;
+}
+
+// Split an FP64 array into hi/lo FP32 pairs.
+__global__ void split_df_kernel(const double* __restrict__ a, float2* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+  }
 }
 
 int apply_edges_per_block(const Params& P) {
@@ -90,7 +183,21 @@ cudaError_t launch_apply64(const Params& P, const double* S, const double* x, do
   const int epb = apply_edges_per_block(P);
   const int grid = (P.n_int + epb - 1) / epb;
   const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(double);
-  apply_kernel<double, double><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  apply_kernel<double, double, double><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
+                            const int* stop, cudaStream_t st) {
+  const int epb = apply_edges_per_block(P);
+  const int grid = (P.n_int + epb - 1) / epb;
+  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float2);
+  apply_df_kernel<<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st) {
+  split_df_kernel<<<2048, 256, 0, st>>>(a, out, n);
   return cudaGetLastError();
 }
 
@@ -99,7 +206,18 @@ cudaError_t launch_apply32(const Params& P, const float* S, const float* x, floa
   const int epb = apply_edges_per_block(P);
   const int grid = (P.n_int + epb - 1) / epb;
   const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float);
-  apply_kernel<float, float><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  apply_kernel<float, float, float><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
+}
+
+// FP32 blocks and FP32 accumulation with FP64 vectors (inner operator of the
+// FP32 + iterative-refinement solve).
+cudaError_t launch_apply32x64(const Params& P, const float* S, const double* x, double* y, const double* escale,
+                              const int* stop, cudaStream_t st) {
+  const int epb = apply_edges_per_block(P);
+  const int grid = (P.n_int + epb - 1) / epb;
+  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float);
+  apply_kernel<float, double, float><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
   return cudaGetLastError();
 }
 

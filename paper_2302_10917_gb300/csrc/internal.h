@@ -171,6 +171,7 @@ struct hdg_ctx {
   double* d_S = nullptr;          // [N][3][n_t][P1]  S_e, row-blocks per edge
   double* d_St = nullptr;         // [N][3][n_t][P1]  Gh^-1 S_e (preconditioned rows)
   float* d_St32 = nullptr;        // FP32 copy of d_St
+  float2* d_Stdf = nullptr;       // d_St as FP32 (hi, lo) pairs
   double* d_gel = nullptr;        // [N][n_t] element right-hand sides
   double* d_g = nullptr;          // [N_tr] assembled right-hand side
   double* d_ws = nullptr;         // factored bordered systems [slots][R][ld]

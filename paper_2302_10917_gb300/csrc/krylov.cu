@@ -131,6 +131,170 @@ __global__ void __launch_bounds__(KT) update_kernel(const double* __restrict__ V
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused CGS2 passes for nv <= NVMAX basis vectors. Each thread keeps the nv
+// basis entries of its index in registers; per-vector partial dot products
+// are reduced across the warp with shuffles and accumulated by lane (i % 32).
+// part[b * stride + i] receives the block's partial sum of vector i.
+// ---------------------------------------------------------------------------
+template <int NVMAX>
+__device__ __forceinline__ void warp_dots_accum(const double (&v)[NVMAX], int nv, double wv,
+                                                double (&acc)[(NVMAX + 31) / 32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NVMAX; ++i) {
+    if (i >= nv) break;
+    double p = v[i] * wv;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+    if (lane == (i & 31)) acc[i >> 5] += p;
+  }
+}
+
+template <int NVMAX>
+__device__ __forceinline__ void block_store_dots(const double (&acc)[(NVMAX + 31) / 32], int nv, double* red,
+                                                 double* out) {
+  // red: [nwarps][NVMAX]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < (NVMAX + 31) / 32; ++a)
+    if (a * 32 + lane < nv) red[wid * NVMAX + a * 32 + lane] = acc[a];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) s += red[w2 * NVMAX + i];
+    out[i] = s;
+  }
+}
+
+// part[b * (nv + 1) + i] = sum_chunk V_i w  (i < nv)
+template <int NVMAX>
+__global__ void __launch_bounds__(KT) cgs_dot_kernel(const double* __restrict__ V, int64_t n, int nv,
+                                                     const double* __restrict__ w, double* part, const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  __shared__ double red[(KT / 32) * NVMAX];
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc[(NVMAX + 31) / 32];
+#pragma unroll
+  for (int a = 0; a < (NVMAX + 31) / 32; ++a) acc[a] = 0.0;
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t idx = base + threadIdx.x;
+    const bool in = idx < hi;
+    double v[NVMAX];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i) v[i] = (i < nv && in) ? V[(size_t)i * n + idx] : 0.0;
+    const double wv = in ? w[idx] : 0.0;
+    warp_dots_accum<NVMAX>(v, nv, wv, acc);
+  }
+  block_store_dots<NVMAX>(acc, nv, red, part + (size_t)blockIdx.x * (nv + 1));
+}
+
+// w' = w - sum_i h_i V_i (stored in place); part[b * (nv + 1) + i] = sum_chunk V_i w',
+// part[b * (nv + 1) + nv] = sum_chunk w'^2
+template <int NVMAX>
+__global__ void __launch_bounds__(KT) cgs_update_dot_kernel(const double* __restrict__ V, int64_t n, int nv,
+                                                            const double* __restrict__ h, double* w, double* part,
+                                                            const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  __shared__ double red[(KT / 32) * NVMAX];
+  __shared__ double hs[NVMAX];
+  __shared__ double ssum[KT / 32];
+  for (int i = threadIdx.x; i < NVMAX; i += blockDim.x) hs[i] = i < nv ? h[i] : 0.0;
+  __syncthreads();
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double acc[(NVMAX + 31) / 32];
+#pragma unroll
+  for (int a = 0; a < (NVMAX + 31) / 32; ++a) acc[a] = 0.0;
+  double ss = 0.0;
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t idx = base + threadIdx.x;
+    const bool in = idx < hi;
+    double v[NVMAX];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i) v[i] = (i < nv && in) ? V[(size_t)i * n + idx] : 0.0;
+    double wv = in ? w[idx] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) wv -= hs[i] * v[i];
+    if (in) w[idx] = wv;
+    ss += wv * wv;
+    warp_dots_accum<NVMAX>(v, nv, wv, acc);
+  }
+  block_store_dots<NVMAX>(acc, nv, red, part + (size_t)blockIdx.x * (nv + 1));
+  for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  if ((threadIdx.x & 31) == 0) ssum[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += ssum[w2];
+    part[(size_t)blockIdx.x * (nv + 1) + nv] = s;
+  }
+}
+
+// V_{j+1} = (w' - sum_i h_i V_i) * sm[inv_off]
+template <int NVMAX>
+__global__ void __launch_bounds__(KT) cgs_update_scale_kernel(const double* __restrict__ V, int64_t n, int nv,
+                                                              const double* __restrict__ h,
+                                                              const double* __restrict__ w, const double* sm,
+                                                              int inv_off, double* out, const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  __shared__ double hs[NVMAX];
+  for (int i = threadIdx.x; i < NVMAX; i += blockDim.x) hs[i] = i < nv ? h[i] : 0.0;
+  __syncthreads();
+  const double inv = sm[inv_off];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double v[NVMAX];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i) v[i] = i < nv ? V[(size_t)i * n + idx] : 0.0;
+    double wv = w[idx];
+#pragma unroll
+    for (int i = 0; i < NVMAX; ++i)
+      if (i < nv) wv -= hs[i] * v[i];
+    out[idx] = wv * inv;
+  }
+}
+
+// Sum the per-block partials of nv dot products (stride nv + 1) in block order.
+// mode 0: H column := s; mode 1: H column += s and the squared norm of the new
+// vector is ||w'||^2 - ||s||^2 (the second projection removes s from w').
+__global__ void cgs_reduce_kernel(const double* part, int G, int nv, double* Hcol, double* htmp, int mode,
+                                  double* sm, int norm_off, const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  __shared__ double sq[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int stride = nv + 1;
+  const int cnt = mode ? nv + 1 : nv;
+  double local_sq = 0.0;
+  for (int i = wid; i < cnt; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += part[(size_t)b * stride + i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      if (i < nv) {
+        htmp[i] = s;
+        Hcol[i] = mode ? Hcol[i] + s : s;
+        local_sq += s * s;
+      } else {
+        sq[31] = s;   // ||w'||^2
+      }
+    }
+  }
+  if (!mode) return;
+  if (lane == 0) sq[wid] = local_sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) hh += sq[w2];
+    const double ww = sq[31];
+    const double d = ww - hh;
+    sm[norm_off] = d > 0.0 ? d : 0.0;
+  }
+}
+
 // out = a * x + b * y; part[b] = block sum of out^2
 __global__ void __launch_bounds__(KT) axpby_norm_kernel(double a, const double* x, double b, const double* y,
                                                         double* out, int64_t n, double* part) {
@@ -172,7 +336,8 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
 // norm of the new basis vector, Givens rotations, residual estimate
 __global__ void givens_kernel(double* sm, SmallLayout L, int* flags, const double* part, int G, int j) {
   if (flags[F_STOP]) return;
-  const double hn = sqrt(warp_sum_partials(part, G));
+  // squared norm of the new vector: from block partials, or precomputed in sm (part == nullptr)
+  const double hn = sqrt(part ? warp_sum_partials(part, G) : sm[L.sc + 5]);
   if (threadIdx.x != 0) return;
   const int K1 = L.K + 1;
   double* h = sm + L.H + (size_t)j * K1;
@@ -227,6 +392,25 @@ __global__ void sum_partials_kernel(const double* part, int G, double* out) {
   if (threadIdx.x == 0) *out = s;
 }
 
+// pass 0: dots of w; pass 1: update w in place + dots + norm; pass 2: update + scale into out
+template <int NV>
+static void cgs_pass(int pass, const double* V, int64_t n, int nv, double* w, double* part, double* sm,
+                     const SmallLayout& L, const int* fl, double* out, cudaStream_t st) {
+  if (pass == 0) cgs_dot_kernel<NV><<<KG, KT, 0, st>>>(V, n, nv, w, part, fl);
+  else if (pass == 1) cgs_update_dot_kernel<NV><<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, w, part, fl);
+  else cgs_update_scale_kernel<NV><<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, w, sm, L.sc + 4, out, fl);
+}
+
+static cudaError_t launch_cgs(int nv, int pass, const double* V, int64_t n, double* w, double* part, double* sm,
+                              const SmallLayout& L, double* Hcol, const int* fl, double* out, cudaStream_t st) {
+  (void)Hcol;
+  if (nv <= 8) cgs_pass<8>(pass, V, n, nv, w, part, sm, L, fl, out, st);
+  else if (nv <= 16) cgs_pass<16>(pass, V, n, nv, w, part, sm, L, fl, out, st);
+  else if (nv <= 32) cgs_pass<32>(pass, V, n, nv, w, part, sm, L, fl, out, st);
+  else cgs_pass<64>(pass, V, n, nv, w, part, sm, L, fl, out, st);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ driver
 namespace {
 struct Cu {
@@ -258,7 +442,7 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   cudaError_t e;
   if ((e = cudaMalloc(&c->d_V, (size_t)(K + 1) * n * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_w, n * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_r, 3 * n * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_part, (size_t)KG * (K + 2) * sizeof(double))) != cudaSuccess) return e;
   SmallLayout L(K);
   if ((e = cudaMalloc(&c->d_small, (size_t)L.total * sizeof(double))) != cudaSuccess) return e;
@@ -276,96 +460,39 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 
 #define LAUNCHED(k) (c->launches += (k))
 
-hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
-  const Params& P = c->prm;
-  const int K = o.restart;
-  const int64_t n = P.N_tr;
-  cudaStream_t st = c->stream;
-  Cu cu{c};
-  if (!cu.ok(ensure_krylov(c, K))) return fail(c, HDG_ERR_OOM, std::string("Krylov workspace: ") + cudaGetErrorString(cu.err));
-  SmallLayout L(K);
-  double* sm = c->d_small;
-  int* fl = c->d_flag;
-  double* V = c->d_V;
-  double* w = c->d_w;
-  double* bt = c->d_r;          // D^-1 g
-  double* rr = c->d_r + n;      // scratch residual
-  double* part = c->d_part;
-  rep = hdg_solve_report{};
+namespace {
 
-  // ||g||, D^-1 g, ||D^-1 g||
-  axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, 0.0, g, rr, n, part);
-  sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
-  LAUNCHED(2);
-  const double gnorm = std::sqrt(read_scalar(c, sm + L.sc + 5, cu));
-  cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, g, bt, st));
-  axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, bt, 0.0, bt, rr, n, part);
-  sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
-  LAUNCHED(3);
-  const double btnorm = std::sqrt(read_scalar(c, sm + L.sc + 5, cu));
-  if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
-  if (gnorm == 0.0) {
-    cu.ok(cudaMemsetAsync(x, 0, n * sizeof(double), st));
-    cu.ok(cudaStreamSynchronize(st));
-    rep.converged = 1;
-    return cu.err == cudaSuccess ? HDG_OK : fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
+__global__ void __launch_bounds__(KT) axpy_kernel(double a, const double* __restrict__ xv, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * xv[i];
+}
+
+// Restart cycles of left-preconditioned GMRES on one context.
+struct Solver {
+  hdg_ctx* c;
+  const Params& P;
+  int K;
+  int64_t n;
+  cudaStream_t st;
+  Cu cu;
+  SmallLayout L;
+  double *sm, *V, *w, *part, *rr;
+  int* fl;
+
+  Solver(hdg_ctx* ctx, int k)
+      : c(ctx), P(ctx->prm), K(k), n(ctx->prm.N_tr), st(ctx->stream), cu{ctx}, L(k), sm(ctx->d_small),
+        V(ctx->d_V), w(ctx->d_w), part(ctx->d_part), rr(ctx->d_r + 2 * ctx->prm.N_tr), fl(ctx->d_flag) {}
+
+  // ||v||^2 (synchronises)
+  double norm2(const double* v) {
+    axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, v, 0.0, v, rr, n, part);
+    sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
+    LAUNCHED(2);
+    return read_scalar(c, sm + L.sc + 5, cu);
   }
-  double target = o.tol * btnorm;
-  int its = 0;
-  double rel = 1.0;
-  while (true) {
-    // r0 = D^-1 g - D^-1 S x ; V0 = r0 / beta
-    double tgt = target;
-    cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &tgt, sizeof(double), cudaMemcpyHostToDevice, st));
-    {
-      ProfScope ps(c, HDG_PROF_APPLY);
-      cu.ok(launch_apply64(P, c->d_St, x, w, c->d_escale, nullptr, st));
-    }
-    axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, bt, -1.0, w, rr, n, part);
-    cycle_init_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG);
-    scale_kernel<<<KG, KT, 0, st>>>(rr, sm, L.sc + 4, V, n, fl);
-    LAUNCHED(4);
-    const int jmax = std::min(K, o.maxit - its);
-    std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
-    for (int j = 0; j < jmax; ++j) {
-      mark[j] = c->prof_ev.size();
-      double* Vj = V + (size_t)j * n;
-      double* Hcol = sm + L.H + (size_t)j * (K + 1);
-      {
-        ProfScope ps(c, HDG_PROF_APPLY);
-        cu.ok(launch_apply64(P, c->d_St, Vj, w, c->d_escale, fl, st));
-      }
-      ProfScope po(c, HDG_PROF_ORTHO);
-      mdot_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, w, part, fl);
-      mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, j + 1, Hcol, sm + L.htmp, 0, fl);
-      update_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, sm + L.htmp, -1.0, w, nullptr, fl);
-      mdot_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, w, part, fl);
-      mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, j + 1, Hcol, sm + L.htmp, 1, fl);
-      update_kernel<<<KG, KT, 0, st>>>(V, n, j + 1, sm + L.htmp, -1.0, w, part, fl);
-      givens_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG, j);
-      scale_kernel<<<KG, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * n, n, fl);
-      LAUNCHED(9);
-    }
-    cu.ok(cudaGetLastError());
-    int hflags[2] = {0, 0};
-    cu.ok(cudaMemcpyAsync(hflags, fl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    cu.ok(cudaStreamSynchronize(st));
-    if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
-    const int jused = hflags[F_JUSED];
-    if (c->prof_on && jused < jmax) {
-      // steps after the stop flag was raised were enqueued but returned at once: not timed work
-      for (size_t i = mark[jused]; i < c->prof_ev.size(); ++i) c->prof_pool.push_back(c->prof_ev[i].second);
-      c->prof_ev.resize(mark[jused]);
-    }
-    const double est = read_scalar(c, sm + L.sc + 1, cu);
-    its += jused;
-    rep.restarts += 1;
-    if (jused > 0) {
-      lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
-      update_kernel<<<KG, KT, 0, st>>>(V, n, jused, sm + L.y, 1.0, x, nullptr, nullptr);
-      LAUNCHED(2);
-    }
-    // true residual with the unpreconditioned FP64 operator
+
+  // ||g - S x|| / gnorm with the FP64 S; leaves g - S x in rr
+  double true_rel(const double* g, const double* x, double gnorm) {
     {
       ProfScope ps(c, HDG_PROF_APPLY);
       cu.ok(launch_apply64(P, c->d_S, x, w, nullptr, nullptr, st));
@@ -373,16 +500,166 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, -1.0, w, rr, n, part);
     sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
     LAUNCHED(3);
-    rel = std::sqrt(read_scalar(c, sm + L.sc + 5, cu)) / gnorm;
-    if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
-    rep.iterations = its;
-    rep.rel_residual = rel;
-    if (rel <= o.tol) {
-      rep.converged = 1;
-      return HDG_OK;
+    return std::sqrt(read_scalar(c, sm + L.sc + 5, cu)) / gnorm;
+  }
+
+  // One restart cycle for op(x) = bt (op = preconditioned operator, phase = its
+  // profiling phase): at most jmax Arnoldi steps, early stop when the residual
+  // estimate falls to target; x is updated. Returns the steps taken.
+  template <class Op>
+  int cycle(Op op, int phase, const double* bt, double* x, double target, int jmax, double& est) {
+    double* r0 = w;   // op(x) lands in w, r0 in rr
+    cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &target, sizeof(double), cudaMemcpyHostToDevice, st));
+    {
+      ProfScope ps(c, phase);
+      cu.ok(op(x, r0, nullptr));
     }
-    if (its >= o.maxit || jused == 0) break;
-    if (est <= target) target *= 0.5 * o.tol / rel;
+    axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, bt, -1.0, r0, rr, n, part);
+    cycle_init_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG);
+    scale_kernel<<<KG, KT, 0, st>>>(rr, sm, L.sc + 4, V, n, fl);
+    LAUNCHED(4);
+    std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
+    for (int j = 0; j < jmax; ++j) {
+      mark[j] = c->prof_ev.size();
+      double* Vj = V + (size_t)j * n;
+      double* Hcol = sm + L.H + (size_t)j * (K + 1);
+      {
+        ProfScope ps(c, phase);
+        cu.ok(op(Vj, w, fl));
+      }
+      ProfScope po(c, HDG_PROF_ORTHO);
+      const int nv = j + 1;
+      if (nv <= 64) {
+        // CGS2 in three passes over the basis: dots, update + second dots + norm, update + scale
+        cu.ok(launch_cgs(nv, 0, V, n, w, part, sm, L, Hcol, fl, V + (size_t)(j + 1) * n, st));
+        cgs_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 0, sm, L.sc + 5, fl);
+        cu.ok(launch_cgs(nv, 1, V, n, w, part, sm, L, Hcol, fl, V + (size_t)(j + 1) * n, st));
+        cgs_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 1, sm, L.sc + 5, fl);
+        givens_kernel<<<1, 32, 0, st>>>(sm, L, fl, nullptr, 0, j);
+        cu.ok(launch_cgs(nv, 2, V, n, w, part, sm, L, Hcol, fl, V + (size_t)(j + 1) * n, st));
+        LAUNCHED(6);
+      } else {
+        mdot_kernel<<<KG, KT, 0, st>>>(V, n, nv, w, part, fl);
+        mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 0, fl);
+        update_kernel<<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, -1.0, w, nullptr, fl);
+        mdot_kernel<<<KG, KT, 0, st>>>(V, n, nv, w, part, fl);
+        mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 1, fl);
+        update_kernel<<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, -1.0, w, part, fl);
+        givens_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG, j);
+        scale_kernel<<<KG, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * n, n, fl);
+        LAUNCHED(9);
+      }
+    }
+    cu.ok(cudaGetLastError());
+    int hflags[2] = {0, 0};
+    cu.ok(cudaMemcpyAsync(hflags, fl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    cu.ok(cudaStreamSynchronize(st));
+    const int jused = hflags[F_JUSED];
+    if (c->prof_on && jused < jmax) {
+      // steps after the stop flag was raised were enqueued but returned at once: not timed work
+      for (size_t i = mark[jused]; i < c->prof_ev.size(); ++i) c->prof_pool.push_back(c->prof_ev[i].second);
+      c->prof_ev.resize(mark[jused]);
+    }
+    est = read_scalar(c, sm + L.sc + 1, cu);
+    if (jused > 0) {
+      lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
+      update_kernel<<<KG, KT, 0, st>>>(V, n, jused, sm + L.y, 1.0, x, nullptr, nullptr);
+      LAUNCHED(2);
+    }
+    return jused;
+  }
+};
+
+}  // namespace
+
+// FP32 + iterative refinement: inner GMRES on the FP32 blocks reduces the
+// preconditioned correction residual by this factor per outer sweep.
+constexpr double IR_INNER_REDUCTION = 1e-4;
+
+hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
+  const Params& P = c->prm;
+  const int K = o.restart;
+  const int64_t n = P.N_tr;
+  cudaStream_t st = c->stream;
+  Cu cu{c};
+  if (!cu.ok(ensure_krylov(c, K))) return fail(c, HDG_ERR_OOM, std::string("Krylov workspace: ") + cudaGetErrorString(cu.err));
+  Solver S(c, K);
+  double* bt = c->d_r;          // preconditioned right-hand side
+  double* d = c->d_r + n;       // IR correction
+  rep = hdg_solve_report{};
+  auto op64 = [&](const double* xin, double* yout, const int* stop) -> cudaError_t {
+    return launch_apply64(P, c->d_St, xin, yout, c->d_escale, stop, st);
+  };
+  auto opdf = [&](const double* xin, double* yout, const int* stop) -> cudaError_t {
+    return launch_apply_df(P, c->d_Stdf, xin, yout, c->d_escale, stop, st);
+  };
+  auto op32 = [&](const double* xin, double* yout, const int* stop) -> cudaError_t {
+    return launch_apply32x64(P, c->d_St32, xin, yout, c->d_escale, stop, st);
+  };
+
+  const double gnorm = std::sqrt(S.norm2(g));
+  if (S.cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(S.cu.err));
+  if (gnorm == 0.0) {
+    cu.ok(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    cu.ok(cudaStreamSynchronize(st));
+    rep.converged = 1;
+    return cu.err == cudaSuccess ? HDG_OK : fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
+  }
+  int its = 0;
+  double rel = 1.0;
+  if (o.mode == 0 || o.mode == 2) {
+    cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, g, bt, st));
+    LAUNCHED(1);
+    const double btnorm = std::sqrt(S.norm2(bt));
+    double target = o.tol * btnorm;
+    while (true) {
+      double est = 0.0;
+      const int jmax = std::min(K, o.maxit - its);
+      const int jused = o.mode == 2 ? S.cycle(opdf, HDG_PROF_APPLY, bt, x, target, jmax, est)
+                                    : S.cycle(op64, HDG_PROF_APPLY, bt, x, target, jmax, est);
+      its += jused;
+      rep.restarts += 1;
+      rel = S.true_rel(g, x, gnorm);
+      if (S.cu.err != cudaSuccess || cu.err != cudaSuccess)
+        return fail(c, HDG_ERR_CUDA, cudaGetErrorString(S.cu.err != cudaSuccess ? S.cu.err : cu.err));
+      rep.iterations = its;
+      rep.rel_residual = rel;
+      if (rel <= o.tol) {
+        rep.converged = 1;
+        return HDG_OK;
+      }
+      if (its >= o.maxit || jused == 0) break;
+      if (est <= target) target *= 0.5 * o.tol / rel;
+    }
+  } else {
+    // FP32 + iterative refinement: r = g - S x in FP64; D^-1 S32 d = D^-1 r
+    // by GMRES on the FP32 blocks; x += d.
+    while (true) {
+      rel = S.true_rel(g, x, gnorm);           // leaves r in S.rr
+      if (S.cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(S.cu.err));
+      rep.rel_residual = rel;
+      rep.iterations = its;
+      if (rel <= o.tol) {
+        rep.converged = 1;
+        return HDG_OK;
+      }
+      if (its >= o.maxit) break;
+      rep.outer += 1;
+      cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, S.rr, bt, st));
+      cu.ok(cudaMemsetAsync(d, 0, n * sizeof(double), st));
+      LAUNCHED(1);
+      const double btnorm = std::sqrt(S.norm2(bt));
+      const double target = IR_INNER_REDUCTION * btnorm;
+      double est = btnorm;
+      while (est > target && its < o.maxit) {
+        const int jused = S.cycle(op32, HDG_PROF_APPLY32, bt, d, target, std::min(K, o.maxit - its), est);
+        its += jused;
+        rep.restarts += 1;
+        if (jused == 0) break;
+      }
+      axpy_kernel<<<KG, KT, 0, st>>>(1.0, d, x, n);
+      LAUNCHED(1);
+    }
   }
   rep.converged = 0;
   return fail(c, HDG_ERR_NOCONV, "GMRES reached maxit with relative residual " + std::to_string(rel));

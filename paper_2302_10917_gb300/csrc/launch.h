@@ -21,6 +21,11 @@ cudaError_t launch_apply64(const Params& P, const double* S, const double* x, do
                            const int* stop, cudaStream_t st);
 cudaError_t launch_apply32(const Params& P, const float* S, const float* x, float* y, const double* escale,
                            const int* stop, cudaStream_t st);
+cudaError_t launch_apply32x64(const Params& P, const float* S, const double* x, double* y, const double* escale,
+                              const int* stop, cudaStream_t st);
+cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
+                            const int* stop, cudaStream_t st);
+cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
                              cudaStream_t st);

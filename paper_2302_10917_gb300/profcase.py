@@ -1,0 +1,58 @@
+"""Small, self-contained run of the hot-path kernels for profiler captures.
+
+    python -m paper_2302_10917_gb300.profcase --n 64 --m 8 --p 3 --applies 4
+
+Builds the n x n macro mesh with the manufactured source, condenses it with a
+chunked workspace (factors not kept, a few GB on the device at most), then
+runs `applies` FP64 preconditioned trace applies, then one unpreconditioned
+FP64 apply, one split-FP32 (df64) apply and one FP32 apply. Prints the device
+time of each phase.
+"""
+import argparse
+import json
+import math
+
+import torch
+
+from . import Problem
+from . import workloads as wl
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--m", type=int, default=8)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--applies", type=int, default=4)
+    a = ap.parse_args(argv)
+    beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
+    pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
+    xy = pr.quad_points()
+    pr.set_source(wl.sin_sin_source(xy, 1.0, beta))
+    del xy
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t = [ev() for _ in range(7)]
+    t[0].record()
+    pr.condense(store_fp32=True, keep_factors=False, store_df64=True)
+    t[1].record()
+    x = torch.from_numpy(wl.random_vector(pr.info["N_tr"], seed=5)).cuda()
+    for _ in range(a.applies):
+        y = pr.apply(x, precond=True)
+    t[2].record()
+    y = pr.apply(x, precond=False)
+    t[3].record()
+    y32 = pr.apply(x.float(), precond=True, prec=32)
+    t[4].record()
+    ydf = pr.apply(x, precond=True, prec=48)
+    t[5].record()
+    torch.cuda.synchronize()
+    out = {"info": pr.info, "condense_ms": t[0].elapsed_time(t[1]),
+           "apply64_pc_ms": t[1].elapsed_time(t[2]) / max(1, a.applies), "apply64_ms": t[2].elapsed_time(t[3]),
+           "apply32_ms": t[3].elapsed_time(t[4]), "apply_df_ms": t[4].elapsed_time(t[5]),
+           "y_norm": float(y.norm()), "y32_norm": float(y32.norm()), "ydf_norm": float(ydf.norm())}
+    print(json.dumps(out))
+    pr.close()
+
+
+if __name__ == "__main__":
+    main()

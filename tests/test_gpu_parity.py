@@ -59,7 +59,7 @@ def case(request):
     gD = g.standard_normal(bpts.shape[:2])
     S_el, g_ora, ghat = ora.condense(f_qp, gD)
     gpu.set_source(torch.from_numpy(f_qp), torch.from_numpy(gD))
-    gpu.condense(store_fp32=True, keep_factors=True)
+    gpu.condense(store_fp32=True, keep_factors=True, store_df64=True)
     torch.cuda.synchronize()
     yield dict(ora=ora, gpu=gpu, f=f_qp, gD=gD, S_el=S_el, g=g_ora, ghat=ghat, n=n, m=m, p=p, rng=g)
     gpu.close()
@@ -124,6 +124,15 @@ def test_fp32_preconditioned_apply(case):
     assert rel(z32, z_ora) < 5e-5
 
 
+def test_split_fp32_preconditioned_apply(case):
+    """Blocks stored as FP32 hi/lo pairs, products on the FP32 pipe: FP64-level agreement."""
+    ora, gpu, S_el = case["ora"], case["gpu"], case["S_el"]
+    x = case["rng"].standard_normal(ora.mesh.N_tr)
+    z_ora = ora.apply_Dinv(ora.apply_S(S_el, x))
+    z_df = gpu.apply(torch.from_numpy(x), precond=True, prec=48).cpu().numpy()
+    assert rel(z_df, z_ora) < 1e-12
+
+
 def test_recover_from_same_trace(case):
     ora, gpu = case["ora"], case["gpu"]
     x = np.linalg.solve(ora.assemble_S(case["S_el"]), case["g"])
@@ -148,6 +157,30 @@ def test_gmres_solution_matches_direct_solve(case):
     u_o, q_o = ora.recover(x_dir, case["f"], case["ghat"])
     assert rel(u_g.cpu().numpy(), u_o) < 1e-8
     assert rel(q_g.cpu().numpy(), q_o) < 1e-7
+
+
+def test_gmres_split_fp32_apply_mode(case):
+    """mode 2: FP64 GMRES with the split-FP32 preconditioned apply; the FP64 residual decides."""
+    ora, gpu = case["ora"], case["gpu"]
+    S = ora.assemble_S(case["S_el"])
+    x_dir = np.linalg.solve(S, case["g"])
+    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=2)
+    assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10
+    x_gpu = x_gpu.cpu().numpy()
+    assert np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) <= 1.01e-10
+    assert rel(x_gpu, x_dir) < 1e-8
+
+
+def test_gmres_fp32_iterative_refinement_mode(case):
+    """mode 1: FP32 blocks inside FP64 iterative refinement still reach the FP64 residual."""
+    ora, gpu = case["ora"], case["gpu"]
+    S = ora.assemble_S(case["S_el"])
+    x_dir = np.linalg.solve(S, case["g"])
+    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=20000, mode=1)
+    assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10 and rep["outer"] >= 1
+    x_gpu = x_gpu.cpu().numpy()
+    assert np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) <= 1.01e-10
+    assert rel(x_gpu, x_dir) < 1e-8
 
 
 def test_solve_is_bitwise_reproducible(case):
