@@ -202,6 +202,29 @@ hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_
                         const hdg_solve_opts* opts, double* x_host, double* u_host,
                         double* q_host, hdg_solve_report* report);
 
+/* Condensation without any device allocation. This entry point has no
+ * counterpart in the paper: it exists for callers that must not allocate
+ * device memory after start-up (an application that owns and pre-plans all
+ * device memory, a run that must not hit out-of-memory midway, code on a path
+ * where an allocation and its implicit synchronisation are not allowed).
+ * It condenses elements e0 .. e0+count-1 exactly like hdg_condense, but the
+ * local factorisations use a fixed scratch array compiled into the library
+ * (MEHDG_STATIC_SCRATCH_BYTES, held on every GPU that loads the library until
+ * the process exits) and the results go to caller buffers: S_dev receives
+ * S_e row-major [count][n_t][n_t] (same layout as hdg_get_schur) and g_dev,
+ * if not NULL, the element right-hand sides -C_e A_e^-1 R_e - S_e g^_e
+ * [count][n_t]. Requires hdg_set_source; needs no hdg_condense and does not
+ * change the context's stored blocks. count is limited to
+ * MEHDG_STATIC_SCRATCH_BYTES / ((Q + n_t) * ld * 8) elements (ld = Q + n_t + 1
+ * rounded up to a multiple of 4); a larger count returns HDG_ERR_ARG with the
+ * limit in the message. The first call on a device looks up the scratch
+ * array's device address (once per device), so make that first call before
+ * any stream capture. Every call shares the array and leaves its contents
+ * behind; calls that overlap on the GPU race on it. Synchronous (it reads a
+ * zero-pivot flag back): HDG_ERR_SINGULAR if a local pivot is zero. */
+#define MEHDG_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+hdg_status hdg_condense_static(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev, double* g_dev);
+
 /* Per-phase device timing (tracing). Phases: */
 #define HDG_PROF_CONDENSE 0   /* condensation kernel launches (element build + LU + Schur) */
 #define HDG_PROF_APPLY 1      /* FP64 trace-operator apply launches (hdg_apply and inside hdg_solve) */

@@ -22,7 +22,9 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_C
 
 EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", "hdg_set_source",
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
-            "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_last_error", "hdg_destroy"]
+            "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_last_error",
+            "hdg_destroy"]
+STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32"]
 
 
@@ -87,6 +89,7 @@ def load_library(path=LIB_PATH):
     lib.hdg_recover.argtypes = [vp, dp, dp, dp, ctypes.c_int]
     lib.hdg_get_schur.argtypes = [vp, i64, i64, dp]
     lib.hdg_run_host.argtypes = [vp, dp, dp, ctypes.POINTER(SolveOpts), dp, dp, dp, ctypes.POINTER(SolveReport)]
+    lib.hdg_condense_static.argtypes = [vp, i64, i64, dp, dp]
     lib.hdg_profile.argtypes = [vp, ctypes.c_int]
     lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
@@ -233,6 +236,11 @@ class Problem:
         S = self._f64(count, self.info["n_t"], self.info["n_t"])
         self._check(self.lib.hdg_get_schur(self.h, e0, count, _ptr(S)))
         return S
+
+    def condense_static(self, e0, count, S_out, g_out=None):
+        """hdg_condense_static: condense elements e0..e0+count-1 into caller buffers using the
+        library's fixed scratch array (no device allocation inside the call)."""
+        self._check(self.lib.hdg_condense_static(self.h, e0, count, _ptr(S_out), _ptr(g_out)))
 
     def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True):
         """End-to-end call on host (ideally pinned) tensors; returns (x, u, q, report)."""
