@@ -104,11 +104,13 @@ typedef struct {
   int64_t launches;      /* CUDA kernels this context has enqueued since hdg_create */
 } hdg_info_t;
 
-/* Solve options. mode: 0 = FP64 GMRES, FP64 preconditioned apply;
- * 1 = FP32 Schur blocks inside FP64 iterative refinement (requires
- * HDG_STORE_FP32); 2 = FP64 GMRES whose preconditioned apply runs in split
- * FP32 ("double-float", 48-bit significand) arithmetic on the FP32 pipe
- * (requires HDG_STORE_DF64). The stopping test always uses the FP64 S. */
+/* Solve options. Every restart cycle starts from the true FP64 residual
+ * g - S x (the stopping test) and builds the Krylov basis in split-FP32
+ * ("double-float", 48-bit significand) arithmetic; mode selects the
+ * preconditioned Arnoldi operator: 0 = FP64 blocks, FP64 arithmetic;
+ * 1 = FP32 blocks (requires HDG_STORE_FP32), i.e. FP32 inside FP64 iterative
+ * refinement; 2 = split-FP32 blocks on the FP32 pipe (requires
+ * HDG_STORE_DF64). */
 typedef struct {
   double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
   int maxit;             /* maximum number of operator applications inside GMRES */
@@ -119,7 +121,7 @@ typedef struct {
 typedef struct {
   int iterations;        /* Arnoldi steps (preconditioned operator applications) */
   int restarts;          /* GMRES cycles */
-  int outer;             /* iterative-refinement sweeps (mode 1), else 0 */
+  int outer;             /* FP64 true-residual evaluations (one per restart cycle, plus the last) */
   int converged;         /* 1 if rel_residual <= tol */
   double rel_residual;   /* true relative residual at exit, computed with FP64 S */
 } hdg_solve_report;
@@ -128,6 +130,8 @@ typedef struct {
 #define HDG_STORE_FP32 1u      /* also keep an FP32 copy of the preconditioned blocks */
 #define HDG_KEEP_FACTORS 2u    /* keep the factored local systems for hdg_recover (else recover refactors) */
 #define HDG_STORE_DF64 4u      /* also keep the preconditioned blocks as FP32 hi/lo pairs (8 bytes per entry) */
+#define HDG_SPLIT_UPDATE 8u    /* form the LU's panel products in split-FP32 arithmetic (FP32 pipe);
+                                  pivots, triangular solves and the stored entries stay FP64 */
 
 /* Build the structured macro mesh, the reference-lattice tables of level m
  * (mass, derivative, boundary and trace matrices, quadrature) and the device

@@ -254,7 +254,9 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
 hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
-  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64)) return set_err(c, HDG_ERR_ARG, "unknown flags");
+  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE))
+    return set_err(c, HDG_ERR_ARG, "unknown flags");
+  const int split = (flags & HDG_SPLIT_UPDATE) ? 1 : 0;
   const Params& P = c->prm;
   cudaError_t e;
   const size_t sblk = (size_t)P.N * 3 * P.n_t * P.P1;
@@ -270,7 +272,9 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
   if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
   const size_t slot = (size_t)P.R * P.ld;
-  const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, 2048);
+  // without HDG_KEEP_FACTORS the elements are condensed in chunks that fit a 1 GiB workspace
+  const int64_t budget_slots = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (slot * sizeof(double))));
+  const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, budget_slots);
   if (c->ws_slots != want) {
     dev_free(c, c->d_ws, (size_t)c->ws_slots * slot);
     c->ws_slots = 0;
@@ -284,7 +288,7 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     {
       ProfScope ps(c, HDG_PROF_CONDENSE);
       e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, keep, 1, c->d_S, c->d_St,
-                          (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream);
+                          (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream, split);
     }
     c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
@@ -372,7 +376,7 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
     for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
       const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
       e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, 0, 0, nullptr, nullptr, nullptr,
-                          nullptr, nullptr, c->stream);
+                          nullptr, nullptr, c->stream, (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
       if (e != cudaSuccess) return cuda_err(c, e, "refactor");
       e = launch_recover(P, c->dt, c->d_ws, e0, cnt, 0, x, gh, u, q, c->stream);
       c->launches += 2;
@@ -468,7 +472,7 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
   cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
-  cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_x32);
+  cudaFree(c->d_small); cudaFree(c->d_flag);
   delete c;
 }
 

@@ -16,8 +16,15 @@
 // (gathered with orientation flips, Dirichlet edges contribute 0) and streams
 // the matching row-blocks S[e][k][j][t] (contiguous in t) from HBM.
 #include "internal.h"
+#include "df64.h"
+#include <type_traits>
 
 namespace mehdg {
+
+int apply_edges_per_block(const Params& P) {
+  int epb = 256 / P.P1;
+  return epb < 1 ? 1 : epb;
+}
 
 template <typename T, typename TX, typename Acc>
 __global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restrict__ S, const TX* __restrict__ x,
@@ -90,18 +97,6 @@ __global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restric
 // Knuth's two-sum) on the FP32 pipe; the two FP32 words are combined in FP64
 // once per output.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void df_fma(float& ah, float& al, float sh, float sl, float xh, float xl) {
-  const float p = sh * xh;
-  const float e = fmaf(sh, xh, -p);          // sh*xh = p + e exactly
-  const float t = ah + p;                    // two-sum(ah, p) = t + err
-  const float bp = t - ah;
-  const float err = (ah - (t - bp)) + (p - bp);
-  ah = t;
-  al = fmaf(sh, xl, al);
-  al = fmaf(sl, xh, al);
-  al += e + err;
-}
-
 __global__ void __launch_bounds__(256) apply_df_kernel(Params P, const float2* __restrict__ S,
                                                        const double* __restrict__ x, double* __restrict__ y,
                                                        const double* __restrict__ escale, int epb,
@@ -150,18 +145,163 @@ __global__ void __launch_bounds__(256) apply_df_kernel(Params P, const float2* _
       for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
-        df_fma(h0, l0, sv[u].x, sv[u].y, xv[j + u].x, xv[j + u].y);
-        df_fma(h1, l1, sv[u + 1].x, sv[u + 1].y, xv[j + u + 1].x, xv[j + u + 1].y);
+        df_fma(h0, l0, sv[u], xv[j + u]);
+        df_fma(h1, l1, sv[u + 1], xv[j + u + 1]);
       }
     }
     for (; j < nt; ++j) {
-      const float2 sv = base[(size_t)j * P1];
-      df_fma(h0, l0, sv.x, sv.y, xv[j].x, xv[j].y);
+      df_fma(h0, l0, base[(size_t)j * P1], xv[j]);
     }
   }
   double r = ((double)h0 + (double)h1) + ((double)l0 + (double)l1);
   if (escale) r *= escale[f];
   y[(size_t)f * P1 + s] = r;
+}
+
+// The same edge-centric apply on split-FP32 vectors (Krylov basis storage):
+// BT = 0: FP64 blocks, FP64 accumulation; BT = 1: split-FP32 blocks and
+// accumulation on the FP32 pipe; BT = 2: FP32 blocks, FP32 accumulation.
+template <int BT>
+__global__ void __launch_bounds__(256) apply_vdf_kernel(Params P, const void* __restrict__ Sv,
+                                                        const float2* __restrict__ x, float2* __restrict__ y,
+                                                        const double* __restrict__ escale, int epb,
+                                                        const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  using XT = typename std::conditional<BT == 0, double, typename std::conditional<BT == 1, float2, float>::type>::type;
+  extern __shared__ unsigned char sraw[];
+  XT* xs = reinterpret_cast<XT*>(sraw);   // [epb][2][n_t]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  const int f0 = blockIdx.x * epb;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < epb * 2 * nt; idx += blockDim.x) {
+    const int le = idx / (2 * nt);
+    const int rem = idx - le * 2 * nt;
+    const int sd = rem / nt, c = rem - sd * nt;
+    const int f = f0 + le;
+    float2 v = make_float2(0.f, 0.f);
+    if (f < P.n_int) {
+      int e[2], k[2], fl[2];
+      double len;
+      edge_sides(f, P.n, e, k, fl, &len);
+      int code[3], flip[3];
+      elem_edges(e[sd], P.n, code, flip);
+      const int kk = c / P1, t = c - kk * P1;
+      if (code[kk] >= 0) v = x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+    }
+    if constexpr (BT == 0) xs[idx] = df_to(v);
+    else if constexpr (BT == 1) xs[idx] = v;
+    else xs[idx] = v.x;
+  }
+  __syncthreads();
+  const int le = tid / P1, s = tid - le * P1;
+  const int f = f0 + le;
+  if (le >= epb || f >= P.n_int) return;
+  int e[2], k[2], fl[2];
+  double len;
+  edge_sides(f, P.n, e, k, fl, &len);
+  float2 out;
+  // both sides' terms as one sequence q = 0 .. 2 n_t - 1; loads of the next
+  // batch of 8 are issued before the arithmetic of the current one
+  const int t0 = fl[0] ? PP - s : s, t1 = fl[1] ? PP - s : s;
+  const int nq = 2 * nt;
+  if constexpr (BT == 1) {
+    const float2* S = static_cast<const float2*>(Sv);
+    const float2* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
+    const float2* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
+    const float2* xv = xs + le * 2 * nt;       // side 0 then side 1, contiguous
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    float2 cur[8], nxt[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : make_float2(0.f, 0.f);
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + 8 + u;
+        nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const int q = q0 + u;
+        if (q < nq) df_fma(h0, l0, cur[u], xv[q]);
+        if (q + 1 < nq) df_fma(h1, l1, cur[u + 1], xv[q + 1]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    }
+    df_add(h0, l0, h1, l1);
+    if (escale) {
+      const float2 sc = df_from(escale[f]);
+      float ph = 0.f, pl = 0.f;
+      df_fma(ph, pl, make_float2(h0, l0), sc);
+      h0 = ph;
+      l0 = pl;
+    }
+    out = df_norm(h0, l0);
+  } else if constexpr (BT == 2) {
+    const float* S = static_cast<const float*>(Sv);
+    const float* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
+    const float* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
+    const float* xv = xs + le * 2 * nt;
+    float acc0 = 0.f, acc1 = 0.f;
+    float cur[8], nxt[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : 0.f;
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + 8 + u;
+        nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const int q = q0 + u;
+        if (q < nq) acc0 = fmaf(cur[u], xv[q], acc0);
+        if (q + 1 < nq) acc1 = fmaf(cur[u + 1], xv[q + 1], acc1);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    }
+    float r = acc0 + acc1;
+    if (escale) r *= (float)escale[f];
+    out = make_float2(r, 0.f);
+  } else {
+    const double* S = static_cast<const double*>(Sv);
+    double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const double* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + (sd ? t1 : t0);
+      const XT* xv = xs + (le * 2 + sd) * nt;
+      int j = 0;
+      for (; j + 8 <= nt; j += 8) {
+        double sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          acc0 += sv[u] * xv[j + u];
+          acc1 += sv[u + 1] * xv[j + u + 1];
+        }
+      }
+      for (; j < nt; ++j) acc0 += base[(size_t)j * P1] * xv[j];
+    }
+    double r = acc0 + acc1;
+    if (escale) r *= escale[f];
+    out = df_from(r);
+  }
+  y[(size_t)f * P1 + s] = out;
+}
+
+cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
+                             const double* escale, const int* stop, cudaStream_t st) {
+  const int epb = apply_edges_per_block(P);
+  const int grid = (P.n_int + epb - 1) / epb;
+  const size_t el = bt == 0 ? sizeof(double) : (bt == 1 ? sizeof(float2) : sizeof(float));
+  const size_t sm = (size_t)epb * 2 * P.n_t * el;
+  if (bt == 0) apply_vdf_kernel<0><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  else if (bt == 1) apply_vdf_kernel<1><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  else apply_vdf_kernel<2><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  return cudaGetLastError();
 }
 
 // Split an FP64 array into hi/lo FP32 pairs.
@@ -173,10 +313,6 @@ __global__ void split_df_kernel(const double* __restrict__ a, float2* __restrict
   }
 }
 
-int apply_edges_per_block(const Params& P) {
-  int epb = 256 / P.P1;
-  return epb < 1 ? 1 : epb;
-}
 
 cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
                            const int* stop, cudaStream_t st) {
@@ -210,16 +346,6 @@ cudaError_t launch_apply32(const Params& P, const float* S, const float* x, floa
   return cudaGetLastError();
 }
 
-// FP32 blocks and FP32 accumulation with FP64 vectors (inner operator of the
-// FP32 + iterative-refinement solve).
-cudaError_t launch_apply32x64(const Params& P, const float* S, const double* x, double* y, const double* escale,
-                              const int* stop, cudaStream_t st) {
-  const int epb = apply_edges_per_block(P);
-  const int grid = (P.n_int + epb - 1) / epb;
-  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float);
-  apply_kernel<float, double, float><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
-  return cudaGetLastError();
-}
 
 // Assembled right-hand side: g_f = gel_{e+}|_f + gel_{e-}|_f (fixed order).
 __global__ void assemble_rhs_kernel(Params P, const double* gel, double* g) {

@@ -17,6 +17,7 @@
 // holds [S_e | -C A^-1 R] with S_e = D_e - C_e A_e^-1 B_e, and rows 0..Q-1
 // hold U, L^-1 P B_u and L^-1 P F for the back-solve.
 #include "internal.h"
+#include "df64.h"
 
 namespace mehdg {
 
@@ -39,6 +40,7 @@ struct CondArgs {
   float* St32;
   double* gel;
   int* info;
+  int split_update;       // 1: trailing updates in split-FP32 arithmetic on the FP32 pipe
 };
 
 __device__ __forceinline__ void warp_argmax(double& v, int& i) {
@@ -233,13 +235,42 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         }
         for (int c = 0; c < nb; ++c) {
           W[(size_t)(j0 + c) * ld + j] = u[c];
-          Us[c * ld + j] = u[c];
+          if (a.split_update) reinterpret_cast<float2*>(Us)[c * ld + j] = df_from(u[c]);
+          else Us[c * ld + j] = u[c];
         }
       }
       __syncthreads();
       // trailing update A22 -= L21 U12 (rows jb..R-1, columns jb..Cc-1)
       const int nrow = R - jb;
       const int ntile = (nrow + RT - 1) / RT;
+      if (a.split_update) {
+        // L21 to (hi, lo) pairs in place; each 16-term panel product is then
+        // formed on the FP32 pipe with error-free transformations and
+        // subtracted from the FP64 entry once
+        for (int idx = tid; idx < nrow * NB; idx += nthr) {
+          const int r = nb + idx / NB, c = idx % NB;
+          double* p = Ls + r * LDP + c;
+          *reinterpret_cast<float2*>(p) = df_from(*p);
+        }
+        __syncthreads();
+        for (int item = tid; item < ntile * ncol; item += nthr) {
+          const int rt = item / ncol, j = jb + (item - rt * ncol);
+          float2 u[NB];
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            u[c] = (c < nb) ? reinterpret_cast<const float2*>(Us)[c * ld + j] : make_float2(0.f, 0.f);
+          const int r0 = jb + rt * RT;
+          const int r1 = min(r0 + RT, R);
+          for (int r = r0; r < r1; ++r) {
+            double* wp = W + (size_t)r * ld + j;
+            const float2* l = reinterpret_cast<const float2*>(Ls + (r - j0) * LDP);
+            float h = 0.f, lo = 0.f;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) df_fma(h, lo, l[c], u[c]);
+            *wp -= df_to(make_float2(h, lo));
+          }
+        }
+      } else
       for (int item = tid; item < ntile * ncol; item += nthr) {
         const int rt = item / ncol, j = jb + (item - rt * ncol);
         double u[NB];
@@ -434,8 +465,9 @@ size_t condense_smem_bytes(const Params& P) {
 cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
                             const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
                             int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
-                            cudaStream_t st) {
+                            cudaStream_t st, int split_update) {
   CondArgs a;
+  a.split_update = split_update;
   a.prm = P; a.dt = dt; a.kappa = kappa; a.f_qp = f_qp; a.ghat = ghat; a.ws = ws; a.e0 = e0;
   a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
   a.S = S; a.St = St; a.St32 = St32; a.gel = gel; a.info = info;

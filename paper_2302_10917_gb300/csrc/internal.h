@@ -179,13 +179,12 @@ struct hdg_ctx {
   int* d_info = nullptr;          // [N] zero-pivot column + 1, or 0
   double* d_escale = nullptr;     // [n_int] -1 / ((tau+ + tau-) L_f)
   // Krylov workspace
-  double* d_V = nullptr;          // [restart + 1][N_tr]
-  double* d_w = nullptr;          // [N_tr]
+  float2* d_V = nullptr;          // Krylov basis, split-FP32 pairs [restart + 1][N_tr]
+  float2* d_w = nullptr;          // Arnoldi work vector, split-FP32 pairs [N_tr]
   double* d_r = nullptr;          // [N_tr]
   double* d_part = nullptr;       // reduction partials
   double* d_small = nullptr;      // Hessenberg, Givens, scalars
   int* d_flag = nullptr;
-  float* d_x32 = nullptr;         // FP32 vectors for mode 1
   int krylov_restart = 0;
   size_t bytes = 0;
   int64_t launches = 0;     // kernels enqueued (reported by hdg_info)

@@ -8,7 +8,7 @@ size_t condense_smem_bytes(const Params& P);
 cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
                             const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
                             int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
-                            cudaStream_t st);
+                            cudaStream_t st, int split_update = 0);
 cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
                            int slot_is_element, const double* x, const double* ghat, double* u, double* q,
                            cudaStream_t st);
@@ -21,10 +21,10 @@ cudaError_t launch_apply64(const Params& P, const double* S, const double* x, do
                            const int* stop, cudaStream_t st);
 cudaError_t launch_apply32(const Params& P, const float* S, const float* x, float* y, const double* escale,
                            const int* stop, cudaStream_t st);
-cudaError_t launch_apply32x64(const Params& P, const float* S, const double* x, double* y, const double* escale,
-                              const int* stop, cudaStream_t st);
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st);
+cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
+                             const double* escale, const int* stop, cudaStream_t st);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,

@@ -24,6 +24,10 @@ def main(argv=None):
     ap.add_argument("--m", type=int, default=8)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--applies", type=int, default=4)
+    ap.add_argument("--gmres-steps", type=int, default=0,
+                    help="also run this many GMRES(50) Arnoldi steps")
+    ap.add_argument("--mode", type=int, default=2, help="GMRES Arnoldi operator (0 FP64, 1 FP32, 2 split FP32)")
+    ap.add_argument("--lean", action="store_true", help="store only the blocks the chosen mode needs")
     a = ap.parse_args(argv)
     beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
     pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
@@ -33,7 +37,8 @@ def main(argv=None):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     t = [ev() for _ in range(7)]
     t[0].record()
-    pr.condense(store_fp32=True, keep_factors=False, store_df64=True)
+    lean = a.lean
+    pr.condense(store_fp32=not lean or a.mode == 1, keep_factors=False, store_df64=not lean or a.mode == 2)
     t[1].record()
     x = torch.from_numpy(wl.random_vector(pr.info["N_tr"], seed=5)).cuda()
     for _ in range(a.applies):
@@ -41,12 +46,16 @@ def main(argv=None):
     t[2].record()
     y = pr.apply(x, precond=False)
     t[3].record()
-    y32 = pr.apply(x.float(), precond=True, prec=32)
+    y32 = pr.apply(x.float(), precond=True, prec=32) if (not lean or a.mode == 1) else y.float()
     t[4].record()
-    ydf = pr.apply(x, precond=True, prec=48)
+    ydf = pr.apply(x, precond=True, prec=48) if (not lean or a.mode == 2) else y
     t[5].record()
     torch.cuda.synchronize()
-    out = {"info": pr.info, "condense_ms": t[0].elapsed_time(t[1]),
+    gm = None
+    if a.gmres_steps > 0:
+        x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=50, maxit=a.gmres_steps, mode=a.mode, check=False)
+        gm = rep
+    out = {"info": pr.info, "gmres": gm, "condense_ms": t[0].elapsed_time(t[1]),
            "apply64_pc_ms": t[1].elapsed_time(t[2]) / max(1, a.applies), "apply64_ms": t[2].elapsed_time(t[3]),
            "apply32_ms": t[3].elapsed_time(t[4]), "apply_df_ms": t[4].elapsed_time(t[5]),
            "y_norm": float(y.norm()), "y32_norm": float(y32.norm()), "ydf_norm": float(ydf.norm())}
