@@ -48,6 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c1")
     ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--mode", type=int, default=2, choices=[0, 1, 2],
+                    help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
+    ap.add_argument("--no-split", action="store_true", help="FP64 panel updates in the condensation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args(argv)
@@ -235,6 +238,9 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- ours
+MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64"}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -255,27 +261,30 @@ def run_ours(args):
     f = wl.sin_sin_source(xy, cfg["kappa"], cfg["beta"]).contiguous()
     del xy
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    split = not args.no_split
 
-    def step(rec=None):
+    def step(rec=None, mode=args.mode):
         marks = [ev() for _ in range(4)] if rec is not None else None
         if marks:
             marks[0].record(stream)
         pr.set_source(f)
-        pr.condense(keep_factors=True)
+        pr.condense(keep_factors=True, store_fp32=True, store_df64=True, split_update=split)
         g = pr.rhs()
         if marks:
             marks[1].record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode)
+        if st != 0:
+            raise RuntimeError(f"solve did not converge: {rep}")
         if marks:
             marks[2].record(stream)
         u, q = pr.recover(x)
         if marks:
             marks[3].record(stream)
             rec.append((marks, rep))
-        return rep, st
+        return rep
 
     for _ in range(args.warmup):
-        rep, st = step()
+        step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -288,7 +297,7 @@ def run_ours(args):
     t_start, t_end = ev(), ev()
     t_start.record(stream)
     for _ in range(args.steps):
-        rep, st = step(recs)
+        step(recs)
     t_end.record(stream)
     torch.cuda.synchronize()
     prof = pr.profile_read()
@@ -299,7 +308,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_s = t_start.elapsed_time(t_end) / 1e3
-    applies = prof["apply"][0]
+    applies = prof["apply"][0] + prof["apply32"][0] + prof["resid"][0]
     units, total_max = aggregate(N_tr * applies, total_s, world)
     value = units / total_max / 1e9
 
@@ -307,54 +316,87 @@ def run_ours(args):
     solve_s = [m[1].elapsed_time(m[2]) / 1e3 for m, _ in recs]
     rec_s = [m[2].elapsed_time(m[3]) / 1e3 for m, _ in recs]
     reps = [r for _, r in recs]
-    apply_ms = prof["apply"][1] / max(1, prof["apply"][0])
-    cond_ms = prof["condense"][1] / max(1, prof["condense"][0])
 
     peaks = measured_peaks()
-    # dominant kernel over the timed region
-    P1, n_t, n_int = cfg["m"] * cfg["p"] + 1, 3 * (cfg["m"] * cfg["p"] + 1), pr.info["n_int_edges"]
-    apply_flops = 4.0 * P1 * n_t * n_int                       # 2 sides x P1 rows x n_t cols x 2 flop per edge
-    apply_bytes = 8.0 * (2 * P1 * n_t * n_int + 2 * N_tr)      # Schur row-blocks + x gathers + y write
+    P1 = cfg["m"] * cfg["p"] + 1
+    n_t, n_int = 3 * P1, pr.info["n_int_edges"]
     R, Cc = Q + n_t, Q + n_t + 1
+    avg = lambda ph: prof[ph][1] / max(1, prof[ph][0])
+    # algorithmic work per launch
+    apply_bytes = 8.0 * (2 * P1 * n_t * n_int + 2 * N_tr)        # blocks of both sides + x once + y once
+    apply_flops = 4.0 * P1 * n_t * n_int
     cond_flops = N * sum(2.0 * (R - 1 - k) * (Cc - 1 - k) for k in range(Q))
-    kern = {"apply": (prof["apply"][1], apply_flops, apply_ms, prof["apply"][0]),
-            "condense": (prof["condense"][1], cond_flops, cond_ms, prof["condense"][0])}
-    dom = max(kern, key=lambda k: kern[k][0])
-    tot_ms, flops, avg_ms, cnt = kern[dom]
-    achieved = flops / (avg_ms / 1e3) / 1e12
-    roofline = {"kernel": "apply_kernel<double,double> (FP64 trace apply)" if dom == "apply"
-                else "condense_kernel (element build + bordered LU + Schur)",
-                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived; no measured "
-                               "FP64 peak in the driver's file)",
-                "algorithmic_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt,
-                "hbm_view": {"bytes_per_launch": apply_bytes if dom == "apply" else None,
-                             "achieved_gbs": apply_bytes / (avg_ms / 1e3) / 1e9 if dom == "apply" else None,
-                             "peak_gbs": peaks.get("hbm_gbs")}}
+    rooflines = {
+        "apply": {"kernel": {0: "apply_vdf_kernel<0> (FP64 blocks)", 1: "apply_vdf_kernel<2> (FP32 blocks)",
+                             2: "apply_vdf_kernel<1> (split-FP32 blocks)"}[args.mode],
+                  "bound": "alu" if args.mode == 0 else "hbm",
+                  "launches": prof["apply32" if args.mode == 1 else "apply"][0],
+                  "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},
+        "condense": {"kernel": "condense_kernel (element build + bordered LU + Schur)"
+                               + (", split-FP32 panel updates" if split else ""),
+                     "bound": "alu", "launches": prof["condense"][0], "avg_launch_ms": avg("condense")},
+    }
+    ra = rooflines["apply"]
+    if args.mode == 0:
+        ra.update(achieved=apply_flops / (ra["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                  algorithmic_per_launch=apply_flops)
+    else:
+        bpl = apply_bytes if args.mode == 2 else apply_bytes / 2
+        ra.update(achieved=bpl / (ra["avg_launch_ms"] / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6800.0),
+                  unit="GB/s", algorithmic_per_launch=bpl,
+                  peak_source="measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s")
+    ra["frac"] = ra["achieved"] / ra["peak"]
+    rc = rooflines["condense"]
+    rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+              algorithmic_per_launch=cond_flops,
+              peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)")
+    rc["frac"] = rc["achieved"] / rc["peak"]
+    dom = max(("apply", "condense"), key=lambda kname: prof["apply32" if (kname == "apply" and args.mode == 1)
+                                                           else kname][1])
+    roof = dict(rooflines[dom])
+    roof["traffic"] = None
+    roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f32 operator + f64 refinement", 2: "df64 (f32x2) operator + f64 residual"}[args.mode],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("GMRES(restart)", f"GMRES({args.restart})"),
-                       "N_tr": N_tr, "macro_elements": N, "parallelism": "replicas" if world > 1 else "single",
+                       "N_tr": N_tr, "macro_elements": N, "solve_mode": MODE_NAMES[args.mode],
+                       "lu_panel_updates": "split-FP32" if split else "FP64",
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: Schur blocks 1.47 GB, factors 42 GB, source 0.42 GB per replica"},
             "time_to_solve_s": statistics.median(solve_s), "condense_s": statistics.median(cond_s),
             "recover_s": statistics.median(rec_s), "iterations": reps[-1]["iterations"],
             "restarts": reps[-1]["restarts"], "rel_residual": reps[-1]["rel_residual"],
-            "apply_gdofs": N_tr / (apply_ms / 1e3) / 1e9, "apply_us": apply_ms * 1e3,
-            "phases_ms": {k: v[1] / args.steps for k, v in prof.items()},
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk}
+            "apply_gdofs": N_tr / (rooflines["apply"]["avg_launch_ms"] / 1e3) / 1e9,
+            "phases_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "roofline": roof, "roofline_other": roof_other, "gpu_launches": int(launches), "clocks": clk}
+
+    # the metric compares FP64 with FP32 + refinement: time-to-1e-10 of every solve mode
+    modes = {}
+    g = pr.rhs()
+    for mode in (0, 1, 2):
+        t0, t1 = ev(), ev()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        modes[MODE_NAMES[mode]] = {"seconds": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
+                                   "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"])}
+    line["time_to_solve_by_mode"] = modes
 
     if not args.no_e2e:
         fh = f.cpu().pin_memory()
         torch.cuda.synchronize()
-        pr.run_host(fh, outputs=True)                 # warm-up of the host path
+        pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode)    # warm-up of the host path
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, u, q, rep = pr.run_host(fh, outputs=True)
+        x, u, q, rep = pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode)
         e2e_s = time.perf_counter() - t0
-        app_e2e = rep["iterations"] + 2 * rep["restarts"]
+        app_e2e = rep["iterations"] + rep["outer"]
         eu, es = aggregate(N_tr * app_e2e, e2e_s, world)
         line["e2e"] = {"value": eu / es / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": int(fh.numel() * 8),
                        "d2h_bytes_per_step": int((x.numel() + u.numel() + q.numel()) * 8), "seconds": e2e_s,

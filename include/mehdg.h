@@ -199,9 +199,10 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double*
 hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
 
 /* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to
- * the device, condenses, assembles g, solves from x = 0, recovers u and q
- * and copies x, u, q back (each output may be NULL to skip its copy).
- * Synchronous. Same layouts as above. */
+ * the device, condenses (factors kept; for opts->mode 1 or 2 also the FP32
+ * or split-FP32 blocks, with split-FP32 panel updates), assembles g, solves
+ * from x = 0, recovers u and q and copies x, u, q back (each output may be
+ * NULL to skip its copy). Synchronous. Same layouts as above. */
 hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_qp_host,
                         const hdg_solve_opts* opts, double* x_host, double* u_host,
                         double* q_host, hdg_solve_report* report);
@@ -231,11 +232,12 @@ hdg_status hdg_condense_static(hdg_ctx* ctx, int64_t e0, int64_t count, double* 
 
 /* Per-phase device timing (tracing). Phases: */
 #define HDG_PROF_CONDENSE 0   /* condensation kernel launches (element build + LU + Schur) */
-#define HDG_PROF_APPLY 1      /* FP64 trace-operator apply launches (hdg_apply and inside hdg_solve) */
+#define HDG_PROF_APPLY 1      /* preconditioned FP64 / split-FP32 apply launches (hdg_apply, GMRES's Arnoldi steps) */
 #define HDG_PROF_ORTHO 2      /* GMRES vector work of one Arnoldi step (CGS2, norm, Givens, scaling) */
 #define HDG_PROF_RECOVER 3    /* back-solve kernel launches */
 #define HDG_PROF_APPLY32 4    /* FP32 trace-operator apply launches */
-#define HDG_PROF_NPHASES 5
+#define HDG_PROF_RESID 5      /* FP64 unpreconditioned applies for GMRES's true residual */
+#define HDG_PROF_NPHASES 6
 typedef struct {
   int64_t count[HDG_PROF_NPHASES];   /* timed launches (or Arnoldi steps for ORTHO) */
   double ms[HDG_PROF_NPHASES];       /* summed CUDA-event time on the context stream */

@@ -25,7 +25,7 @@ EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", 
             "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
-PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32"]
+PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32", "resid"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -56,7 +56,7 @@ class SolveReport(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5)]
+    _fields_ = [("count", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
 
 
 class HDGError(RuntimeError):
@@ -242,13 +242,13 @@ class Problem:
         library's fixed scratch array (no device allocation inside the call)."""
         self._check(self.lib.hdg_condense_static(self.h, e0, count, _ptr(S_out), _ptr(g_out)))
 
-    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True):
+    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True, mode=0):
         """End-to-end call on host (ideally pinned) tensors; returns (x, u, q, report)."""
         N, Q, N_tr = self.info["N"], self.info["Q"], self.info["N_tr"]
         x = torch.empty(N_tr, dtype=torch.float64, pin_memory=True) if outputs else None
         u = torch.empty(N, Q, dtype=torch.float64, pin_memory=True) if outputs else None
         q = torch.empty(N, 2, Q, dtype=torch.float64, pin_memory=True) if outputs else None
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=0)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode)
         r = SolveReport()
         st = self.lib.hdg_run_host(self.h, _ptr(f_host), _ptr(gD_host), ctypes.byref(o), _ptr(x), _ptr(u),
                                    _ptr(q), ctypes.byref(r))

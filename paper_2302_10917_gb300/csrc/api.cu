@@ -420,7 +420,10 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
     cleanup();
     return cuda_err(c, e, "hdg_run_host upload");
   }
-  if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, HDG_KEEP_FACTORS)) == HDG_OK &&
+  // the blocks the requested solve mode needs, split-FP32 panel updates for modes 1 and 2
+  const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? (HDG_STORE_FP32 | HDG_SPLIT_UPDATE) : 0u) |
+                          (o->mode == 2 ? (HDG_STORE_DF64 | HDG_SPLIT_UPDATE) : 0u);
+  if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, cflags)) == HDG_OK &&
       (s = hdg_rhs(c, dgv)) == HDG_OK) {
     s = hdg_solve(c, dgv, dx, 1, o, rep);
     if (s == HDG_OK || s == HDG_ERR_NOCONV) {

@@ -26,7 +26,7 @@
 
 namespace mehdg {
 
-constexpr int KG = 608;       // blocks of the vector kernels (4 per SM)
+constexpr int KG = 304;       // blocks (partial sums) of the vector kernels, 2 per SM
 constexpr int KT = 256;       // threads per block
 constexpr int VG = 8;         // basis vectors per pass of the multi-dot
 
@@ -46,7 +46,8 @@ struct SmallLayout {
     total = sc + 8;
   }
 };
-enum { F_STOP = 0, F_JUSED = 1 };
+enum { F_STOP = 0, F_JUSED = 1, F_REORTH = 2 };
+constexpr int KGU = 1216;     // blocks of the streaming update / scale kernels, 8 per SM
 
 // ------------------------------------------------------------ FP64 helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -110,87 +111,115 @@ __device__ __forceinline__ void df_block_reduce(float (&h)[NV], float (&l)[NV], 
   __syncthreads();
 }
 
-// part[b * nv + i] = sum_{idx in chunk b} V_i[idx] w[idx]; blockIdx.y selects
-// a group of VG basis vectors, blockIdx.x an index chunk; each thread keeps
-// 2 x VG loads in flight.
-__global__ void __launch_bounds__(KT) df_mdot_kernel(const float2* __restrict__ V, int64_t n, int nv,
-                                                     const float2* __restrict__ w, double* part, const int* stop) {
+// Basis rows have an even leading dimension ldv (zero padding), so the
+// vector kernels below move element PAIRS with 16-byte loads: (x, y) is the
+// first split-FP32 entry of a float4, (z, w) the second.
+__device__ __forceinline__ void df_fma4(float& h, float& l, float4 a, float4 b) {
+  df_fma(h, l, make_float2(a.x, a.y), make_float2(b.x, b.y));
+  df_fma(h, l, make_float2(a.z, a.w), make_float2(b.z, b.w));
+}
+
+// part[b * nv + i] = sum over pair chunk b of V_i . w; blockIdx.y selects a
+// group of VG basis vectors; two pairs per thread per iteration (2 VG loads).
+// ncol = nv, or nv + 1 to append the squared norm w . w as column nv.
+// skip_if_no_reorth: return at once unless the device flag asks for the
+// second Gram-Schmidt pass.
+__global__ void __launch_bounds__(KT) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
+                                                     const float4* __restrict__ w, double* part, const int* stop,
+                                                     int skip_if_no_reorth) {
   if (stop && stop[F_STOP]) return;
+  if (skip_if_no_reorth && !stop[F_REORTH]) return;
   __shared__ float2 red[(KT / 32) * VG];
   const int g0 = blockIdx.y * VG;
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const int64_t hi = lo + chunk < np ? lo + chunk : np;
   float h[VG], l[VG];
 #pragma unroll
   for (int g = 0; g < VG; ++g) { h[g] = 0.f; l[g] = 0.f; }
-  int64_t idx = lo + threadIdx.x;
-  for (; idx + (int64_t)blockDim.x < hi; idx += 2 * (int64_t)blockDim.x) {
-    const int64_t i2 = idx + blockDim.x;
-    float2 a[VG], b[VG];
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  int64_t p = lo + threadIdx.x;
+  for (; p + (int64_t)blockDim.x < hi; p += 2 * (int64_t)blockDim.x) {
+    const int64_t p2 = p + blockDim.x;
+    float4 a[VG], b[VG];
+    const float4 wa = w[p], wb = w[p2];
 #pragma unroll
     for (int g = 0; g < VG; ++g) {
-      a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * n + idx] : make_float2(0.f, 0.f);
-      b[g] = g0 + g < nv ? V[(size_t)(g0 + g) * n + i2] : make_float2(0.f, 0.f);
+      a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p] : (g0 + g < ncol ? wa : z4);
+      b[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p2] : (g0 + g < ncol ? wb : z4);
     }
-    const float2 wa = w[idx], wb = w[i2];
 #pragma unroll
     for (int g = 0; g < VG; ++g) {
-      df_fma(h[g], l[g], a[g], wa);
-      df_fma(h[g], l[g], b[g], wb);
+      df_fma4(h[g], l[g], a[g], wa);
+      df_fma4(h[g], l[g], b[g], wb);
     }
   }
-  if (idx < hi) {
-    const float2 wa = w[idx];
+  if (p < hi) {
+    const float4 wa = w[p];
 #pragma unroll
-    for (int g = 0; g < VG; ++g)
-      if (g0 + g < nv) df_fma(h[g], l[g], V[(size_t)(g0 + g) * n + idx], wa);
+    for (int g = 0; g < VG; ++g) {
+      if (g0 + g < nv) df_fma4(h[g], l[g], V[(size_t)(g0 + g) * np + p], wa);
+      else if (g0 + g < ncol) df_fma4(h[g], l[g], wa, wa);
+    }
   }
-  df_block_reduce<VG>(h, l, nv - g0, red, part + (size_t)blockIdx.x * nv + g0);
+  df_block_reduce<VG>(h, l, ncol - g0, red, part + (size_t)blockIdx.x * ncol + g0);
 }
 
-// w += sign * sum_i coef[i] V_i (coef in FP64, split once per block);
-// optionally part[b] = block sum of w^2. Two indices per thread, eight basis
-// vectors per batch: 16 loads in flight.
-__global__ void __launch_bounds__(KT) df_update_kernel(const float2* __restrict__ V, int64_t n, int nv,
-                                                       const double* __restrict__ coef, double sign, float2* w,
-                                                       double* part, const int* stop) {
+// w += sign * sum_i coef[i] V_i over element pairs (coef in FP64, split once
+// per block); optionally part[b] = block sum of w^2. Eight basis vectors per
+// batch: eight 16-byte loads in flight per thread.
+// pass 1 (wnorm2 != nullptr): also decides whether the second Gram-Schmidt
+// pass is needed: w' = w - V h has ||w'||^2 = ||w||^2 - ||h||^2 for an
+// orthonormal basis, and the pass is repeated when ||w'|| < ||w|| / sqrt(2)
+// (Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30, 1976). Every block
+// evaluates the same test; block 0 publishes it in stop[F_REORTH].
+// pass 2 (wnorm2 == nullptr): returns at once unless the flag is set.
+__global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict__ V, int64_t np, int nv,
+                                                       const double* __restrict__ coef, double sign, float4* w,
+                                                       double* part, int* stop, const double* wnorm2) {
   if (stop && stop[F_STOP]) return;
+  if (!wnorm2 && !stop[F_REORTH]) return;
   __shared__ float2 cf[136];
   __shared__ float2 red[KT / 32];
-  for (int i = threadIdx.x; i < 136; i += blockDim.x) cf[i] = i < nv ? df_from(sign * coef[i]) : make_float2(0.f, 0.f);
+  __shared__ double hh2[KT / 32];
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < 136; i += blockDim.x) {
+    cf[i] = i < nv ? df_from(sign * coef[i]) : make_float2(0.f, 0.f);
+    if (wnorm2 && i < nv) s2 += coef[i] * coef[i];
+  }
+  if (wnorm2) {
+    for (int off = 16; off > 0; off >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    if ((threadIdx.x & 31) == 0) hh2[threadIdx.x >> 5] = s2;
+  }
   __syncthreads();
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  if (wnorm2 && blockIdx.x == 0 && threadIdx.x == 0) {
+    double t2 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t2 += hh2[i];
+    stop[F_REORTH] = (t2 > 0.5 * (*wnorm2)) ? 1 : 0;
+  }
+  const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const int64_t hi = lo + chunk < np ? lo + chunk : np;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float sh = 0.f, sl = 0.f;
-  for (int64_t idx = lo + threadIdx.x; idx < hi; idx += 2 * (int64_t)blockDim.x) {
-    const int64_t i2 = idx + blockDim.x;
-    const bool has2 = i2 < hi;
-    const float2 wa = w[idx];
-    const float2 wb = has2 ? w[i2] : make_float2(0.f, 0.f);
-    float ah = wa.x, al = wa.y, bh = wb.x, bl = wb.y;
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    const float4 wv = w[p];
+    float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
     for (int i0 = 0; i0 < nv; i0 += 8) {
-      float2 va[8], vb[8];
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = i0 + u < nv ? V[(size_t)(i0 + u) * np + p] : z4;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const bool ok = i0 + u < nv;
-        va[u] = ok ? V[(size_t)(i0 + u) * n + idx] : make_float2(0.f, 0.f);
-        vb[u] = (ok && has2) ? V[(size_t)(i0 + u) * n + i2] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        df_fma(ah, al, cf[i0 + u], va[u]);
-        df_fma(bh, bl, cf[i0 + u], vb[u]);
+        df_fma(ah, al, cf[i0 + u], make_float2(v[u].x, v[u].y));
+        df_fma(bh, bl, cf[i0 + u], make_float2(v[u].z, v[u].w));
       }
     }
-    const float2 ra = df_norm(ah, al);
-    w[idx] = ra;
-    if (part) df_fma(sh, sl, ra, ra);
-    if (has2) {
-      const float2 rb = df_norm(bh, bl);
-      w[i2] = rb;
-      if (part) df_fma(sh, sl, rb, rb);
+    const float2 ra = df_norm(ah, al), rb = df_norm(bh, bl);
+    w[p] = make_float4(ra.x, ra.y, rb.x, rb.y);
+    if (part) {
+      df_fma(sh, sl, ra, ra);
+      df_fma(sh, sl, rb, rb);
     }
   }
   if (part) {
@@ -220,30 +249,47 @@ __global__ void __launch_bounds__(KT) to_df_kernel(const double* a, const double
     out[idx] = df_from(a[idx] * f);
 }
 
-// x += sum_i y_i V_i (x in FP64; the sum in split FP32)
-__global__ void __launch_bounds__(KT) df_xupdate_kernel(const float2* __restrict__ V, int64_t n, int nv,
+// x += sum_i y_i V_i (x in FP64; the sum in split FP32; basis row length ldv)
+__global__ void __launch_bounds__(KT) df_xupdate_kernel(const float2* __restrict__ V, int64_t n, int64_t ldv, int nv,
                                                         const double* __restrict__ y, double* x) {
   __shared__ float2 cf[130];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = df_from(y[i]);
   __syncthreads();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     float ah = 0.f, al = 0.f;
-    for (int i = 0; i < nv; ++i) df_fma(ah, al, cf[i], V[(size_t)i * n + idx]);
+    for (int i = 0; i < nv; ++i) df_fma(ah, al, cf[i], V[(size_t)i * ldv + idx]);
     x[idx] += df_to(make_float2(ah, al));
   }
 }
 
-// out[i] = sum_b part[b * nv + i] in block order; mode 0: H column := s,
-// mode 1: H column += s. htmp receives s (the coefficients of the update).
-__global__ void mdot_reduce_kernel(const double* part, int G, int nv, double* Hcol, double* htmp, int mode,
-                                   const int* stop) {
-  if (stop && stop[F_STOP]) return;
+// Fixed-order block sum (all threads get the result).
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < nv; i += nw) {
-    double s = 0.0;
-    for (int b = lane; b < G; b += 32) s += part[(size_t)b * nv + i];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// out[i] = sum_b part[b * nv + i] in block order (block i sums vector i);
+// mode 0: H column := s, mode 1: H column += s; htmp receives s.
+// Column i = nv of a ncol = nv + 1 layout is ||w||^2 and goes to *wnorm2.
+__global__ void mdot_reduce_kernel(const double* part, int G, int nv, int ncol, double* Hcol, double* htmp, int mode,
+                                   const int* stop, double* wnorm2) {
+  if (stop && stop[F_STOP]) return;
+  if (mode && !stop[F_REORTH]) return;
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[(size_t)b * ncol + i];
+  s = block_sum_all(s, red);
+  if (threadIdx.x == 0) {
+    if (i == nv) {
+      *wnorm2 = s;
+    } else {
       htmp[i] = s;
       Hcol[i] = mode ? Hcol[i] + s : s;
     }
@@ -253,7 +299,10 @@ __global__ void mdot_reduce_kernel(const double* part, int G, int nv, double* Hc
 // start of a cycle: beta = ||r0||, g = beta e1, inv = 1/beta; the target held
 // in sm[sc + 2] as a reduction factor becomes an absolute target factor * beta
 __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const double* part, int G) {
-  const double beta = sqrt(warp_sum_partials(part, G));
+  __shared__ double red[32];
+  double s0 = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s0 += part[b];
+  const double beta = sqrt(block_sum_all(s0, red));
   if (threadIdx.x == 0) {
     sm[L.sc + 0] = beta;
     sm[L.sc + 1] = beta;
@@ -269,18 +318,29 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
 // norm of the new basis vector, Givens rotations, residual estimate
 __global__ void givens_kernel(double* sm, SmallLayout L, int* flags, const double* part, int G, int j) {
   if (flags[F_STOP]) return;
-  const double hn = sqrt(warp_sum_partials(part, G));
-  if (threadIdx.x != 0) return;
+  __shared__ double red[32];
+  double ps = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) ps += part[b];
+  const double hn = sqrt(block_sum_all(ps, red));
   const int K1 = L.K + 1;
+  __shared__ double hs[130], cs_s[130], sn_s[130];
   double* h = sm + L.H + (size_t)j * K1;
-  h[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double c = sm[L.cs + i], s = sm[L.sn + i];
-    const double t = c * h[i] + s * h[i + 1];
-    h[i + 1] = -s * h[i] + c * h[i + 1];
-    h[i] = t;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    hs[i] = h[i];
+    cs_s[i] = i < j ? sm[L.cs + i] : 0.0;
+    sn_s[i] = i < j ? sm[L.sn + i] : 0.0;
   }
-  const double a = h[j], b = h[j + 1];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  hs[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double c = cs_s[i], s = sn_s[i];
+    const double t = c * hs[i] + s * hs[i + 1];
+    hs[i + 1] = -s * hs[i] + c * hs[i + 1];
+    hs[i] = t;
+  }
+  for (int i = 0; i < j; ++i) h[i] = hs[i];
+  const double a = hs[j], b = hs[j + 1];
   const double r = hypot(a, b);
   const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
   sm[L.cs + j] = c;
@@ -338,12 +398,15 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   c->d_V = nullptr; c->d_part = nullptr; c->d_small = nullptr; c->d_flag = nullptr; c->d_w = nullptr; c->d_r = nullptr;
   c->krylov_restart = 0;
   const size_t n = (size_t)c->prm.N_tr;
+  const size_t ldv = n + (n & 1);   // even row length: 16-byte element pairs, zero padding
   cudaError_t e;
   // basis and work vector in split-FP32 pairs (8 bytes per entry)
-  if ((e = cudaMalloc(&c->d_V, (size_t)(K + 1) * n * sizeof(float2))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_w, n * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_V, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_w, ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_V, 0, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_w, 0, ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_part, (size_t)KG * (K + 2) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_part, ((size_t)KG * (K + 2) + KGU) * sizeof(double))) != cudaSuccess) return e;
   SmallLayout L(K);
   if ((e = cudaMalloc(&c->d_small, (size_t)L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flag, 4 * sizeof(int))) != cudaSuccess) return e;
@@ -372,9 +435,13 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   int* fl = c->d_flag;
   float2* V = c->d_V;
   float2* w = c->d_w;
+  const int64_t ldv = n + (n & 1), np = ldv / 2;   // basis row length (even) and element pairs
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  float4* w4 = reinterpret_cast<float4*>(w);
   double* t = c->d_r;           // true residual g - S x (FP64)
   double* r0 = c->d_r + n;      // S x, then D^-1 t
   double* part = c->d_part;
+  double* pnorm = c->d_part + (size_t)KG * (K + 2);   // norm partials of the update kernels
   rep = hdg_solve_report{};
   // Arnoldi operator D^-1 S on split-FP32 vectors
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
@@ -398,7 +465,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   while (true) {
     // true residual with the unpreconditioned FP64 operator (the stopping test)
     {
-      ProfScope ps(c, HDG_PROF_APPLY);
+      ProfScope ps(c, HDG_PROF_RESID);
       cu.ok(launch_apply64(P, c->d_S, x, r0, nullptr, nullptr, st));
     }
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, -1.0, r0, t, n, part);
@@ -419,7 +486,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     const double factor = 0.5 * o.tol / rel;
     cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &factor, sizeof(double), cudaMemcpyHostToDevice, st));
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, r0, 0.0, r0, r0, n, part);
-    cycle_init_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG);
+    cycle_init_kernel<<<1, 256, 0, st>>>(sm, L, fl, part, KG);
     to_df_kernel<<<KG, KT, 0, st>>>(r0, sm, L.sc + 4, V, n, fl);
     LAUNCHED(4);
     const int jmax = std::min(K, o.maxit - its);
@@ -430,18 +497,20 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       double* Hcol = sm + L.H + (size_t)j * (K + 1);
       {
         ProfScope ps(c, phase);
-        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * n, w, c->d_escale, fl, st));
+        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, st));
       }
       ProfScope po(c, HDG_PROF_ORTHO);
-      const dim3 gdot(KG, (nv + VG - 1) / VG);
-      df_mdot_kernel<<<gdot, KT, 0, st>>>(V, n, nv, w, part, fl);
-      mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 0, fl);
-      df_update_kernel<<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, -1.0, w, nullptr, fl);
-      df_mdot_kernel<<<gdot, KT, 0, st>>>(V, n, nv, w, part, fl);
-      mdot_reduce_kernel<<<1, 256, 0, st>>>(part, KG, nv, Hcol, sm + L.htmp, 1, fl);
-      df_update_kernel<<<KG, KT, 0, st>>>(V, n, nv, sm + L.htmp, -1.0, w, part, fl);
-      givens_kernel<<<1, 32, 0, st>>>(sm, L, fl, part, KG, j);
-      df_scale_kernel<<<KG, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * n, n, fl);
+      // pass 1: h = V^T w and ||w||^2; w -= V h and ||w||^2 partials; decide on pass 2
+      const dim3 gdot1(KG, (nv + 1 + VG - 1) / VG), gdot2(KG, (nv + VG - 1) / VG);
+      df_mdot_kernel<<<gdot1, KT, 0, st>>>(V4, np, nv, nv + 1, w4, part, fl, 0);
+      mdot_reduce_kernel<<<nv + 1, 128, 0, st>>>(part, KG, nv, nv + 1, Hcol, sm + L.htmp, 0, fl, sm + L.sc + 6);
+      df_update_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, -1.0, w4, pnorm, fl, sm + L.sc + 6);
+      // pass 2 (only when the projection cancelled more than half of ||w||^2)
+      df_mdot_kernel<<<gdot2, KT, 0, st>>>(V4, np, nv, nv, w4, part, fl, 1);
+      mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, KG, nv, nv, Hcol, sm + L.htmp, 1, fl, nullptr);
+      df_update_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, -1.0, w4, pnorm, fl, nullptr);
+      givens_kernel<<<1, 256, 0, st>>>(sm, L, fl, pnorm, KGU, j);
+      df_scale_kernel<<<KGU, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * ldv, n, fl);
       LAUNCHED(9);
     }
     cu.ok(cudaGetLastError());
@@ -459,7 +528,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     rep.restarts += 1;
     if (jused == 0) break;
     lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
-    df_xupdate_kernel<<<KG, KT, 0, st>>>(V, n, jused, sm + L.y, x);
+    df_xupdate_kernel<<<KG, KT, 0, st>>>(V, n, ldv, jused, sm + L.y, x);
     LAUNCHED(2);
   }
   rep.converged = 0;
