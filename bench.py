@@ -4,7 +4,7 @@
 One step = the whole hot path on the 128 x 128 macro mesh (32,768
 macro-triangles, m = 8, p = 3, beta = 50 (cos 0.3, sin 0.3), kappa = 1,
 manufactured source of u = sin(pi x) sin(pi y)): element formation and batched
-condensation, right-hand-side assembly, left-preconditioned GMRES(50) to a
+condensation, right-hand-side assembly, left-preconditioned GMRES(80) to a
 1e-10 true relative residual, and the back-solve for u and q. Inputs (the
 source at the quadrature points) are resident in HBM before the timed region.
 
@@ -36,8 +36,8 @@ WORKLOAD = ("2D steady advection-diffusion, 128x128 macro grid (32768 macro-tria
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
-# trace-operator applications per step of the GPU path (GMRES(50) Arnoldi steps + 2 per restart)
-REFERENCE_APPLIES_PER_STEP = 5250
+# trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
+REFERENCE_APPLIES_PER_STEP = 4375
 
 
 def parse_args(argv=None):
@@ -47,7 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--restart", type=int, default=80)
     ap.add_argument("--mode", type=int, default=2, choices=[0, 1, 2],
                     help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
     ap.add_argument("--no-split", action="store_true", help="FP64 panel updates in the condensation")

@@ -11,8 +11,9 @@
 //  * the Arnoldi operator D^-1 S is applied from FP64 blocks (mode 0, FP64
 //    arithmetic), FP32 blocks (mode 1) or split-FP32 blocks (mode 2);
 //  * the Krylov basis is stored and orthogonalised (classical Gram-Schmidt
-//    applied twice, CGS2) in split-FP32 arithmetic on the FP32 pipe, because
-//    FP64 vector arithmetic runs at 2 lanes/clock/SM on GB300;
+//    applied twice, CGS2, in three passes over the basis) in split-FP32
+//    arithmetic on the FP32 pipe, because FP64 vector arithmetic runs at
+//    2 lanes/clock/SM on GB300;
 //  * Givens rotations run on the device and a device stop flag lets a whole
 //    cycle be enqueued without host round trips (every kernel of the cycle
 //    returns at once when the flag is set);
@@ -46,7 +47,7 @@ struct SmallLayout {
     total = sc + 8;
   }
 };
-enum { F_STOP = 0, F_JUSED = 1, F_REORTH = 2 };
+enum { F_STOP = 0, F_JUSED = 1 };
 constexpr int KGU = 1216;     // blocks of the streaming update / scale kernels, 8 per SM
 
 // ------------------------------------------------------------ FP64 helpers
@@ -122,13 +123,9 @@ __device__ __forceinline__ void df_fma4(float& h, float& l, float4 a, float4 b) 
 // part[b * nv + i] = sum over pair chunk b of V_i . w; blockIdx.y selects a
 // group of VG basis vectors; two pairs per thread per iteration (2 VG loads).
 // ncol = nv, or nv + 1 to append the squared norm w . w as column nv.
-// skip_if_no_reorth: return at once unless the device flag asks for the
-// second Gram-Schmidt pass.
 __global__ void __launch_bounds__(KT) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
-                                                     const float4* __restrict__ w, double* part, const int* stop,
-                                                     int skip_if_no_reorth) {
+                                                     const float4* __restrict__ w, double* part, const int* stop) {
   if (stop && stop[F_STOP]) return;
-  if (skip_if_no_reorth && !stop[F_REORTH]) return;
   __shared__ float2 red[(KT / 32) * VG];
   const int g0 = blockIdx.y * VG;
   const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
@@ -165,44 +162,157 @@ __global__ void __launch_bounds__(KT) df_mdot_kernel(const float4* __restrict__ 
   df_block_reduce<VG>(h, l, ncol - g0, red, part + (size_t)blockIdx.x * ncol + g0);
 }
 
-// w += sign * sum_i coef[i] V_i over element pairs (coef in FP64, split once
-// per block); optionally part[b] = block sum of w^2. Eight basis vectors per
-// batch: eight 16-byte loads in flight per thread.
-// pass 1 (wnorm2 != nullptr): also decides whether the second Gram-Schmidt
-// pass is needed: w' = w - V h has ||w'||^2 = ||w||^2 - ||h||^2 for an
-// orthonormal basis, and the pass is repeated when ||w'|| < ||w|| / sqrt(2)
-// (Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30, 1976). Every block
-// evaluates the same test; block 0 publishes it in stop[F_REORTH].
-// pass 2 (wnorm2 == nullptr): returns at once unless the flag is set.
-__global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict__ V, int64_t np, int nv,
-                                                       const double* __restrict__ coef, double sign, float4* w,
-                                                       double* part, int* stop, const double* wnorm2) {
+// Pass 2 of CGS2, fused: w' = w - sum_i h_i V_i is written back, and the
+// block's partial dots V_i . w' (columns 0..nv-1) and ||w'||^2 (column nv)
+// go to part[b * (nv + 1) + .]. The block walks its chunk in sub-chunks of
+// blockDim pairs: phase A streams V from HBM to form w' (kept in shared
+// memory), phase B re-reads the same V sub-chunk (now in L1/L2) one warp per
+// basis vector and accumulates the dots in shared memory.
+__global__ void __launch_bounds__(KT) df_update_dot_kernel(const float4* __restrict__ V, int64_t np, int nv,
+                                                           const double* __restrict__ coef, float4* w, double* part,
+                                                           const int* stop) {
   if (stop && stop[F_STOP]) return;
-  if (!wnorm2 && !stop[F_REORTH]) return;
   __shared__ float2 cf[136];
+  __shared__ float2 acc[136];
+  __shared__ float4 wsub[KT];
   __shared__ float2 red[KT / 32];
-  __shared__ double hh2[KT / 32];
-  double s2 = 0.0;
   for (int i = threadIdx.x; i < 136; i += blockDim.x) {
-    cf[i] = i < nv ? df_from(sign * coef[i]) : make_float2(0.f, 0.f);
-    if (wnorm2 && i < nv) s2 += coef[i] * coef[i];
-  }
-  if (wnorm2) {
-    for (int off = 16; off > 0; off >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, off);
-    if ((threadIdx.x & 31) == 0) hh2[threadIdx.x >> 5] = s2;
+    cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
+    acc[i] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  if (wnorm2 && blockIdx.x == 0 && threadIdx.x == 0) {
-    double t2 = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t2 += hh2[i];
-    stop[F_REORTH] = (t2 > 0.5 * (*wnorm2)) ? 1 : 0;
-  }
   const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < np ? lo + chunk : np;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float sh = 0.f, sl = 0.f;
-  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t p = base + threadIdx.x;
+    const bool in = p < hi;
+    // phase A: w' for this thread's pair
+    const float4 wv = in ? w[p] : z4;
+    float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
+    for (int i0 = 0; i0 < nv; i0 += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (in && i0 + u < nv) ? V[(size_t)(i0 + u) * np + p] : z4;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        df_fma(ah, al, cf[i0 + u], make_float2(v[u].x, v[u].y));
+        df_fma(bh, bl, cf[i0 + u], make_float2(v[u].z, v[u].w));
+      }
+    }
+    const float2 ra = df_norm(ah, al), rb = df_norm(bh, bl);
+    const float4 r4 = make_float4(ra.x, ra.y, rb.x, rb.y);
+    if (in) {
+      w[p] = r4;
+      df_fma(sh, sl, ra, ra);
+      df_fma(sh, sl, rb, rb);
+    }
+    wsub[threadIdx.x] = in ? r4 : z4;
+    __syncthreads();
+    // phase B: dots of the sub-chunk, warp `wid` owns vectors wid, wid + nw, ...
+    const int cnt = (int)(hi - base < (int64_t)blockDim.x ? hi - base : (int64_t)blockDim.x);
+    for (int i = wid; i < nv; i += nw) {
+      float h = 0.f, l = 0.f;
+      const float4* Vi = V + (size_t)i * np + base;
+      for (int q = lane; q < cnt; q += 32) df_fma4(h, l, Vi[q], wsub[q]);
+      df_warp_sum(h, l);
+      if (lane == 0) {
+        float2 a2 = acc[i];
+        df_add(a2.x, a2.y, h, l);
+        acc[i] = a2;
+      }
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.x * (nv + 1);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) out[i] = df_to(acc[i]);
+  float hh[1] = {sh}, ll[1] = {sl};
+  df_block_reduce<1>(hh, ll, 1, red, out + nv);
+}
+
+// Sums pass-2 partials (stride nv + 1) in block order, adds the correction to
+// the Hessenberg column, takes the new vector's norm from
+// ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 (orthonormal V), and applies the
+// Givens rotations. One block.
+__global__ void reduce2_givens_kernel(const double* part, int G, int nv, double* sm, SmallLayout L, int* flags,
+                                      int j) {
+  if (flags[F_STOP]) return;
+  __shared__ double vals[136];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i <= nv; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += part[(size_t)b * (nv + 1) + i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) vals[i] = s;
+  }
+  __syncthreads();
+  const int K1 = L.K + 1;
+  double* h = sm + L.H + (size_t)j * K1;
+  double q2 = 0.0;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double s = vals[i];
+    sm[L.htmp + i] = s;
+    h[i] += s;
+    q2 += s * s;
+  }
+  for (int off = 16; off > 0; off >>= 1) q2 += __shfl_down_sync(0xffffffffu, q2, off);
+  if (lane == 0) red[wid] = q2;
+  __syncthreads();
+  // stage the column and the previous rotations: the rotations are a serial chain
+  __shared__ double hs[136], cs_s[136], sn_s[136];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    hs[i] = h[i];
+    cs_s[i] = i < j ? sm[L.cs + i] : 0.0;
+    sn_s[i] = i < j ? sm[L.sn + i] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double hh = 0.0;
+  for (int i = 0; i < nw; ++i) hh += red[i];
+  const double d = vals[nv] - hh;
+  const double hn = d > 0.0 ? sqrt(d) : 0.0;
+  hs[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double c = cs_s[i], s = sn_s[i];
+    const double t = c * hs[i] + s * hs[i + 1];
+    hs[i + 1] = -s * hs[i] + c * hs[i + 1];
+    hs[i] = t;
+  }
+  for (int i = 0; i < j; ++i) h[i] = hs[i];
+  const double a = hs[j], b = hs[j + 1];
+  const double r = hypot(a, b);
+  const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
+  sm[L.cs + j] = c;
+  sm[L.sn + j] = s;
+  h[j] = r;
+  h[j + 1] = 0.0;
+  const double gj = sm[L.gv + j];
+  sm[L.gv + j] = c * gj;
+  sm[L.gv + j + 1] = -s * gj;
+  const double est = fabs(sm[L.gv + j + 1]);
+  sm[L.sc + 1] = est;
+  sm[L.sc + 3] = hn;
+  sm[L.sc + 4] = hn > 0.0 ? 1.0 / hn : 0.0;
+  flags[F_JUSED] = j + 1;
+  if (est <= sm[L.sc + 2] || hn == 0.0) flags[F_STOP] = 1;
+}
+
+// Pass 3: V_{j+1} = (w' - sum_i h_i V_i) * sm[inv_off] over element pairs.
+__global__ void __launch_bounds__(KT) df_update_scale_kernel(const float4* __restrict__ V, int64_t np, int nv,
+                                                             const double* __restrict__ coef, const float4* w,
+                                                             const double* sm, int inv_off, float4* out,
+                                                             const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  __shared__ float2 cf[136];
+  for (int i = threadIdx.x; i < 136; i += blockDim.x) cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2 inv = df_from(sm[inv_off]);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
     const float4 wv = w[p];
     float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
     for (int i0 = 0; i0 < nv; i0 += 8) {
@@ -215,28 +325,11 @@ __global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict_
         df_fma(bh, bl, cf[i0 + u], make_float2(v[u].z, v[u].w));
       }
     }
-    const float2 ra = df_norm(ah, al), rb = df_norm(bh, bl);
-    w[p] = make_float4(ra.x, ra.y, rb.x, rb.y);
-    if (part) {
-      df_fma(sh, sl, ra, ra);
-      df_fma(sh, sl, rb, rb);
-    }
-  }
-  if (part) {
-    float hh[1] = {sh}, ll[1] = {sl};
-    df_block_reduce<1>(hh, ll, 1, red, part + blockIdx.x);
-  }
-}
-
-// out = w * sm[off] (FP64 scalar split once)
-__global__ void __launch_bounds__(KT) df_scale_kernel(const float2* w, const double* sm, int off, float2* out,
-                                                      int64_t n, const int* stop) {
-  if (stop && stop[F_STOP]) return;
-  const float2 f = df_from(sm[off]);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    float h = 0.f, l = 0.f;
-    df_fma(h, l, w[idx], f);
-    out[idx] = df_norm(h, l);
+    float sah = 0.f, sal = 0.f, sbh = 0.f, sbl = 0.f;
+    df_fma(sah, sal, df_norm(ah, al), inv);
+    df_fma(sbh, sbl, df_norm(bh, bl), inv);
+    const float2 ra = df_norm(sah, sal), rb = df_norm(sbh, sbl);
+    out[p] = make_float4(ra.x, ra.y, rb.x, rb.y);
   }
 }
 
@@ -280,7 +373,6 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 __global__ void mdot_reduce_kernel(const double* part, int G, int nv, int ncol, double* Hcol, double* htmp, int mode,
                                    const int* stop, double* wnorm2) {
   if (stop && stop[F_STOP]) return;
-  if (mode && !stop[F_REORTH]) return;
   __shared__ double red[32];
   const int i = blockIdx.x;
   double s = 0.0;
@@ -313,49 +405,6 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
     flags[F_STOP] = beta > 0.0 ? 0 : 1;
     flags[F_JUSED] = 0;
   }
-}
-
-// norm of the new basis vector, Givens rotations, residual estimate
-__global__ void givens_kernel(double* sm, SmallLayout L, int* flags, const double* part, int G, int j) {
-  if (flags[F_STOP]) return;
-  __shared__ double red[32];
-  double ps = 0.0;
-  for (int b = threadIdx.x; b < G; b += blockDim.x) ps += part[b];
-  const double hn = sqrt(block_sum_all(ps, red));
-  const int K1 = L.K + 1;
-  __shared__ double hs[130], cs_s[130], sn_s[130];
-  double* h = sm + L.H + (size_t)j * K1;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    hs[i] = h[i];
-    cs_s[i] = i < j ? sm[L.cs + i] : 0.0;
-    sn_s[i] = i < j ? sm[L.sn + i] : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  hs[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double c = cs_s[i], s = sn_s[i];
-    const double t = c * hs[i] + s * hs[i + 1];
-    hs[i + 1] = -s * hs[i] + c * hs[i + 1];
-    hs[i] = t;
-  }
-  for (int i = 0; i < j; ++i) h[i] = hs[i];
-  const double a = hs[j], b = hs[j + 1];
-  const double r = hypot(a, b);
-  const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
-  sm[L.cs + j] = c;
-  sm[L.sn + j] = s;
-  h[j] = r;
-  h[j + 1] = 0.0;
-  const double gj = sm[L.gv + j];
-  sm[L.gv + j] = c * gj;
-  sm[L.gv + j + 1] = -s * gj;
-  const double est = fabs(sm[L.gv + j + 1]);
-  sm[L.sc + 1] = est;
-  sm[L.sc + 3] = hn;
-  sm[L.sc + 4] = hn > 0.0 ? 1.0 / hn : 0.0;
-  flags[F_JUSED] = j + 1;
-  if (est <= sm[L.sc + 2] || hn == 0.0) flags[F_STOP] = 1;
 }
 
 // y = R^-1 g for the rotated Hessenberg matrix (jused columns)
@@ -406,7 +455,7 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   if ((e = cudaMemset(c->d_V, 0, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMemset(c->d_w, 0, ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_part, ((size_t)KG * (K + 2) + KGU) * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_part, (size_t)KG * (K + 2) * sizeof(double))) != cudaSuccess) return e;
   SmallLayout L(K);
   if ((e = cudaMalloc(&c->d_small, (size_t)L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flag, 4 * sizeof(int))) != cudaSuccess) return e;
@@ -441,7 +490,6 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   double* t = c->d_r;           // true residual g - S x (FP64)
   double* r0 = c->d_r + n;      // S x, then D^-1 t
   double* part = c->d_part;
-  double* pnorm = c->d_part + (size_t)KG * (K + 2);   // norm partials of the update kernels
   rep = hdg_solve_report{};
   // Arnoldi operator D^-1 S on split-FP32 vectors
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
@@ -500,18 +548,17 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, st));
       }
       ProfScope po(c, HDG_PROF_ORTHO);
-      // pass 1: h = V^T w and ||w||^2; w -= V h and ||w||^2 partials; decide on pass 2
-      const dim3 gdot1(KG, (nv + 1 + VG - 1) / VG), gdot2(KG, (nv + VG - 1) / VG);
-      df_mdot_kernel<<<gdot1, KT, 0, st>>>(V4, np, nv, nv + 1, w4, part, fl, 0);
-      mdot_reduce_kernel<<<nv + 1, 128, 0, st>>>(part, KG, nv, nv + 1, Hcol, sm + L.htmp, 0, fl, sm + L.sc + 6);
-      df_update_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, -1.0, w4, pnorm, fl, sm + L.sc + 6);
-      // pass 2 (only when the projection cancelled more than half of ||w||^2)
-      df_mdot_kernel<<<gdot2, KT, 0, st>>>(V4, np, nv, nv, w4, part, fl, 1);
-      mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, KG, nv, nv, Hcol, sm + L.htmp, 1, fl, nullptr);
-      df_update_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, -1.0, w4, pnorm, fl, nullptr);
-      givens_kernel<<<1, 256, 0, st>>>(sm, L, fl, pnorm, KGU, j);
-      df_scale_kernel<<<KGU, KT, 0, st>>>(w, sm, L.sc + 4, V + (size_t)(j + 1) * ldv, n, fl);
-      LAUNCHED(9);
+      // CGS2 in three passes over the basis:
+      // (1) h1 = V^T w; (2) w' = w - V h1 with h2 = V^T w' and ||w'||^2;
+      // (3) V_{j+1} = (w' - V h2) / ||w' - V h2||, the norm from ||w'||^2 - ||h2||^2
+      const dim3 gdot(KG, (nv + VG - 1) / VG);
+      df_mdot_kernel<<<gdot, KT, 0, st>>>(V4, np, nv, nv, w4, part, fl);
+      mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, KG, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
+      df_update_dot_kernel<<<KG, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, part, fl);
+      reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, KG, nv, sm, L, fl, j);
+      df_update_scale_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4,
+                                                 reinterpret_cast<float4*>(V + (size_t)(j + 1) * ldv), fl);
+      LAUNCHED(6);
     }
     cu.ok(cudaGetLastError());
     int hflags[2] = {0, 0};
