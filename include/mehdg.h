@@ -128,7 +128,8 @@ typedef struct {
 
 /* hdg_condense flags */
 #define HDG_STORE_FP32 1u      /* also keep an FP32 copy of the preconditioned blocks */
-#define HDG_KEEP_FACTORS 2u    /* keep the factored local systems for hdg_recover (else recover refactors) */
+#define HDG_KEEP_FACTORS 2u    /* keep the factored local systems and their pivots for hdg_recover and the
+                                  adjoint (else hdg_recover refactors) */
 #define HDG_STORE_DF64 4u      /* also keep the preconditioned blocks as FP32 hi/lo pairs (8 bytes per entry) */
 #define HDG_SPLIT_UPDATE 8u    /* form the LU's panel products in split-FP32 arithmetic (FP32 pipe);
                                   pivots, triangular solves and the stored entries stay FP64 */
@@ -230,6 +231,55 @@ hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_
 #define MEHDG_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 hdg_status hdg_condense_static(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev, double* g_dev);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint and gradient. The paper has no counterpart: these entry
+ * points differentiate a functional J(u) of the recovered element values u
+ * with respect to the per-element diffusivities kappa_e and the source values
+ * f at the quadrature points, through the reduced element system that
+ * hdg_condense eliminates (q eliminated exactly):
+ *     A_u u_e + B_u x_e = F_e,   sum_e (C_u u_e + D_u x_e) = 0 on interior
+ * trace dofs (x_e includes g^ on Dirichlet edges). With r = dJ/du the adjoint
+ * state solves S^T nu = g_adj = -sum_e L_e^T B_u^T A_u^-T r_e and
+ * mu_e = A_u^-T (r_e - C_u^T nu_e); then
+ *     dJ/dkappa_e = -[mu_e; nu_e]^T (dK_e/dkappa_e) [u_e; x_e],
+ *     dJ/df_{e,i} = mu_e^T dF_e/df_{e,i}.
+ * Sequence: forward solve and hdg_recover; hdg_adjoint_rhs; hdg_transpose;
+ * hdg_solve(g_adj) -> nu; hdg_transpose (back); hdg_adjoint_recover -> mu;
+ * hdg_gradient. hdg_adjoint_rhs and hdg_adjoint_recover need the factors
+ * kept by hdg_condense (HDG_KEEP_FACTORS); otherwise HDG_ERR_STATE.
+ * ------------------------------------------------------------------------ */
+
+/* Replace the per-element diffusivities by kappa_dev ([N] FP64, device,
+ * each >= 0 and finite; read before the call returns) and recompute the
+ * face preconditioner's scales. The condensed blocks become stale: the
+ * context returns to the "source set" state (hdg_condense required before
+ * hdg_apply/hdg_solve/hdg_recover). Synchronous (it reads a validity count
+ * back): HDG_ERR_ARG if an entry is negative or not finite (the stored
+ * diffusivities are then undefined until a valid call). */
+hdg_status hdg_set_kappa(hdg_ctx* ctx, const double* kappa_dev);
+
+/* Transpose the stored trace operator in place, element by element
+ * (S_e <- S_e^T and its preconditioned, FP32 and split-FP32 copies), so that
+ * hdg_apply and hdg_solve act on S^T; D^-1 is symmetric and unchanged.
+ * Calling it again restores S. hdg_condense resets the state to S. */
+hdg_status hdg_transpose(hdg_ctx* ctx);
+
+/* Adjoint right-hand side: g_dev ([N_tr] FP64) = -sum_e L_e^T B_u^T A_u^-T r_e
+ * with r_dev = dJ/du as [N][Q] FP64 (the layout of hdg_recover's u). */
+hdg_status hdg_adjoint_rhs(hdg_ctx* ctx, const double* r_dev, double* g_dev);
+
+/* Adjoint element values: mu_dev ([N][Q] FP64) = A_u^-T (r_e - C_u^T nu_e)
+ * for every element, nu_dev the solution of S^T nu = g_adj ([N_tr]). */
+hdg_status hdg_adjoint_recover(hdg_ctx* ctx, const double* r_dev, const double* nu_dev, double* mu_dev);
+
+/* Gradient of J: dkappa_dev[e] = dJ/dkappa_e ([N]) and, if df_dev is not
+ * NULL, df_dev = dJ/df at the source points ([N][n_qp], layout of
+ * hdg_set_source). x_dev: forward trace solution, u_dev: forward element
+ * values (hdg_recover), mu_dev/nu_dev: adjoint state. Uses the current
+ * diffusivities and Dirichlet data. Requires hdg_set_source. */
+hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, const double* mu_dev,
+                        const double* nu_dev, double* dkappa_dev, double* df_dev);
+
 /* Per-phase device timing (tracing). Phases: */
 #define HDG_PROF_CONDENSE 0   /* condensation kernel launches (element build + LU + Schur) */
 #define HDG_PROF_APPLY 1      /* preconditioned FP64 / split-FP32 apply launches (hdg_apply, GMRES's Arnoldi steps) */
@@ -237,7 +287,8 @@ hdg_status hdg_condense_static(hdg_ctx* ctx, int64_t e0, int64_t count, double* 
 #define HDG_PROF_RECOVER 3    /* back-solve kernel launches */
 #define HDG_PROF_APPLY32 4    /* FP32 trace-operator apply launches */
 #define HDG_PROF_RESID 5      /* FP64 unpreconditioned applies for GMRES's true residual */
-#define HDG_PROF_NPHASES 6
+#define HDG_PROF_ADJOINT 6    /* adjoint kernels: transposition, adjoint right-hand side and back-solve, gradient */
+#define HDG_PROF_NPHASES 7
 typedef struct {
   int64_t count[HDG_PROF_NPHASES];   /* timed launches (or Arnoldi steps for ORTHO) */
   double ms[HDG_PROF_NPHASES];       /* summed CUDA-event time on the context stream */

@@ -50,6 +50,7 @@ class HDGProblem:
         self.n, self.m, self.p = n, m, p
         self.beta = np.asarray(beta, dtype=np.float64)
         self.kappa = np.broadcast_to(np.asarray(kappa, dtype=np.float64), (msh.N,)).copy()
+        self.tau_len = float(tau_len)
         self.tau = self.kappa / tau_len + np.hypot(self.beta[0], self.beta[1])
         self.ng = p + 2              # source rule: exact to degree 2p + 2
         self.ng_edge = p + 2         # boundary-data rule per sub-edge
@@ -202,6 +203,16 @@ class HDGProblem:
         Ga = em["G"] * em["bn"][None, :]       # G is block diagonal per edge
         D = Ga - tau * em["G"]
         return A, B, C, D
+
+    def blocks_at(self, e, kappa_e):
+        """A_e, B_e, C_e, D_e evaluated with diffusivity kappa_e (tau_e follows kappa_e)."""
+        k0, t0 = self.kappa[e], self.tau[e]
+        self.kappa[e] = kappa_e
+        self.tau[e] = kappa_e / self.tau_len + np.hypot(self.beta[0], self.beta[1])
+        try:
+            return self.local_blocks(e)
+        finally:
+            self.kappa[e], self.tau[e] = k0, t0
 
     def load_vector(self, e, f_vals):
         """R_e = [0; 0; (f, phi_i)_K] from f at the published source points of e."""

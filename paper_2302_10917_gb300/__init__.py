@@ -22,10 +22,11 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_C
 
 EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", "hdg_set_source",
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
-            "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_last_error",
+            "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_set_kappa",
+            "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
-PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32", "resid"]
+PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32", "resid", "adjoint"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -56,7 +57,7 @@ class SolveReport(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("count", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("count", ctypes.c_int64 * 7), ("ms", ctypes.c_double * 7)]
 
 
 class HDGError(RuntimeError):
@@ -90,6 +91,11 @@ def load_library(path=LIB_PATH):
     lib.hdg_get_schur.argtypes = [vp, i64, i64, dp]
     lib.hdg_run_host.argtypes = [vp, dp, dp, ctypes.POINTER(SolveOpts), dp, dp, dp, ctypes.POINTER(SolveReport)]
     lib.hdg_condense_static.argtypes = [vp, i64, i64, dp, dp]
+    lib.hdg_set_kappa.argtypes = [vp, dp]
+    lib.hdg_transpose.argtypes = [vp]
+    lib.hdg_adjoint_rhs.argtypes = [vp, dp, dp]
+    lib.hdg_adjoint_recover.argtypes = [vp, dp, dp, dp]
+    lib.hdg_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp]
     lib.hdg_profile.argtypes = [vp, ctypes.c_int]
     lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
@@ -144,6 +150,7 @@ class Problem:
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
         self.n, self.m, self.p = n, m, p
         self._src = None
+        self.version = 0        # bumped by every condensation (the factors the adjoint reuses)
 
     def launches(self):
         """Kernels this context has enqueued so far (counted by the library)."""
@@ -201,6 +208,7 @@ class Problem:
         flags = ((HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
                  | (HDG_STORE_DF64 if store_df64 else 0) | (HDG_SPLIT_UPDATE if split_update else 0))
         self._check(self.lib.hdg_condense(self.h, flags))
+        self.version += 1
 
     def rhs(self):
         g = self._f64(self.info["N_tr"])
@@ -255,3 +263,97 @@ class Problem:
         if st not in (HDG_OK, HDG_ERR_NOCONV):
             self._check(st)
         return x, u, q, r.as_dict()
+
+    # ------------------------------------------------------- adjoint / gradient
+    def set_kappa(self, kappa):
+        """hdg_set_kappa: new per-element diffusivities ([N], >= 0); condense again afterwards."""
+        k = torch.as_tensor(kappa, dtype=torch.float64).to(self.device).contiguous()
+        self._check(self.lib.hdg_set_kappa(self.h, _ptr(k)))
+        self.version += 1
+
+    def transpose(self):
+        """hdg_transpose: the stored operator becomes S^T (again: S)."""
+        self._check(self.lib.hdg_transpose(self.h))
+
+    def adjoint_rhs(self, r):
+        r = r.to(self.device, torch.float64).contiguous()
+        g = self._f64(self.info["N_tr"])
+        self._check(self.lib.hdg_adjoint_rhs(self.h, _ptr(r), _ptr(g)))
+        return g
+
+    def adjoint_recover(self, r, nu):
+        r = r.to(self.device, torch.float64).contiguous()
+        nu = nu.to(self.device, torch.float64).contiguous()
+        mu = self._f64(self.info["N"], self.info["Q"])
+        self._check(self.lib.hdg_adjoint_recover(self.h, _ptr(r), _ptr(nu), _ptr(mu)))
+        return mu
+
+    def gradient(self, x, u, mu, nu, want_df=True):
+        dk = self._f64(self.info["N"])
+        df = self._f64(self.info["N"], self.info["n_qp"]) if want_df else None
+        args = [t.to(self.device, torch.float64).contiguous() for t in (x, u, mu, nu)]
+        self._check(self.lib.hdg_gradient(self.h, *[_ptr(t) for t in args], _ptr(dk), _ptr(df)))
+        return dk, df
+
+    def adjoint(self, r, x, u, tol=1e-10, maxit=20000, restart=80, mode=0, want_df=True):
+        """dJ/dkappa [N] and dJ/df [N, n_qp] for dJ/du = r [N, Q], at the forward solution
+        (x, u) of the current condensation (factors kept). Returns (dkappa, df, report)."""
+        g = self.adjoint_rhs(r)
+        self.transpose()
+        try:
+            nu, rep, st = self.solve(g, tol=tol, maxit=maxit, restart=restart, mode=mode)
+        finally:
+            self.transpose()
+        if st != HDG_OK:
+            raise HDGError(st, f"adjoint solve did not converge: {rep}")
+        mu = self.adjoint_recover(r, nu)
+        dk, df = self.gradient(x, u, mu, nu, want_df)
+        return dk, df, rep
+
+
+class HDGSolve(torch.autograd.Function):
+    """u = solve(kappa, f): element values of the macro-element HDG solution as a
+    differentiable function of the per-element diffusivities and the source values
+    at the quadrature points; the backward pass is the discrete adjoint
+    (hdg_adjoint_rhs, a transposed GMRES solve, hdg_adjoint_recover, hdg_gradient).
+    If the problem was condensed again between forward and backward, the
+    backward pass first condenses it again at the saved kappa and f."""
+
+    @staticmethod
+    def _prepare(problem, kappa, f, gD, mode, split):
+        problem.set_kappa(kappa)
+        problem.set_source(f, gD)
+        problem.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split)
+
+    @staticmethod
+    def forward(ctx, kappa, f, problem, gD, opts):
+        opts = dict(opts or {})
+        tol, restart, mode = opts.get("tol", 1e-10), opts.get("restart", 80), opts.get("mode", 0)
+        split = opts.get("split_update", False)
+        kappa_d, f_d = kappa.detach(), f.detach()
+        HDGSolve._prepare(problem, kappa_d, f_d, gD, mode, split)
+        x, rep, st = problem.solve(problem.rhs(), tol=tol, restart=restart, mode=mode,
+                                   maxit=opts.get("maxit", 20000))
+        if st != HDG_OK:
+            raise HDGError(st, f"forward solve did not converge: {rep}")
+        u, _ = problem.recover(x)
+        ctx.problem, ctx.version, ctx.opts = problem, problem.version, (tol, restart, mode, split)
+        ctx.gD = gD
+        ctx.save_for_backward(x, u, kappa_d, f_d)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        pr = ctx.problem
+        x, u, kappa, f = ctx.saved_tensors
+        tol, restart, mode, split = ctx.opts
+        if pr.version != ctx.version:
+            HDGSolve._prepare(pr, kappa, f, ctx.gD, mode, split)
+        dk, df, _ = pr.adjoint(grad_u, x, u, tol=tol, restart=restart, mode=mode,
+                               want_df=ctx.needs_input_grad[1])
+        return (dk if ctx.needs_input_grad[0] else None), df, None, None, None
+
+
+def solve_u(problem, kappa, f, gD=None, **opts):
+    """Differentiable u = solve(kappa, f) on `problem` (see HDGSolve)."""
+    return HDGSolve.apply(kappa, f, problem, gD, opts)

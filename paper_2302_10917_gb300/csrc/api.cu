@@ -282,13 +282,18 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     c->ws_slots = want;
   }
   const int keep = (flags & HDG_KEEP_FACTORS) ? 1 : 0;
+  if (keep && !c->d_piv && (e = dev_alloc(c, &c->d_piv, (size_t)P.N * P.Q)) != cudaSuccess)
+    return cuda_err(c, e, "pivots");
+  if (!keep) dev_free(c, c->d_piv, (size_t)P.N * P.Q);
+  c->transposed = 0;
   const double* gh = c->gD_qp ? c->d_ghat : nullptr;
   for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
     const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
     {
       ProfScope ps(c, HDG_PROF_CONDENSE);
       e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, keep, 1, c->d_S, c->d_St,
-                          (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream, split);
+                          (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr, c->d_gel, c->d_info, c->stream, split,
+                          keep ? c->d_piv : nullptr);
     }
     c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
@@ -448,6 +453,77 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
   return s;
 }
 
+hdg_status hdg_set_kappa(hdg_ctx* c, const double* kappa) {
+  if (!c) return HDG_ERR_ARG;
+  if (!kappa) return set_err(c, HDG_ERR_ARG, "kappa must be a device pointer");
+  if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  cudaError_t e;
+  if (!c->d_bad && (e = dev_alloc(c, &c->d_bad, 1)) != cudaSuccess) return cuda_err(c, e, "kappa check");
+  int bad = 0;
+  if ((e = cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream)) != cudaSuccess ||
+      (e = launch_copy_kappa(c->prm, kappa, c->d_kappa, c->d_bad, c->stream)) != cudaSuccess ||
+      (e = launch_face_scale(c->prm, c->d_kappa, c->d_escale, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_err(c, e, "hdg_set_kappa");
+  c->launches += 2;
+  if (c->state > 1) c->state = 1;
+  if (bad) return set_err(c, HDG_ERR_ARG, std::to_string(bad) + " diffusivities are negative or not finite");
+  return HDG_OK;
+}
+
+hdg_status hdg_transpose(hdg_ctx* c) {
+  if (!c) return HDG_ERR_ARG;
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_transpose before hdg_condense");
+  ProfScope ps(c, HDG_PROF_ADJOINT);
+  cudaError_t e = launch_transpose(c->prm, c->dt, c->d_S, c->d_St, c->d_St32, c->d_Stdf, c->stream);
+  c->launches += 1;
+  if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose");
+  c->transposed ^= 1;
+  return HDG_OK;
+}
+
+hdg_status hdg_adjoint_rhs(hdg_ctx* c, const double* r, double* g) {
+  if (!c) return HDG_ERR_ARG;
+  if (!r || !g) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 2 || !(c->flags & HDG_KEEP_FACTORS) || !c->d_piv)
+    return set_err(c, HDG_ERR_STATE, "hdg_adjoint_rhs needs hdg_condense with HDG_KEEP_FACTORS");
+  const Params& P = c->prm;
+  cudaError_t e;
+  if (!c->d_gadj && (e = dev_alloc(c, &c->d_gadj, (size_t)P.N * P.n_t)) != cudaSuccess)
+    return cuda_err(c, e, "adjoint element vectors");
+  {
+    ProfScope ps(c, HDG_PROF_ADJOINT);
+    e = launch_adjoint_rhs(P, c->d_ws, r, c->d_gadj, c->stream);
+  }
+  if (e == cudaSuccess) e = launch_assemble_rhs(P, c->d_gadj, g, c->stream);
+  c->launches += 2;
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_adjoint_rhs");
+}
+
+hdg_status hdg_adjoint_recover(hdg_ctx* c, const double* r, const double* nu, double* mu) {
+  if (!c) return HDG_ERR_ARG;
+  if (!r || !nu || !mu) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 2 || !(c->flags & HDG_KEEP_FACTORS) || !c->d_piv)
+    return set_err(c, HDG_ERR_STATE, "hdg_adjoint_recover needs hdg_condense with HDG_KEEP_FACTORS");
+  ProfScope ps(c, HDG_PROF_ADJOINT);
+  cudaError_t e = launch_adjoint_recover(c->prm, c->d_ws, c->d_piv, r, nu, mu, c->stream);
+  c->launches += 1;
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_adjoint_recover");
+}
+
+hdg_status hdg_gradient(hdg_ctx* c, const double* x, const double* u, const double* mu, const double* nu,
+                        double* dkappa, double* df) {
+  if (!c) return HDG_ERR_ARG;
+  if (!x || !u || !mu || !nu || !dkappa) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_gradient before hdg_set_source");
+  ProfScope ps(c, HDG_PROF_ADJOINT);
+  const double* gh = c->gD_qp ? c->d_ghat : nullptr;
+  cudaError_t e = launch_gradient(c->prm, c->dt, x, gh, u, mu, nu, dkappa, df, c->stream);
+  c->launches += 1;
+  return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_gradient");
+}
+
 hdg_status hdg_profile(hdg_ctx* c, int enable) {
   if (!c) return HDG_ERR_ARG;
   profile_collect(c);
@@ -475,7 +551,7 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
   cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
-  cudaFree(c->d_small); cudaFree(c->d_flag);
+  cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   delete c;
 }
 

@@ -41,6 +41,7 @@ struct CondArgs {
   double* gel;
   int* info;
   int split_update;       // 1: trailing updates in split-FP32 arithmetic on the FP32 pipe
+  int* piv;               // [N][Q] pivot row of every column (factors kept), or null
 };
 
 __device__ __forceinline__ void warp_argmax(double& v, int& i) {
@@ -180,6 +181,19 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
       }
       __syncthreads();
       const int pr = piv_s[c];
+      if (a.piv) {
+        // kept factors: record the interchange and apply it to the columns of
+        // the earlier panels too, so that rows 0..Q-1 hold P A_u = L U
+        if (tid == 0) a.piv[(size_t)e * Q + j0 + c] = j0 + pr;
+        if (pr != c)
+          for (int cc = tid; cc < j0; cc += nthr) {
+            double* x0 = W + (size_t)(j0 + c) * ld + cc;
+            double* x1 = W + (size_t)(j0 + pr) * ld + cc;
+            const double t0 = *x0;
+            *x0 = *x1;
+            *x1 = t0;
+          }
+      }
       if (pr != c) {
         for (int cc = tid; cc < nb; cc += nthr) {
           const double t0 = Ls[c * LDP + cc];
@@ -465,9 +479,10 @@ size_t condense_smem_bytes(const Params& P) {
 cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
                             const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
                             int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
-                            cudaStream_t st, int split_update) {
+                            cudaStream_t st, int split_update, int* piv) {
   CondArgs a;
   a.split_update = split_update;
+  a.piv = piv;
   a.prm = P; a.dt = dt; a.kappa = kappa; a.f_qp = f_qp; a.ghat = ghat; a.ws = ws; a.e0 = e0;
   a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
   a.S = S; a.St = St; a.St32 = St32; a.gel = gel; a.info = info;

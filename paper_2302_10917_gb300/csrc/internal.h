@@ -177,6 +177,10 @@ struct hdg_ctx {
   double* d_ws = nullptr;         // factored bordered systems [slots][R][ld]
   int64_t ws_slots = 0;
   int* d_info = nullptr;          // [N] zero-pivot column + 1, or 0
+  int* d_piv = nullptr;           // [N][Q] pivot rows of the kept factors
+  double* d_gadj = nullptr;       // [N][n_t] element parts of the adjoint right-hand side
+  int* d_bad = nullptr;           // invalid-kappa counter of hdg_set_kappa
+  int transposed = 0;             // 1 while the stored blocks hold S_e^T (hdg_transpose)
   double* d_escale = nullptr;     // [n_int] -1 / ((tau+ + tau-) L_f)
   // Krylov workspace
   float2* d_V = nullptr;          // Krylov basis, split-FP32 pairs [restart + 1][N_tr]

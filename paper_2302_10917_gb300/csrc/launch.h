@@ -8,7 +8,7 @@ size_t condense_smem_bytes(const Params& P);
 cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
                             const double* ghat, double* ws, int64_t e0, int64_t count, int slot_is_element,
                             int write_outputs, double* S, double* St, float* St32, double* gel, int* info,
-                            cudaStream_t st, int split_update = 0);
+                            cudaStream_t st, int split_update = 0, int* piv = nullptr);
 cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
                            int slot_is_element, const double* x, const double* ghat, double* u, double* q,
                            cudaStream_t st);
@@ -30,6 +30,17 @@ cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, c
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
                              cudaStream_t st);
 cudaError_t launch_face_scale(const Params& P, const double* kappa, double* escale, cudaStream_t st);
+
+// Adjoint path (adjoint.cu).
+cudaError_t launch_copy_kappa(const Params& P, const double* src, double* kappa, int* bad, cudaStream_t st);
+cudaError_t launch_transpose(const Params& P, const DevTables& dt, double* S, double* St, float* St32, float2* Stdf,
+                             cudaStream_t st);
+cudaError_t launch_adjoint_rhs(const Params& P, const double* ws, const double* r, double* gel, cudaStream_t st);
+cudaError_t launch_adjoint_recover(const Params& P, const double* ws, const int* piv, const double* r,
+                                   const double* nu, double* mu, cudaStream_t st);
+cudaError_t launch_gradient(const Params& P, const DevTables& dt, const double* x, const double* ghat,
+                            const double* u, const double* mu, const double* nu, double* dkappa, double* df,
+                            cudaStream_t st);
 
 // Restarted GMRES on the condensed system (krylov.cu).
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep);

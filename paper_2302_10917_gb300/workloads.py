@@ -41,6 +41,28 @@ def random_kappa(N, seed, lo=0.5, hi=2.0):
     return np.exp(g.uniform(np.log(lo), np.log(hi), size=N))
 
 
+def grf_kappa(n, seed, std=0.5, ell=0.1, features=1024):
+    """kappa_e = exp(g(c_e)) at the centroids c_e of the n x n "/"-split mesh, with g a
+    Gaussian random field of standard deviation std and squared-exponential
+    correlation length ell, drawn as `features` random Fourier features
+    g(x) = std sqrt(2 / F) sum_k cos(w_k . x + phi_k), w_k ~ N(0, I / ell^2),
+    phi_k ~ U[0, 2 pi) (Rahimi and Recht, 2007)."""
+    g = np.random.default_rng([MASTER_SEED, 43, int(seed)])
+    w = g.standard_normal((features, 2)) / ell
+    phi = g.uniform(0.0, 2.0 * np.pi, features)
+    h = 1.0 / n
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    i, j = i.ravel(), j.ravel()          # square index j n + i
+    c = np.empty((2 * n * n, 2))
+    # t = 0: (x_{i+1}, y_j), (x_{i+1}, y_{j+1}), (x_i, y_j); t = 1: (x_i, y_{j+1}), (x_i, y_j), (x_{i+1}, y_{j+1})
+    c[0::2, 0] = (i + 2.0 / 3.0) * h
+    c[0::2, 1] = (j + 1.0 / 3.0) * h
+    c[1::2, 0] = (i + 1.0 / 3.0) * h
+    c[1::2, 1] = (j + 2.0 / 3.0) * h
+    field = std * np.sqrt(2.0 / features) * np.cos(c @ w.T + phi[None, :]).sum(axis=1)
+    return np.exp(field)
+
+
 def random_vector(n, seed):
     g = np.random.default_rng([MASTER_SEED, 29, int(seed)])
     return g.standard_normal(n)

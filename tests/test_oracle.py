@@ -368,3 +368,67 @@ def test_dirichlet_projection_reproduces_polynomials_and_is_l2_projection():
             sl = slice(s * x.size, (s + 1) * x.size)
             tot[cols] += psi.T @ (bw[b, sl] * (gs[b, sl] - psi @ gh[b, cols]))
         assert np.abs(tot).max() < 1e-15
+
+
+# --------------------------------------------------------------------- adjoint
+def _adjoint_case(seed, beta=(0.7, -0.4)):
+    from oracle.adjoint import forward
+    rng = np.random.default_rng(seed)
+    n, m, p = 2, 2, 2
+    N = 2 * n * n
+    kap = rng.uniform(0.5, 2.0, N)
+    pr = HDGProblem(n, m, p, beta=beta, kappa=kap)
+    pts, _ = pr.quad_points()
+    bpts, _ = pr.bnd_quad_points()
+    f = rng.standard_normal(pts.shape[:2])
+    gD = rng.standard_normal(bpts.shape[:2])
+    u_obs = rng.standard_normal((N, pr.mesh.Q))
+    J = lambda u: 0.5 * np.sum((u - u_obs) ** 2)
+
+    def J_of(kappa, ff):
+        return J(forward(HDGProblem(n, m, p, beta=beta, kappa=kappa), ff, gD)[2])
+    return pr, kap, f, gD, u_obs, J_of
+
+
+@pytest.mark.parametrize("beta", [(0.7, -0.4), (0.0, 0.0)])
+def test_adjoint_kappa_gradient_matches_central_differences(beta):
+    """Brute force: every component of dJ/dkappa against a central difference
+    of J (h = 1e-5; the truncation error is O(h^2) ~ 1e-10 relative)."""
+    from oracle.adjoint import forward, gradient
+    pr, kap, f, gD, u_obs, J_of = _adjoint_case(3, beta)
+    _, _, u, _ = forward(pr, f, gD)
+    gk, _, _ = gradient(pr, f, u - u_obs, gD)
+    h = 1e-5
+    for e in range(len(kap)):
+        d = np.zeros_like(kap)
+        d[e] = h
+        fd = (J_of(kap + d, f) - J_of(kap - d, f)) / (2 * h)
+        assert abs(gk[e] - fd) <= 1e-7 * max(abs(fd), 1e-3), (e, gk[e], fd)
+
+
+def test_adjoint_source_gradient_matches_differences():
+    """J is quadratic in f, so a central difference along any direction is exact
+    up to rounding: dJ/df . d must match it to ~1e-9."""
+    from oracle.adjoint import forward, gradient
+    pr, kap, f, gD, u_obs, J_of = _adjoint_case(5)
+    _, _, u, _ = forward(pr, f, gD)
+    _, gf, _ = gradient(pr, f, u - u_obs, gD)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        d = rng.standard_normal(f.shape)
+        h = 1e-3
+        fd = (J_of(kap, f + h * d) - J_of(kap, f - h * d)) / (2 * h)
+        assert abs(np.sum(gf * d) - fd) <= 1e-9 * max(abs(fd), 1.0)
+
+
+def test_adjoint_blocks_affine_in_kappa():
+    """The element blocks are affine in kappa_e (tau_e = kappa_e / tau_len + |beta|):
+    K(k0 + 2) - K(k0) = 2 (K(k0 + 1) - K(k0)) entry by entry."""
+    pr = HDGProblem(2, 2, 2, beta=(1.0, 0.5), kappa=1.3, tau_len=0.7)
+    for e in (0, 5):
+        k0 = pr.kappa[e]
+        b0, b1, b2 = pr.blocks_at(e, k0), pr.blocks_at(e, k0 + 1), pr.blocks_at(e, k0 + 2)
+        for X0, X1, X2 in zip(b0, b1, b2):
+            assert np.abs((X2 - X0) - 2 * (X1 - X0)).max() <= 1e-12 * max(np.abs(X1).max(), 1.0)
+        # and blocks_at restores the problem's own diffusivity
+        assert pr.kappa[e] == k0
