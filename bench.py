@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--restart", type=int, default=80)
     ap.add_argument("--mode", type=int, default=2, choices=[0, 1, 2],
                     help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
+    ap.add_argument("--orth", type=int, default=1, choices=[0, 1],
+                    help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes)")
     ap.add_argument("--no-split", action="store_true", help="FP64 panel updates in the condensation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -272,7 +274,7 @@ def run_ours(args):
         g = pr.rhs()
         if marks:
             marks[1].record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth)
         if st != 0:
             raise RuntimeError(f"solve did not converge: {rep}")
         if marks:
@@ -364,6 +366,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("GMRES(restart)", f"GMRES({args.restart})"),
                        "N_tr": N_tr, "macro_elements": N, "solve_mode": MODE_NAMES[args.mode],
+                       "orthogonalisation": ["CGS2", "CGS, Pythagorean norm"][args.orth],
                        "lu_panel_updates": "split-FP32" if split else "FP64",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: Schur blocks 1.47 GB, factors 42 GB, source 0.42 GB per replica"},
@@ -381,7 +384,7 @@ def run_ours(args):
         t0, t1 = ev(), ev()
         torch.cuda.synchronize()
         t0.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth)
         t1.record(stream)
         torch.cuda.synchronize()
         modes[MODE_NAMES[mode]] = {"seconds": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
@@ -391,10 +394,10 @@ def run_ours(args):
     if not args.no_e2e:
         fh = f.cpu().pin_memory()
         torch.cuda.synchronize()
-        pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode)    # warm-up of the host path
+        pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode, orth=args.orth)    # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, u, q, rep = pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode)
+        x, u, q, rep = pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode, orth=args.orth)
         e2e_s = time.perf_counter() - t0
         app_e2e = rep["iterations"] + rep["outer"]
         eu, es = aggregate(N_tr * app_e2e, e2e_s, world)

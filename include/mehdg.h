@@ -116,6 +116,10 @@ typedef struct {
   int maxit;             /* maximum number of operator applications inside GMRES */
   int restart;           /* GMRES restart length, 1 <= restart <= 128 */
   int mode;
+  int orth;              /* Arnoldi orthogonalisation: 0 = classical Gram-Schmidt applied twice
+                            (CGS2, four passes over the basis); 1 = classical Gram-Schmidt once,
+                            the new vector's norm from ||w||^2 - ||V^T w||^2 (two passes; loses
+                            orthogonality faster, which the restart from the true residual bounds) */
 } hdg_solve_opts;
 
 typedef struct {

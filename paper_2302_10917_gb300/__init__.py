@@ -45,7 +45,7 @@ class Info(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
-                ("mode", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("orth", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -222,10 +222,10 @@ class Problem:
         self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), 1, prec, 1 if precond else 0))
         return y
 
-    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True):
+    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0):
         g = g.to(self.device, torch.float64).contiguous()
         x = torch.zeros_like(g) if x0 is None else x0.to(self.device, torch.float64).clone()
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
         r = SolveReport()
         st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), 1, ctypes.byref(o), ctypes.byref(r))
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
@@ -250,13 +250,13 @@ class Problem:
         library's fixed scratch array (no device allocation inside the call)."""
         self._check(self.lib.hdg_condense_static(self.h, e0, count, _ptr(S_out), _ptr(g_out)))
 
-    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True, mode=0):
+    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True, mode=0, orth=0):
         """End-to-end call on host (ideally pinned) tensors; returns (x, u, q, report)."""
         N, Q, N_tr = self.info["N"], self.info["Q"], self.info["N_tr"]
         x = torch.empty(N_tr, dtype=torch.float64, pin_memory=True) if outputs else None
         u = torch.empty(N, Q, dtype=torch.float64, pin_memory=True) if outputs else None
         q = torch.empty(N, 2, Q, dtype=torch.float64, pin_memory=True) if outputs else None
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
         r = SolveReport()
         st = self.lib.hdg_run_host(self.h, _ptr(f_host), _ptr(gD_host), ctypes.byref(o), _ptr(x), _ptr(u),
                                    _ptr(q), ctypes.byref(r))
@@ -295,13 +295,13 @@ class Problem:
         self._check(self.lib.hdg_gradient(self.h, *[_ptr(t) for t in args], _ptr(dk), _ptr(df)))
         return dk, df
 
-    def adjoint(self, r, x, u, tol=1e-10, maxit=20000, restart=80, mode=0, want_df=True):
+    def adjoint(self, r, x, u, tol=1e-10, maxit=20000, restart=80, mode=0, want_df=True, orth=0):
         """dJ/dkappa [N] and dJ/df [N, n_qp] for dJ/du = r [N, Q], at the forward solution
         (x, u) of the current condensation (factors kept). Returns (dkappa, df, report)."""
         g = self.adjoint_rhs(r)
         self.transpose()
         try:
-            nu, rep, st = self.solve(g, tol=tol, maxit=maxit, restart=restart, mode=mode)
+            nu, rep, st = self.solve(g, tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
         finally:
             self.transpose()
         if st != HDG_OK:

@@ -354,7 +354,8 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!c) return HDG_ERR_ARG;
   if (!g || !x || !o || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
-  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
+  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
+      o->orth < 0 || o->orth > 1)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)

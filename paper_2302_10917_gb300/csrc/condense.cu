@@ -16,6 +16,13 @@
 // u-rows (blocked right-looking LU, panel width NB). The trailing block then
 // holds [S_e | -C A^-1 R] with S_e = D_e - C_e A_e^-1 B_e, and rows 0..Q-1
 // hold U, L^-1 P B_u and L^-1 P F for the back-solve.
+//
+// With split_update the system lives in split-FP32 form (hi, lo FP32 pairs in
+// the same 8 bytes per entry) from its formation to the end of the
+// elimination: the trailing updates, the bulk of the work, then run entirely
+// on the FP32 pipe. Pivot search, panel factorisation and the U12 triangular
+// solves convert their entries to FP64 and back; a last pass converts the
+// whole system to FP64 in place, so every reader sees FP64 entries.
 #include "internal.h"
 #include "df64.h"
 
@@ -43,6 +50,16 @@ struct CondArgs {
   int split_update;       // 1: trailing updates in split-FP32 arithmetic on the FP32 pipe
   int* piv;               // [N][Q] pivot row of every column (factors kept), or null
 };
+
+// An entry of the bordered system: FP64, or (split) a split-FP32 (hi, lo) pair
+// in the same 8 bytes.
+__device__ __forceinline__ double load_entry(const double* p, int split) {
+  return split ? df_to(*reinterpret_cast<const float2*>(p)) : *p;
+}
+__device__ __forceinline__ void store_entry(double* p, double v, int split) {
+  if (split) *reinterpret_cast<float2*>(p) = df_from(v);
+  else *p = v;
+}
 
 __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   for (int off = 16; off > 0; off >>= 1) {
@@ -119,7 +136,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         } else {
           v = 0.0;
         }
-        row[j] = v;
+        store_entry(row + j, v, a.split_update);
       }
     } else {
       const int r = i - Q, k = r / P1, t = r - k * P1;
@@ -136,7 +153,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         } else {
           v = 0.0;
         }
-        row[j] = v;
+        store_entry(row + j, v, a.split_update);
       }
     }
   }
@@ -146,7 +163,8 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {
       const int t = idx / P1, t2 = idx - t * P1;
       const int ni = a.dt.enode[k * P1 + t], nj = a.dt.enode[k * P1 + t2];
-      W[(size_t)ni * ld + nj] += tau * g.L[k] * a.dt.Gh[idx];
+      double* wp = W + (size_t)ni * ld + nj;
+      store_entry(wp, load_entry(wp, a.split_update) + tau * g.L[k] * a.dt.Gh[idx], a.split_update);
     }
     __syncthreads();
   }
@@ -158,7 +176,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     const int rows = R - j0;
     for (int idx = tid; idx < rows * NB; idx += nthr) {
       const int r = idx / NB, c = idx - r * NB;
-      Ls[r * LDP + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : 0.0;
+      Ls[r * LDP + c] = (c < nb) ? load_entry(W + (size_t)(j0 + r) * ld + j0 + c, a.split_update) : 0.0;
     }
     __syncthreads();
     for (int c = 0; c < nb; ++c) {
@@ -219,7 +237,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
     for (int idx = tid; idx < rows * nb; idx += nthr) {
       const int r = idx / nb, c = idx - r * nb;
-      W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDP + c];
+      store_entry(W + (size_t)(j0 + r) * ld + j0 + c, Ls[r * LDP + c], a.split_update);
     }
     const int jb = j0 + nb, ncol = Cc - jb;
     if (ncol > 0) {
@@ -237,7 +255,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           }
         }
 #pragma unroll
-        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : 0.0;
+        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? load_entry(W + (size_t)(j0 + c) * ld + j, a.split_update) : 0.0;
 #pragma unroll
         for (int c = 1; c < NB; ++c) {
           if (c < nb) {
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           }
         }
         for (int c = 0; c < nb; ++c) {
-          W[(size_t)(j0 + c) * ld + j] = u[c];
+          store_entry(W + (size_t)(j0 + c) * ld + j, u[c], a.split_update);
           if (a.split_update) reinterpret_cast<float2*>(Us)[c * ld + j] = df_from(u[c]);
           else Us[c * ld + j] = u[c];
         }
@@ -258,30 +276,44 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
       const int nrow = R - jb;
       const int ntile = (nrow + RT - 1) / RT;
       if (a.split_update) {
-        // L21 to (hi, lo) pairs in place; each 16-term panel product is then
-        // formed on the FP32 pipe with error-free transformations and
-        // subtracted from the FP64 entry once
+        // -L21 to (hi, lo) pairs in place; every trailing entry, itself a
+        // (hi, lo) pair, takes its 16 panel products with error-free
+        // transformations on the FP32 pipe
         for (int idx = tid; idx < nrow * NB; idx += nthr) {
           const int r = nb + idx / NB, c = idx % NB;
           double* p = Ls + r * LDP + c;
-          *reinterpret_cast<float2*>(p) = df_from(*p);
+          *reinterpret_cast<float2*>(p) = df_from(-*p);
         }
         __syncthreads();
         for (int item = tid; item < ntile * ncol; item += nthr) {
           const int rt = item / ncol, j = jb + (item - rt * ncol);
-          float2 u[NB];
-#pragma unroll
-          for (int c = 0; c < NB; ++c)
-            u[c] = (c < nb) ? reinterpret_cast<const float2*>(Us)[c * ld + j] : make_float2(0.f, 0.f);
           const int r0 = jb + rt * RT;
-          const int r1 = min(r0 + RT, R);
-          for (int r = r0; r < r1; ++r) {
-            double* wp = W + (size_t)r * ld + j;
-            const float2* l = reinterpret_cast<const float2*>(Ls + (r - j0) * LDP);
-            float h = 0.f, lo = 0.f;
+          // the RT entries are loaded first (in flight during the products)
+          float2 w0[RT];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) df_fma(h, lo, l[c], u[c]);
-            *wp -= df_to(make_float2(h, lo));
+          for (int rr = 0; rr < RT; ++rr)
+            w0[rr] = r0 + rr < R ? *reinterpret_cast<const float2*>(W + (size_t)(r0 + rr) * ld + j)
+                                 : make_float2(0.f, 0.f);
+          float h[RT], lo[RT];
+#pragma unroll
+          for (int rr = 0; rr < RT; ++rr) { h[rr] = 0.f; lo[rr] = 0.f; }
+          // RT independent product chains (rows past R repeat row R-1 and are not stored)
+#pragma unroll
+          for (int c = 0; c < NB; ++c) {
+            const float2 uc = (c < nb) ? reinterpret_cast<const float2*>(Us)[c * ld + j] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+              const int r = min(r0 + rr, R - 1);
+              df_fma(h[rr], lo[rr], reinterpret_cast<const float2*>(Ls + (r - j0) * LDP)[c], uc);
+            }
+          }
+#pragma unroll
+          for (int rr = 0; rr < RT; ++rr) {
+            if (r0 + rr < R) {
+              float wh = w0[rr].x, wl = w0[rr].y;
+              df_add(wh, wl, h[rr], lo[rr]);
+              *reinterpret_cast<float2*>(W + (size_t)(r0 + rr) * ld + j) = df_norm(wh, wl);
+            }
           }
         }
       } else
@@ -301,6 +333,15 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           *wp = acc;
         }
       }
+    }
+    __syncthreads();
+  }
+  if (a.split_update) {
+    // back to FP64 in place for every reader of the factored system
+    for (int idx = tid; idx < R * Cc; idx += nthr) {
+      const int r = idx / Cc, c = idx - r * Cc;
+      double* p = W + (size_t)r * ld + c;
+      *p = df_to(*reinterpret_cast<const float2*>(p));
     }
     __syncthreads();
   }

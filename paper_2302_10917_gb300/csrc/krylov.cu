@@ -48,7 +48,8 @@ struct SmallLayout {
   }
 };
 enum { F_STOP = 0, F_JUSED = 1 };
-constexpr int KGU = 1216;     // blocks of the streaming update / scale kernels, 8 per SM
+constexpr int KGU = 1216;     // blocks of the streaming update kernel, 8 per SM
+constexpr int KGD = 1216;     // blocks (over all vector groups) of the multi-dot, 8 per SM
 
 // ------------------------------------------------------------ FP64 helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -120,11 +121,11 @@ __device__ __forceinline__ void df_fma4(float& h, float& l, float4 a, float4 b) 
   df_fma(h, l, make_float2(a.z, a.w), make_float2(b.z, b.w));
 }
 
-// part[b * nv + i] = sum over pair chunk b of V_i . w; blockIdx.y selects a
-// group of VG basis vectors; two pairs per thread per iteration (2 VG loads).
-// ncol = nv, or nv + 1 to append the squared norm w . w as column nv.
-__global__ void __launch_bounds__(KT) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
-                                                     const float4* __restrict__ w, double* part, const int* stop) {
+// part[b * ncol + i] = sum over pair chunk b of V_i . w; blockIdx.y selects a
+// group of VG basis vectors. ncol = nv, or nv + 1 to append the squared norm
+// w . w as column nv. One pair per thread per iteration; four blocks per SM.
+__global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
+                                                        const float4* __restrict__ w, double* part, const int* stop) {
   if (stop && stop[F_STOP]) return;
   __shared__ float2 red[(KT / 32) * VG];
   const int g0 = blockIdx.y * VG;
@@ -135,110 +136,25 @@ __global__ void __launch_bounds__(KT) df_mdot_kernel(const float4* __restrict__ 
 #pragma unroll
   for (int g = 0; g < VG; ++g) { h[g] = 0.f; l[g] = 0.f; }
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  int64_t p = lo + threadIdx.x;
-  for (; p + (int64_t)blockDim.x < hi; p += 2 * (int64_t)blockDim.x) {
-    const int64_t p2 = p + blockDim.x;
-    float4 a[VG], b[VG];
-    const float4 wa = w[p], wb = w[p2];
-#pragma unroll
-    for (int g = 0; g < VG; ++g) {
-      a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p] : (g0 + g < ncol ? wa : z4);
-      b[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p2] : (g0 + g < ncol ? wb : z4);
-    }
-#pragma unroll
-    for (int g = 0; g < VG; ++g) {
-      df_fma4(h[g], l[g], a[g], wa);
-      df_fma4(h[g], l[g], b[g], wb);
-    }
-  }
-  if (p < hi) {
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    float4 a[VG];
     const float4 wa = w[p];
 #pragma unroll
-    for (int g = 0; g < VG; ++g) {
-      if (g0 + g < nv) df_fma4(h[g], l[g], V[(size_t)(g0 + g) * np + p], wa);
-      else if (g0 + g < ncol) df_fma4(h[g], l[g], wa, wa);
-    }
+    for (int g = 0; g < VG; ++g) a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p] : (g0 + g < ncol ? wa : z4);
+#pragma unroll
+    for (int g = 0; g < VG; ++g) df_fma4(h[g], l[g], a[g], wa);
   }
   df_block_reduce<VG>(h, l, ncol - g0, red, part + (size_t)blockIdx.x * ncol + g0);
 }
 
-// Pass 2 of CGS2, fused: w' = w - sum_i h_i V_i is written back, and the
-// block's partial dots V_i . w' (columns 0..nv-1) and ||w'||^2 (column nv)
-// go to part[b * (nv + 1) + .]. The block walks its chunk in sub-chunks of
-// blockDim pairs: phase A streams V from HBM to form w' (kept in shared
-// memory), phase B re-reads the same V sub-chunk (now in L1/L2) one warp per
-// basis vector and accumulates the dots in shared memory.
-__global__ void __launch_bounds__(KT) df_update_dot_kernel(const float4* __restrict__ V, int64_t np, int nv,
-                                                           const double* __restrict__ coef, float4* w, double* part,
-                                                           const int* stop) {
-  if (stop && stop[F_STOP]) return;
-  __shared__ float2 cf[136];
-  __shared__ float2 acc[136];
-  __shared__ float4 wsub[KT];
-  __shared__ float2 red[KT / 32];
-  for (int i = threadIdx.x; i < 136; i += blockDim.x) {
-    cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
-    acc[i] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = lo + chunk < np ? lo + chunk : np;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  float sh = 0.f, sl = 0.f;
-  for (int64_t base = lo; base < hi; base += blockDim.x) {
-    const int64_t p = base + threadIdx.x;
-    const bool in = p < hi;
-    // phase A: w' for this thread's pair
-    const float4 wv = in ? w[p] : z4;
-    float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
-    for (int i0 = 0; i0 < nv; i0 += 8) {
-      float4 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (in && i0 + u < nv) ? V[(size_t)(i0 + u) * np + p] : z4;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        df_fma(ah, al, cf[i0 + u], make_float2(v[u].x, v[u].y));
-        df_fma(bh, bl, cf[i0 + u], make_float2(v[u].z, v[u].w));
-      }
-    }
-    const float2 ra = df_norm(ah, al), rb = df_norm(bh, bl);
-    const float4 r4 = make_float4(ra.x, ra.y, rb.x, rb.y);
-    if (in) {
-      w[p] = r4;
-      df_fma(sh, sl, ra, ra);
-      df_fma(sh, sl, rb, rb);
-    }
-    wsub[threadIdx.x] = in ? r4 : z4;
-    __syncthreads();
-    // phase B: dots of the sub-chunk, warp `wid` owns vectors wid, wid + nw, ...
-    const int cnt = (int)(hi - base < (int64_t)blockDim.x ? hi - base : (int64_t)blockDim.x);
-    for (int i = wid; i < nv; i += nw) {
-      float h = 0.f, l = 0.f;
-      const float4* Vi = V + (size_t)i * np + base;
-      for (int q = lane; q < cnt; q += 32) df_fma4(h, l, Vi[q], wsub[q]);
-      df_warp_sum(h, l);
-      if (lane == 0) {
-        float2 a2 = acc[i];
-        df_add(a2.x, a2.y, h, l);
-        acc[i] = a2;
-      }
-    }
-    __syncthreads();
-  }
-  double* out = part + (size_t)blockIdx.x * (nv + 1);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) out[i] = df_to(acc[i]);
-  float hh[1] = {sh}, ll[1] = {sl};
-  df_block_reduce<1>(hh, ll, 1, red, out + nv);
-}
-
-// Sums pass-2 partials (stride nv + 1) in block order, adds the correction to
-// the Hessenberg column, takes the new vector's norm from
-// ||w' - V h2||^2 = ||w'||^2 - ||h2||^2 (orthonormal V), and applies the
-// Givens rotations. One block.
+// Sums the partials of one Arnoldi step (stride nv + 1: columns 0..nv-1 the
+// projections, column nv the squared norm of the vector they were taken of)
+// in block order; add = 1 adds them to the Hessenberg column (second
+// projection of CGS2), add = 0 sets it (single projection). The new vector's
+// norm follows from ||x - V s||^2 = ||x||^2 - ||s||^2 (orthonormal V). Then
+// the Givens rotations. One block.
 __global__ void reduce2_givens_kernel(const double* part, int G, int nv, double* sm, SmallLayout L, int* flags,
-                                      int j) {
+                                      int j, int add) {
   if (flags[F_STOP]) return;
   __shared__ double vals[136];
   __shared__ double red[32];
@@ -256,7 +172,7 @@ __global__ void reduce2_givens_kernel(const double* part, int G, int nv, double*
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     const double s = vals[i];
     sm[L.htmp + i] = s;
-    h[i] += s;
+    h[i] = add ? h[i] + s : s;
     q2 += s * s;
   }
   for (int off = 16; off > 0; off >>= 1) q2 += __shfl_down_sync(0xffffffffu, q2, off);
@@ -301,34 +217,45 @@ __global__ void reduce2_givens_kernel(const double* part, int G, int nv, double*
   if (est <= sm[L.sc + 2] || hn == 0.0) flags[F_STOP] = 1;
 }
 
-// Pass 3: V_{j+1} = (w' - sum_i h_i V_i) * sm[inv_off] over element pairs.
-__global__ void __launch_bounds__(KT) df_update_scale_kernel(const float4* __restrict__ V, int64_t np, int nv,
-                                                             const double* __restrict__ coef, const float4* w,
-                                                             const double* sm, int inv_off, float4* out,
-                                                             const int* stop) {
+// out = (w - sum_i coef_i V_i) * scale over element pairs, scale = sm[scale_off]
+// (or 1 when scale_off < 0); out may be w itself. The loads of the next group
+// of 8 basis vectors are issued before the products of the current group.
+__global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict__ V, int64_t np, int nv,
+                                                       const double* __restrict__ coef, const float4* w,
+                                                       const double* sm, int scale_off, float4* out,
+                                                       const int* stop) {
   if (stop && stop[F_STOP]) return;
-  __shared__ float2 cf[136];
-  for (int i = threadIdx.x; i < 136; i += blockDim.x) cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
+  __shared__ float2 cf[144];
+  for (int i = threadIdx.x; i < 144; i += blockDim.x) cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
   __syncthreads();
-  const float2 inv = df_from(sm[inv_off]);
+  const bool scaled = scale_off >= 0;
+  const float2 inv = scaled ? df_from(sm[scale_off]) : make_float2(1.f, 0.f);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
     const float4 wv = w[p];
     float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
-    for (int i0 = 0; i0 < nv; i0 += 8) {
-      float4 v[8];
+    float4 v[8], nx[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = i0 + u < nv ? V[(size_t)(i0 + u) * np + p] : z4;
+    for (int u = 0; u < 8; ++u) v[u] = u < nv ? V[(size_t)u * np + p] : z4;
+    for (int i0 = 0; i0 < nv; i0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) nx[u] = i0 + 8 + u < nv ? V[(size_t)(i0 + 8 + u) * np + p] : z4;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         df_fma(ah, al, cf[i0 + u], make_float2(v[u].x, v[u].y));
         df_fma(bh, bl, cf[i0 + u], make_float2(v[u].z, v[u].w));
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = nx[u];
     }
-    float sah = 0.f, sal = 0.f, sbh = 0.f, sbl = 0.f;
-    df_fma(sah, sal, df_norm(ah, al), inv);
-    df_fma(sbh, sbl, df_norm(bh, bl), inv);
-    const float2 ra = df_norm(sah, sal), rb = df_norm(sbh, sbl);
+    float2 ra = df_norm(ah, al), rb = df_norm(bh, bl);
+    if (scaled) {
+      float sah = 0.f, sal = 0.f, sbh = 0.f, sbl = 0.f;
+      df_fma(sah, sal, ra, inv);
+      df_fma(sbh, sbl, rb, inv);
+      ra = df_norm(sah, sal);
+      rb = df_norm(sbh, sbl);
+    }
     out[p] = make_float4(ra.x, ra.y, rb.x, rb.y);
   }
 }
@@ -455,7 +382,8 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   if ((e = cudaMemset(c->d_V, 0, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMemset(c->d_w, 0, ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_part, (size_t)KG * (K + 2) * sizeof(double))) != cudaSuccess) return e;
+  // partial rows: at most KGD over all groups, or 152 per group (KGD / 8 groups of 8 = 152)
+  if ((e = cudaMalloc(&c->d_part, (size_t)(KG > KGD ? KG : KGD) * (K + 2) * sizeof(double))) != cudaSuccess) return e;
   SmallLayout L(K);
   if ((e = cudaMalloc(&c->d_small, (size_t)L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flag, 4 * sizeof(int))) != cudaSuccess) return e;
@@ -471,6 +399,19 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 }
 
 #define LAUNCHED(k) (c->launches += (k))
+
+// Multi-dot over nv basis vectors (ncol = nv + 1 appends ||w||^2): about KGD
+// blocks over all groups of VG vectors (at least one per SM along x), fewer
+// for short vectors. Returns the number of partial rows (blocks along x).
+static int launch_mdot(const float4* V4, int64_t np, int nv, int ncol, const float4* w4, double* part,
+                       const int* fl, cudaStream_t st) {
+  const int gy = (ncol + VG - 1) / VG;
+  int64_t gx = KGD / gy > 152 ? KGD / gy : 152;
+  const int64_t need = (np + KT - 1) / KT;
+  if (gx > need) gx = need > 1 ? need : 1;
+  df_mdot_kernel<<<dim3((unsigned)gx, (unsigned)gy), KT, 0, st>>>(V4, np, nv, ncol, w4, part, fl);
+  return (int)gx;
+}
 
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
   const Params& P = c->prm;
@@ -495,6 +436,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
   const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
   const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
+  // streaming-update grid: at most KGU blocks, no more than one pass of KT pairs each
+  const int gu = (int)std::min<int64_t>(KGU, std::max<int64_t>(1, (np + KT - 1) / KT));
 
   // ||g||
   axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, 0.0, g, t, n, part);
@@ -548,17 +491,26 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, st));
       }
       ProfScope po(c, HDG_PROF_ORTHO);
-      // CGS2 in three passes over the basis:
-      // (1) h1 = V^T w; (2) w' = w - V h1 with h2 = V^T w' and ||w'||^2;
-      // (3) V_{j+1} = (w' - V h2) / ||w' - V h2||, the norm from ||w'||^2 - ||h2||^2
-      const dim3 gdot(KG, (nv + VG - 1) / VG);
-      df_mdot_kernel<<<gdot, KT, 0, st>>>(V4, np, nv, nv, w4, part, fl);
-      mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, KG, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
-      df_update_dot_kernel<<<KG, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, part, fl);
-      reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, KG, nv, sm, L, fl, j);
-      df_update_scale_kernel<<<KGU, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4,
-                                                 reinterpret_cast<float4*>(V + (size_t)(j + 1) * ldv), fl);
-      LAUNCHED(6);
+      float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * ldv);
+      if (o.orth == 0) {
+        // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
+        // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
+        // the norm from ||w'||^2 - ||h2||^2
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, st);
+        mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
+        df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st);
+        reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1);
+        LAUNCHED(4);
+      } else {
+        // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
+        // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st);
+        reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0);
+        LAUNCHED(2);
+      }
+      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl);
+      LAUNCHED(2);
     }
     cu.ok(cudaGetLastError());
     int hflags[2] = {0, 0};

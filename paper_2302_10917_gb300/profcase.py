@@ -1,12 +1,20 @@
 """Small, self-contained run of the hot-path kernels for profiler captures.
 
     python -m paper_2302_10917_gb300.profcase --n 64 --m 8 --p 3 --applies 4
+    python -m paper_2302_10917_gb300.profcase --n 128 --step --restart 80 --mode 2
 
-Builds the n x n macro mesh with the manufactured source, condenses it with a
-chunked workspace (factors not kept, a few GB on the device at most), then
-runs `applies` FP64 preconditioned trace applies, then one unpreconditioned
-FP64 apply, one split-FP32 (df64) apply and one FP32 apply. Prints the device
-time of each phase.
+Default: builds the n x n macro mesh with the manufactured source, condenses it
+with a chunked workspace (factors not kept, a few GB on the device at most),
+then runs `applies` FP64 preconditioned trace applies, then one
+unpreconditioned FP64 apply, one split-FP32 (df64) apply and one FP32 apply,
+and optionally `gmres-steps` Arnoldi steps. Prints the device time of each
+phase.
+
+--step: one step of the benchmark's pipeline with GMRES cut to one restart
+cycle: set_source, condensation (factors kept, the blocks the mode needs,
+split-FP32 panel updates), right-hand side, GMRES(restart) for `restart`
+Arnoldi steps, back-solve. Its kernel mix is that of a full step with fewer
+restart cycles.
 """
 import argparse
 import json
@@ -28,17 +36,24 @@ def main(argv=None):
                     help="also run this many GMRES(50) Arnoldi steps")
     ap.add_argument("--mode", type=int, default=2, help="GMRES Arnoldi operator (0 FP64, 1 FP32, 2 split FP32)")
     ap.add_argument("--lean", action="store_true", help="store only the blocks the chosen mode needs")
+    ap.add_argument("--step", action="store_true", help="one benchmark step cut to one restart cycle")
+    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--split", action="store_true", help="split-FP32 LU panel updates")
     a = ap.parse_args(argv)
     beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
     pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
     xy = pr.quad_points()
-    pr.set_source(wl.sin_sin_source(xy, 1.0, beta))
+    f = wl.sin_sin_source(xy, 1.0, beta)
     del xy
+    if a.step:
+        return _step(pr, f, a)
+    pr.set_source(f)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     t = [ev() for _ in range(7)]
     t[0].record()
     lean = a.lean
-    pr.condense(store_fp32=not lean or a.mode == 1, keep_factors=False, store_df64=not lean or a.mode == 2)
+    pr.condense(store_fp32=not lean or a.mode == 1, keep_factors=False, store_df64=not lean or a.mode == 2,
+                split_update=a.split)
     t[1].record()
     x = torch.from_numpy(wl.random_vector(pr.info["N_tr"], seed=5)).cuda()
     for _ in range(a.applies):
@@ -53,12 +68,34 @@ def main(argv=None):
     torch.cuda.synchronize()
     gm = None
     if a.gmres_steps > 0:
-        x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=50, maxit=a.gmres_steps, mode=a.mode, check=False)
+        x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=a.restart, maxit=a.gmres_steps, mode=a.mode,
+                               check=False)
         gm = rep
     out = {"info": pr.info, "gmres": gm, "condense_ms": t[0].elapsed_time(t[1]),
            "apply64_pc_ms": t[1].elapsed_time(t[2]) / max(1, a.applies), "apply64_ms": t[2].elapsed_time(t[3]),
            "apply32_ms": t[3].elapsed_time(t[4]), "apply_df_ms": t[4].elapsed_time(t[5]),
            "y_norm": float(y.norm()), "y32_norm": float(y32.norm()), "ydf_norm": float(ydf.norm())}
+    print(json.dumps(out))
+    pr.close()
+
+
+def _step(pr, f, a):
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t = [ev() for _ in range(5)]
+    torch.cuda.synchronize()
+    t[0].record()
+    pr.set_source(f)
+    pr.condense(keep_factors=True, store_fp32=a.mode == 1, store_df64=a.mode == 2, split_update=True)
+    t[1].record()
+    g = pr.rhs()
+    x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False)
+    t[2].record()
+    u, q = pr.recover(x)
+    t[3].record()
+    torch.cuda.synchronize()
+    out = {"info": pr.info, "gmres": rep, "condense_ms": t[0].elapsed_time(t[1]),
+           "gmres_ms": t[1].elapsed_time(t[2]), "recover_ms": t[2].elapsed_time(t[3]),
+           "u_norm": float(u.norm()), "launches": pr.launches()}
     print(json.dumps(out))
     pr.close()
 
