@@ -101,6 +101,22 @@ cudaError_t upload_tables(hdg_ctx* c) {
       {T.subnode.data(), T.subnode.size() * 4, (void**)&d.subnode},
       {T.ns_ptr.data(), T.ns_ptr.size() * 4, (void**)&d.ns_ptr}, {T.ns_idx.data(), T.ns_idx.size() * 4, (void**)&d.ns_idx},
   };
+  // split-FP32 copies: hi = (float) v, lo = (float) (v - hi)
+  std::vector<std::vector<float>> split;
+  auto add_split = [&](const std::vector<double>& v, float2** dst) {
+    std::vector<float> h(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float hi = (float)v[i];
+      h[2 * i] = hi;
+      h[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    split.push_back(std::move(h));
+    items.push_back({split.back().data(), split.back().size() * 4, (void**)dst});
+  };
+  split.reserve(10);
+  add_split(T.Kxx, &d.Kxx2); add_split(T.Kyy, &d.Kyy2); add_split(T.Ksym, &d.Ksym2);
+  add_split(T.Dxi, &d.Dxi2); add_split(T.Deta, &d.Deta2); add_split(T.Fh, &d.Fh2);
+  add_split(T.Pxi, &d.Pxi2); add_split(T.Peta, &d.Peta2); add_split(T.Hh, &d.Hh2); add_split(T.Gh, &d.Gh2);
   size_t total = 0;
   for (auto& it : items) total += round_up(it.bytes, 256);
   cudaError_t e = cudaMalloc(&c->d_tables, total);

@@ -17,12 +17,13 @@
 // holds [S_e | -C A^-1 R] with S_e = D_e - C_e A_e^-1 B_e, and rows 0..Q-1
 // hold U, L^-1 P B_u and L^-1 P F for the back-solve.
 //
-// With split_update the system lives in split-FP32 form (hi, lo FP32 pairs in
-// the same 8 bytes per entry) from its formation to the end of the
-// elimination: the trailing updates, the bulk of the work, then run entirely
-// on the FP32 pipe. Pivot search, panel factorisation and the U12 triangular
-// solves convert their entries to FP64 and back; a last pass converts the
-// whole system to FP64 in place, so every reader sees FP64 entries.
+// condense_df_kernel (split_update) does the same elimination with the system
+// in split-FP32 form (hi, lo FP32 pairs, 48-bit significand, the same 8 bytes
+// per entry) from its formation to the end of the elimination: formation from
+// split copies of the tables, pivot search on the high words, panel
+// factorisation, triangular solves and trailing updates with error-free
+// transformations, all on the FP32 pipe. A last pass converts the system to
+// FP64 in place, so that every reader sees FP64 entries.
 #include "internal.h"
 #include "df64.h"
 
@@ -47,19 +48,11 @@ struct CondArgs {
   float* St32;
   double* gel;
   int* info;
-  int split_update;       // 1: trailing updates in split-FP32 arithmetic on the FP32 pipe
+  int split_update;       // 1: condense_df_kernel (split-FP32 elimination on the FP32 pipe)
   int* piv;               // [N][Q] pivot row of every column (factors kept), or null
 };
 
-// An entry of the bordered system: FP64, or (split) a split-FP32 (hi, lo) pair
-// in the same 8 bytes.
-__device__ __forceinline__ double load_entry(const double* p, int split) {
-  return split ? df_to(*reinterpret_cast<const float2*>(p)) : *p;
-}
-__device__ __forceinline__ void store_entry(double* p, double v, int split) {
-  if (split) *reinterpret_cast<float2*>(p) = df_from(v);
-  else *p = v;
-}
+__device__ void condense_outputs(const CondArgs& a, const double* W, int e);
 
 __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   for (int off = 16; off > 0; off >>= 1) {
@@ -136,7 +129,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         } else {
           v = 0.0;
         }
-        store_entry(row + j, v, a.split_update);
+        row[j] = v;
       }
     } else {
       const int r = i - Q, k = r / P1, t = r - k * P1;
@@ -153,7 +146,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         } else {
           v = 0.0;
         }
-        store_entry(row + j, v, a.split_update);
+        row[j] = v;
       }
     }
   }
@@ -163,8 +156,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {
       const int t = idx / P1, t2 = idx - t * P1;
       const int ni = a.dt.enode[k * P1 + t], nj = a.dt.enode[k * P1 + t2];
-      double* wp = W + (size_t)ni * ld + nj;
-      store_entry(wp, load_entry(wp, a.split_update) + tau * g.L[k] * a.dt.Gh[idx], a.split_update);
+      W[(size_t)ni * ld + nj] += tau * g.L[k] * a.dt.Gh[idx];
     }
     __syncthreads();
   }
@@ -176,7 +168,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     const int rows = R - j0;
     for (int idx = tid; idx < rows * NB; idx += nthr) {
       const int r = idx / NB, c = idx - r * NB;
-      Ls[r * LDP + c] = (c < nb) ? load_entry(W + (size_t)(j0 + r) * ld + j0 + c, a.split_update) : 0.0;
+      Ls[r * LDP + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : 0.0;
     }
     __syncthreads();
     for (int c = 0; c < nb; ++c) {
@@ -237,7 +229,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
     for (int idx = tid; idx < rows * nb; idx += nthr) {
       const int r = idx / nb, c = idx - r * nb;
-      store_entry(W + (size_t)(j0 + r) * ld + j0 + c, Ls[r * LDP + c], a.split_update);
+      W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDP + c];
     }
     const int jb = j0 + nb, ncol = Cc - jb;
     if (ncol > 0) {
@@ -255,7 +247,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           }
         }
 #pragma unroll
-        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? load_entry(W + (size_t)(j0 + c) * ld + j, a.split_update) : 0.0;
+        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : 0.0;
 #pragma unroll
         for (int c = 1; c < NB; ++c) {
           if (c < nb) {
@@ -266,57 +258,14 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           }
         }
         for (int c = 0; c < nb; ++c) {
-          store_entry(W + (size_t)(j0 + c) * ld + j, u[c], a.split_update);
-          if (a.split_update) reinterpret_cast<float2*>(Us)[c * ld + j] = df_from(u[c]);
-          else Us[c * ld + j] = u[c];
+          W[(size_t)(j0 + c) * ld + j] = u[c];
+          Us[c * ld + j] = u[c];
         }
       }
       __syncthreads();
       // trailing update A22 -= L21 U12 (rows jb..R-1, columns jb..Cc-1)
       const int nrow = R - jb;
       const int ntile = (nrow + RT - 1) / RT;
-      if (a.split_update) {
-        // -L21 to (hi, lo) pairs in place; every trailing entry, itself a
-        // (hi, lo) pair, takes its 16 panel products with error-free
-        // transformations on the FP32 pipe
-        for (int idx = tid; idx < nrow * NB; idx += nthr) {
-          const int r = nb + idx / NB, c = idx % NB;
-          double* p = Ls + r * LDP + c;
-          *reinterpret_cast<float2*>(p) = df_from(-*p);
-        }
-        __syncthreads();
-        for (int item = tid; item < ntile * ncol; item += nthr) {
-          const int rt = item / ncol, j = jb + (item - rt * ncol);
-          const int r0 = jb + rt * RT;
-          // the RT entries are loaded first (in flight during the products)
-          float2 w0[RT];
-#pragma unroll
-          for (int rr = 0; rr < RT; ++rr)
-            w0[rr] = r0 + rr < R ? *reinterpret_cast<const float2*>(W + (size_t)(r0 + rr) * ld + j)
-                                 : make_float2(0.f, 0.f);
-          float h[RT], lo[RT];
-#pragma unroll
-          for (int rr = 0; rr < RT; ++rr) { h[rr] = 0.f; lo[rr] = 0.f; }
-          // RT independent product chains (rows past R repeat row R-1 and are not stored)
-#pragma unroll
-          for (int c = 0; c < NB; ++c) {
-            const float2 uc = (c < nb) ? reinterpret_cast<const float2*>(Us)[c * ld + j] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int rr = 0; rr < RT; ++rr) {
-              const int r = min(r0 + rr, R - 1);
-              df_fma(h[rr], lo[rr], reinterpret_cast<const float2*>(Ls + (r - j0) * LDP)[c], uc);
-            }
-          }
-#pragma unroll
-          for (int rr = 0; rr < RT; ++rr) {
-            if (r0 + rr < R) {
-              float wh = w0[rr].x, wl = w0[rr].y;
-              df_add(wh, wl, h[rr], lo[rr]);
-              *reinterpret_cast<float2*>(W + (size_t)(r0 + rr) * ld + j) = df_norm(wh, wl);
-            }
-          }
-        }
-      } else
       for (int item = tid; item < ntile * ncol; item += nthr) {
         const int rt = item / ncol, j = jb + (item - rt * ncol);
         double u[NB];
@@ -336,19 +285,16 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
     __syncthreads();
   }
-  if (a.split_update) {
-    // back to FP64 in place for every reader of the factored system
-    for (int idx = tid; idx < R * Cc; idx += nthr) {
-      const int r = idx / Cc, c = idx - r * Cc;
-      double* p = W + (size_t)r * ld + c;
-      *p = df_to(*reinterpret_cast<const float2*>(p));
-    }
-    __syncthreads();
-  }
   if (tid == 0 && a.info) a.info[e] = singular_col >= 0 ? singular_col + 1 : 0;
-  if (!a.write_outputs) return;
+  if (a.write_outputs) condense_outputs(a, W, e);
+}
 
-  // ------------------------------------------------------------- outputs
+// S_e, its preconditioned copies and the element right-hand side from the
+// factored bordered system (FP64 entries).
+__device__ void condense_outputs(const CondArgs& a, const double* W, int e) {
+  const Params& P = a.prm;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, ld = P.ld;
   // S_e row-blocks per local edge: S[e][k][j][t] = S_e(k P1 + t, j)
   const size_t sb = (size_t)e * 3 * nt * P1;
   for (int idx = tid; idx < nt * nt; idx += nthr) {
@@ -381,6 +327,311 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
     a.gel[(size_t)e * nt + r] = acc;
   }
+}
+
+// ------------------------------------------------------ split-FP32 kernel
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// a * b for split-FP32 values (Dekker product through FMA)
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return df_norm(p, e);
+}
+
+// 1 / d: FP32 quotient refined by one Newton step in split arithmetic
+__device__ __forceinline__ float2 df_recip(float2 d) {
+  const float q = 1.0f / d.x;
+  float r = fmaf(-d.x, q, 1.0f);
+  r = fmaf(-d.y, q, r);
+  return df_norm(q, q * r);
+}
+
+__device__ __forceinline__ void warp_argmax_f(float& v, int& i) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, v, off);
+    const int oi = __shfl_down_sync(0xffffffffu, i, off);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+
+__global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
+  const Params& P = a.prm;
+  const int e = (int)(a.e0 + blockIdx.x);
+  if (e >= P.N) return;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, Cc = P.Cc, ld = P.ld;
+  double* Wd = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)R * ld;
+  float2* W = reinterpret_cast<float2*>(Wd);
+
+  extern __shared__ double smem[];
+  float2* Ls = reinterpret_cast<float2*>(smem);             // [R][LDP]
+  float2* Us = reinterpret_cast<float2*>(smem + (size_t)R * LDP);   // [NB][ld]
+  __shared__ int piv_s[NB];
+  __shared__ float red_v[8];
+  __shared__ int red_i[8];
+  __shared__ float2 sc[24];     // element and edge scalars of the formation
+
+  // ---------------------------------------------------------- element data
+  ElemGeom g;
+  elem_geom(e, P.n, g);
+  const double kap = a.kappa[e];
+  const double tau = kap / P.tau_len + P.babs;
+  if (tid == 0) {
+    const double gxx = g.gxi[0] * g.gxi[0] + g.gxi[1] * g.gxi[1];
+    const double gxy = g.gxi[0] * g.geta[0] + g.gxi[1] * g.geta[1];
+    const double gyy = g.geta[0] * g.geta[0] + g.geta[1] * g.geta[1];
+    const double cK = kap * g.detJ;
+    sc[0] = df_from(cK * gxx);
+    sc[1] = df_from(cK * gxy);
+    sc[2] = df_from(cK * gyy);
+    sc[3] = df_from(-g.detJ * (P.bx * g.gxi[0] + P.by * g.gxi[1]));
+    sc[4] = df_from(-g.detJ * (P.bx * g.geta[0] + P.by * g.geta[1]));
+    for (int k = 0; k < 3; ++k) {
+      const double nxi = g.nrm[k][0] * g.gxi[0] + g.nrm[k][1] * g.gxi[1];
+      const double neta = g.nrm[k][0] * g.geta[0] + g.nrm[k][1] * g.geta[1];
+      const double bn = P.bx * g.nrm[k][0] + P.by * g.nrm[k][1];
+      sc[5 + k] = df_from(g.L[k] * (bn - tau));          // Fh and Gh terms of B_u and D_u
+      sc[8 + k] = df_from(g.L[k] * kap * nxi);           // Pxi terms
+      sc[11 + k] = df_from(g.L[k] * kap * neta);         // Peta terms
+      sc[14 + k] = df_from(g.L[k] * tau);                // Fh term of C_u, E
+      for (int l = 0; l < 3; ++l) {
+        const double nn = g.nrm[k][0] * g.nrm[l][0] + g.nrm[k][1] * g.nrm[l][1];
+        if (l >= k) sc[17 + (k == 0 ? l : (k == 1 ? 2 + l : 5))] = df_from(-kap * g.L[k] * g.L[l] * nn / g.detJ);
+      }
+    }
+  }
+  // source: per sub-triangle projections (FP64) in the panel area
+  double* proj = smem;
+  {
+    const double* fe = a.f_qp + (size_t)e * P.n_qp;
+    for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
+      const int s2 = idx / P.nloc, b = idx - s2 * P.nloc;
+      double acc = 0.0;
+      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s2 * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
+      proj[idx] = acc;
+    }
+  }
+  __syncthreads();
+
+  // --------------------------------------------------- form the bordered system
+  // one flat loop over all entries: independent table loads per thread
+  const float2 z2 = make_float2(0.f, 0.f);
+  for (int idx = tid; idx < R * ld; idx += nthr) {
+    const int i = idx / ld, j = idx - i * ld;
+    float h = 0.f, l = 0.f;
+    if (i < Q) {
+      if (j < Q) {
+        const size_t qi = (size_t)i * Q + j;
+        df_fma(h, l, sc[0], a.dt.Kxx2[qi]);
+        df_fma(h, l, sc[1], a.dt.Ksym2[qi]);
+        df_fma(h, l, sc[2], a.dt.Kyy2[qi]);
+        df_fma(h, l, sc[3], a.dt.Dxi2[qi]);
+        df_fma(h, l, sc[4], a.dt.Deta2[qi]);
+      } else if (j < Q + nt) {
+        const int c = j - Q, k = c / P1;
+        const size_t ic = (size_t)i * nt + c;
+        df_fma(h, l, sc[5 + k], a.dt.Fh2[ic]);
+        df_fma(h, l, df_neg(sc[8 + k]), a.dt.Pxi2[ic]);
+        df_fma(h, l, df_neg(sc[11 + k]), a.dt.Peta2[ic]);
+      } else if (j == Q + nt) {
+        double acc = 0.0;
+        for (int q = a.dt.ns_ptr[i]; q < a.dt.ns_ptr[i + 1]; ++q) acc += proj[a.dt.ns_idx[q]];
+        const float2 v = df_from(acc * g.detJ / (double)(P.m * P.m));
+        h = v.x;
+        l = v.y;
+      }
+    } else {
+      const int r = i - Q, k = r / P1, t = r - k * P1;
+      if (j < Q) {
+        const size_t jr = (size_t)j * nt + r;
+        df_fma(h, l, sc[8 + k], a.dt.Pxi2[jr]);
+        df_fma(h, l, sc[11 + k], a.dt.Peta2[jr]);
+        df_fma(h, l, sc[14 + k], a.dt.Fh2[jr]);
+      } else if (j < Q + nt) {
+        const int c = j - Q, l2 = c / P1, t2 = c - l2 * P1;
+        const int kk = k < l2 ? k : l2, ll = k < l2 ? l2 : k;
+        df_fma(h, l, sc[17 + (kk == 0 ? ll : (kk == 1 ? 2 + ll : 5))], a.dt.Hh2[(size_t)r * nt + c]);
+        if (l2 == k) df_fma(h, l, sc[5 + k], a.dt.Gh2[t * P1 + t2]);
+      }
+    }
+    W[idx] = df_norm(h, l);
+  }
+  __syncthreads();
+  // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
+  for (int k = 0; k < 3; ++k) {
+    for (int idx = tid; idx < P1 * P1; idx += nthr) {
+      const int ni = a.dt.enode[k * P1 + idx / P1], nj = a.dt.enode[k * P1 + idx % P1];
+      float2* wp = W + (size_t)ni * ld + nj;
+      const float2 w0 = *wp;
+      float h = w0.x, l = w0.y;
+      df_fma(h, l, sc[14 + k], a.dt.Gh2[idx]);
+      *wp = df_norm(h, l);
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------- blocked LU, Q pivots
+  int singular_col = -1;
+  for (int j0 = 0; j0 < Q; j0 += NB) {
+    const int nb = min(NB, Q - j0);
+    const int rows = R - j0;
+    for (int idx = tid; idx < rows * NB; idx += nthr) {
+      const int r = idx / NB, c = idx - r * NB;
+      Ls[r * LDP + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : z2;
+    }
+    __syncthreads();
+    // panel factorisation: each thread owns rows tid, tid + 256, ... of the
+    // panel; the pivot candidates of column c + 1 come out of the update of
+    // column c, so one column costs one block argmax and one barrier more
+    // when rows are interchanged
+    float cv = -1.0f;
+    int ci = 0x7fffffff;
+    for (int r = tid; r < Q - j0; r += nthr) {
+      const float v = fabsf(Ls[r * LDP].x);
+      if (v > cv) { cv = v; ci = r; }
+    }
+    for (int c = 0; c < nb; ++c) {
+      // pivot: largest |hi| among u-rows j0+c .. Q-1 (first one on ties)
+      warp_argmax_f(cv, ci);
+      if ((tid & 31) == 0) { red_v[tid >> 5] = cv; red_i[tid >> 5] = ci; }
+      __syncthreads();
+      if (tid < 32) {
+        float v = tid < (nthr >> 5) ? red_v[tid] : -1.0f;
+        int ii = tid < (nthr >> 5) ? red_i[tid] : 0x7fffffff;
+        warp_argmax_f(v, ii);
+        if (tid == 0) piv_s[c] = (v >= 0.0f && ii < Q - j0) ? ii : c;
+      }
+      __syncthreads();
+      const int pr = piv_s[c];
+      if (a.piv) {
+        if (tid == 0) a.piv[(size_t)e * Q + j0 + c] = j0 + pr;
+        if (pr != c)
+          for (int cc = tid; cc < j0; cc += nthr) {
+            float2* x0 = W + (size_t)(j0 + c) * ld + cc;
+            float2* x1 = W + (size_t)(j0 + pr) * ld + cc;
+            const float2 t0 = *x0;
+            *x0 = *x1;
+            *x1 = t0;
+          }
+      }
+      if (pr != c) {
+        if (tid < nb) {
+          const float2 t0 = Ls[c * LDP + tid];
+          Ls[c * LDP + tid] = Ls[pr * LDP + tid];
+          Ls[pr * LDP + tid] = t0;
+        }
+        __syncthreads();
+      }
+      const float2 d = Ls[c * LDP + c];
+      if (d.x == 0.0f && singular_col < 0) singular_col = j0 + c;
+      const float2 inv = (d.x != 0.0f) ? df_recip(d) : z2;
+      cv = -1.0f;
+      ci = 0x7fffffff;
+      for (int r = c + 1 + tid; r < rows; r += nthr) {
+        const float2 m = df_mul(Ls[r * LDP + c], inv);
+        Ls[r * LDP + c] = m;
+        const float2 nm = df_neg(m);
+        for (int cc = c + 1; cc < nb; ++cc) {
+          const float2 w0 = Ls[r * LDP + cc];
+          float h = w0.x, l = w0.y;
+          df_fma(h, l, nm, Ls[c * LDP + cc]);
+          Ls[r * LDP + cc] = df_norm(h, l);
+        }
+        if (c + 1 < nb && r < Q - j0) {
+          const float v = fabsf(Ls[r * LDP + c + 1].x);
+          if (v > cv) { cv = v; ci = r; }
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * nb; idx += nthr) {
+      const int r = idx / nb, c = idx - r * nb;
+      W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDP + c];
+    }
+    const int jb = j0 + nb, ncol = Cc - jb;
+    if (ncol > 0) {
+      // row interchanges and U12 = L11^-1 A12, one column per thread
+      for (int j = jb + tid; j < Cc; j += nthr) {
+        float2 u[NB];
+        for (int c = 0; c < nb; ++c) {
+          const int pr = piv_s[c];
+          if (pr != c) {
+            float2* x0 = W + (size_t)(j0 + c) * ld + j;
+            float2* x1 = W + (size_t)(j0 + pr) * ld + j;
+            const float2 t0 = *x0;
+            *x0 = *x1;
+            *x1 = t0;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : z2;
+#pragma unroll
+        for (int c = 1; c < NB; ++c) {
+          if (c < nb) {
+            float h = u[c].x, l = u[c].y;
+#pragma unroll
+            for (int t = 0; t < c; ++t) df_fma(h, l, df_neg(Ls[c * LDP + t]), u[t]);
+            u[c] = df_norm(h, l);
+          }
+        }
+        for (int c = 0; c < nb; ++c) {
+          W[(size_t)(j0 + c) * ld + j] = u[c];
+          Us[c * ld + j] = u[c];
+        }
+      }
+      __syncthreads();
+      // -L21 in place, then A22 -= L21 U12 (rows jb..R-1, columns jb..Cc-1)
+      const int nrow = R - jb;
+      for (int idx = tid; idx < nrow * NB; idx += nthr) {
+        float2* p = Ls + (nb + idx / NB) * LDP + idx % NB;
+        *p = df_neg(*p);
+      }
+      __syncthreads();
+      const int ntile = (nrow + RT - 1) / RT;
+      for (int item = tid; item < ntile * ncol; item += nthr) {
+        const int rt = item / ncol, j = jb + (item - rt * ncol);
+        const int r0 = jb + rt * RT;
+        // the RT entries are loaded first (in flight during the products)
+        float2 w0[RT];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) w0[rr] = r0 + rr < R ? W[(size_t)(r0 + rr) * ld + j] : z2;
+        float h[RT], lo[RT];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) { h[rr] = 0.f; lo[rr] = 0.f; }
+        // RT independent product chains (rows past R repeat row R-1 and are not stored)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const float2 uc = (c < nb) ? Us[c * ld + j] : z2;
+#pragma unroll
+          for (int rr = 0; rr < RT; ++rr) {
+            const int r = min(r0 + rr, R - 1);
+            df_fma(h[rr], lo[rr], Ls[(r - j0) * LDP + c], uc);
+          }
+        }
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) {
+          if (r0 + rr < R) {
+            float wh = w0[rr].x, wl = w0[rr].y;
+            df_add(wh, wl, h[rr], lo[rr]);
+            W[(size_t)(r0 + rr) * ld + j] = df_norm(wh, wl);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // back to FP64 in place for every reader of the factored system
+  for (int idx = tid; idx < R * Cc; idx += nthr) {
+    const int r = idx / Cc, c = idx - r * Cc;
+    const size_t o = (size_t)r * ld + c;
+    Wd[o] = df_to(W[o]);
+  }
+  __syncthreads();
+  if (tid == 0 && a.info) a.info[e] = singular_col >= 0 ? singular_col + 1 : 0;
+  if (a.write_outputs) condense_outputs(a, Wd, e);
 }
 
 // Back-solve Eq. (local_matrix_problem) on the factored bordered system:
@@ -528,9 +779,15 @@ cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* 
   a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
   a.S = S; a.St = St; a.St32 = St32; a.gel = gel; a.info = info;
   const size_t sm = condense_smem_bytes(P);
-  cudaError_t err = cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (err != cudaSuccess) return err;
-  condense_kernel<<<(unsigned)count, 256, sm, st>>>(a);
+  if (split_update) {
+    cudaError_t err = cudaFuncSetAttribute(condense_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    condense_df_kernel<<<(unsigned)count, 256, sm, st>>>(a);
+  } else {
+    cudaError_t err = cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err != cudaSuccess) return err;
+    condense_kernel<<<(unsigned)count, 256, sm, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct DevTables {
   double *phiq, *wq, *uq;
   int *subtri, *subnode, *ns_ptr, *ns_idx;
   double *bpsi, *bw, *bu;
+  // split-FP32 (hi, lo) copies of the element-formation tables
+  float2 *Kxx2, *Kyy2, *Ksym2, *Dxi2, *Deta2, *Fh2, *Pxi2, *Peta2, *Hh2, *Gh2;
 };
 
 // Scalar problem parameters passed by value to kernels.
