@@ -34,6 +34,12 @@ WORKLOAD = ("2D steady advection-diffusion, 128x128 macro grid (32768 macro-tria
             "p=3, beta=50(cos 0.3, sin 0.3), kappa=1, u=sin(pi x)sin(pi y), Dirichlet; step = condense + rhs + "
             "GMRES(restart) to 1e-10 true relative residual + back-solve")
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# split-FP32 multiply-add (Dekker product + two-sum accumulation): 1 FMUL + 3 FFMA + 8 FADD
+DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
+# DRAM bytes (read + write) of one apply_vdf_kernel<1> launch per interior edge, from an ncu
+# capture at n = 64, m = 8, p = 3 (376.2 MB for 12 160 edges); the traffic scales with the
+# edges. Only valid for that kernel and element (m = 8, p = 3).
+APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.2e6 / 12160
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
@@ -334,8 +340,8 @@ def run_ours(args):
                   "bound": "alu" if args.mode == 0 else "hbm",
                   "launches": prof["apply32" if args.mode == 1 else "apply"][0],
                   "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},
-        "condense": {"kernel": "condense_kernel (element build + bordered LU + Schur)"
-                               + (", split-FP32 panel updates" if split else ""),
+        "condense": {"kernel": ("condense_df_kernel (split-FP32 formation + bordered LU + Schur)" if split
+                                else "condense_kernel (FP64 formation + bordered LU + Schur)"),
                      "bound": "alu", "launches": prof["condense"][0], "avg_launch_ms": avg("condense")},
     }
     ra = rooflines["apply"]
@@ -349,14 +355,42 @@ def run_ours(args):
                   peak_source="measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s")
     ra["frac"] = ra["achieved"] / ra["peak"]
     rc = rooflines["condense"]
-    rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-              algorithmic_per_launch=cond_flops,
-              peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)")
+    if split:
+        rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=DF_PEAK_TFLOPS, unit="TFLOP/s",
+                  algorithmic_per_launch=cond_flops,
+                  peak_source="FP32 pipe in FP64-equivalent flop: 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 "
+                              "instructions per split-FP32 multiply-add x 2 flop (derived)")
+    else:
+        rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                  algorithmic_per_launch=cond_flops,
+                  peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)")
     rc["frac"] = rc["achieved"] / rc["peak"]
-    dom = max(("apply", "condense"), key=lambda kname: prof["apply32" if (kname == "apply" and args.mode == 1)
+    # Krylov vector passes: algorithmic bytes of every Arnoldi step of the timed solves
+    # (CGS: multi-dot over nv + 1 vectors, update reading nv + 1 and writing 1;
+    #  CGS2: two multi-dots and two updates)
+    K = args.restart
+    steps_bytes = 0.0
+    for r in reps:
+        its, cyc = r["iterations"], r["restarts"]
+        for ci in range(cyc):
+            jused = min(K, its - ci * K)
+            for j in range(max(jused, 0)):
+                nv = j + 1
+                steps_bytes += ((2 * nv + 3) if args.orth == 1 else (4 * nv + 6)) * 8.0 * N_tr
+    rooflines["ortho"] = {"kernel": "df_mdot_kernel + df_update_kernel (+ reduce2_givens_kernel)",
+                          "bound": "hbm", "launches": prof["ortho"][0], "avg_launch_ms": avg("ortho"),
+                          "achieved": steps_bytes / (prof["ortho"][1] / 1e3) / 1e9 if prof["ortho"][1] else 0.0,
+                          "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                          "algorithmic_total": steps_bytes,
+                          "note": "per Arnoldi step (launches = steps), all passes of that step"}
+    rooflines["ortho"]["frac"] = rooflines["ortho"]["achieved"] / rooflines["ortho"]["peak"]
+    dom = max(("apply", "condense", "ortho"), key=lambda kname: prof["apply32" if (kname == "apply" and args.mode == 1)
                                                            else kname][1])
     roof = dict(rooflines[dom])
     roof["traffic"] = None
+    if dom == "apply" and args.mode == 2 and (cfg["m"], cfg["p"]) == (8, 3):
+        roof["traffic"] = APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 * n_int
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 64, scaled by interior edges"
     roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,

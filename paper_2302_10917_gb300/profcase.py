@@ -38,7 +38,8 @@ def main(argv=None):
     ap.add_argument("--lean", action="store_true", help="store only the blocks the chosen mode needs")
     ap.add_argument("--step", action="store_true", help="one benchmark step cut to one restart cycle")
     ap.add_argument("--restart", type=int, default=50)
-    ap.add_argument("--split", action="store_true", help="split-FP32 LU panel updates")
+    ap.add_argument("--split", action="store_true", help="split-FP32 condensation")
+    ap.add_argument("--orth", type=int, default=1, help="0: CGS2, 1: single-projection Gram-Schmidt")
     a = ap.parse_args(argv)
     beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
     pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
@@ -69,7 +70,7 @@ def main(argv=None):
     gm = None
     if a.gmres_steps > 0:
         x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=a.restart, maxit=a.gmres_steps, mode=a.mode,
-                               check=False)
+                               check=False, orth=a.orth)
         gm = rep
     out = {"info": pr.info, "gmres": gm, "condense_ms": t[0].elapsed_time(t[1]),
            "apply64_pc_ms": t[1].elapsed_time(t[2]) / max(1, a.applies), "apply64_ms": t[2].elapsed_time(t[3]),
@@ -88,7 +89,7 @@ def _step(pr, f, a):
     pr.condense(keep_factors=True, store_fp32=a.mode == 1, store_df64=a.mode == 2, split_update=True)
     t[1].record()
     g = pr.rhs()
-    x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False)
+    x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False, orth=a.orth)
     t[2].record()
     u, q = pr.recover(x)
     t[3].record()
