@@ -569,6 +569,9 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
+  if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
+  for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 

@@ -192,6 +192,10 @@ struct hdg_ctx {
   double* d_small = nullptr;      // Hessenberg, Givens, scalars
   int* d_flag = nullptr;
   int krylov_restart = 0;
+  cudaGraphExec_t gm_exec = nullptr;   // captured GMRES cycle (one restart cycle of Arnoldi steps)
+  std::vector<intptr_t> gm_key;        // configuration the capture is valid for
+  cudaStream_t cap_stream = nullptr;   // private stream used only for the capture
+  std::vector<cudaEvent_t> gm_ev;      // per-step event quadruples of a timed capture
   size_t bytes = 0;
   int64_t launches = 0;     // kernels enqueued (reported by hdg_info)
   // per-phase event timing
@@ -209,7 +213,7 @@ struct ProfScope {
   int phase;
   cudaEvent_t b = nullptr, e = nullptr;
   ProfScope(hdg_ctx* ctx, int ph) : c(ctx), phase(ph) {
-    if (!c->prof_on) return;
+    if (!c->prof_on || ph < 0) return;
     if (!c->prof_pool.empty()) {
       b = c->prof_pool.back().first;
       e = c->prof_pool.back().second;

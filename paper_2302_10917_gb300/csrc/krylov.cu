@@ -153,17 +153,33 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 // projection of CGS2), add = 0 sets it (single projection). The new vector's
 // norm follows from ||x - V s||^2 = ||x||^2 - ||s||^2 (orthonormal V). Then
 // the Givens rotations. One block.
-__global__ void reduce2_givens_kernel(const double* part, int G, int nv, double* sm, SmallLayout L, int* flags,
-                                      int j, int add) {
+__global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part, int G, int nv, double* sm,
+                                                               SmallLayout L, int* flags, int j, int add) {
   if (flags[F_STOP]) return;
   __shared__ double vals[136];
   __shared__ double red[32];
+  __shared__ double wsum[32][132];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i <= nv; i += nw) {
-    double s = 0.0;
-    for (int b = lane; b < G; b += 32) s += part[(size_t)b * (nv + 1) + i];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) vals[i] = s;
+  // partial rows are read whole (coalesced): warp w sums rows w, w + nw, ...
+  // into per-lane column accumulators; then the warps' sums in fixed order
+  {
+    const int ncol = nv + 1;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = wid; b < G; b += nw) {
+      const double* row = part + (size_t)b * ncol;
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if (lane + 32 * k < ncol) acc[k] += row[lane + 32 * k];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (lane + 32 * k < ncol) wsum[wid][lane + 32 * k] = acc[k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < nw; ++w2) t += wsum[w2][i];
+      vals[i] = t;
+    }
   }
   __syncthreads();
   const int K1 = L.K + 1;
@@ -192,14 +208,14 @@ __global__ void reduce2_givens_kernel(const double* part, int G, int nv, double*
   const double d = vals[nv] - hh;
   const double hn = d > 0.0 ? sqrt(d) : 0.0;
   hs[j + 1] = hn;
+  // previous rotations: the running entry stays in a register
+  double x = hs[0];
   for (int i = 0; i < j; ++i) {
-    const double c = cs_s[i], s = sn_s[i];
-    const double t = c * hs[i] + s * hs[i + 1];
-    hs[i + 1] = -s * hs[i] + c * hs[i + 1];
-    hs[i] = t;
+    const double c = cs_s[i], s = sn_s[i], y = hs[i + 1];
+    h[i] = c * x + s * y;
+    x = -s * x + c * y;
   }
-  for (int i = 0; i < j; ++i) h[i] = hs[i];
-  const double a = hs[j], b = hs[j + 1];
+  const double a = x, b = hn;
   const double r = hypot(a, b);
   const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
   sm[L.cs + j] = c;
@@ -334,15 +350,19 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
   }
 }
 
-// y = R^-1 g for the rotated Hessenberg matrix (jused columns)
+// y = R^-1 g for the rotated Hessenberg matrix (jused columns), one warp:
+// rows from the bottom, each row's sum over the solved entries across lanes
 __global__ void lsq_kernel(double* sm, SmallLayout L, const int* flags) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   const int k = flags[F_JUSED];
   const int K1 = L.K + 1;
   for (int i = k - 1; i >= 0; --i) {
-    double s = sm[L.gv + i];
-    for (int c = i + 1; c < k; ++c) s -= sm[L.H + (size_t)c * K1 + i] * sm[L.y + c];
-    sm[L.y + i] = s / sm[L.H + (size_t)i * K1 + i];
+    double s = 0.0;
+    for (int c = i + 1 + lane; c < k; c += 32) s += sm[L.H + (size_t)c * K1 + i] * sm[L.y + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) sm[L.y + i] = (sm[L.gv + i] - s) / sm[L.H + (size_t)i * K1 + i];
+    __syncwarp();
   }
 }
 
@@ -482,35 +502,83 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     LAUNCHED(4);
     const int jmax = std::min(K, o.maxit - its);
     std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
-    for (int j = 0; j < jmax; ++j) {
-      mark[j] = c->prof_ev.size();
+    // one Arnoldi step j on stream s (timed phases only when profiling, i.e. not captured)
+    // (ev: event quadruple of a captured, timed step: apply begin/end, vector work begin/end)
+    auto enqueue_step = [&](int j, cudaStream_t s, bool timed, cudaEvent_t* ev) {
       const int nv = j + 1;
       double* Hcol = sm + L.H + (size_t)j * (K + 1);
+      if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
-        ProfScope ps(c, phase);
-        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, st));
+        ProfScope ps(c, timed ? phase : -1);
+        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s));
       }
-      ProfScope po(c, HDG_PROF_ORTHO);
+      if (ev) {
+        cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+        cu.ok(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+      }
+      ProfScope po(c, timed ? HDG_PROF_ORTHO : -1);
       float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * ldv);
       if (o.orth == 0) {
         // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
         // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
         // the norm from ||w'||^2 - ||h2||^2
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, st);
-        mdot_reduce_kernel<<<nv, 128, 0, st>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
-        df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st);
-        reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1);
-        LAUNCHED(4);
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s);
+        mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
+        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1);
       } else {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st);
-        reduce2_givens_kernel<<<1, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0);
-        LAUNCHED(2);
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0);
       }
-      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl);
-      LAUNCHED(2);
+      df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl);
+      if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
+    };
+    const int per_step = o.orth == 0 ? 6 : 4;
+    const bool graph_cycle = jmax == K;
+    if (graph_cycle) {
+      // the whole cycle as one CUDA graph, captured once per configuration on a
+      // private stream and replayed on the context stream; the device stop flag
+      // turns the steps after convergence into immediate returns. With
+      // profiling on, the capture carries an event quadruple per step.
+      const int timed = c->prof_on ? 1 : 0;
+      const std::vector<intptr_t> key = {K, bt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
+                                         (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)c->d_escale,
+                                         (intptr_t)np};
+      if (timed && (int)c->gm_ev.size() < 4 * K) {
+        while ((int)c->gm_ev.size() < 4 * K) {
+          cudaEvent_t ev;
+          if (!cu.ok(cudaEventCreate(&ev))) break;
+          c->gm_ev.push_back(ev);
+        }
+        c->gm_key.clear();   // event handles are part of a timed capture
+      }
+      if (!c->gm_exec || c->gm_key != key) {
+        if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
+        c->gm_exec = nullptr;
+        if (!c->cap_stream) cu.ok(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        if (cu.ok(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal))) {
+          for (int j = 0; j < K; ++j) enqueue_step(j, c->cap_stream, false, timed ? &c->gm_ev[4 * j] : nullptr);
+          cu.ok(cudaStreamEndCapture(c->cap_stream, &graph));
+        }
+        if (graph) {
+          cu.ok(cudaGraphInstantiate(&c->gm_exec, graph, 0));
+          cudaGraphDestroy(graph);
+        }
+        if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, std::string("GMRES cycle capture: ") + cudaGetErrorString(cu.err));
+        c->gm_key = key;
+      }
+      cu.ok(cudaGraphLaunch(c->gm_exec, st));
+      LAUNCHED(per_step * K);
+    } else {
+      for (int j = 0; j < jmax; ++j) {
+        mark[j] = c->prof_ev.size();
+        enqueue_step(j, st, true, nullptr);
+        LAUNCHED(per_step);
+      }
     }
     cu.ok(cudaGetLastError());
     int hflags[2] = {0, 0};
@@ -518,7 +586,20 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     cu.ok(cudaStreamSynchronize(st));
     if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
     const int jused = hflags[F_JUSED];
-    if (c->prof_on && jused < jmax) {
+    if (c->prof_on && graph_cycle) {
+      // timed capture: fold the per-step events of the steps that did work
+      for (int j = 0; j < jused; ++j) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->gm_ev[4 * j], c->gm_ev[4 * j + 1]) == cudaSuccess) {
+          c->prof_ms[phase] += ms;
+          c->prof_count[phase] += 1;
+        }
+        if (cudaEventElapsedTime(&ms, c->gm_ev[4 * j + 2], c->gm_ev[4 * j + 3]) == cudaSuccess) {
+          c->prof_ms[HDG_PROF_ORTHO] += ms;
+          c->prof_count[HDG_PROF_ORTHO] += 1;
+        }
+      }
+    } else if (c->prof_on && jused < jmax) {
       // steps after the stop flag was raised were enqueued but returned at once: not timed work
       for (size_t i = mark[jused]; i < c->prof_ev.size(); ++i) c->prof_pool.push_back(c->prof_ev[i].second);
       c->prof_ev.resize(mark[jused]);
