@@ -291,7 +291,10 @@ def run_ours(args):
             rec.append((marks, rep))
         return rep
 
-    for _ in range(args.warmup):
+    # the project's launch-shape autotuner runs once per problem (outside the timed region)
+    step()
+    tune = pr.autotune(mode=args.mode, restart=args.restart)
+    for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
     if world > 1:
@@ -409,7 +412,8 @@ def run_ours(args):
             "restarts": reps[-1]["restarts"], "rel_residual": reps[-1]["rel_residual"],
             "apply_gdofs": N_tr / (rooflines["apply"]["avg_launch_ms"] / 1e3) / 1e9,
             "phases_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-            "roofline": roof, "roofline_other": roof_other, "gpu_launches": int(launches), "clocks": clk}
+            "roofline": roof, "roofline_other": roof_other, "gpu_launches": int(launches), "clocks": clk,
+            "autotune": tune}
 
     # the metric compares FP64 with FP32 + refinement: time-to-1e-10 of every solve mode
     modes = {}

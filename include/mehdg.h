@@ -284,6 +284,28 @@ hdg_status hdg_adjoint_recover(hdg_ctx* ctx, const double* r_dev, const double* 
 hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, const double* mu_dev,
                         const double* nu_dev, double* dkappa_dev, double* df_dev);
 
+/* Launch-shape autotuner (no counterpart in the paper; project-written).
+ * Times, with CUDA events on the context stream, the candidate launch shapes
+ * of the GMRES kernels for opts->mode at this problem size: edges per block
+ * of the trace-operator apply (one thread per edge and trace position, up to
+ * 512 threads), blocks of the multi-dot and of the streaming update (at
+ * opts->restart / 2 basis vectors). Keeps the fastest of each in the context
+ * for every later hdg_solve / hdg_apply and reports them. Arithmetic and
+ * results are unchanged by the apply's shape; the multi-dot's partial sums
+ * follow its block count (fixed per context, so solves stay reproducible).
+ * Needs hdg_condense (with the blocks the mode uses). Synchronous. */
+typedef struct {
+  int apply_edges_per_block; /* chosen edges per block of the apply */
+  int apply_threads;         /* threads per block that implies */
+  int mdot_blocks;           /* multi-dot blocks over all vector groups */
+  int update_blocks;         /* streaming-update blocks */
+  double apply_ms;           /* best times of the three kernels */
+  double mdot_ms;
+  double update_ms;
+  double default_ms;         /* the three kernels with the built-in shapes */
+} hdg_tune_report;
+hdg_status hdg_autotune(hdg_ctx* ctx, const hdg_solve_opts* opts, hdg_tune_report* report);
+
 /* Per-phase device timing (tracing). Phases: */
 #define HDG_PROF_CONDENSE 0   /* condensation kernel launches (element build + LU + Schur) */
 #define HDG_PROF_APPLY 1      /* preconditioned FP64 / split-FP32 apply launches (hdg_apply, GMRES's Arnoldi steps) */

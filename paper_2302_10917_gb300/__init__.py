@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_C
 EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", "hdg_set_source",
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
             "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_set_kappa",
-            "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_last_error",
+            "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_autotune",
+            "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32", "resid", "adjoint"]
@@ -51,6 +52,15 @@ class SolveOpts(ctypes.Structure):
 class SolveReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("apply_edges_per_block", ctypes.c_int), ("apply_threads", ctypes.c_int),
+                ("mdot_blocks", ctypes.c_int), ("update_blocks", ctypes.c_int), ("apply_ms", ctypes.c_double),
+                ("mdot_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -96,6 +106,7 @@ def load_library(path=LIB_PATH):
     lib.hdg_adjoint_rhs.argtypes = [vp, dp, dp]
     lib.hdg_adjoint_recover.argtypes = [vp, dp, dp, dp]
     lib.hdg_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.hdg_autotune.argtypes = [vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(TuneReport)]
     lib.hdg_profile.argtypes = [vp, ctypes.c_int]
     lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
@@ -231,6 +242,14 @@ class Problem:
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
             self._check(st)
         return x, r.as_dict(), st
+
+    def autotune(self, mode=0, restart=80):
+        """hdg_autotune: time candidate launch shapes of the GMRES kernels for this mode and
+        problem size, keep the fastest; returns the report as a dict."""
+        o = SolveOpts(tol=1e-10, maxit=1, restart=restart, mode=mode, orth=0)
+        r = TuneReport()
+        self._check(self.lib.hdg_autotune(self.h, ctypes.byref(o), ctypes.byref(r)))
+        return r.as_dict()
 
     def recover(self, x):
         x = x.to(self.device, torch.float64).contiguous()

@@ -382,6 +382,18 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   return s;
 }
 
+hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* rep) {
+  if (!c) return HDG_ERR_ARG;
+  if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
+  if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
+    return set_err(c, HDG_ERR_ARG, "bad solve options");
+  if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
+  if (o->mode == 2 && !c->d_Stdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  *rep = hdg_tune_report{};
+  return autotune(c, *o, *rep);
+}
+
 hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nrhs) {
   if (!c) return HDG_ERR_ARG;
   if (!x || !u || !q || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) apply_df_kernel(Params P, const float2* _
 // BT = 0: FP64 blocks, FP64 accumulation; BT = 1: split-FP32 blocks and
 // accumulation on the FP32 pipe; BT = 2: FP32 blocks, FP32 accumulation.
 template <int BT>
-__global__ void __launch_bounds__(256) apply_vdf_kernel(Params P, const void* __restrict__ Sv,
+__global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __restrict__ Sv,
                                                         const float2* __restrict__ x, float2* __restrict__ y,
                                                         const double* __restrict__ escale, int epb,
                                                         const int* __restrict__ stop) {
@@ -293,14 +293,16 @@ __global__ void __launch_bounds__(256) apply_vdf_kernel(Params P, const void* __
 }
 
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
-                             const double* escale, const int* stop, cudaStream_t st) {
-  const int epb = apply_edges_per_block(P);
+                             const double* escale, const int* stop, cudaStream_t st, int epb) {
+  // epb edges per block, one thread per (edge, trace position): at most 512 threads
+  if (epb <= 0 || epb * P.P1 > 512) epb = apply_edges_per_block(P);
+  const int threads = (epb * P.P1 + 31) / 32 * 32;
   const int grid = (P.n_int + epb - 1) / epb;
   const size_t el = bt == 0 ? sizeof(double) : (bt == 1 ? sizeof(float2) : sizeof(float));
   const size_t sm = (size_t)epb * 2 * P.n_t * el;
-  if (bt == 0) apply_vdf_kernel<0><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
-  else if (bt == 1) apply_vdf_kernel<1><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
-  else apply_vdf_kernel<2><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
+  if (bt == 0) apply_vdf_kernel<0><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
+  else if (bt == 1) apply_vdf_kernel<1><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
+  else apply_vdf_kernel<2><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
   return cudaGetLastError();
 }
 

@@ -192,6 +192,10 @@ struct hdg_ctx {
   double* d_small = nullptr;      // Hessenberg, Givens, scalars
   int* d_flag = nullptr;
   int krylov_restart = 0;
+  // launch shapes chosen by hdg_autotune (0: built-in defaults)
+  int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)
+  int tune_kgd = 0;               // multi-dot blocks over all vector groups
+  int tune_kgu = 0;               // streaming-update blocks
   cudaGraphExec_t gm_exec = nullptr;   // captured GMRES cycle (one restart cycle of Arnoldi steps)
   std::vector<intptr_t> gm_key;        // configuration the capture is valid for
   cudaStream_t cap_stream = nullptr;   // private stream used only for the capture

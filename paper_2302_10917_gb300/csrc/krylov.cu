@@ -50,6 +50,8 @@ struct SmallLayout {
 enum { F_STOP = 0, F_JUSED = 1 };
 constexpr int KGU = 1216;     // blocks of the streaming update kernel, 8 per SM
 constexpr int KGD = 1216;     // blocks (over all vector groups) of the multi-dot, 8 per SM
+constexpr int KGD_MAX = 2432; // largest multi-dot block count the autotuner tries
+constexpr int KGU_MAX = 4864; // largest streaming-update block count the autotuner tries
 
 // ------------------------------------------------------------ FP64 helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -402,8 +404,10 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   if ((e = cudaMemset(c->d_V, 0, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMemset(c->d_w, 0, ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
-  // partial rows: at most KGD over all groups, or 152 per group (KGD / 8 groups of 8 = 152)
-  if ((e = cudaMalloc(&c->d_part, (size_t)(KG > KGD ? KG : KGD) * (K + 2) * sizeof(double))) != cudaSuccess) return e;
+  // partial rows of a multi-dot: kgd / gy per group (at most KGD_MAX over all
+  // groups) or 152 per group, each row (K + 2) columns at most
+  if ((e = cudaMalloc(&c->d_part, (size_t)(KG > KGD_MAX ? KG : KGD_MAX) * (K + 2) * sizeof(double))) != cudaSuccess)
+    return e;
   SmallLayout L(K);
   if ((e = cudaMalloc(&c->d_small, (size_t)L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flag, 4 * sizeof(int))) != cudaSuccess) return e;
@@ -420,13 +424,13 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 
 #define LAUNCHED(k) (c->launches += (k))
 
-// Multi-dot over nv basis vectors (ncol = nv + 1 appends ||w||^2): about KGD
+// Multi-dot over nv basis vectors (ncol = nv + 1 appends ||w||^2): about kgd
 // blocks over all groups of VG vectors (at least one per SM along x), fewer
 // for short vectors. Returns the number of partial rows (blocks along x).
 static int launch_mdot(const float4* V4, int64_t np, int nv, int ncol, const float4* w4, double* part,
-                       const int* fl, cudaStream_t st) {
+                       const int* fl, cudaStream_t st, int kgd) {
   const int gy = (ncol + VG - 1) / VG;
-  int64_t gx = KGD / gy > 152 ? KGD / gy : 152;
+  int64_t gx = kgd / gy > 152 ? kgd / gy : 152;
   const int64_t need = (np + KT - 1) / KT;
   if (gx > need) gx = need > 1 ? need : 1;
   df_mdot_kernel<<<dim3((unsigned)gx, (unsigned)gy), KT, 0, st>>>(V4, np, nv, ncol, w4, part, fl);
@@ -456,8 +460,12 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
   const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
   const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
-  // streaming-update grid: at most KGU blocks, no more than one pass of KT pairs each
-  const int gu = (int)std::min<int64_t>(KGU, std::max<int64_t>(1, (np + KT - 1) / KT));
+  // launch shapes: the autotuner's choices, else the defaults; the streaming
+  // update needs no more than one pass of KT pairs per block
+  const int kgd = c->tune_kgd > 0 ? c->tune_kgd : KGD;
+  const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
+  const int epb = c->tune_epb[bt];
+  const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
 
   // ||g||
   axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, 0.0, g, t, n, part);
@@ -510,7 +518,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s));
+        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s, epb));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -522,15 +530,15 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
         // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
         // the norm from ||w'||^2 - ||h2||^2
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s);
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd);
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
         df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd);
         reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1);
       } else {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s);
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd);
         reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0);
       }
       df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl);
@@ -546,7 +554,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       const int timed = c->prof_on ? 1 : 0;
       const std::vector<intptr_t> key = {K, bt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)c->d_escale,
-                                         (intptr_t)np};
+                                         (intptr_t)np, kgd, kgu, epb};
       if (timed && (int)c->gm_ev.size() < 4 * K) {
         while ((int)c->gm_ev.size() < 4 * K) {
           cudaEvent_t ev;
@@ -613,6 +621,92 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   }
   rep.converged = 0;
   return fail(c, HDG_ERR_NOCONV, "GMRES reached maxit with relative residual " + std::to_string(rel));
+}
+
+// ------------------------------------------------------------- autotuner
+hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
+  const Params& P = c->prm;
+  const int K = o.restart;
+  Cu cu{c};
+  if (!cu.ok(ensure_krylov(c, K))) return fail(c, HDG_ERR_OOM, std::string("Krylov workspace: ") + cudaGetErrorString(cu.err));
+  cudaStream_t st = c->stream;
+  const int64_t n = P.N_tr, ldv = n + (n & 1), np = ldv / 2;
+  const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
+  const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+  float2* V = c->d_V;
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  float4* w4 = reinterpret_cast<float4*>(c->d_w);
+  // scratch: the update writes basis vector nv (contents of the basis are not
+  // kept across solves); no stop flag, so every candidate does its full work
+  const int nv = K / 2 > 1 ? K / 2 : 1;
+  double* coef = c->d_small;   // coefficients read by the update (any values)
+  cudaEvent_t e0, e1;
+  cu.ok(cudaEventCreate(&e0));
+  cu.ok(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& launch) -> double {
+    launch();
+    float best = 1e30f;
+    for (int r = 0; r < 5; ++r) {
+      cu.ok(cudaEventRecord(e0, st));
+      launch();
+      cu.ok(cudaEventRecord(e1, st));
+      cu.ok(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cu.ok(cudaEventElapsedTime(&ms, e0, e1));
+      best = ms < best ? ms : best;
+    }
+    return best;
+  };
+  // apply: edges per block for 128 .. 512 threads
+  const int def_epb = apply_edges_per_block(P);
+  int best_epb = def_epb;
+  double best_apply = 1e30, def_apply = 0.0;
+  for (int threads : {128, 256, 384, 512}) {
+    const int epb = threads / P.P1 > 0 ? threads / P.P1 : 1;
+    if (epb * P.P1 > 512) continue;
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, c->d_escale, nullptr, st, epb)); });
+    if (epb == def_epb) def_apply = t;
+    if (t < best_apply) { best_apply = t; best_epb = epb; }
+  }
+  if (def_apply == 0.0)
+    def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, c->d_escale, nullptr, st, def_epb)); });
+  // multi-dot blocks
+  int best_kgd = KGD;
+  double best_mdot = 1e30, def_mdot = 0.0;
+  for (int kgd : {608, 1216, 2432}) {
+    const double t = time_it([&] { launch_mdot(V4, np, nv, nv + 1, w4, c->d_part, nullptr, st, kgd); });
+    if (kgd == KGD) def_mdot = t;
+    if (t < best_mdot) { best_mdot = t; best_kgd = kgd; }
+  }
+  // streaming-update blocks
+  int best_kgu = KGU;
+  double best_upd = 1e30, def_upd = 0.0;
+  float4* out = reinterpret_cast<float4*>(V + (size_t)nv * ldv);
+  for (int kgu : {608, 1216, 2432, 4864}) {
+    const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
+    const double t = time_it([&] {
+      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, coef, w4, nullptr, -1, out, nullptr);
+      cu.ok(cudaGetLastError());
+    });
+    if (kgu == KGU) def_upd = t;
+    if (t < best_upd) { best_upd = t; best_kgu = kgu; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->launches += 6 * (4 + 3 + 4) + 1;
+  if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(cu.err));
+  c->tune_epb[bt] = best_epb;
+  c->tune_kgd = best_kgd;
+  c->tune_kgu = best_kgu;
+  rep.apply_edges_per_block = best_epb;
+  rep.apply_threads = (best_epb * P.P1 + 31) / 32 * 32;
+  rep.mdot_blocks = best_kgd;
+  rep.update_blocks = best_kgu;
+  rep.apply_ms = best_apply;
+  rep.mdot_ms = best_mdot;
+  rep.update_ms = best_upd;
+  rep.default_ms = def_apply + def_mdot + def_upd;
+  return HDG_OK;
 }
 
 }  // namespace mehdg

@@ -24,7 +24,8 @@ cudaError_t launch_apply32(const Params& P, const float* S, const float* x, floa
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st);
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
-                             const double* escale, const int* stop, cudaStream_t st);
+                             const double* escale, const int* stop, cudaStream_t st, int epb = 0);
+int apply_edges_per_block(const Params& P);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
@@ -44,5 +45,7 @@ cudaError_t launch_gradient(const Params& P, const DevTables& dt, const double* 
 
 // Restarted GMRES on the condensed system (krylov.cu).
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep);
+// Launch-shape autotuner of the GMRES kernels (krylov.cu).
+hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep);
 
 }  // namespace mehdg
