@@ -53,7 +53,10 @@
  * message that hdg_last_error returns; the context stays usable unless the
  * status is HDG_ERR_CUDA. Call order: hdg_create -> hdg_set_source ->
  * hdg_condense -> {hdg_rhs, hdg_apply, hdg_solve} -> hdg_recover; a call out
- * of order returns HDG_ERR_STATE. Only nrhs = 1 is accepted by this version.
+ * of order returns HDG_ERR_STATE.
+ * Several right-hand sides (1 <= nrhs <= HDG_MAX_RHS, fixed by
+ * hdg_set_source) share one condensation: every per-RHS array is RHS-major,
+ * i.e. nrhs consecutive copies of the single-RHS layout ([nrhs][...]).
  * Nothing here falls back to the CPU: without a usable sm_103a device every
  * entry point that launches work returns HDG_ERR_CUDA.
  */
@@ -156,11 +159,13 @@ hdg_status hdg_quad_points(const hdg_ctx* ctx, double* xy_dev);
 /* Physical coordinates of the Dirichlet-data points, [4 n][n_bqp][2] FP64. */
 hdg_status hdg_bnd_quad_points(const hdg_ctx* ctx, double* xy_dev);
 
-/* Record the source f at the quadrature points ([N][n_qp] FP64, device) and
- * the Dirichlet data g_D at the boundary points ([4 n][n_bqp] FP64, device,
- * or NULL for g_D = 0). The arrays are read by hdg_condense and
+/* Record nrhs sources f at the quadrature points ([nrhs][N][n_qp] FP64,
+ * device) and Dirichlet data g_D at the boundary points ([nrhs][4 n][n_bqp]
+ * FP64, device, or NULL for g_D = 0). The arrays are read by hdg_condense and
  * hdg_recover and must stay valid until then. Eq. (weak_form): l(V), with
- * u^ = v^ + g^ (Sec. 3.1) and g^ the L2 projection of g_D (Sec. 2.3). */
+ * u^ = v^ + g^ (Sec. 3.1) and g^ the L2 projection of g_D (Sec. 2.3).
+ * nrhs > 1 adds nrhs load columns to every element's bordered system. */
+#define HDG_MAX_RHS 64
 hdg_status hdg_set_source(hdg_ctx* ctx, const double* f_qp_dev, const double* gD_qp_dev, int nrhs);
 
 /* Static condensation of every macro-element, Eqs. (global_problem) and
@@ -174,15 +179,18 @@ hdg_status hdg_set_source(hdg_ctx* ctx, const double* f_qp_dev, const double* gD
  * in the message), HDG_ERR_OOM, HDG_ERR_STATE before hdg_set_source. */
 hdg_status hdg_condense(hdg_ctx* ctx, unsigned flags);
 
-/* Assembled condensed right-hand side g = R_u^ - C A^-1 R_u (Eq.
- * global_problem) including the Dirichlet lift; [N_tr] FP64 device. */
+/* Assembled condensed right-hand sides g = R_u^ - C A^-1 R_u (Eq.
+ * global_problem) including the Dirichlet lift; [nrhs][N_tr] FP64 device. */
 hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
 
 /* Matrix-free trace-operator apply (Sec. 3.3.2, steps 1-4):
  *   precond = 0: y = S x, S = sum_e L_e^T (D_e - C_e A_e^-1 B_e) L_e;
  *   precond = 1: y = D^-1 S x, the left-preconditioned operator of Sec. 6.1.
- * x, y: [N_tr] device arrays, FP64 (prec = 64) or FP32 (prec = 32, uses the
- * FP32 blocks; precond must be 1). x and y must not overlap. */
+ * x, y: [nrhs][N_tr] device arrays (1 <= nrhs <= HDG_MAX_RHS, independent of
+ * hdg_set_source's nrhs), FP64 (prec = 64), FP64 with the split-FP32 blocks
+ * (prec = 48, precond = 1, HDG_STORE_DF64) or FP32 (prec = 32, the FP32
+ * blocks, precond = 1). nrhs > 1 streams every block once for all columns
+ * (multi-RHS apply). x and y must not overlap. */
 hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int prec, int precond);
 
 /* Solve S x = g (Eq. global_problem) with restarted GMRES, left-

@@ -161,6 +161,7 @@ class Problem:
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
         self.n, self.m, self.p = n, m, p
         self._src = None
+        self.nrhs = 1
         self.version = 0        # bumped by every condensation (the factors the adjoint reuses)
 
     def launches(self):
@@ -210,10 +211,14 @@ class Problem:
         return xy
 
     def set_source(self, f_qp, gD_qp=None):
+        """f_qp: [N, n_qp] (one source) or [nrhs, N, n_qp]; gD_qp likewise ([4n, n_bqp] or
+        [nrhs, 4n, n_bqp]) or None."""
         f_qp = f_qp.to(self.device, torch.float64).contiguous()
+        nrhs = 1 if f_qp.dim() == 2 else f_qp.shape[0]
         gD_qp = None if gD_qp is None else gD_qp.to(self.device, torch.float64).contiguous()
         self._src = (f_qp, gD_qp)       # keep alive until condense / recover
-        self._check(self.lib.hdg_set_source(self.h, _ptr(f_qp), _ptr(gD_qp), 1))
+        self.nrhs = nrhs
+        self._check(self.lib.hdg_set_source(self.h, _ptr(f_qp), _ptr(gD_qp), nrhs))
 
     def condense(self, store_fp32=False, keep_factors=True, store_df64=False, split_update=False):
         flags = ((HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
@@ -222,23 +227,30 @@ class Problem:
         self.version += 1
 
     def rhs(self):
-        g = self._f64(self.info["N_tr"])
+        """[N_tr], or [nrhs, N_tr] for several sources."""
+        nrhs = getattr(self, "nrhs", 1)
+        g = self._f64(self.info["N_tr"]) if nrhs == 1 else self._f64(nrhs, self.info["N_tr"])
         self._check(self.lib.hdg_rhs(self.h, _ptr(g)))
         return g
 
     def apply(self, x, precond=False, prec=64, out=None):
+        """x: [N_tr] or [nrhs, N_tr] (multi-RHS apply)."""
         dt = torch.float32 if prec == 32 else torch.float64
         x = x.to(self.device, dt).contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
         y = out if out is not None else torch.empty_like(x)
-        self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), 1, prec, 1 if precond else 0))
+        self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), nrhs, prec, 1 if precond else 0))
         return y
 
     def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0):
+        """g: [N_tr], or [nrhs, N_tr] (independent systems solved in lockstep: one multi-RHS
+        apply and batched vector kernels per Arnoldi step; the report is the worst column's)."""
         g = g.to(self.device, torch.float64).contiguous()
+        nrhs = 1 if g.dim() == 1 else g.shape[0]
         x = torch.zeros_like(g) if x0 is None else x0.to(self.device, torch.float64).clone()
         o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
         r = SolveReport()
-        st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), 1, ctypes.byref(o), ctypes.byref(r))
+        st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), nrhs, ctypes.byref(o), ctypes.byref(r))
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
             self._check(st)
         return x, r.as_dict(), st
@@ -252,10 +264,14 @@ class Problem:
         return r.as_dict()
 
     def recover(self, x):
+        """x: [N_tr] -> u [N, Q], q [N, 2, Q]; or [nrhs, N_tr] -> [nrhs, ...]."""
         x = x.to(self.device, torch.float64).contiguous()
-        u = self._f64(self.info["N"], self.info["Q"])
-        q = self._f64(self.info["N"], 2, self.info["Q"])
-        self._check(self.lib.hdg_recover(self.h, _ptr(x), _ptr(u), _ptr(q), 1))
+        N, Q = self.info["N"], self.info["Q"]
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        lead = () if x.dim() == 1 else (nrhs,)
+        u = self._f64(*lead, N, Q)
+        q = self._f64(*lead, N, 2, Q)
+        self._check(self.lib.hdg_recover(self.h, _ptr(x), _ptr(u), _ptr(q), nrhs))
         return u, q
 
     def schur(self, e0=0, count=None):

@@ -199,6 +199,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   P.bx = d->beta[0]; P.by = d->beta[1]; P.babs = std::hypot(d->beta[0], d->beta[1]);
   P.kappa0 = d->kappa0; P.tau_len = d->tau_len;
   P.R = T.Q + T.n_t;
+  P.nrhs = 1;
   P.Cc = T.Q + T.n_t + 1;
   P.ld = (int)round_up(P.Cc, 4);
   *out = c;
@@ -214,6 +215,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if ((e = dev_alloc(c, &c->d_ghat, (size_t)P.n_bnd * P.P1)) != cudaSuccess) return cuda_err(c, e, "ghat");
   if ((e = cudaMemsetAsync(c->d_ghat, 0, (size_t)P.n_bnd * P.P1 * 8, c->stream)) != cudaSuccess)
     return cuda_err(c, e, "ghat");
+  c->alloc_nrhs = 1;
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_err(c, e, "create");
   return HDG_OK;
 }
@@ -251,16 +253,33 @@ hdg_status hdg_bnd_quad_points(const hdg_ctx* cc, double* xy) {
 hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, int nrhs) {
   if (!c) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
-  if (!f_qp || nrhs != 1) return set_err(c, HDG_ERR_ARG, "f_qp must be a device pointer and nrhs must be 1");
+  if (!f_qp || nrhs < 1 || nrhs > HDG_MAX_RHS)
+    return set_err(c, HDG_ERR_ARG, "f_qp must be a device pointer and 1 <= nrhs <= HDG_MAX_RHS");
+  Params& P = c->prm;
+  cudaError_t e = cudaSuccess;
+  if (nrhs != c->alloc_nrhs) {
+    // per-RHS buffers follow the number of right-hand sides
+    dev_free(c, c->d_ghat, (size_t)c->alloc_nrhs * P.n_bnd * P.P1);
+    dev_free(c, c->d_gel, (size_t)c->alloc_nrhs * P.N * P.n_t);
+    dev_free(c, c->d_g, (size_t)c->alloc_nrhs * P.N_tr);
+    c->alloc_nrhs = 0;
+    if ((e = dev_alloc(c, &c->d_ghat, (size_t)nrhs * P.n_bnd * P.P1)) != cudaSuccess) return cuda_err(c, e, "ghat");
+    c->alloc_nrhs = nrhs;
+  }
+  P.nrhs = nrhs;
+  P.Cc = P.Q + P.n_t + nrhs;
+  P.ld = (int)round_up(P.Cc, 4);
   c->f_qp = f_qp;
   c->gD_qp = gD_qp;
-  cudaError_t e;
   if (gD_qp) {
-    e = launch_project_dirichlet(c->prm, c->dt, gD_qp, c->d_ghat, c->stream);
-    c->launches += 1;
+    for (int r = 0; r < nrhs && e == cudaSuccess; ++r) {
+      e = launch_project_dirichlet(P, c->dt, gD_qp + (size_t)r * P.n_bnd * P.n_bqp, c->d_ghat + (size_t)r * P.n_bnd * P.P1,
+                                   c->stream);
+      c->launches += 1;
+    }
   }
   else {
-    e = cudaMemsetAsync(c->d_ghat, 0, (size_t)c->prm.n_bnd * c->prm.P1 * 8, c->stream);
+    e = cudaMemsetAsync(c->d_ghat, 0, (size_t)nrhs * P.n_bnd * P.P1 * 8, c->stream);
   }
   if (e != cudaSuccess) return cuda_err(c, e, "hdg_set_source");
   c->state = 1;
@@ -284,18 +303,19 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if ((flags & HDG_STORE_DF64) && !c->d_Stdf && (e = dev_alloc(c, &c->d_Stdf, sblk)) != cudaSuccess)
     return cuda_err(c, e, "split-FP32 S blocks");
   if (!(flags & HDG_STORE_DF64)) dev_free(c, c->d_Stdf, sblk);
-  if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
-  if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
+  if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.nrhs * P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
+  if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.nrhs * P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
   if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
   const size_t slot = (size_t)P.R * P.ld;
   // without HDG_KEEP_FACTORS the elements are condensed in chunks that fit a 1 GiB workspace
   const int64_t budget_slots = std::max<int64_t>(1, (int64_t)((size_t(1) << 30) / (slot * sizeof(double))));
   const int64_t want = (flags & HDG_KEEP_FACTORS) ? P.N : std::min<int64_t>(P.N, budget_slots);
-  if (c->ws_slots != want) {
-    dev_free(c, c->d_ws, (size_t)c->ws_slots * slot);
+  if (c->ws_slots != want || c->ws_ld != P.ld) {
+    dev_free(c, c->d_ws, (size_t)c->ws_slots * P.R * c->ws_ld);
     c->ws_slots = 0;
     if ((e = dev_alloc(c, &c->d_ws, (size_t)want * slot)) != cudaSuccess) return cuda_err(c, e, "local workspace");
     c->ws_slots = want;
+    c->ws_ld = P.ld;
   }
   const int keep = (flags & HDG_KEEP_FACTORS) ? 1 : 0;
   if (keep && !c->d_piv && (e = dev_alloc(c, &c->d_piv, (size_t)P.N * P.Q)) != cudaSuccess)
@@ -319,8 +339,12 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     if ((e = launch_split_df(c->d_St, c->d_Stdf, (int64_t)sblk, c->stream)) != cudaSuccess)
       return cuda_err(c, e, "split");
   }
-  c->launches += 1;
-  if ((e = launch_assemble_rhs(P, c->d_gel, c->d_g, c->stream)) != cudaSuccess) return cuda_err(c, e, "rhs");
+  for (int r = 0; r < P.nrhs; ++r) {
+    c->launches += 1;
+    if ((e = launch_assemble_rhs(P, c->d_gel + (size_t)r * P.N * P.n_t, c->d_g + (size_t)r * P.N_tr, c->stream)) !=
+        cudaSuccess)
+      return cuda_err(c, e, "rhs");
+  }
   std::vector<int> info(P.N);
   if ((e = cudaMemcpyAsync(info.data(), c->d_info, (size_t)P.N * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
     return cuda_err(c, e, "info");
@@ -339,16 +363,35 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
 hdg_status hdg_rhs(hdg_ctx* c, double* g) {
   if (!c || !g) return HDG_ERR_ARG;
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_rhs before hdg_condense");
-  cudaError_t e = cudaMemcpyAsync(g, c->d_g, (size_t)c->prm.N_tr * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(g, c->d_g, (size_t)c->prm.nrhs * c->prm.N_tr * 8, cudaMemcpyDeviceToDevice,
+                                  c->stream);
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_rhs");
 }
 
 hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int precond) {
   if (!c) return HDG_ERR_ARG;
-  if (!x || !y || x == y || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad x/y or nrhs");
+  if (!x || !y || x == y || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad x/y or nrhs");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
   cudaError_t e;
   ProfScope ps(c, prec == 32 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY);
+  if (nrhs > 1) {
+    // multi-RHS apply: every block streamed once for all columns
+    const Params& P = c->prm;
+    if (prec == 64) {
+      e = launch_apply_mrhs(0, 0, P, precond ? c->d_St : c->d_S, x, y, nrhs, P.N_tr, precond ? c->d_escale : nullptr,
+                            c->stream);
+    } else if (prec == 48) {
+      if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
+      e = launch_apply_mrhs(1, 0, P, c->d_Stdf, x, y, nrhs, P.N_tr, c->d_escale, c->stream);
+    } else if (prec == 32) {
+      if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
+      e = launch_apply_mrhs(2, 2, P, c->d_St32, x, y, nrhs, P.N_tr, c->d_escale, c->stream);
+    } else {
+      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
+    }
+    c->launches += 1;
+    return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply (multi-RHS)");
+  }
   if (prec == 64) {
     e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream)
                 : launch_apply64(c->prm, c->d_S, (const double*)x, (double*)y, nullptr, nullptr, c->stream);
@@ -368,7 +411,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
 hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg_solve_opts* o,
                      hdg_solve_report* rep) {
   if (!c) return HDG_ERR_ARG;
-  if (!g || !x || !o || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
       o->orth < 0 || o->orth > 1)
@@ -377,7 +420,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)
   if (o->mode == 2 && !c->d_Stdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
   hdg_solve_report r{};
-  const hdg_status s = gmres_solve(c, g, x, *o, r);
+  const hdg_status s = nrhs == 1 ? gmres_solve(c, g, x, *o, r) : gmres_solve_batched(c, g, x, nrhs, *o, r);
   if (rep) *rep = r;
   return s;
 }
@@ -396,25 +439,37 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
 
 hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nrhs) {
   if (!c) return HDG_ERR_ARG;
-  if (!x || !u || !q || nrhs != 1) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (!x || !u || !q) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_recover before hdg_condense");
   const Params& P = c->prm;
-  const double* gh = c->gD_qp ? c->d_ghat : nullptr;
+  if (nrhs != P.nrhs) return set_err(c, HDG_ERR_ARG, "nrhs must equal the nrhs of hdg_set_source");
   cudaError_t e;
+  // column r: x_r, g^_r, u_r, q_r at r * (one RHS) offsets
+  auto rec = [&](int64_t e0, int64_t cnt, int slot_is_element, int r) {
+    return launch_recover(P, c->dt, c->d_ws, e0, cnt, slot_is_element, x + (size_t)r * P.N_tr,
+                          c->gD_qp ? c->d_ghat + (size_t)r * P.n_bnd * P.P1 : nullptr, u + (size_t)r * P.N * P.Q,
+                          q + (size_t)r * P.N * 2 * P.Q, c->stream, r);
+  };
   if (c->flags & HDG_KEEP_FACTORS) {
     ProfScope ps(c, HDG_PROF_RECOVER);
-    e = launch_recover(P, c->dt, c->d_ws, 0, P.N, 1, x, gh, u, q, c->stream);
-    c->launches += 1;
-    if (e != cudaSuccess) return cuda_err(c, e, "recover");
+    for (int r = 0; r < nrhs; ++r) {
+      e = rec(0, P.N, 1, r);
+      c->launches += 1;
+      if (e != cudaSuccess) return cuda_err(c, e, "recover");
+    }
   } else {
+    const double* gh = c->gD_qp ? c->d_ghat : nullptr;
     for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
       const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
       e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, 0, 0, nullptr, nullptr, nullptr,
                           nullptr, nullptr, c->stream, (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
       if (e != cudaSuccess) return cuda_err(c, e, "refactor");
-      e = launch_recover(P, c->dt, c->d_ws, e0, cnt, 0, x, gh, u, q, c->stream);
-      c->launches += 2;
-      if (e != cudaSuccess) return cuda_err(c, e, "recover");
+      c->launches += 1;
+      for (int r = 0; r < nrhs; ++r) {
+        e = rec(e0, cnt, 0, r);
+        c->launches += 1;
+        if (e != cudaSuccess) return cuda_err(c, e, "recover");
+      }
     }
   }
   return HDG_OK;
@@ -581,6 +636,8 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
+  cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb);
   if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
   for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -1,0 +1,171 @@
+// Multi-RHS trace-operator apply (Sec. 3.3.2, steps 1-4, for nrhs vectors at
+// once): Y_r = S X_r (or D^-1 S X_r) for r = 0 .. nrhs-1, every Schur block
+// streamed from HBM once for all columns.
+//
+// One CTA per interior edge f. Its two element sides' trace values of all
+// columns are gathered into shared memory (rows of the columns padded to a
+// multiple of RPT, plus one against bank conflicts); thread (t, g) owns edge
+// dof t and the RPT columns
+// g RPT .. g RPT + RPT - 1, and accumulates
+//     y_r(t) = sum_side sum_j S_side(t_side, j) x_side,r(j)
+// over both sides in a fixed order (bitwise reproducible). Block types BT:
+// 0 FP64, 1 split-FP32 pairs, 2 FP32; vector types VT: 0 FP64, 1 split-FP32
+// pairs, 2 FP32. FP64 blocks with FP64 vectors use FP64 arithmetic, FP32
+// blocks with FP32 vectors FP32 arithmetic, every other pairing split-FP32
+// arithmetic.
+#include "internal.h"
+#include "df64.h"
+
+namespace mehdg {
+
+constexpr int RPT = 8;   // columns per thread
+
+// shared-memory row length for nrhs columns
+__host__ __device__ __forceinline__ int mrhs_row(int nrhs) { return (nrhs + RPT - 1) / RPT * RPT + 1; }
+
+template <int BT, int VT>
+struct MrhsTypes {
+  static constexpr bool f64 = (BT == 0 && VT == 0);
+  static constexpr bool f32 = (BT == 2 && VT == 2);
+  using Acc = typename std::conditional<f64, double, typename std::conditional<f32, float, float2>::type>::type;
+};
+
+template <int VT>
+__device__ __forceinline__ float2 load_split(const void* x, size_t i) {
+  if constexpr (VT == 0) return df_from(static_cast<const double*>(x)[i]);
+  else if constexpr (VT == 1) return static_cast<const float2*>(x)[i];
+  else return make_float2(static_cast<const float*>(x)[i], 0.f);
+}
+
+template <int BT>
+__device__ __forceinline__ float2 block_split(const void* S, size_t i) {
+  if constexpr (BT == 0) return df_from(static_cast<const double*>(S)[i]);
+  else if constexpr (BT == 1) return static_cast<const float2*>(S)[i];
+  else return make_float2(static_cast<const float*>(S)[i], 0.f);
+}
+
+template <int BT, int VT>
+__global__ void __launch_bounds__(544) apply_mrhs_kernel(Params P, const void* __restrict__ Sv,
+                                                         const void* __restrict__ xv, void* __restrict__ yv,
+                                                         int nrhs, int64_t vstride,
+                                                         const double* __restrict__ escale) {
+  using T = MrhsTypes<BT, VT>;
+  using Acc = typename T::Acc;
+  extern __shared__ unsigned char sraw[];
+  // [2 n_t][NR1]: columns padded to a multiple of RPT (zeros), plus one against
+  // bank conflicts, so that a thread's RPT reads stay inside its row
+  Acc* xs = reinterpret_cast<Acc*>(sraw);
+  const int nt = P.n_t, P1 = P.P1, PP = P.P, NR1 = mrhs_row(nrhs);
+  const int f = blockIdx.x;
+  const int tid = threadIdx.x;
+  int e[2], k[2], fl[2];
+  double len;
+  edge_sides(f, P.n, e, k, fl, &len);
+  // gather: consecutive threads take consecutive local dofs of one column
+  for (int idx = tid; idx < 2 * nt * (NR1 - 1); idx += blockDim.x) {
+    const int r = idx / (2 * nt), q = idx - r * 2 * nt;
+    const int sd = q / nt, c = q - sd * nt;
+    int code[3], flip[3];
+    elem_edges(e[sd], P.n, code, flip);
+    const int kk = c / P1, t = c - kk * P1;
+    Acc v;
+    if (r < nrhs && code[kk] >= 0) {
+      const size_t gi = (size_t)r * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t);
+      if constexpr (T::f64) v = static_cast<const double*>(xv)[gi];
+      else if constexpr (T::f32) v = static_cast<const float*>(xv)[gi];
+      else v = load_split<VT>(xv, gi);
+    } else {
+      if constexpr (T::f64 || T::f32) v = 0;
+      else v = make_float2(0.f, 0.f);
+    }
+    xs[q * NR1 + r] = v;
+  }
+  __syncthreads();
+  const int s = tid % P1, grp = tid / P1;
+  const int r0 = grp * RPT;
+  if (r0 >= nrhs) return;
+  const int t0 = fl[0] ? PP - s : s, t1 = fl[1] ? PP - s : s;
+  const size_t base0 = ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
+  const size_t base1 = ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1;
+  Acc acc[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    if constexpr (T::f64 || T::f32) acc[u] = 0;
+    else acc[u] = make_float2(0.f, 0.f);
+  }
+  for (int q = 0; q < 2 * nt; ++q) {
+    const size_t bi = (q < nt ? base0 + (size_t)q * P1 : base1 + (size_t)(q - nt) * P1);
+    const Acc* xr = xs + q * NR1 + r0;
+    if constexpr (T::f64) {
+      const double b = static_cast<const double*>(Sv)[bi];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = fma(b, xr[u], acc[u]);
+    } else if constexpr (T::f32) {
+      const float b = static_cast<const float*>(Sv)[bi];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = fmaf(b, xr[u], acc[u]);
+    } else {
+      const float2 b = block_split<BT>(Sv, bi);
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) df_fma(acc[u].x, acc[u].y, b, xr[u]);
+    }
+  }
+  const size_t oi = (size_t)f * P1 + s;
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int r = r0 + u;
+    if (r >= nrhs) break;
+    const size_t yo = (size_t)r * vstride + oi;
+    if constexpr (T::f64) {
+      double v = acc[u];
+      if (escale) v *= escale[f];
+      static_cast<double*>(yv)[yo] = v;
+    } else if constexpr (T::f32) {
+      float v = acc[u];
+      if (escale) v = (float)((double)v * escale[f]);
+      static_cast<float*>(yv)[yo] = v;
+    } else {
+      float h = acc[u].x, l = acc[u].y;
+      if (escale) {
+        float ph = 0.f, pl = 0.f;
+        df_fma(ph, pl, df_norm(h, l), df_from(escale[f]));
+        h = ph;
+        l = pl;
+      }
+      const float2 o = df_norm(h, l);
+      if constexpr (VT == 0) static_cast<double*>(yv)[yo] = df_to(o);
+      else if constexpr (VT == 1) static_cast<float2*>(yv)[yo] = o;
+      else static_cast<float*>(yv)[yo] = o.x + o.y;
+    }
+  }
+}
+
+template <int BT, int VT>
+static cudaError_t launch_mrhs_t(const Params& P, const void* S, const void* x, void* y, int nrhs, int64_t vstride,
+                                 const double* escale, cudaStream_t st) {
+  using Acc = typename MrhsTypes<BT, VT>::Acc;
+  const int groups = (nrhs + RPT - 1) / RPT;
+  const int threads = (P.P1 * groups + 31) / 32 * 32;
+  const size_t sm = (size_t)2 * P.n_t * mrhs_row(nrhs) * sizeof(Acc);
+  if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t err = cudaFuncSetAttribute(apply_mrhs_kernel<BT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+  if (err != cudaSuccess) return err;
+  apply_mrhs_kernel<BT, VT><<<P.n_int, threads, sm, st>>>(P, S, x, y, nrhs, vstride, escale);
+  return cudaGetLastError();
+}
+
+// bt: 0 FP64 blocks, 1 split-FP32 blocks, 2 FP32 blocks; vt: 0 FP64, 1 split, 2 FP32 vectors.
+cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
+                              int64_t vstride, const double* escale, cudaStream_t st) {
+  if (nrhs < 1 || nrhs > HDG_MAX_RHS || P.P1 * ((nrhs + RPT - 1) / RPT) > 544) return cudaErrorInvalidValue;
+  if (bt == 0 && vt == 0) return launch_mrhs_t<0, 0>(P, S, x, y, nrhs, vstride, escale, st);
+  if (bt == 1 && vt == 0) return launch_mrhs_t<1, 0>(P, S, x, y, nrhs, vstride, escale, st);
+  if (bt == 2 && vt == 2) return launch_mrhs_t<2, 2>(P, S, x, y, nrhs, vstride, escale, st);
+  if (bt == 0 && vt == 1) return launch_mrhs_t<0, 1>(P, S, x, y, nrhs, vstride, escale, st);
+  if (bt == 1 && vt == 1) return launch_mrhs_t<1, 1>(P, S, x, y, nrhs, vstride, escale, st);
+  if (bt == 2 && vt == 1) return launch_mrhs_t<2, 1>(P, S, x, y, nrhs, vstride, escale, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mehdg

@@ -54,6 +54,34 @@ struct CondArgs {
 
 __device__ void condense_outputs(const CondArgs& a, const double* W, int e);
 
+// The load columns of element e, one source at a time: per sub-triangle
+// projections of f_r (FP64, in proj: nsub * nloc doubles of shared memory)
+// summed over the sub-triangles that share a lattice node, times
+// detJ / m^2; put(i, r, value) stores row i of column r. Block-wide; ends
+// with a barrier.
+template <typename Put>
+__device__ void load_columns(const CondArgs& a, int e, double detJ, double* proj, Put put) {
+  const Params& P = a.prm;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const double scale = detJ / (double)(P.m * P.m);
+  for (int r = 0; r < P.nrhs; ++r) {
+    const double* fe = a.f_qp + ((size_t)r * P.N + e) * P.n_qp;
+    for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
+      const int s = idx / P.nloc, b = idx - s * P.nloc;
+      double acc = 0.0;
+      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
+      proj[idx] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < P.Q; i += nthr) {
+      double acc = 0.0;
+      for (int q = a.dt.ns_ptr[i]; q < a.dt.ns_ptr[i + 1]; ++q) acc += proj[a.dt.ns_idx[q]];
+      put(i, r, acc * scale);
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   for (int off = 16; off > 0; off >>= 1) {
     const double ov = __shfl_down_sync(0xffffffffu, v, off);
@@ -95,18 +123,6 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
   }
   const double cK = kap * g.detJ;
 
-  // source: per sub-triangle projections into Ls (free before the LU starts)
-  double* proj = Ls;
-  {
-    const double* fe = a.f_qp + (size_t)e * P.n_qp;
-    for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
-      const int s = idx / P.nloc, b = idx - s * P.nloc;
-      double acc = 0.0;
-      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
-      proj[idx] = acc;
-    }
-  }
-  __syncthreads();
 
   // --------------------------------------------------- form the bordered system
   for (int i = 0; i < R; ++i) {
@@ -122,12 +138,8 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
           const int c = j - Q, k = c / P1;
           const size_t ic = (size_t)i * nt + c;
           v = g.L[k] * ((bn[k] - tau) * a.dt.Fh[ic] - kap * (nxi[k] * a.dt.Pxi[ic] + neta[k] * a.dt.Peta[ic]));
-        } else if (j == Q + nt) {
-          double acc = 0.0;
-          for (int q = a.dt.ns_ptr[i]; q < a.dt.ns_ptr[i + 1]; ++q) acc += proj[a.dt.ns_idx[q]];
-          v = acc * g.detJ / (double)(P.m * P.m);
         } else {
-          v = 0.0;
+          v = 0.0;   // load columns: formed below
         }
         row[j] = v;
       }
@@ -151,6 +163,9 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
   }
   __syncthreads();
+  // load columns Q + n_t + r: per sub-triangle projections of source r (in
+  // the panel area, free before the LU starts), summed per lattice node
+  load_columns(a, e, g.detJ, Ls, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = v; });
   // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
   for (int k = 0; k < 3; ++k) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {
@@ -312,20 +327,22 @@ __device__ void condense_outputs(const CondArgs& a, const double* W, int e) {
     a.St[o] = acc;
     if (a.St32) a.St32[o] = (float)acc;
   }
-  // element right-hand side -C A^-1 R - S_e g^_e
+  // element right-hand sides -C A^-1 R_r - S_e g^_e,r of every source r
   int code[3], flip[3];
   elem_edges(e, P.n, code, flip);
-  for (int r = tid; r < nt; r += nthr) {
-    double acc = W[(size_t)(Q + r) * ld + Q + nt];
+  for (int idx = tid; idx < P.nrhs * nt; idx += nthr) {
+    const int rr = idx / nt, r = idx - rr * nt;
+    double acc = W[(size_t)(Q + r) * ld + Q + nt + rr];
     if (a.ghat) {
+      const double* ghr = a.ghat + (size_t)rr * P.n_bnd * P1;
       for (int k = 0; k < 3; ++k) {
         if (code[k] >= 0) continue;
-        const double* gb = a.ghat + (size_t)(-1 - code[k]) * P1;
+        const double* gb = ghr + (size_t)(-1 - code[k]) * P1;
         for (int t = 0; t < P1; ++t)
           acc -= W[(size_t)(Q + r) * ld + Q + k * P1 + t] * gb[flip[k] ? P.P - t : t];
       }
     }
-    a.gel[(size_t)e * nt + r] = acc;
+    a.gel[((size_t)rr * P.N + e) * nt + r] = acc;
   }
 }
 
@@ -403,17 +420,6 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
       }
     }
   }
-  // source: per sub-triangle projections (FP64) in the panel area
-  double* proj = smem;
-  {
-    const double* fe = a.f_qp + (size_t)e * P.n_qp;
-    for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
-      const int s2 = idx / P.nloc, b = idx - s2 * P.nloc;
-      double acc = 0.0;
-      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s2 * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
-      proj[idx] = acc;
-    }
-  }
   __syncthreads();
 
   // --------------------------------------------------- form the bordered system
@@ -436,12 +442,6 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
         df_fma(h, l, sc[5 + k], a.dt.Fh2[ic]);
         df_fma(h, l, df_neg(sc[8 + k]), a.dt.Pxi2[ic]);
         df_fma(h, l, df_neg(sc[11 + k]), a.dt.Peta2[ic]);
-      } else if (j == Q + nt) {
-        double acc = 0.0;
-        for (int q = a.dt.ns_ptr[i]; q < a.dt.ns_ptr[i + 1]; ++q) acc += proj[a.dt.ns_idx[q]];
-        const float2 v = df_from(acc * g.detJ / (double)(P.m * P.m));
-        h = v.x;
-        l = v.y;
       }
     } else {
       const int r = i - Q, k = r / P1, t = r - k * P1;
@@ -460,6 +460,8 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
     W[idx] = df_norm(h, l);
   }
   __syncthreads();
+  // load columns (FP64 projections in the panel area, stored split)
+  load_columns(a, e, g.detJ, smem, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = df_from(v); });
   // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
   for (int k = 0; k < 3; ++k) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {
@@ -639,6 +641,7 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
 struct RecArgs {
   Params prm;
   DevTables dt;
+  int rcol;               // which source's load column (0 .. nrhs-1)
   const double* ws;
   int64_t e0;
   int slot_is_element;
@@ -677,7 +680,7 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
     double acc = 0.0;
     for (int c = lane; c < nt; c += 32) acc += row[c] * xe[c];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (lane == 0) rhs[i] = row[nt] - acc;
+    if (lane == 0) rhs[i] = row[nt + a.rcol] - acc;
   }
   __syncthreads();
   // back substitution by warp 0
@@ -793,9 +796,9 @@ cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* 
 
 cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
                            int slot_is_element, const double* x, const double* ghat, double* u, double* q,
-                           cudaStream_t st) {
+                           cudaStream_t st, int rcol) {
   RecArgs a;
-  a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element;
+  a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element; a.rcol = rcol;
   a.x = x; a.ghat = ghat; a.u = u; a.q = q;
   const size_t sm = (size_t)(P.n_t + 2 * P.Q) * sizeof(double);
   recover_kernel<<<(unsigned)count, 128, sm, st>>>(a);

@@ -63,6 +63,7 @@ struct Params {
   int ng, nqs, nloc, nsub, n_qp, ngb, n_bqp;
   double bx, by, babs, kappa0, tau_len;
   int R, Cc, ld;         // bordered local system: rows, used columns, leading dimension
+  int nrhs;              // right-hand sides (source columns of the bordered system)
 };
 
 // ---------------------------------------------------------------------------
@@ -183,6 +184,8 @@ struct hdg_ctx {
   double* d_gadj = nullptr;       // [N][n_t] element parts of the adjoint right-hand side
   int* d_bad = nullptr;           // invalid-kappa counter of hdg_set_kappa
   int transposed = 0;             // 1 while the stored blocks hold S_e^T (hdg_transpose)
+  int alloc_nrhs = 0;             // right-hand sides the per-RHS buffers (ghat, gel, g) are sized for
+  int ws_ld = 0;                  // leading dimension the local workspace was allocated with
   double* d_escale = nullptr;     // [n_int] -1 / ((tau+ + tau-) L_f)
   // Krylov workspace
   float2* d_V = nullptr;          // Krylov basis, split-FP32 pairs [restart + 1][N_tr]
@@ -192,6 +195,15 @@ struct hdg_ctx {
   double* d_small = nullptr;      // Hessenberg, Givens, scalars
   int* d_flag = nullptr;
   int krylov_restart = 0;
+  // batched (several right-hand sides) Krylov workspace, sized for (restart, nrhs)
+  float2* d_Vb = nullptr;         // [restart + 1][nrhs][ldv] split-FP32 pairs
+  float2* d_wb = nullptr;         // [nrhs][ldv]
+  double* d_rb = nullptr;         // [2][nrhs][N_tr]: true residuals, then S x / D^-1 t
+  double* d_partb = nullptr;      // [nrhs][partial rows x (restart + 2)]
+  double* d_smallb = nullptr;     // [nrhs][small-array layout]
+  int* d_flagb = nullptr;         // [nrhs][4]
+  double* d_scalb = nullptr;      // [nrhs] gathered scalars
+  int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)
   int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)
   int tune_kgd = 0;               // multi-dot blocks over all vector groups

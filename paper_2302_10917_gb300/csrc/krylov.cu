@@ -18,6 +18,7 @@
 //    cycle be enqueued without host round trips (every kernel of the cycle
 //    returns at once when the flag is set);
 //  * all reductions have a fixed order: results are bitwise reproducible.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -48,6 +49,16 @@ struct SmallLayout {
   }
 };
 enum { F_STOP = 0, F_JUSED = 1 };
+
+// Strides of a batch of independent GMRES instances (several right-hand
+// sides, blockIdx.z / .y / .x selecting the instance r): offsets per r of the
+// basis, the work vector, the partial sums, the small arrays and the flags;
+// vstr separates consecutive basis vectors of one instance. One instance:
+// vstr = pairs per vector, every offset 0.
+struct Batch {
+  int64_t vstr, rv, rw, rpart, rsm;
+  int rflag;
+};
 constexpr int KGU = 1216;     // blocks of the streaming update kernel, 8 per SM
 constexpr int KGD = 1216;     // blocks (over all vector groups) of the multi-dot, 8 per SM
 constexpr int KGD_MAX = 2432; // largest multi-dot block count the autotuner tries
@@ -127,8 +138,13 @@ __device__ __forceinline__ void df_fma4(float& h, float& l, float4 a, float4 b) 
 // group of VG basis vectors. ncol = nv, or nv + 1 to append the squared norm
 // w . w as column nv. One pair per thread per iteration; four blocks per SM.
 __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
-                                                        const float4* __restrict__ w, double* part, const int* stop) {
-  if (stop && stop[F_STOP]) return;
+                                                        const float4* __restrict__ w, double* part, const int* stop,
+                                                        Batch bt) {
+  const int rb = blockIdx.z;
+  if (stop && stop[rb * bt.rflag + F_STOP]) return;
+  V += rb * bt.rv;
+  w += rb * bt.rw;
+  part += rb * bt.rpart;
   __shared__ float2 red[(KT / 32) * VG];
   const int g0 = blockIdx.y * VG;
   const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
@@ -142,7 +158,7 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
     float4 a[VG];
     const float4 wa = w[p];
 #pragma unroll
-    for (int g = 0; g < VG; ++g) a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * np + p] : (g0 + g < ncol ? wa : z4);
+    for (int g = 0; g < VG; ++g) a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * bt.vstr + p] : (g0 + g < ncol ? wa : z4);
 #pragma unroll
     for (int g = 0; g < VG; ++g) df_fma4(h[g], l[g], a[g], wa);
   }
@@ -156,7 +172,11 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 // norm follows from ||x - V s||^2 = ||x||^2 - ||s||^2 (orthonormal V). Then
 // the Givens rotations. One block.
 __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part, int G, int nv, double* sm,
-                                                               SmallLayout L, int* flags, int j, int add) {
+                                                               SmallLayout L, int* flags, int j, int add, Batch bt) {
+  const int rb = blockIdx.x;
+  part += rb * bt.rpart;
+  sm += rb * bt.rsm;
+  flags += rb * bt.rflag;
   if (flags[F_STOP]) return;
   __shared__ double vals[136];
   __shared__ double red[32];
@@ -241,8 +261,14 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
 __global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict__ V, int64_t np, int nv,
                                                        const double* __restrict__ coef, const float4* w,
                                                        const double* sm, int scale_off, float4* out,
-                                                       const int* stop) {
-  if (stop && stop[F_STOP]) return;
+                                                       const int* stop, Batch bt, int64_t rout) {
+  const int rb = blockIdx.y;
+  if (stop && stop[rb * bt.rflag + F_STOP]) return;
+  V += rb * bt.rv;
+  coef += rb * bt.rsm;
+  w += rb * bt.rw;
+  if (sm) sm += rb * bt.rsm;
+  out += rb * rout;
   __shared__ float2 cf[144];
   for (int i = threadIdx.x; i < 144; i += blockDim.x) cf[i] = i < nv ? df_from(-coef[i]) : make_float2(0.f, 0.f);
   __syncthreads();
@@ -254,10 +280,10 @@ __global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict_
     float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
     float4 v[8], nx[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = u < nv ? V[(size_t)u * np + p] : z4;
+    for (int u = 0; u < 8; ++u) v[u] = u < nv ? V[(size_t)u * bt.vstr + p] : z4;
     for (int i0 = 0; i0 < nv; i0 += 8) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) nx[u] = i0 + 8 + u < nv ? V[(size_t)(i0 + 8 + u) * np + p] : z4;
+      for (int u = 0; u < 8; ++u) nx[u] = i0 + 8 + u < nv ? V[(size_t)(i0 + 8 + u) * bt.vstr + p] : z4;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         df_fma(ah, al, cf[i0 + u], make_float2(v[u].x, v[u].y));
@@ -428,12 +454,12 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 // blocks over all groups of VG vectors (at least one per SM along x), fewer
 // for short vectors. Returns the number of partial rows (blocks along x).
 static int launch_mdot(const float4* V4, int64_t np, int nv, int ncol, const float4* w4, double* part,
-                       const int* fl, cudaStream_t st, int kgd) {
+                       const int* fl, cudaStream_t st, int kgd, const Batch& bt, int nb = 1) {
   const int gy = (ncol + VG - 1) / VG;
   int64_t gx = kgd / gy > 152 ? kgd / gy : 152;
   const int64_t need = (np + KT - 1) / KT;
   if (gx > need) gx = need > 1 ? need : 1;
-  df_mdot_kernel<<<dim3((unsigned)gx, (unsigned)gy), KT, 0, st>>>(V4, np, nv, ncol, w4, part, fl);
+  df_mdot_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)nb), KT, 0, st>>>(V4, np, nv, ncol, w4, part, fl, bt);
   return (int)gx;
 }
 
@@ -450,6 +476,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   float2* V = c->d_V;
   float2* w = c->d_w;
   const int64_t ldv = n + (n & 1), np = ldv / 2;   // basis row length (even) and element pairs
+  const Batch one{np, 0, 0, 0, 0, 0};
   const float4* V4 = reinterpret_cast<const float4*>(V);
   float4* w4 = reinterpret_cast<float4*>(w);
   double* t = c->d_r;           // true residual g - S x (FP64)
@@ -530,18 +557,18 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
         // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
         // the norm from ||w'||^2 - ||h2||^2
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd);
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd, one);
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
-        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1);
+        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one);
       } else {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0);
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one);
       }
-      df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl);
+      df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     };
     const int per_step = o.orth == 0 ? 6 : 4;
@@ -631,6 +658,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   if (!cu.ok(ensure_krylov(c, K))) return fail(c, HDG_ERR_OOM, std::string("Krylov workspace: ") + cudaGetErrorString(cu.err));
   cudaStream_t st = c->stream;
   const int64_t n = P.N_tr, ldv = n + (n & 1), np = ldv / 2;
+  const Batch one{np, 0, 0, 0, 0, 0};
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
   const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
   float2* V = c->d_V;
@@ -674,7 +702,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   int best_kgd = KGD;
   double best_mdot = 1e30, def_mdot = 0.0;
   for (int kgd : {608, 1216, 2432}) {
-    const double t = time_it([&] { launch_mdot(V4, np, nv, nv + 1, w4, c->d_part, nullptr, st, kgd); });
+    const double t = time_it([&] { launch_mdot(V4, np, nv, nv + 1, w4, c->d_part, nullptr, st, kgd, one); });
     if (kgd == KGD) def_mdot = t;
     if (t < best_mdot) { best_mdot = t; best_kgd = kgd; }
   }
@@ -685,7 +713,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   for (int kgu : {608, 1216, 2432, 4864}) {
     const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
     const double t = time_it([&] {
-      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, coef, w4, nullptr, -1, out, nullptr);
+      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, coef, w4, nullptr, -1, out, nullptr, one, 0);
       cu.ok(cudaGetLastError());
     });
     if (kgu == KGU) def_upd = t;
@@ -707,6 +735,196 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   rep.update_ms = best_upd;
   rep.default_ms = def_apply + def_mdot + def_upd;
   return HDG_OK;
+}
+
+// ------------------------------------------------- batched (several RHS)
+// out[r] = sm[r * rsm + off]
+__global__ void gather_scalar_kernel(const double* sm, int64_t rsm, int off, double* out, int nb) {
+  for (int r = threadIdx.x; r < nb; r += blockDim.x) out[r] = sm[(size_t)r * rsm + off];
+}
+
+// per instance r: stop flag = done[r] (an instance that has converged sits out
+// the cycle), used-steps = 0; sm[r][off] = vals[r] when vals is not null
+__global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double* sm, int64_t rsm, int off,
+                                 const double* vals, int nb) {
+  for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+    flags[r * rflag + F_STOP] = done[r];
+    flags[r * rflag + F_JUSED] = 0;
+    if (vals) sm[(size_t)r * rsm + off] = vals[r];
+  }
+}
+
+static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
+  if (c->kb_restart == K && c->kb_nrhs == nb && c->d_Vb) return cudaSuccess;
+  cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb);
+  c->d_Vb = nullptr; c->d_wb = nullptr; c->d_rb = nullptr; c->d_partb = nullptr; c->d_smallb = nullptr;
+  c->d_flagb = nullptr; c->d_scalb = nullptr;
+  c->kb_restart = c->kb_nrhs = 0;
+  const size_t n = (size_t)c->prm.N_tr, ldv = n + (n & 1);
+  SmallLayout L(K);
+  const size_t rows = (size_t)(KG > KGD_MAX ? KG : KGD_MAX) * (K + 2);
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->d_Vb, (size_t)(K + 1) * nb * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_Vb, 0, (size_t)(K + 1) * nb * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_wb, (size_t)nb * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_wb, 0, (size_t)nb * ldv * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_rb, 2 * (size_t)nb * n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_partb, (size_t)nb * rows * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_smallb, (size_t)nb * L.total * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_flagb, (size_t)nb * 4 * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_scalb, (size_t)nb * 2 * sizeof(double))) != cudaSuccess) return e;
+  c->kb_restart = K;
+  c->kb_nrhs = nb;
+  return cudaSuccess;
+}
+
+hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, const hdg_solve_opts& o,
+                               hdg_solve_report& rep) {
+  const Params& P = c->prm;
+  const int K = o.restart;
+  const int64_t n = P.N_tr;
+  cudaStream_t st = c->stream;
+  Cu cu{c};
+  if (!cu.ok(ensure_krylov_batched(c, K, nb)))
+    return fail(c, HDG_ERR_OOM, std::string("batched Krylov workspace: ") + cudaGetErrorString(cu.err));
+  SmallLayout L(K);
+  const int64_t ldv = n + (n & 1), np = ldv / 2;
+  const int64_t rpart = (int64_t)(KG > KGD_MAX ? KG : KGD_MAX) * (K + 2);
+  const Batch bt{(int64_t)nb * np, np, np, rpart, L.total, 4};
+  float2* V = c->d_Vb;
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  float4* w4 = reinterpret_cast<float4*>(c->d_wb);
+  double* t = c->d_rb;                 // [nb][n] true residuals
+  double* r0 = c->d_rb + (size_t)nb * n;   // [nb][n] S x, then D^-1 t
+  double* part = c->d_partb;
+  double* sm = c->d_smallb;
+  int* fl = c->d_flagb;
+  double* scal = c->d_scalb;
+  const int btype = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
+  const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+  const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
+  const int kgd = c->tune_kgd > 0 ? c->tune_kgd : KGD;
+  const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
+  const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
+  rep = hdg_solve_report{};
+  std::vector<double> host(nb), gnorm(nb), rel(nb, 1.0);
+  std::vector<int> done(nb, 0), its(nb, 0), hfl(4 * nb);
+  int* d_done = reinterpret_cast<int*>(scal + nb);   // [nb] converged flags (device copy)
+  auto norms = [&](const double* vec, int64_t stride, double a, const double* y2, double bcoef, double* outv) {
+    for (int r = 0; r < nb; ++r) {
+      axpby_norm_kernel<<<KG, KT, 0, st>>>(a, vec + (size_t)r * stride, bcoef, y2 ? y2 + (size_t)r * stride : vec,
+                                           outv + (size_t)r * stride, n, part + (size_t)r * rpart);
+      sum_partials_kernel<<<1, 32, 0, st>>>(part + (size_t)r * rpart, KG, sm + (size_t)r * L.total + L.sc + 5);
+    }
+    gather_scalar_kernel<<<1, 64, 0, st>>>(sm, L.total, L.sc + 5, scal, nb);
+    cu.ok(cudaMemcpyAsync(host.data(), scal, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    cu.ok(cudaStreamSynchronize(st));
+    c->launches += 2 * nb + 1;
+  };
+  norms(g, n, 1.0, nullptr, 0.0, t);
+  for (int r = 0; r < nb; ++r) gnorm[r] = std::sqrt(host[r]);
+  if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
+  for (int r = 0; r < nb; ++r)
+    if (gnorm[r] == 0.0) {
+      cu.ok(cudaMemsetAsync(x + (size_t)r * n, 0, n * sizeof(double), st));
+      done[r] = 1;
+      rel[r] = 0.0;
+    }
+  while (true) {
+    // true residuals t_r = g_r - S x_r with the FP64 blocks (multi-RHS apply)
+    {
+      ProfScope ps(c, HDG_PROF_RESID);
+      cu.ok(launch_apply_mrhs(0, 0, P, c->d_S, x, r0, nb, n, nullptr, st));
+      c->launches += 1;
+    }
+    norms(g, n, 1.0, r0, -1.0, t);
+    if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
+    rep.outer += 1;
+    int left = 0, maxits = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (gnorm[r] > 0.0) rel[r] = std::sqrt(host[r]) / gnorm[r];
+      if (rel[r] <= o.tol) done[r] = 1;
+      if (!done[r]) ++left;
+      maxits = std::max(maxits, its[r]);
+    }
+    rep.iterations = maxits;
+    rep.rel_residual = *std::max_element(rel.begin(), rel.end());
+    if (left == 0) {
+      rep.converged = 1;
+      return HDG_OK;
+    }
+    if (maxits >= o.maxit) break;
+    // cycle start for the instances still running: r0 = D^-1 t, V_0 = r0 / ||r0||
+    std::vector<double> factor(nb, 0.0);
+    for (int r = 0; r < nb; ++r) factor[r] = done[r] ? 1.0 : 0.5 * o.tol / rel[r];
+    cu.ok(cudaMemcpyAsync(scal, factor.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    cu.ok(cudaMemcpyAsync(d_done, done.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    set_cycle_kernel<<<1, 64, 0, st>>>(fl, 4, d_done, sm, L.total, L.sc + 2, scal, nb);
+    c->launches += 1;
+    for (int r = 0; r < nb; ++r) {
+      if (done[r]) continue;
+      double* tr = t + (size_t)r * n;
+      double* rr = r0 + (size_t)r * n;
+      double* smr = sm + (size_t)r * L.total;
+      int* flr = fl + 4 * r;
+      double* pr = part + (size_t)r * rpart;
+      cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, tr, rr, st));
+      axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, rr, 0.0, rr, rr, n, pr);
+      cycle_init_kernel<<<1, 256, 0, st>>>(smr, L, flr, pr, KG);
+      to_df_kernel<<<KG, KT, 0, st>>>(rr, smr, L.sc + 4, V + (size_t)r * ldv, n, flr);
+      c->launches += 4;
+    }
+    const int jmax = std::min(K, o.maxit - maxits);
+    for (int j = 0; j < jmax; ++j) {
+      const int nv = j + 1;
+      {
+        ProfScope ps(c, phase);
+        cu.ok(launch_apply_mrhs(btype, 1, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale, st));
+      }
+      ProfScope po(c, HDG_PROF_ORTHO);
+      float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * nb * ldv);
+      if (o.orth == 0) {
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, st, kgd, bt, nb);
+        for (int r = 0; r < nb; ++r)
+          mdot_reduce_kernel<<<nv, 128, 0, st>>>(part + (size_t)r * rpart, G, nv, nv,
+                                                 sm + (size_t)r * L.total + L.H + (size_t)j * (K + 1),
+                                                 sm + (size_t)r * L.total + L.htmp, 0, fl + 4 * r, nullptr);
+        df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, bt, np);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt);
+        c->launches += 4 + nb;
+      } else {
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt);
+        c->launches += 2;
+      }
+      df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, bt, np);
+      c->launches += 2;
+    }
+    cu.ok(cudaGetLastError());
+    cu.ok(cudaMemcpyAsync(hfl.data(), fl, 4 * nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    cu.ok(cudaStreamSynchronize(st));
+    if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
+    rep.restarts += 1;
+    int any = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (done[r]) continue;
+      const int jused = hfl[4 * r + F_JUSED];
+      its[r] += jused;
+      if (jused == 0) continue;
+      any = 1;
+      double* smr = sm + (size_t)r * L.total;
+      lsq_kernel<<<1, 32, 0, st>>>(smr, L, fl + 4 * r);
+      df_xupdate_kernel<<<KG, KT, 0, st>>>(V + (size_t)r * ldv, n, (int64_t)nb * ldv, jused, smr + L.y,
+                                           x + (size_t)r * n);
+      c->launches += 2;
+    }
+    if (!any) break;
+  }
+  rep.converged = 0;
+  return fail(c, HDG_ERR_NOCONV, "batched GMRES reached maxit with largest relative residual " +
+                                     std::to_string(rep.rel_residual));
 }
 
 }  // namespace mehdg

@@ -11,7 +11,7 @@ cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* 
                             cudaStream_t st, int split_update = 0, int* piv = nullptr);
 cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* ws, int64_t e0, int64_t count,
                            int slot_is_element, const double* x, const double* ghat, double* u, double* q,
-                           cudaStream_t st);
+                           cudaStream_t st, int rcol = 0);
 cudaError_t launch_project_dirichlet(const Params& P, const DevTables& dt, const double* gD, double* ghat,
                                      cudaStream_t st);
 cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64_t count, double* out,
@@ -26,6 +26,8 @@ cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, d
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
                              const double* escale, const int* stop, cudaStream_t st, int epb = 0);
 int apply_edges_per_block(const Params& P);
+cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
+                              int64_t vstride, const double* escale, cudaStream_t st);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
@@ -45,6 +47,10 @@ cudaError_t launch_gradient(const Params& P, const DevTables& dt, const double* 
 
 // Restarted GMRES on the condensed system (krylov.cu).
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep);
+// nrhs independent instances in lockstep: one multi-RHS apply and batched
+// vector kernels per Arnoldi step (krylov.cu).
+hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg_solve_opts& o,
+                               hdg_solve_report& rep);
 // Launch-shape autotuner of the GMRES kernels (krylov.cu).
 hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep);
 
