@@ -168,4 +168,107 @@ cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, co
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Element-centric variant for split-FP32 vectors (the batched GMRES operator):
+// (A) one CTA per element: Z_e,r = S_e X_e,r for all columns r, X_e gathered
+//     once per element ([n_t][nrhs] in shared memory), Z written per element
+//     ([N][nrhs][n_t] split pairs);
+// (B) one thread per (column, edge dof): y_r(f, s) = scale_f (Z_e+,r(t+) +
+//     Z_e-,r(t-)) in a fixed order. Each element's trace values are read once
+//     (the edge-centric kernel reads them once per edge of the element).
+template <int BT>
+__global__ void __launch_bounds__(256) mrhs_element_kernel(Params P, const void* __restrict__ Sv,
+                                                           const float2* __restrict__ x, int nrhs, int64_t vstride,
+                                                           float2* __restrict__ Z) {
+  extern __shared__ float2 xs2[];            // [n_t][NR1]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P, NR1 = mrhs_row(nrhs);
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x;
+  int code[3], flip[3];
+  elem_edges(e, P.n, code, flip);
+  for (int idx = tid; idx < nt * (NR1 - 1); idx += blockDim.x) {
+    const int r = idx / nt, c = idx - r * nt;
+    const int kk = c / P1, t = c - kk * P1;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nrhs && code[kk] >= 0) v = x[(size_t)r * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+    xs2[c * NR1 + r] = v;
+  }
+  __syncthreads();
+  const int groups = (nrhs + RPT - 1) / RPT;
+  const size_t sb = (size_t)e * 3 * nt * P1;
+  for (int item = tid; item < nt * groups; item += blockDim.x) {
+    const int row = item % nt, grp = item / nt;
+    const int k = row / P1, t = row - k * P1;
+    const int r0 = grp * RPT;
+    float h[RPT], l[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) { h[u] = 0.f; l[u] = 0.f; }
+    const size_t rb = sb + (size_t)k * nt * P1 + t;     // S_e(row, c) = S[e][k][c][t]
+    for (int c = 0; c < nt; ++c) {
+      const float2 b = block_split<BT>(Sv, rb + (size_t)c * P1);
+      const float2* xr = xs2 + c * NR1 + r0;
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) df_fma(h[u], l[u], b, xr[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int r = r0 + u;
+      if (r < nrhs) Z[((size_t)e * nrhs + r) * nt + row] = df_norm(h[u], l[u]);
+    }
+  }
+}
+
+__global__ void mrhs_edge_sum_kernel(Params P, const float2* __restrict__ Z, int nrhs, int64_t vstride,
+                                     const double* __restrict__ escale, float2* __restrict__ y) {
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  const int64_t per = (int64_t)P.n_int * P1;
+  const int64_t total = per * nrhs;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / per);
+    const int64_t fs = idx - (int64_t)r * per;
+    const int f = (int)(fs / P1), s = (int)(fs - (int64_t)f * P1);
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    float h = 0.f, l = 0.f;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const int t = fl[sd] ? PP - s : s;
+      const float2 z = Z[((size_t)e[sd] * nrhs + r) * nt + k[sd] * P1 + t];
+      df_add(h, l, z.x, z.y);
+    }
+    if (escale) {
+      float ph = 0.f, pl = 0.f;
+      df_fma(ph, pl, df_norm(h, l), df_from(escale[f]));
+      h = ph;
+      l = pl;
+    }
+    y[(size_t)r * vstride + fs] = df_norm(h, l);
+  }
+}
+
+// Element-centric multi-RHS apply on split vectors; Z: [N][nrhs][n_t] pairs.
+cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
+                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st) {
+  if (nrhs < 1 || nrhs > HDG_MAX_RHS) return cudaErrorInvalidValue;
+  const size_t sm = (size_t)P.n_t * mrhs_row(nrhs) * sizeof(float2);
+  if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t err;
+  if (bt == 0) {
+    err = cudaFuncSetAttribute(mrhs_element_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err == cudaSuccess) mrhs_element_kernel<0><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+  } else if (bt == 1) {
+    err = cudaFuncSetAttribute(mrhs_element_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err == cudaSuccess) mrhs_element_kernel<1><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+  } else {
+    err = cudaFuncSetAttribute(mrhs_element_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err == cudaSuccess) mrhs_element_kernel<2><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+  }
+  if (err != cudaSuccess) return err;
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  mrhs_edge_sum_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, Z, nrhs, vstride, escale, y);
+  return cudaGetLastError();
+}
+
 }  // namespace mehdg

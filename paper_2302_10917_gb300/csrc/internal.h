@@ -203,6 +203,7 @@ struct hdg_ctx {
   double* d_smallb = nullptr;     // [nrhs][small-array layout]
   int* d_flagb = nullptr;         // [nrhs][4]
   double* d_scalb = nullptr;      // [nrhs] gathered scalars
+  float2* d_Zb = nullptr;         // [N][nrhs][n_t] element products of the multi-RHS apply
   int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)
   int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)

@@ -757,9 +757,9 @@ __global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double*
 static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if (c->kb_restart == K && c->kb_nrhs == nb && c->d_Vb) return cudaSuccess;
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
-  cudaFree(c->d_flagb); cudaFree(c->d_scalb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb);
   c->d_Vb = nullptr; c->d_wb = nullptr; c->d_rb = nullptr; c->d_partb = nullptr; c->d_smallb = nullptr;
-  c->d_flagb = nullptr; c->d_scalb = nullptr;
+  c->d_flagb = nullptr; c->d_scalb = nullptr; c->d_Zb = nullptr;
   c->kb_restart = c->kb_nrhs = 0;
   const size_t n = (size_t)c->prm.N_tr, ldv = n + (n & 1);
   SmallLayout L(K);
@@ -774,6 +774,7 @@ static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if ((e = cudaMalloc(&c->d_smallb, (size_t)nb * L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flagb, (size_t)nb * 4 * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_scalb, (size_t)nb * 2 * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_Zb, (size_t)c->prm.N * nb * c->prm.n_t * sizeof(float2))) != cudaSuccess) return e;
   c->kb_restart = K;
   c->kb_nrhs = nb;
   return cudaSuccess;
@@ -880,7 +881,9 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       const int nv = j + 1;
       {
         ProfScope ps(c, phase);
-        cu.ok(launch_apply_mrhs(btype, 1, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale, st));
+        cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale, c->d_Zb,
+                                   st));
+        c->launches += 1;
       }
       ProfScope po(c, HDG_PROF_ORTHO);
       float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * nb * ldv);

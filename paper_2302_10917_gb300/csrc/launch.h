@@ -28,6 +28,8 @@ cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float
 int apply_edges_per_block(const Params& P);
 cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
                               int64_t vstride, const double* escale, cudaStream_t st);
+cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
+                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,

@@ -19,6 +19,8 @@ CONFIGS = {
     "c1": dict(n=128, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
     "c2": dict(n=256, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
     "c4": dict(n=256, m=4, p=2, beta=(1.0, 0.5), kappa=1.0),
+    # many right-hand sides on one level (uniform stand-in of the banded-level workload)
+    "c3u": dict(n=128, m=4, p=2, beta=(1.0, 0.0), kappa=1e-2),
 }
 
 
@@ -61,6 +63,15 @@ def grf_kappa(n, seed, std=0.5, ell=0.1, features=1024):
     c[1::2, 1] = (j + 2.0 / 3.0) * h
     field = std * np.sqrt(2.0 / features) * np.cos(c @ w.T + phi[None, :]).sum(axis=1)
     return np.exp(field)
+
+
+def gaussian_bumps(xy, count, seed, width=0.05):
+    """count sources f_k(x) = exp(-|x - c_k|^2 / (2 width^2)) with seeded centres
+    c_k ~ U[0, 1]^2, evaluated at points xy[..., 2]: [count, *xy.shape[:-1]]."""
+    g = np.random.default_rng([MASTER_SEED, 59, int(seed)])
+    c = torch.from_numpy(g.uniform(0.0, 1.0, (count, 2))).to(xy.device, xy.dtype)
+    d2 = ((xy.unsqueeze(0) - c.view(count, *([1] * (xy.dim() - 1)), 2)) ** 2).sum(-1)
+    return torch.exp(-d2 / (2.0 * width * width))
 
 
 def random_vector(n, seed):
