@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-split", action="store_true", help="FP64 panel updates in the condensation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the many-source and gradient measurements that follow the main line")
     return ap.parse_args(argv)
 
 
@@ -442,13 +444,103 @@ def run_ours(args):
         line["e2e"] = {"value": eu / es / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": int(fh.numel() * 8),
                        "d2h_bytes_per_step": int((x.numel() + u.numel() + q.numel()) * 8), "seconds": e2e_s,
                        "call": "hdg_run_host (pinned host f in; x, u, q out)"}
+    pr.close()
+    del f
+    torch.cuda.synchronize()
+    if not args.no_extras:
+        line["multi_rhs"] = bench_multi_rhs(stream)
+        line["gradient"] = bench_gradient(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, int(round(applies / args.steps)))
-    pr.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_multi_rhs(stream, count=64):
+    """64 Gaussian-bump sources on one level (n=128, m=4, p=2, kappa=1e-2, beta=(1,0)):
+    one condensation with 64 load columns, the lockstep batched GMRES to 1e-10 for all
+    columns, against one single-source solve of the same problem (x count = sequential)."""
+    import torch
+    from paper_2302_10917_gb300 import Problem
+    from paper_2302_10917_gb300 import workloads as wl
+    cfg = wl.CONFIGS["c3u"]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
+    f = wl.gaussian_bumps(pr.quad_points(), count, seed=3).contiguous()
+    a, b, c2, d = ev(), ev(), ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    pr.set_source(f)
+    pr.condense(keep_factors=True, store_df64=True, split_update=True)
+    g = pr.rhs()
+    b.record(stream)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1, maxit=40000)
+    c2.record(stream)
+    u, q = pr.recover(x)
+    d.record(stream)
+    torch.cuda.synchronize()
+    batched_s = b.elapsed_time(c2) / 1e3
+    # one source alone on the same mesh
+    p1 = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
+    p1.set_source(f[0])
+    p1.condense(keep_factors=True, store_df64=True, split_update=True)
+    g1 = p1.rhs()
+    p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=1)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    x1, rep1, st1 = p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_s = e0.elapsed_time(e1) / 1e3
+    out = {"workload": f"n={cfg['n']} m={cfg['m']} p={cfg['p']} kappa={cfg['kappa']} beta={cfg['beta']}, "
+                       f"{count} Gaussian-bump sources (width 0.05, seeded centres), uniform level",
+           "N_tr": pr.info["N_tr"], "sources": count,
+           "condense_and_rhs_s": a.elapsed_time(b) / 1e3, "batched_solve_s": batched_s,
+           "batched_iterations": rep["iterations"], "batched_converged": bool(rep["converged"]),
+           "batched_max_rel_residual": rep["rel_residual"], "recover_s": c2.elapsed_time(d) / 1e3,
+           "single_solve_s": single_s, "single_iterations": rep1["iterations"],
+           "sequential_estimate_s": single_s * count, "speedup_vs_sequential": single_s * count / batched_s,
+           "column0_rel_diff_to_single": float((x1 - x[0]).abs().max() / x1.abs().max())}
+    pr.close()
+    p1.close()
+    return out
+
+
+def bench_gradient(stream):
+    """Adjoint gradient of J = 1/2 |u - u_obs|^2 (nodal) with respect to the per-element
+    diffusivities and the source, n=64, m=4, p=2, beta=(1,0.5), kappa_e = exp(GRF)."""
+    import torch
+    from paper_2302_10917_gb300 import Problem, solve_u
+    from paper_2302_10917_gb300 import workloads as wl
+    n, m, p, beta = 64, 4, 2, (1.0, 0.5)
+    kap = torch.from_numpy(wl.grf_kappa(n, 1)).cuda()
+    kobs = torch.from_numpy(wl.grf_kappa(n, 1001)).cuda()
+    pr = Problem(n, m, p, beta=beta, kappa=kap.cpu().numpy(), stream=stream)
+    f = wl.sin_sin_source(pr.quad_points(), 1.0, beta).contiguous()
+    opts = dict(tol=1e-10, restart=128, mode=2, split_update=True, orth=1)
+    with torch.no_grad():
+        u_obs = solve_u(pr, kobs, f, **opts).clone()
+    times = []
+    for _ in range(2):
+        k = kap.clone().requires_grad_(True)
+        ff = f.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = 0.5 * ((solve_u(pr, k, ff, **opts) - u_obs) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        times.append((t1 - t0, time.perf_counter() - t1))
+    out = {"workload": f"n={n} m={m} p={p} beta={beta}, kappa_e = exp(GRF std 0.5, length 0.1), "
+                       "J = 1/2 |u - u_obs|^2 nodal", "N_tr": pr.info["N_tr"],
+           "forward_s": times[-1][0], "backward_s": times[-1][1], "J": float(J.detach()),
+           "grad_kappa_norm": float(k.grad.norm()), "grad_f_norm": float(ff.grad.norm())}
+    pr.close()
+    return out
 
 
 def main(argv=None):
