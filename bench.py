@@ -450,6 +450,7 @@ def run_ours(args):
     if not args.no_extras:
         line["multi_rhs"] = bench_multi_rhs(stream)
         line["gradient"] = bench_gradient(stream)
+        line["macro_vs_standard"] = bench_macro_vs_standard(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, int(round(applies / args.steps)))
     if rank == 0:
@@ -506,6 +507,64 @@ def bench_multi_rhs(stream, count=64):
            "column0_rel_diff_to_single": float((x1 - x[0]).abs().max() / x1.abs().max())}
     pr.close()
     p1.close()
+    return out
+
+
+def _lattice_nodes(n, m, p, device):
+    """Physical coordinates [N, Q, 2] of every element's lattice nodes (the "/" mesh
+    conventions of the C ABI: element 2 (j n + i) + t, node (a, b) at v0 + a/P (v1 - v0)
+    + b/P (v2 - v0), b-major)."""
+    import torch
+    P = m * p
+    ab = torch.tensor([(a, b) for b in range(P + 1) for a in range(P + 1 - b)], dtype=torch.float64, device=device) / P
+    h = 1.0 / n
+    sq = torch.arange(n * n, device=device)
+    i, j = (sq % n).double(), (sq // n).double()
+    x0, x1, y0, y1 = i * h, (i + 1) * h, j * h, (j + 1) * h
+    v = torch.empty(2 * n * n, 3, 2, dtype=torch.float64, device=device)
+    v[0::2, 0, 0], v[0::2, 0, 1], v[0::2, 1, 0], v[0::2, 1, 1], v[0::2, 2, 0], v[0::2, 2, 1] = x1, y0, x1, y1, x0, y0
+    v[1::2, 0, 0], v[1::2, 0, 1], v[1::2, 1, 0], v[1::2, 1, 1], v[1::2, 2, 0], v[1::2, 2, 1] = x0, y1, x0, y0, x1, y1
+    return v[:, None, 0, :] + ab[None, :, 0:1] * (v[:, None, 1, :] - v[:, None, 0, :]) + \
+        ab[None, :, 1:2] * (v[:, None, 2, :] - v[:, None, 0, :])
+
+
+def bench_macro_vs_standard(stream):
+    """The paper's comparison (Sec. 4, Tables 8 and 10) in 2D: the same 65 536 sub-triangles
+    of degree 3 as n = 32 macro-squares with m = 8 (macro-element HDG) and as n = 256 squares
+    with m = 1 (standard HDG), beta = 50 (cos 0.3, sin 0.3), kappa = 1, u = sin(pi x) sin(pi y);
+    GMRES(80), split-FP32 operator, to 1e-10."""
+    import math
+    import torch
+    from paper_2302_10917_gb300 import Problem
+    from paper_2302_10917_gb300 import workloads as wl
+    beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, (n, m) in {"macro_m8": (32, 8), "standard_m1": (256, 1)}.items():
+        pr = Problem(n, m, 3, beta=beta, kappa=1.0, stream=stream)
+        f = wl.sin_sin_source(pr.quad_points(), 1.0, beta).contiguous()
+        pr.set_source(f)
+        pr.condense(keep_factors=True, store_df64=True, split_update=True)
+        g = pr.rhs()
+        pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1)      # warm-up (graph capture)
+        a, b, c2 = ev(), ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        pr.set_source(f)
+        pr.condense(keep_factors=True, store_df64=True, split_update=True)
+        g = pr.rhs()
+        b.record(stream)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1)
+        c2.record(stream)
+        u, q = pr.recover(x)
+        torch.cuda.synchronize()
+        xy = _lattice_nodes(n, m, 3, u.device)
+        err = float((u - wl.sin_sin_exact(xy)).abs().max())
+        out[name] = {"n": n, "m": m, "p": 3, "sub_triangles": 2 * n * n * m * m, "N_tr": pr.info["N_tr"],
+                     "condense_s": a.elapsed_time(b) / 1e3, "solve_s": b.elapsed_time(c2) / 1e3,
+                     "iterations": rep["iterations"], "converged": bool(rep["converged"]),
+                     "max_nodal_error": err}
+        pr.close()
     return out
 
 
