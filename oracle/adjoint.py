@@ -38,6 +38,7 @@ def gradient(pr: HDGProblem, f_qp, r, gD_qp=None, return_state=False):
     """dJ/dkappa [N] and dJ/df [N, n_qp] for dJ/du = r [N, Q] (and u [N, Q]); with
     return_state also a dict of the adjoint right-hand side g_adj [N_tr], the
     trace adjoint nu [N_tr] and the u-part of Lambda [N, Q]."""
+    assert not pr.supg, "the kappa-derivative below assumes blocks affine in kappa (no SUPG)"
     msh = pr.mesh
     Q, n_t = msh.Q, msh.n_t
     X, U, u, g_hat = forward(pr, f_qp, gD_qp)

@@ -47,6 +47,42 @@ def tri_lagrange(alphas, p, lam, dlam):
     return phi, grad
 
 
+def tri_lagrange_laplacian(alphas, p, lam, dlam):
+    """Physical Laplacian of the P_p Lagrange basis on one triangle at the points
+    lam: Lap phi = sum_{k,l} (d^2 phi / d lambda_k d lambda_l) (grad lambda_k . grad lambda_l)
+    (the lambda_k are affine). Returns (npts, nb)."""
+    npts = lam.shape[0]
+    G = dlam @ dlam.T                       # grad lambda_k . grad lambda_l
+    out = np.zeros((npts, len(alphas)))
+    for b, alpha in enumerate(alphas):
+        f = np.ones((npts, 3))
+        d1 = np.zeros((npts, 3))
+        d2 = np.zeros((npts, 3))
+        for k in range(3):
+            v = np.ones(npts)
+            dv = np.zeros(npts)
+            ddv = np.zeros(npts)
+            for j in range(alpha[k]):
+                g = (p * lam[:, k] - j) / (j + 1)
+                dg = p / (j + 1)
+                ddv = ddv * g + 2.0 * dv * dg
+                dv = dv * g + v * dg
+                v = v * g
+            f[:, k], d1[:, k], d2[:, k] = v, dv, ddv
+        lap = np.zeros(npts)
+        for k in range(3):
+            for l in range(3):
+                if k == l:
+                    o = [t for t in range(3) if t != k]
+                    h = d2[:, k] * f[:, o[0]] * f[:, o[1]]
+                else:
+                    o = 3 - k - l
+                    h = d1[:, k] * d1[:, l] * f[:, o]
+                lap += h * G[k, l]
+        out[:, b] = lap
+    return out
+
+
 def line_lagrange(p, s):
     """P_p Lagrange basis on [0, 1] with nodes k / p, evaluated at points s."""
     s = np.asarray(s, dtype=np.float64)

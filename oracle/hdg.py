@@ -32,19 +32,43 @@ Static condensation, Eqs. (global_problem)/(local_problem):
     A_e U_e = R_e - B_e (v^_e + g^_e).
 The stabilisation tau is not given a value in the paper; the reading used is
 tau_e = kappa_e / tau_len + |beta| on every edge of the element.
+
+SUPG (Sec. 3.4, optional): every sub-triangle T of the macro-element adds
+tau_s (beta . grad w, beta . grad u - kappa Lap u)_T to the u-equation and
+tau_s (f, beta . grad w)_T to its load, with tau_s = h / (2 |beta|)
+(coth Pe - 1 / Pe), Pe = |beta| h / (2 kappa_e), h the sub-triangle diameter.
+Readings: the terms act on u (the printed form adds them to B), the printed
+"+ 1/Pe" is "- 1/Pe", and Pe and h are the sub-triangle's.
 """
 import numpy as np
 import scipy.linalg as sla
 
-from .basis import line_lagrange, tri_lagrange
+from .basis import line_lagrange, tri_lagrange, tri_lagrange_laplacian
 from .mesh import StructuredMesh
 from .quadrature import gauss_legendre, triangle_rule
+
+
+def supg_tau(h, abs_a, kappa):
+    """SUPG parameter (Sec. 3.4, read with "- 1/Pe"): h / (2 |a|) (coth Pe - 1 / Pe),
+    Pe = |a| h / (2 kappa); h / (2 |a|) for kappa = 0; 0 without advection."""
+    if abs_a <= 0.0:
+        return 0.0
+    if kappa <= 0.0:
+        return h / (2.0 * abs_a)
+    pe = abs_a * h / (2.0 * kappa)
+    if pe < 0.1:
+        # Laurent series of coth x - 1/x (Bernoulli numbers): x/3 - x^3/45 + 2x^5/945 - x^7/4725 + 2x^9/93555
+        x2 = pe * pe
+        xi = pe * (1.0 / 3.0 + x2 * (-1.0 / 45.0 + x2 * (2.0 / 945.0 + x2 * (-1.0 / 4725.0 + x2 * 2.0 / 93555.0))))
+    else:
+        xi = 1.0 / np.tanh(pe) - 1.0 / pe
+    return h / (2.0 * abs_a) * xi
 
 
 class HDGProblem:
     """One discrete macro-element HDG problem on the structured unit-square mesh."""
 
-    def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0):
+    def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, supg=False):
         self.mesh = StructuredMesh(n, m, p)
         msh = self.mesh
         self.n, self.m, self.p = n, m, p
@@ -54,6 +78,7 @@ class HDGProblem:
         self.tau = self.kappa / tau_len + np.hypot(self.beta[0], self.beta[1])
         self.ng = p + 2              # source rule: exact to degree 2p + 2
         self.ng_edge = p + 2         # boundary-data rule per sub-edge
+        self.supg = bool(supg)
         self._cache = {}
 
     # ------------------------------------------------------------- quadrature
@@ -118,6 +143,12 @@ class HDGProblem:
         Dx = np.zeros((Q, Q))
         Dy = np.zeros((Q, Q))
         Phi = np.zeros((len(subs) * xi_q.size, Q))      # basis at source points
+        # SUPG (Sec. 3.4): (a.grad phi_i, a.grad phi_j) and (a.grad phi_i, Lap phi_j) per
+        # sub-triangle, and a.grad phi at the source points
+        Kbb = np.zeros((Q, Q))
+        KbL = np.zeros((Q, Q))
+        PhiB = np.zeros((len(subs) * xi_q.size, Q))
+        hsub = 0.0
         for s, tri in enumerate(subs):
             alphas, nodes = msh.sub_nodes(tri)
             nodes = np.array(nodes)
@@ -129,6 +160,12 @@ class HDGProblem:
             np.add.at(Dx, ix, np.einsum("q,qa,qb->ab", wq, grad[:, :, 0], phi))
             np.add.at(Dy, ix, np.einsum("q,qa,qb->ab", wq, grad[:, :, 1], phi))
             Phi[s * xi_q.size:(s + 1) * xi_q.size, nodes] = phi
+            bgrad = self.beta[0] * grad[:, :, 0] + self.beta[1] * grad[:, :, 1]
+            lap = tri_lagrange_laplacian(alphas, p, lam_q, dlam)
+            np.add.at(Kbb, ix, np.einsum("q,qa,qb->ab", wq, bgrad, bgrad))
+            np.add.at(KbL, ix, np.einsum("q,qa,qb->ab", wq, bgrad, lap))
+            PhiB[s * xi_q.size:(s + 1) * xi_q.size, nodes] = bgrad
+            hsub = max(hsub, np.linalg.norm(B - A), np.linalg.norm(C - A), np.linalg.norm(C - B))
 
         # boundary terms, edge k from v_{k+1} to v_{k+2}
         xg, wg = gauss_legendre(self.ng)
@@ -176,7 +213,8 @@ class HDGProblem:
                 np.add.at(G, np.ix_(cols, cols), np.einsum("q,qs,qt->st", wq, psi, psi))
         nx = np.repeat(normals[:, 0], P1)
         ny = np.repeat(normals[:, 1], P1)
-        out = dict(M=M, Dx=Dx, Dy=Dy, E=E, Ex=Ex, Ey=Ey, F=F, Fx=F * nx[None, :],
+        out = dict(M=M, Dx=Dx, Dy=Dy, E=E, Ex=Ex, Ey=Ey, F=F, Fx=F * nx[None, :], Kbb=Kbb, KbL=KbL, PhiB=PhiB,
+                   hsub=hsub,
                    Fy=F * ny[None, :], G=G, Phi=Phi, normals=normals, lengths=lengths,
                    bn=self.beta[0] * nx + self.beta[1] * ny)
         self._cache[e] = out
@@ -202,7 +240,16 @@ class HDGProblem:
         C = np.hstack([kap * em["Fx"].T, kap * em["Fy"].T, tau * em["F"].T])
         Ga = em["G"] * em["bn"][None, :]       # G is block diagonal per edge
         D = Ga - tau * em["G"]
+        if self.supg:
+            ts = self.supg_tau(e)
+            A[2 * Q:, 2 * Q:] += ts * (em["Kbb"] - kap * em["KbL"])
         return A, B, C, D
+
+    def supg_tau(self, e):
+        """tau_s of Sec. 3.4 for macro-element e: h / (2 |a|) (coth Pe - 1 / Pe), Pe = |a| h /
+        (2 kappa_e), h the sub-triangle diameter (the printed "+ 1/Pe" read as "- 1/Pe")."""
+        h = self.element_matrices(e)["hsub"]
+        return supg_tau(h, float(np.hypot(self.beta[0], self.beta[1])), float(self.kappa[e]))
 
     def blocks_at(self, e, kappa_e):
         """A_e, B_e, C_e, D_e evaluated with diffusivity kappa_e (tau_e follows kappa_e)."""
@@ -221,6 +268,8 @@ class HDGProblem:
         _, wts = self._qp_cache()
         R = np.zeros(3 * Q)
         R[2 * Q:] = em["Phi"].T @ (wts[e] * f_vals)
+        if self.supg:
+            R[2 * Q:] += self.supg_tau(e) * (em["PhiB"].T @ (wts[e] * f_vals))
         return R
 
     def _qp_cache(self):

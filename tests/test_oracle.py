@@ -432,3 +432,78 @@ def test_adjoint_blocks_affine_in_kappa():
             assert np.abs((X2 - X0) - 2 * (X1 - X0)).max() <= 1e-12 * max(np.abs(X1).max(), 1.0)
         # and blocks_at restores the problem's own diffusivity
         assert pr.kappa[e] == k0
+
+
+# ------------------------------------------------------------------------ SUPG
+def test_supg_tau_closed_form():
+    """Sec. 3.4 (read with "- 1/Pe"): tau_s = h/(2|a|) (coth Pe - 1/Pe)."""
+    from oracle.hdg import supg_tau
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    h, a = 0.1, 2.0
+    for kap in (1e-6, 0.05, 0.3, 10.0, 1e3):
+        pe = mpmath.mpf(a) * h / (2 * mpmath.mpf(kap))
+        exact = float(mpmath.mpf(h) / (2 * a) * (mpmath.coth(pe) - 1 / pe))
+        assert abs(supg_tau(h, a, kap) - exact) <= 1e-12 * exact
+    assert supg_tau(h, a, 0.0) == h / (2 * a)          # pure advection limit
+    assert supg_tau(h, 0.0, 1.0) == 0.0                # no advection, no stabilisation
+    # the small-Pe series agrees with the direct formula at the switch (Pe = 0.1)
+    kap = a * h / (2 * 0.1)
+    lo, hi = supg_tau(h, a, kap * (1 + 1e-14)), supg_tau(h, a, kap * (1 - 1e-14))
+    assert abs(hi - lo) < 1e-11 * hi
+
+
+def test_laplacian_of_basis_reproduces_quadratics():
+    """Lap of the P_p interpolant of x^2 + y^2 is 4 on every sub-triangle (p >= 2)."""
+    from oracle.basis import tri_lagrange_laplacian
+    rng = np.random.default_rng(3)
+    for p in (2, 3):
+        msh = StructuredMesh(1, 2, p)
+        pr = HDGProblem(1, 2, p)
+        v = msh.vertices(0)
+        for tri in msh.sub_triangles():
+            alphas, nodes = msh.sub_nodes(tri)
+            A, B, C, Js, Jinv, dlam = pr._sub_triangle_data(v, tri)
+            lam_nodes = np.array([[a[0] / p, a[1] / p, a[2] / p] for a in alphas])
+            X = A[None, :] + np.outer(lam_nodes[:, 1], B - A) + np.outer(lam_nodes[:, 2], C - A)
+            coef = X[:, 0] ** 2 + X[:, 1] ** 2
+            lam = rng.dirichlet(np.ones(3), size=5)
+            L = tri_lagrange_laplacian(alphas, p, lam, dlam)
+            assert np.abs(L @ coef - 4.0).max() < 1e-10
+
+
+@pytest.mark.parametrize("n,m,p", [(2, 2, 1), (2, 2, 2), (1, 4, 3)])
+def test_supg_keeps_polynomial_exactness(n, m, p):
+    """The SUPG residual a.grad u - kappa Lap u - f vanishes for the exact solution, so
+    u in P_p is still reproduced to roundoff with SUPG on (a dropped Laplacian term or a
+    wrong sign of a SUPG term breaks this for p >= 2)."""
+    kap, beta = 0.05, (0.9, -0.4)
+    pr = HDGProblem(n, m, p, beta=beta, kappa=kap, supg=True)
+    u, gr, f = polynomial(random_polynomial(p, seed=21 + p), kap, beta)
+    pts, _ = pr.quad_points()
+    bpts, _ = pr.bnd_quad_points()
+    fq = f(pts[..., 0], pts[..., 1])
+    gq = u(bpts[..., 0], bpts[..., 1])
+    S_el, g, gh = pr.condense(fq, gq)
+    x = np.linalg.solve(pr.assemble_S(S_el), g)
+    uu, qq = pr.recover(x, fq, gh)
+    eu, eq = pr.l2_errors(uu, qq, u, gr)
+    assert eu < 1e-11 and eq < 1e-10
+    # and the SUPG terms are active: the condensed operator differs from the plain one
+    S0, _, _ = HDGProblem(n, m, p, beta=beta, kappa=kap).condense(fq, gq)
+    assert np.abs(np.stack(S_el) - np.stack(S0)).max() > 1e-6 * np.abs(np.stack(S0)).max()
+
+
+def test_supg_vanishes_for_small_peclet():
+    """tau_s ~ h Pe / (6 |a|) as Pe -> 0, so the SUPG terms relative to diffusion scale like
+    |a| h^2 / kappa: at kappa = 1e6 the SUPG and plain solutions agree to ~1e-8."""
+    kap, beta = 1e6, (1.0, 0.5)
+    u, gr, f = sin_sin(kap, beta)
+    sols = []
+    for supg in (False, True):
+        pr = HDGProblem(2, 2, 2, beta=beta, kappa=kap, supg=supg)
+        pts, _ = pr.quad_points()
+        fq = f(pts[..., 0], pts[..., 1])
+        S_el, g, gh = pr.condense(fq)
+        sols.append(np.linalg.solve(pr.assemble_S(S_el), g))
+    assert np.abs(sols[1] - sols[0]).max() < 1e-6 * np.abs(sols[0]).max()
