@@ -92,6 +92,11 @@ typedef struct {
   const double* kappa;   /* host pointer, N per-element diffusivities >= 0, or NULL */
   double tau_len;        /* length scale of tau_e = kappa_e / tau_len + |beta|; > 0 */
   int bc[4];             /* boundary type per side (bottom, top, left, right); 0 = Dirichlet (only value accepted) */
+  int supg;              /* 1: SUPG stabilisation inside every macro-element (Sec. 3.4), 0: none.
+                            Adds tau_s (a . grad w, a . grad u - kappa Lap u - f) over the sub-triangles,
+                            tau_s = h / (2 |a|) (coth Pe - 1 / Pe), Pe = |a| h / (2 kappa), h the
+                            sub-triangle diameter (the printed formula's "+ 1/Pe" read as "- 1/Pe").
+                            hdg_gradient refuses SUPG (its terms are not affine in kappa). */
 } hdg_mesh_desc;
 
 typedef struct {

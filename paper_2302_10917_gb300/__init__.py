@@ -34,7 +34,7 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
                 ("beta", ctypes.c_double * 2), ("kappa0", ctypes.c_double),
                 ("kappa", ctypes.POINTER(ctypes.c_double)), ("tau_len", ctypes.c_double),
-                ("bc", ctypes.c_int * 4)]
+                ("bc", ctypes.c_int * 4), ("supg", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -127,7 +127,8 @@ def _ptr(t):
 class Problem:
     """One macro-element HDG problem on the structured unit-square mesh (one GPU)."""
 
-    def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, device="cuda:0", stream=None):
+    def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, device="cuda:0", stream=None,
+                 supg=False):
         self.lib = load_library()
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -146,6 +147,7 @@ class Problem:
             d.kappa = ctypes.cast(ctypes.c_void_p(k.data_ptr()), ctypes.POINTER(ctypes.c_double))
         for s in range(4):
             d.bc[s] = 0
+        d.supg = 1 if supg else 0
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = self.lib.hdg_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))

@@ -100,6 +100,11 @@ cudaError_t upload_tables(hdg_ctx* c) {
       {T.enode.data(), T.enode.size() * 4, (void**)&d.enode}, {T.subtri.data(), T.subtri.size() * 4, (void**)&d.subtri},
       {T.subnode.data(), T.subnode.size() * 4, (void**)&d.subnode},
       {T.ns_ptr.data(), T.ns_ptr.size() * 4, (void**)&d.ns_ptr}, {T.ns_idx.data(), T.ns_idx.size() * 4, (void**)&d.ns_idx},
+      {T.Sxx.data(), T.Sxx.size() * 8, (void**)&d.Sxx},   {T.Syy.data(), T.Syy.size() * 8, (void**)&d.Syy},
+      {T.Ssym.data(), T.Ssym.size() * 8, (void**)&d.Ssym}, {T.Lx_xx.data(), T.Lx_xx.size() * 8, (void**)&d.Lx_xx},
+      {T.Lx_xy.data(), T.Lx_xy.size() * 8, (void**)&d.Lx_xy}, {T.Lx_yy.data(), T.Lx_yy.size() * 8, (void**)&d.Lx_yy},
+      {T.Ly_xx.data(), T.Ly_xx.size() * 8, (void**)&d.Ly_xx}, {T.Ly_xy.data(), T.Ly_xy.size() * 8, (void**)&d.Ly_xy},
+      {T.Ly_yy.data(), T.Ly_yy.size() * 8, (void**)&d.Ly_yy}, {T.dphq.data(), T.dphq.size() * 8, (void**)&d.dphq},
   };
   // split-FP32 copies: hi = (float) v, lo = (float) (v - hi)
   std::vector<std::vector<float>> split;
@@ -113,10 +118,15 @@ cudaError_t upload_tables(hdg_ctx* c) {
     split.push_back(std::move(h));
     items.push_back({split.back().data(), split.back().size() * 4, (void**)dst});
   };
-  split.reserve(10);
+  split.reserve(19);
   add_split(T.Kxx, &d.Kxx2); add_split(T.Kyy, &d.Kyy2); add_split(T.Ksym, &d.Ksym2);
   add_split(T.Dxi, &d.Dxi2); add_split(T.Deta, &d.Deta2); add_split(T.Fh, &d.Fh2);
   add_split(T.Pxi, &d.Pxi2); add_split(T.Peta, &d.Peta2); add_split(T.Hh, &d.Hh2); add_split(T.Gh, &d.Gh2);
+  {
+    const std::vector<double>* sup[9] = {&T.Sxx, &T.Ssym, &T.Syy, &T.Lx_xx, &T.Lx_xy, &T.Lx_yy,
+                                         &T.Ly_xx, &T.Ly_xy, &T.Ly_yy};
+    for (int k = 0; k < 9; ++k) add_split(*sup[k], &d.Sup2[k]);
+  }
   size_t total = 0;
   for (auto& it : items) total += round_up(it.bytes, 256);
   cudaError_t e = cudaMalloc(&c->d_tables, total);
@@ -163,6 +173,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if (!(d->tau_len > 0.0) || !std::isfinite(d->beta[0]) || !std::isfinite(d->beta[1])) return HDG_ERR_ARG;
   for (int s = 0; s < 4; ++s)
     if (d->bc[s] != 0) return HDG_ERR_ARG;
+  if (d->supg != 0 && d->supg != 1) return HDG_ERR_ARG;
   const int64_t N = 2LL * d->n * d->n;
   if (!d->kappa && !(d->kappa0 >= 0.0 && std::isfinite(d->kappa0))) return HDG_ERR_ARG;
   if (d->kappa)
@@ -198,6 +209,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   P.ngb = T.ngb; P.n_bqp = d->m * T.ngb;
   P.bx = d->beta[0]; P.by = d->beta[1]; P.babs = std::hypot(d->beta[0], d->beta[1]);
   P.kappa0 = d->kappa0; P.tau_len = d->tau_len;
+  P.supg = d->supg;
   P.R = T.Q + T.n_t;
   P.nrhs = 1;
   P.Cc = T.Q + T.n_t + 1;
@@ -601,6 +613,7 @@ hdg_status hdg_gradient(hdg_ctx* c, const double* x, const double* u, const doub
   if (!c) return HDG_ERR_ARG;
   if (!x || !u || !mu || !nu || !dkappa) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_gradient before hdg_set_source");
+  if (c->prm.supg) return set_err(c, HDG_ERR_STATE, "hdg_gradient: SUPG terms are not affine in kappa");
   ProfScope ps(c, HDG_PROF_ADJOINT);
   const double* gh = c->gD_qp ? c->d_ghat : nullptr;
   cudaError_t e = launch_gradient(c->prm, c->dt, x, gh, u, mu, nu, dkappa, df, c->stream);

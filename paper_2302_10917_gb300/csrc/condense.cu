@@ -60,7 +60,8 @@ __device__ void condense_outputs(const CondArgs& a, const double* W, int e);
 // detJ / m^2; put(i, r, value) stores row i of column r. Block-wide; ends
 // with a barrier.
 template <typename Put>
-__device__ void load_columns(const CondArgs& a, int e, double detJ, double* proj, Put put) {
+__device__ void load_columns(const CondArgs& a, int e, double detJ, double* proj, Put put, double ts = 0.0,
+                             double bxi = 0.0, double beta_ = 0.0) {
   const Params& P = a.prm;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const double scale = detJ / (double)(P.m * P.m);
@@ -69,7 +70,15 @@ __device__ void load_columns(const CondArgs& a, int e, double detJ, double* proj
     for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
       const int s = idx / P.nloc, b = idx - s * P.nloc;
       double acc = 0.0;
-      for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
+      if (P.supg) {
+        // SUPG load: (f, phi_b + tau_s a . grad phi_b) on the sub-triangle
+        for (int q = 0; q < P.nqs; ++q) {
+          const double* dg = a.dt.dphq + (((size_t)s * P.nqs + q) * P.nloc + b) * 2;
+          acc += a.dt.wq[q] * fe[s * P.nqs + q] * (a.dt.phiq[q * P.nloc + b] + ts * (bxi * dg[0] + beta_ * dg[1]));
+        }
+      } else {
+        for (int q = 0; q < P.nqs; ++q) acc += a.dt.wq[q] * fe[s * P.nqs + q] * a.dt.phiq[q * P.nloc + b];
+      }
       proj[idx] = acc;
     }
     __syncthreads();
@@ -122,6 +131,15 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     bn[k] = P.bx * g.nrm[k][0] + P.by * g.nrm[k][1];
   }
   const double cK = kap * g.detJ;
+  // SUPG (Sec. 3.4): tau_s detJ [(a.grad)^2 products - kappa (a.grad)(Lap) products]
+  const double ts = P.supg ? supg_tau(fmax(g.L[0], fmax(g.L[1], g.L[2])) / P.m, P.babs, kap) : 0.0;
+  double cs[9];
+  {
+    const double bs = ts * g.detJ;
+    cs[0] = bs * bxi * bxi; cs[1] = bs * bxi * beta_; cs[2] = bs * beta_ * beta_;
+    cs[3] = -bs * kap * bxi * gxx; cs[4] = -bs * kap * bxi * 2.0 * gxy; cs[5] = -bs * kap * bxi * gyy;
+    cs[6] = -bs * kap * beta_ * gxx; cs[7] = -bs * kap * beta_ * 2.0 * gxy; cs[8] = -bs * kap * beta_ * gyy;
+  }
 
 
   // --------------------------------------------------- form the bordered system
@@ -134,6 +152,12 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
         if (j < Q) {
           v = cK * (gxx * a.dt.Kxx[qi + j] + gxy * a.dt.Ksym[qi + j] + gyy * a.dt.Kyy[qi + j])
               - g.detJ * (bxi * a.dt.Dxi[qi + j] + beta_ * a.dt.Deta[qi + j]);
+          if (P.supg) {
+            const size_t ij = qi + j;
+            v += cs[0] * a.dt.Sxx[ij] + cs[1] * a.dt.Ssym[ij] + cs[2] * a.dt.Syy[ij] + cs[3] * a.dt.Lx_xx[ij] +
+                 cs[4] * a.dt.Lx_xy[ij] + cs[5] * a.dt.Lx_yy[ij] + cs[6] * a.dt.Ly_xx[ij] + cs[7] * a.dt.Ly_xy[ij] +
+                 cs[8] * a.dt.Ly_yy[ij];
+          }
         } else if (j < Q + nt) {
           const int c = j - Q, k = c / P1;
           const size_t ic = (size_t)i * nt + c;
@@ -165,7 +189,8 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
   __syncthreads();
   // load columns Q + n_t + r: per sub-triangle projections of source r (in
   // the panel area, free before the LU starts), summed per lattice node
-  load_columns(a, e, g.detJ, Ls, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = v; });
+  load_columns(a, e, g.detJ, Ls, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = v; }, ts, bxi,
+               beta_);
   // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
   for (int k = 0; k < 3; ++k) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {
@@ -389,13 +414,16 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
   __shared__ int piv_s[NB];
   __shared__ float red_v[8];
   __shared__ int red_i[8];
-  __shared__ float2 sc[24];     // element and edge scalars of the formation
+  __shared__ float2 sc[32];     // element and edge scalars of the formation (23 .. 31: SUPG)
 
   // ---------------------------------------------------------- element data
   ElemGeom g;
   elem_geom(e, P.n, g);
   const double kap = a.kappa[e];
   const double tau = kap / P.tau_len + P.babs;
+  const double bxi_e = P.bx * g.gxi[0] + P.by * g.gxi[1];
+  const double beta_e = P.bx * g.geta[0] + P.by * g.geta[1];
+  const double ts = P.supg ? supg_tau(fmax(g.L[0], fmax(g.L[1], g.L[2])) / P.m, P.babs, kap) : 0.0;
   if (tid == 0) {
     const double gxx = g.gxi[0] * g.gxi[0] + g.gxi[1] * g.gxi[1];
     const double gxy = g.gxi[0] * g.geta[0] + g.gxi[1] * g.geta[1];
@@ -419,6 +447,17 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
         if (l >= k) sc[17 + (k == 0 ? l : (k == 1 ? 2 + l : 5))] = df_from(-kap * g.L[k] * g.L[l] * nn / g.detJ);
       }
     }
+    // SUPG scalars (Sec. 3.4), in the order of the split SUPG tables
+    const double bs = ts * g.detJ;
+    sc[23] = df_from(bs * bxi_e * bxi_e);
+    sc[24] = df_from(bs * bxi_e * beta_e);
+    sc[25] = df_from(bs * beta_e * beta_e);
+    sc[26] = df_from(-bs * kap * bxi_e * gxx);
+    sc[27] = df_from(-bs * kap * bxi_e * 2.0 * gxy);
+    sc[28] = df_from(-bs * kap * bxi_e * gyy);
+    sc[29] = df_from(-bs * kap * beta_e * gxx);
+    sc[30] = df_from(-bs * kap * beta_e * 2.0 * gxy);
+    sc[31] = df_from(-bs * kap * beta_e * gyy);
   }
   __syncthreads();
 
@@ -436,6 +475,9 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
         df_fma(h, l, sc[2], a.dt.Kyy2[qi]);
         df_fma(h, l, sc[3], a.dt.Dxi2[qi]);
         df_fma(h, l, sc[4], a.dt.Deta2[qi]);
+        if (P.supg)
+#pragma unroll
+          for (int k9 = 0; k9 < 9; ++k9) df_fma(h, l, sc[23 + k9], a.dt.Sup2[k9][qi]);
       } else if (j < Q + nt) {
         const int c = j - Q, k = c / P1;
         const size_t ic = (size_t)i * nt + c;
@@ -461,7 +503,8 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
   }
   __syncthreads();
   // load columns (FP64 projections in the panel area, stored split)
-  load_columns(a, e, g.detJ, smem, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = df_from(v); });
+  load_columns(a, e, g.detJ, smem, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = df_from(v); },
+               ts, bxi_e, beta_e);
   // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
   for (int k = 0; k < 3; ++k) {
     for (int idx = tid; idx < P1 * P1; idx += nthr) {

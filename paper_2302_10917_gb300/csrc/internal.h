@@ -1,6 +1,7 @@
 // Internal declarations of the macro-element HDG library (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -39,6 +40,10 @@ struct RefTables {
   std::vector<int> subnode;
   std::vector<int> ns_ptr, ns_idx;      // CSR: node -> entries s * nloc + a
   std::vector<double> bpsi, bw, bu;     // boundary rule: nodes bu, weights bw (ngb)
+  // SUPG (Sec. 3.4): Sxx = int d_xi phi_i d_xi phi_j, Syy, Ssym (mixed, symmetrised);
+  // Lx_ab = int d_xi phi_i d_ab phi_j, Ly_ab = int d_eta phi_i d_ab phi_j (sub-triangle-wise
+  // second derivatives); dphq [nsub][nqs][nloc][2] macro-reference gradients at source points
+  std::vector<double> Sxx, Syy, Ssym, Lx_xx, Lx_xy, Lx_yy, Ly_xx, Ly_xy, Ly_yy, dphq;
 };
 
 // Builds the tables of level (m, p). Throws std::runtime_error on failure.
@@ -54,6 +59,9 @@ struct DevTables {
   double *bpsi, *bw, *bu;
   // split-FP32 (hi, lo) copies of the element-formation tables
   float2 *Kxx2, *Kyy2, *Ksym2, *Dxi2, *Deta2, *Fh2, *Pxi2, *Peta2, *Hh2, *Gh2;
+  // SUPG tables (FP64 and split copies of the nine Q x Q products)
+  double *Sxx, *Syy, *Ssym, *Lx_xx, *Lx_xy, *Lx_yy, *Ly_xx, *Ly_xy, *Ly_yy, *dphq;
+  float2 *Sup2[9];
 };
 
 // Scalar problem parameters passed by value to kernels.
@@ -62,6 +70,7 @@ struct Params {
   int N, n_int, n_bnd, N_tr;
   int ng, nqs, nloc, nsub, n_qp, ngb, n_bqp;
   double bx, by, babs, kappa0, tau_len;
+  int supg;              // 1: SUPG terms in the u-equations (Sec. 3.4)
   int R, Cc, ld;         // bordered local system: rows, used columns, leading dimension
   int nrhs;              // right-hand sides (source columns of the bordered system)
 };
@@ -69,6 +78,23 @@ struct Params {
 // ---------------------------------------------------------------------------
 // Structured-mesh geometry (closed form, host and device).
 // ---------------------------------------------------------------------------
+// SUPG parameter of Sec. 3.4: tau_s = h / (2 |a|) (coth Pe - 1 / Pe), Pe = |a| h / (2 kappa)
+// (the Laurent series below Pe = 0.1, the limit h / (2 |a|) for kappa = 0, 0 without advection).
+__host__ __device__ inline double supg_tau(double h, double babs, double kappa) {
+  if (!(babs > 0.0)) return 0.0;
+  if (!(kappa > 0.0)) return h / (2.0 * babs);
+  const double pe = babs * h / (2.0 * kappa);
+  double xi;
+  if (pe < 0.1) {
+    // coth x - 1/x = x/3 - x^3/45 + 2 x^5/945 - x^7/4725 + 2 x^9/93555 - ... (Bernoulli numbers)
+    const double x2 = pe * pe;
+    xi = pe * (1.0 / 3.0 + x2 * (-1.0 / 45.0 + x2 * (2.0 / 945.0 + x2 * (-1.0 / 4725.0 + x2 * (2.0 / 93555.0)))));
+  } else {
+    xi = 1.0 / tanh(pe) - 1.0 / pe;
+  }
+  return h / (2.0 * babs) * xi;
+}
+
 __host__ __device__ inline void elem_vertices(int e, int n, double v[3][2]) {
   const int sq = e >> 1, t = e & 1;
   const int j = sq / n, i = sq - j * n;

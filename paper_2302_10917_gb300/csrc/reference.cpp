@@ -74,6 +74,34 @@ void lagrange_tri(int p, const std::vector<int>& al, int nloc, const double lam[
   }
 }
 
+// Second derivatives of the same basis: h[b][k][l] = d^2 phi_b / d lambda_k d lambda_l.
+void lagrange_tri_hess(int p, const std::vector<int>& al, int nloc, const double lam[3], double (*h)[3][3]) {
+  for (int b = 0; b < nloc; ++b) {
+    double f[3], df[3], ddf[3];
+    for (int k = 0; k < 3; ++k) {
+      double v = 1.0, d = 0.0, dd = 0.0;
+      for (int j = 0; j < al[3 * b + k]; ++j) {
+        const double g = (p * lam[k] - j) / (j + 1.0), gp = p / (j + 1.0);
+        dd = dd * g + 2.0 * d * gp;
+        d = d * g + v * gp;
+        v *= g;
+      }
+      f[k] = v;
+      df[k] = d;
+      ddf[k] = dd;
+    }
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        double v = 1.0;
+        for (int t = 0; t < 3; ++t) {
+          if (k == l) v *= (t == k ? ddf[t] : f[t]);
+          else v *= (t == k || t == l) ? df[t] : f[t];
+        }
+        h[b][k][l] = v;
+      }
+  }
+}
+
 // 1D P_p Lagrange basis on [0,1] with equispaced nodes.
 void lagrange_1d(int p, double s, double* out) {
   for (int k = 0; k <= p; ++k) {
@@ -240,6 +268,77 @@ void build_reference_tables(int m, int p, RefTables& T) {
           T.Dxi[ij] += w * pb * dxi_a;
           T.Deta[ij] += w * pb * deta_a;
         }
+      }
+    }
+  }
+
+  // SUPG tables (Sec. 3.4): products of first derivatives and of first with
+  // second derivatives of the lattice basis, sub-triangle by sub-triangle, and
+  // the macro-reference gradients of every local basis function at the
+  // source points
+  T.Sxx.assign((size_t)Q * Q, 0.0);
+  T.Syy.assign((size_t)Q * Q, 0.0);
+  T.Ssym.assign((size_t)Q * Q, 0.0);
+  for (auto* Lt : {&T.Lx_xx, &T.Lx_xy, &T.Lx_yy, &T.Ly_xx, &T.Ly_xy, &T.Ly_yy}) Lt->assign((size_t)Q * Q, 0.0);
+  T.dphq.assign((size_t)T.nsub * T.nqs * T.nloc * 2, 0.0);
+  {
+    std::vector<double[3][3]> hl(T.nloc);
+    std::vector<double> hq((size_t)T.nqs * T.nloc * 3);   // d2/dxi^2, d2/dxi^deta^, d2/deta^2 (local)
+    for (int j = 0; j < T.ng; ++j)
+      for (int i = 0; i < T.ng; ++i) {
+        const int q = j * T.ng + i;
+        const double xh = gx[i] * (1.0 - gx[j]), eh = gx[j];
+        const double lam[3] = {1.0 - xh - eh, xh, eh};
+        lagrange_tri_hess(p, al, T.nloc, lam, hl.data());
+        const double u[3] = {-1.0, 1.0, 0.0}, v[3] = {-1.0, 0.0, 1.0};
+        for (int b = 0; b < T.nloc; ++b) {
+          double uu = 0.0, uv = 0.0, vv = 0.0;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+              uu += u[k] * hl[b][k][l] * u[l];
+              uv += u[k] * hl[b][k][l] * v[l];
+              vv += v[k] * hl[b][k][l] * v[l];
+            }
+          hq[((size_t)q * T.nloc + b) * 3 + 0] = uu;
+          hq[((size_t)q * T.nloc + b) * 3 + 1] = uv;
+          hq[((size_t)q * T.nloc + b) * 3 + 2] = vv;
+        }
+      }
+    std::vector<double> gxi(T.nloc), geta(T.nloc), hxx(T.nloc), hxy(T.nloc), hyy(T.nloc);
+    for (int s = 0; s < T.nsub; ++s) {
+      const int* c = &T.subtri[6 * s];
+      const double j00 = double(c[2] - c[0]) / m, j10 = double(c[3] - c[1]) / m;
+      const double j01 = double(c[4] - c[0]) / m, j11 = double(c[5] - c[1]) / m;
+      const double det = j00 * j11 - j01 * j10;
+      const double i00 = j11 / det, i01 = -j01 / det, i10 = -j10 / det, i11 = j00 / det;
+      const int* nd = &T.subnode[(size_t)s * T.nloc];
+      for (int q = 0; q < T.nqs; ++q) {
+        const double w = T.wq[q] * std::fabs(det);
+        for (int a = 0; a < T.nloc; ++a) {
+          const double* da = &dphi[((size_t)q * T.nloc + a) * 2];
+          gxi[a] = da[0] * i00 + da[1] * i10;
+          geta[a] = da[0] * i01 + da[1] * i11;
+          const double* ha = &hq[((size_t)q * T.nloc + a) * 3];
+          // (xi^, eta^) second derivatives to (xi, eta): c_xi = (i00, i10), c_eta = (i01, i11)
+          hxx[a] = i00 * i00 * ha[0] + 2.0 * i00 * i10 * ha[1] + i10 * i10 * ha[2];
+          hxy[a] = i00 * i01 * ha[0] + (i00 * i11 + i10 * i01) * ha[1] + i10 * i11 * ha[2];
+          hyy[a] = i01 * i01 * ha[0] + 2.0 * i01 * i11 * ha[1] + i11 * i11 * ha[2];
+          T.dphq[(((size_t)s * T.nqs + q) * T.nloc + a) * 2 + 0] = gxi[a];
+          T.dphq[(((size_t)s * T.nqs + q) * T.nloc + a) * 2 + 1] = geta[a];
+        }
+        for (int a = 0; a < T.nloc; ++a)
+          for (int b = 0; b < T.nloc; ++b) {
+            const size_t ij = (size_t)nd[a] * Q + nd[b];
+            T.Sxx[ij] += w * gxi[a] * gxi[b];
+            T.Syy[ij] += w * geta[a] * geta[b];
+            T.Ssym[ij] += w * (gxi[a] * geta[b] + geta[a] * gxi[b]);
+            T.Lx_xx[ij] += w * gxi[a] * hxx[b];
+            T.Lx_xy[ij] += w * gxi[a] * hxy[b];
+            T.Lx_yy[ij] += w * gxi[a] * hyy[b];
+            T.Ly_xx[ij] += w * geta[a] * hxx[b];
+            T.Ly_xy[ij] += w * geta[a] * hxy[b];
+            T.Ly_yy[ij] += w * geta[a] * hyy[b];
+          }
       }
     }
   }
