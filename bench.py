@@ -451,6 +451,7 @@ def run_ours(args):
         line["multi_rhs"] = bench_multi_rhs(stream)
         line["gradient"] = bench_gradient(stream)
         line["macro_vs_standard"] = bench_macro_vs_standard(stream)
+        line["supg_layer"] = bench_supg_layer(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, int(round(applies / args.steps)))
     if rank == 0:
@@ -565,6 +566,34 @@ def bench_macro_vs_standard(stream):
                      "iterations": rep["iterations"], "converged": bool(rep["converged"]),
                      "max_nodal_error": err}
         pr.close()
+    return out
+
+
+def bench_supg_layer(stream):
+    """The paper's SUPG comparison (Sec. 3.4 and its kappa = 1e-5 figure) in 2D, as
+    source-free transport: kappa = 1e-5, beta = (1, 1), f = 0, g_D = the interior-layer
+    profile (1 + tanh((y - 2x + 0.4) / kappa)) / 2 on the boundary (a step), n = 32, m = 4,
+    p = 3, without and with SUPG. The maximum principle bounds u to [0, 1]; reported: the
+    range of the nodal values and the solve statistics."""
+    import torch
+    from paper_2302_10917_gb300 import Problem
+    from paper_2302_10917_gb300 import workloads as wl
+    n, m, p, kap, beta = 32, 4, 3, 1e-5, (1.0, 1.0)
+    out = {}
+    for supg in (False, True):
+        pr = Problem(n, m, p, beta=beta, kappa=kap, stream=stream, supg=supg)
+        f = torch.zeros(pr.info["N"], pr.info["n_qp"], dtype=torch.float64, device="cuda")
+        gD = wl.tanh_layer_exact(pr.bnd_quad_points(), kap).contiguous()
+        pr.set_source(f, gD)
+        pr.condense(keep_factors=True, store_df64=True, split_update=True)
+        x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, mode=2, orth=1, maxit=40000, check=False)
+        u, q = pr.recover(x)
+        out["supg" if supg else "plain"] = {"u_min": float(u.min()), "u_max": float(u.max()),
+                                            "overshoot": float(max(u.max() - 1.0, -u.min(), 0.0)),
+                                            "iterations": rep["iterations"], "converged": bool(rep["converged"])}
+        pr.close()
+    out["workload"] = (f"n={n} m={m} p={p} kappa={kap} beta={beta}, f = 0, g_D = interior-layer step; "
+                       "exact range [0, 1]")
     return out
 
 

@@ -37,6 +37,22 @@ def sin_sin_exact(xy):
     return torch.sin(math.pi * xy[..., 0]) * torch.sin(math.pi * xy[..., 1])
 
 
+def tanh_layer_exact(xy, kappa):
+    """The interior-layer benchmark of Sec. 4.1: u = (1 + tanh((y - 2x + 0.4) / kappa)) / 2."""
+    return 0.5 * (1.0 + torch.tanh((xy[..., 1] - 2.0 * xy[..., 0] + 0.4) / kappa))
+
+
+def tanh_layer_source(xy, kappa, beta):
+    """f = -kappa Lap u + beta . grad u for the interior layer (beta . grad u is kept: the
+    layer is not parallel to beta = (1, 1))."""
+    z = (xy[..., 1] - 2.0 * xy[..., 0] + 0.4) / kappa
+    t = torch.tanh(z)
+    s = 1.0 - t * t                      # sech^2
+    lap = -s * t * 5.0 / (kappa * kappa)  # 0.5 * (-2 s t) * |grad z|^2, |grad z|^2 = 5 / kappa^2
+    ux, uy = -s / kappa, 0.5 * s / kappa
+    return -kappa * lap + beta[0] * ux + beta[1] * uy
+
+
 def random_kappa(N, seed, lo=0.5, hi=2.0):
     """Per-element diffusivities, log-uniform in [lo, hi]."""
     g = np.random.default_rng([MASTER_SEED, 17, int(seed)])
