@@ -200,34 +200,39 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
   double len;
   edge_sides(f, P.n, e, k, fl, &len);
   float2 out;
-  // both sides' terms as one sequence q = 0 .. 2 n_t - 1; loads of the next
-  // batch of 8 are issued before the arithmetic of the current one
+  // row t_side of each side's row-block (the edge dof s in the element's orientation)
   const int t0 = fl[0] ? PP - s : s, t1 = fl[1] ? PP - s : s;
-  const int nq = 2 * nt;
   if constexpr (BT == 1) {
     const float2* S = static_cast<const float2*>(Sv);
-    const float2* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
-    const float2* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
-    const float2* xv = xs + le * 2 * nt;       // side 0 then side 1, contiguous
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    float2 cur[8], nxt[8];
+    // side by side: the row of this trace position is a stride-P1 walk through the
+    // element's row-block; groups of 8 loads, the next group issued before the
+    // products of the current one, two independent accumulators
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : make_float2(0.f, 0.f);
-    for (int q0 = 0; q0 < nq; q0 += 8) {
+    for (int sd = 0; sd < 2; ++sd) {
+      const float2* bp = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + (sd ? t1 : t0);
+      const float2* xv = xs + (le * 2 + sd) * nt;
+      const int ng = nt / 8;                 // full groups of 8
+      float2 cur[8], nxt[8];
+      if (ng > 0) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + 8 + u;
-        nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : make_float2(0.f, 0.f);
+        for (int u = 0; u < 8; ++u) cur[u] = bp[u * P1];
       }
+      for (int g = 0; g < ng; ++g) {
+        const int j = g * 8;
+        if (g + 1 < ng) {
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        const int q = q0 + u;
-        if (q < nq) df_fma(h0, l0, cur[u], xv[q]);
-        if (q + 1 < nq) df_fma(h1, l1, cur[u + 1], xv[q + 1]);
+          for (int u = 0; u < 8; ++u) nxt[u] = bp[(j + 8 + u) * P1];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          df_fma(h0, l0, cur[u], xv[j + u]);
+          df_fma(h1, l1, cur[u + 1], xv[j + u + 1]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+      for (int j = ng * 8; j < nt; ++j) df_fma(h0, l0, bp[j * P1], xv[j]);
     }
     df_add(h0, l0, h1, l1);
     if (escale) {
@@ -239,6 +244,9 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
     }
     out = df_norm(h0, l0);
   } else if constexpr (BT == 2) {
+    // both sides' terms as one sequence q = 0 .. 2 n_t - 1; loads of the next
+    // batch of 8 are issued before the arithmetic of the current one
+    const int nq = 2 * nt;
     const float* S = static_cast<const float*>(Sv);
     const float* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
     const float* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
