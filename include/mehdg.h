@@ -85,7 +85,9 @@ typedef enum {
 
 typedef struct {
   int n;                 /* macro squares per side (N = 2 n^2 macro-triangles), n >= 1 */
-  int m;                 /* sub-edges per macro-edge (m^2 sub-triangles), 1 <= m <= 16 */
+  int m;                 /* sub-edges per macro-edge (m^2 sub-triangles), 1 <= m <= 16; one element's
+                            condensation panel must fit 227 KB of shared memory, which excludes
+                            m >= 13 at p = 3 and m >= 10 at p = 4 (HDG_ERR_ARG with the size) */
   int p;                 /* polynomial degree, 1 <= p <= 4 */
   double beta[2];        /* constant advection velocity a */
   double kappa0;         /* diffusivity used when kappa == NULL; >= 0 (0 = pure advection) */

@@ -81,6 +81,8 @@ __global__ void bnd_points_kernel(Params P, DevTables dt, double* xy) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory one CTA may use on sm_103a
+
 // Copy the host tables into one device allocation.
 cudaError_t upload_tables(hdg_ctx* c) {
   const RefTables& T = c->ref;
@@ -215,6 +217,10 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   P.Cc = T.Q + T.n_t + 1;
   P.ld = (int)round_up(P.Cc, 4);
   *out = c;
+  if (condense_smem_bytes(P) > kMaxSmem)
+    return set_err(c, HDG_ERR_ARG, "level m = " + std::to_string(d->m) + ", p = " + std::to_string(d->p) +
+                                       ": one element's panel needs " + std::to_string(condense_smem_bytes(P) / 1024) +
+                                       " KB of shared memory (at most 227 KB)");
   if ((e = upload_tables(c)) != cudaSuccess) return cuda_err(c, e, "uploading reference tables");
   std::vector<double> kap(N, d->kappa0);
   if (d->kappa) std::copy(d->kappa, d->kappa + N, kap.begin());
@@ -277,6 +283,16 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
     c->alloc_nrhs = 0;
     if ((e = dev_alloc(c, &c->d_ghat, (size_t)nrhs * P.n_bnd * P.P1)) != cudaSuccess) return cuda_err(c, e, "ghat");
     c->alloc_nrhs = nrhs;
+  }
+  {
+    Params t = P;
+    t.nrhs = nrhs;
+    t.Cc = P.Q + P.n_t + nrhs;
+    t.ld = (int)round_up(t.Cc, 4);
+    if (condense_smem_bytes(t) > kMaxSmem)
+      return set_err(c, HDG_ERR_ARG, std::to_string(nrhs) + " sources need " +
+                                         std::to_string(condense_smem_bytes(t) / 1024) +
+                                         " KB of shared memory per element (at most 227 KB)");
   }
   P.nrhs = nrhs;
   P.Cc = P.Q + P.n_t + nrhs;

@@ -268,3 +268,16 @@ def test_error_statuses():
         bad.condense()
     assert ei.value.status == HDG_ERR_SINGULAR and "element 7" in str(ei.value)
     bad.close()
+
+
+def test_levels_beyond_shared_memory_are_refused():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_10917_gb300 import HDG_ERR_ARG, HDGError, Problem
+    with pytest.raises(HDGError) as ei:
+        Problem(1, 16, 3, beta=(1.0, 0.0), kappa=1.0)
+    assert ei.value.status == HDG_ERR_ARG and "shared memory" in str(ei.value)
+    pr = Problem(1, 16, 2, beta=(1.0, 0.0), kappa=1.0)       # the largest m at p = 2 fits, also with 64 sources
+    pr.set_source(torch.zeros(64, pr.info["N"], pr.info["n_qp"], dtype=torch.float64))
+    pr.condense()
+    pr.close()
