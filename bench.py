@@ -37,9 +37,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop 
 # split-FP32 multiply-add (Dekker product + two-sum accumulation): 1 FMUL + 3 FFMA + 8 FADD
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 # DRAM bytes (read + write) of one apply_vdf_kernel<1> launch per interior edge, from an ncu
-# capture at n = 64, m = 8, p = 3 (376.2 MB for 12 160 edges); the traffic scales with the
-# edges. Only valid for that kernel and element (m = 8, p = 3).
-APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.2e6 / 12160
+# capture at n = 64, m = 8, p = 3 (376.57 MB for 12 160 edges, 128-thread blocks); the traffic
+# scales with the edges. Only valid for that kernel and element (m = 8, p = 3).
+APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.57e6 / 12160
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)

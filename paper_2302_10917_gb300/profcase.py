@@ -40,6 +40,7 @@ def main(argv=None):
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--split", action="store_true", help="split-FP32 condensation")
     ap.add_argument("--orth", type=int, default=1, help="0: CGS2, 1: single-projection Gram-Schmidt")
+    ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner before the solve")
     a = ap.parse_args(argv)
     beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
     pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
@@ -68,6 +69,8 @@ def main(argv=None):
     t[5].record()
     torch.cuda.synchronize()
     gm = None
+    if a.autotune:
+        pr.autotune(mode=a.mode, restart=a.restart)
     if a.gmres_steps > 0:
         x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=a.restart, maxit=a.gmres_steps, mode=a.mode,
                                check=False, orth=a.orth)
@@ -89,6 +92,8 @@ def _step(pr, f, a):
     pr.condense(keep_factors=True, store_fp32=a.mode == 1, store_df64=a.mode == 2, split_update=True)
     t[1].record()
     g = pr.rhs()
+    if a.autotune:
+        pr.autotune(mode=a.mode, restart=a.restart)
     x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False, orth=a.orth)
     t[2].record()
     u, q = pr.recover(x)
