@@ -16,7 +16,9 @@ It is a slow, literal restatement of the paper's discrete problem:
   (global_problem)/(local_problem), and the four-step matrix-free apply of
   Section 3.3.2 with the D^-1 preconditioner of Section 6.1;
 * GMRES (Section 6.1) and the local back-solve Eq. (local_matrix_problem);
-* the counting formulas of Section 5 (Tables 1-2).
+* the counting formulas of Section 5 (Tables 1-2);
+* macro-elements of uneven refinement level with faces at the finer side's
+  level (Section 5.3, ``levels.py``).
 
 Every element matrix is integrated in PHYSICAL coordinates, sub-triangle by
 sub-triangle, with a Gauss rule built here from the Legendre recurrence. It
