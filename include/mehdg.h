@@ -59,6 +59,27 @@
  * i.e. nrhs consecutive copies of the single-RHS layout ([nrhs][...]).
  * Nothing here falls back to the CPU: without a usable sm_103a device every
  * entry point that launches work returns HDG_ERR_CUDA.
+ *
+ * Level meshes (Sec. 5.3, local adaptive refinement; hdg_mesh_desc.level)
+ * ------------------------------------------------------------------------
+ * Element e carries its own level r_e (0 <= r_e <= 4, m_e = 2^r_e and the
+ * level-m_e lattice inside); interior edge f carries the level R_f =
+ * max(r+, r-) of its finer side and 2^R_f p + 1 trace dofs (C0 P_p on 2^R_f
+ * sub-edges, along its orientation); a boundary edge has its element's
+ * level. Every per-element or per-edge array is ragged, concatenated in
+ * element (edge) order with the prefix sums hdg_offsets returns:
+ *   trace vectors:   edge f's dofs at HDG_OFF_TRACE[f];  N_tr = last entry;
+ *   source points:   element e's m_e^2 (p + 2)^2 points (the uniform-level
+ *                    order of that level) at HDG_OFF_SOURCE[e];
+ *   Dirichlet data:  boundary edge b's 2^r_b (p + 2) points at HDG_OFF_DIRICHLET_POINTS[b];
+ *   u:               element e's Q_e lattice values at HDG_OFF_LATTICE[e];
+ *   q:               element e's [2][Q_e] at 2 HDG_OFF_LATTICE[e];
+ *   Schur blocks:    element e's n_t,e x n_t,e block (row-major, local trace
+ *                    dofs face by face in the element's own edge orientation)
+ *                    at HDG_OFF_SCHUR[e].
+ * Several right-hand sides stack those arrays (RHS-major). On a level mesh
+ * hdg_run_host, hdg_condense_static, hdg_autotune, hdg_set_kappa and the
+ * adjoint entry points return HDG_ERR_ARG.
  */
 #ifndef MEHDG_H
 #define MEHDG_H
@@ -99,6 +120,9 @@ typedef struct {
                             tau_s = h / (2 |a|) (coth Pe - 1 / Pe), Pe = |a| h / (2 kappa), h the
                             sub-triangle diameter (the printed formula's "+ 1/Pe" read as "- 1/Pe").
                             hdg_gradient refuses SUPG (its terms are not affine in kappa). */
+  const int8_t* level;   /* host pointer, N refinement levels r_e in 0 .. 4 (m_e = 2^r_e), or NULL for the
+                            uniform level m; with levels, m is ignored and every level present must fit the
+                            same shared-memory bound as m (see the level-mesh conventions above) */
 } hdg_mesh_desc;
 
 typedef struct {
@@ -112,6 +136,11 @@ typedef struct {
   int64_t n_bqp;         /* Dirichlet-data points per boundary edge */
   size_t device_bytes;   /* device memory currently held by the context */
   int64_t launches;      /* CUDA kernels this context has enqueued since hdg_create */
+  int64_t levels;        /* 1 on a level mesh (Q, n_t: the largest element's; n_qp = n_bqp = 0), else 0 */
+  int64_t n_qp_total;    /* source points per right-hand side */
+  int64_t n_bqp_total;   /* Dirichlet-data points per right-hand side */
+  int64_t n_u_total;     /* lattice values of u per right-hand side */
+  int64_t n_s_total;     /* Schur-block entries */
 } hdg_info_t;
 
 /* Solve options. Every restart cycle starts from the true FP64 residual
@@ -159,8 +188,25 @@ hdg_status hdg_create(const hdg_mesh_desc* desc, void* stream, hdg_ctx** out);
 /* Sizes of the problem and the context's device memory (host struct). */
 hdg_status hdg_info(const hdg_ctx* ctx, hdg_info_t* out);
 
+/* Prefix sums of a ragged layout (host array, count + 1 entries): which =
+ * HDG_OFF_SOURCE (per element: source points, N + 1), HDG_OFF_DIRICHLET_POINTS
+ * (per boundary edge: Dirichlet-data points, 4 n + 1), HDG_OFF_LATTICE (per
+ * element: lattice nodes, N + 1), HDG_OFF_TRACE (per interior edge: trace
+ * dofs, n_int_edges + 1), HDG_OFF_SCHUR (per element: Schur-block entries,
+ * N + 1), HDG_OFF_DIRICHLET_TRACE (per boundary edge: projected Dirichlet
+ * trace values, 4 n + 1). Uniform meshes give the regular sums.
+ * Errors: HDG_ERR_ARG for an unknown table. */
+#define HDG_OFF_SOURCE 0
+#define HDG_OFF_DIRICHLET_POINTS 1
+#define HDG_OFF_LATTICE 2
+#define HDG_OFF_TRACE 3
+#define HDG_OFF_SCHUR 4
+#define HDG_OFF_DIRICHLET_TRACE 5
+hdg_status hdg_offsets(const hdg_ctx* ctx, int which, int64_t* out_host);
+
 /* Physical coordinates of the source quadrature points, [N][n_qp][2] FP64
- * device array (layout in the header comment). The caller evaluates f there. */
+ * device array (layout in the header comment; ragged on a level mesh). The
+ * caller evaluates f there. */
 hdg_status hdg_quad_points(const hdg_ctx* ctx, double* xy_dev);
 
 /* Physical coordinates of the Dirichlet-data points, [4 n][n_bqp][2] FP64. */
@@ -215,7 +261,8 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double*
 
 /* Copy the FP64 Schur blocks S_e of elements e0 .. e0+count-1 into S_dev as
  * row-major [count][n_t][n_t] (element-local trace order: local edge k,
- * then position along the edge from v_{k+1} to v_{k+2}). */
+ * then position along the edge from v_{k+1} to v_{k+2}). On a level mesh the
+ * blocks are ragged: element e's at HDG_OFF_SCHUR[e] - HDG_OFF_SCHUR[e0]. */
 hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
 
 /* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to

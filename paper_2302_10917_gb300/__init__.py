@@ -24,7 +24,7 @@ EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", 
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
             "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_set_kappa",
             "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_autotune",
-            "hdg_last_error",
+            "hdg_offsets", "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 PROF_PHASES = ["condense", "apply", "ortho", "recover", "apply32", "resid", "adjoint"]
@@ -34,14 +34,20 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("p", ctypes.c_int),
                 ("beta", ctypes.c_double * 2), ("kappa0", ctypes.c_double),
                 ("kappa", ctypes.POINTER(ctypes.c_double)), ("tau_len", ctypes.c_double),
-                ("bc", ctypes.c_int * 4), ("supg", ctypes.c_int)]
+                ("bc", ctypes.c_int * 4), ("supg", ctypes.c_int), ("level", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("Q", ctypes.c_int64), ("n_t", ctypes.c_int64),
                 ("N_tr", ctypes.c_int64), ("n_int_edges", ctypes.c_int64),
                 ("n_bnd_edges", ctypes.c_int64), ("n_qp", ctypes.c_int64), ("n_bqp", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int64), ("levels", ctypes.c_int64),
+                ("n_qp_total", ctypes.c_int64), ("n_bqp_total", ctypes.c_int64), ("n_u_total", ctypes.c_int64),
+                ("n_s_total", ctypes.c_int64)]
+
+
+# ragged-layout tables of hdg_offsets
+OFF_SOURCE, OFF_DIRICHLET_POINTS, OFF_LATTICE, OFF_TRACE, OFF_SCHUR, OFF_DIRICHLET_TRACE = range(6)
 
 
 class SolveOpts(ctypes.Structure):
@@ -90,6 +96,7 @@ def load_library(path=LIB_PATH):
     vp, dp, i64 = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64
     lib.hdg_create.argtypes = [ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)]
     lib.hdg_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.hdg_offsets.argtypes = [vp, ctypes.c_int, dp]
     lib.hdg_quad_points.argtypes = [vp, dp]
     lib.hdg_bnd_quad_points.argtypes = [vp, dp]
     lib.hdg_set_source.argtypes = [vp, dp, dp, ctypes.c_int]
@@ -125,10 +132,14 @@ def _ptr(t):
 
 
 class Problem:
-    """One macro-element HDG problem on the structured unit-square mesh (one GPU)."""
+    """One macro-element HDG problem on the structured unit-square mesh (one GPU).
+
+    levels: None (every element of level m), or N per-element refinement levels r_e in 0..4
+    (m_e = 2^r_e; faces at the finer side's level, Sec. 5.3). On such a level mesh every
+    per-element array is ragged (flat, element-ordered; offsets())."""
 
     def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, device="cuda:0", stream=None,
-                 supg=False):
+                 supg=False, levels=None):
         self.lib = load_library()
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -148,6 +159,15 @@ class Problem:
         for s in range(4):
             d.bc[s] = 0
         d.supg = 1 if supg else 0
+        self._level_host = None
+        if levels is not None:
+            lv = torch.as_tensor(levels).to(torch.int8).contiguous().cpu()
+            if lv.numel() != 2 * n * n:
+                raise ValueError("levels: one entry per macro-element (2 n^2)")
+            self._level_host = lv
+            d.level = ctypes.c_void_p(lv.data_ptr())
+        else:
+            d.level = ctypes.c_void_p(0)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = self.lib.hdg_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
@@ -162,6 +182,7 @@ class Problem:
         self._check(self.lib.hdg_info(self.h, ctypes.byref(info)))
         self.info = {k: getattr(info, k) for k, _ in Info._fields_}
         self.n, self.m, self.p = n, m, p
+        self.levels = self.info["levels"] == 1
         self._src = None
         self.nrhs = 1
         self.version = 0        # bumped by every condensation (the factors the adjoint reuses)
@@ -202,13 +223,29 @@ class Problem:
             pass
 
     # ------------------------------------------------------------------- API
+    def offsets(self, which):
+        """Prefix sums of a ragged layout (OFF_* table), host int64 tensor."""
+        count = {OFF_SOURCE: self.info["N"], OFF_LATTICE: self.info["N"], OFF_SCHUR: self.info["N"],
+                 OFF_TRACE: self.info["n_int_edges"], OFF_DIRICHLET_POINTS: self.info["n_bnd_edges"],
+                 OFF_DIRICHLET_TRACE: self.info["n_bnd_edges"]}[which]
+        out = torch.empty(count + 1, dtype=torch.int64)
+        self._check(self.lib.hdg_offsets(self.h, which, _ptr(out)))
+        return out
+
     def quad_points(self):
-        xy = self._f64(self.info["N"], self.info["n_qp"], 2)
+        """[N, n_qp, 2]; on a level mesh [n_qp_total, 2] (element e's at offsets(OFF_SOURCE)[e])."""
+        if self.levels:
+            xy = self._f64(self.info["n_qp_total"], 2)
+        else:
+            xy = self._f64(self.info["N"], self.info["n_qp"], 2)
         self._check(self.lib.hdg_quad_points(self.h, _ptr(xy)))
         return xy
 
     def bnd_quad_points(self):
-        xy = self._f64(self.info["n_bnd_edges"], self.info["n_bqp"], 2)
+        if self.levels:
+            xy = self._f64(self.info["n_bqp_total"], 2)
+        else:
+            xy = self._f64(self.info["n_bnd_edges"], self.info["n_bqp"], 2)
         self._check(self.lib.hdg_bnd_quad_points(self.h, _ptr(xy)))
         return xy
 
@@ -216,7 +253,8 @@ class Problem:
         """f_qp: [N, n_qp] (one source) or [nrhs, N, n_qp]; gD_qp likewise ([4n, n_bqp] or
         [nrhs, 4n, n_bqp]) or None."""
         f_qp = f_qp.to(self.device, torch.float64).contiguous()
-        nrhs = 1 if f_qp.dim() == 2 else f_qp.shape[0]
+        one = 1 if self.levels else 2          # dimensions of one source
+        nrhs = 1 if f_qp.dim() == one else f_qp.shape[0]
         gD_qp = None if gD_qp is None else gD_qp.to(self.device, torch.float64).contiguous()
         self._src = (f_qp, gD_qp)       # keep alive until condense / recover
         self.nrhs = nrhs
@@ -271,14 +309,24 @@ class Problem:
         N, Q = self.info["N"], self.info["Q"]
         nrhs = 1 if x.dim() == 1 else x.shape[0]
         lead = () if x.dim() == 1 else (nrhs,)
-        u = self._f64(*lead, N, Q)
-        q = self._f64(*lead, N, 2, Q)
+        if self.levels:
+            # ragged: u [n_u_total], q [2 n_u_total] (element e's [2][Q_e] at 2 offsets(OFF_LATTICE)[e])
+            u = self._f64(*lead, self.info["n_u_total"])
+            q = self._f64(*lead, 2 * self.info["n_u_total"])
+        else:
+            u = self._f64(*lead, N, Q)
+            q = self._f64(*lead, N, 2, Q)
         self._check(self.lib.hdg_recover(self.h, _ptr(x), _ptr(u), _ptr(q), nrhs))
         return u, q
 
     def schur(self, e0=0, count=None):
+        """[count, n_t, n_t]; on a level mesh the ragged blocks flat (offsets(OFF_SCHUR))."""
         count = self.info["N"] - e0 if count is None else count
-        S = self._f64(count, self.info["n_t"], self.info["n_t"])
+        if self.levels:
+            off = self.offsets(OFF_SCHUR)
+            S = self._f64(int(off[e0 + count] - off[e0]))
+        else:
+            S = self._f64(count, self.info["n_t"], self.info["n_t"])
         self._check(self.lib.hdg_get_schur(self.h, e0, count, _ptr(S)))
         return S
 

@@ -83,11 +83,12 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory one CTA may use on sm_103a
 
+}  // namespace
+
+namespace mehdg {
 // Copy the host tables into one device allocation.
-cudaError_t upload_tables(hdg_ctx* c) {
-  const RefTables& T = c->ref;
+cudaError_t upload_ref_tables(const RefTables& T, DevTables& d, void** dmem, size_t* bytes, cudaStream_t st) {
   struct Item { const void* src; size_t bytes; void** dst; };
-  DevTables& d = c->dt;
   std::vector<Item> items = {
       {T.Dxi.data(), T.Dxi.size() * 8, (void**)&d.Dxi},   {T.Deta.data(), T.Deta.size() * 8, (void**)&d.Deta},
       {T.Kxx.data(), T.Kxx.size() * 8, (void**)&d.Kxx},   {T.Kyy.data(), T.Kyy.size() * 8, (void**)&d.Kyy},
@@ -131,21 +132,29 @@ cudaError_t upload_tables(hdg_ctx* c) {
   }
   size_t total = 0;
   for (auto& it : items) total += round_up(it.bytes, 256);
-  cudaError_t e = cudaMalloc(&c->d_tables, total);
+  cudaError_t e = cudaMalloc(dmem, total);
   if (e != cudaSuccess) return e;
-  c->bytes += total;
+  *bytes = total;
   std::vector<unsigned char> host(total, 0);
   size_t off = 0;
   for (auto& it : items) {
-    std::memcpy(host.data() + off, it.src, it.bytes);
-    *it.dst = (unsigned char*)c->d_tables + off;
+    if (it.bytes) std::memcpy(host.data() + off, it.src, it.bytes);
+    *it.dst = (unsigned char*)*dmem + off;
     off += round_up(it.bytes, 256);
   }
-  e = cudaMemcpyAsync(c->d_tables, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+  e = cudaMemcpyAsync(*dmem, host.data(), total, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(c->stream);
+  return cudaStreamSynchronize(st);
 }
+}  // namespace mehdg
 
+namespace {
+cudaError_t upload_tables(hdg_ctx* c) {
+  size_t b = 0;
+  cudaError_t e = upload_ref_tables(c->ref, c->dt, &c->d_tables, &b, c->stream);
+  c->bytes += b;
+  return e;
+}
 }  // namespace
 
 namespace mehdg {
@@ -171,17 +180,23 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if (!out) return HDG_ERR_ARG;
   *out = nullptr;
   if (!d) return HDG_ERR_ARG;
-  if (d->n < 1 || d->n > 1448 || d->m < 1 || d->m > 16 || d->p < 1 || d->p > 4) return HDG_ERR_ARG;
+  const int64_t N = 2LL * d->n * d->n;
+  if (d->n < 1 || d->n > 1448 || d->p < 1 || d->p > 4) return HDG_ERR_ARG;
+  if (d->level) {
+    for (int64_t e = 0; e < N; ++e)
+      if (d->level[e] < 0 || d->level[e] > kMaxLevel) return HDG_ERR_ARG;
+  } else if (d->m < 1 || d->m > 16) {
+    return HDG_ERR_ARG;
+  }
   if (!(d->tau_len > 0.0) || !std::isfinite(d->beta[0]) || !std::isfinite(d->beta[1])) return HDG_ERR_ARG;
   for (int s = 0; s < 4; ++s)
     if (d->bc[s] != 0) return HDG_ERR_ARG;
   if (d->supg != 0 && d->supg != 1) return HDG_ERR_ARG;
-  const int64_t N = 2LL * d->n * d->n;
   if (!d->kappa && !(d->kappa0 >= 0.0 && std::isfinite(d->kappa0))) return HDG_ERR_ARG;
   if (d->kappa)
     for (int64_t e = 0; e < N; ++e)
       if (!(d->kappa[e] >= 0.0) || !std::isfinite(d->kappa[e])) return HDG_ERR_ARG;
-  const int P_ = d->m * d->p;
+  const int P_ = (d->level ? (1 << kMaxLevel) : d->m) * d->p;
   const int64_t n_int = (int64_t)d->n * d->n + 2LL * d->n * (d->n - 1);
   if (n_int * (P_ + 1) > 0x7fffffffLL) return HDG_ERR_ARG;
 
@@ -193,6 +208,20 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if (e != cudaSuccess || ndev == 0) {
     *out = c;
     return set_err(c, HDG_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (d->level) {
+    // per-element refinement levels: kappa here, everything else in the level mesh
+    *out = c;
+    std::vector<double> kap(N, d->kappa0);
+    if (d->kappa) std::copy(d->kappa, d->kappa + N, kap.begin());
+    if ((e = dev_alloc(c, &c->d_kappa, N)) != cudaSuccess) return cuda_err(c, e, "kappa");
+    if ((e = cudaMemcpyAsync(c->d_kappa, kap.data(), N * 8, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+      return cuda_err(c, e, "kappa upload");
+    const hdg_status s = level_create(c, d);
+    if (s != HDG_OK) return s;
+    c->alloc_nrhs = 0;
+    c->d_tables = c->lv->d_mem;   // marks the context initialised (owned by the level mesh)
+    return HDG_OK;
   }
   try {
     build_reference_tables(d->m, d->p, c->ref);
@@ -245,13 +274,73 @@ hdg_status hdg_info(const hdg_ctx* c, hdg_info_t* out) {
   out->n_int_edges = P.n_int; out->n_bnd_edges = P.n_bnd; out->n_qp = P.n_qp; out->n_bqp = P.n_bqp;
   out->device_bytes = c->bytes;
   out->launches = c->launches;
+  if (c->lv) {
+    const LevelMesh& L = *c->lv;
+    int64_t qmax = 0;
+    for (int64_t e = 0; e < P.N; ++e) qmax = std::max(qmax, L.uoff[e + 1] - L.uoff[e]);
+    out->Q = qmax;
+    out->n_qp = 0;
+    out->n_bqp = 0;
+    out->levels = 1;
+    out->n_qp_total = L.qoff.back();
+    out->n_bqp_total = L.boff.back();
+    out->n_u_total = L.uoff.back();
+    out->n_s_total = L.ns;
+  } else {
+    out->levels = 0;
+    out->n_qp_total = (int64_t)P.N * P.n_qp;
+    out->n_bqp_total = (int64_t)P.n_bnd * P.n_bqp;
+    out->n_u_total = (int64_t)P.N * P.Q;
+    out->n_s_total = (int64_t)P.N * P.n_t * P.n_t;
+  }
   return HDG_OK;
+}
+
+hdg_status hdg_offsets(const hdg_ctx* cc, int which, int64_t* out) {
+  hdg_ctx* c = const_cast<hdg_ctx*>(cc);
+  if (!c || !out) return HDG_ERR_ARG;
+  if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  const Params& P = c->prm;
+  const LevelMesh* L = c->lv;
+  auto fill = [&](int64_t count, auto size_of) {
+    out[0] = 0;
+    for (int64_t i = 0; i < count; ++i) out[i + 1] = out[i] + size_of(i);
+  };
+  switch (which) {
+    case HDG_OFF_SOURCE:
+      if (L) std::copy(L->qoff.begin(), L->qoff.end(), out);
+      else fill(P.N, [&](int64_t) { return (int64_t)P.n_qp; });
+      return HDG_OK;
+    case HDG_OFF_DIRICHLET_POINTS:
+      if (L) std::copy(L->boff.begin(), L->boff.end(), out);
+      else fill(P.n_bnd, [&](int64_t) { return (int64_t)P.n_bqp; });
+      return HDG_OK;
+    case HDG_OFF_LATTICE:
+      if (L) std::copy(L->uoff.begin(), L->uoff.end(), out);
+      else fill(P.N, [&](int64_t) { return (int64_t)P.Q; });
+      return HDG_OK;
+    case HDG_OFF_TRACE:
+      if (L) std::copy(L->eoff.begin(), L->eoff.end(), out);
+      else fill(P.n_int, [&](int64_t) { return (int64_t)P.P1; });
+      return HDG_OK;
+    case HDG_OFF_SCHUR:
+      if (L) fill(P.N, [&](int64_t e) { return (int64_t)L->nt_e[e] * L->nt_e[e]; });
+      else fill(P.N, [&](int64_t) { return (int64_t)P.n_t * P.n_t; });
+      return HDG_OK;
+    case HDG_OFF_DIRICHLET_TRACE:
+      if (L) std::copy(L->goff.begin(), L->goff.end(), out);
+      else fill(P.n_bnd, [&](int64_t) { return (int64_t)P.P1; });
+      return HDG_OK;
+    default:
+      return set_err(c, HDG_ERR_ARG, "unknown offset table");
+  }
 }
 
 hdg_status hdg_quad_points(const hdg_ctx* cc, double* xy) {
   hdg_ctx* c = const_cast<hdg_ctx*>(cc);
   if (!c || !xy) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  if (c->lv) return level_quad_points(c, xy);
   quad_points_kernel<<<1024, 256, 0, c->stream>>>(c->prm, c->dt, xy);
   c->launches += 1;
   cudaError_t e = cudaGetLastError();
@@ -262,6 +351,7 @@ hdg_status hdg_bnd_quad_points(const hdg_ctx* cc, double* xy) {
   hdg_ctx* c = const_cast<hdg_ctx*>(cc);
   if (!c || !xy) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
+  if (c->lv) return level_bnd_quad_points(c, xy);
   bnd_points_kernel<<<64, 256, 0, c->stream>>>(c->prm, c->dt, xy);
   c->launches += 1;
   cudaError_t e = cudaGetLastError();
@@ -273,6 +363,7 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
   if (!f_qp || nrhs < 1 || nrhs > HDG_MAX_RHS)
     return set_err(c, HDG_ERR_ARG, "f_qp must be a device pointer and 1 <= nrhs <= HDG_MAX_RHS");
+  if (c->lv) return level_set_source(c, f_qp, gD_qp, nrhs);
   Params& P = c->prm;
   cudaError_t e = cudaSuccess;
   if (nrhs != c->alloc_nrhs) {
@@ -319,6 +410,7 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
   if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE))
     return set_err(c, HDG_ERR_ARG, "unknown flags");
+  if (c->lv) return level_condense(c, flags);
   const int split = (flags & HDG_SPLIT_UPDATE) ? 1 : 0;
   const Params& P = c->prm;
   cudaError_t e;
@@ -402,6 +494,25 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
   cudaError_t e;
   ProfScope ps(c, prec == 32 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY);
+  if (c->lv) {
+    const LevelMesh& L = *c->lv;
+    if ((e = level_ensure_z(c, nrhs)) != cudaSuccess) return cuda_err(c, e, "element-side buffer");
+    const int64_t n = c->prm.N_tr;
+    if (prec == 64) {
+      e = launch_level_apply(c, 0, 0, precond ? L.d_St : L.d_S, x, y, nrhs, n, precond ? c->d_escale : nullptr,
+                             nullptr, c->stream);
+    } else if (prec == 48) {
+      if (!L.d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
+      e = launch_level_apply(c, 1, 0, L.d_Stdf, x, y, nrhs, n, c->d_escale, nullptr, c->stream);
+    } else if (prec == 32) {
+      if (!L.d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
+      e = launch_level_apply(c, 2, 2, L.d_St32, x, y, nrhs, n, c->d_escale, nullptr, c->stream);
+    } else {
+      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
+    }
+    c->launches += 2;
+    return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
+  }
   if (nrhs > 1) {
     // multi-RHS apply: every block streamed once for all columns
     const Params& P = c->prm;
@@ -444,9 +555,15 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
       o->orth < 0 || o->orth > 1)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
-  if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
+  const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
+  const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
+  if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)
-  if (o->mode == 2 && !c->d_Stdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  if (c->lv) {
+    const cudaError_t e = level_ensure_z(c, nrhs);
+    if (e != cudaSuccess) return cuda_err(c, e, "element-side buffer");
+  }
   hdg_solve_report r{};
   const hdg_status s = nrhs == 1 ? gmres_solve(c, g, x, *o, r) : gmres_solve_batched(c, g, x, nrhs, *o, r);
   if (rep) *rep = r;
@@ -457,6 +574,7 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
   if (!c) return HDG_ERR_ARG;
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_autotune: not available on a level mesh");
   if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
@@ -471,6 +589,7 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_recover before hdg_condense");
   const Params& P = c->prm;
   if (nrhs != P.nrhs) return set_err(c, HDG_ERR_ARG, "nrhs must equal the nrhs of hdg_set_source");
+  if (c->lv) return level_recover(c, x, u, q, nrhs);
   cudaError_t e;
   // column r: x_r, g^_r, u_r, q_r at r * (one RHS) offsets
   auto rec = [&](int64_t e0, int64_t cnt, int slot_is_element, int r) {
@@ -507,6 +626,7 @@ hdg_status hdg_get_schur(hdg_ctx* c, int64_t e0, int64_t count, double* S) {
   if (!c) return HDG_ERR_ARG;
   if (!S || e0 < 0 || count < 1 || e0 + count > c->prm.N) return set_err(c, HDG_ERR_ARG, "bad element range");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_get_schur before hdg_condense");
+  if (c->lv) return level_get_schur(c, e0, count, S);
   cudaError_t e = launch_get_schur(c->prm, c->d_S, e0, count, S, c->stream);
   c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_get_schur");
@@ -516,6 +636,7 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
                         double* x_host, double* u_host, double* q_host, hdg_solve_report* rep) {
   if (!c) return HDG_ERR_ARG;
   if (!f_host || !o) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_run_host: not available on a level mesh");
   const Params& P = c->prm;
   const size_t nf = (size_t)P.N * P.n_qp, ng = (size_t)P.n_bnd * P.n_bqp;
   const size_t nu = (size_t)P.N * P.Q;
@@ -568,6 +689,7 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
 hdg_status hdg_set_kappa(hdg_ctx* c, const double* kappa) {
   if (!c) return HDG_ERR_ARG;
   if (!kappa) return set_err(c, HDG_ERR_ARG, "kappa must be a device pointer");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_set_kappa: not available on a level mesh");
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
   cudaError_t e;
   if (!c->d_bad && (e = dev_alloc(c, &c->d_bad, 1)) != cudaSuccess) return cuda_err(c, e, "kappa check");
@@ -586,6 +708,7 @@ hdg_status hdg_set_kappa(hdg_ctx* c, const double* kappa) {
 
 hdg_status hdg_transpose(hdg_ctx* c) {
   if (!c) return HDG_ERR_ARG;
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_transpose: not available on a level mesh");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_transpose before hdg_condense");
   ProfScope ps(c, HDG_PROF_ADJOINT);
   cudaError_t e = launch_transpose(c->prm, c->dt, c->d_S, c->d_St, c->d_St32, c->d_Stdf, c->stream);
@@ -598,6 +721,7 @@ hdg_status hdg_transpose(hdg_ctx* c) {
 hdg_status hdg_adjoint_rhs(hdg_ctx* c, const double* r, double* g) {
   if (!c) return HDG_ERR_ARG;
   if (!r || !g) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_adjoint_rhs: not available on a level mesh");
   if (c->state < 2 || !(c->flags & HDG_KEEP_FACTORS) || !c->d_piv)
     return set_err(c, HDG_ERR_STATE, "hdg_adjoint_rhs needs hdg_condense with HDG_KEEP_FACTORS");
   const Params& P = c->prm;
@@ -616,6 +740,7 @@ hdg_status hdg_adjoint_rhs(hdg_ctx* c, const double* r, double* g) {
 hdg_status hdg_adjoint_recover(hdg_ctx* c, const double* r, const double* nu, double* mu) {
   if (!c) return HDG_ERR_ARG;
   if (!r || !nu || !mu) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_adjoint_recover: not available on a level mesh");
   if (c->state < 2 || !(c->flags & HDG_KEEP_FACTORS) || !c->d_piv)
     return set_err(c, HDG_ERR_STATE, "hdg_adjoint_recover needs hdg_condense with HDG_KEEP_FACTORS");
   ProfScope ps(c, HDG_PROF_ADJOINT);
@@ -628,6 +753,7 @@ hdg_status hdg_gradient(hdg_ctx* c, const double* x, const double* u, const doub
                         double* dkappa, double* df) {
   if (!c) return HDG_ERR_ARG;
   if (!x || !u || !mu || !nu || !dkappa) return set_err(c, HDG_ERR_ARG, "bad arguments");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_gradient: not available on a level mesh");
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_gradient before hdg_set_source");
   if (c->prm.supg) return set_err(c, HDG_ERR_STATE, "hdg_gradient: SUPG terms are not affine in kappa");
   ProfScope ps(c, HDG_PROF_ADJOINT);
@@ -661,6 +787,10 @@ void hdg_destroy(hdg_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   profile_collect(c);
   for (auto& pr : c->prof_pool) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (c->lv) {
+    level_destroy(c);    // also releases d_tables' target and the face scales
+    c->d_tables = nullptr;
+  }
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
   cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);

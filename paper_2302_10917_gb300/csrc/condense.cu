@@ -50,9 +50,17 @@ struct CondArgs {
   int* info;
   int split_update;       // 1: condense_df_kernel (split-FP32 elimination on the FP32 pipe)
   int* piv;               // [N][Q] pivot row of every column (factors kept), or null
+  // one refinement level of a level mesh: the launch covers slots e0.. of the
+  // element list elist (outputs, workspace, info and pivots by slot; geometry,
+  // kappa, sources and Dirichlet data by element id), nslots slots in all
+  const int* elist;       // null: slot = element id
+  int64_t nslots;         // slots of the outputs (N without a list)
+  const int64_t* qoff;    // first source point of every element, or null (e n_qp)
+  int64_t fstride;        // source values per right-hand side (N n_qp without qoff)
 };
 
-__device__ void condense_outputs(const CondArgs& a, const double* W, int e);
+__device__ void condense_outputs(const CondArgs& a, const double* W, int e, int eb);
+static cudaError_t launch_condense_args(CondArgs& a, int64_t count, cudaStream_t st);
 
 // The load columns of element e, one source at a time: per sub-triangle
 // projections of f_r (FP64, in proj: nsub * nloc doubles of shared memory)
@@ -66,7 +74,7 @@ __device__ void load_columns(const CondArgs& a, int e, double detJ, double* proj
   const int tid = threadIdx.x, nthr = blockDim.x;
   const double scale = detJ / (double)(P.m * P.m);
   for (int r = 0; r < P.nrhs; ++r) {
-    const double* fe = a.f_qp + ((size_t)r * P.N + e) * P.n_qp;
+    const double* fe = a.f_qp + (size_t)r * a.fstride + (a.qoff ? a.qoff[e] : (int64_t)e * P.n_qp);
     for (int idx = tid; idx < P.nsub * P.nloc; idx += nthr) {
       const int s = idx / P.nloc, b = idx - s * P.nloc;
       double acc = 0.0;
@@ -101,11 +109,12 @@ __device__ __forceinline__ void warp_argmax(double& v, int& i) {
 
 __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
   const Params& P = a.prm;
-  const int e = (int)(a.e0 + blockIdx.x);
-  if (e >= P.N) return;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, Cc = P.Cc, ld = P.ld;
-  double* W = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)R * ld;
+  double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)R * ld;
 
   extern __shared__ double smem[];
   double* Ls = smem;                       // [R][LDP]
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
       if (a.piv) {
         // kept factors: record the interchange and apply it to the columns of
         // the earlier panels too, so that rows 0..Q-1 hold P A_u = L U
-        if (tid == 0) a.piv[(size_t)e * Q + j0 + c] = j0 + pr;
+        if (tid == 0) a.piv[(size_t)eb * Q + j0 + c] = j0 + pr;
         if (pr != c)
           for (int cc = tid; cc < j0; cc += nthr) {
             double* x0 = W + (size_t)(j0 + c) * ld + cc;
@@ -325,25 +334,25 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     }
     __syncthreads();
   }
-  if (tid == 0 && a.info) a.info[e] = singular_col >= 0 ? singular_col + 1 : 0;
-  if (a.write_outputs) condense_outputs(a, W, e);
+  if (tid == 0 && a.info) a.info[eb] = singular_col >= 0 ? singular_col + 1 : 0;
+  if (a.write_outputs) condense_outputs(a, W, e, eb);
 }
 
 // S_e, its preconditioned copies and the element right-hand side from the
 // factored bordered system (FP64 entries).
-__device__ void condense_outputs(const CondArgs& a, const double* W, int e) {
+__device__ void condense_outputs(const CondArgs& a, const double* W, int e, int eb) {
   const Params& P = a.prm;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int Q = P.Q, nt = P.n_t, P1 = P.P1, ld = P.ld;
-  // S_e row-blocks per local edge: S[e][k][j][t] = S_e(k P1 + t, j)
-  const size_t sb = (size_t)e * 3 * nt * P1;
+  // S_e row-blocks per local edge: S[eb][k][j][t] = S_e(k P1 + t, j)
+  const size_t sb = (size_t)eb * 3 * nt * P1;
   for (int idx = tid; idx < nt * nt; idx += nthr) {
     const int j = idx / nt, r = idx - j * nt;
     const int k = r / P1, t = r - k * P1;
     a.S[sb + ((size_t)k * nt + j) * P1 + t] = W[(size_t)(Q + r) * ld + Q + j];
   }
   // preconditioned rows: Gh^-1 applied to each edge block of rows
-  for (int idx = tid; idx < nt * nt; idx += nthr) {
+  for (int idx = tid; a.St && idx < nt * nt; idx += nthr) {
     const int j = idx / nt, r = idx - j * nt;
     const int k = r / P1, t = r - k * P1;
     double acc = 0.0;
@@ -367,7 +376,7 @@ __device__ void condense_outputs(const CondArgs& a, const double* W, int e) {
           acc -= W[(size_t)(Q + r) * ld + Q + k * P1 + t] * gb[flip[k] ? P.P - t : t];
       }
     }
-    a.gel[((size_t)rr * P.N + e) * nt + r] = acc;
+    a.gel[((size_t)rr * a.nslots + eb) * nt + r] = acc;
   }
 }
 
@@ -401,11 +410,12 @@ __device__ __forceinline__ void warp_argmax_f(float& v, int& i) {
 
 __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
   const Params& P = a.prm;
-  const int e = (int)(a.e0 + blockIdx.x);
-  if (e >= P.N) return;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, Cc = P.Cc, ld = P.ld;
-  double* Wd = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)R * ld;
+  double* Wd = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)R * ld;
   float2* W = reinterpret_cast<float2*>(Wd);
 
   extern __shared__ double smem[];
@@ -552,7 +562,7 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
       __syncthreads();
       const int pr = piv_s[c];
       if (a.piv) {
-        if (tid == 0) a.piv[(size_t)e * Q + j0 + c] = j0 + pr;
+        if (tid == 0) a.piv[(size_t)eb * Q + j0 + c] = j0 + pr;
         if (pr != c)
           for (int cc = tid; cc < j0; cc += nthr) {
             float2* x0 = W + (size_t)(j0 + c) * ld + cc;
@@ -675,8 +685,8 @@ __global__ void __launch_bounds__(256) condense_df_kernel(CondArgs a) {
     Wd[o] = df_to(W[o]);
   }
   __syncthreads();
-  if (tid == 0 && a.info) a.info[e] = singular_col >= 0 ? singular_col + 1 : 0;
-  if (a.write_outputs) condense_outputs(a, Wd, e);
+  if (tid == 0 && a.info) a.info[eb] = singular_col >= 0 ? singular_col + 1 : 0;
+  if (a.write_outputs) condense_outputs(a, Wd, e, eb);
 }
 
 // Back-solve Eq. (local_matrix_problem) on the factored bordered system:
@@ -692,14 +702,21 @@ struct RecArgs {
   const double* ghat;
   double* u;
   double* q;
+  // one refinement level of a level mesh (see CondArgs): slots of elist, the
+  // element traces already gathered (xel [nslots][n_t]) and u, q at uoff[e]
+  const int* elist;
+  int64_t nslots;
+  const double* xel;
+  const int64_t* uoff;
 };
 
 __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
   const Params& P = a.prm;
-  const int e = (int)(a.e0 + blockIdx.x);
-  if (e >= P.N) return;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
   const int Q = P.Q, nt = P.n_t, P1 = P.P1, ld = P.ld;
-  const double* W = a.ws + (size_t)(a.slot_is_element ? e : blockIdx.x) * (size_t)P.R * ld;
+  const double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)P.R * ld;
   extern __shared__ double sm[];
   double* xe = sm;             // n_t
   double* rhs = xe + nt;       // Q
@@ -712,7 +729,8 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
     const int k = c / P1, t = c - k * P1;
     const int s = flip[k] ? P.P - t : t;
     double v = 0.0;
-    if (code[k] >= 0) v = a.x[(size_t)code[k] * P1 + s];
+    if (a.xel) v = a.xel[(size_t)eb * nt + c];
+    else if (code[k] >= 0) v = a.x[(size_t)code[k] * P1 + s];
     else if (a.ghat) v = a.ghat[(size_t)(-1 - code[k]) * P1 + s];
     xe[c] = v;
   }
@@ -740,8 +758,8 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
   __syncthreads();
   ElemGeom g;
   elem_geom(e, P.n, g);
-  double* ue = a.u + (size_t)e * Q;
-  double* qe = a.q + (size_t)e * 2 * Q;
+  double* ue = a.u + (a.uoff ? a.uoff[e] : (int64_t)e * Q);
+  double* qe = a.q + 2 * (a.uoff ? a.uoff[e] : (int64_t)e * Q);
   for (int i = warp; i < Q; i += nw) {
     const double* xr = a.dt.Xxi + (size_t)i * Q;
     const double* yr = a.dt.Xeta + (size_t)i * Q;
@@ -774,14 +792,16 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
 }
 
 // Dirichlet data: g^ = L2 projection of g_D on every boundary edge (Sec. 2.3).
-__global__ void project_dirichlet_kernel(Params P, DevTables dt, const double* gD, double* ghat) {
-  const int b = blockIdx.x;
+// blist / boff (a level mesh): the listed boundary edges only, edge b's points at boff[b].
+__global__ void project_dirichlet_kernel(Params P, DevTables dt, const double* gD, double* ghat, const int* blist,
+                                         const int64_t* boff) {
+  const int b = blist ? blist[blockIdx.x] : (int)blockIdx.x;
   if (b >= P.n_bnd) return;
   extern __shared__ double rhs[];
   for (int t = threadIdx.x; t < P.P1; t += blockDim.x) rhs[t] = 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double* gb = gD + (size_t)b * P.n_bqp;
+    const double* gb = gD + (boff ? boff[b] : (int64_t)b * P.n_bqp);
     for (int s = 0; s < P.m; ++s)
       for (int q = 0; q < P.ngb; ++q) {
         const double w = dt.bw[q] / P.m * gb[s * P.ngb + q];
@@ -824,6 +844,13 @@ cudaError_t launch_condense(const Params& P, const DevTables& dt, const double* 
   a.prm = P; a.dt = dt; a.kappa = kappa; a.f_qp = f_qp; a.ghat = ghat; a.ws = ws; a.e0 = e0;
   a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
   a.S = S; a.St = St; a.St32 = St32; a.gel = gel; a.info = info;
+  a.elist = nullptr; a.nslots = P.N; a.qoff = nullptr; a.fstride = (int64_t)P.N * P.n_qp;
+  return launch_condense_args(a, count, st);
+}
+
+static cudaError_t launch_condense_args(CondArgs& a, int64_t count, cudaStream_t st) {
+  const Params& P = a.prm;
+  const int split_update = a.split_update;
   const size_t sm = condense_smem_bytes(P);
   if (split_update) {
     cudaError_t err = cudaFuncSetAttribute(condense_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -843,6 +870,7 @@ cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* w
   RecArgs a;
   a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element; a.rcol = rcol;
   a.x = x; a.ghat = ghat; a.u = u; a.q = q;
+  a.elist = nullptr; a.nslots = P.N; a.xel = nullptr; a.uoff = nullptr;
   const size_t sm = (size_t)(P.n_t + 2 * P.Q) * sizeof(double);
   recover_kernel<<<(unsigned)count, 128, sm, st>>>(a);
   return cudaGetLastError();
@@ -850,7 +878,41 @@ cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* w
 
 cudaError_t launch_project_dirichlet(const Params& P, const DevTables& dt, const double* gD, double* ghat,
                                      cudaStream_t st) {
-  project_dirichlet_kernel<<<P.n_bnd, 64, P.P1 * sizeof(double), st>>>(P, dt, gD, ghat);
+  project_dirichlet_kernel<<<P.n_bnd, 64, P.P1 * sizeof(double), st>>>(P, dt, gD, ghat, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- one refinement level of a level mesh
+cudaError_t launch_condense_bin(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
+                                const int64_t* qoff, int64_t fstride, const double* ghat, double* ws,
+                                const int* elist, int64_t nslots, int64_t e0, int64_t count, int slot_is_element,
+                                int write_outputs, double* S, double* gel, int* info, cudaStream_t st,
+                                int split_update) {
+  CondArgs a;
+  a.prm = P; a.dt = dt; a.kappa = kappa; a.f_qp = f_qp; a.ghat = ghat; a.ws = ws; a.e0 = e0;
+  a.slot_is_element = slot_is_element; a.write_outputs = write_outputs;
+  a.S = S; a.St = nullptr; a.St32 = nullptr; a.gel = gel; a.info = info;
+  a.split_update = split_update; a.piv = nullptr;
+  a.elist = elist; a.nslots = nslots; a.qoff = qoff; a.fstride = fstride;
+  return launch_condense_args(a, count, st);
+}
+
+cudaError_t launch_recover_bin(const Params& P, const DevTables& dt, const double* ws, const int* elist,
+                               int64_t nslots, int64_t e0, int64_t count, int slot_is_element, const double* xel,
+                               const int64_t* uoff, double* u, double* q, cudaStream_t st, int rcol) {
+  RecArgs a;
+  a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element; a.rcol = rcol;
+  a.x = nullptr; a.ghat = nullptr; a.u = u; a.q = q;
+  a.elist = elist; a.nslots = nslots; a.xel = xel; a.uoff = uoff;
+  const size_t sm = (size_t)(P.n_t + 2 * P.Q) * sizeof(double);
+  recover_kernel<<<(unsigned)count, 128, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_dirichlet_bin(const Params& P, const DevTables& dt, const int* blist, int nbnd,
+                                         const int64_t* boff, const double* gD, double* ghat, cudaStream_t st) {
+  if (nbnd <= 0) return cudaSuccess;
+  project_dirichlet_kernel<<<nbnd, 64, P.P1 * sizeof(double), st>>>(P, dt, gD, ghat, blist, boff);
   return cudaGetLastError();
 }
 

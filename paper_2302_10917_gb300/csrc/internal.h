@@ -49,6 +49,18 @@ struct RefTables {
 // Builds the tables of level (m, p). Throws std::runtime_error on failure.
 void build_reference_tables(int m, int p, RefTables& T);
 
+// Trace tables of the face levels of a level mesh (Sec. 5.3), one host array:
+// Gh_R (trace mass on [0,1] with 2^R sub-intervals) at G_off[R], its inverse at
+// Gi_off[R], and for r < R the transfer T_rR ((2^r p + 1) x (2^R p + 1),
+// row-major) at T_off[r][R] (-1 where not defined).
+constexpr int kMaxLevel = 4;
+struct LevelTables {
+  int p = 0;
+  int64_t G_off[kMaxLevel + 1], Gi_off[kMaxLevel + 1], T_off[kMaxLevel + 1][kMaxLevel + 1];
+  std::vector<double> data;
+};
+void build_level_tables(int p, LevelTables& L);
+
 // Device copies of the reference tables (pointers into one allocation).
 struct DevTables {
   double *Dxi, *Deta, *Kxx, *Kyy, *Ksym, *Xxi, *Xeta;
@@ -74,6 +86,36 @@ struct Params {
   int R, Cc, ld;         // bordered local system: rows, used columns, leading dimension
   int nrhs;              // right-hand sides (source columns of the bordered system)
 };
+
+// By-value view of a level mesh for kernels (device pointers).
+// Element-side rows: the n_t,e trace dofs of every element, elements in
+// "apply order" (decreasing n_t,e, then id); element e's rows start at zoff[e]
+// and its blocks (n_t,e x n_t,e, column-major) at soff[e].
+struct LevelDev {
+  int N, n, n_int, p;
+  int64_t N_tr, nz;
+  const int64_t* eoff;        // [n_int + 1] first trace dof of every interior edge
+  const int* dof_edge;        // [N_tr] interior edge of every trace dof
+  const int* ez;              // [n_int][2] element-side row of dof 0 of the face block on each side
+  const int* eflip;           // [n_int] bit s: side s runs against the edge's orientation
+  const signed char* flev;    // [n_int] face level
+  const signed char* elev;    // [N] element level
+  const int* row_ap;          // [nz] apply-order position of the element of every row
+  const int64_t* ap_soff;     // [N] first block entry, by apply-order position
+  const int* ap_zoff;         // [N] first row, by apply-order position
+  const int* ap_nt;           // [N] n_t,e, by apply-order position
+  const int64_t* soff;        // [N] first block entry, by element id
+  const int* zoff;            // [N] first row, by element id
+  const int* xmap;            // [nz] trace dof of every row, -1 on Dirichlet faces
+  const double* tab;          // level tables (LevelTables::data)
+  int64_t G_off[kMaxLevel + 1], Gi_off[kMaxLevel + 1], T_off[kMaxLevel + 1][kMaxLevel + 1];
+  const double* escale;       // [n_int] -1 / ((tau+ + tau-) L_f)
+};
+
+// Face levels of element e from the per-edge and per-element levels.
+__host__ __device__ inline int face_level(const signed char* flev, const signed char* elev, int e, int code) {
+  return code >= 0 ? (int)flev[code] : (int)elev[e];
+}
 
 // ---------------------------------------------------------------------------
 // Structured-mesh geometry (closed form, host and device).
@@ -179,6 +221,51 @@ __host__ __device__ inline void elem_geom(int e, int n, ElemGeom& g) {
   }
 }
 
+
+// One refinement level of a level mesh: the uniform-level tables and the
+// condensation state of the elements of that level.
+struct LevelBin {
+  int r = 0, count = 0, nbnd = 0, max_nt = 0;   // level, elements, boundary edges, largest lifted n_t
+  Params prm;                   // uniform-level parameters (N, n, N_tr as the whole mesh)
+  RefTables ref;
+  DevTables dt;
+  void* d_tables = nullptr;
+  int* d_elist = nullptr;       // [count] element ids, ascending
+  int* d_blist = nullptr;       // [nbnd] boundary edges whose element is in the bin
+  double* d_Sb = nullptr;       // [count][3][n_t][P1] own-level Schur blocks
+  double* d_gelb = nullptr;     // [nrhs][count][n_t] own-level element right-hand sides
+  double* d_ghat = nullptr;     // [nrhs][n_bnd][P1] projected Dirichlet data (the bin's edges)
+  double* d_ws = nullptr;       // factored local systems
+  int64_t ws_slots = 0;
+  int ws_ld = 0;
+  int* d_info = nullptr;
+  double* d_xel = nullptr;      // [count][n_t] own-level traces for the back-solve
+  size_t bytes_S = 0, bytes_gel = 0, bytes_ghat = 0, bytes_ws = 0, bytes_tables = 0;
+};
+
+struct LevelMesh {
+  std::vector<signed char> elev, flev;
+  std::vector<int64_t> eoff, goff, qoff, boff, uoff, soff_e;   // host prefix sums (element / edge order)
+  std::vector<int> zoff_e, nt_e;
+  int64_t nz = 0, ns = 0;
+  int max_nt = 0;
+  LevelTables lt;
+  std::vector<LevelBin> bins;
+  void* d_mem = nullptr;        // one allocation for the index arrays and tables
+  size_t mem_bytes = 0;
+  LevelDev dv;
+  int64_t* d_qoff = nullptr;
+  int64_t* d_boff = nullptr;
+  int64_t* d_uoff = nullptr;
+  int64_t* d_seoff = nullptr;   // [N + 1] n_t,e^2 prefix sums in element order
+  double* d_S = nullptr;        // [ns] lifted Schur blocks
+  double* d_St = nullptr;       // [ns] preconditioned lifted blocks
+  float* d_St32 = nullptr;
+  float2* d_Stdf = nullptr;
+  double* d_gel = nullptr;      // [nrhs][nz] lifted element right-hand sides
+  double* d_z = nullptr;        // [HDG_MAX_RHS][nz] element-side products
+  int z_rhs = 0;
+};
 }  // namespace mehdg
 
 // ---------------------------------------------------------------------------
@@ -239,6 +326,7 @@ struct hdg_ctx {
   std::vector<intptr_t> gm_key;        // configuration the capture is valid for
   cudaStream_t cap_stream = nullptr;   // private stream used only for the capture
   std::vector<cudaEvent_t> gm_ev;      // per-step event quadruples of a timed capture
+  mehdg::LevelMesh* lv = nullptr;     // per-element refinement levels (null: one level m)
   size_t bytes = 0;
   int64_t launches = 0;     // kernels enqueued (reported by hdg_info)
   // per-phase event timing

@@ -463,6 +463,27 @@ static int launch_mdot(const float4* V4, int64_t np, int nv, int ncol, const flo
   return (int)gx;
 }
 
+// The operator of the condensed system: the uniform-level kernels, or the
+// level-mesh kernels (element-side products and a per-face sum).
+static const void* op_blocks(hdg_ctx* c, int mode) {
+  if (c->lv)
+    return mode == 0 ? (const void*)c->lv->d_St : (mode == 2 ? (const void*)c->lv->d_Stdf : (const void*)c->lv->d_St32);
+  return mode == 0 ? (const void*)c->d_St : (mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+}
+
+// y = S x with the unpreconditioned FP64 blocks, nb columns of stride n
+static cudaError_t op_resid(hdg_ctx* c, const double* x, double* y, int nb, int64_t n, cudaStream_t st) {
+  if (c->lv) return launch_level_apply(c, 0, 0, c->lv->d_S, x, y, nb, n, nullptr, nullptr, st);
+  if (nb == 1) return launch_apply64(c->prm, c->d_S, x, y, nullptr, nullptr, st);
+  return launch_apply_mrhs(0, 0, c->prm, c->d_S, x, y, nb, n, nullptr, st);
+}
+
+// z = D^-1 y on one FP64 vector
+static cudaError_t op_dinv(hdg_ctx* c, const double* y, double* z, cudaStream_t st) {
+  if (c->lv) return launch_level_dinv(c, y, z, 1, c->prm.N_tr, st);
+  return launch_face_dinv(c->prm, c->dt.Ghinv, c->d_escale, y, z, st);
+}
+
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
   const Params& P = c->prm;
   const int K = o.restart;
@@ -485,7 +506,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   rep = hdg_solve_report{};
   // Arnoldi operator D^-1 S on split-FP32 vectors
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
-  const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+  const void* Sop = op_blocks(c, o.mode);
   const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
   // launch shapes: the autotuner's choices, else the defaults; the streaming
   // update needs no more than one pass of KT pairs per block
@@ -512,7 +533,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     // true residual with the unpreconditioned FP64 operator (the stopping test)
     {
       ProfScope ps(c, HDG_PROF_RESID);
-      cu.ok(launch_apply64(P, c->d_S, x, r0, nullptr, nullptr, st));
+      cu.ok(op_resid(c, x, r0, 1, n, st));
     }
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, -1.0, r0, t, n, part);
     sum_partials_kernel<<<1, 32, 0, st>>>(part, KG, sm + L.sc + 5);
@@ -528,7 +549,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     }
     if (its >= o.maxit) break;
     // r0 = D^-1 t; V0 = r0 / beta; the cycle aims at the reduction the true residual still needs
-    cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, t, r0, st));
+    cu.ok(op_dinv(c, t, r0, st));
     const double factor = 0.5 * o.tol / rel;
     cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &factor, sizeof(double), cudaMemcpyHostToDevice, st));
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, r0, 0.0, r0, r0, n, part);
@@ -545,7 +566,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s, epb));
+        if (c->lv) cu.ok(launch_level_apply(c, bt, 1, Sop, V + (size_t)j * ldv, w, 1, ldv, c->d_escale, fl, s));
+        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s, epb));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -774,7 +796,8 @@ static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if ((e = cudaMalloc(&c->d_smallb, (size_t)nb * L.total * sizeof(double))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_flagb, (size_t)nb * 4 * sizeof(int))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_scalb, (size_t)nb * 2 * sizeof(double))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&c->d_Zb, (size_t)c->prm.N * nb * c->prm.n_t * sizeof(float2))) != cudaSuccess) return e;
+  const size_t nzb = c->lv ? 1 : (size_t)c->prm.N * nb * c->prm.n_t;   // level meshes use their own buffer
+  if ((e = cudaMalloc(&c->d_Zb, nzb * sizeof(float2))) != cudaSuccess) return e;
   c->kb_restart = K;
   c->kb_nrhs = nb;
   return cudaSuccess;
@@ -803,7 +826,7 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
   int* fl = c->d_flagb;
   double* scal = c->d_scalb;
   const int btype = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
-  const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+  const void* Sop = op_blocks(c, o.mode);
   const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
   const int kgd = c->tune_kgd > 0 ? c->tune_kgd : KGD;
   const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
@@ -836,7 +859,7 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
     // true residuals t_r = g_r - S x_r with the FP64 blocks (multi-RHS apply)
     {
       ProfScope ps(c, HDG_PROF_RESID);
-      cu.ok(launch_apply_mrhs(0, 0, P, c->d_S, x, r0, nb, n, nullptr, st));
+      cu.ok(op_resid(c, x, r0, nb, n, st));
       c->launches += 1;
     }
     norms(g, n, 1.0, r0, -1.0, t);
@@ -870,7 +893,7 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       double* smr = sm + (size_t)r * L.total;
       int* flr = fl + 4 * r;
       double* pr = part + (size_t)r * rpart;
-      cu.ok(launch_face_dinv(P, c->dt.Ghinv, c->d_escale, tr, rr, st));
+      cu.ok(op_dinv(c, tr, rr, st));
       axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, rr, 0.0, rr, rr, n, pr);
       cycle_init_kernel<<<1, 256, 0, st>>>(smr, L, flr, pr, KG);
       to_df_kernel<<<KG, KT, 0, st>>>(rr, smr, L.sc + 4, V + (size_t)r * ldv, n, flr);
@@ -881,8 +904,12 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       const int nv = j + 1;
       {
         ProfScope ps(c, phase);
-        cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale, c->d_Zb,
-                                   st));
+        if (c->lv)
+          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale,
+                                   nullptr, st));
+        else
+          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale,
+                                     c->d_Zb, st));
         c->launches += 1;
       }
       ProfScope po(c, HDG_PROF_ORTHO);

@@ -14,6 +14,17 @@ cudaError_t launch_recover(const Params& P, const DevTables& dt, const double* w
                            cudaStream_t st, int rcol = 0);
 cudaError_t launch_project_dirichlet(const Params& P, const DevTables& dt, const double* gD, double* ghat,
                                      cudaStream_t st);
+// one refinement level of a level mesh (condense.cu)
+cudaError_t launch_condense_bin(const Params& P, const DevTables& dt, const double* kappa, const double* f_qp,
+                                const int64_t* qoff, int64_t fstride, const double* ghat, double* ws,
+                                const int* elist, int64_t nslots, int64_t e0, int64_t count, int slot_is_element,
+                                int write_outputs, double* S, double* gel, int* info, cudaStream_t st,
+                                int split_update);
+cudaError_t launch_recover_bin(const Params& P, const DevTables& dt, const double* ws, const int* elist,
+                               int64_t nslots, int64_t e0, int64_t count, int slot_is_element, const double* xel,
+                               const int64_t* uoff, double* u, double* q, cudaStream_t st, int rcol);
+cudaError_t launch_project_dirichlet_bin(const Params& P, const DevTables& dt, const int* blist, int nbnd,
+                                         const int64_t* boff, const double* gD, double* ghat, cudaStream_t st);
 cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64_t count, double* out,
                              cudaStream_t st);
 
@@ -35,6 +46,26 @@ cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, c
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
                              cudaStream_t st);
 cudaError_t launch_face_scale(const Params& P, const double* kappa, double* escale, cudaStream_t st);
+
+// Reference tables to the device (api.cu): one allocation, its size in *bytes.
+cudaError_t upload_ref_tables(const RefTables& T, DevTables& d, void** dmem, size_t* bytes, cudaStream_t st);
+
+// Level meshes (levels.cu): per-element refinement levels, faces at the finer side's level.
+hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d);
+void level_destroy(hdg_ctx* c);
+hdg_status level_quad_points(hdg_ctx* c, double* xy);
+hdg_status level_bnd_quad_points(hdg_ctx* c, double* xy);
+hdg_status level_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, int nrhs);
+hdg_status level_condense(hdg_ctx* c, unsigned flags);
+hdg_status level_recover(hdg_ctx* c, const double* x, double* u, double* q, int nrhs);
+hdg_status level_get_schur(hdg_ctx* c, int64_t e0, int64_t count, double* S);
+// element-side product buffer for nrhs columns (allocated outside any stream capture)
+cudaError_t level_ensure_z(hdg_ctx* c, int nrhs);
+// y = S x (escale null) or D^-1 S x (preconditioned blocks, escale) for nrhs columns of stride vstride;
+// bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks, vt: 0 FP64 / 1 split-FP32 / 2 FP32 vectors
+cudaError_t launch_level_apply(hdg_ctx* c, int bt, int vt, const void* S, const void* x, void* y, int nrhs,
+                               int64_t vstride, const double* escale, const int* stop, cudaStream_t st);
+cudaError_t launch_level_dinv(hdg_ctx* c, const double* y, double* z, int nrhs, int64_t vstride, cudaStream_t st);
 
 // Adjoint path (adjoint.cu).
 cudaError_t launch_copy_kappa(const Params& P, const double* src, double* kappa, int* bad, cudaStream_t st);

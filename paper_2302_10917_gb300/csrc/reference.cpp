@@ -398,3 +398,69 @@ void build_reference_tables(int m, int p, RefTables& T) {
 }
 
 }  // namespace mehdg
+
+namespace mehdg {
+
+// Trace tables of every face level R = 0 .. kMaxLevel (m = 2^R sub-intervals of
+// [0,1]): the C0 P_p trace mass Gh_R and its inverse, and for r < R the
+// transfer T_rR = Gh_r^-1 Pi^T Gh_R, Pi the level-r nodal basis at the
+// level-R nodes. T_rR maps a level-R trace to the coefficients of its L2
+// projection onto the level-r space, and the coarse side's face couplings
+// to a level-R face are its own-level couplings times T_rR (the coarse
+// basis restricted to the edge lies in the level-r trace space, Sec. 5.3).
+void build_level_tables(int p, LevelTables& L) {
+  L.p = p;
+  std::vector<double> gx, gw;
+  gauss01(p + 2, gx, gw);
+  std::vector<double> psi((size_t)gx.size() * (p + 1));
+  for (size_t q = 0; q < gx.size(); ++q) lagrange_1d(p, gx[q], &psi[q * (p + 1)]);
+  std::vector<std::vector<double>> G(kMaxLevel + 1), Gi(kMaxLevel + 1);
+  L.data.clear();
+  for (int R = 0; R <= kMaxLevel; ++R) {
+    const int m = 1 << R, n1 = m * p + 1;
+    G[R].assign((size_t)n1 * n1, 0.0);
+    for (int s = 0; s < m; ++s)
+      for (size_t q = 0; q < gx.size(); ++q)
+        for (int a = 0; a <= p; ++a)
+          for (int b = 0; b <= p; ++b)
+            G[R][(size_t)(s * p + a) * n1 + s * p + b] += gw[q] / m * psi[q * (p + 1) + a] * psi[q * (p + 1) + b];
+    std::vector<double> Lc(G[R]);
+    cholesky(Lc, n1);
+    std::vector<double> I((size_t)n1 * n1, 0.0);
+    for (int i = 0; i < n1; ++i) I[(size_t)i * n1 + i] = 1.0;
+    Gi[R] = chol_solve(Lc, n1, I, n1);
+    L.G_off[R] = (int64_t)L.data.size();
+    L.data.insert(L.data.end(), G[R].begin(), G[R].end());
+    L.Gi_off[R] = (int64_t)L.data.size();
+    L.data.insert(L.data.end(), Gi[R].begin(), Gi[R].end());
+  }
+  for (int r = 0; r <= kMaxLevel; ++r)
+    for (int R = 0; R <= kMaxLevel; ++R) {
+      L.T_off[r][R] = -1;
+      if (R <= r) continue;
+      const int nc = (1 << r) * p + 1, nf = (1 << R) * p + 1;
+      // Pi (nf x nc): level-r basis at the level-R nodes j / (nf - 1)
+      std::vector<double> Pi((size_t)nf * nc, 0.0), v(p + 1);
+      const int mc = 1 << r;
+      for (int j = 0; j < nf; ++j) {
+        const int num = j * mc, den = nf - 1;          // t = j / den, t * mc = num / den
+        int s = num / den;
+        if (s > mc - 1) s = mc - 1;
+        const double loc = (double)(num - s * den) / den;
+        lagrange_1d(p, loc, v.data());
+        for (int a = 0; a <= p; ++a) Pi[(size_t)j * nc + s * p + a] = v[a];
+      }
+      // Pi^T G_R (nc x nf), then G_r^-1 (...)
+      const std::vector<double> PtG = atb(Pi, nf, nc, G[R], nf);
+      std::vector<double> T((size_t)nc * nf, 0.0);
+      for (int i = 0; i < nc; ++i)
+        for (int k = 0; k < nc; ++k) {
+          const double g = Gi[r][(size_t)i * nc + k];
+          for (int j = 0; j < nf; ++j) T[(size_t)i * nf + j] += g * PtG[(size_t)k * nf + j];
+        }
+      L.T_off[r][R] = (int64_t)L.data.size();
+      L.data.insert(L.data.end(), T.begin(), T.end());
+    }
+}
+
+}  // namespace mehdg

@@ -94,6 +94,10 @@ using namespace mehdg;
 
 extern "C" hdg_status hdg_condense_static(hdg_ctx* c, int64_t e0, int64_t count, double* S_dev, double* g_dev) {
   if (!c) return HDG_ERR_ARG;
+  if (c->lv) {
+    c->err = "hdg_condense_static: not available on a level mesh";
+    return HDG_ERR_ARG;
+  }
   if (!S_dev || e0 < 0 || count < 1 || e0 + count > c->prm.N) {
     c->err = "hdg_condense_static: bad element range or null S";
     return HDG_ERR_ARG;

@@ -1,0 +1,234 @@
+"""Level meshes on the GPU (Sec. 5.3): per-element refinement levels, faces at
+the finer side's level, against the level-mesh oracle (oracle/levels.py).
+
+The oracle integrates the coarse side's face couplings on the fine sub-edges;
+the library condenses every element at its own level and lifts the blocks
+with the face transfer T = Gh_r^-1 Pi^T Gh_R. Parity: Schur blocks, the
+condensed right-hand side, the plain and preconditioned apply (FP64 to
+1e-12; split-FP32 to 1e-12; FP32 to 1e-6), the solution and the back-solve
+(GMRES to 1e-13 against the oracle's direct solve, 1e-9), several right-hand
+sides, and polynomial exactness through non-conforming faces.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.levels import LevelHDGProblem, band_levels
+from oracle.problems import polynomial, random_polynomial
+from paper_2302_10917_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _levels(kind, n, p):
+    g = np.random.default_rng([wl.MASTER_SEED, 71, n, p])
+    if kind == "random":
+        hi = 3 if p <= 2 else 2
+        return g.integers(0, hi + 1, size=2 * n * n)
+    if kind == "band":
+        return band_levels(n, edges=(0.4, 0.6, 0.8), base=0)
+    if kind == "level4":
+        lev = np.ones(2 * n * n, dtype=np.int64)
+        lev[:2] = 4
+        return lev
+    raise ValueError(kind)
+
+
+CASES = [
+    # id, n, p, levels, beta
+    ("rand_p2", 2, 2, "random", (0.8, -0.3)),
+    ("band_p2", 4, 2, "band", (1.0, 0.0)),
+    ("rand_p3", 2, 3, "random", (0.5, 0.9)),
+    ("lev4_p1", 2, 1, "level4", (0.3, 0.7)),
+]
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def case(request):
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    cid, n, p, kind, beta = request.param
+    lev = _levels(kind, n, p)
+    N = 2 * n * n
+    kappa = wl.random_kappa(N, seed=13 * n + p)
+    ora = LevelHDGProblem(n, lev, p, beta=beta, kappa=kappa)
+    gpu = Problem(n, 1, p, beta=beta, kappa=kappa, levels=lev)
+    g = np.random.default_rng([wl.MASTER_SEED, 72, n, p])
+    f = g.standard_normal(ora.qoff[-1])
+    gD = g.standard_normal(ora.boff[-1])
+    gpu.set_source(torch.from_numpy(f), torch.from_numpy(gD))
+    gpu.condense(keep_factors=True, store_fp32=True, store_df64=True)
+    S_el, g_o, gh = ora.condense(f, gD)
+    yield dict(ora=ora, gpu=gpu, f=f, gD=gD, S=S_el, g=g_o, gh=gh, rng=g, lev=lev)
+    gpu.close()
+
+
+def test_ragged_offsets_match_the_oracle(case):
+    from paper_2302_10917_gb300 import (OFF_DIRICHLET_POINTS, OFF_DIRICHLET_TRACE, OFF_LATTICE, OFF_SCHUR,
+                                        OFF_SOURCE, OFF_TRACE)
+    ora, gpu = case["ora"], case["gpu"]
+    assert gpu.info["levels"] == 1 and gpu.info["N_tr"] == ora.N_tr
+    assert np.array_equal(gpu.offsets(OFF_SOURCE).numpy(), ora.qoff)
+    assert np.array_equal(gpu.offsets(OFF_DIRICHLET_POINTS).numpy(), ora.boff)
+    assert np.array_equal(gpu.offsets(OFF_LATTICE).numpy(), ora.uoff)
+    assert np.array_equal(gpu.offsets(OFF_TRACE).numpy(), ora.eoff)
+    assert np.array_equal(gpu.offsets(OFF_DIRICHLET_TRACE).numpy(), ora.goff)
+    nt = np.array([ora.n_t(e) for e in range(ora.N)])
+    assert np.array_equal(gpu.offsets(OFF_SCHUR).numpy(), np.concatenate([[0], np.cumsum(nt * nt)]))
+
+
+def test_quadrature_points_match_the_oracle(case):
+    ora, gpu = case["ora"], case["gpu"]
+    assert np.abs(gpu.quad_points().cpu().numpy() - ora.quad_points()[0]).max() < 1e-15
+    assert np.abs(gpu.bnd_quad_points().cpu().numpy() - ora.bnd_quad_points()[0]).max() < 1e-15
+
+
+def test_schur_blocks_and_rhs_match_the_oracle(case):
+    ora, gpu = case["ora"], case["gpu"]
+    S = gpu.schur().cpu().numpy()
+    from paper_2302_10917_gb300 import OFF_SCHUR
+    off = gpu.offsets(OFF_SCHUR).numpy()
+    for e in range(ora.N):
+        nt = ora.n_t(e)
+        Se = S[off[e]:off[e + 1]].reshape(nt, nt)
+        assert rel(Se, case["S"][e]) < 1e-12, e
+    assert rel(gpu.rhs().cpu().numpy(), case["g"]) < 1e-12
+    # a sub-range of elements
+    part = gpu.schur(3, 4).cpu().numpy()
+    assert np.array_equal(part, S[off[3]:off[7]])
+
+
+@pytest.mark.parametrize("prec", [64, 48, 32])
+def test_apply_matches_the_oracle(case, prec):
+    ora, gpu = case["ora"], case["gpu"]
+    Sg = ora.assemble_S(case["S"])
+    x = case["rng"].standard_normal(ora.N_tr)
+    tol = 1e-6 if prec == 32 else 1e-12
+    yp = gpu.apply(torch.from_numpy(x), precond=True, prec=prec).double().cpu().numpy()
+    assert rel(yp, ora.apply_Dinv(Sg @ x)) < tol
+    if prec == 64:
+        assert rel(gpu.apply(torch.from_numpy(x)).cpu().numpy(), Sg @ x) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_solve_and_recover_match_the_oracle(case, mode):
+    ora, gpu = case["ora"], case["gpu"]
+    x_dir = np.linalg.solve(ora.assemble_S(case["S"]), case["g"])
+    x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60, mode=mode, maxit=20000)
+    assert st == 0, rep
+    assert rel(x.cpu().numpy(), x_dir) < 1e-9
+    u, q = gpu.recover(x)
+    u_o, q_o = ora.recover(x_dir, case["f"], case["gh"])
+    assert rel(u.cpu().numpy(), u_o) < 1e-9
+    assert rel(q.cpu().numpy(), q_o) < 1e-9
+
+
+def test_several_right_hand_sides(case):
+    from paper_2302_10917_gb300 import Problem
+    ora, lev = case["ora"], case["lev"]
+    rng = np.random.default_rng([wl.MASTER_SEED, 73, ora.n, ora.p])
+    nrhs = 3
+    f = rng.standard_normal((nrhs, ora.qoff[-1]))
+    gD = rng.standard_normal((nrhs, ora.boff[-1]))
+    gpu = Problem(ora.n, 1, ora.p, beta=tuple(ora.beta), kappa=ora.kappa, levels=lev)
+    try:
+        gpu.set_source(torch.from_numpy(f), torch.from_numpy(gD))
+        gpu.condense(keep_factors=False, store_df64=True, split_update=True)
+        g = gpu.rhs()
+        x, rep, st = gpu.solve(g, tol=1e-13, restart=60, mode=2)
+        assert st == 0, rep
+        u, q = gpu.recover(x)
+        Sg = ora.assemble_S(case["S"])
+        for r in range(nrhs):
+            _, g_o, gh = ora.condense(f[r], gD[r])
+            assert rel(g[r].cpu().numpy(), g_o) < 1e-11
+            x_dir = np.linalg.solve(Sg, g_o)
+            assert rel(x[r].cpu().numpy(), x_dir) < 1e-9
+            u_o, q_o = ora.recover(x_dir, f[r], gh)
+            assert rel(u[r].cpu().numpy(), u_o) < 1e-9 and rel(q[r].cpu().numpy(), q_o) < 1e-9
+        # the multi-column apply equals column-by-column applies
+        X = torch.from_numpy(rng.standard_normal((nrhs, ora.N_tr))).cuda()
+        Y = gpu.apply(X, precond=True)
+        for r in range(nrhs):
+            assert rel(Y[r].cpu().numpy(), gpu.apply(X[r], precond=True).cpu().numpy()) < 1e-14
+    finally:
+        gpu.close()
+
+
+@pytest.mark.parametrize("n,p,kind", [(2, 2, "random"), (3, 3, "band"), (2, 1, "level4")])
+def test_polynomial_exactness_through_nonconforming_faces(n, p, kind):
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    lev = _levels(kind, n, p)
+    kap, beta = 0.7, (0.9, -0.4)
+    u, _, f = polynomial(random_polynomial(p, seed=31 + p), kap, beta)
+    ora = LevelHDGProblem(n, lev, p, beta=beta, kappa=kap)
+    gpu = Problem(n, 1, p, beta=beta, kappa=kap, levels=lev)
+    try:
+        xy = gpu.quad_points().cpu().numpy()
+        bxy = gpu.bnd_quad_points().cpu().numpy()
+        gpu.set_source(torch.from_numpy(f(xy[:, 0], xy[:, 1])), torch.from_numpy(u(bxy[:, 0], bxy[:, 1])))
+        gpu.condense()
+        x, rep, st = gpu.solve(gpu.rhs(), tol=1e-14, restart=80, mode=0, maxit=40000)
+        assert st == 0, rep
+        uu, _ = gpu.recover(x)
+        uu = uu.cpu().numpy()
+        for e in range(ora.N):
+            X = ora.lattice_points(e)
+            assert np.abs(uu[ora.uoff[e]:ora.uoff[e + 1]] - u(X[:, 0], X[:, 1])).max() < 1e-10
+    finally:
+        gpu.close()
+
+
+def test_uniform_levels_equal_the_uniform_context():
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    n, r, p, beta = 3, 2, 2, (0.6, 0.2)
+    a = Problem(n, 2 ** r, p, beta=beta, kappa=0.8)
+    b = Problem(n, 1, p, beta=beta, kappa=0.8, levels=np.full(2 * n * n, r))
+    try:
+        f = torch.from_numpy(np.random.default_rng(4).standard_normal((2 * n * n, a.info["n_qp"])))
+        a.set_source(f)
+        b.set_source(f.reshape(-1))
+        a.condense()
+        b.condense()
+        assert rel(b.schur().cpu().numpy(), a.schur().reshape(-1).cpu().numpy()) < 1e-13
+        assert rel(b.rhs().cpu().numpy(), a.rhs().cpu().numpy()) < 1e-13
+        v = torch.ones(a.info["N_tr"], dtype=torch.float64, device="cuda")
+        assert rel(b.apply(v, precond=True).cpu().numpy(), a.apply(v, precond=True).cpu().numpy()) < 1e-13
+    finally:
+        a.close()
+        b.close()
+
+
+def test_level_mesh_errors():
+    _need_gpu()
+    from paper_2302_10917_gb300 import HDG_ERR_ARG, HDGError, Problem
+    with pytest.raises(HDGError) as ei:
+        Problem(2, 1, 2, levels=np.full(8, 5))
+    assert ei.value.status == HDG_ERR_ARG
+    with pytest.raises(HDGError) as ei:
+        Problem(2, 1, 3, levels=np.full(8, 4))          # level 4 at p = 3 exceeds shared memory
+    assert ei.value.status == HDG_ERR_ARG
+    pr = Problem(2, 1, 2, levels=np.arange(8) % 3)
+    try:
+        pr.set_source(torch.zeros(pr.info["n_qp_total"], dtype=torch.float64))
+        pr.condense()
+        for call in (lambda: pr.autotune(), lambda: pr.transpose(),
+                     lambda: pr.set_kappa(torch.ones(8, dtype=torch.float64))):
+            with pytest.raises(HDGError) as ei:
+                call()
+            assert ei.value.status == HDG_ERR_ARG and "level mesh" in str(ei.value)
+    finally:
+        pr.close()
