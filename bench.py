@@ -449,6 +449,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if not args.no_extras:
         line["multi_rhs"] = bench_multi_rhs(stream)
+        line["levels_many_source"] = bench_levels_many_source(stream)
         line["gradient"] = bench_gradient(stream)
         line["macro_vs_standard"] = bench_macro_vs_standard(stream)
         line["supg_layer"] = bench_supg_layer(stream)
@@ -508,6 +509,87 @@ def bench_multi_rhs(stream, count=64):
            "column0_rel_diff_to_single": float((x1 - x[0]).abs().max() / x1.abs().max())}
     pr.close()
     p1.close()
+    return out
+
+
+def bench_levels_many_source(stream, count=64):
+    """64 Gaussian-bump sources on the banded-level mesh (n=128, p=2, kappa=1e-2, beta=(1,0);
+    levels r = 1 below x = 0.7, 2, 3, r = 4 from x = 0.9 on, faces at the finer side's level):
+    one condensation with 64 load columns per level plus the face lift, the lockstep batched
+    GMRES to 1e-10 for all columns, the back-solve, and the element-side apply kernels alone
+    (one column FP64; 64 columns FP64, split-FP32 and FP32 blocks)."""
+    import torch
+    from paper_2302_10917_gb300 import Problem
+    from paper_2302_10917_gb300 import workloads as wl
+    cfg = wl.CONFIGS["c3"]
+    lev = wl.band_levels(cfg["n"])
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    pr = Problem(cfg["n"], 1, cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream, levels=lev)
+    f = wl.gaussian_bumps(pr.quad_points(), count, seed=3, width=cfg["width"]).contiguous()
+    N_tr, ns = pr.info["N_tr"], pr.info["n_s_total"]
+    flags = dict(keep_factors=True, store_df64=True, store_fp32=True, split_update=True)
+    pr.set_source(f)
+    pr.condense(**flags)            # first pass: allocations and launch set-up
+    a, b, c2, d = ev(), ev(), ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    pr.set_source(f)
+    pr.condense(**flags)
+    g = pr.rhs()
+    b.record(stream)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1, maxit=40000)
+    c2.record(stream)
+    u, q = pr.recover(x)
+    d.record(stream)
+    torch.cuda.synchronize()
+    # the apply kernels alone (inputs of 64 x 3.7 MB: the blocks, 0.39 GB, exceed L2 for FP64)
+    X = torch.randn(count, N_tr, dtype=torch.float64, device=pr.device)
+
+    def time_apply(xx, prec, reps=10):
+        xin = xx.float() if prec == 32 else xx
+        for _ in range(2):
+            pr.apply(xin, precond=True, prec=prec)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            pr.apply(xin, precond=True, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts)
+    t1 = time_apply(X[0], 64)
+    t64 = {prec: time_apply(X, prec) for prec in (64, 48, 32)}
+    from paper_2302_10917_gb300 import OFF_SCHUR
+    offs = pr.offsets(OFF_SCHUR)
+    rows = int(sum(int(round(math.sqrt(int(offs[e + 1] - offs[e])))) for e in range(pr.info["N"])))
+    # one column, FP64: blocks + gathered x (element-side rows) + element-side products written and
+    # read + one y write
+    bytes1 = ns * 8 + rows * 8 + 2 * rows * 8 + N_tr * 8
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    flops64 = 2.0 * ns * count
+    out = {"workload": f"n={cfg['n']} p={cfg['p']} kappa={cfg['kappa']} beta={cfg['beta']}, levels by band of x "
+                       f"(r=1..4: {[int((lev == r).sum()) for r in (1, 2, 3, 4)]} elements), faces at the finer "
+                       f"side, {count} Gaussian-bump sources (width {cfg['width']}, seeded centres), g_D = 0",
+           "N_tr": N_tr, "element_side_rows": rows, "schur_bytes_fp64": ns * 8, "sources": count,
+           "condense_and_rhs_s": a.elapsed_time(b) / 1e3, "batched_solve_s": b.elapsed_time(c2) / 1e3,
+           "batched_iterations": rep["iterations"], "batched_converged": bool(rep["converged"]),
+           "batched_max_rel_residual": rep["rel_residual"], "recover_s": c2.elapsed_time(d) / 1e3,
+           "apply_1col_fp64_s": t1, "apply_1col_gdofs": N_tr / t1 / 1e9,
+           "apply_1col_roofline": {"bound": "hbm", "achieved": bytes1 / t1 / 1e9, "peak": hbm, "unit": "GB/s",
+                                   "frac": (bytes1 / t1 / 1e9 / hbm) if hbm else None, "traffic": None,
+                                   "bytes_per_launch": bytes1},
+           "apply_64col_s": {"fp64": t64[64], "split_fp32": t64[48], "fp32": t64[32]},
+           "apply_64col_gdofs": {k: N_tr * count / v / 1e9 for k, v in
+                                 (("fp64", t64[64]), ("split_fp32", t64[48]), ("fp32", t64[32]))},
+           "apply_64col_roofline": {
+               "fp64": {"bound": "fp64 pipe", "achieved": flops64 / t64[64] / 1e12, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": flops64 / t64[64] / 1e12 / FP64_PEAK_TFLOPS},
+               "split_fp32": {"bound": "alu (FP32 pipe, split arithmetic)", "achieved": flops64 / t64[48] / 1e12,
+                              "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s (FP64-equivalent)",
+                              "frac": flops64 / t64[48] / 1e12 / DF_PEAK_TFLOPS}}}
+    pr.close()
     return out
 
 

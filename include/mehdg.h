@@ -174,8 +174,13 @@ typedef struct {
 #define HDG_KEEP_FACTORS 2u    /* keep the factored local systems and their pivots for hdg_recover and the
                                   adjoint (else hdg_recover refactors) */
 #define HDG_STORE_DF64 4u      /* also keep the preconditioned blocks as FP32 hi/lo pairs (8 bytes per entry) */
-#define HDG_SPLIT_UPDATE 8u    /* form the LU's panel products in split-FP32 arithmetic (FP32 pipe);
-                                  pivots, triangular solves and the stored entries stay FP64 */
+#define HDG_SPLIT_UPDATE 8u    /* eliminate in split-FP32 arithmetic on the FP32 pipe (formation, pivot search,
+                                  panel, triangular solves and trailing updates); the stored entries are FP64 */
+#define HDG_PRECOND_FACE_SCHUR 16u  /* precondition with the inverted diagonal face blocks of the condensed
+                                       operator, S_ff = sum over both sides of S_e's face rows and columns,
+                                       instead of D_f of Sec. 6.1 (folded into the stored preconditioned rows
+                                       the same way; the apply costs the same). hdg_transpose returns to D^-1;
+                                       HDG_ERR_SINGULAR if a face block has a zero pivot. */
 
 /* Build the structured macro mesh, the reference-lattice tables of level m
  * (mass, derivative, boundary and trace matrices, quadrature) and the device

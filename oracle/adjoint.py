@@ -63,7 +63,7 @@ def gradient(pr: HDGProblem, f_qp, r, gD_qp=None, return_state=False):
                 if kb == "int":
                     St[ia, ib] += Se_T[la, lb]
     nu = np.linalg.solve(St, gadj)
-    _, wts = pr._qp_cache()
+    _, wts = pr.quad_points()
     gk = np.zeros(msh.N)
     gf = np.zeros((msh.N, wts.shape[1]))
     lam_u = np.zeros((msh.N, Q))

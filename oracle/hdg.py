@@ -85,20 +85,25 @@ class HDGProblem:
     def quad_points(self):
         """Physical source quadrature points [N, n_qp, 2] and weights [N, n_qp]."""
         msh = self.mesh
+        pw = [self.element_quad_points(e) for e in range(msh.N)]
+        return np.stack([a for a, _ in pw]), np.stack([b for _, b in pw])
+
+    def element_quad_points(self, e):
+        """Source points [n_qp, 2] and weights [n_qp] of macro-element e (published order)."""
+        msh = self.mesh
         xi_q, eta_q, w_q = triangle_rule(self.ng)
         nq = xi_q.size
         subs = msh.sub_triangles()
-        pts = np.empty((msh.N, len(subs) * nq, 2))
-        wts = np.empty((msh.N, len(subs) * nq))
-        for e in range(msh.N):
-            v = msh.vertices(e)
-            for s, tri in enumerate(subs):
-                A, B, C = [v[0] + (v[1] - v[0]) * (t[0] / msh.m) + (v[2] - v[0]) * (t[1] / msh.m)
-                           for t in tri]
-                area = 0.5 * abs((B - A)[0] * (C - A)[1] - (B - A)[1] * (C - A)[0])
-                sl = slice(s * nq, (s + 1) * nq)
-                pts[e, sl, :] = A[None, :] + np.outer(xi_q, B - A) + np.outer(eta_q, C - A)
-                wts[e, sl] = w_q * 2.0 * area
+        pts = np.empty((len(subs) * nq, 2))
+        wts = np.empty(len(subs) * nq)
+        v = msh.vertices(e)
+        for s, tri in enumerate(subs):
+            A, B, C = [v[0] + (v[1] - v[0]) * (t[0] / msh.m) + (v[2] - v[0]) * (t[1] / msh.m)
+                       for t in tri]
+            area = 0.5 * abs((B - A)[0] * (C - A)[1] - (B - A)[1] * (C - A)[0])
+            sl = slice(s * nq, (s + 1) * nq)
+            pts[sl, :] = A[None, :] + np.outer(xi_q, B - A) + np.outer(eta_q, C - A)
+            wts[sl] = w_q * 2.0 * area
         return pts, wts
 
     def bnd_quad_points(self):
@@ -265,17 +270,15 @@ class HDGProblem:
         """R_e = [0; 0; (f, phi_i)_K] from f at the published source points of e."""
         em = self.element_matrices(e)
         Q = self.mesh.Q
-        _, wts = self._qp_cache()
+        key = ("qw", e)
+        if key not in self._cache:
+            self._cache[key] = self.element_quad_points(e)[1]
+        w = self._cache[key]
         R = np.zeros(3 * Q)
-        R[2 * Q:] = em["Phi"].T @ (wts[e] * f_vals)
+        R[2 * Q:] = em["Phi"].T @ (w * f_vals)
         if self.supg:
-            R[2 * Q:] += self.supg_tau(e) * (em["PhiB"].T @ (wts[e] * f_vals))
+            R[2 * Q:] += self.supg_tau(e) * (em["PhiB"].T @ (w * f_vals))
         return R
-
-    def _qp_cache(self):
-        if "qp" not in self._cache:
-            self._cache["qp"] = self.quad_points()
-        return self._cache["qp"]
 
     # ---------------------------------------------------------- Dirichlet data
     def dirichlet_trace(self, gD_vals):

@@ -120,11 +120,6 @@ class LevelHDGProblem:
             wts[self.boff[b]:self.boff[b + 1]] = sw[b]
         return pts, wts
 
-    def _qp(self):
-        if "qp" not in self._cache:
-            self._cache["qp"] = self.quad_points()
-        return self._cache["qp"]
-
     # ------------------------------------------------------ element matrices
     def element_matrices(self, e):
         """Volume matrices of e's own level; F, G, normals per face at the face levels."""
@@ -235,21 +230,37 @@ class LevelHDGProblem:
                 out[i] += vec_loc[loc]
 
     # -------------------------------------------------- static condensation
+    def condense_element(self, e, f_flat=None, g_hat=None):
+        """S_e = D_e - C_e A_e^-1 B_e and g_e = -C_e A_e^-1 R_e - S_e g^_e (dense LU of A_e)."""
+        A, B, C, D = self.local_blocks(e)
+        lu = sla.lu_factor(A)
+        S = D - C @ sla.lu_solve(lu, B)
+        ge = np.zeros(S.shape[0])
+        if g_hat is not None:
+            ge -= S @ self.element_trace(e, np.zeros(self.N_tr), g_hat)
+        if f_flat is not None:
+            ge -= C @ sla.lu_solve(lu, self.load_vector(e, f_flat))
+        return S, ge
+
     def condense(self, f_flat=None, gD_flat=None):
         """S_e (list), the assembled right-hand side g and the Dirichlet trace g^."""
         g_hat = self.dirichlet_trace(gD_flat) if gD_flat is not None else np.zeros(self.goff[-1])
-        zero = np.zeros(self.N_tr)
         S_el, g = [], np.zeros(self.N_tr)
         for e in range(self.N):
-            A, B, C, D = self.local_blocks(e)
-            lu = sla.lu_factor(A)
-            S = D - C @ sla.lu_solve(lu, B)
-            ge = -S @ self.element_trace(e, zero, g_hat)
-            if f_flat is not None:
-                ge -= C @ sla.lu_solve(lu, self.load_vector(e, f_flat))
+            S, ge = self.condense_element(e, f_flat, g_hat)
             S_el.append(S)
             self.scatter(e, ge, g)
         return S_el, g, g_hat
+
+    def recover_element(self, e, v_hat, f_flat=None, g_hat=None):
+        """(u_e, q_e) of Eq. (local_matrix_problem) for one element: u [Q_e], q [2, Q_e]."""
+        A, B, _, _ = self.local_blocks(e)
+        Q = self.Qe[e]
+        if g_hat is None:
+            g_hat = np.zeros(self.goff[-1])
+        R = self.load_vector(e, f_flat) if f_flat is not None else np.zeros(3 * Q)
+        U = np.linalg.solve(A, R - B @ self.element_trace(e, v_hat, g_hat))
+        return U[2 * Q:], U[:2 * Q].reshape(2, Q)
 
     def assemble_S(self, S_el):
         S = np.zeros((self.N_tr, self.N_tr))

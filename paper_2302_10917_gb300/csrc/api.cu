@@ -408,7 +408,7 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
 hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
-  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE))
+  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE | HDG_PRECOND_FACE_SCHUR))
     return set_err(c, HDG_ERR_ARG, "unknown flags");
   if (c->lv) return level_condense(c, flags);
   const int split = (flags & HDG_SPLIT_UPDATE) ? 1 : 0;
@@ -453,6 +453,26 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     }
     c->launches += 1;
     if (e != cudaSuccess) return cuda_err(c, e, "condense kernel");
+  }
+  c->pc_face = 0;
+  if (flags & HDG_PRECOND_FACE_SCHUR) {
+    // inverted diagonal face blocks of S folded into the preconditioned rows
+    if (!c->d_Pinv && (e = dev_alloc(c, &c->d_Pinv, (size_t)P.n_int * P.P1 * P.P1)) != cudaSuccess)
+      return cuda_err(c, e, "face blocks");
+    if (!c->d_bad && (e = dev_alloc(c, &c->d_bad, 1)) != cudaSuccess) return cuda_err(c, e, "face block check");
+    int bad = 0;
+    if ((e = cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream)) != cudaSuccess ||
+        (e = launch_face_schur(P, c->d_S, c->d_Pinv, c->d_St, (flags & HDG_STORE_FP32) ? c->d_St32 : nullptr,
+                               c->d_bad, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_err(c, e, "face blocks");
+    c->launches += 2;
+    if (bad) {
+      c->state = 1;
+      return set_err(c, HDG_ERR_SINGULAR, std::to_string(bad) + " diagonal face blocks of S have a zero pivot");
+    }
+    c->pc_face = 1;
   }
   if (flags & HDG_STORE_DF64) {
     c->launches += 1;
@@ -499,14 +519,14 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     if ((e = level_ensure_z(c, nrhs)) != cudaSuccess) return cuda_err(c, e, "element-side buffer");
     const int64_t n = c->prm.N_tr;
     if (prec == 64) {
-      e = launch_level_apply(c, 0, 0, precond ? L.d_St : L.d_S, x, y, nrhs, n, precond ? c->d_escale : nullptr,
+      e = launch_level_apply(c, 0, 0, precond ? L.d_St : L.d_S, x, y, nrhs, n, precond ? precond_scale(c) : nullptr,
                              nullptr, c->stream);
     } else if (prec == 48) {
       if (!L.d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
-      e = launch_level_apply(c, 1, 0, L.d_Stdf, x, y, nrhs, n, c->d_escale, nullptr, c->stream);
+      e = launch_level_apply(c, 1, 0, L.d_Stdf, x, y, nrhs, n, precond_scale(c), nullptr, c->stream);
     } else if (prec == 32) {
       if (!L.d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
-      e = launch_level_apply(c, 2, 2, L.d_St32, x, y, nrhs, n, c->d_escale, nullptr, c->stream);
+      e = launch_level_apply(c, 2, 2, L.d_St32, x, y, nrhs, n, precond_scale(c), nullptr, c->stream);
     } else {
       return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
     }
@@ -517,14 +537,14 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     // multi-RHS apply: every block streamed once for all columns
     const Params& P = c->prm;
     if (prec == 64) {
-      e = launch_apply_mrhs(0, 0, P, precond ? c->d_St : c->d_S, x, y, nrhs, P.N_tr, precond ? c->d_escale : nullptr,
+      e = launch_apply_mrhs(0, 0, P, precond ? c->d_St : c->d_S, x, y, nrhs, P.N_tr, precond ? precond_scale(c) : nullptr,
                             c->stream);
     } else if (prec == 48) {
       if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
-      e = launch_apply_mrhs(1, 0, P, c->d_Stdf, x, y, nrhs, P.N_tr, c->d_escale, c->stream);
+      e = launch_apply_mrhs(1, 0, P, c->d_Stdf, x, y, nrhs, P.N_tr, precond_scale(c), c->stream);
     } else if (prec == 32) {
       if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
-      e = launch_apply_mrhs(2, 2, P, c->d_St32, x, y, nrhs, P.N_tr, c->d_escale, c->stream);
+      e = launch_apply_mrhs(2, 2, P, c->d_St32, x, y, nrhs, P.N_tr, precond_scale(c), c->stream);
     } else {
       return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
     }
@@ -532,14 +552,14 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply (multi-RHS)");
   }
   if (prec == 64) {
-    e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream)
+    e = precond ? launch_apply64(c->prm, c->d_St, (const double*)x, (double*)y, precond_scale(c), nullptr, c->stream)
                 : launch_apply64(c->prm, c->d_S, (const double*)x, (double*)y, nullptr, nullptr, c->stream);
   } else if (prec == 48) {
     if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
-    e = launch_apply_df(c->prm, c->d_Stdf, (const double*)x, (double*)y, c->d_escale, nullptr, c->stream);
+    e = launch_apply_df(c->prm, c->d_Stdf, (const double*)x, (double*)y, precond_scale(c), nullptr, c->stream);
   } else if (prec == 32) {
     if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
-    e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, c->d_escale, nullptr, c->stream);
+    e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, precond_scale(c), nullptr, c->stream);
   } else {
     return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
   }
@@ -715,6 +735,7 @@ hdg_status hdg_transpose(hdg_ctx* c) {
   c->launches += 1;
   if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose");
   c->transposed ^= 1;
+  c->pc_face = 0;      // the preconditioned rows are D^-1-folded again
   return HDG_OK;
 }
 
@@ -796,7 +817,7 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
-  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_Pinv);
   if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
   for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

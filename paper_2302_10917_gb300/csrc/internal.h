@@ -110,6 +110,9 @@ struct LevelDev {
   const double* tab;          // level tables (LevelTables::data)
   int64_t G_off[kMaxLevel + 1], Gi_off[kMaxLevel + 1], T_off[kMaxLevel + 1][kMaxLevel + 1];
   const double* escale;       // [n_int] -1 / ((tau+ + tau-) L_f)
+  const int* eside;           // [n_int][2] element of each side
+  const int* nte;             // [N] n_t,e by element id
+  const int64_t* poff;        // [n_int + 1] first entry of every face's n_f x n_f block (face preconditioner)
 };
 
 // Face levels of element e from the per-edge and per-element levels.
@@ -265,6 +268,9 @@ struct LevelMesh {
   double* d_gel = nullptr;      // [nrhs][nz] lifted element right-hand sides
   double* d_z = nullptr;        // [HDG_MAX_RHS][nz] element-side products
   int z_rhs = 0;
+  int max_nf = 0;               // largest face block (2^R p + 1)
+  double* d_Pinv = nullptr;     // [poff[n_int]] inverted face blocks (HDG_PRECOND_FACE_SCHUR)
+  int64_t pinv_count = 0;
 };
 }  // namespace mehdg
 
@@ -300,6 +306,8 @@ struct hdg_ctx {
   int alloc_nrhs = 0;             // right-hand sides the per-RHS buffers (ghat, gel, g) are sized for
   int ws_ld = 0;                  // leading dimension the local workspace was allocated with
   double* d_escale = nullptr;     // [n_int] -1 / ((tau+ + tau-) L_f)
+  int pc_face = 0;                // 1: the stored preconditioned rows hold S_ff^-1 (HDG_PRECOND_FACE_SCHUR)
+  double* d_Pinv = nullptr;       // [n_int][P1][P1] inverted diagonal face blocks of S
   // Krylov workspace
   float2* d_V = nullptr;          // Krylov basis, split-FP32 pairs [restart + 1][N_tr]
   float2* d_w = nullptr;          // Arnoldi work vector, split-FP32 pairs [N_tr]
@@ -338,6 +346,11 @@ struct hdg_ctx {
 };
 
 namespace mehdg {
+// Face scale of the preconditioned apply: -1 / ((tau+ + tau-) L_f) with the
+// D^-1 preconditioner of Sec. 6.1 (Gh^-1 folded into the rows), none when the
+// rows hold the inverted diagonal face blocks of S.
+inline const double* precond_scale(const hdg_ctx* c) { return c->pc_face ? nullptr : c->d_escale; }
+
 // Event pair around a launch when profiling is on (no-op otherwise).
 struct ProfScope {
   hdg_ctx* c;

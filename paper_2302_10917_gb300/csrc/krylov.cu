@@ -478,8 +478,12 @@ static cudaError_t op_resid(hdg_ctx* c, const double* x, double* y, int nb, int6
   return launch_apply_mrhs(0, 0, c->prm, c->d_S, x, y, nb, n, nullptr, st);
 }
 
-// z = D^-1 y on one FP64 vector
+// z = D^-1 y (or S_ff^-1 y face by face) on one FP64 vector
 static cudaError_t op_dinv(hdg_ctx* c, const double* y, double* z, cudaStream_t st) {
+  if (c->pc_face) {
+    if (c->lv) return launch_level_face_pinv(c->lv->dv, c->lv->d_Pinv, y, z, 1, c->prm.N_tr, st);
+    return launch_face_pinv(c->prm, c->d_Pinv, y, z, st);
+  }
   if (c->lv) return launch_level_dinv(c, y, z, 1, c->prm.N_tr, st);
   return launch_face_dinv(c->prm, c->dt.Ghinv, c->d_escale, y, z, st);
 }
@@ -566,8 +570,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        if (c->lv) cu.ok(launch_level_apply(c, bt, 1, Sop, V + (size_t)j * ldv, w, 1, ldv, c->d_escale, fl, s));
-        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, c->d_escale, fl, s, epb));
+        if (c->lv) cu.ok(launch_level_apply(c, bt, 1, Sop, V + (size_t)j * ldv, w, 1, ldv, precond_scale(c), fl, s));
+        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, precond_scale(c), fl, s, epb));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -602,7 +606,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       // profiling on, the capture carries an event quadruple per step.
       const int timed = c->prof_on ? 1 : 0;
       const std::vector<intptr_t> key = {K, bt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
-                                         (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)c->d_escale,
+                                         (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
                                          (intptr_t)np, kgd, kgu, epb};
       if (timed && (int)c->gm_ev.size() < 4 * K) {
         while ((int)c->gm_ev.size() < 4 * K) {
@@ -714,12 +718,12 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   for (int threads : {128, 256, 384, 512}) {
     const int epb = threads / P.P1 > 0 ? threads / P.P1 : 1;
     if (epb * P.P1 > 512) continue;
-    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, c->d_escale, nullptr, st, epb)); });
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, epb)); });
     if (epb == def_epb) def_apply = t;
     if (t < best_apply) { best_apply = t; best_epb = epb; }
   }
   if (def_apply == 0.0)
-    def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, c->d_escale, nullptr, st, def_epb)); });
+    def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb)); });
   // multi-dot blocks
   int best_kgd = KGD;
   double best_mdot = 1e30, def_mdot = 0.0;
@@ -905,10 +909,10 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       {
         ProfScope ps(c, phase);
         if (c->lv)
-          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale,
+          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, precond_scale(c),
                                    nullptr, st));
         else
-          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, c->d_escale,
+          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, precond_scale(c),
                                      c->d_Zb, st));
         c->launches += 1;
       }

@@ -67,6 +67,15 @@ cudaError_t launch_level_apply(hdg_ctx* c, int bt, int vt, const void* S, const 
                                int64_t vstride, const double* escale, const int* stop, cudaStream_t st);
 cudaError_t launch_level_dinv(hdg_ctx* c, const double* y, double* z, int nrhs, int64_t vstride, cudaStream_t st);
 
+// Face-block preconditioner with the diagonal blocks of S (precond.cu).
+cudaError_t launch_face_schur(const Params& P, const double* S, double* Pinv, double* St, float* St32, int* bad,
+                              cudaStream_t st);
+cudaError_t launch_face_pinv(const Params& P, const double* Pinv, const double* y, double* z, cudaStream_t st);
+cudaError_t launch_level_face_schur(const LevelDev& L, int max_nf, const double* S, double* Pinv, double* St,
+                                    int* bad, cudaStream_t st);
+cudaError_t launch_level_face_pinv(const LevelDev& L, const double* Pinv, const double* y, double* z, int nrhs,
+                                   int64_t vstride, cudaStream_t st);
+
 // Adjoint path (adjoint.cu).
 cudaError_t launch_copy_kappa(const Params& P, const double* src, double* kappa, int* bad, cudaStream_t st);
 cudaError_t launch_transpose(const Params& P, const DevTables& dt, double* S, double* St, float* St32, float2* Stdf,

@@ -571,13 +571,19 @@ hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d) {
       }
     }
   }
-  std::vector<int> dof_edge(N_tr), ez(2 * (size_t)n_int), eflip(n_int);
+  std::vector<int> dof_edge(N_tr), ez(2 * (size_t)n_int), eflip(n_int), eside(2 * (size_t)n_int);
   std::vector<double> escale(n_int);
+  std::vector<int64_t> poff(n_int + 1, 0);
   for (int f = 0; f < n_int; ++f) {
     for (int64_t i = L.eoff[f]; i < L.eoff[f + 1]; ++i) dof_edge[i] = f;
+    const int64_t nf = L.eoff[f + 1] - L.eoff[f];
+    poff[f + 1] = poff[f] + nf * nf;
+    L.max_nf = std::max(L.max_nf, (int)nf);
     int es[2], ks[2], fl[2];
     double len;
     edge_sides(f, n, es, ks, fl, &len);
+    eside[2 * f] = es[0];
+    eside[2 * f + 1] = es[1];
     double tsum = 0.0;
     for (int sd = 0; sd < 2; ++sd) {
       int code[3], flip[3], o = 0;
@@ -605,7 +611,10 @@ hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d) {
       {escale.data(), escale.size() * 8, (void**)&dv.escale},     {L.qoff.data(), L.qoff.size() * 8, (void**)&L.d_qoff},
       {L.boff.data(), L.boff.size() * 8, (void**)&L.d_boff},      {L.uoff.data(), L.uoff.size() * 8, (void**)&L.d_uoff},
       {seoff.data(), seoff.size() * 8, (void**)&L.d_seoff},
+      {eside.data(), eside.size() * 4, (void**)&dv.eside},        {L.nt_e.data(), L.nt_e.size() * 4, (void**)&dv.nte},
+      {poff.data(), poff.size() * 8, (void**)&dv.poff},
   };
+  L.pinv_count = poff[n_int];
   size_t total = 0;
   for (auto& it : items) total += (it.bytes + 255) / 256 * 256;
   cudaError_t e;
@@ -694,7 +703,7 @@ void level_destroy(hdg_ctx* c) {
     cudaFree(B.d_ghat); cudaFree(B.d_ws); cudaFree(B.d_info); cudaFree(B.d_xel);
   }
   cudaFree(L.d_mem); cudaFree(L.d_S); cudaFree(L.d_St); cudaFree(L.d_St32); cudaFree(L.d_Stdf);
-  cudaFree(L.d_gel); cudaFree(L.d_z);
+  cudaFree(L.d_gel); cudaFree(L.d_z); cudaFree(L.d_Pinv);
   c->d_escale = nullptr;   // part of d_mem
   delete c->lv;
   c->lv = nullptr;
@@ -821,6 +830,24 @@ hdg_status level_condense(hdg_ctx* c, unsigned flags) {
     }
     c->launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return lv_cuda(c, e, "lift kernel");
+  }
+  c->pc_face = 0;
+  if (flags & HDG_PRECOND_FACE_SCHUR) {
+    if (!L.d_Pinv && (e = lv_alloc(c, &L.d_Pinv, (size_t)L.pinv_count)) != cudaSuccess)
+      return lv_cuda(c, e, "face blocks");
+    if (!c->d_bad && (e = lv_alloc(c, &c->d_bad, 1)) != cudaSuccess) return lv_cuda(c, e, "face block check");
+    int bad = 0;
+    if ((e = cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream)) != cudaSuccess ||
+        (e = launch_level_face_schur(L.dv, L.max_nf, L.d_S, L.d_Pinv, L.d_St, c->d_bad, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return lv_cuda(c, e, "face blocks");
+    c->launches += 2;
+    if (bad) {
+      c->state = 1;
+      return lv_err(c, HDG_ERR_SINGULAR, std::to_string(bad) + " diagonal face blocks of S have a zero pivot");
+    }
+    c->pc_face = 1;
   }
   if (flags & HDG_STORE_FP32) {
     lv_to_fp32_kernel<<<2048, 256, 0, c->stream>>>(L.d_St, L.d_St32, L.ns);

@@ -15,6 +15,13 @@ cycle: set_source, condensation (factors kept, the blocks the mode needs,
 split-FP32 panel updates), right-hand side, GMRES(restart) for `restart`
 Arnoldi steps, back-solve. Its kernel mix is that of a full step with fewer
 restart cycles.
+
+--levels: the banded-level mesh (p = 2, kappa = 1e-2, beta = (1, 0), levels
+r = 1 .. 4 by band of x) with `nrhs` Gaussian-bump sources: condensation
+(factors not kept), then `applies` preconditioned applies of nrhs columns with
+FP64, split-FP32 and FP32 blocks each.
+
+    python -m paper_2302_10917_gb300.profcase --levels --n 64 --nrhs 1 --applies 3
 """
 import argparse
 import json
@@ -41,7 +48,11 @@ def main(argv=None):
     ap.add_argument("--split", action="store_true", help="split-FP32 condensation")
     ap.add_argument("--orth", type=int, default=1, help="0: CGS2, 1: single-projection Gram-Schmidt")
     ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner before the solve")
+    ap.add_argument("--levels", action="store_true", help="the banded-level mesh (see the module docstring)")
+    ap.add_argument("--nrhs", type=int, default=1, help="columns of the level-mesh applies")
     a = ap.parse_args(argv)
+    if a.levels:
+        return _levels(a)
     beta = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
     pr = Problem(a.n, a.m, a.p, beta=beta, kappa=1.0)
     xy = pr.quad_points()
@@ -103,6 +114,38 @@ def _step(pr, f, a):
            "gmres_ms": t[1].elapsed_time(t[2]), "recover_ms": t[2].elapsed_time(t[3]),
            "u_norm": float(u.norm()), "launches": pr.launches()}
     print(json.dumps(out))
+    pr.close()
+
+
+
+def _levels(a):
+    cfg = wl.CONFIGS["c3"]
+    lev = wl.band_levels(a.n)
+    pr = Problem(a.n, 1, cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], levels=lev)
+    f = wl.gaussian_bumps(pr.quad_points(), a.nrhs, seed=3, width=cfg["width"]).contiguous()
+    pr.set_source(f[0] if a.nrhs == 1 else f)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t = [ev() for _ in range(5)]
+    t[0].record()
+    pr.condense(store_fp32=True, keep_factors=False, store_df64=True, split_update=True)
+    t[1].record()
+    X = torch.randn(a.nrhs, pr.info["N_tr"], dtype=torch.float64, device=pr.device)
+    X = X[0] if a.nrhs == 1 else X
+    for _ in range(a.applies):
+        pr.apply(X, precond=True, prec=64)
+    t[2].record()
+    for _ in range(a.applies):
+        pr.apply(X, precond=True, prec=48)
+    t[3].record()
+    X32 = X.float()
+    for _ in range(a.applies):
+        pr.apply(X32, precond=True, prec=32)
+    t[4].record()
+    torch.cuda.synchronize()
+    k = max(1, a.applies)
+    print(json.dumps({"info": pr.info, "condense_ms": t[0].elapsed_time(t[1]),
+                      "apply64_ms": t[1].elapsed_time(t[2]) / k, "apply_df_ms": t[2].elapsed_time(t[3]) / k,
+                      "apply32_ms": t[3].elapsed_time(t[4]) / k}))
     pr.close()
 
 

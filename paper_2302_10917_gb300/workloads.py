@@ -19,9 +19,26 @@ CONFIGS = {
     "c1": dict(n=128, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
     "c2": dict(n=256, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
     "c4": dict(n=256, m=4, p=2, beta=(1.0, 0.5), kappa=1.0),
-    # many right-hand sides on one level (uniform stand-in of the banded-level workload)
+    # many right-hand sides on one level (uniform counterpart of the banded-level workload)
     "c3u": dict(n=128, m=4, p=2, beta=(1.0, 0.0), kappa=1e-2),
+    # many right-hand sides on levels by band of x (band_levels: r = 1 .. 4, faces at the finer side)
+    "c3": dict(n=128, m=0, p=2, beta=(1.0, 0.0), kappa=1e-2, nrhs=64, width=0.05),
 }
+
+
+def band_levels(n, edges=(0.7, 0.8, 0.9), base=1):
+    """Refinement level of every macro-triangle by band of its centroid's x: base below
+    edges[0], base + 1 in [edges[0], edges[1]), ..., base + len(edges) from edges[-1] on
+    (int8 [2 n^2], element order e = 2 (j n + i) + t)."""
+    e = np.arange(2 * n * n)
+    sq, t = e // 2, e % 2
+    i = sq % n
+    # centroid x: (2 x_{i+1} + x_i) / 3 for t = 0, (2 x_i + x_{i+1}) / 3 for t = 1
+    cx = np.where(t == 0, (3 * i + 2) / (3.0 * n), (3 * i + 1) / (3.0 * n))
+    lev = np.full(e.shape, base, dtype=np.int64)
+    for th in edges:
+        lev += (cx >= th)
+    return lev.astype(np.int8)
 
 
 def sin_sin_source(xy, kappa, beta):

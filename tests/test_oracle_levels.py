@@ -220,3 +220,24 @@ def test_band_levels_of_the_many_source_workload():
     """n = 128, r = 4 for centroid x >= 0.9, 3 in [0.8, 0.9), 2 in [0.7, 0.8), 1 elsewhere."""
     lev = band_levels(128)
     assert [int((lev == r).sum()) for r in (1, 2, 3, 4)] == [22912, 3328, 3200, 3328]
+
+
+def test_band_levels_of_the_workload_generator_agree():
+    from paper_2302_10917_gb300 import workloads as wl
+    for n in (3, 10, 128):
+        assert np.array_equal(wl.band_levels(n), band_levels(n))
+    assert np.array_equal(wl.band_levels(5, (0.4, 0.6, 0.8), 0), band_levels(5, (0.4, 0.6, 0.8), 0))
+
+
+def test_element_condensation_and_recovery_equal_the_global_route():
+    pr = LevelHDGProblem(2, random_levels(2, seed=12), 2, beta=(0.7, 0.2), kappa=0.6)
+    rng = np.random.default_rng(17)
+    fq = rng.standard_normal(pr.qoff[-1])
+    gq = rng.standard_normal(pr.boff[-1])
+    S_el, g, gh = pr.condense(fq, gq)
+    x = np.linalg.solve(pr.assemble_S(S_el), g)
+    u, q = pr.recover(x, fq, gh)
+    for e in (0, 3, 7):
+        ue, qe = pr.recover_element(e, x, fq, gh)
+        assert np.abs(ue - u[pr.uoff[e]:pr.uoff[e + 1]]).max() < 1e-13 * np.abs(u).max()
+        assert np.abs(qe.reshape(-1) - q[2 * pr.uoff[e]:2 * pr.uoff[e + 1]]).max() < 1e-13 * np.abs(q).max()
