@@ -179,8 +179,9 @@ typedef struct {
 #define HDG_PRECOND_FACE_SCHUR 16u  /* precondition with the inverted diagonal face blocks of the condensed
                                        operator, S_ff = sum over both sides of S_e's face rows and columns,
                                        instead of D_f of Sec. 6.1 (folded into the stored preconditioned rows
-                                       the same way; the apply costs the same). hdg_transpose returns to D^-1;
-                                       HDG_ERR_SINGULAR if a face block has a zero pivot. */
+                                       the same way; the apply costs the same). hdg_transpose keeps it (the
+                                       transposed operator's face blocks are S_ff^T); HDG_ERR_SINGULAR if a
+                                       face block has a zero pivot. */
 
 /* Build the structured macro mesh, the reference-lattice tables of level m
  * (mass, derivative, boundary and trace matrices, quadrature) and the device

@@ -409,24 +409,26 @@ class HDGSolve(torch.autograd.Function):
     backward pass first condenses it again at the saved kappa and f."""
 
     @staticmethod
-    def _prepare(problem, kappa, f, gD, mode, split):
+    def _prepare(problem, kappa, f, gD, mode, split, precond="d"):
         problem.set_kappa(kappa)
         problem.set_source(f, gD)
-        problem.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split)
+        problem.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split,
+                         precond=precond)
 
     @staticmethod
     def forward(ctx, kappa, f, problem, gD, opts):
         opts = dict(opts or {})
         tol, restart, mode = opts.get("tol", 1e-10), opts.get("restart", 80), opts.get("mode", 0)
         split, orth = opts.get("split_update", False), opts.get("orth", 0)
+        precond = opts.get("precond", "d")
         kappa_d, f_d = kappa.detach(), f.detach()
-        HDGSolve._prepare(problem, kappa_d, f_d, gD, mode, split)
+        HDGSolve._prepare(problem, kappa_d, f_d, gD, mode, split, precond)
         x, rep, st = problem.solve(problem.rhs(), tol=tol, restart=restart, mode=mode,
                                    maxit=opts.get("maxit", 20000), orth=orth)
         if st != HDG_OK:
             raise HDGError(st, f"forward solve did not converge: {rep}")
         u, _ = problem.recover(x)
-        ctx.problem, ctx.version, ctx.opts = problem, problem.version, (tol, restart, mode, split, orth)
+        ctx.problem, ctx.version, ctx.opts = problem, problem.version, (tol, restart, mode, split, orth, precond)
         ctx.gD = gD
         ctx.save_for_backward(x, u, kappa_d, f_d)
         return u
@@ -435,9 +437,9 @@ class HDGSolve(torch.autograd.Function):
     def backward(ctx, grad_u):
         pr = ctx.problem
         x, u, kappa, f = ctx.saved_tensors
-        tol, restart, mode, split, orth = ctx.opts
+        tol, restart, mode, split, orth, precond = ctx.opts
         if pr.version != ctx.version:
-            HDGSolve._prepare(pr, kappa, f, ctx.gD, mode, split)
+            HDGSolve._prepare(pr, kappa, f, ctx.gD, mode, split, precond)
         dk, df, _ = pr.adjoint(grad_u, x, u, tol=tol, restart=restart, mode=mode,
                                want_df=ctx.needs_input_grad[1], orth=orth)
         return (dk if ctx.needs_input_grad[0] else None), df, None, None, None

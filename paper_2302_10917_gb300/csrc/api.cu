@@ -735,7 +735,14 @@ hdg_status hdg_transpose(hdg_ctx* c) {
   c->launches += 1;
   if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose");
   c->transposed ^= 1;
-  c->pc_face = 0;      // the preconditioned rows are D^-1-folded again
+  if (c->pc_face) {
+    // the transposed operator's face blocks are S_ff^T: fold (S_ff^-1)^T into the rows again
+    e = launch_face_fold(c->prm, c->d_S, c->d_Pinv, c->transposed, c->d_St, c->d_St32, c->stream);
+    if (e == cudaSuccess && c->d_Stdf)
+      e = launch_split_df(c->d_St, c->d_Stdf, (int64_t)c->prm.N * 3 * c->prm.n_t * c->prm.P1, c->stream);
+    c->launches += 2;
+    if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose (face blocks)");
+  }
   return HDG_OK;
 }
 

@@ -482,7 +482,7 @@ static cudaError_t op_resid(hdg_ctx* c, const double* x, double* y, int nb, int6
 static cudaError_t op_dinv(hdg_ctx* c, const double* y, double* z, cudaStream_t st) {
   if (c->pc_face) {
     if (c->lv) return launch_level_face_pinv(c->lv->dv, c->lv->d_Pinv, y, z, 1, c->prm.N_tr, st);
-    return launch_face_pinv(c->prm, c->d_Pinv, y, z, st);
+    return launch_face_pinv(c->prm, c->d_Pinv, c->transposed, y, z, st);
   }
   if (c->lv) return launch_level_dinv(c, y, z, 1, c->prm.N_tr, st);
   return launch_face_dinv(c->prm, c->dt.Ghinv, c->d_escale, y, z, st);

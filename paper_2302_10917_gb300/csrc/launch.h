@@ -70,7 +70,11 @@ cudaError_t launch_level_dinv(hdg_ctx* c, const double* y, double* z, int nrhs, 
 // Face-block preconditioner with the diagonal blocks of S (precond.cu).
 cudaError_t launch_face_schur(const Params& P, const double* S, double* Pinv, double* St, float* St32, int* bad,
                               cudaStream_t st);
-cudaError_t launch_face_pinv(const Params& P, const double* Pinv, const double* y, double* z, cudaStream_t st);
+// refold the preconditioned rows from S (trans: S holds S_e^T, the inverse blocks are transposed)
+cudaError_t launch_face_fold(const Params& P, const double* S, const double* Pinv, int trans, double* St, float* St32,
+                             cudaStream_t st);
+cudaError_t launch_face_pinv(const Params& P, const double* Pinv, int trans, const double* y, double* z,
+                             cudaStream_t st);
 cudaError_t launch_level_face_schur(const LevelDev& L, int max_nf, const double* S, double* Pinv, double* St,
                                     int* bad, cudaStream_t st);
 cudaError_t launch_level_face_pinv(const LevelDev& L, const double* Pinv, const double* y, double* z, int nrhs,

@@ -99,8 +99,9 @@ __global__ void face_schur_kernel(Params P, const double* __restrict__ S, double
   }
 }
 
-// St[e][k][j][t] = sum_t2 S_ff^-1(t, t2) S[e][k][j][t2] on interior faces (element orientation)
-__global__ void fold_kernel(Params P, const double* __restrict__ S, const double* __restrict__ Pinv,
+// St[e][k][j][t] = sum_t2 S_ff^-1(t, t2) S[e][k][j][t2] on interior faces (element orientation);
+// trans: the blocks hold S_e^T (hdg_transpose), whose face blocks are S_ff^T, inverse (S_ff^-1)^T
+__global__ void fold_kernel(Params P, const double* __restrict__ S, const double* __restrict__ Pinv, int trans,
                             double* __restrict__ St, float* __restrict__ St32) {
   const int e = blockIdx.x / 3, k = blockIdx.x - 3 * (blockIdx.x / 3);
   if (e >= P.N) return;
@@ -113,7 +114,7 @@ __global__ void fold_kernel(Params P, const double* __restrict__ S, const double
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int t = idx / n, t2 = idx - t * n;
     const int s = flip[k] ? PP - t : t, s2 = flip[k] ? PP - t2 : t2;
-    Li[idx] = Pf[s * n + s2];
+    Li[idx] = trans ? Pf[s2 * n + s] : Pf[s * n + s2];
   }
   __syncthreads();
   const size_t base = ((size_t)e * 3 + k) * nt * n;
@@ -127,18 +128,18 @@ __global__ void fold_kernel(Params P, const double* __restrict__ S, const double
   }
 }
 
-// z_f = S_ff^-1 y_f on one FP64 vector (global orientation)
-__global__ void face_pinv_kernel(Params P, const double* __restrict__ Pinv, const double* __restrict__ y,
+// z_f = S_ff^-1 y_f (trans: (S_ff^-1)^T y_f) on one FP64 vector (global orientation)
+__global__ void face_pinv_kernel(Params P, const double* __restrict__ Pinv, int trans, const double* __restrict__ y,
                                  double* __restrict__ z) {
   const int64_t total = (int64_t)P.n_int * P.P1;
   const int n = P.P1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int f = (int)(idx / n), s = (int)(idx - (int64_t)f * n);
-    const double* row = Pinv + ((size_t)f * n + s) * n;
+    const double* Pf = Pinv + (size_t)f * n * n;
     const double* yf = y + (size_t)f * n;
     double acc = 0.0;
-    for (int t = 0; t < n; ++t) acc += row[t] * yf[t];
+    for (int t = 0; t < n; ++t) acc += (trans ? Pf[t * n + s] : Pf[s * n + t]) * yf[t];
     z[idx] = acc;
   }
 }
@@ -242,14 +243,22 @@ cudaError_t launch_face_schur(const Params& P, const double* S, double* Pinv, do
   cudaError_t e = set_smem((const void*)face_schur_kernel, sm);
   if (e != cudaSuccess) return e;
   face_schur_kernel<<<P.n_int, 128, sm, st>>>(P, S, Pinv, bad);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_face_fold(P, S, Pinv, 0, St, St32, st);
+}
+
+cudaError_t launch_face_fold(const Params& P, const double* S, const double* Pinv, int trans, double* St, float* St32,
+                             cudaStream_t st) {
   const size_t sm2 = (size_t)P.P1 * P.P1 * sizeof(double);
-  if ((e = set_smem((const void*)fold_kernel, sm2)) != cudaSuccess) return e;
-  fold_kernel<<<3 * P.N, 128, sm2, st>>>(P, S, Pinv, St, St32);
+  cudaError_t e = set_smem((const void*)fold_kernel, sm2);
+  if (e != cudaSuccess) return e;
+  fold_kernel<<<3 * P.N, 128, sm2, st>>>(P, S, Pinv, trans, St, St32);
   return cudaGetLastError();
 }
 
-cudaError_t launch_face_pinv(const Params& P, const double* Pinv, const double* y, double* z, cudaStream_t st) {
-  face_pinv_kernel<<<1024, 256, 0, st>>>(P, Pinv, y, z);
+cudaError_t launch_face_pinv(const Params& P, const double* Pinv, int trans, const double* y, double* z,
+                             cudaStream_t st) {
+  face_pinv_kernel<<<1024, 256, 0, st>>>(P, Pinv, trans, y, z);
   return cudaGetLastError();
 }
 

@@ -3,7 +3,9 @@ bench.py times: n = 128 (32,768 macro-elements), p = 2, levels by band of x
 (r = 1 below x = 0.7, 2, 3, r = 4 from x = 0.9 on; 462,020 trace unknowns,
 384 elements with a face finer than themselves), kappa = 1e-2, beta = (1, 0),
 64 Gaussian-bump sources (width 0.05, seeded centres), g_D = 0; split-FP32
-condensation, 64 right-hand sides in lockstep GMRES (split-FP32 operator).
+condensation, the face-block preconditioner with the diagonal blocks of S
+(restarted GMRES with D^-1 of Sec. 6.1 stalls on this mesh), 64 right-hand
+sides in lockstep GMRES (split-FP32 operator).
 
 The oracle checks sampled outputs one by one: Schur blocks of sampled
 elements of every level (conforming and non-conforming), the condensed
@@ -33,7 +35,7 @@ def big():
     gpu = Problem(CFG["n"], 1, CFG["p"], beta=CFG["beta"], kappa=CFG["kappa"], levels=lev)
     f = wl.gaussian_bumps(gpu.quad_points(), CFG["nrhs"], seed=3, width=CFG["width"]).contiguous()
     gpu.set_source(f)
-    gpu.condense(keep_factors=True, store_df64=True, split_update=True)
+    gpu.condense(keep_factors=True, store_df64=True, split_update=True, precond="face_schur")
     ora = LevelHDGProblem(CFG["n"], lev, CFG["p"], beta=CFG["beta"], kappa=CFG["kappa"])
     fc = {r: f[r].cpu().numpy() for r in COLS}
     yield gpu, ora, lev, fc

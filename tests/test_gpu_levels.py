@@ -232,3 +232,34 @@ def test_level_mesh_errors():
             assert ei.value.status == HDG_ERR_ARG and "level mesh" in str(ei.value)
     finally:
         pr.close()
+
+
+def test_band_levels_n32_against_the_oracle_direct_solution():
+    """n = 32 banded-level mesh (2 048 elements, 28 336 trace unknowns): the condensed
+    right-hand side and the solution at 600 sampled trace dofs against the oracle's sparse
+    direct solve (tests/golden/levels_band_n32.json, written by make_levels_band_n32.py),
+    with the D^-1 preconditioner (FP64 operator) and with the face blocks of S (split-FP32)."""
+    _need_gpu()
+    import json
+    import os
+    from paper_2302_10917_gb300 import Problem
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "levels_band_n32.json")))
+    n = gold["n"]
+    pr = Problem(n, 1, gold["p"], beta=tuple(gold["beta"]), kappa=gold["kappa"], levels=wl.band_levels(n))
+    try:
+        assert pr.info["N_tr"] == gold["N_tr"]
+        f = wl.gaussian_bumps(pr.quad_points(), 1, seed=gold["seed"], width=gold["width"])[0].contiguous()
+        pr.set_source(f)
+        dofs = torch.tensor(gold["dofs"], device="cuda")
+        xg, gg = np.array(gold["x"]), np.array(gold["g"])
+        for pc, mode, restart in (("d", 0, 128), ("face_schur", 2, 80)):
+            pr.condense(keep_factors=True, store_df64=True, split_update=(mode == 2), precond=pc)
+            g = pr.rhs()
+            assert abs(float(g.norm()) - gold["g_norm"]) <= 1e-12 * gold["g_norm"]
+            assert np.abs(g[dofs].cpu().numpy() - gg).max() <= 1e-12 * np.abs(gg).max()
+            x, rep, st = pr.solve(g, tol=1e-13, restart=restart, mode=mode, maxit=60000)
+            assert st == 0, (pc, rep)
+            assert np.abs(x[dofs].cpu().numpy() - xg).max() <= 1e-9 * gold["x_absmax"], pc
+            assert abs(float(x.norm()) - gold["x_norm"]) <= 1e-9 * gold["x_norm"]
+    finally:
+        pr.close()
