@@ -582,12 +582,13 @@ def bench_levels_many_source(stream, count=64):
             ts.append(e0.elapsed_time(e1) / 1e3)
         return statistics.median(ts)
     t1 = time_apply(X[0], 64)
+    t1df = time_apply(X[0], 48)
     t64 = {prec: time_apply(X, prec) for prec in (64, 48, 32)}
     from paper_2302_10917_gb300 import OFF_SCHUR
     offs = pr.offsets(OFF_SCHUR)
     rows = int(sum(int(round(math.sqrt(int(offs[e + 1] - offs[e])))) for e in range(pr.info["N"])))
-    # one column, FP64: blocks + gathered x (element-side rows) + element-side products written and
-    # read + one y write
+    # one column: blocks (8 B per entry, FP64 or split-FP32 pairs) + gathered x (element-side rows)
+    # + element-side products written and read + one y write
     bytes1 = ns * 8 + rows * 8 + 2 * rows * 8 + N_tr * 8
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
@@ -599,10 +600,13 @@ def bench_levels_many_source(stream, count=64):
            "condense_and_rhs_s": a.elapsed_time(b) / 1e3, "batched_solve_s": b.elapsed_time(c2) / 1e3,
            "batched_iterations": rep["iterations"], "batched_converged": bool(rep["converged"]),
            "batched_max_rel_residual": rep["rel_residual"], "recover_s": c2.elapsed_time(d) / 1e3,
-           "apply_1col_fp64_s": t1, "apply_1col_gdofs": N_tr / t1 / 1e9,
-           "apply_1col_roofline": {"bound": "hbm", "achieved": bytes1 / t1 / 1e9, "peak": hbm, "unit": "GB/s",
-                                   "frac": (bytes1 / t1 / 1e9 / hbm) if hbm else None, "traffic": None,
-                                   "bytes_per_launch": bytes1},
+           "apply_1col_fp64_s": t1, "apply_1col_split_s": t1df, "apply_1col_gdofs": N_tr / t1df / 1e9,
+           "apply_1col_roofline": {
+               "split_fp32": {"bound": "hbm", "achieved": bytes1 / t1df / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": (bytes1 / t1df / 1e9 / hbm) if hbm else None, "traffic": None,
+                              "bytes_per_launch": bytes1},
+               "fp64": {"bound": "fp64 pipe", "achieved": 2.0 * ns / t1 / 1e12, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": 2.0 * ns / t1 / 1e12 / FP64_PEAK_TFLOPS}},
            "apply_64col_s": {"fp64": t64[64], "split_fp32": t64[48], "fp32": t64[32]},
            "apply_64col_gdofs": {k: N_tr * count / v / 1e9 for k, v in
                                  (("fp64", t64[64]), ("split_fp32", t64[48]), ("fp32", t64[32]))},
