@@ -228,11 +228,14 @@ __device__ __forceinline__ typename LvAcc<BT>::T lv_zero() {
   else return typename LvAcc<BT>::T(0);
 }
 
-// z_r[row] = (S_e x_e,r)_a for the element-side rows of the CTA and RPT columns
+// z_r[row] = (S_e x_e,r)_a for the element-side rows of the CTA and RPT columns.
+// cols_fast: blockIdx.x = column group, blockIdx.y = row block, so that the CTAs
+// sharing a row block (and its blocks of S) run together and read S once from HBM.
 template <int BT, int VT, int RPT>
 __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* __restrict__ Sv,
                                                         const void* __restrict__ xv, int nrhs, int64_t vstride,
-                                                        void* __restrict__ zv, const int* __restrict__ stop) {
+                                                        void* __restrict__ zv, const int* __restrict__ stop,
+                                                        int cols_fast) {
   if (stop && *stop) return;
   using Acc = typename LvAcc<BT>::T;
   using ST = typename LvAcc<BT>::S;
@@ -240,12 +243,13 @@ __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* 
   Acc* zb = static_cast<Acc*>(zv);
   extern __shared__ unsigned char sraw[];
   Acc* xs = reinterpret_cast<Acc*>(sraw);   // rows of the CTA's elements x RPT columns
-  const int64_t z0 = (int64_t)blockIdx.x * LV_RB;
+  const int rb = cols_fast ? blockIdx.y : blockIdx.x, cg = cols_fast ? blockIdx.x : blockIdx.y;
+  const int64_t z0 = (int64_t)rb * LV_RB;
   const int64_t zl = min(z0 + (int64_t)LV_RB, L.nz) - 1;
   const int apf = L.row_ap[z0], apl = L.row_ap[zl];
   const int64_t xb = L.ap_zoff[apf];
   const int64_t xn = (int64_t)L.ap_zoff[apl] + L.ap_nt[apl] - xb;
-  const int c0 = blockIdx.y * RPT;
+  const int c0 = cg * RPT;
   for (int64_t i = threadIdx.x; i < xn * RPT; i += blockDim.x) {
     const int64_t row = xb + i / RPT;
     const int rr = (int)(i % RPT);
@@ -446,14 +450,16 @@ template <int BT, int VT, int RPT>
 cudaError_t lv_apply_t(const LevelMesh& L, const void* S, const void* x, void* y, int nrhs, int64_t vstride,
                        const double* escale, const int* stop, void* z, cudaStream_t st) {
   using Acc = typename LvAcc<BT>::T;
-  const dim3 grid((unsigned)((L.nz + LV_RB - 1) / LV_RB), (unsigned)((nrhs + RPT - 1) / RPT));
+  const unsigned rblocks = (unsigned)((L.nz + LV_RB - 1) / LV_RB), cgroups = (unsigned)((nrhs + RPT - 1) / RPT);
+  const int cols_fast = (cgroups > 1 && rblocks <= 65535u) ? 1 : 0;
+  const dim3 grid = cols_fast ? dim3(cgroups, rblocks) : dim3(rblocks, cgroups);
   const size_t sm = (size_t)(LV_RB + 2 * L.max_nt) * RPT * sizeof(Acc);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(lv_elem_kernel<BT, VT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
   }
-  lv_elem_kernel<BT, VT, RPT><<<grid, LV_RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop);
+  lv_elem_kernel<BT, VT, RPT><<<grid, LV_RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop, cols_fast);
   const int64_t total = L.dv.N_tr * nrhs;
   const int fg = (int)std::min<int64_t>(152 * 8, (total + 255) / 256);
   lv_face_kernel<BT, VT><<<fg, 256, 0, st>>>(L.dv, z, y, nrhs, vstride, escale, stop);
