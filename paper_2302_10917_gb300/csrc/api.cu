@@ -824,7 +824,7 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
-  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_Pinv);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_Pinv); cudaFree(c->d_cmapb);
   if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
   for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

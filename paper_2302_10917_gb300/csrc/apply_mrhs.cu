@@ -176,10 +176,12 @@ cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, co
 // (B) one thread per (column, edge dof): y_r(f, s) = scale_f (Z_e+,r(t+) +
 //     Z_e-,r(t-)) in a fixed order. Each element's trace values are read once
 //     (the edge-centric kernel reads them once per edge of the element).
+// cmap (optional): the nrhs columns computed are cmap[0 .. nrhs-1] of x and y
+// (the columns still iterating in the batched solver); Z holds them compactly.
 template <int BT>
 __global__ void __launch_bounds__(256) mrhs_element_kernel(Params P, const void* __restrict__ Sv,
                                                            const float2* __restrict__ x, int nrhs, int64_t vstride,
-                                                           float2* __restrict__ Z) {
+                                                           float2* __restrict__ Z, const int* __restrict__ cmap) {
   extern __shared__ float2 xs2[];            // [n_t][NR1]
   const int nt = P.n_t, P1 = P.P1, PP = P.P, NR1 = mrhs_row(nrhs);
   const int e = blockIdx.x;
@@ -190,7 +192,8 @@ __global__ void __launch_bounds__(256) mrhs_element_kernel(Params P, const void*
     const int r = idx / nt, c = idx - r * nt;
     const int kk = c / P1, t = c - kk * P1;
     float2 v = make_float2(0.f, 0.f);
-    if (r < nrhs && code[kk] >= 0) v = x[(size_t)r * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+    if (r < nrhs && code[kk] >= 0)
+      v = x[(size_t)(cmap ? cmap[r] : r) * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
     xs2[c * NR1 + r] = v;
   }
   __syncthreads();
@@ -219,7 +222,8 @@ __global__ void __launch_bounds__(256) mrhs_element_kernel(Params P, const void*
 }
 
 __global__ void mrhs_edge_sum_kernel(Params P, const float2* __restrict__ Z, int nrhs, int64_t vstride,
-                                     const double* __restrict__ escale, float2* __restrict__ y) {
+                                     const double* __restrict__ escale, float2* __restrict__ y,
+                                     const int* __restrict__ cmap) {
   const int nt = P.n_t, P1 = P.P1, PP = P.P;
   const int64_t per = (int64_t)P.n_int * P1;
   const int64_t total = per * nrhs;
@@ -244,30 +248,30 @@ __global__ void mrhs_edge_sum_kernel(Params P, const float2* __restrict__ Z, int
       h = ph;
       l = pl;
     }
-    y[(size_t)r * vstride + fs] = df_norm(h, l);
+    y[(size_t)(cmap ? cmap[r] : r) * vstride + fs] = df_norm(h, l);
   }
 }
 
 // Element-centric multi-RHS apply on split vectors; Z: [N][nrhs][n_t] pairs.
 cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
-                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st) {
+                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st, const int* cmap) {
   if (nrhs < 1 || nrhs > HDG_MAX_RHS) return cudaErrorInvalidValue;
   const size_t sm = (size_t)P.n_t * mrhs_row(nrhs) * sizeof(float2);
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t err;
   if (bt == 0) {
     err = cudaFuncSetAttribute(mrhs_element_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<0><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+    if (err == cudaSuccess) mrhs_element_kernel<0><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
   } else if (bt == 1) {
     err = cudaFuncSetAttribute(mrhs_element_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<1><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+    if (err == cudaSuccess) mrhs_element_kernel<1><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
   } else {
     err = cudaFuncSetAttribute(mrhs_element_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<2><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z);
+    if (err == cudaSuccess) mrhs_element_kernel<2><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
   }
   if (err != cudaSuccess) return err;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  mrhs_edge_sum_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, Z, nrhs, vstride, escale, y);
+  mrhs_edge_sum_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, Z, nrhs, vstride, escale, y, cmap);
   return cudaGetLastError();
 }
 

@@ -324,6 +324,7 @@ struct hdg_ctx {
   double* d_smallb = nullptr;     // [nrhs][small-array layout]
   int* d_flagb = nullptr;         // [nrhs][4]
   double* d_scalb = nullptr;      // [nrhs] gathered scalars
+  int* d_cmapb = nullptr;         // [nrhs] columns still iterating in the current restart cycle
   float2* d_Zb = nullptr;         // [N][nrhs][n_t] element products of the multi-RHS apply
   int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)

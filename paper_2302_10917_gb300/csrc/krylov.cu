@@ -783,9 +783,9 @@ __global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double*
 static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if (c->kb_restart == K && c->kb_nrhs == nb && c->d_Vb) return cudaSuccess;
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
-  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_cmapb);
   c->d_Vb = nullptr; c->d_wb = nullptr; c->d_rb = nullptr; c->d_partb = nullptr; c->d_smallb = nullptr;
-  c->d_flagb = nullptr; c->d_scalb = nullptr; c->d_Zb = nullptr;
+  c->d_flagb = nullptr; c->d_scalb = nullptr; c->d_Zb = nullptr; c->d_cmapb = nullptr;
   c->kb_restart = c->kb_nrhs = 0;
   const size_t n = (size_t)c->prm.N_tr, ldv = n + (n & 1);
   SmallLayout L(K);
@@ -802,6 +802,7 @@ static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if ((e = cudaMalloc(&c->d_scalb, (size_t)nb * 2 * sizeof(double))) != cudaSuccess) return e;
   const size_t nzb = c->lv ? 1 : (size_t)c->prm.N * nb * c->prm.n_t;   // level meshes use their own buffer
   if ((e = cudaMalloc(&c->d_Zb, nzb * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_cmapb, (size_t)nb * sizeof(int))) != cudaSuccess) return e;
   c->kb_restart = K;
   c->kb_nrhs = nb;
   return cudaSuccess;
@@ -890,6 +891,16 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
     cu.ok(cudaMemcpyAsync(d_done, done.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
     set_cycle_kernel<<<1, 64, 0, st>>>(fl, 4, d_done, sm, L.total, L.sc + 2, scal, nb);
     c->launches += 1;
+    // the Arnoldi operator of this cycle computes only the columns still iterating
+    std::vector<int> act;
+    for (int r = 0; r < nb; ++r)
+      if (!done[r]) act.push_back(r);
+    const int na = (int)act.size();
+    const int* cmap = nullptr;
+    if (na < nb) {
+      cu.ok(cudaMemcpyAsync(c->d_cmapb, act.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
+      cmap = c->d_cmapb;
+    }
     for (int r = 0; r < nb; ++r) {
       if (done[r]) continue;
       double* tr = t + (size_t)r * n;
@@ -909,11 +920,11 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       {
         ProfScope ps(c, phase);
         if (c->lv)
-          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, precond_scale(c),
-                                   nullptr, st));
+          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, na, ldv, precond_scale(c),
+                                   nullptr, st, cmap));
         else
-          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, nb, ldv, precond_scale(c),
-                                     c->d_Zb, st));
+          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, na, ldv, precond_scale(c),
+                                     c->d_Zb, st, cmap));
         c->launches += 1;
       }
       ProfScope po(c, HDG_PROF_ORTHO);

@@ -39,8 +39,10 @@ cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float
 int apply_edges_per_block(const Params& P);
 cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
                               int64_t vstride, const double* escale, cudaStream_t st);
+// cmap (optional): compute only the nrhs columns cmap[0 .. nrhs-1] of x and y
 cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
-                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st);
+                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st,
+                                 const int* cmap = nullptr);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,
@@ -64,7 +66,8 @@ cudaError_t level_ensure_z(hdg_ctx* c, int nrhs);
 // y = S x (escale null) or D^-1 S x (preconditioned blocks, escale) for nrhs columns of stride vstride;
 // bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks, vt: 0 FP64 / 1 split-FP32 / 2 FP32 vectors
 cudaError_t launch_level_apply(hdg_ctx* c, int bt, int vt, const void* S, const void* x, void* y, int nrhs,
-                               int64_t vstride, const double* escale, const int* stop, cudaStream_t st);
+                               int64_t vstride, const double* escale, const int* stop, cudaStream_t st,
+                               const int* cmap = nullptr);
 cudaError_t launch_level_dinv(hdg_ctx* c, const double* y, double* z, int nrhs, int64_t vstride, cudaStream_t st);
 
 // Face-block preconditioner with the diagonal blocks of S (precond.cu).

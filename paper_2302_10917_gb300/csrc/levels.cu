@@ -235,7 +235,7 @@ template <int BT, int VT, int RPT>
 __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* __restrict__ Sv,
                                                         const void* __restrict__ xv, int nrhs, int64_t vstride,
                                                         void* __restrict__ zv, const int* __restrict__ stop,
-                                                        int cols_fast) {
+                                                        int cols_fast, const int* __restrict__ cmap) {
   if (stop && *stop) return;
   using Acc = typename LvAcc<BT>::T;
   using ST = typename LvAcc<BT>::S;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* 
     const int rr = (int)(i % RPT);
     const int d = L.xmap[row];
     Acc v = lv_zero<BT>();
-    if (d >= 0 && c0 + rr < nrhs) v = lv_load<BT, VT>(xv, (size_t)(c0 + rr) * vstride + d);
+    if (d >= 0 && c0 + rr < nrhs) v = lv_load<BT, VT>(xv, (size_t)(cmap ? cmap[c0 + rr] : c0 + rr) * vstride + d);
     xs[i] = v;
   }
   __syncthreads();
@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* 
 // y_r(i) = scale_f ((S x)_{side 0} + (S x)_{side 1}) at trace dof i of face f
 template <int BT, int VT>
 __global__ void lv_face_kernel(LevelDev L, const void* __restrict__ zv, void* __restrict__ yv, int nrhs,
-                               int64_t vstride, const double* __restrict__ escale, const int* __restrict__ stop) {
+                               int64_t vstride, const double* __restrict__ escale, const int* __restrict__ stop,
+                               const int* __restrict__ cmap) {
   if (stop && *stop) return;
   using Acc = typename LvAcc<BT>::T;
   const Acc* zb = static_cast<const Acc*>(zv);
@@ -335,7 +336,7 @@ __global__ void lv_face_kernel(LevelDev L, const void* __restrict__ zv, void* __
     const int t0 = (fl & 1) ? Pf - s : s, t1 = (fl & 2) ? Pf - s : s;
     const Acc a0 = zb[(size_t)r * L.nz + L.ez[2 * f] + t0];
     const Acc a1 = zb[(size_t)r * L.nz + L.ez[2 * f + 1] + t1];
-    const size_t o = (size_t)r * vstride + i;
+    const size_t o = (size_t)(cmap ? cmap[r] : r) * vstride + i;
     if constexpr (BT == 1) {
       float h = a0.x, l = a0.y;
       df_add(h, l, a1.x, a1.y);
@@ -448,7 +449,7 @@ __global__ void lv_bnd_points_kernel(Params P, DevTables dt, const int* __restri
 
 template <int BT, int VT, int RPT>
 cudaError_t lv_apply_t(const LevelMesh& L, const void* S, const void* x, void* y, int nrhs, int64_t vstride,
-                       const double* escale, const int* stop, void* z, cudaStream_t st) {
+                       const double* escale, const int* stop, void* z, cudaStream_t st, const int* cmap) {
   using Acc = typename LvAcc<BT>::T;
   const unsigned rblocks = (unsigned)((L.nz + LV_RB - 1) / LV_RB), cgroups = (unsigned)((nrhs + RPT - 1) / RPT);
   const int cols_fast = (cgroups > 1 && rblocks <= 65535u) ? 1 : 0;
@@ -459,18 +460,18 @@ cudaError_t lv_apply_t(const LevelMesh& L, const void* S, const void* x, void* y
                                          (int)sm);
     if (e != cudaSuccess) return e;
   }
-  lv_elem_kernel<BT, VT, RPT><<<grid, LV_RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop, cols_fast);
+  lv_elem_kernel<BT, VT, RPT><<<grid, LV_RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop, cols_fast, cmap);
   const int64_t total = L.dv.N_tr * nrhs;
   const int fg = (int)std::min<int64_t>(152 * 8, (total + 255) / 256);
-  lv_face_kernel<BT, VT><<<fg, 256, 0, st>>>(L.dv, z, y, nrhs, vstride, escale, stop);
+  lv_face_kernel<BT, VT><<<fg, 256, 0, st>>>(L.dv, z, y, nrhs, vstride, escale, stop, cmap);
   return cudaGetLastError();
 }
 
 template <int BT, int VT>
 cudaError_t lv_apply_r(const LevelMesh& L, const void* S, const void* x, void* y, int nrhs, int64_t vstride,
-                       const double* escale, const int* stop, void* z, cudaStream_t st) {
-  return nrhs > 1 ? lv_apply_t<BT, VT, 8>(L, S, x, y, nrhs, vstride, escale, stop, z, st)
-                  : lv_apply_t<BT, VT, 1>(L, S, x, y, nrhs, vstride, escale, stop, z, st);
+                       const double* escale, const int* stop, void* z, cudaStream_t st, const int* cmap) {
+  return nrhs > 1 ? lv_apply_t<BT, VT, 8>(L, S, x, y, nrhs, vstride, escale, stop, z, st, cmap)
+                  : lv_apply_t<BT, VT, 1>(L, S, x, y, nrhs, vstride, escale, stop, z, st, cmap);
 }
 
 Params level_params(const hdg_mesh_desc* d, const RefTables& T, int N, int n_int) {
@@ -867,7 +868,8 @@ hdg_status level_condense(hdg_ctx* c, unsigned flags) {
   {
     const int64_t total = L.dv.N_tr * nrhs;
     const int fg = (int)std::min<int64_t>(152 * 8, (total + 255) / 256);
-    lv_face_kernel<0, 0><<<fg, 256, 0, c->stream>>>(L.dv, L.d_gel, c->d_g, nrhs, L.dv.N_tr, nullptr, nullptr);
+    lv_face_kernel<0, 0><<<fg, 256, 0, c->stream>>>(L.dv, L.d_gel, c->d_g, nrhs, L.dv.N_tr, nullptr, nullptr,
+                                                    nullptr);
     c->launches += 1;
   }
   for (LevelBin& B : L.bins) {
@@ -939,12 +941,13 @@ cudaError_t level_ensure_z(hdg_ctx* c, int nrhs) {
 }
 
 cudaError_t launch_level_apply(hdg_ctx* c, int bt, int vt, const void* S, const void* x, void* y, int nrhs,
-                               int64_t vstride, const double* escale, const int* stop, cudaStream_t st) {
+                               int64_t vstride, const double* escale, const int* stop, cudaStream_t st,
+                               const int* cmap) {
   const LevelMesh& L = *c->lv;
   if (!L.d_z || L.z_rhs < nrhs) return cudaErrorInvalidValue;
   void* z = L.d_z;
 #define LV_CASE(B, V) \
-  if (bt == B && vt == V) return lv_apply_r<B, V>(L, S, x, y, nrhs, vstride, escale, stop, z, st);
+  if (bt == B && vt == V) return lv_apply_r<B, V>(L, S, x, y, nrhs, vstride, escale, stop, z, st, cmap);
   LV_CASE(0, 0) LV_CASE(0, 1) LV_CASE(1, 0) LV_CASE(1, 1) LV_CASE(2, 1) LV_CASE(2, 2)
 #undef LV_CASE
   return cudaErrorInvalidValue;

@@ -263,3 +263,70 @@ def test_band_levels_n32_against_the_oracle_direct_solution():
             assert abs(float(x.norm()) - gold["x_norm"]) <= 1e-9 * gold["x_norm"]
     finally:
         pr.close()
+
+
+@pytest.mark.parametrize("n,lev,p,supg", [
+    (1, [0, 3], 2, False),            # one macro square, its two elements three levels apart
+    (2, [0] * 8, 2, False),           # every element of level 0: standard HDG with level-mesh layouts
+    (2, [1, 2, 2, 1, 0, 1, 2, 0], 2, True),   # SUPG inside macro-elements of different levels
+    (2, [2, 0, 1, 1, 0, 2, 1, 0], 3, True),
+])
+def test_edge_cases_and_supg(n, lev, p, supg):
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    lev = np.array(lev)
+    beta, kappa = (0.9, -0.5), (0.05 if supg else 0.8)
+    ora = LevelHDGProblem(n, lev, p, beta=beta, kappa=kappa, supg=supg)
+    gpu = Problem(n, 1, p, beta=beta, kappa=kappa, levels=lev, supg=supg)
+    try:
+        g = np.random.default_rng([wl.MASTER_SEED, 74, n, p, int(supg)])
+        f = g.standard_normal(ora.qoff[-1])
+        gD = g.standard_normal(ora.boff[-1])
+        gpu.set_source(torch.from_numpy(f), torch.from_numpy(gD))
+        gpu.condense(keep_factors=True)
+        S_el, g_o, gh = ora.condense(f, gD)
+        from paper_2302_10917_gb300 import OFF_SCHUR
+        S = gpu.schur().cpu().numpy()
+        off = gpu.offsets(OFF_SCHUR).numpy()
+        # SUPG's consistency term makes A_u less well conditioned (see test_gpu_supg.py)
+        tol = 2e-10 if supg else 1e-12
+        for e in range(ora.N):
+            assert rel(S[off[e]:off[e + 1]], S_el[e].reshape(-1)) < tol, e
+        assert rel(gpu.rhs().cpu().numpy(), g_o) < tol
+        x_dir = np.linalg.solve(ora.assemble_S(S_el), g_o)
+        x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60, mode=0, maxit=40000)
+        assert st == 0, rep
+        assert rel(x.cpu().numpy(), x_dir) < 1e-8
+        u, q = gpu.recover(x)
+        u_o, q_o = ora.recover(x_dir, f, gh)
+        assert rel(u.cpu().numpy(), u_o) < 1e-8 and rel(q.cpu().numpy(), q_o) < 1e-8
+    finally:
+        gpu.close()
+
+
+def test_batched_columns_finishing_in_different_cycles():
+    """Lockstep GMRES whose columns converge in different restart cycles (a zero column, a
+    smooth and a rough source): the Arnoldi operator then runs on the remaining columns
+    only; every column equals its own single-column solve."""
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    n, p = 3, 2
+    lev = band_levels(n, edges=(0.4, 0.6, 0.8), base=0)
+    pr = Problem(n, 1, p, beta=(1.0, 0.3), kappa=0.05, levels=lev)
+    try:
+        xy = pr.quad_points()
+        rough = torch.from_numpy(np.random.default_rng([wl.MASTER_SEED, 75]).standard_normal(xy.shape[0])).cuda()
+        f = torch.stack([torch.sin(3.0 * xy[:, 0]) * xy[:, 1], torch.zeros_like(rough), rough, 0.5 * rough])
+        pr.set_source(f)
+        pr.condense(keep_factors=True, store_df64=True, split_update=True)
+        g = pr.rhs()
+        x, rep, st = pr.solve(g, tol=1e-12, restart=10, mode=2, maxit=20000)
+        assert st == 0, rep
+        assert torch.count_nonzero(x[1]) == 0
+        for r in (0, 2, 3):
+            xr, rr, sr = pr.solve(g[r].contiguous(), tol=1e-12, restart=10, mode=2, maxit=20000)
+            assert sr == 0, rr
+            assert rel(x[r].cpu().numpy(), xr.cpu().numpy()) < 1e-9, r
+        assert rel(x[3].cpu().numpy(), 0.5 * x[2].cpu().numpy()) < 1e-9
+    finally:
+        pr.close()
