@@ -472,6 +472,7 @@ def run_ours(args):
     if not args.no_extras:
         line["multi_rhs"] = bench_multi_rhs(stream)
         line["levels_many_source"] = bench_levels_many_source(stream)
+        line["mixed_precision_n256"] = bench_mixed_precision_n256(stream)
         line["gradient"] = bench_gradient(stream)
         line["macro_vs_standard"] = bench_macro_vs_standard(stream)
         line["supg_layer"] = bench_supg_layer(stream)
@@ -616,6 +617,51 @@ def bench_levels_many_source(stream, count=64):
                "split_fp32": {"bound": "alu (FP32 pipe, split arithmetic)", "achieved": flops64 / t64[48] / 1e12,
                               "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s (FP64-equivalent)",
                               "frac": flops64 / t64[48] / 1e12 / DF_PEAK_TFLOPS}}}
+    pr.close()
+    return out
+
+
+def bench_mixed_precision_n256(stream):
+    """The large workload's element at n = 256 (131 072 macro-elements, N_tr = 4 902 400):
+    one condensation (split-FP32 elimination, FP64-accurate blocks; FP32 and split-FP32
+    copies of the preconditioned blocks), then the solve to 1e-10 with the FP64 operator,
+    the FP32 operator inside FP64 residual replacement and the split-FP32 operator (face-block
+    preconditioner), and the reduced-precision solutions' relative l2 differences from the
+    FP64 one (trace, u, q)."""
+    import torch
+    from paper_2302_10917_gb300 import Problem
+    from paper_2302_10917_gb300 import workloads as wl
+    cfg = wl.CONFIGS["c2"]
+    pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
+    pr.set_source(wl.sin_sin_source(pr.quad_points(), cfg["kappa"], cfg["beta"]).contiguous())
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    a, b = ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    # factors not kept (131 072 local systems would take 169 GB): chunked condensation, the
+    # back-solve condenses each chunk again
+    pr.condense(keep_factors=False, store_fp32=True, store_df64=True, split_update=True, precond="face_schur")
+    b.record(stream)
+    torch.cuda.synchronize()
+    g = pr.rhs()
+    sols, out = {}, {"workload": f"n={cfg['n']} m={cfg['m']} p={cfg['p']} beta=50(cos 0.3, sin 0.3) kappa=1, "
+                                 "u = sin(pi x) sin(pi y); face-block preconditioner, GMRES(80), CGS",
+                     "N_tr": pr.info["N_tr"], "condense_s": a.elapsed_time(b) / 1e3, "modes": {}}
+    for mode in (0, 1, 2):
+        t0, t1 = ev(), ev()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, maxit=60000, mode=mode, orth=1)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        u, q = pr.recover(x)
+        sols[mode] = (x, u, q)
+        out["modes"][MODE_NAMES[mode]] = {"seconds": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
+                                          "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"])}
+    rel = lambda a, b: float((a - b).norm() / b.norm())
+    for mode in (1, 2):
+        out["modes"][MODE_NAMES[mode]]["rel_l2_vs_fp64"] = {
+            name: rel(sols[mode][k], sols[0][k]) for k, name in enumerate(("trace", "u", "q"))}
     pr.close()
     return out
 

@@ -136,3 +136,35 @@ def test_mixed_precision_solutions_match_fp64_at_full_size(big):
     for mode in (1, 2):
         for k in range(3):
             assert rel(sols[mode][k], sols[0][k]) < 1e-9, (mode, k, rel(sols[mode][k], sols[0][k]))
+
+
+def test_n256_sampled_blocks_and_mixed_precision_solutions():
+    """n = 256 (131 072 macro-elements, N_tr = 4 902 400), the calls the benchmark's
+    mixed-precision section makes: sampled Schur blocks against the oracle, and the FP32
+    (with FP64 residual replacement) and split-FP32 solutions against the FP64 one."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_10917_gb300 import Problem
+    cfg = wl.CONFIGS["c2"]
+    gpu = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"])
+    try:
+        gpu.set_source(wl.sin_sin_source(gpu.quad_points(), cfg["kappa"], cfg["beta"]))
+        # factors not kept (they would take 169 GB): chunked condensation, re-condensed for the back-solve
+        gpu.condense(keep_factors=False, store_fp32=True, store_df64=True, split_update=True, precond="face_schur")
+        ora = HDGProblem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"])
+        for e in (0, 77777, ora.mesh.N - 1):
+            S_o, _ = ora.condense_element(int(e))
+            S_g = gpu.schur(int(e), 1)[0].cpu().numpy()
+            assert np.abs(S_g - S_o).max() / np.abs(S_o).max() < 1e-12, e
+        g = gpu.rhs()
+        sols = {}
+        for mode in (0, 1, 2):
+            x, rep, st = gpu.solve(g, tol=1e-10, restart=80, mode=mode, orth=1, maxit=60000)
+            assert st == 0 and rep["rel_residual"] <= 1e-10, (mode, rep)
+            sols[mode] = (x,) + tuple(gpu.recover(x))
+        rel = lambda a, b: float((a - b).norm() / b.norm())
+        for mode in (1, 2):
+            for k in range(3):
+                assert rel(sols[mode][k], sols[0][k]) < 1e-8, (mode, k)
+    finally:
+        gpu.close()
