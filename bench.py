@@ -554,6 +554,7 @@ def bench_levels_many_source(stream, count=64):
     flags = dict(keep_factors=True, store_df64=True, store_fp32=True, split_update=True, precond="face_schur")
     pr.set_source(f)
     pr.condense(**flags)            # first pass: allocations and launch set-up
+    tune = pr.autotune(mode=2, restart=80)     # element-side rows per CTA, Krylov launch shapes
     a, b, c2, d = ev(), ev(), ev(), ev()
     torch.cuda.synchronize()
     a.record(stream)
@@ -598,6 +599,7 @@ def bench_levels_many_source(stream, count=64):
                        f"(r=1..4: {[int((lev == r).sum()) for r in (1, 2, 3, 4)]} elements), faces at the finer "
                        f"side, {count} Gaussian-bump sources (width {cfg['width']}, seeded centres), g_D = 0",
            "N_tr": N_tr, "element_side_rows": rows, "schur_bytes_fp64": ns * 8, "sources": count,
+           "autotune": tune,
            "condense_and_rhs_s": a.elapsed_time(b) / 1e3, "batched_solve_s": b.elapsed_time(c2) / 1e3,
            "batched_iterations": rep["iterations"], "batched_converged": bool(rep["converged"]),
            "batched_max_rel_residual": rep["rel_residual"], "recover_s": c2.elapsed_time(d) / 1e3,
@@ -608,6 +610,12 @@ def bench_levels_many_source(stream, count=64):
                               "bytes_per_launch": bytes1},
                "fp64": {"bound": "fp64 pipe", "achieved": 2.0 * ns / t1 / 1e12, "peak": FP64_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": 2.0 * ns / t1 / 1e12 / FP64_PEAK_TFLOPS}},
+           "arnoldi_operator_roofline": {
+               "kernel": "lv_elem_kernel<1,1,1> + lv_face_kernel (split-FP32 blocks and vectors: the GMRES operator), "
+                         "best of 5 in hdg_autotune", "bound": "hbm", "launch_ms": tune["apply_ms"],
+               "achieved": bytes1 / (tune["apply_ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": (bytes1 / (tune["apply_ms"] / 1e3) / 1e9 / hbm) if hbm else None,
+               "bytes_per_launch": bytes1},
            "apply_64col_s": {"fp64": t64[64], "split_fp32": t64[48], "fp32": t64[32]},
            "apply_64col_gdofs": {k: N_tr * count / v / 1e9 for k, v in
                                  (("fp64", t64[64]), ("split_fp32", t64[48]), ("fp32", t64[32]))},

@@ -78,8 +78,9 @@
  *                    dofs face by face in the element's own edge orientation)
  *                    at HDG_OFF_SCHUR[e].
  * Several right-hand sides stack those arrays (RHS-major). On a level mesh
- * hdg_run_host, hdg_condense_static, hdg_autotune, hdg_set_kappa and the
- * adjoint entry points return HDG_ERR_ARG.
+ * hdg_run_host, hdg_condense_static, hdg_set_kappa and the adjoint entry
+ * points return HDG_ERR_ARG; hdg_autotune tunes the element-side rows per
+ * CTA of the apply (128, 256 or 512) and the Krylov kernels.
  */
 #ifndef MEHDG_H
 #define MEHDG_H
@@ -363,8 +364,8 @@ hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, 
  * follow its block count (fixed per context, so solves stay reproducible).
  * Needs hdg_condense (with the blocks the mode uses). Synchronous. */
 typedef struct {
-  int apply_edges_per_block; /* chosen edges per block of the apply */
-  int apply_threads;         /* threads per block that implies */
+  int apply_edges_per_block; /* chosen edges per block of the apply (0 on a level mesh) */
+  int apply_threads;         /* threads per block that implies (level mesh: element-side rows per CTA) */
   int mdot_blocks;           /* multi-dot blocks over all vector groups */
   int update_blocks;         /* streaming-update blocks */
   double apply_ms;           /* best times of the three kernels */

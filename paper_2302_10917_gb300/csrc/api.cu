@@ -594,11 +594,12 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
   if (!c) return HDG_ERR_ARG;
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
-  if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_autotune: not available on a level mesh");
   if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
-  if (o->mode == 1 && !c->d_St32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
-  if (o->mode == 2 && !c->d_Stdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
+  const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
+  if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
+  if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
   *rep = hdg_tune_report{};
   return autotune(c, *o, *rep);
 }

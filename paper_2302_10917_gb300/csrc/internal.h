@@ -269,6 +269,7 @@ struct LevelMesh {
   double* d_z = nullptr;        // [HDG_MAX_RHS][nz] element-side products
   int z_rhs = 0;
   int max_nf = 0;               // largest face block (2^R p + 1)
+  int rb = 256;                 // element-side rows per CTA of the apply (hdg_autotune: 128, 256 or 512)
   double* d_Pinv = nullptr;     // [poff[n_int]] inverted face blocks (HDG_PRECOND_FACE_SCHUR)
   int64_t pinv_count = 0;
 };

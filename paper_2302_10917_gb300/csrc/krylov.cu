@@ -607,7 +607,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       const int timed = c->prof_on ? 1 : 0;
       const std::vector<intptr_t> key = {K, bt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
-                                         (intptr_t)np, kgd, kgu, epb};
+                                         (intptr_t)np, kgd, kgu, epb, c->lv ? c->lv->rb : 0};
       if (timed && (int)c->gm_ev.size() < 4 * K) {
         while ((int)c->gm_ev.size() < 4 * K) {
           cudaEvent_t ev;
@@ -686,7 +686,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   const int64_t n = P.N_tr, ldv = n + (n & 1), np = ldv / 2;
   const Batch one{np, 0, 0, 0, 0, 0};
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
-  const void* Sop = o.mode == 0 ? (const void*)c->d_St : (o.mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
+  const void* Sop = op_blocks(c, o.mode);
   float2* V = c->d_V;
   const float4* V4 = reinterpret_cast<const float4*>(V);
   float4* w4 = reinterpret_cast<float4*>(c->d_w);
@@ -711,18 +711,30 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
     }
     return best;
   };
-  // apply: edges per block for 128 .. 512 threads
-  const int def_epb = apply_edges_per_block(P);
-  int best_epb = def_epb;
+  // apply: edges per block for 128 .. 512 threads (level meshes: element-side rows per CTA)
+  const int def_epb = c->lv ? 0 : apply_edges_per_block(P);
+  int best_epb = def_epb, best_rb = 256;
   double best_apply = 1e30, def_apply = 0.0;
+  if (c->lv) {
+    if (!cu.ok(level_ensure_z(c, 1))) return fail(c, HDG_ERR_OOM, "element-side buffer");
+    for (int rb : {128, 256, 512}) {
+      c->lv->rb = rb;
+      const double t = time_it([&] { cu.ok(launch_level_apply(c, bt, 1, Sop, V, c->d_w, 1, ldv, precond_scale(c),
+                                                              nullptr, st)); });
+      if (rb == 256) def_apply = t;
+      if (t < best_apply) { best_apply = t; best_rb = rb; }
+    }
+    c->lv->rb = best_rb;
+  }
   for (int threads : {128, 256, 384, 512}) {
+    if (c->lv) break;
     const int epb = threads / P.P1 > 0 ? threads / P.P1 : 1;
     if (epb * P.P1 > 512) continue;
     const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, epb)); });
     if (epb == def_epb) def_apply = t;
     if (t < best_apply) { best_apply = t; best_epb = epb; }
   }
-  if (def_apply == 0.0)
+  if (def_apply == 0.0 && !c->lv)
     def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb)); });
   // multi-dot blocks
   int best_kgd = KGD;
@@ -749,11 +761,11 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   cudaEventDestroy(e1);
   c->launches += 6 * (4 + 3 + 4) + 1;
   if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(cu.err));
-  c->tune_epb[bt] = best_epb;
+  if (!c->lv) c->tune_epb[bt] = best_epb;
   c->tune_kgd = best_kgd;
   c->tune_kgu = best_kgu;
   rep.apply_edges_per_block = best_epb;
-  rep.apply_threads = (best_epb * P.P1 + 31) / 32 * 32;
+  rep.apply_threads = c->lv ? best_rb : (best_epb * P.P1 + 31) / 32 * 32;
   rep.mdot_blocks = best_kgd;
   rep.update_blocks = best_kgu;
   rep.apply_ms = best_apply;

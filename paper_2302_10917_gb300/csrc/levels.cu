@@ -34,7 +34,7 @@ namespace mehdg {
 
 namespace {
 
-constexpr int LV_RB = 256;                  // element-side rows per CTA of the apply
+constexpr int LV_RB_MAX = 512;              // element-side rows per CTA of the apply: at most (default 256)
 constexpr size_t kLvMaxSmem = 227 * 1024;
 
 template <typename T>
@@ -232,7 +232,7 @@ __device__ __forceinline__ typename LvAcc<BT>::T lv_zero() {
 // cols_fast: blockIdx.x = column group, blockIdx.y = row block, so that the CTAs
 // sharing a row block (and its blocks of S) run together and read S once from HBM.
 template <int BT, int VT, int RPT>
-__global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* __restrict__ Sv,
+__global__ void __launch_bounds__(LV_RB_MAX) lv_elem_kernel(LevelDev L, const void* __restrict__ Sv,
                                                         const void* __restrict__ xv, int nrhs, int64_t vstride,
                                                         void* __restrict__ zv, const int* __restrict__ stop,
                                                         int cols_fast, const int* __restrict__ cmap) {
@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(LV_RB) lv_elem_kernel(LevelDev L, const void* 
   extern __shared__ unsigned char sraw[];
   Acc* xs = reinterpret_cast<Acc*>(sraw);   // rows of the CTA's elements x RPT columns
   const int rb = cols_fast ? blockIdx.y : blockIdx.x, cg = cols_fast ? blockIdx.x : blockIdx.y;
-  const int64_t z0 = (int64_t)rb * LV_RB;
-  const int64_t zl = min(z0 + (int64_t)LV_RB, L.nz) - 1;
+  const int64_t z0 = (int64_t)rb * blockDim.x;    // one thread per element-side row
+  const int64_t zl = min(z0 + (int64_t)blockDim.x, L.nz) - 1;
   const int apf = L.row_ap[z0], apl = L.row_ap[zl];
   const int64_t xb = L.ap_zoff[apf];
   const int64_t xn = (int64_t)L.ap_zoff[apl] + L.ap_nt[apl] - xb;
@@ -451,16 +451,17 @@ template <int BT, int VT, int RPT>
 cudaError_t lv_apply_t(const LevelMesh& L, const void* S, const void* x, void* y, int nrhs, int64_t vstride,
                        const double* escale, const int* stop, void* z, cudaStream_t st, const int* cmap) {
   using Acc = typename LvAcc<BT>::T;
-  const unsigned rblocks = (unsigned)((L.nz + LV_RB - 1) / LV_RB), cgroups = (unsigned)((nrhs + RPT - 1) / RPT);
+  const int RB = L.rb;
+  const unsigned rblocks = (unsigned)((L.nz + RB - 1) / RB), cgroups = (unsigned)((nrhs + RPT - 1) / RPT);
   const int cols_fast = (cgroups > 1 && rblocks <= 65535u) ? 1 : 0;
   const dim3 grid = cols_fast ? dim3(cgroups, rblocks) : dim3(rblocks, cgroups);
-  const size_t sm = (size_t)(LV_RB + 2 * L.max_nt) * RPT * sizeof(Acc);
+  const size_t sm = (size_t)(RB + 2 * L.max_nt) * RPT * sizeof(Acc);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(lv_elem_kernel<BT, VT, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
   }
-  lv_elem_kernel<BT, VT, RPT><<<grid, LV_RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop, cols_fast, cmap);
+  lv_elem_kernel<BT, VT, RPT><<<grid, RB, sm, st>>>(L.dv, S, x, nrhs, vstride, z, stop, cols_fast, cmap);
   const int64_t total = L.dv.N_tr * nrhs;
   const int fg = (int)std::min<int64_t>(152 * 8, (total + 255) / 256);
   lv_face_kernel<BT, VT><<<fg, 256, 0, st>>>(L.dv, z, y, nrhs, vstride, escale, stop, cmap);

@@ -225,8 +225,7 @@ def test_level_mesh_errors():
     try:
         pr.set_source(torch.zeros(pr.info["n_qp_total"], dtype=torch.float64))
         pr.condense()
-        for call in (lambda: pr.autotune(), lambda: pr.transpose(),
-                     lambda: pr.set_kappa(torch.ones(8, dtype=torch.float64))):
+        for call in (lambda: pr.transpose(), lambda: pr.set_kappa(torch.ones(8, dtype=torch.float64))):
             with pytest.raises(HDGError) as ei:
                 call()
             assert ei.value.status == HDG_ERR_ARG and "level mesh" in str(ei.value)
@@ -330,3 +329,15 @@ def test_batched_columns_finishing_in_different_cycles():
         assert rel(x[3].cpu().numpy(), 0.5 * x[2].cpu().numpy()) < 1e-9
     finally:
         pr.close()
+
+
+def test_autotune_on_a_level_mesh(case):
+    """hdg_autotune picks the apply's element-side rows per CTA (and the Krylov launch
+    shapes); the tuned solve still matches the oracle."""
+    ora, gpu = case["ora"], case["gpu"]
+    rep = gpu.autotune(mode=2, restart=60)
+    assert rep["apply_threads"] in (128, 256, 512) and rep["apply_edges_per_block"] == 0
+    x_dir = np.linalg.solve(ora.assemble_S(case["S"]), case["g"])
+    x, r, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60, mode=2, maxit=20000)
+    assert st == 0, r
+    assert rel(x.cpu().numpy(), x_dir) < 1e-9
