@@ -245,30 +245,32 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
     out = df_norm(h0, l0);
   } else if constexpr (BT == 2) {
     // both sides' terms as one sequence q = 0 .. 2 n_t - 1; loads of the next
-    // batch of 8 are issued before the arithmetic of the current one
+    // batch of G2 are issued before the arithmetic of the current one (4-byte
+    // entries: twice the split variant's loads in flight for the same bytes)
+    constexpr int G2 = 16;
     const int nq = 2 * nt;
     const float* S = static_cast<const float*>(Sv);
     const float* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
     const float* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
     const float* xv = xs + le * 2 * nt;
     float acc0 = 0.f, acc1 = 0.f;
-    float cur[8], nxt[8];
+    float cur[G2], nxt[G2];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : 0.f;
-    for (int q0 = 0; q0 < nq; q0 += 8) {
+    for (int u = 0; u < G2; ++u) cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : 0.f;
+    for (int q0 = 0; q0 < nq; q0 += G2) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + 8 + u;
+      for (int u = 0; u < G2; ++u) {
+        const int q = q0 + G2 + u;
         nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < G2; u += 2) {
         const int q = q0 + u;
         if (q < nq) acc0 = fmaf(cur[u], xv[q], acc0);
         if (q + 1 < nq) acc1 = fmaf(cur[u + 1], xv[q + 1], acc1);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+      for (int u = 0; u < G2; ++u) cur[u] = nxt[u];
     }
     float r = acc0 + acc1;
     if (escale) r *= (float)escale[f];
