@@ -214,13 +214,24 @@ def test_uniform_levels_equal_the_uniform_context():
 
 def test_level_mesh_errors():
     _need_gpu()
-    from paper_2302_10917_gb300 import HDG_ERR_ARG, HDGError, Problem
+    from paper_2302_10917_gb300 import HDG_ERR_ARG, HDG_ERR_SINGULAR, HDGError, Problem
     with pytest.raises(HDGError) as ei:
         Problem(2, 1, 2, levels=np.full(8, 5))
     assert ei.value.status == HDG_ERR_ARG
     with pytest.raises(HDGError) as ei:
         Problem(2, 1, 3, levels=np.full(8, 4))          # level 4 at p = 3 exceeds shared memory
     assert ei.value.status == HDG_ERR_ARG
+    # a zero local matrix (kappa = 0, beta = 0) on element 5 of level 2 is reported with its element id
+    kap = np.ones(8)
+    kap[5] = 0.0
+    bad = Problem(2, 1, 2, beta=(0.0, 0.0), kappa=kap, levels=np.arange(8) % 3)
+    try:
+        bad.set_source(torch.zeros(bad.info["n_qp_total"], dtype=torch.float64))
+        with pytest.raises(HDGError) as ei:
+            bad.condense()
+        assert ei.value.status == HDG_ERR_SINGULAR and "element 5" in str(ei.value)
+    finally:
+        bad.close()
     pr = Problem(2, 1, 2, levels=np.arange(8) % 3)
     try:
         pr.set_source(torch.zeros(pr.info["n_qp_total"], dtype=torch.float64))
