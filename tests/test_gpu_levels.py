@@ -29,7 +29,7 @@ def rel(a, b):
 def _levels(kind, n, p):
     g = np.random.default_rng([wl.MASTER_SEED, 71, n, p])
     if kind == "random":
-        hi = 3 if p <= 2 else 2
+        hi = 3 if p <= 2 else 2      # p = 3, 4: levels 0..2
         return g.integers(0, hi + 1, size=2 * n * n)
     if kind == "band":
         return band_levels(n, edges=(0.4, 0.6, 0.8), base=0)
@@ -46,6 +46,7 @@ CASES = [
     ("band_p2", 4, 2, "band", (1.0, 0.0)),
     ("rand_p3", 2, 3, "random", (0.5, 0.9)),
     ("lev4_p1", 2, 1, "level4", (0.3, 0.7)),
+    ("rand_p4", 2, 4, "random", (0.4, -0.6)),
 ]
 
 
