@@ -52,7 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="c1")
+    ap.add_argument("--config", default="n128_m8_p3")
     ap.add_argument("--restart", type=int, default=80)
     ap.add_argument("--mode", type=int, default=2, choices=[0, 1, 2],
                     help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
@@ -335,7 +335,7 @@ def run_ours(args):
     n_t, n_int = 3 * P1, pr.info["n_int_edges"]
     R, Cc = Q + n_t, Q + n_t + 1
     avg = lambda ph: prof[ph][1] / max(1, prof[ph][0])
-    # algorithmic work per launch
+    # algorithmic work per launch (blocks of both sides, x once, y once)
     apply_bytes = 8.0 * (2 * P1 * n_t * n_int + 2 * N_tr)        # blocks of both sides + x once + y once
     apply_flops = 4.0 * P1 * n_t * n_int
     cond_flops = N * sum(2.0 * (R - 1 - k) * (Cc - 1 - k) for k in range(Q))
@@ -491,7 +491,7 @@ def bench_multi_rhs(stream, count=64):
     import torch
     from paper_2302_10917_gb300 import Problem
     from paper_2302_10917_gb300 import workloads as wl
-    cfg = wl.CONFIGS["c3u"]
+    cfg = wl.CONFIGS["n128_m4_p2_64src"]
     ev = lambda: torch.cuda.Event(enable_timing=True)
     pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
     f = wl.gaussian_bumps(pr.quad_points(), count, seed=3).contiguous()
@@ -545,7 +545,7 @@ def bench_levels_many_source(stream, count=64):
     import torch
     from paper_2302_10917_gb300 import Problem
     from paper_2302_10917_gb300 import workloads as wl
-    cfg = wl.CONFIGS["c3"]
+    cfg = wl.CONFIGS["levels_n128_p2_64src"]
     lev = wl.band_levels(cfg["n"])
     ev = lambda: torch.cuda.Event(enable_timing=True)
     pr = Problem(cfg["n"], 1, cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream, levels=lev)
@@ -639,7 +639,7 @@ def bench_mixed_precision_n256(stream):
     import torch
     from paper_2302_10917_gb300 import Problem
     from paper_2302_10917_gb300 import workloads as wl
-    cfg = wl.CONFIGS["c2"]
+    cfg = wl.CONFIGS["n256_m8_p3"]
     pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
     pr.set_source(wl.sin_sin_source(pr.quad_points(), cfg["kappa"], cfg["beta"]).contiguous())
     ev = lambda: torch.cuda.Event(enable_timing=True)

@@ -119,7 +119,7 @@ def _step(pr, f, a):
 
 
 def _levels(a):
-    cfg = wl.CONFIGS["c3"]
+    cfg = wl.CONFIGS["levels_n128_p2_64src"]
     lev = wl.band_levels(a.n)
     pr = Problem(a.n, 1, cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], levels=lev)
     f = wl.gaussian_bumps(pr.quad_points(), a.nrhs, seed=3, width=cfg["width"]).contiguous()

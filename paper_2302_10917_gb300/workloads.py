@@ -15,14 +15,14 @@ MASTER_SEED = 0x230210917
 
 # Workloads (n macro squares per side, m sub-edges per macro-edge, degree p).
 CONFIGS = {
-    "c0": dict(n=4, m=2, p=2, beta=(1.0, 1.0), kappa=1.0),
-    "c1": dict(n=128, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
-    "c2": dict(n=256, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
-    "c4": dict(n=256, m=4, p=2, beta=(1.0, 0.5), kappa=1.0),
+    "smoke_n4_m2_p2": dict(n=4, m=2, p=2, beta=(1.0, 1.0), kappa=1.0),
+    "n128_m8_p3": dict(n=128, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
+    "n256_m8_p3": dict(n=256, m=8, p=3, beta=(50.0 * math.cos(0.3), 50.0 * math.sin(0.3)), kappa=1.0),
+    "n256_m4_p2_grf": dict(n=256, m=4, p=2, beta=(1.0, 0.5), kappa=1.0),
     # many right-hand sides on one level (uniform counterpart of the banded-level workload)
-    "c3u": dict(n=128, m=4, p=2, beta=(1.0, 0.0), kappa=1e-2),
+    "n128_m4_p2_64src": dict(n=128, m=4, p=2, beta=(1.0, 0.0), kappa=1e-2),
     # many right-hand sides on levels by band of x (band_levels: r = 1 .. 4, faces at the finer side)
-    "c3": dict(n=128, m=0, p=2, beta=(1.0, 0.0), kappa=1e-2, nrhs=64, width=0.05),
+    "levels_n128_p2_64src": dict(n=128, m=0, p=2, beta=(1.0, 0.0), kappa=1e-2, nrhs=64, width=0.05),
 }
 
 

@@ -18,7 +18,7 @@ from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-CFG = wl.CONFIGS["c1"]
+CFG = wl.CONFIGS["n128_m8_p3"]
 
 
 @pytest.fixture(scope="module")
@@ -145,7 +145,7 @@ def test_n256_sampled_blocks_and_mixed_precision_solutions():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2302_10917_gb300 import Problem
-    cfg = wl.CONFIGS["c2"]
+    cfg = wl.CONFIGS["n256_m8_p3"]
     gpu = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"])
     try:
         gpu.set_source(wl.sin_sin_source(gpu.quad_points(), cfg["kappa"], cfg["beta"]))

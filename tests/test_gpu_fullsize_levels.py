@@ -22,7 +22,7 @@ from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-CFG = wl.CONFIGS["c3"]
+CFG = wl.CONFIGS["levels_n128_p2_64src"]
 COLS = (0, 37, 63)          # sampled right-hand sides
 
 

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 B1 = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
 CASES = [
     # id, n, m, p, beta, kappa mode
-    ("c0", 4, 2, 2, (1.0, 1.0), "const"),        # the small workload
+    ("smoke_n4_m2_p2", 4, 2, 2, (1.0, 1.0), "const"),        # the small workload
     ("m4p2", 3, 4, 2, (0.8, -0.3), "rand"),
     ("m8p3", 2, 8, 3, B1, "rand"),              # the large workload's element (Q = 325: 21 LU panels)
     ("n1", 1, 1, 1, (0.3, 0.2), "rand"),         # two elements, one interior edge

@@ -139,7 +139,7 @@ def test_face_blocks_need_fewer_iterations_on_the_large_workload_element():
     """m = 8, p = 3, beta = 50 (cos 0.3, sin 0.3), kappa = 1 on an 8 x 8 macro grid: GMRES(80) to 1e-10."""
     _need_gpu()
     from paper_2302_10917_gb300 import Problem
-    cfg = wl.CONFIGS["c1"]
+    cfg = wl.CONFIGS["n128_m8_p3"]
     pr = Problem(8, cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"])
     try:
         pr.set_source(wl.sin_sin_source(pr.quad_points(), cfg["kappa"], cfg["beta"]))
