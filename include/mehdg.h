@@ -159,7 +159,10 @@ typedef struct {
   int orth;              /* Arnoldi orthogonalisation: 0 = classical Gram-Schmidt applied twice
                             (CGS2, four passes over the basis); 1 = classical Gram-Schmidt once,
                             the new vector's norm from ||w||^2 - ||V^T w||^2 (two passes; loses
-                            orthogonality faster, which the restart from the true residual bounds) */
+                            orthogonality faster, which the restart from the true residual bounds);
+                            2 = as 1, with a second projection in the steps where ||w - V V^T w||^2 <
+                            ||w||^2 / 2 (Kahan-Parlett "twice is enough"; decided on the device, two
+                            passes in the other steps) */
 } hdg_solve_opts;
 
 typedef struct {

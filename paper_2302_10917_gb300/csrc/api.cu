@@ -573,7 +573,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
-      o->orth < 0 || o->orth > 1)
+      o->orth < 0 || o->orth > 2)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;

@@ -10,10 +10,12 @@
 //    lower-precision Arnoldi operator this is iterative refinement in FP64);
 //  * the Arnoldi operator D^-1 S is applied from FP64 blocks (mode 0, FP64
 //    arithmetic), FP32 blocks (mode 1) or split-FP32 blocks (mode 2);
-//  * the Krylov basis is stored and orthogonalised (classical Gram-Schmidt
-//    applied twice, CGS2, in three passes over the basis) in split-FP32
-//    arithmetic on the FP32 pipe, because FP64 vector arithmetic runs at
-//    2 lanes/clock/SM on GB300;
+//  * the Krylov basis is stored and orthogonalised in split-FP32 arithmetic
+//    on the FP32 pipe, because FP64 vector arithmetic runs at 2 lanes/clock/SM
+//    on GB300: classical Gram-Schmidt applied twice (CGS2, four passes over
+//    the basis), once with the norm from Pythagoras (two passes), or once with
+//    a second projection only in the steps where more than half of the new
+//    vector lay in the basis (Kahan-Parlett; decided on the device);
 //  * Givens rotations run on the device and a device stop flag lets a whole
 //    cycle be enqueued without host round trips (every kernel of the cycle
 //    returns at once when the flag is set);
@@ -48,7 +50,9 @@ struct SmallLayout {
     total = sc + 8;
   }
 };
-enum { F_STOP = 0, F_JUSED = 1 };
+// F_P2 = 1: the Arnoldi step needs no second Gram-Schmidt pass, or the instance has stopped (kept
+// 1 whenever F_STOP is set, so that the second-pass kernels can use it as their stop flag)
+enum { F_STOP = 0, F_JUSED = 1, F_P2 = 3 };
 
 // Strides of a batch of independent GMRES instances (several right-hand
 // sides, blockIdx.z / .y / .x selecting the instance r): offsets per r of the
@@ -171,13 +175,19 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 // projection of CGS2), add = 0 sets it (single projection). The new vector's
 // norm follows from ||x - V s||^2 = ||x||^2 - ||s||^2 (orthonormal V). Then
 // the Givens rotations. One block.
+// add: 0 first (only) pass, 1 second pass (H += h), 2 first pass that decides
+// whether a second pass is needed (Kahan-Parlett: ||w - V h||^2 < ||w||^2 / 2,
+// i.e. more than half of w lay in the basis and the Pythagorean norm has lost
+// digits): then it stores h, clears F_P2 and leaves the rotations to the second
+// pass. stopslot: the flag that makes the launch return at once.
 __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part, int G, int nv, double* sm,
-                                                               SmallLayout L, int* flags, int j, int add, Batch bt) {
+                                                               SmallLayout L, int* flags, int j, int add, Batch bt,
+                                                               int stopslot) {
   const int rb = blockIdx.x;
   part += rb * bt.rpart;
   sm += rb * bt.rsm;
   flags += rb * bt.rflag;
-  if (flags[F_STOP]) return;
+  if (flags[stopslot]) return;
   __shared__ double vals[136];
   __shared__ double red[32];
   __shared__ double wsum[32][132];
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     const double s = vals[i];
     sm[L.htmp + i] = s;
-    h[i] = add ? h[i] + s : s;
+    h[i] = add == 1 ? h[i] + s : s;
     q2 += s * s;
   }
   for (int off = 16; off > 0; off >>= 1) q2 += __shfl_down_sync(0xffffffffu, q2, off);
@@ -228,6 +238,13 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
   double hh = 0.0;
   for (int i = 0; i < nw; ++i) hh += red[i];
   const double d = vals[nv] - hh;
+  if (add == 2) {
+    if (!(d >= 0.5 * vals[nv])) {   // second pass needed (also for a non-finite estimate)
+      flags[F_P2] = 0;
+      return;
+    }
+    flags[F_P2] = 1;
+  }
   const double hn = d > 0.0 ? sqrt(d) : 0.0;
   hs[j + 1] = hn;
   // previous rotations: the running entry stays in a register
@@ -252,6 +269,7 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
   sm[L.sc + 3] = hn;
   sm[L.sc + 4] = hn > 0.0 ? 1.0 / hn : 0.0;
   flags[F_JUSED] = j + 1;
+  flags[F_P2] = 1;
   if (est <= sm[L.sc + 2] || hn == 0.0) flags[F_STOP] = 1;
 }
 
@@ -375,6 +393,7 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
     sm[L.gv] = beta;
     flags[F_STOP] = beta > 0.0 ? 0 : 1;
     flags[F_JUSED] = 0;
+    flags[F_P2] = 1;
   }
 }
 
@@ -587,17 +606,26 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
         df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one);
-      } else {
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_STOP);
+      } else if (o.orth == 1) {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
         const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one, F_STOP);
+      } else {
+        // as orth = 1, plus a second projection (w' = w - V h; h2 = V^T w', ||w'||^2) only
+        // when the first pass finds ||w - V h||^2 < ||w||^2 / 2; the second-pass kernels
+        // are always launched and return at once when flag F_P2 says it is not needed
+        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 2, one, F_STOP);
+        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, one, 0);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, s, kgd, one);
+        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_P2);
       }
       df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     };
-    const int per_step = o.orth == 0 ? 6 : 4;
+    const int per_step = o.orth == 1 ? 4 : 6;
     const bool graph_cycle = jmax == K;
     if (graph_cycle) {
       // the whole cycle as one CUDA graph, captured once per configuration on a
@@ -788,6 +816,7 @@ __global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double*
   for (int r = threadIdx.x; r < nb; r += blockDim.x) {
     flags[r * rflag + F_STOP] = done[r];
     flags[r * rflag + F_JUSED] = 0;
+    flags[r * rflag + F_P2] = 1;
     if (vals) sm[(size_t)r * rsm + off] = vals[r];
   }
 }
@@ -949,12 +978,19 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
                                                  sm + (size_t)r * L.total + L.htmp, 0, fl + 4 * r, nullptr);
         df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, bt, np);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_STOP);
         c->launches += 4 + nb;
-      } else {
+      } else if (o.orth == 1) {
         const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt, F_STOP);
         c->launches += 2;
+      } else {
+        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 2, bt, F_STOP);
+        df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, bt, np);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, st, kgd, bt, nb);
+        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_P2);
+        c->launches += 5;
       }
       df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, bt, np);
       c->launches += 2;

@@ -122,7 +122,7 @@ def _local_rows(ora, e, f):
 def test_batched_solve_and_sampled_back_solve(big):
     gpu, ora, lev, fc = big
     g = gpu.rhs()
-    x, rep, st = gpu.solve(g, tol=1e-10, restart=80, mode=2, orth=1, maxit=40000)
+    x, rep, st = gpu.solve(g, tol=1e-10, restart=80, mode=2, orth=2, maxit=40000)
     assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10, rep
     # every column's residual with the FP64 operator, independently of the solver's own test
     res = (g - gpu.apply(x)).norm(dim=1) / g.norm(dim=1)

@@ -79,7 +79,7 @@ def test_multi_rhs_apply_matches_oracle(mcase, k):
     assert rel(y32, ref_p) < 5e-5
 
 
-@pytest.mark.parametrize("mode,orth", [(2, 1), (0, 0), (1, 1)])
+@pytest.mark.parametrize("mode,orth", [(2, 1), (0, 0), (1, 1), (2, 2)])
 def test_batched_solve_and_recover_match_oracle(mcase, mode, orth):
     ora, pr, S, nrhs = mcase["ora"], mcase["pr"], mcase["S"], mcase["nrhs"]
     g = pr.rhs()

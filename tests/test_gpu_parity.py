@@ -200,6 +200,21 @@ def test_gmres_fp32_iterative_refinement_mode(case):
     assert rel(x_gpu, x_dir) < 1e-8
 
 
+@pytest.mark.parametrize("orth", [1, 2])
+def test_gmres_single_projection_variants(case, orth):
+    """orth = 1 (one projection, norm from Pythagoras) and orth = 2 (a second projection
+    where the first removed more than half of the new vector): same solution, same residual."""
+    ora, gpu = case["ora"], case["gpu"]
+    S = ora.assemble_S(case["S_el"])
+    x_dir = np.linalg.solve(S, case["g"])
+    for mode in (0, 2):
+        x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth)
+        assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10, (mode, rep)
+        x_gpu = x_gpu.cpu().numpy()
+        assert abs(np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) - rep["rel_residual"]) < 1e-12
+        assert rel(x_gpu, x_dir) < 1e-8
+
+
 def test_solve_is_bitwise_reproducible(case):
     gpu = case["gpu"]
     g = gpu.rhs()
