@@ -241,3 +241,24 @@ def test_element_condensation_and_recovery_equal_the_global_route():
         ue, qe = pr.recover_element(e, x, fq, gh)
         assert np.abs(ue - u[pr.uoff[e]:pr.uoff[e + 1]]).max() < 1e-13 * np.abs(u).max()
         assert np.abs(qe.reshape(-1) - q[2 * pr.uoff[e]:2 * pr.uoff[e + 1]]).max() < 1e-13 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_convergence_rate_on_a_nonconforming_band_mesh(p):
+    """u = sin(pi x) sin(pi y) on band meshes (level 0 left of x = 0.5, level 1 right of it,
+    non-conforming faces along the band edge) refined n = 2, 4, 8: the L2 errors of u and
+    q = -grad u fall at order p + 1 (Sec. 4.1's rate, here through non-conforming faces)."""
+    import math
+    from oracle.problems import sin_sin
+    errs = []
+    for n in (2, 4, 8):
+        pr = LevelHDGProblem(n, band_levels(n, edges=(0.5,), base=0), p, beta=(1.0, 1.0), kappa=1.0)
+        u, gr, f = sin_sin(1.0, (1.0, 1.0))
+        pts, _ = pr.quad_points()
+        fq = f(pts[:, 0], pts[:, 1])
+        S_el, g, gh = pr.condense(fq, None)
+        x = np.linalg.solve(pr.assemble_S(S_el), g)
+        uu, qq = pr.recover(x, fq, gh)
+        errs.append(pr.l2_errors(uu, qq, u, gr))
+    for k in (0, 1):
+        assert math.log2(errs[1][k] / errs[2][k]) > p + 1 - 0.15, (k, errs)
