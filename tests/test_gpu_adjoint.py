@@ -121,6 +121,23 @@ def test_adjoint_driver_in_every_solve_mode(case, mode):
     assert rel(df.cpu().numpy(), case["gf"]) < 1e-8
 
 
+def test_adjoint_with_face_blocks(case):
+    """The face-block preconditioner kept through the transpose ((S_ff^-1)^T for S^T):
+    the same gradients as the oracle adjoint."""
+    gpu = case["gpu"]
+    gpu.condense(keep_factors=True, store_df64=True, store_fp32=True, precond="face_schur")
+    try:
+        x, rep, st = gpu.solve(gpu.rhs(), tol=TIGHT, restart=60, mode=2)
+        assert st == 0, rep
+        u, _ = gpu.recover(x)
+        dk, df, rep = gpu.adjoint(case["r"], x, u, tol=TIGHT, restart=60, mode=2)
+        assert rep["converged"] == 1
+        assert rel(dk.cpu().numpy(), case["gk"]) < 1e-8
+        assert rel(df.cpu().numpy(), case["gf"]) < 1e-8
+    finally:
+        gpu.condense(keep_factors=True, store_df64=True, store_fp32=True)
+
+
 # ------------------------------------------------------------- without oracle
 def _J_problem(n=4, m=4, p=2, beta=(1.0, 0.5), seed=1):
     from paper_2302_10917_gb300 import Problem

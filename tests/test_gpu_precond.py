@@ -152,3 +152,31 @@ def test_face_blocks_need_fewer_iterations_on_the_large_workload_element():
         assert its["face_schur"] < 0.5 * its["d"], its
     finally:
         pr.close()
+
+
+def test_face_blocks_with_supg():
+    """SUPG inside the macro-elements (Sec. 3.4): S_ff^-1 S x against the oracle's blocks;
+    SUPG's consistency term conditions A_u less well, hence 2e-10 (see test_gpu_supg.py)."""
+    _need_gpu()
+    from paper_2302_10917_gb300 import Problem
+    n, m, p, beta, kap = 2, 2, 2, (0.9, -0.5), 0.05
+    ora = HDGProblem(n, m, p, beta=beta, kappa=kap, supg=True)
+    gpu = Problem(n, m, p, beta=beta, kappa=kap, supg=True)
+    try:
+        g = np.random.default_rng([wl.MASTER_SEED, 82])
+        pts, _ = ora.quad_points()
+        f = g.standard_normal(pts.shape[:2])
+        gpu.set_source(torch.from_numpy(f))
+        gpu.condense(keep_factors=True, precond="face_schur")
+        S_el, g_o, _ = ora.condense(f, None)
+        S = ora.assemble_S(S_el)
+        P1 = ora.mesh.P1
+        Pinv = face_block_inverse(S, np.arange(ora.mesh.n_int_edges + 1) * P1)
+        x = g.standard_normal(S.shape[0])
+        y = gpu.apply(torch.from_numpy(x), precond=True).cpu().numpy()
+        assert rel(y, Pinv @ (S @ x)) < 2e-10
+        xs, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=40, mode=0)
+        assert st == 0, rep
+        assert rel(xs.cpu().numpy(), np.linalg.solve(S, g_o)) < 1e-8
+    finally:
+        gpu.close()
