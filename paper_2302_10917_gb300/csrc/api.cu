@@ -618,10 +618,21 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
                           c->gD_qp ? c->d_ghat + (size_t)r * P.n_bnd * P.P1 : nullptr, u + (size_t)r * P.N * P.Q,
                           q + (size_t)r * P.N * 2 * P.Q, c->stream, r);
   };
+  // several sources: one launch per element range for all of them
+  auto rec_all = [&](int64_t e0, int64_t cnt, int slot_is_element) {
+    return launch_recover_mrhs(P, c->dt, c->d_ws, nullptr, P.N, e0, cnt, slot_is_element, x, P.N_tr,
+                               c->gD_qp ? c->d_ghat : nullptr, (int64_t)P.n_bnd * P.P1, nullptr, 0, nullptr, u, q,
+                               (int64_t)P.N * P.Q, nrhs, c->stream);
+  };
   if (c->flags & HDG_KEEP_FACTORS) {
     ProfScope ps(c, HDG_PROF_RECOVER);
-    for (int r = 0; r < nrhs; ++r) {
-      e = rec(0, P.N, 1, r);
+    if (nrhs > 1) {
+      e = rec_all(0, P.N, 1);
+      c->launches += 1;
+      if (e != cudaSuccess) return cuda_err(c, e, "recover");
+    }
+    if (nrhs == 1) {
+      e = rec(0, P.N, 1, 0);
       c->launches += 1;
       if (e != cudaSuccess) return cuda_err(c, e, "recover");
     }
@@ -633,8 +644,13 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
                           nullptr, nullptr, c->stream, (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
       if (e != cudaSuccess) return cuda_err(c, e, "refactor");
       c->launches += 1;
-      for (int r = 0; r < nrhs; ++r) {
-        e = rec(e0, cnt, 0, r);
+      if (nrhs > 1) {
+        e = rec_all(e0, cnt, 0);
+        c->launches += 1;
+        if (e != cudaSuccess) return cuda_err(c, e, "recover");
+      }
+      if (nrhs == 1) {
+        e = rec(e0, cnt, 0, 0);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_err(c, e, "recover");
       }

@@ -708,6 +708,9 @@ struct RecArgs {
   int64_t nslots;
   const double* xel;
   const int64_t* uoff;
+  // several sources (recover_mrhs_kernel): per-source strides of x, g^, xel, u (q: 2 ustride)
+  int nrhs;
+  int64_t xstride, ghstride, xelstride, ustride;
 };
 
 __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
@@ -788,6 +791,92 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
       qe[Q + i] = g.gxi[1] * sx + g.geta[1] * sy - cy / g.detJ;
       ue[i] = uu[i];
     }
+  }
+}
+
+// The same back-solve for RCM sources at a time (blockIdx.y = group of
+// sources): the element's traces and right-hand sides for the group staged
+// once ([n_t][RCM], [Q][RCM] in shared memory), the right-hand sides
+// F_r - B_u x_e,r with one thread per (row, source), the back substitution
+// with two sources per warp (16 lanes each, no block barriers), u and q with
+// one thread per (row, source). FP64 arithmetic, as recover_kernel.
+constexpr int RCM = 16;
+__global__ void __launch_bounds__(256) recover_mrhs_kernel(RecArgs a) {
+  const Params& P = a.prm;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, ld = P.ld;
+  const int c0 = blockIdx.y * RCM;
+  const int nc = min(RCM, a.nrhs - c0);
+  const double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)P.R * ld;
+  extern __shared__ double sm[];
+  double* xe = sm;                 // [nt][RCM]
+  double* B = sm + nt * RCM;       // [Q][RCM]: right-hand sides, then the solution
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  int code[3], flip[3];
+  elem_edges(e, P.n, code, flip);
+  for (int idx = tid; idx < nt * RCM; idx += nthr) {
+    const int c = idx / RCM, r = idx - c * RCM;
+    double v = 0.0;
+    if (r < nc) {
+      const int col = c0 + r, k = c / P1, t = c - k * P1, s = flip[k] ? P.P - t : t;
+      if (a.xel) v = a.xel[(size_t)col * a.xelstride + (size_t)eb * nt + c];
+      else if (code[k] >= 0) v = a.x[(size_t)col * a.xstride + (size_t)code[k] * P1 + s];
+      else if (a.ghat) v = a.ghat[(size_t)col * a.ghstride + (size_t)(-1 - code[k]) * P1 + s];
+    }
+    xe[idx] = v;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < Q * RCM; idx += nthr) {
+    const int i = idx / RCM, r = idx - i * RCM;
+    const double* row = W + (size_t)i * ld + Q;
+    double acc = r < nc ? row[nt + c0 + r] : 0.0;
+    for (int c = 0; c < nt; ++c) acc -= row[c] * xe[c * RCM + r];
+    B[idx] = acc;
+  }
+  __syncthreads();
+  {
+    const int hl = lane & 15, r = 2 * warp + (lane >> 4);     // 8 warps x 2 sources
+    for (int i = Q - 1; i >= 0; --i) {
+      const double* row = W + (size_t)i * ld;
+      double acc = 0.0;
+      for (int j = i + 1 + hl; j < Q; j += 16) acc += row[j] * B[j * RCM + r];
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (hl == 0) B[i * RCM + r] = (B[i * RCM + r] - acc) / row[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  ElemGeom g;
+  elem_geom(e, P.n, g);
+  const int64_t ub = a.uoff ? a.uoff[e] : (int64_t)e * Q;
+  for (int idx = tid; idx < Q * RCM; idx += nthr) {
+    const int i = idx / RCM, r = idx - i * RCM;
+    if (r >= nc) continue;
+    const int col = c0 + r;
+    const double* xr = a.dt.Xxi + (size_t)i * Q;
+    const double* yr = a.dt.Xeta + (size_t)i * Q;
+    double sx = 0.0, sy = 0.0;
+    for (int j = 0; j < Q; ++j) {
+      const double b = B[j * RCM + r];
+      sx += xr[j] * b;
+      sy += yr[j] * b;
+    }
+    const double* fr = a.dt.Yh + (size_t)i * nt;
+    double cx = 0.0, cy = 0.0;
+    for (int c = 0; c < nt; ++c) {
+      const int k = c / P1;
+      const double v = fr[c] * xe[c * RCM + r] * g.L[k];
+      cx += g.nrm[k][0] * v;
+      cy += g.nrm[k][1] * v;
+    }
+    double* ue = a.u + (size_t)col * a.ustride + ub;
+    double* qe = a.q + (size_t)col * 2 * a.ustride + 2 * ub;
+    qe[i] = g.gxi[0] * sx + g.geta[0] * sy - cx / g.detJ;
+    qe[Q + i] = g.gxi[1] * sx + g.geta[1] * sy - cy / g.detJ;
+    ue[i] = B[i * RCM + r];
   }
 }
 
@@ -906,6 +995,29 @@ cudaError_t launch_recover_bin(const Params& P, const DevTables& dt, const doubl
   a.elist = elist; a.nslots = nslots; a.xel = xel; a.uoff = uoff;
   const size_t sm = (size_t)(P.n_t + 2 * P.Q) * sizeof(double);
   recover_kernel<<<(unsigned)count, 128, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Back-solve of nrhs sources at once (elements e0 .. e0+count-1 of the launch's
+// slots): per-source strides xstride (x), ghstride (g^), xelstride (xel, or
+// null), ustride (u; q has twice that).
+cudaError_t launch_recover_mrhs(const Params& P, const DevTables& dt, const double* ws, const int* elist,
+                                int64_t nslots, int64_t e0, int64_t count, int slot_is_element, const double* x,
+                                int64_t xstride, const double* ghat, int64_t ghstride, const double* xel,
+                                int64_t xelstride, const int64_t* uoff, double* u, double* q, int64_t ustride,
+                                int nrhs, cudaStream_t st) {
+  RecArgs a;
+  a.prm = P; a.dt = dt; a.ws = ws; a.e0 = e0; a.slot_is_element = slot_is_element; a.rcol = 0;
+  a.x = x; a.ghat = ghat; a.u = u; a.q = q;
+  a.elist = elist; a.nslots = nslots; a.xel = xel; a.uoff = uoff;
+  a.nrhs = nrhs; a.xstride = xstride; a.ghstride = ghstride; a.xelstride = xelstride; a.ustride = ustride;
+  const size_t sm = (size_t)(P.n_t + P.Q) * RCM * sizeof(double);
+  if (sm > 48 * 1024) {
+    const cudaError_t err = cudaFuncSetAttribute(recover_mrhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+    if (err != cudaSuccess) return err;
+  }
+  recover_mrhs_kernel<<<dim3((unsigned)count, (unsigned)((nrhs + RCM - 1) / RCM)), 256, sm, st>>>(a);
   return cudaGetLastError();
 }
 

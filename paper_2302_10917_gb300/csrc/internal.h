@@ -243,7 +243,7 @@ struct LevelBin {
   int ws_ld = 0;
   int* d_info = nullptr;
   double* d_xel = nullptr;      // [count][n_t] own-level traces for the back-solve
-  size_t bytes_S = 0, bytes_gel = 0, bytes_ghat = 0, bytes_ws = 0, bytes_tables = 0;
+  size_t bytes_S = 0, bytes_gel = 0, bytes_ghat = 0, bytes_ws = 0, bytes_tables = 0, bytes_xel = 0;
 };
 
 struct LevelMesh {

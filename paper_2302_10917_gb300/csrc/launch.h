@@ -23,6 +23,11 @@ cudaError_t launch_condense_bin(const Params& P, const DevTables& dt, const doub
 cudaError_t launch_recover_bin(const Params& P, const DevTables& dt, const double* ws, const int* elist,
                                int64_t nslots, int64_t e0, int64_t count, int slot_is_element, const double* xel,
                                const int64_t* uoff, double* u, double* q, cudaStream_t st, int rcol);
+cudaError_t launch_recover_mrhs(const Params& P, const DevTables& dt, const double* ws, const int* elist,
+                                int64_t nslots, int64_t e0, int64_t count, int slot_is_element, const double* x,
+                                int64_t xstride, const double* ghat, int64_t ghstride, const double* xel,
+                                int64_t xelstride, const int64_t* uoff, double* u, double* q, int64_t ustride,
+                                int nrhs, cudaStream_t st);
 cudaError_t launch_project_dirichlet_bin(const Params& P, const DevTables& dt, const int* blist, int nbnd,
                                          const int64_t* boff, const double* gD, double* ghat, cudaStream_t st);
 cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64_t count, double* out,

@@ -897,10 +897,41 @@ hdg_status level_recover(hdg_ctx* c, const double* x, double* u, double* q, int 
   const int64_t nu = L.uoff.back();
   for (LevelBin& B : L.bins) {
     const Params& P = B.prm;
-    if (!B.d_xel && (e = lv_alloc(c, &B.d_xel, (size_t)B.count * P.n_t)) != cudaSuccess)
-      return lv_cuda(c, e, "element traces");
+    const size_t nxel = (size_t)B.count * P.n_t * nrhs;
+    if (B.bytes_xel < nxel * 8) {
+      lv_free(c, B.d_xel, B.bytes_xel / 8);
+      B.bytes_xel = 0;
+      if ((e = lv_alloc(c, &B.d_xel, nxel)) != cudaSuccess) return lv_cuda(c, e, "element traces");
+      B.bytes_xel = nxel * 8;
+    }
     const int keep = (c->flags & HDG_KEEP_FACTORS) ? 1 : 0;
     const double* gh = c->gD_qp ? B.d_ghat : nullptr;
+    if (nrhs > 1) {
+      // own-level traces of every source, then one back-solve launch per element range
+      for (int r = 0; r < nrhs; ++r) {
+        lv_own_trace_kernel<<<256, 256, 0, c->stream>>>(L.dv, P, B.r, B.d_elist, B.count,
+                                                        x + (size_t)r * c->prm.N_tr,
+                                                        gh ? gh + (size_t)r * P.n_bnd * P.P1 : nullptr,
+                                                        B.d_xel + (size_t)r * B.count * P.n_t);
+        c->launches += 1;
+      }
+      for (int64_t e0 = 0; e0 < B.count; e0 += (keep ? B.count : B.ws_slots)) {
+        const int64_t cnt = keep ? B.count : std::min<int64_t>(B.ws_slots, B.count - e0);
+        if (!keep) {
+          e = launch_condense_bin(P, B.dt, c->d_kappa, c->f_qp, L.d_qoff, L.qoff.back(), gh, B.d_ws, B.d_elist,
+                                  B.count, e0, cnt, 0, 0, nullptr, nullptr, nullptr, c->stream,
+                                  (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
+          c->launches += 1;
+          if (e != cudaSuccess) return lv_cuda(c, e, "refactor");
+        }
+        ProfScope ps(c, HDG_PROF_RECOVER);
+        e = launch_recover_mrhs(P, B.dt, B.d_ws, B.d_elist, B.count, e0, cnt, keep, nullptr, 0, nullptr, 0, B.d_xel,
+                                (int64_t)B.count * P.n_t, L.d_uoff, u, q, nu, nrhs, c->stream);
+        c->launches += 1;
+        if (e != cudaSuccess) return lv_cuda(c, e, "recover");
+      }
+      continue;
+    }
     for (int64_t e0 = 0; e0 < B.count; e0 += (keep ? B.count : B.ws_slots)) {
       const int64_t cnt = keep ? B.count : std::min<int64_t>(B.ws_slots, B.count - e0);
       if (!keep) {
