@@ -52,7 +52,7 @@ struct SmallLayout {
 };
 // F_P2 = 1: the Arnoldi step needs no second Gram-Schmidt pass, or the instance has stopped (kept
 // 1 whenever F_STOP is set, so that the second-pass kernels can use it as their stop flag)
-enum { F_STOP = 0, F_JUSED = 1, F_P2 = 3 };
+enum { F_STOP = 0, F_JUSED = 1, F_CNT = 2, F_P2 = 3 };   // F_CNT: arrivals in reduce2_givens_kernel
 
 // Strides of a batch of independent GMRES instances (several right-hand
 // sides, blockIdx.z / .y / .x selecting the instance r): offsets per r of the
@@ -180,38 +180,45 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 // i.e. more than half of w lay in the basis and the Pythagorean norm has lost
 // digits): then it stores h, clears F_P2 and leaves the rotations to the second
 // pass. stopslot: the flag that makes the launch return at once.
+// Grid (column groups, instances), 1024 threads: block k sums columns
+// 32 k .. 32 k + 31 of the partial rows (warp w the rows w, w + 32, ..., then
+// the 32 warps' sums in order) into sm[htmp + col]; the last block of an
+// instance to arrive (arrival counter F_CNT, no waiting) reads all sums and
+// applies the rotations. The order of every sum does not depend on the grid.
 __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part, int G, int nv, double* sm,
                                                                SmallLayout L, int* flags, int j, int add, Batch bt,
                                                                int stopslot) {
-  const int rb = blockIdx.x;
+  const int rb = blockIdx.y;
   part += rb * bt.rpart;
   sm += rb * bt.rsm;
   flags += rb * bt.rflag;
   if (flags[stopslot]) return;
   __shared__ double vals[136];
   __shared__ double red[32];
-  __shared__ double wsum[32][132];
+  __shared__ double wsum[32][33];
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // partial rows are read whole (coalesced): warp w sums rows w, w + nw, ...
-  // into per-lane column accumulators; then the warps' sums in fixed order
+  const int ncol = nv + 1;
   {
-    const int ncol = nv + 1;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = wid; b < G; b += nw) {
-      const double* row = part + (size_t)b * ncol;
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-        if (lane + 32 * k < ncol) acc[k] += row[lane + 32 * k];
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-      if (lane + 32 * k < ncol) wsum[wid][lane + 32 * k] = acc[k];
+    const int col = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (col < ncol)
+      for (int b = wid; b < G; b += nw) acc += part[(size_t)b * ncol + col];
+    wsum[wid][lane] = acc;
     __syncthreads();
-    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+    if (threadIdx.x < 32 && blockIdx.x * 32 + threadIdx.x < ncol) {
       double t = 0.0;
-      for (int w2 = 0; w2 < nw; ++w2) t += wsum[w2][i];
-      vals[i] = t;
+      for (int w2 = 0; w2 < nw; ++w2) t += wsum[w2][threadIdx.x];
+      sm[L.htmp + blockIdx.x * 32 + threadIdx.x] = t;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&flags[F_CNT], 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) vals[i] = __ldcg(&sm[L.htmp + i]);
+    if (threadIdx.x == 0) flags[F_CNT] = 0;
   }
   __syncthreads();
   const int K1 = L.K + 1;
@@ -393,6 +400,7 @@ __global__ void cycle_init_kernel(double* sm, SmallLayout L, int* flags, const d
     sm[L.gv] = beta;
     flags[F_STOP] = beta > 0.0 ? 0 : 1;
     flags[F_JUSED] = 0;
+    flags[F_CNT] = 0;
     flags[F_P2] = 1;
   }
 }
@@ -606,21 +614,21 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
         df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_STOP);
       } else if (o.orth == 1) {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
         const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one, F_STOP);
       } else {
         // as orth = 1, plus a second projection (w' = w - V h; h2 = V^T w', ||w'||^2) only
         // when the first pass finds ||w - V h||^2 < ||w||^2 / 2; the second-pass kernels
         // are always launched and return at once when flag F_P2 says it is not needed
         int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 2, one, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 2, one, F_STOP);
         df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, one, 0);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, s, kgd, one);
-        reduce2_givens_kernel<<<1, 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_P2);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_P2);
       }
       df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
@@ -816,6 +824,7 @@ __global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double*
   for (int r = threadIdx.x; r < nb; r += blockDim.x) {
     flags[r * rflag + F_STOP] = done[r];
     flags[r * rflag + F_JUSED] = 0;
+    flags[r * rflag + F_CNT] = 0;
     flags[r * rflag + F_P2] = 1;
     if (vals) sm[(size_t)r * rsm + off] = vals[r];
   }
@@ -978,18 +987,18 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
                                                  sm + (size_t)r * L.total + L.htmp, 0, fl + 4 * r, nullptr);
         df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, bt, np);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_STOP);
         c->launches += 4 + nb;
       } else if (o.orth == 1) {
         const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt, F_STOP);
         c->launches += 2;
       } else {
         int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 2, bt, F_STOP);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 2, bt, F_STOP);
         df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, bt, np);
         G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<nb, 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_P2);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_P2);
         c->launches += 5;
       }
       df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, bt, np);
