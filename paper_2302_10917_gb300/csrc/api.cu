@@ -96,6 +96,8 @@ cudaError_t upload_ref_tables(const RefTables& T, DevTables& d, void** dmem, siz
       {T.Xeta.data(), T.Xeta.size() * 8, (void**)&d.Xeta}, {T.Fh.data(), T.Fh.size() * 8, (void**)&d.Fh},
       {T.Pxi.data(), T.Pxi.size() * 8, (void**)&d.Pxi},   {T.Peta.data(), T.Peta.size() * 8, (void**)&d.Peta},
       {T.Yh.data(), T.Yh.size() * 8, (void**)&d.Yh},      {T.Hh.data(), T.Hh.size() * 8, (void**)&d.Hh},
+      {T.XxiT.data(), T.XxiT.size() * 8, (void**)&d.XxiT}, {T.XetaT.data(), T.XetaT.size() * 8, (void**)&d.XetaT},
+      {T.YhT.data(), T.YhT.size() * 8, (void**)&d.YhT},
       {T.Gh.data(), T.Gh.size() * 8, (void**)&d.Gh},      {T.Ghinv.data(), T.Ghinv.size() * 8, (void**)&d.Ghinv},
       {T.phiq.data(), T.phiq.size() * 8, (void**)&d.phiq}, {T.wq.data(), T.wq.size() * 8, (void**)&d.wq},
       {T.uq.data(), T.uq.size() * 8, (void**)&d.uq},      {T.bpsi.data(), T.bpsi.size() * 8, (void**)&d.bpsi},

@@ -763,34 +763,25 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
   elem_geom(e, P.n, g);
   double* ue = a.u + (a.uoff ? a.uoff[e] : (int64_t)e * Q);
   double* qe = a.q + 2 * (a.uoff ? a.uoff[e] : (int64_t)e * Q);
-  for (int i = warp; i < Q; i += nw) {
-    const double* xr = a.dt.Xxi + (size_t)i * Q;
-    const double* yr = a.dt.Xeta + (size_t)i * Q;
+  // one thread per row i, the tables read column-major (coalesced over i)
+  for (int i = tid; i < Q; i += blockDim.x) {
     double sx = 0.0, sy = 0.0;
-    for (int j = lane; j < Q; j += 32) {
-      sx += xr[j] * uu[j];
-      sy += yr[j] * uu[j];
+    for (int j = 0; j < Q; ++j) {
+      const double b = uu[j];
+      sx += a.dt.XxiT[(size_t)j * Q + i] * b;
+      sy += a.dt.XetaT[(size_t)j * Q + i] * b;
     }
-    const double* fr = a.dt.Yh + (size_t)i * nt;
     double cx = 0.0, cy = 0.0;
-    for (int c = lane; c < nt; c += 32) {
+    for (int c = 0; c < nt; ++c) {
       const int k = c / P1;
-      const double v = fr[c] * xe[c] * g.L[k];
+      const double v = a.dt.YhT[(size_t)c * Q + i] * xe[c] * g.L[k];
       cx += g.nrm[k][0] * v;
       cy += g.nrm[k][1] * v;
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      sx += __shfl_down_sync(0xffffffffu, sx, off);
-      sy += __shfl_down_sync(0xffffffffu, sy, off);
-      cx += __shfl_down_sync(0xffffffffu, cx, off);
-      cy += __shfl_down_sync(0xffffffffu, cy, off);
-    }
-    if (lane == 0) {
-      // grad_x = gxi_x d_xi + geta_x d_eta, and M^-1 = Mh^-1 / detJ
-      qe[i] = g.gxi[0] * sx + g.geta[0] * sy - cx / g.detJ;
-      qe[Q + i] = g.gxi[1] * sx + g.geta[1] * sy - cy / g.detJ;
-      ue[i] = uu[i];
-    }
+    // grad_x = gxi_x d_xi + geta_x d_eta, and M^-1 = Mh^-1 / detJ
+    qe[i] = g.gxi[0] * sx + g.geta[0] * sy - cx / g.detJ;
+    qe[Q + i] = g.gxi[1] * sx + g.geta[1] * sy - cy / g.detJ;
+    ue[i] = uu[i];
   }
 }
 

@@ -34,6 +34,7 @@ struct RefTables {
   int ng = 0, nqs = 0, nloc = 0, nsub = 0, ngb = 0;
   std::vector<double> Mh, Dxi, Deta, Kxx, Kyy, Ksym, Xxi, Xeta;
   std::vector<double> Fh, Pxi, Peta, Yh, Hh, Gh, Ghinv;
+  std::vector<double> XxiT, XetaT, YhT;  // transposes of Xxi, Xeta (Q x Q) and Yh (n_t x Q)
   std::vector<int> enode;
   std::vector<double> phiq, wq, uq;     // uq: Gauss nodes on [0,1] (ng)
   std::vector<int> subtri;              // nsub x 6 corners (a,b) in units of 1/m
@@ -65,6 +66,7 @@ void build_level_tables(int p, LevelTables& L);
 struct DevTables {
   double *Dxi, *Deta, *Kxx, *Kyy, *Ksym, *Xxi, *Xeta;
   double *Fh, *Pxi, *Peta, *Yh, *Hh, *Gh, *Ghinv;
+  double *XxiT, *XetaT, *YhT;
   int* enode;
   double *phiq, *wq, *uq;
   int *subtri, *subnode, *ns_ptr, *ns_idx;

@@ -395,6 +395,17 @@ void build_reference_tables(int m, int p, RefTables& T) {
   T.Pxi = atb(T.Dxi, Q, Q, T.Yh, nt);
   T.Peta = atb(T.Deta, Q, Q, T.Yh, nt);
   T.Hh = atb(T.Fh, Q, nt, T.Yh, nt);
+  // column-major copies of the q-recovery tables (one thread per row reads them coalesced)
+  T.XxiT.resize((size_t)Q * Q);
+  T.XetaT.resize((size_t)Q * Q);
+  T.YhT.resize((size_t)nt * Q);
+  for (int i = 0; i < Q; ++i) {
+    for (int j = 0; j < Q; ++j) {
+      T.XxiT[(size_t)j * Q + i] = T.Xxi[(size_t)i * Q + j];
+      T.XetaT[(size_t)j * Q + i] = T.Xeta[(size_t)i * Q + j];
+    }
+    for (int c = 0; c < nt; ++c) T.YhT[(size_t)c * Q + i] = T.Yh[(size_t)i * nt + c];
+  }
 }
 
 }  // namespace mehdg
