@@ -138,9 +138,13 @@ __device__ __forceinline__ void df_fma4(float& h, float& l, float4 a, float4 b) 
   df_fma(h, l, make_float2(a.z, a.w), make_float2(b.z, b.w));
 }
 
-// part[b * ncol + i] = sum over pair chunk b of V_i . w; blockIdx.y selects a
-// group of VG basis vectors. ncol = nv, or nv + 1 to append the squared norm
-// w . w as column nv. One pair per thread per iteration; four blocks per SM.
+// part[b * ncol + i] = sum over pair chunk b of V_i . w, for gridDim.x chunks
+// and gridDim.y groups of VG basis vectors. ncol = nv, or nv + 1 to append the
+// squared norm w . w as column nv. One pair per thread per iteration; four
+// blocks per SM. Blocks are numbered group-fastest (block k: chunk k / gy,
+// group k % gy), so blocks dispatched together read all vectors of the same
+// rows and the last rows of the basis are what the L2 holds when the update
+// (which walks the rows backwards) starts. The sums do not depend on this.
 __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict__ V, int64_t np, int nv, int ncol,
                                                         const float4* __restrict__ w, double* part, const int* stop,
                                                         Batch bt) {
@@ -150,9 +154,11 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
   w += rb * bt.rw;
   part += rb * bt.rpart;
   __shared__ float2 red[(KT / 32) * VG];
-  const int g0 = blockIdx.y * VG;
+  const unsigned k = blockIdx.y * gridDim.x + blockIdx.x;
+  const int64_t cb = k / gridDim.y;
+  const int g0 = (int)(k % gridDim.y) * VG;
   const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * chunk;
+  const int64_t lo = cb * chunk;
   const int64_t hi = lo + chunk < np ? lo + chunk : np;
   float h[VG], l[VG];
 #pragma unroll
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 #pragma unroll
     for (int g = 0; g < VG; ++g) df_fma4(h[g], l[g], a[g], wa);
   }
-  df_block_reduce<VG>(h, l, ncol - g0, red, part + (size_t)blockIdx.x * ncol + g0);
+  df_block_reduce<VG>(h, l, ncol - g0, red, part + (size_t)cb * ncol + g0);
 }
 
 // Sums the partials of one Arnoldi step (stride nv + 1: columns 0..nv-1 the
@@ -283,11 +289,13 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
 // out = (w - sum_i coef_i V_i) * scale over element pairs, scale = sm[scale_off]
 // (or 1 when scale_off < 0); out may be w itself. The loads of the next group
 // of 8 basis vectors are issued before the products of the current group.
+// Instances and pairs are walked last to first: the multi-dot before it read
+// them first to last, so its most recent lines are still in L2.
 __global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict__ V, int64_t np, int nv,
                                                        const double* __restrict__ coef, const float4* w,
                                                        const double* sm, int scale_off, float4* out,
                                                        const int* stop, Batch bt, int64_t rout) {
-  const int rb = blockIdx.y;
+  const int rb = gridDim.y - 1 - blockIdx.y;
   if (stop && stop[rb * bt.rflag + F_STOP]) return;
   V += rb * bt.rv;
   coef += rb * bt.rsm;
@@ -300,7 +308,8 @@ __global__ void __launch_bounds__(KT) df_update_kernel(const float4* __restrict_
   const bool scaled = scale_off >= 0;
   const float2 inv = scaled ? df_from(sm[scale_off]) : make_float2(1.f, 0.f);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pf < np; pf += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = np - 1 - pf;
     const float4 wv = w[p];
     float ah = wv.x, al = wv.y, bh = wv.z, bl = wv.w;
     float4 v[8], nx[8];
