@@ -340,8 +340,10 @@ def run_ours(args):
     apply_flops = 4.0 * P1 * n_t * n_int
     cond_flops = N * sum(2.0 * (R - 1 - k) * (Cc - 1 - k) for k in range(Q))
     rooflines = {
-        "apply": {"kernel": {0: "apply_vdf_kernel<0> (FP64 blocks)", 1: "apply_vdf_kernel<2> (FP32 blocks)",
-                             2: "apply_vdf_kernel<1> (split-FP32 blocks)"}[args.mode],
+        "apply": {"kernel": ({0: "apply_vdf_kernel<0> (FP64 blocks)", 1: "apply_vdf_kernel<2> (FP32 blocks)",
+                              2: "apply_vdf_kernel<1> (split-FP32 blocks)"}[args.mode] if not tune.get("apply_bulk")
+                             else f"apply_bulk_kernel (split-FP32 blocks, bulk-copy stage ring, "
+                                  f"{tune['apply_bulk']} CTAs per SM)"),
                   "bound": "alu" if args.mode == 0 else "hbm",
                   "launches": prof["apply32" if args.mode == 1 else "apply"][0],
                   "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},
@@ -393,7 +395,7 @@ def run_ours(args):
                                                            else kname][1])
     roof = dict(rooflines[dom])
     roof["traffic"] = None
-    if dom == "apply" and args.mode == 2 and (cfg["m"], cfg["p"]) == (8, 3):
+    if dom == "apply" and args.mode == 2 and (cfg["m"], cfg["p"]) == (8, 3) and not tune.get("apply_bulk"):
         roof["traffic"] = APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 * n_int
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 64, scaled by interior edges"
     roof_other = {k: v for k, v in rooflines.items() if k != dom}

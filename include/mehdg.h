@@ -253,8 +253,22 @@ hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
  * hdg_set_source's nrhs), FP64 (prec = 64), FP64 with the split-FP32 blocks
  * (prec = 48, precond = 1, HDG_STORE_DF64) or FP32 (prec = 32, the FP32
  * blocks, precond = 1). nrhs > 1 streams every block once for all columns
- * (multi-RHS apply). x and y must not overlap. */
+ * (multi-RHS apply). x and y must not overlap.
+ * prec = 49 (uniform mesh, nrhs = 1, precond = 1, HDG_STORE_DF64): the
+ * Arnoldi operator of the split-FP32 solve (mode 2) itself, on split-FP32
+ * vectors (x and y [N_tr][2] FP32: entry i is x[i][0] + x[i][1]), with the
+ * launch shape that solve uses (hdg_autotune's choice or hdg_set_apply_shape's);
+ * with the pipelined shape it synchronises the stream to read that kernel's
+ * timeout flag (HDG_ERR_TIMEOUT if a bounded wait gave up). */
 hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int prec, int precond);
+
+/* Sets the launch shape of the trace-operator apply inside hdg_solve for one
+ * mode (0 FP64, 1 FP32 + refinement, 2 split-FP32), as hdg_autotune would:
+ * edges_per_block > 0 (with edges_per_block (m p + 1) <= 512) for the
+ * one-thread-per-row apply, or bulk_ctas_per_sm > 0 (mode 2 only) for the
+ * pipelined apply with that many CTAs per SM; both 0 restores the default.
+ * Uniform meshes only; HDG_ERR_ARG for a shape that does not apply. */
+hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_ctas_per_sm);
 
 /* Solve S x = g (Eq. global_problem) with restarted GMRES, left-
  * preconditioned by D^-1 (Sec. 6.1). x_dev holds the initial guess on entry
@@ -360,10 +374,14 @@ hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, 
  * Times, with CUDA events on the context stream, the candidate launch shapes
  * of the GMRES kernels for opts->mode at this problem size: edges per block
  * of the trace-operator apply (one thread per edge and trace position, up to
- * 512 threads), blocks of the multi-dot and of the streaming update (at
+ * 512 threads) and, for split-FP32 blocks on a uniform mesh, the pipelined
+ * apply with 1 to 3 CTAs per SM (bulk asynchronous copies of the row-blocks
+ * into shared memory; the sum over an edge's columns is then taken in a few
+ * parts, so its last bits differ from the one-thread-per-row apply's),
+ * blocks of the multi-dot and of the streaming update (at
  * opts->restart / 2 basis vectors). Keeps the fastest of each in the context
  * for every later hdg_solve / hdg_apply and reports them. Arithmetic and
- * results are unchanged by the apply's shape; the multi-dot's partial sums
+ * results are unchanged by the edges per block; the multi-dot's partial sums
  * follow its block count (fixed per context, so solves stay reproducible).
  * Needs hdg_condense (with the blocks the mode uses). Synchronous. */
 typedef struct {
@@ -375,6 +393,11 @@ typedef struct {
   double mdot_ms;
   double update_ms;
   double default_ms;         /* the three kernels with the built-in shapes */
+  int apply_bulk;            /* > 0: the pipelined apply was chosen, with this many CTAs per SM (split-FP32
+                                blocks on a uniform mesh: each edge's two row-blocks are brought into shared
+                                memory by bulk asynchronous copies, several edges ahead; apply_edges_per_block
+                                is then 0 and apply_threads 256) */
+  double apply_bulk_ms;      /* best time of the pipelined apply (0 where it was not a candidate) */
 } hdg_tune_report;
 hdg_status hdg_autotune(hdg_ctx* ctx, const hdg_solve_opts* opts, hdg_tune_report* report);
 

@@ -24,6 +24,7 @@ EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", 
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
             "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_set_kappa",
             "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_autotune",
+            "hdg_set_apply_shape",
             "hdg_offsets", "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
@@ -66,7 +67,8 @@ class SolveReport(ctypes.Structure):
 class TuneReport(ctypes.Structure):
     _fields_ = [("apply_edges_per_block", ctypes.c_int), ("apply_threads", ctypes.c_int),
                 ("mdot_blocks", ctypes.c_int), ("update_blocks", ctypes.c_int), ("apply_ms", ctypes.c_double),
-                ("mdot_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("mdot_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("apply_bulk", ctypes.c_int), ("apply_bulk_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +116,7 @@ def load_library(path=LIB_PATH):
     lib.hdg_adjoint_recover.argtypes = [vp, dp, dp, dp]
     lib.hdg_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp]
     lib.hdg_autotune.argtypes = [vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(TuneReport)]
+    lib.hdg_set_apply_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.hdg_profile.argtypes = [vp, ctypes.c_int]
     lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
@@ -278,10 +281,11 @@ class Problem:
         return g
 
     def apply(self, x, precond=False, prec=64, out=None):
-        """x: [N_tr] or [nrhs, N_tr] (multi-RHS apply)."""
-        dt = torch.float32 if prec == 32 else torch.float64
+        """x: [N_tr] or [nrhs, N_tr] (multi-RHS apply); prec = 49: x [N_tr, 2] FP32 split pairs
+        (the split-FP32 solve's own operator and launch shape), y likewise."""
+        dt = torch.float32 if prec in (32, 49) else torch.float64
         x = x.to(self.device, dt).contiguous()
-        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        nrhs = 1 if x.dim() == 1 or prec == 49 else x.shape[0]
         y = out if out is not None else torch.empty_like(x)
         self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), nrhs, prec, 1 if precond else 0))
         return y
@@ -298,6 +302,10 @@ class Problem:
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
             self._check(st)
         return x, r.as_dict(), st
+
+    def set_apply_shape(self, mode, edges_per_block=0, bulk_ctas_per_sm=0):
+        """hdg_set_apply_shape: the apply's launch shape inside solves of this mode."""
+        self._check(self.lib.hdg_set_apply_shape(self.h, mode, edges_per_block, bulk_ctas_per_sm))
 
     def autotune(self, mode=0, restart=80):
         """hdg_autotune: time candidate launch shapes of the GMRES kernels for this mode and

@@ -422,9 +422,11 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if ((flags & HDG_STORE_FP32) && !c->d_St32 && (e = dev_alloc(c, &c->d_St32, sblk)) != cudaSuccess)
     return cuda_err(c, e, "FP32 S blocks");
   if (!(flags & HDG_STORE_FP32)) dev_free(c, c->d_St32, sblk);
-  if ((flags & HDG_STORE_DF64) && !c->d_Stdf && (e = dev_alloc(c, &c->d_Stdf, sblk)) != cudaSuccess)
+  // split-FP32 blocks: 16 bytes of slack at the end for the pipelined apply's
+  // copies, which round each row-block out to 16-byte boundaries
+  if ((flags & HDG_STORE_DF64) && !c->d_Stdf && (e = dev_alloc(c, &c->d_Stdf, sblk + 2)) != cudaSuccess)
     return cuda_err(c, e, "split-FP32 S blocks");
-  if (!(flags & HDG_STORE_DF64)) dev_free(c, c->d_Stdf, sblk);
+  if (!(flags & HDG_STORE_DF64)) dev_free(c, c->d_Stdf, sblk + 2);
   if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.nrhs * P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
   if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.nrhs * P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
   if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
@@ -516,6 +518,21 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
   cudaError_t e;
   ProfScope ps(c, prec == 32 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY);
+  if (prec == 49) {
+    // the Arnoldi operator of the split-FP32 solve, on split-FP32 vectors, in the launch shape the solve uses
+    if (c->lv || nrhs != 1) return set_err(c, HDG_ERR_ARG, "prec 49 is the one-column operator of a uniform mesh");
+    if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
+    const int epb = c->tune_epb[1];
+    e = launch_apply_vdf(1, c->prm, c->d_Stdf, static_cast<const float2*>(x), static_cast<float2*>(y), precond_scale(c),
+                         nullptr, c->stream, epb);
+    c->launches += 1;
+    if (e == cudaSuccess && epb < 0) {
+      int err = 0;
+      e = apply_bulk_take_error(c->stream, &err);
+      if (e == cudaSuccess && err) return set_err(c, HDG_ERR_TIMEOUT, "pipelined apply: a bounded copy wait gave up");
+    }
+    return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply (split vectors)");
+  }
   if (c->lv) {
     const LevelMesh& L = *c->lv;
     if ((e = level_ensure_z(c, nrhs)) != cudaSuccess) return cuda_err(c, e, "element-side buffer");
@@ -567,6 +584,20 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   }
   c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
+}
+
+hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bulk_ctas_per_sm) {
+  if (!c) return HDG_ERR_ARG;
+  if (mode < 0 || mode > 2 || edges_per_block < 0 || bulk_ctas_per_sm < 0 ||
+      (edges_per_block > 0 && bulk_ctas_per_sm > 0))
+    return set_err(c, HDG_ERR_ARG, "mode 0..2 and at most one of edges_per_block, bulk_ctas_per_sm");
+  if (c->lv) return set_err(c, HDG_ERR_ARG, "a level mesh has no per-edge apply shape");
+  const int bt = mode == 0 ? 0 : (mode == 2 ? 1 : 2);
+  if (edges_per_block * c->prm.P1 > 512) return set_err(c, HDG_ERR_ARG, "edges_per_block * (m p + 1) above 512");
+  if (bulk_ctas_per_sm > 0 && (bt != 1 || !apply_bulk_available(c->prm, bulk_ctas_per_sm)))
+    return set_err(c, HDG_ERR_ARG, "the pipelined apply needs mode 2 and a shape that fits shared memory");
+  c->tune_epb[bt] = bulk_ctas_per_sm > 0 ? -bulk_ctas_per_sm : edges_per_block;
+  return HDG_OK;
 }
 
 hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg_solve_opts* o,

@@ -18,6 +18,7 @@
 #include "internal.h"
 #include "df64.h"
 #include <type_traits>
+#include <algorithm>
 
 namespace mehdg {
 
@@ -302,8 +303,280 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
   y[(size_t)f * P1 + s] = out;
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined variant of the split-FP32 apply (the GMRES operator). The two
+// element-side row-blocks of each edge are moved HBM -> shared memory by the
+// bulk-copy (TMA) engine several edges ahead of the arithmetic, so the bytes
+// in flight no longer depend on how many loads the threads keep outstanding.
+// Persistent CTAs (a few per SM) take the edges f = blockIdx.x + i gridDim.x;
+// stage i % ns of a ring holds edge i's two row-blocks and an mbarrier counts
+// their transaction bytes. The trace values of edge i + 1 are gathered into
+// registers while edge i is computed. Thread (part, s): trace position s of
+// the edge and one contiguous part of its 2 n_t columns (side 0, then side 1);
+// the parts' sums are added in part order, so the result does not depend on
+// the grid. A row-block starts on an 8-byte boundary: the copy starts at the
+// 16-byte boundary below it and covers the block rounded up to 16 bytes (the
+// split-FP32 array carries 16 bytes of slack at its end). Every wait is
+// bounded: on timeout the CTA sets apply_bulk_wait_error, waits (bounded) for
+// the copies it issued and returns.
+// ---------------------------------------------------------------------------
+constexpr int ABK_THREADS = 256;
+constexpr int ABK_MAX_STAGES = 6;
+constexpr long long ABK_WAIT_CYCLES = 2000000000LL;   // about one second at 2 GHz
+
+__device__ int apply_bulk_wait_error;
+
+struct BulkShape {
+  int ns;      // stages of the ring
+  int seg;     // bytes of one side's segment in a stage (multiple of 16)
+  int parts;   // column parts per edge
+  int cpp;     // columns per part
+};
+
+namespace {
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// true once the phase of this parity has completed; false after the cycle limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > ABK_WAIT_CYCLES) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+}  // namespace
+
+__global__ void __launch_bounds__(ABK_THREADS) apply_bulk_kernel(Params P, const float2* __restrict__ S,
+                                                                 const float2* __restrict__ x, float2* __restrict__ y,
+                                                                 const double* __restrict__ escale,
+                                                                 const int* __restrict__ stop, BulkShape B) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(128) unsigned char sraw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sraw);                 // [ns]
+  unsigned char* stages = sraw + 128;                                   // [ns][2][seg]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  float2* xs = reinterpret_cast<float2*>(stages + (size_t)B.ns * 2 * B.seg);   // [2][2 n_t]
+  float2* red = xs + 4 * nt;                                            // [2][parts][P1]
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int nE = (int)blockIdx.x < P.n_int ? (P.n_int - 1 - (int)blockIdx.x) / G + 1 : 0;
+  const size_t blk_bytes = (size_t)nt * P1 * sizeof(float2);
+  if (tid == 0) {
+    s_abort = 0;
+    for (int i = 0; i < B.ns; ++i) mbar_init(smem_addr(&bars[i]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0: the two row-blocks of edge i into stage i % ns
+  auto issue = [&](int i) {
+    const int f = (int)blockIdx.x + i * G;
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    const int st = i % B.ns;
+    const uint32_t bar = smem_addr(&bars[st]);
+    const char* src[2];
+    uint32_t sz[2];
+    for (int sd = 0; sd < 2; ++sd) {
+      const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
+      const size_t a0 = off & ~(size_t)15;
+      src[sd] = reinterpret_cast<const char*>(S) + a0;
+      sz[sd] = (uint32_t)(((off - a0) + blk_bytes + 15) & ~(size_t)15);
+    }
+    mbar_arrive_tx(bar, sz[0] + sz[1]);
+    for (int sd = 0; sd < 2; ++sd) bulk_load(smem_addr(stages + ((size_t)st * 2 + sd) * B.seg), src[sd], sz[sd], bar);
+  };
+  // trace value c2 (side c2 / n_t, element column c2 % n_t) of edge i
+  auto gather = [&](int i, int c2) -> float2 {
+    const int f = (int)blockIdx.x + i * G;
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    const int sd = c2 >= nt ? 1 : 0, c = c2 - sd * nt;
+    int code[3], flip[3];
+    elem_edges(e[sd], P.n, code, flip);
+    const int kk = c / P1, t = c - kk * P1;
+    return code[kk] >= 0 ? x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)] : make_float2(0.f, 0.f);
+  };
+  if (tid == 0)
+    for (int i = 0; i < B.ns && i < nE; ++i) issue(i);
+  if (nE > 0 && tid < 2 * nt) xs[tid] = gather(0, tid);
+  __syncthreads();
+  const int part = tid / P1, s = tid - part * P1;
+  const bool active = part < B.parts;
+  int i = 0;
+  for (; i < nE; ++i) {
+    const int st = i % B.ns;
+    const int f = (int)blockIdx.x + i * G;
+    float2 xn = make_float2(0.f, 0.f);
+    if (i + 1 < nE && tid < 2 * nt) xn = gather(i + 1, tid);
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    if (!mbar_wait_bounded(smem_addr(&bars[st]), (uint32_t)((i / B.ns) & 1))) s_abort = 1;
+    if (active) {
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      const float2* xv = xs + (i & 1) * 2 * nt;
+      const int q0 = part * B.cpp, q1 = min(2 * nt, q0 + B.cpp);
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int lo = max(q0, sd * nt), hi = min(q1, (sd + 1) * nt);
+        if (lo >= hi) continue;
+        const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
+        const float2* blk = reinterpret_cast<const float2*>(stages + ((size_t)st * 2 + sd) * B.seg + (off & 15));
+        const float2* row = blk + (fl[sd] ? PP - s : s);   // entry (column j, this row) at j * P1
+        int j = lo - sd * nt;
+        const int jend = hi - sd * nt;
+        const float2* xq = xv + sd * nt;
+        for (; j + 1 < jend; j += 2) {
+          df_fma(h0, l0, row[j * P1], xq[j]);
+          df_fma(h1, l1, row[(j + 1) * P1], xq[j + 1]);
+        }
+        if (j < jend) df_fma(h0, l0, row[j * P1], xq[j]);
+      }
+      df_add(h0, l0, h1, l1);
+      red[((i & 1) * B.parts + part) * P1 + s] = make_float2(h0, l0);
+    }
+    if (i + 1 < nE && tid < 2 * nt) xs[((i + 1) & 1) * 2 * nt + tid] = xn;
+    __syncthreads();
+    if (s_abort) break;
+    // stage st has been read by every thread: refill it with edge i + ns
+    if (tid == 0 && i + B.ns < nE) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(i + B.ns);
+    }
+    if (tid < P1) {
+      float rh = 0.f, rl = 0.f;
+      for (int pp = 0; pp < B.parts; ++pp) {
+        const float2 v = red[((i & 1) * B.parts + pp) * P1 + tid];
+        df_add(rh, rl, v.x, v.y);
+      }
+      if (escale) {
+        const float2 sc = df_from(escale[f]);
+        float ph = 0.f, pl = 0.f;
+        df_fma(ph, pl, make_float2(rh, rl), sc);
+        rh = ph;
+        rl = pl;
+      }
+      y[(size_t)f * P1 + tid] = df_norm(rh, rl);
+    }
+  }
+  if (i < nE) {   // a wait gave up at edge i: record it, let the copies issued for edges i .. i + ns - 1 land
+    if (tid == 0) {
+      atomicExch(&apply_bulk_wait_error, 1);
+      for (int d = i; d < nE && d < i + B.ns; ++d) mbar_wait_bounded(smem_addr(&bars[d % B.ns]), (uint32_t)((d / B.ns) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+// Device limits of the pipelined apply, queried once: SM count and the
+// dynamic shared memory a CTA may take (the opt-in maximum less the kernel's
+// static shared memory), which the kernel's attribute is raised to.
+static cudaError_t bulk_limits(int* sms, size_t* max_dyn) {
+  static bool done = false;
+  static int s_sms = 0;
+  static size_t s_max = 0;
+  if (!done) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, apply_bulk_kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)optin <= fa.sharedSizeBytes) return cudaErrorInvalidValue;
+    s_max = (size_t)optin - fa.sharedSizeBytes;
+    if ((e = cudaFuncSetAttribute(apply_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_max)) !=
+        cudaSuccess)
+      return e;
+    done = true;
+  }
+  *sms = s_sms;
+  *max_dyn = s_max;
+  return cudaSuccess;
+}
+
+// Shape of the pipelined apply for bps CTAs per SM within max_dyn bytes of
+// dynamic shared memory per CTA; false where it does not apply (a trace gather
+// wider than the CTA, or fewer than two stages fit).
+static bool bulk_shape(const Params& P, int bps, size_t max_dyn, BulkShape& B, size_t& smem) {
+  if (bps < 1 || P.P1 > ABK_THREADS || 2 * P.n_t > ABK_THREADS) return false;
+  const size_t blk_bytes = (size_t)P.n_t * P.P1 * sizeof(float2);
+  B.seg = (int)((blk_bytes + 8 + 15) & ~(size_t)15);
+  B.parts = ABK_THREADS / P.P1;
+  B.cpp = (2 * P.n_t + B.parts - 1) / B.parts;
+  const size_t fixed = 128 + (size_t)4 * P.n_t * sizeof(float2) + (size_t)2 * B.parts * P.P1 * sizeof(float2);
+  // 228 KB of shared memory per SM, 1 KB reserved per CTA, 1 KB left for static shared memory
+  const size_t per_cta = (size_t)228 * 1024 / bps - 2048;
+  const size_t cap = per_cta < max_dyn ? per_cta : max_dyn;
+  if (cap <= fixed) return false;
+  int ns = (int)((cap - fixed) / ((size_t)2 * B.seg));
+  if (ns > ABK_MAX_STAGES) ns = ABK_MAX_STAGES;
+  if (ns < 2) return false;
+  B.ns = ns;
+  smem = fixed + (size_t)ns * 2 * B.seg;
+  return true;
+}
+
+bool apply_bulk_available(const Params& P, int bps) {
+  BulkShape B;
+  size_t smem, max_dyn;
+  int sms;
+  if (bulk_limits(&sms, &max_dyn) != cudaSuccess) return false;
+  return bulk_shape(P, bps, max_dyn, B, smem);
+}
+
+cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x, float2* y, const double* escale,
+                              const int* stop, cudaStream_t st, int bps) {
+  BulkShape B;
+  size_t smem, max_dyn;
+  int sms;
+  cudaError_t e = bulk_limits(&sms, &max_dyn);
+  if (e != cudaSuccess) return e;
+  if (!bulk_shape(P, bps, max_dyn, B, smem)) return cudaErrorInvalidValue;
+  const int grid = std::min(sms * bps, P.n_int > 0 ? P.n_int : 1);
+  apply_bulk_kernel<<<grid, ABK_THREADS, smem, st>>>(P, S, x, y, escale, stop, B);
+  return cudaGetLastError();
+}
+
+// Reads (and clears) the timeout flag of the pipelined apply.
+cudaError_t apply_bulk_take_error(cudaStream_t st, int* err) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(err, apply_bulk_wait_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && *err) e = cudaMemcpyToSymbolAsync(apply_bulk_wait_error, &zero, sizeof(int), 0,
+                                                             cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
                              const double* escale, const int* stop, cudaStream_t st, int epb) {
+  // epb < 0: the pipelined bulk-copy apply with -epb CTAs per SM (split-FP32 blocks only)
+  if (epb < 0 && bt == 1)
+    return launch_apply_bulk(P, static_cast<const float2*>(S), x, y, escale, stop, st, -epb);
   // epb edges per block, one thread per (edge, trace position): at most 512 threads
   if (epb <= 0 || epb * P.P1 > 512) epb = apply_edges_per_block(P);
   const int threads = (epb * P.P1 + 31) / 32 * 32;

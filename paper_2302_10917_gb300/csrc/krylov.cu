@@ -554,6 +554,12 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
   const int epb = c->tune_epb[bt];
   const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
+  // the pipelined apply's timeout flag, read once the solve has synchronised
+  auto bulk_wait_gave_up = [&]() -> bool {
+    if (!(epb < 0 && bt == 1)) return false;
+    int err = 0;
+    return !cu.ok(apply_bulk_take_error(st, &err)) || err != 0;
+  };
 
   // ||g||
   axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, g, 0.0, g, t, n, part);
@@ -585,7 +591,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     rep.outer += 1;
     if (rel <= o.tol) {
       rep.converged = 1;
-      return HDG_OK;
+      return bulk_wait_gave_up() ? fail(c, HDG_ERR_TIMEOUT, "pipelined apply: a bounded copy wait gave up") : HDG_OK;
     }
     if (its >= o.maxit) break;
     // r0 = D^-1 t; V0 = r0 / beta; the cycle aims at the reduction the true residual still needs
@@ -718,6 +724,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     LAUNCHED(2);
   }
   rep.converged = 0;
+  if (bulk_wait_gave_up()) return fail(c, HDG_ERR_TIMEOUT, "pipelined apply: a bounded copy wait gave up");
   return fail(c, HDG_ERR_NOCONV, "GMRES reached maxit with relative residual " + std::to_string(rel));
 }
 
@@ -781,6 +788,18 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   }
   if (def_apply == 0.0 && !c->lv)
     def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb)); });
+  // split-FP32 blocks: the pipelined bulk-copy apply with 1 .. 3 CTAs per SM
+  double best_bulk = 0.0;
+  for (int bps = 1; bps <= 3 && bt == 1 && !c->lv; ++bps) {
+    if (!apply_bulk_available(P, bps)) continue;
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -bps)); });
+    int err = 0;
+    if (!cu.ok(apply_bulk_take_error(st, &err)) || err)
+      return fail(c, HDG_ERR_TIMEOUT, "autotune: pipelined apply: a bounded copy wait gave up");
+    c->launches += 6;
+    if (best_bulk == 0.0 || t < best_bulk) best_bulk = t;
+    if (t < best_apply) { best_apply = t; best_epb = -bps; }
+  }
   // multi-dot blocks
   int best_kgd = KGD;
   double best_mdot = 1e30, def_mdot = 0.0;
@@ -809,8 +828,10 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   if (!c->lv) c->tune_epb[bt] = best_epb;
   c->tune_kgd = best_kgd;
   c->tune_kgu = best_kgu;
-  rep.apply_edges_per_block = best_epb;
-  rep.apply_threads = c->lv ? best_rb : (best_epb * P.P1 + 31) / 32 * 32;
+  rep.apply_edges_per_block = best_epb > 0 ? best_epb : 0;
+  rep.apply_threads = c->lv ? best_rb : (best_epb < 0 ? 256 : (best_epb * P.P1 + 31) / 32 * 32);
+  rep.apply_bulk = best_epb < 0 ? -best_epb : 0;
+  rep.apply_bulk_ms = best_bulk;
   rep.mdot_blocks = best_kgd;
   rep.update_blocks = best_kgu;
   rep.apply_ms = best_apply;

@@ -48,6 +48,9 @@ def main(argv=None):
     ap.add_argument("--split", action="store_true", help="split-FP32 condensation")
     ap.add_argument("--orth", type=int, default=1, help="0: CGS2, 1: single-projection Gram-Schmidt")
     ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner before the solve")
+    ap.add_argument("--bulk", type=int, default=0,
+                    help="split-FP32 operator in the pipelined bulk-copy shape with this many CTAs per SM "
+                         "(after --autotune); without --step also times it against the default shape")
     ap.add_argument("--levels", action="store_true", help="the banded-level mesh (see the module docstring)")
     ap.add_argument("--nrhs", type=int, default=1, help="columns of the level-mesh applies")
     a = ap.parse_args(argv)
@@ -82,6 +85,19 @@ def main(argv=None):
     gm = None
     if a.autotune:
         pr.autotune(mode=a.mode, restart=a.restart)
+    bulk_ms = {}
+    if a.bulk > 0:
+        xs = torch.stack([x.float(), (x - x.float().double()).float()], dim=1).contiguous()
+        for name, bulk in (("default", 0), ("bulk", a.bulk)):
+            pr.set_apply_shape(2, bulk_ctas_per_sm=bulk)
+            pr.apply(xs, precond=True, prec=49)
+            e0, e1 = ev(), ev()
+            e0.record()
+            for _ in range(max(1, a.applies)):
+                pr.apply(xs, precond=True, prec=49)
+            e1.record()
+            torch.cuda.synchronize()
+            bulk_ms[name] = e0.elapsed_time(e1) / max(1, a.applies)
     if a.gmres_steps > 0:
         x0, rep, st = pr.solve(pr.rhs(), tol=1e-14, restart=a.restart, maxit=a.gmres_steps, mode=a.mode,
                                check=False, orth=a.orth)
@@ -89,7 +105,8 @@ def main(argv=None):
     out = {"info": pr.info, "gmres": gm, "condense_ms": t[0].elapsed_time(t[1]),
            "apply64_pc_ms": t[1].elapsed_time(t[2]) / max(1, a.applies), "apply64_ms": t[2].elapsed_time(t[3]),
            "apply32_ms": t[3].elapsed_time(t[4]), "apply_df_ms": t[4].elapsed_time(t[5]),
-           "y_norm": float(y.norm()), "y32_norm": float(y32.norm()), "ydf_norm": float(ydf.norm())}
+           "y_norm": float(y.norm()), "y32_norm": float(y32.norm()), "ydf_norm": float(ydf.norm()),
+           "apply49_ms": bulk_ms}
     print(json.dumps(out))
     pr.close()
 
@@ -105,6 +122,8 @@ def _step(pr, f, a):
     g = pr.rhs()
     if a.autotune:
         pr.autotune(mode=a.mode, restart=a.restart)
+    if a.bulk > 0:
+        pr.set_apply_shape(2, bulk_ctas_per_sm=a.bulk)
     x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False, orth=a.orth)
     t[2].record()
     u, q = pr.recover(x)
