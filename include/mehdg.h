@@ -376,12 +376,11 @@ hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, 
  * of the trace-operator apply (one thread per edge and trace position, up to
  * 512 threads) and, for split-FP32 blocks on a uniform mesh, the pipelined
  * apply with 1 to 3 CTAs per SM (bulk asynchronous copies of the row-blocks
- * into shared memory; the sum over an edge's columns is then taken in a few
- * parts, so its last bits differ from the one-thread-per-row apply's),
+ * into shared memory, consumed row by row in the same summation order),
  * blocks of the multi-dot and of the streaming update (at
  * opts->restart / 2 basis vectors). Keeps the fastest of each in the context
  * for every later hdg_solve / hdg_apply and reports them. Arithmetic and
- * results are unchanged by the edges per block; the multi-dot's partial sums
+ * results are unchanged by the apply's shape; the multi-dot's partial sums
  * follow its block count (fixed per context, so solves stay reproducible).
  * Needs hdg_condense (with the blocks the mode uses). Synchronous. */
 typedef struct {

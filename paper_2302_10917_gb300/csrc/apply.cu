@@ -306,31 +306,32 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
 // ---------------------------------------------------------------------------
 // Pipelined variant of the split-FP32 apply (the GMRES operator). The two
 // element-side row-blocks of each edge are moved HBM -> shared memory by the
-// bulk-copy (TMA) engine several edges ahead of the arithmetic, so the bytes
-// in flight no longer depend on how many loads the threads keep outstanding.
-// Persistent CTAs (a few per SM) take the edges f = blockIdx.x + i gridDim.x;
-// stage i % ns of a ring holds edge i's two row-blocks and an mbarrier counts
-// their transaction bytes. The trace values of edge i + 1 are gathered into
-// registers while edge i is computed. Thread (part, s): trace position s of
-// the edge and one contiguous part of its 2 n_t columns (side 0, then side 1);
-// the parts' sums are added in part order, so the result does not depend on
-// the grid. A row-block starts on an 8-byte boundary: the copy starts at the
-// 16-byte boundary below it and covers the block rounded up to 16 bytes (the
+// bulk-copy (TMA) engine, so the bytes in flight no longer depend on how many
+// loads the threads keep outstanding. Warp-specialised persistent CTAs (a few
+// per SM) take the edges f = blockIdx.x + i gridDim.x: warp 0 (one lane)
+// issues the copies, warps 1 .. NC each own one shared-memory slot and compute
+// the edges i = c - 1, c - 1 + NC, ... that land in it. Per slot an mbarrier
+// counts the copy's transaction bytes (full) and one counts the consumer's
+// release (empty), so warps only wait on their own slot: no CTA-wide barrier
+// inside the loop. A consumer lane walks one row of the edge (trace position
+// s) through both sides' row-blocks with the one-thread-per-row apply's
+// summation order, so both shapes give the same bits; it gathers the next
+// edge's trace values into registers while it computes the current one. A
+// row-block starts on an 8-byte boundary: the copy starts at the 16-byte
+// boundary below it and covers the block rounded up to 16 bytes (the
 // split-FP32 array carries 16 bytes of slack at its end). Every wait is
-// bounded: on timeout the CTA sets apply_bulk_wait_error, waits (bounded) for
-// the copies it issued and returns.
+// bounded: on timeout the CTA sets apply_bulk_wait_error, lets the copies it
+// issued land (bounded again) and returns.
 // ---------------------------------------------------------------------------
-constexpr int ABK_THREADS = 256;
-constexpr int ABK_MAX_STAGES = 6;
+constexpr int ABK_MAX_CONSUMERS = 7;
+constexpr int ABK_XR = 8;                              // trace values per lane: 2 n_t <= 32 ABK_XR
 constexpr long long ABK_WAIT_CYCLES = 2000000000LL;   // about one second at 2 GHz
 
 __device__ int apply_bulk_wait_error;
 
 struct BulkShape {
-  int ns;      // stages of the ring
-  int seg;     // bytes of one side's segment in a stage (multiple of 16)
-  int parts;   // column parts per edge
-  int cpp;     // columns per part
+  int nc;      // consumer warps = slots
+  int seg;     // bytes of one side's segment in a slot (multiple of 16)
 };
 
 namespace {
@@ -339,6 +340,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -353,10 +357,13 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0u;
 }
 // true once the phase of this parity has completed; false after the cycle limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// or once another warp of the CTA has given up (abort flag)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
   const long long t0 = clock64();
-  while (!mbar_test(bar, parity))
+  while (!mbar_test(bar, parity)) {
+    if (abort_flag && *abort_flag) return false;
     if (clock64() - t0 > ABK_WAIT_CYCLES) return false;
+  }
   return true;
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -366,126 +373,157 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 }  // namespace
 
-__global__ void __launch_bounds__(ABK_THREADS) apply_bulk_kernel(Params P, const float2* __restrict__ S,
-                                                                 const float2* __restrict__ x, float2* __restrict__ y,
-                                                                 const double* __restrict__ escale,
-                                                                 const int* __restrict__ stop, BulkShape B) {
+__global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kernel(
+    Params P, const float2* __restrict__ S, const float2* __restrict__ x, float2* __restrict__ y,
+    const double* __restrict__ escale, const int* __restrict__ stop, BulkShape B) {
   if (stop && *stop) return;
   extern __shared__ __align__(128) unsigned char sraw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sraw);                 // [ns]
-  unsigned char* stages = sraw + 128;                                   // [ns][2][seg]
-  const int nt = P.n_t, P1 = P.P1, PP = P.P;
-  float2* xs = reinterpret_cast<float2*>(stages + (size_t)B.ns * 2 * B.seg);   // [2][2 n_t]
-  float2* red = xs + 4 * nt;                                            // [2][parts][P1]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sraw);                  // [nc]
+  uint64_t* empty = full + ABK_MAX_CONSUMERS;                           // [nc]
+  unsigned char* slots = sraw + 128;                                     // [nc][2][seg]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P, NC = B.nc;
+  float2* xsall = reinterpret_cast<float2*>(slots + (size_t)NC * 2 * B.seg);   // [nc][2 n_t]
   __shared__ int s_abort;
-  const int tid = threadIdx.x;
+  __shared__ int s_issued[ABK_MAX_CONSUMERS], s_done[ABK_MAX_CONSUMERS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = gridDim.x;
   const int nE = (int)blockIdx.x < P.n_int ? (P.n_int - 1 - (int)blockIdx.x) / G + 1 : 0;
   const size_t blk_bytes = (size_t)nt * P1 * sizeof(float2);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int i = 0; i < B.ns; ++i) mbar_init(smem_addr(&bars[i]), 1);
+    for (int c = 0; c < NC; ++c) {
+      mbar_init(smem_addr(&full[c]), 1);
+      mbar_init(smem_addr(&empty[c]), 1);
+      s_issued[c] = 0;
+      s_done[c] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // thread 0: the two row-blocks of edge i into stage i % ns
-  auto issue = [&](int i) {
-    const int f = (int)blockIdx.x + i * G;
-    int e[2], k[2], fl[2];
-    double len;
-    edge_sides(f, P.n, e, k, fl, &len);
-    const int st = i % B.ns;
-    const uint32_t bar = smem_addr(&bars[st]);
-    const char* src[2];
-    uint32_t sz[2];
-    for (int sd = 0; sd < 2; ++sd) {
-      const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
-      const size_t a0 = off & ~(size_t)15;
-      src[sd] = reinterpret_cast<const char*>(S) + a0;
-      sz[sd] = (uint32_t)(((off - a0) + blk_bytes + 15) & ~(size_t)15);
-    }
-    mbar_arrive_tx(bar, sz[0] + sz[1]);
-    for (int sd = 0; sd < 2; ++sd) bulk_load(smem_addr(stages + ((size_t)st * 2 + sd) * B.seg), src[sd], sz[sd], bar);
-  };
-  // trace value c2 (side c2 / n_t, element column c2 % n_t) of edge i
-  auto gather = [&](int i, int c2) -> float2 {
-    const int f = (int)blockIdx.x + i * G;
-    int e[2], k[2], fl[2];
-    double len;
-    edge_sides(f, P.n, e, k, fl, &len);
-    const int sd = c2 >= nt ? 1 : 0, c = c2 - sd * nt;
-    int code[3], flip[3];
-    elem_edges(e[sd], P.n, code, flip);
-    const int kk = c / P1, t = c - kk * P1;
-    return code[kk] >= 0 ? x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)] : make_float2(0.f, 0.f);
-  };
-  if (tid == 0)
-    for (int i = 0; i < B.ns && i < nE; ++i) issue(i);
-  if (nE > 0 && tid < 2 * nt) xs[tid] = gather(0, tid);
-  __syncthreads();
-  const int part = tid / P1, s = tid - part * P1;
-  const bool active = part < B.parts;
-  int i = 0;
-  for (; i < nE; ++i) {
-    const int st = i % B.ns;
-    const int f = (int)blockIdx.x + i * G;
-    float2 xn = make_float2(0.f, 0.f);
-    if (i + 1 < nE && tid < 2 * nt) xn = gather(i + 1, tid);
-    int e[2], k[2], fl[2];
-    double len;
-    edge_sides(f, P.n, e, k, fl, &len);
-    if (!mbar_wait_bounded(smem_addr(&bars[st]), (uint32_t)((i / B.ns) & 1))) s_abort = 1;
-    if (active) {
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-      const float2* xv = xs + (i & 1) * 2 * nt;
-      const int q0 = part * B.cpp, q1 = min(2 * nt, q0 + B.cpp);
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int lo = max(q0, sd * nt), hi = min(q1, (sd + 1) * nt);
-        if (lo >= hi) continue;
-        const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
-        const float2* blk = reinterpret_cast<const float2*>(stages + ((size_t)st * 2 + sd) * B.seg + (off & 15));
-        const float2* row = blk + (fl[sd] ? PP - s : s);   // entry (column j, this row) at j * P1
-        int j = lo - sd * nt;
-        const int jend = hi - sd * nt;
-        const float2* xq = xv + sd * nt;
-        for (; j + 1 < jend; j += 2) {
-          df_fma(h0, l0, row[j * P1], xq[j]);
-          df_fma(h1, l1, row[(j + 1) * P1], xq[j + 1]);
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // producer: edge i into slot i % NC once its consumer has released the slot's previous edge
+    if (lane == 0) {
+      for (int i = 0; i < nE; ++i) {
+        const int c = i % NC, u = i / NC;
+        if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[c]), (uint32_t)((u - 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          break;
         }
-        if (j < jend) df_fma(h0, l0, row[j * P1], xq[j]);
+        const int f = (int)blockIdx.x + i * G;
+        int e[2], k[2], fl[2];
+        double len;
+        edge_sides(f, P.n, e, k, fl, &len);
+        const uint32_t bar = smem_addr(&full[c]);
+        const char* src[2];
+        uint32_t sz[2];
+        for (int sd = 0; sd < 2; ++sd) {
+          const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
+          const size_t a0 = off & ~(size_t)15;
+          src[sd] = reinterpret_cast<const char*>(S) + a0;
+          sz[sd] = (uint32_t)(((off - a0) + blk_bytes + 15) & ~(size_t)15);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_tx(bar, sz[0] + sz[1]);
+        for (int sd = 0; sd < 2; ++sd)
+          bulk_load(smem_addr(slots + ((size_t)c * 2 + sd) * B.seg), src[sd], sz[sd], bar);
+        s_issued[c] = u + 1;
       }
-      df_add(h0, l0, h1, l1);
-      red[((i & 1) * B.parts + part) * P1 + s] = make_float2(h0, l0);
     }
-    if (i + 1 < nE && tid < 2 * nt) xs[((i + 1) & 1) * 2 * nt + tid] = xn;
-    __syncthreads();
-    if (s_abort) break;
-    // stage st has been read by every thread: refill it with edge i + ns
-    if (tid == 0 && i + B.ns < nE) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(i + B.ns);
+  } else if (warp <= NC) {
+    // consumer of slot c: edges i = c, c + NC, ...
+    const int c = warp - 1;
+    float2* xs = xsall + (size_t)c * 2 * nt;
+    const unsigned char* seg0 = slots + (size_t)c * 2 * B.seg;
+    const int nk = nE > c ? (nE - 1 - c) / NC + 1 : 0;
+    float2 xr[ABK_XR];
+    // trace values of edge i: lane holds columns lane + 32 r of the [2][n_t] gather
+    auto gather = [&](int i) {
+      const int f = (int)blockIdx.x + i * G;
+      int e[2], k[2], fl[2];
+      double len;
+      edge_sides(f, P.n, e, k, fl, &len);
+      int code[2][3], flip[2][3];
+      elem_edges(e[0], P.n, code[0], flip[0]);
+      elem_edges(e[1], P.n, code[1], flip[1]);
+#pragma unroll
+      for (int r = 0; r < ABK_XR; ++r) {
+        const int c2 = lane + 32 * r;
+        float2 v = make_float2(0.f, 0.f);
+        if (c2 < 2 * nt) {
+          const int sd = c2 >= nt ? 1 : 0, cc = c2 - sd * nt;
+          const int kk = cc / P1, t = cc - kk * P1;
+          if (code[sd][kk] >= 0) v = x[(size_t)code[sd][kk] * P1 + (flip[sd][kk] ? PP - t : t)];
+        }
+        xr[r] = v;
+      }
+    };
+    auto stash = [&]() {
+#pragma unroll
+      for (int r = 0; r < ABK_XR; ++r)
+        if (lane + 32 * r < 2 * nt) xs[lane + 32 * r] = xr[r];
+      __syncwarp();
+    };
+    if (nk > 0) {
+      gather(c);
+      stash();
     }
-    if (tid < P1) {
-      float rh = 0.f, rl = 0.f;
-      for (int pp = 0; pp < B.parts; ++pp) {
-        const float2 v = red[((i & 1) * B.parts + pp) * P1 + tid];
-        df_add(rh, rl, v.x, v.y);
+    int kq = 0;
+    for (; kq < nk; ++kq) {
+      const int i = c + kq * NC;
+      if (kq + 1 < nk) gather(i + NC);   // loads in flight during the products below
+      // every lane polls; the warp proceeds only if all lanes saw the copy land (a uniform decision)
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)(kq & 1), abort_flag));
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+        break;
       }
-      if (escale) {
-        const float2 sc = df_from(escale[f]);
-        float ph = 0.f, pl = 0.f;
-        df_fma(ph, pl, make_float2(rh, rl), sc);
-        rh = ph;
-        rl = pl;
+      const int f = (int)blockIdx.x + i * G;
+      if (lane < P1) {
+        int e[2], k[2], fl[2];
+        double len;
+        edge_sides(f, P.n, e, k, fl, &len);
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        const int ng = nt / 8;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
+          const float2* row = reinterpret_cast<const float2*>(seg0 + (size_t)sd * B.seg + (off & 15)) +
+                              (fl[sd] ? PP - lane : lane);
+          const float2* xv = xs + sd * nt;
+          // the one-thread-per-row apply's order: pairs over groups of 8, the rest into the first sum
+          for (int j = 0; j < ng * 8; j += 2) {
+            df_fma(h0, l0, row[j * P1], xv[j]);
+            df_fma(h1, l1, row[(j + 1) * P1], xv[j + 1]);
+          }
+          for (int j = ng * 8; j < nt; ++j) df_fma(h0, l0, row[j * P1], xv[j]);
+        }
+        df_add(h0, l0, h1, l1);
+        if (escale) {
+          const float2 sc = df_from(escale[f]);
+          float ph = 0.f, pl = 0.f;
+          df_fma(ph, pl, make_float2(h0, l0), sc);
+          h0 = ph;
+          l0 = pl;
+        }
+        y[(size_t)f * P1 + lane] = df_norm(h0, l0);
       }
-      y[(size_t)f * P1 + tid] = df_norm(rh, rl);
+      __syncwarp();
+      if (lane == 0) {
+        s_done[c] = kq + 1;
+        mbar_arrive(smem_addr(&empty[c]));
+      }
+      if (kq + 1 < nk) stash();
     }
   }
-  if (i < nE) {   // a wait gave up at edge i: record it, let the copies issued for edges i .. i + ns - 1 land
-    if (tid == 0) {
+  __syncthreads();
+  if (s_abort) {   // a wait gave up: record it and let every copy still in flight land
+    if (threadIdx.x == 0) {
       atomicExch(&apply_bulk_wait_error, 1);
-      for (int d = i; d < nE && d < i + B.ns; ++d) mbar_wait_bounded(smem_addr(&bars[d % B.ns]), (uint32_t)((d / B.ns) & 1));
+      for (int c = 0; c < NC; ++c)
+        if (s_issued[c] > s_done[c])
+          mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)((s_issued[c] - 1) & 1), nullptr);
     }
     __syncthreads();
   }
@@ -519,24 +557,22 @@ static cudaError_t bulk_limits(int* sms, size_t* max_dyn) {
 }
 
 // Shape of the pipelined apply for bps CTAs per SM within max_dyn bytes of
-// dynamic shared memory per CTA; false where it does not apply (a trace gather
-// wider than the CTA, or fewer than two stages fit).
+// dynamic shared memory per CTA: as many consumer slots as fit (at most
+// ABK_MAX_CONSUMERS); false where it does not apply (an edge row wider than a
+// warp, a trace gather beyond the lanes' registers, or no slot fits).
 static bool bulk_shape(const Params& P, int bps, size_t max_dyn, BulkShape& B, size_t& smem) {
-  if (bps < 1 || P.P1 > ABK_THREADS || 2 * P.n_t > ABK_THREADS) return false;
+  if (bps < 1 || P.P1 > 32 || 2 * P.n_t > 32 * ABK_XR) return false;
   const size_t blk_bytes = (size_t)P.n_t * P.P1 * sizeof(float2);
   B.seg = (int)((blk_bytes + 8 + 15) & ~(size_t)15);
-  B.parts = ABK_THREADS / P.P1;
-  B.cpp = (2 * P.n_t + B.parts - 1) / B.parts;
-  const size_t fixed = 128 + (size_t)4 * P.n_t * sizeof(float2) + (size_t)2 * B.parts * P.P1 * sizeof(float2);
+  const size_t per_slot = (size_t)2 * B.seg + (size_t)2 * P.n_t * sizeof(float2);
   // 228 KB of shared memory per SM, 1 KB reserved per CTA, 1 KB left for static shared memory
   const size_t per_cta = (size_t)228 * 1024 / bps - 2048;
   const size_t cap = per_cta < max_dyn ? per_cta : max_dyn;
-  if (cap <= fixed) return false;
-  int ns = (int)((cap - fixed) / ((size_t)2 * B.seg));
-  if (ns > ABK_MAX_STAGES) ns = ABK_MAX_STAGES;
-  if (ns < 2) return false;
-  B.ns = ns;
-  smem = fixed + (size_t)ns * 2 * B.seg;
+  if (cap <= 128 + per_slot) return false;
+  int nc = (int)((cap - 128) / per_slot);
+  if (nc > ABK_MAX_CONSUMERS) nc = ABK_MAX_CONSUMERS;
+  B.nc = nc;
+  smem = 128 + (size_t)nc * per_slot;
   return true;
 }
 
@@ -557,7 +593,7 @@ cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x,
   if (e != cudaSuccess) return e;
   if (!bulk_shape(P, bps, max_dyn, B, smem)) return cudaErrorInvalidValue;
   const int grid = std::min(sms * bps, P.n_int > 0 ? P.n_int : 1);
-  apply_bulk_kernel<<<grid, ABK_THREADS, smem, st>>>(P, S, x, y, escale, stop, B);
+  apply_bulk_kernel<<<grid, 32 * (B.nc + 1), smem, st>>>(P, S, x, y, escale, stop, B);
   return cudaGetLastError();
 }
 

@@ -2,12 +2,13 @@
 split-FP32 vectors, the kernel and launch shape hdg_solve's mode 2 uses) in
 every launch shape: the one-thread-per-row apply (default and 1 edge per
 block) and the pipelined apply (bulk asynchronous copies of each edge's two
-row-blocks into a ring of shared-memory stages) with 1, 2 and 3 CTAs per SM.
+row-blocks into shared-memory slots, one consumer warp per slot) with 1, 2
+and 3 CTAs per SM.
 
 Reference: the oracle's D_f^-1 S x (Sec. 6.1) or, with face blocks, the
 inverted diagonal face blocks of the oracle's assembled S times S x; on the
-small meshes every edge, on a mesh with many edges per CTA (the stage ring
-wraps many times) sampled edges from the oracle's blocks of the two adjacent
+small meshes every edge, on a mesh with many edges per CTA (every slot
+refilled many times) sampled edges from the oracle's blocks of the two adjacent
 elements. Tolerance 1e-12 relative (max norm), as for the FP64-vector split
 apply: split-FP32 arithmetic carries about 48 significant bits.
 """
@@ -104,6 +105,21 @@ def test_split_operator_matches_oracle_in_every_shape(case, shape):
         gpu.set_apply_shape(2)
 
 
+def test_pipelined_apply_gives_the_same_bits(case):
+    """The pipelined consumers walk each row in the one-thread-per-row apply's
+    summation order: every launch shape returns the same bits."""
+    ora, gpu = case["ora"], case["gpu"]
+    x = split(case["rng"].standard_normal(ora.mesh.N_tr))
+    gpu.set_apply_shape(2)
+    y0 = gpu.apply(x, precond=True, prec=49)
+    try:
+        for epb, bulk in ((1, 0), (0, 1), (0, 2), (0, 3)):
+            _set_shape(gpu, epb, bulk)
+            assert torch.equal(gpu.apply(x, precond=True, prec=49), y0), (epb, bulk)
+    finally:
+        gpu.set_apply_shape(2)
+
+
 def test_solve_with_the_pipelined_apply(case):
     ora, gpu = case["ora"], case["gpu"]
     _set_shape(gpu, 0, 2)
@@ -167,7 +183,7 @@ def _elements_of_edge(n, f):
 
 def test_many_edges_per_cta_sampled_edges():
     """n = 64, m = 8, p = 3 (12,160 interior edges: 27 to 80 edges per CTA, so
-    every stage of the ring is refilled many times): sampled edges, the first and
+    every slot is refilled many times): sampled edges, the first and
     the last, against the oracle's blocks of their two elements and D_f^-1."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
