@@ -342,8 +342,8 @@ def run_ours(args):
     rooflines = {
         "apply": {"kernel": ({0: "apply_vdf_kernel<0> (FP64 blocks)", 1: "apply_vdf_kernel<2> (FP32 blocks)",
                               2: "apply_vdf_kernel<1> (split-FP32 blocks)"}[args.mode] if not tune.get("apply_bulk")
-                             else f"apply_bulk_kernel (split-FP32 blocks, bulk-copy stage ring, "
-                                  f"{tune['apply_bulk']} CTAs per SM)"),
+                             else f"apply_bulk_kernel (split-FP32 blocks, bulk copies into shared-memory slots, "
+                                  f"{tune['apply_bulk']} consumer warps per edge)"),
                   "bound": "alu" if args.mode == 0 else "hbm",
                   "launches": prof["apply32" if args.mode == 1 else "apply"][0],
                   "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},

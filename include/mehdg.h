@@ -265,10 +265,11 @@ hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int
 /* Sets the launch shape of the trace-operator apply inside hdg_solve for one
  * mode (0 FP64, 1 FP32 + refinement, 2 split-FP32), as hdg_autotune would:
  * edges_per_block > 0 (with edges_per_block (m p + 1) <= 512) for the
- * one-thread-per-row apply, or bulk_ctas_per_sm > 0 (mode 2 only) for the
- * pipelined apply with that many CTAs per SM; both 0 restores the default.
- * Uniform meshes only; HDG_ERR_ARG for a shape that does not apply. */
-hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_ctas_per_sm);
+ * one-thread-per-row apply, or bulk_warps = 1 .. 3 (mode 2 only) for the
+ * pipelined apply with that many consumer warps per edge; both 0 restores
+ * the default. Uniform meshes only; HDG_ERR_ARG for a shape that does not
+ * apply. */
+hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_warps);
 
 /* Solve S x = g (Eq. global_problem) with restarted GMRES, left-
  * preconditioned by D^-1 (Sec. 6.1). x_dev holds the initial guess on entry
@@ -375,12 +376,13 @@ hdg_status hdg_gradient(hdg_ctx* ctx, const double* x_dev, const double* u_dev, 
  * of the GMRES kernels for opts->mode at this problem size: edges per block
  * of the trace-operator apply (one thread per edge and trace position, up to
  * 512 threads) and, for split-FP32 blocks on a uniform mesh, the pipelined
- * apply with 1 to 3 CTAs per SM (bulk asynchronous copies of the row-blocks
- * into shared memory, consumed row by row in the same summation order),
+ * apply with 1 to 3 consumer warps per edge (bulk asynchronous copies of the
+ * row-blocks into shared memory, consumed row by row; with one warp per edge
+ * in the same summation order, with more in a fixed order of their own),
  * blocks of the multi-dot and of the streaming update (at
  * opts->restart / 2 basis vectors). Keeps the fastest of each in the context
  * for every later hdg_solve / hdg_apply and reports them. Arithmetic and
- * results are unchanged by the apply's shape; the multi-dot's partial sums
+ * results are unchanged by the apply's edges per block; the multi-dot's partial sums
  * follow its block count (fixed per context, so solves stay reproducible).
  * Needs hdg_condense (with the blocks the mode uses). Synchronous. */
 typedef struct {
@@ -392,10 +394,10 @@ typedef struct {
   double mdot_ms;
   double update_ms;
   double default_ms;         /* the three kernels with the built-in shapes */
-  int apply_bulk;            /* > 0: the pipelined apply was chosen, with this many CTAs per SM (split-FP32
-                                blocks on a uniform mesh: each edge's two row-blocks are brought into shared
-                                memory by bulk asynchronous copies, several edges ahead; apply_edges_per_block
-                                is then 0 and apply_threads 256) */
+  int apply_bulk;            /* > 0: the pipelined apply was chosen, with this many consumer warps per edge
+                                (split-FP32 blocks on a uniform mesh: the element-side row-blocks are brought
+                                into shared memory by bulk asynchronous copies ahead of the products;
+                                apply_edges_per_block is then 0 and apply_threads the CTA's threads) */
   double apply_bulk_ms;      /* best time of the pipelined apply (0 where it was not a candidate) */
 } hdg_tune_report;
 hdg_status hdg_autotune(hdg_ctx* ctx, const hdg_solve_opts* opts, hdg_tune_report* report);

@@ -303,9 +303,9 @@ class Problem:
             self._check(st)
         return x, r.as_dict(), st
 
-    def set_apply_shape(self, mode, edges_per_block=0, bulk_ctas_per_sm=0):
+    def set_apply_shape(self, mode, edges_per_block=0, bulk_warps=0):
         """hdg_set_apply_shape: the apply's launch shape inside solves of this mode."""
-        self._check(self.lib.hdg_set_apply_shape(self.h, mode, edges_per_block, bulk_ctas_per_sm))
+        self._check(self.lib.hdg_set_apply_shape(self.h, mode, edges_per_block, bulk_warps))
 
     def autotune(self, mode=0, restart=80):
         """hdg_autotune: time candidate launch shapes of the GMRES kernels for this mode and

@@ -586,17 +586,16 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
 }
 
-hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bulk_ctas_per_sm) {
+hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bulk_warps) {
   if (!c) return HDG_ERR_ARG;
-  if (mode < 0 || mode > 2 || edges_per_block < 0 || bulk_ctas_per_sm < 0 ||
-      (edges_per_block > 0 && bulk_ctas_per_sm > 0))
-    return set_err(c, HDG_ERR_ARG, "mode 0..2 and at most one of edges_per_block, bulk_ctas_per_sm");
+  if (mode < 0 || mode > 2 || edges_per_block < 0 || bulk_warps < 0 || (edges_per_block > 0 && bulk_warps > 0))
+    return set_err(c, HDG_ERR_ARG, "mode 0..2 and at most one of edges_per_block, bulk_warps");
   if (c->lv) return set_err(c, HDG_ERR_ARG, "a level mesh has no per-edge apply shape");
   const int bt = mode == 0 ? 0 : (mode == 2 ? 1 : 2);
   if (edges_per_block * c->prm.P1 > 512) return set_err(c, HDG_ERR_ARG, "edges_per_block * (m p + 1) above 512");
-  if (bulk_ctas_per_sm > 0 && (bt != 1 || !apply_bulk_available(c->prm, bulk_ctas_per_sm)))
+  if (bulk_warps > 0 && (bt != 1 || !apply_bulk_available(c->prm, bulk_warps)))
     return set_err(c, HDG_ERR_ARG, "the pipelined apply needs mode 2 and a shape that fits shared memory");
-  c->tune_epb[bt] = bulk_ctas_per_sm > 0 ? -bulk_ctas_per_sm : edges_per_block;
+  c->tune_epb[bt] = bulk_warps > 0 ? -bulk_warps : edges_per_block;
   return HDG_OK;
 }
 

@@ -307,30 +307,36 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
 // Pipelined variant of the split-FP32 apply (the GMRES operator). The two
 // element-side row-blocks of each edge are moved HBM -> shared memory by the
 // bulk-copy (TMA) engine, so the bytes in flight no longer depend on how many
-// loads the threads keep outstanding. Warp-specialised persistent CTAs (a few
+// loads the threads keep outstanding. Warp-specialised persistent CTAs (one
 // per SM) take the edges f = blockIdx.x + i gridDim.x: warp 0 (one lane)
-// issues the copies, warps 1 .. NC each own one shared-memory slot and compute
-// the edges i = c - 1, c - 1 + NC, ... that land in it. Per slot an mbarrier
-// counts the copy's transaction bytes (full) and one counts the consumer's
-// release (empty), so warps only wait on their own slot: no CTA-wide barrier
-// inside the loop. A consumer lane walks one row of the edge (trace position
-// s) through both sides' row-blocks with the one-thread-per-row apply's
-// summation order, so both shapes give the same bits; it gathers the next
-// edge's trace values into registers while it computes the current one. A
-// row-block starts on an 8-byte boundary: the copy starts at the 16-byte
-// boundary below it and covers the block rounded up to 16 bytes (the
-// split-FP32 array carries 16 bytes of slack at its end). Every wait is
-// bounded: on timeout the CTA sets apply_bulk_wait_error, lets the copies it
-// issued land (bounded again) and returns.
+// issues the copies of edge i into slot i % NC once the slot's consumers have
+// released it; the slot's Q consumer warps split the edge's 2 n_t columns
+// (side 0, then side 1) into Q contiguous parts. Per slot an mbarrier counts
+// the copy's transaction bytes (full) and one counts the Q consumers' releases
+// (empty), so warps wait only on their own slot. A consumer lane walks one row
+// (trace position s) through its part with the one-thread-per-row apply's
+// accumulator pattern; parts 1 .. Q-1 hand their sums to part 0 through
+// shared memory and a per-slot mbarrier, part 0 adds them in part order, so
+// Q = 1 gives that apply's bits and every Q its own fixed order. Each consumer gathers its part of the next edge's
+// trace values into registers while it computes the current one. A row-block
+// starts on an 8-byte boundary: the copy starts at the 16-byte boundary below
+// it and covers the block rounded up to 16 bytes (the split-FP32 array
+// carries 16 bytes of slack at its end). Every wait is bounded: on timeout the
+// CTA sets apply_bulk_wait_error, lets the copies it issued land (bounded
+// again) and returns.
 // ---------------------------------------------------------------------------
-constexpr int ABK_MAX_CONSUMERS = 7;
-constexpr int ABK_XR = 8;                              // trace values per lane: 2 n_t <= 32 ABK_XR
+constexpr int ABK_MAX_WARPS = 16;                      // producer + consumers
+constexpr int ABK_MAX_SLOTS = 14;
+constexpr int ABK_BARRIER_BYTES = 3 * ABK_MAX_SLOTS * 8 + 48;   // full, empty, parts (multiple of 16)
+constexpr int ABK_XR = 5;                              // trace values per lane: part width <= 32 ABK_XR
 constexpr long long ABK_WAIT_CYCLES = 2000000000LL;   // about one second at 2 GHz
 
 __device__ int apply_bulk_wait_error;
 
 struct BulkShape {
-  int nc;      // consumer warps = slots
+  int nc;      // slots
+  int q;       // consumer warps per slot
+  int cpw;     // columns per consumer warp
   int seg;     // bytes of one side's segment in a slot (multiple of 16)
 };
 
@@ -373,18 +379,20 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 }  // namespace
 
-__global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kernel(
+__global__ void __launch_bounds__(32 * ABK_MAX_WARPS) apply_bulk_kernel(
     Params P, const float2* __restrict__ S, const float2* __restrict__ x, float2* __restrict__ y,
     const double* __restrict__ escale, const int* __restrict__ stop, BulkShape B) {
   if (stop && *stop) return;
   extern __shared__ __align__(128) unsigned char sraw[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sraw);                  // [nc]
-  uint64_t* empty = full + ABK_MAX_CONSUMERS;                           // [nc]
-  unsigned char* slots = sraw + 128;                                     // [nc][2][seg]
-  const int nt = P.n_t, P1 = P.P1, PP = P.P, NC = B.nc;
-  float2* xsall = reinterpret_cast<float2*>(slots + (size_t)NC * 2 * B.seg);   // [nc][2 n_t]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sraw);                  // [nc] copy landed
+  uint64_t* empty = full + ABK_MAX_SLOTS;                               // [nc] slot released by its Q warps
+  uint64_t* parts = empty + ABK_MAX_SLOTS;                              // [nc] parts 1 .. Q-1 written
+  unsigned char* slots = sraw + ABK_BARRIER_BYTES;                       // [nc][2][seg]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P, NC = B.nc, Q = B.q, CPW = B.cpw;
+  float2* xsall = reinterpret_cast<float2*>(slots + (size_t)NC * 2 * B.seg);   // [nc q][cpw]
+  float2* redall = xsall + (size_t)NC * Q * CPW;                               // [nc][q][32]
   __shared__ int s_abort;
-  __shared__ int s_issued[ABK_MAX_CONSUMERS], s_done[ABK_MAX_CONSUMERS];
+  __shared__ int s_issued[ABK_MAX_SLOTS], s_done[ABK_MAX_SLOTS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = gridDim.x;
   const int nE = (int)blockIdx.x < P.n_int ? (P.n_int - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -393,7 +401,8 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
     s_abort = 0;
     for (int c = 0; c < NC; ++c) {
       mbar_init(smem_addr(&full[c]), 1);
-      mbar_init(smem_addr(&empty[c]), 1);
+      mbar_init(smem_addr(&empty[c]), (uint32_t)Q);
+      if (Q > 1) mbar_init(smem_addr(&parts[c]), (uint32_t)(Q - 1));
       s_issued[c] = 0;
       s_done[c] = 0;
     }
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
   volatile int* abort_flag = &s_abort;
 
   if (warp == 0) {
-    // producer: edge i into slot i % NC once its consumer has released the slot's previous edge
+    // producer: edge i into slot i % NC once its Q consumers have released the slot's previous edge
     if (lane == 0) {
       for (int i = 0; i < nE; ++i) {
         const int c = i % NC, u = i / NC;
@@ -431,14 +440,16 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
         s_issued[c] = u + 1;
       }
     }
-  } else if (warp <= NC) {
-    // consumer of slot c: edges i = c, c + NC, ...
-    const int c = warp - 1;
-    float2* xs = xsall + (size_t)c * 2 * nt;
+  } else if (warp <= NC * Q) {
+    // consumer part pq of slot c: edges i = c, c + NC, ...; columns [q0, q1) of the edge's 2 n_t
+    const int cw = warp - 1, c = cw / Q, pq = cw - c * Q;
+    const int q0 = pq * CPW, q1 = min(2 * nt, q0 + CPW);
+    float2* xs = xsall + (size_t)cw * CPW;
+    float2* red = redall + (size_t)c * Q * 32;
     const unsigned char* seg0 = slots + (size_t)c * 2 * B.seg;
     const int nk = nE > c ? (nE - 1 - c) / NC + 1 : 0;
+    const int e8 = (nt / 8) * 8;   // the one-thread-per-row apply pairs columns below e8 (per side)
     float2 xr[ABK_XR];
-    // trace values of edge i: lane holds columns lane + 32 r of the [2][n_t] gather
     auto gather = [&](int i) {
       const int f = (int)blockIdx.x + i * G;
       int e[2], k[2], fl[2];
@@ -449,12 +460,12 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
       elem_edges(e[1], P.n, code[1], flip[1]);
 #pragma unroll
       for (int r = 0; r < ABK_XR; ++r) {
-        const int c2 = lane + 32 * r;
+        const int c2 = q0 + lane + 32 * r;
         float2 v = make_float2(0.f, 0.f);
-        if (c2 < 2 * nt) {
+        if (c2 < q1) {
           const int sd = c2 >= nt ? 1 : 0, cc = c2 - sd * nt;
-          const int kk = cc / P1, t = cc - kk * P1;
-          if (code[sd][kk] >= 0) v = x[(size_t)code[sd][kk] * P1 + (flip[sd][kk] ? PP - t : t)];
+          const int kq = cc / P1, t = cc - kq * P1;
+          if (code[sd][kq] >= 0) v = x[(size_t)code[sd][kq] * P1 + (flip[sd][kq] ? PP - t : t)];
         }
         xr[r] = v;
       }
@@ -462,44 +473,70 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
     auto stash = [&]() {
 #pragma unroll
       for (int r = 0; r < ABK_XR; ++r)
-        if (lane + 32 * r < 2 * nt) xs[lane + 32 * r] = xr[r];
+        if (q0 + lane + 32 * r < q1) xs[lane + 32 * r] = xr[r];
       __syncwarp();
     };
     if (nk > 0) {
       gather(c);
       stash();
     }
-    int kq = 0;
-    for (; kq < nk; ++kq) {
+    for (int kq = 0; kq < nk; ++kq) {
       const int i = c + kq * NC;
       if (kq + 1 < nk) gather(i + NC);   // loads in flight during the products below
-      // every lane polls; the warp proceeds only if all lanes saw the copy land (a uniform decision)
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)(kq & 1), abort_flag));
-      if (!ok) {
+      // every lane polls; the warp goes on only if all lanes saw the copy land (a uniform decision)
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)(kq & 1), abort_flag))) {
         if (lane == 0) *abort_flag = 1;
         break;
       }
       const int f = (int)blockIdx.x + i * G;
+      int e[2], k[2], fl[2];
+      double len;
+      edge_sides(f, P.n, e, k, fl, &len);
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
       if (lane < P1) {
-        int e[2], k[2], fl[2];
-        double len;
-        edge_sides(f, P.n, e, k, fl, &len);
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-        const int ng = nt / 8;
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
+          const int jlo = max(q0, sd * nt) - sd * nt, jhi = min(q1, (sd + 1) * nt) - sd * nt;
+          if (jlo >= jhi) continue;
           const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
           const float2* row = reinterpret_cast<const float2*>(seg0 + (size_t)sd * B.seg + (off & 15)) +
                               (fl[sd] ? PP - lane : lane);
-          const float2* xv = xs + sd * nt;
-          // the one-thread-per-row apply's order: pairs over groups of 8, the rest into the first sum
-          for (int j = 0; j < ng * 8; j += 2) {
-            df_fma(h0, l0, row[j * P1], xv[j]);
-            df_fma(h1, l1, row[(j + 1) * P1], xv[j + 1]);
+          const int xb = sd * nt - q0;   // xs[xb + j]: trace value of column j of side sd
+          // columns below e8 alternate between the two sums (odd j to the second), the rest go to the first
+          const int jp = min(jhi, e8);
+          int j = jlo;
+          if ((j & 1) && j < jp) {
+            df_fma(h1, l1, row[j * P1], xs[xb + j]);
+            ++j;
           }
-          for (int j = ng * 8; j < nt; ++j) df_fma(h0, l0, row[j * P1], xv[j]);
+          for (; j + 1 < jp; j += 2) {
+            df_fma(h0, l0, row[j * P1], xs[xb + j]);
+            df_fma(h1, l1, row[(j + 1) * P1], xs[xb + j + 1]);
+          }
+          for (; j < jhi; ++j) {
+            if (j < e8 && (j & 1)) df_fma(h1, l1, row[j * P1], xs[xb + j]);
+            else df_fma(h0, l0, row[j * P1], xs[xb + j]);
+          }
         }
-        df_add(h0, l0, h1, l1);
+      }
+      df_add(h0, l0, h1, l1);   // this part's sum
+      if (Q > 1) {
+        if (pq > 0) {
+          red[pq * 32 + lane] = make_float2(h0, l0);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_addr(&parts[c]));
+        } else if (!__all_sync(0xffffffffu,
+                               mbar_wait_bounded(smem_addr(&parts[c]), (uint32_t)(kq & 1), abort_flag))) {
+          if (lane == 0) *abort_flag = 1;
+          break;
+        } else {
+          for (int pp = 1; pp < Q; ++pp) {   // the parts' sums in part order
+            const float2 v = red[pp * 32 + lane];
+            df_add(h0, l0, v.x, v.y);
+          }
+        }
+      }
+      if (pq == 0 && lane < P1) {
         if (escale) {
           const float2 sc = df_from(escale[f]);
           float ph = 0.f, pl = 0.f;
@@ -510,8 +547,9 @@ __global__ void __launch_bounds__(32 * (ABK_MAX_CONSUMERS + 1)) apply_bulk_kerne
         y[(size_t)f * P1 + lane] = df_norm(h0, l0);
       }
       __syncwarp();
+      // the slot (and, for part 0, the other parts' sums) has been read: release it
       if (lane == 0) {
-        s_done[c] = kq + 1;
+        if (pq == 0) s_done[c] = kq + 1;
         mbar_arrive(smem_addr(&empty[c]));
       }
       if (kq + 1 < nk) stash();
@@ -556,44 +594,56 @@ static cudaError_t bulk_limits(int* sms, size_t* max_dyn) {
   return cudaSuccess;
 }
 
-// Shape of the pipelined apply for bps CTAs per SM within max_dyn bytes of
-// dynamic shared memory per CTA: as many consumer slots as fit (at most
-// ABK_MAX_CONSUMERS); false where it does not apply (an edge row wider than a
-// warp, a trace gather beyond the lanes' registers, or no slot fits).
-static bool bulk_shape(const Params& P, int bps, size_t max_dyn, BulkShape& B, size_t& smem) {
-  if (bps < 1 || P.P1 > 32 || 2 * P.n_t > 32 * ABK_XR) return false;
+// Shape of the pipelined apply with q = 1 .. 3 consumer warps per edge: one
+// CTA per SM with as many slots as fit in max_dyn bytes of dynamic shared
+// memory and in ABK_MAX_WARPS warps; false where it does not apply (an edge
+// row wider than a warp, a part wider than the lanes' registers, or no slot
+// fits).
+static bool bulk_shape(const Params& P, int q, size_t max_dyn, BulkShape& B, size_t& smem) {
+  if (q < 1 || q > 3 || P.P1 > 32) return false;
+  B.q = q;
+  B.cpw = (2 * P.n_t + q - 1) / q;
+  if (B.cpw > 32 * ABK_XR) return false;
   const size_t blk_bytes = (size_t)P.n_t * P.P1 * sizeof(float2);
   B.seg = (int)((blk_bytes + 8 + 15) & ~(size_t)15);
-  const size_t per_slot = (size_t)2 * B.seg + (size_t)2 * P.n_t * sizeof(float2);
+  const size_t per_slot = (size_t)2 * B.seg + (size_t)q * B.cpw * sizeof(float2) + (size_t)q * 32 * sizeof(float2);
   // 228 KB of shared memory per SM, 1 KB reserved per CTA, 1 KB left for static shared memory
-  const size_t per_cta = (size_t)228 * 1024 / bps - 2048;
+  const size_t per_cta = (size_t)228 * 1024 - 2048;
   const size_t cap = per_cta < max_dyn ? per_cta : max_dyn;
-  if (cap <= 128 + per_slot) return false;
-  int nc = (int)((cap - 128) / per_slot);
-  if (nc > ABK_MAX_CONSUMERS) nc = ABK_MAX_CONSUMERS;
+  if (cap < ABK_BARRIER_BYTES + per_slot) return false;
+  int nc = (int)((cap - ABK_BARRIER_BYTES) / per_slot);
+  nc = std::min(nc, std::min(ABK_MAX_SLOTS, (ABK_MAX_WARPS - 1) / q));
   B.nc = nc;
-  smem = 128 + (size_t)nc * per_slot;
+  smem = ABK_BARRIER_BYTES + (size_t)nc * per_slot;
   return true;
 }
 
-bool apply_bulk_available(const Params& P, int bps) {
+int apply_bulk_threads(const Params& P, int q) {
+  BulkShape B;
+  size_t smem, max_dyn;
+  int sms;
+  if (bulk_limits(&sms, &max_dyn) != cudaSuccess || !bulk_shape(P, q, max_dyn, B, smem)) return 0;
+  return 32 * (1 + B.nc * B.q);
+}
+
+bool apply_bulk_available(const Params& P, int q) {
   BulkShape B;
   size_t smem, max_dyn;
   int sms;
   if (bulk_limits(&sms, &max_dyn) != cudaSuccess) return false;
-  return bulk_shape(P, bps, max_dyn, B, smem);
+  return bulk_shape(P, q, max_dyn, B, smem);
 }
 
 cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x, float2* y, const double* escale,
-                              const int* stop, cudaStream_t st, int bps) {
+                              const int* stop, cudaStream_t st, int q) {
   BulkShape B;
   size_t smem, max_dyn;
   int sms;
   cudaError_t e = bulk_limits(&sms, &max_dyn);
   if (e != cudaSuccess) return e;
-  if (!bulk_shape(P, bps, max_dyn, B, smem)) return cudaErrorInvalidValue;
-  const int grid = std::min(sms * bps, P.n_int > 0 ? P.n_int : 1);
-  apply_bulk_kernel<<<grid, 32 * (B.nc + 1), smem, st>>>(P, S, x, y, escale, stop, B);
+  if (!bulk_shape(P, q, max_dyn, B, smem)) return cudaErrorInvalidValue;
+  const int grid = std::max(1, std::min(sms, P.n_int));
+  apply_bulk_kernel<<<grid, 32 * (1 + B.nc * B.q), smem, st>>>(P, S, x, y, escale, stop, B);
   return cudaGetLastError();
 }
 
@@ -610,7 +660,7 @@ cudaError_t apply_bulk_take_error(cudaStream_t st, int* err) {
 
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
                              const double* escale, const int* stop, cudaStream_t st, int epb) {
-  // epb < 0: the pipelined bulk-copy apply with -epb CTAs per SM (split-FP32 blocks only)
+  // epb < 0: the pipelined bulk-copy apply with -epb consumer warps per edge (split-FP32 blocks only)
   if (epb < 0 && bt == 1)
     return launch_apply_bulk(P, static_cast<const float2*>(S), x, y, escale, stop, st, -epb);
   // epb edges per block, one thread per (edge, trace position): at most 512 threads

@@ -788,17 +788,17 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   }
   if (def_apply == 0.0 && !c->lv)
     def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb)); });
-  // split-FP32 blocks: the pipelined bulk-copy apply with 1 .. 3 CTAs per SM
+  // split-FP32 blocks: the pipelined bulk-copy apply with 1 .. 3 consumer warps per edge
   double best_bulk = 0.0;
-  for (int bps = 1; bps <= 3 && bt == 1 && !c->lv; ++bps) {
-    if (!apply_bulk_available(P, bps)) continue;
-    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -bps)); });
+  for (int q = 1; q <= 3 && bt == 1 && !c->lv; ++q) {
+    if (!apply_bulk_available(P, q)) continue;
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -q)); });
     int err = 0;
     if (!cu.ok(apply_bulk_take_error(st, &err)) || err)
       return fail(c, HDG_ERR_TIMEOUT, "autotune: pipelined apply: a bounded copy wait gave up");
     c->launches += 6;
     if (best_bulk == 0.0 || t < best_bulk) best_bulk = t;
-    if (t < best_apply) { best_apply = t; best_epb = -bps; }
+    if (t < best_apply) { best_apply = t; best_epb = -q; }
   }
   // multi-dot blocks
   int best_kgd = KGD;
@@ -829,7 +829,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   c->tune_kgd = best_kgd;
   c->tune_kgu = best_kgu;
   rep.apply_edges_per_block = best_epb > 0 ? best_epb : 0;
-  rep.apply_threads = c->lv ? best_rb : (best_epb < 0 ? 256 : (best_epb * P.P1 + 31) / 32 * 32);
+  rep.apply_threads = c->lv ? best_rb : (best_epb < 0 ? apply_bulk_threads(P, -best_epb) : (best_epb * P.P1 + 31) / 32 * 32);
   rep.apply_bulk = best_epb < 0 ? -best_epb : 0;
   rep.apply_bulk_ms = best_bulk;
   rep.mdot_blocks = best_kgd;

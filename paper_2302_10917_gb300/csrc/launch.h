@@ -42,11 +42,13 @@ cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, d
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
                              const double* escale, const int* stop, cudaStream_t st, int epb = 0);
 int apply_edges_per_block(const Params& P);
-// Pipelined bulk-copy apply of split-FP32 blocks (bps CTAs per SM); whether it
-// applies to this problem shape; its timeout flag (read and cleared, synchronous).
-bool apply_bulk_available(const Params& P, int bps);
+// Pipelined bulk-copy apply of split-FP32 blocks (q = 1 .. 3 consumer warps
+// per edge); whether it applies to this problem shape; its timeout flag (read
+// and cleared, synchronous).
+bool apply_bulk_available(const Params& P, int q);
+int apply_bulk_threads(const Params& P, int q);   // threads per CTA of that shape (0: not available)
 cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x, float2* y, const double* escale,
-                              const int* stop, cudaStream_t st, int bps);
+                              const int* stop, cudaStream_t st, int q);
 cudaError_t apply_bulk_take_error(cudaStream_t st, int* err);
 cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
                               int64_t vstride, const double* escale, cudaStream_t st);

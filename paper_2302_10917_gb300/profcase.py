@@ -49,7 +49,7 @@ def main(argv=None):
     ap.add_argument("--orth", type=int, default=1, help="0: CGS2, 1: single-projection Gram-Schmidt")
     ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner before the solve")
     ap.add_argument("--bulk", type=int, default=0,
-                    help="split-FP32 operator in the pipelined bulk-copy shape with this many CTAs per SM "
+                    help="split-FP32 operator in the pipelined bulk-copy shape with this many warps per edge "
                          "(after --autotune); without --step also times it against the default shape")
     ap.add_argument("--levels", action="store_true", help="the banded-level mesh (see the module docstring)")
     ap.add_argument("--nrhs", type=int, default=1, help="columns of the level-mesh applies")
@@ -89,7 +89,7 @@ def main(argv=None):
     if a.bulk > 0:
         xs = torch.stack([x.float(), (x - x.float().double()).float()], dim=1).contiguous()
         for name, bulk in (("default", 0), ("bulk", a.bulk)):
-            pr.set_apply_shape(2, bulk_ctas_per_sm=bulk)
+            pr.set_apply_shape(2, bulk_warps=bulk)
             pr.apply(xs, precond=True, prec=49)
             e0, e1 = ev(), ev()
             e0.record()
@@ -123,7 +123,7 @@ def _step(pr, f, a):
     if a.autotune:
         pr.autotune(mode=a.mode, restart=a.restart)
     if a.bulk > 0:
-        pr.set_apply_shape(2, bulk_ctas_per_sm=a.bulk)
+        pr.set_apply_shape(2, bulk_warps=a.bulk)
     x, rep, st = pr.solve(g, tol=1e-14, restart=a.restart, maxit=a.restart, mode=a.mode, check=False, orth=a.orth)
     t[2].record()
     u, q = pr.recover(x)
