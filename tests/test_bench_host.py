@@ -1,0 +1,55 @@
+"""Host logic of bench.py that decides whether a measurement stands: the clock
+summary taken from nvidia-smi rows sampled during the timed region (a run that
+saw a hardware or thermal slowdown is rejected; a power cap is kept and noted),
+and the measured-peaks file the roofline fractions divide by. CPU only."""
+import json
+import os
+
+import bench
+
+ROW = "0, {sm}, 2070, {pw}, 0x{mask}, {hw}, {hwt}, {swt}, {pc}"
+
+
+def row(sm=2070, pw=900.0, hw="Not Active", hwt="Not Active", swt="Not Active", pc="Not Active", mask="0"):
+    return ROW.format(sm=sm, pw=pw, hw=hw, hwt=hwt, swt=swt, pc=pc, mask=mask) + "\n"
+
+
+def test_clean_run_median_and_maxima():
+    lines = [row(sm=v, pw=p) for v, p in ((2070, 800.0), (2055, 950.5), (1980, 1010.0), (2070, 700.0), (2040, 990.0))]
+    s = bench.summarize_clock_lines(lines)
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == [] and s["samples"] == 5 and s["power_w_max"] == 1010.0
+
+
+def test_each_throttle_reason_is_reported():
+    kinds = {"hw": "hw_slowdown", "hwt": "hw_thermal_slowdown", "swt": "sw_thermal_slowdown", "pc": "sw_power_cap"}
+    for key, name in kinds.items():
+        lines = [row(), row(**{key: "Active"}), row()]
+        assert bench.summarize_clock_lines(lines)["reasons"] == [name], key
+    both = [row(hw="Active"), row(pc="Active")]
+    assert bench.summarize_clock_lines(both)["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_not_active_is_not_a_reason_and_bad_rows_are_skipped():
+    lines = ["index, clocks.current.sm [MHz], ...\n", row(), "0, 2070, 20\n", "0, [N/A], 2070, 900, 0x0, a, b, c, d\n",
+             "0, 1500, [N/A], 900, 0x0, Active, b, c, d\n", row(sm=2000)]
+    s = bench.summarize_clock_lines(lines)
+    assert s["samples"] == 2 and s["reasons"] == [] and s["sm_mhz"] == 2035
+
+
+def test_no_samples():
+    assert bench.summarize_clock_lines([])["reasons"] == ["no samples"]
+    assert bench.summarize_clock_lines(["garbage\n"])["sm_mhz"] is None
+
+
+def test_measured_peaks_file(tmp_path, monkeypatch):
+    path = tmp_path / "peaks.json"
+    path.write_text(json.dumps({"hbm_gbs": 6753.8, "bf16_tflops": 1923.9}))
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(path))
+    assert bench.measured_peaks()["hbm_gbs"] == 6753.8
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "absent.json"))
+    assert bench.measured_peaks() == {}
+    path.write_text("{not json")
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(path))
+    assert bench.measured_peaks() == {}
+    assert os.path.exists(path)
