@@ -129,13 +129,18 @@ class ClockSampler:
 def summarize_clock_lines(lines):
     """Median SM clock, maximum clock and power, and the throttle reasons seen, from
     `nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,noheader,nounits` rows;
-    malformed rows (a header, an interrupted last line) are skipped."""
+    short rows (a header, an interrupted last line) are skipped, and a row whose
+    clocks do not parse still contributes its throttle reasons."""
     sm, smax, reasons, power = [], [], set(), []
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     for line in lines:
         parts = [p.strip() for p in line.split(",")]
         if len(parts) < 9:
             continue
+        # a throttle reason counts on every complete row, the clocks only where all three parse
+        for name, val in zip(names, parts[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
         try:
             vals = float(parts[1]), float(parts[2]), float(parts[3])
         except ValueError:
@@ -143,11 +148,8 @@ def summarize_clock_lines(lines):
         sm.append(vals[0])
         smax.append(vals[1])
         power.append(vals[2])
-        for name, val in zip(names, parts[5:9]):
-            if val.lower().startswith("active"):
-                reasons.add(name)
     if not sm:
-        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"] + sorted(reasons)}
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
             "samples": len(sm), "power_w_max": max(power) if power else None}
 

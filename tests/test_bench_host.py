@@ -32,9 +32,17 @@ def test_each_throttle_reason_is_reported():
 
 def test_not_active_is_not_a_reason_and_bad_rows_are_skipped():
     lines = ["index, clocks.current.sm [MHz], ...\n", row(), "0, 2070, 20\n", "0, [N/A], 2070, 900, 0x0, a, b, c, d\n",
-             "0, 1500, [N/A], 900, 0x0, Active, b, c, d\n", row(sm=2000)]
+             row(sm=2000)]
     s = bench.summarize_clock_lines(lines)
     assert s["samples"] == 2 and s["reasons"] == [] and s["sm_mhz"] == 2035
+
+
+def test_a_row_without_clocks_still_reports_its_throttle_reason():
+    lines = [row(), "0, 1500, [N/A], 900, 0x0, Active, Not Active, Not Active, Not Active\n", row(sm=2000)]
+    s = bench.summarize_clock_lines(lines)
+    assert s["samples"] == 2 and s["sm_mhz"] == 2035 and s["reasons"] == ["hw_slowdown"]
+    only = bench.summarize_clock_lines(["0, [N/A], [N/A], [N/A], 0x0, Not Active, Active, Not Active, Not Active\n"])
+    assert only["sm_mhz"] is None and only["reasons"] == ["no samples", "hw_thermal_slowdown"]
 
 
 def test_no_samples():
