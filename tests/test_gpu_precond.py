@@ -14,6 +14,7 @@ import torch
 
 from oracle.hdg import HDGProblem
 from oracle.levels import LevelHDGProblem
+from oracle.precond import face_block_inverse
 from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -28,14 +29,6 @@ def rel(a, b):
 def _need_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-
-
-def face_block_inverse(S, eoff):
-    out = np.zeros_like(S)
-    for f in range(len(eoff) - 1):
-        sl = slice(eoff[f], eoff[f + 1])
-        out[sl, sl] = np.linalg.inv(S[sl, sl])
-    return out
 
 
 B1 = (50.0 * math.cos(0.3), 50.0 * math.sin(0.3))
