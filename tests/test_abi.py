@@ -65,3 +65,31 @@ def test_argument_validation_without_gpu(lib):
     assert lib.hdg_create(None, None, ctypes.byref(h)) == HDG_ERR_ARG
     assert lib.hdg_last_error(None) == b"null context"
     lib.hdg_destroy(None)
+
+
+def _null_args(fn):
+    args = []
+    for t in fn.argtypes or []:
+        if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint, ctypes.c_size_t, ctypes.c_long):
+            args.append(0)
+        elif t in (ctypes.c_double, ctypes.c_float):
+            args.append(0.0)
+        else:
+            args.append(None)
+    return args
+
+
+def test_every_entry_point_refuses_a_null_context(lib):
+    """Each call that takes a context returns HDG_ERR_ARG for NULL (and NULL
+    arguments) before any device work: no crash, no CUDA call."""
+    from paper_2302_10917_gb300 import EXPORTED, HDG_ERR_ARG
+    skip = {"hdg_create", "hdg_last_error", "hdg_destroy"}
+    checked = 0
+    for name in EXPORTED:
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        assert fn.argtypes, name
+        assert fn(*_null_args(fn)) == HDG_ERR_ARG, name
+        checked += 1
+    assert checked == len(EXPORTED) - len(skip)
