@@ -61,3 +61,41 @@ def test_measured_peaks_file(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PEAKS_FILE", str(path))
     assert bench.measured_peaks() == {}
     assert os.path.exists(path)
+
+
+def _run_reference(env_extra):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        if k not in env_extra:
+            env.pop(k, None)
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    return res
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm (the oracle timed on the host cores) prints exactly one JSON
+    line with the contract's keys; its ratio inputs are the same metric and unit."""
+    res = _run_reference({})
+    assert res.returncode == 0, res.stderr[-500:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GDoF/s"
+    for key in ("value", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling", "vs_baseline",
+                "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["config"]["workload"].startswith(bench.WORKLOAD)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    res = _run_reference({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
+    assert res.returncode == 0, res.stderr[-500:]
+    assert not [ln for ln in res.stdout.splitlines() if ln.strip().startswith("{")]
