@@ -85,6 +85,14 @@ def grf_kappa(n, seed, std=0.5, ell=0.1, features=1024):
     g = np.random.default_rng([MASTER_SEED, 43, int(seed)])
     w = g.standard_normal((features, 2)) / ell
     phi = g.uniform(0.0, 2.0 * np.pi, features)
+    c = element_centroids(n)
+    field = std * np.sqrt(2.0 / features) * np.cos(c @ w.T + phi[None, :]).sum(axis=1)
+    return np.exp(field)
+
+
+def element_centroids(n):
+    """Centroids [2 n^2, 2] of the macro-triangles of the n x n "/"-split unit square,
+    element order e = 2 (j n + i) + t."""
     h = 1.0 / n
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
     i, j = i.ravel(), j.ravel()          # square index j n + i
@@ -94,17 +102,21 @@ def grf_kappa(n, seed, std=0.5, ell=0.1, features=1024):
     c[0::2, 1] = (j + 1.0 / 3.0) * h
     c[1::2, 0] = (i + 1.0 / 3.0) * h
     c[1::2, 1] = (j + 2.0 / 3.0) * h
-    field = std * np.sqrt(2.0 / features) * np.cos(c @ w.T + phi[None, :]).sum(axis=1)
-    return np.exp(field)
+    return c
 
 
 def gaussian_bumps(xy, count, seed, width=0.05):
     """count sources f_k(x) = exp(-|x - c_k|^2 / (2 width^2)) with seeded centres
     c_k ~ U[0, 1]^2, evaluated at points xy[..., 2]: [count, *xy.shape[:-1]]."""
-    g = np.random.default_rng([MASTER_SEED, 59, int(seed)])
-    c = torch.from_numpy(g.uniform(0.0, 1.0, (count, 2))).to(xy.device, xy.dtype)
+    c = torch.from_numpy(bump_centres(count, seed)).to(xy.device, xy.dtype)
     d2 = ((xy.unsqueeze(0) - c.view(count, *([1] * (xy.dim() - 1)), 2)) ** 2).sum(-1)
     return torch.exp(-d2 / (2.0 * width * width))
+
+
+def bump_centres(count, seed):
+    """The seeded centres c_k ~ U[0, 1]^2 of gaussian_bumps: [count, 2]."""
+    g = np.random.default_rng([MASTER_SEED, 59, int(seed)])
+    return g.uniform(0.0, 1.0, (count, 2))
 
 
 def random_vector(n, seed):
