@@ -93,3 +93,21 @@ def test_every_entry_point_refuses_a_null_context(lib):
         assert fn(*_null_args(fn)) == HDG_ERR_ARG, name
         checked += 1
     assert checked == len(EXPORTED) - len(skip)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library the package raises instead of computing."""
+    import paper_2302_10917_gb300 as pkg
+    monkeypatch.setattr(pkg, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        pkg.load_library(str(tmp_path / "libmehdg.so"))
+
+
+def test_no_cpu_path_without_a_gpu():
+    """On a machine without a CUDA device a problem cannot be created (there is no CPU route)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2302_10917_gb300 import Problem
+    with pytest.raises(RuntimeError):
+        Problem(2, 2, 2)
