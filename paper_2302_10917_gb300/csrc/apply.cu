@@ -14,7 +14,11 @@
 // One thread per (interior edge, trace position); a CTA covers EPB whole
 // edges, stages the two element trace vectors of each edge in shared memory
 // (gathered with orientation flips, Dirichlet edges contribute 0) and streams
-// the matching row-blocks S[e][k][j][t] (contiguous in t) from HBM.
+// the matching row-blocks S[e][k][j][t] (contiguous in t) from HBM. The
+// split-FP32 operator also has a pipelined form further down
+// (apply_bulk_kernel: bulk asynchronous copies of the row-blocks into shared
+// memory, consumed by warps), which the launch-shape autotuner times beside
+// this one.
 #include "internal.h"
 #include "df64.h"
 #include <type_traits>
