@@ -262,13 +262,16 @@ hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
  * timeout flag (HDG_ERR_TIMEOUT if a bounded wait gave up). */
 hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int prec, int precond);
 
-/* Sets the launch shape of the trace-operator apply inside hdg_solve for one
+/* Launch-shape override (no counterpart in the paper; project-written).
+ * Sets the launch shape of the trace-operator apply inside hdg_solve for one
  * mode (0 FP64, 1 FP32 + refinement, 2 split-FP32), as hdg_autotune would:
  * edges_per_block > 0 (with edges_per_block (m p + 1) <= 512) for the
  * one-thread-per-row apply, or bulk_warps = 1 .. 3 (mode 2 only) for the
  * pipelined apply with that many consumer warps per edge; both 0 restores
- * the default. Uniform meshes only; HDG_ERR_ARG for a shape that does not
- * apply. */
+ * the default. The shape stays in the context until set again or replaced by
+ * hdg_autotune; it applies from the next hdg_solve (and hdg_apply prec = 49).
+ * Any state after hdg_create; no device work. Uniform meshes only;
+ * HDG_ERR_ARG for a shape that does not apply (the context is unchanged). */
 hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_warps);
 
 /* Solve S x = g (Eq. global_problem) with restarted GMRES, left-
