@@ -270,7 +270,8 @@ hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int
  * pipelined apply with that many consumer warps per edge; both 0 restores
  * the default. The shape stays in the context until set again or replaced by
  * hdg_autotune; it applies from the next hdg_solve (and hdg_apply prec = 49).
- * Any state after hdg_create; no device work. Uniform meshes only;
+ * Any state after hdg_create; no launch or copy (a pipelined shape queries
+ * the device limits once). Uniform meshes only;
  * HDG_ERR_ARG for a shape that does not apply (the context is unchanged). */
 hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_warps);
 
