@@ -40,6 +40,8 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 # capture at n = 64, m = 8, p = 3 (376.57 MB for 12 160 edges, 128-thread blocks); the traffic
 # scales with the edges. Only valid for that kernel and element (m = 8, p = 3).
 APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.57e6 / 12160
+# the same for apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors); None until captured
+APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3 = None
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
@@ -54,15 +56,24 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="n128_m8_p3")
     ap.add_argument("--restart", type=int, default=80)
-    ap.add_argument("--mode", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2],
                     help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
-    ap.add_argument("--orth", type=int, default=1, choices=[0, 1],
-                    help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes)")
-    ap.add_argument("--no-split", action="store_true", help="FP64 panel updates in the condensation")
+    ap.add_argument("--basis", type=int, default=0, choices=[0, 1],
+                    help="Krylov basis and orthogonalisation: 0 FP64, 1 split FP32")
+    ap.add_argument("--orth", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes), "
+                         "2 CGS with a second projection where more than half of the vector lay in the basis, "
+                         "3 the same where the single projection cancelled more than six digits")
+    ap.add_argument("--split", action="store_true",
+                    help="split-FP32 elimination in the condensation (default: FP64 local factorisations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the many-source and gradient measurements that follow the main line")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the whole-step comparison of the precision forms and preconditioners")
+    ap.add_argument("--n", type=int, default=0,
+                    help="macro squares per side instead of the workload's (small cases for profiler captures)")
     return ap.parse_args(argv)
 
 
@@ -278,6 +289,11 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------- ours
 MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64"}
+# precision forms of one step: (Arnoldi operator mode, Krylov basis, split-FP32 elimination)
+FORMS = {"fp64": (0, 0, False), "fp32_ir": (1, 0, False), "df64": (2, 1, True)}
+FORM_DTYPES = {(0, 0, False): "f64",
+               (1, 0, False): "f32 blocks (FP32 operator) + f64 factorisation, orthogonalisation and refinement",
+               (2, 1, True): "df64 (f32x2) elimination, blocks and Krylov basis + f64 residual"}
 
 
 def run_ours(args):
@@ -291,7 +307,9 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_2302_10917_gb300 import Problem
     from paper_2302_10917_gb300 import workloads as wl
-    cfg = wl.CONFIGS[args.config]
+    cfg = dict(wl.CONFIGS[args.config])
+    if args.n > 0:
+        cfg["n"] = args.n
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
     pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], device=dev, stream=stream)
@@ -300,18 +318,22 @@ def run_ours(args):
     f = wl.sin_sin_source(xy, cfg["kappa"], cfg["beta"]).contiguous()
     del xy
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    split = not args.no_split
+    split = args.split
 
-    def step(rec=None, mode=args.mode):
+    def condense_flags(mode, split_update):
+        # only the blocks the solve mode needs
+        return dict(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split_update)
+
+    def step(rec=None, mode=args.mode, basis=args.basis, split_update=split, precond="d"):
         marks = [ev() for _ in range(4)] if rec is not None else None
         if marks:
             marks[0].record(stream)
         pr.set_source(f)
-        pr.condense(keep_factors=True, store_fp32=True, store_df64=True, split_update=split)
+        pr.condense(precond=precond, **condense_flags(mode, split_update))
         g = pr.rhs()
         if marks:
             marks[1].record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth, basis=basis)
         if st != 0:
             raise RuntimeError(f"solve did not converge: {rep}")
         if marks:
@@ -320,11 +342,11 @@ def run_ours(args):
         if marks:
             marks[3].record(stream)
             rec.append((marks, rep))
-        return rep
+        return rep, x, u, q
 
     # the project's launch-shape autotuner runs once per problem (outside the timed region)
     step()
-    tune = pr.autotune(mode=args.mode, restart=args.restart)
+    tune = pr.autotune(mode=args.mode, restart=args.restart, basis=args.basis)
     for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
@@ -368,12 +390,17 @@ def run_ours(args):
     apply_bytes = 8.0 * (2 * P1 * n_t * n_int + 2 * N_tr)        # blocks of both sides + x once + y once
     apply_flops = 4.0 * P1 * n_t * n_int
     cond_flops = N * sum(2.0 * (R - 1 - k) * (Cc - 1 - k) for k in range(Q))
+    fp64_ceiling = FP64_PEAK_TFLOPS * 1e12 / 2 * 8 / 1e9     # GB/s at one FP64 FMA per 8-byte entry
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    apply_kernels = {0: "apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors)",
+                     1: "apply_vdf_kernel<2,%d> (FP32 blocks)" % (1 - args.basis),
+                     2: "apply_vdf_kernel<1,%d> (split-FP32 blocks)" % (1 - args.basis)}
     rooflines = {
-        "apply": {"kernel": ({0: "apply_vdf_kernel<0> (FP64 blocks)", 1: "apply_vdf_kernel<2> (FP32 blocks)",
-                              2: "apply_vdf_kernel<1> (split-FP32 blocks)"}[args.mode] if not tune.get("apply_bulk")
+        "apply": {"kernel": (apply_kernels[args.mode] if not tune.get("apply_bulk")
                              else f"apply_bulk_kernel (split-FP32 blocks, bulk copies into shared-memory slots, "
                                   f"{tune['apply_bulk']} consumer warps per edge)"),
-                  "bound": "alu" if args.mode == 0 else "hbm",
+                  "bound": "hbm",
                   "launches": prof["apply32" if args.mode == 1 else "apply"][0],
                   "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},
         "condense": {"kernel": ("condense_df_kernel (split-FP32 formation + bordered LU + Schur)" if split
@@ -381,15 +408,17 @@ def run_ours(args):
                      "bound": "alu", "launches": prof["condense"][0], "avg_launch_ms": avg("condense")},
     }
     ra = rooflines["apply"]
-    if args.mode == 0:
-        ra.update(achieved=apply_flops / (ra["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                  algorithmic_per_launch=apply_flops)
-    else:
-        bpl = apply_bytes if args.mode == 2 else apply_bytes / 2
-        ra.update(achieved=bpl / (ra["avg_launch_ms"] / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6800.0),
-                  unit="GB/s", algorithmic_per_launch=bpl,
-                  peak_source="measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s")
+    # FP32 blocks move 4 bytes per entry; the vectors are 8 bytes per entry in either basis
+    bpl = apply_bytes - (4.0 * 2 * P1 * n_t * n_int if args.mode == 1 else 0.0)
+    ra.update(achieved=bpl / (ra["avg_launch_ms"] / 1e3) / 1e9, peak=hbm_peak, unit="GB/s",
+              algorithmic_per_launch=bpl, peak_source=hbm_src)
     ra["frac"] = ra["achieved"] / ra["peak"]
+    if args.mode == 0:
+        # FP64 blocks: one FP64 FMA per 8-byte entry; GB300's FP64 pipe caps this at fp64_ceiling
+        tf = apply_flops / (ra["avg_launch_ms"] / 1e3) / 1e12
+        ra["fp64_pipe"] = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+                           "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
+                           "hbm_frac_at_fp64_peak": fp64_ceiling / hbm_peak}
     rc = rooflines["condense"]
     if split:
         rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=DF_PEAK_TFLOPS, unit="TFLOP/s",
@@ -402,8 +431,8 @@ def run_ours(args):
                   peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)")
     rc["frac"] = rc["achieved"] / rc["peak"]
     # Krylov vector passes: algorithmic bytes of every Arnoldi step of the timed solves
-    # (CGS: multi-dot over nv + 1 vectors, update reading nv + 1 and writing 1;
-    #  CGS2: two multi-dots and two updates)
+    # (CGS: multi-dot over nv + 1 vectors, update reading nv + 1 and writing 1; CGS2 (and the
+    #  second projection of orth = 2, counted as not taken): two multi-dots and two updates)
     K = args.restart
     steps_bytes = 0.0
     for r in reps:
@@ -412,32 +441,41 @@ def run_ours(args):
             jused = min(K, its - ci * K)
             for j in range(max(jused, 0)):
                 nv = j + 1
-                steps_bytes += ((2 * nv + 3) if args.orth == 1 else (4 * nv + 6)) * 8.0 * N_tr
-    rooflines["ortho"] = {"kernel": "df_mdot_kernel + df_update_kernel (+ reduce2_givens_kernel)",
+                steps_bytes += ((4 * nv + 6) if args.orth == 0 else (2 * nv + 3)) * 8.0 * N_tr
+    vk = "d_mdot_kernel + d_update_kernel" if args.basis == 0 else "df_mdot_kernel + df_update_kernel"
+    rooflines["ortho"] = {"kernel": vk + " (+ reduce2_givens_kernel)",
                           "bound": "hbm", "launches": prof["ortho"][0], "avg_launch_ms": avg("ortho"),
                           "achieved": steps_bytes / (prof["ortho"][1] / 1e3) / 1e9 if prof["ortho"][1] else 0.0,
-                          "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                          "peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src,
                           "algorithmic_total": steps_bytes,
                           "note": "per Arnoldi step (launches = steps), all passes of that step"}
     rooflines["ortho"]["frac"] = rooflines["ortho"]["achieved"] / rooflines["ortho"]["peak"]
+    if args.basis == 0:
+        rooflines["ortho"]["fp64_pipe_ceiling_frac_of_hbm"] = fp64_ceiling / hbm_peak
     dom = max(("apply", "condense", "ortho"), key=lambda kname: prof["apply32" if (kname == "apply" and args.mode == 1)
                                                            else kname][1])
     roof = dict(rooflines[dom])
     roof["traffic"] = None
-    if dom == "apply" and args.mode == 2 and (cfg["m"], cfg["p"]) == (8, 3) and not tune.get("apply_bulk"):
-        roof["traffic"] = APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 * n_int
+    traffic_per_edge = {(0, 0): APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3}
+    if dom == "apply" and (cfg["m"], cfg["p"]) == (8, 3) and (args.mode, args.basis) in traffic_per_edge \
+            and not tune.get("apply_bulk") and traffic_per_edge[(args.mode, args.basis)]:
+        roof["traffic"] = traffic_per_edge[(args.mode, args.basis)] * n_int
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 64, scaled by interior edges"
     roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
+    all_fp64 = args.mode == 0 and args.basis == 0 and not split
+    dtype = "f64" if all_fp64 else FORM_DTYPES.get((args.mode, args.basis, split), "mixed")
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {0: "f64", 1: "f32 operator + f64 refinement", 2: "df64 (f32x2) operator + f64 residual"}[args.mode],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("GMRES(restart)", f"GMRES({args.restart})"),
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("GMRES(restart)", f"GMRES({args.restart})").replace(
+                           "128x128 macro grid (32768", f"{cfg['n']}x{cfg['n']} macro grid ({N}"),
                        "N_tr": N_tr, "macro_elements": N, "solve_mode": MODE_NAMES[args.mode],
-                       "orthogonalisation": ["CGS2", "CGS, Pythagorean norm"][args.orth],
-                       "lu_panel_updates": "split-FP32" if split else "FP64",
+                       "local_factorisation": "split-FP32" if split else "FP64",
+                       "krylov_basis": ["FP64", "split-FP32"][args.basis],
+                       "orthogonalisation": ["CGS2", "CGS, Pythagorean norm",
+                                             "CGS + second projection where ||w - V h||^2 < ||w||^2 / 2",
+                                             "CGS + second projection where ||w - V h||^2 < 1e-6 ||w||^2"][args.orth],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2: Schur blocks 1.47 GB, factors 42 GB, source 0.42 GB per replica"},
             "time_to_solve_s": statistics.median(solve_s), "condense_s": statistics.median(cond_s),
@@ -448,54 +486,76 @@ def run_ours(args):
             "roofline": roof, "roofline_other": roof_other, "gpu_launches": int(launches), "clocks": clk,
             "autotune": tune}
 
-    # the metric compares FP64 with FP32 + refinement: time-to-1e-10 of every solve mode
-    modes = {}
-    g = pr.rhs()
-    for mode in (0, 1, 2):
-        t0, t1 = ev(), ev()
+    # The metric compares FP64 with FP32 + refinement: the whole step of each precision form
+    # (condensation + rhs + GMRES to 1e-10 + back-solve), each with its own autotuned shapes,
+    # and each result's relative l2 distance from the all-FP64 step's x, u and q.
+    if not args.no_forms:
+        _, x64, u64, q64 = step(mode=0, basis=0, split_update=False)
         torch.cuda.synchronize()
-        t0.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth)
-        t1.record(stream)
+    forms = {}
+    for name, (mode, basis, spl) in ({} if args.no_forms else FORMS).items():
+        step(mode=mode, basis=basis, split_update=spl)
+        pr.autotune(mode=mode, restart=args.restart, basis=basis)
+        recf = []
+        for _ in range(2):
+            rep_f, xf, uf, qf = step(recf, mode=mode, basis=basis, split_update=spl)
         torch.cuda.synchronize()
-        modes[MODE_NAMES[mode]] = {"seconds": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
-                                   "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"])}
-    line["time_to_solve_by_mode"] = modes
+        cs = [m[0].elapsed_time(m[1]) / 1e3 for m, _ in recf]
+        ss = [m[1].elapsed_time(m[2]) / 1e3 for m, _ in recf]
+        rs = [m[2].elapsed_time(m[3]) / 1e3 for m, _ in recf]
+        dist = lambda a, b: float((a - b).norm() / b.norm())
+        forms[name] = {"dtype": FORM_DTYPES[(mode, basis, spl)],
+                       "step_s": statistics.median([c + s2 + r2 for c, s2, r2 in zip(cs, ss, rs)]),
+                       "condense_s": statistics.median(cs), "solve_s": statistics.median(ss),
+                       "recover_s": statistics.median(rs), "iterations": rep_f["iterations"],
+                       "rel_residual": rep_f["rel_residual"], "converged": bool(rep_f["converged"]),
+                       "rel_l2_vs_fp64_step": {"trace": dist(xf, x64), "u": dist(uf, u64), "q": dist(qf, q64)}}
+    if not args.no_forms:
+        pr.autotune(mode=args.mode, restart=args.restart, basis=args.basis)
+        del x64, u64, q64
+        line["forms"] = forms
 
     # the same solve with the preconditioner of the inverted diagonal face blocks of S
     pcs = {}
-    for pc in ("d", "face_schur"):
-        pr.condense(keep_factors=True, store_fp32=True, store_df64=True, split_update=split, precond=pc)
+    solve_kw = dict(tol=1e-10, restart=args.restart, maxit=60000, mode=args.mode, orth=args.orth, basis=args.basis)
+    for pc in () if args.no_forms else ("d", "face_schur"):
+        pr.condense(precond=pc, **condense_flags(args.mode, split))
         g = pr.rhs()
-        pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=args.mode, orth=args.orth)
+        pr.solve(g, **solve_kw)
         t0, t1, t2 = ev(), ev(), ev()
         torch.cuda.synchronize()
         t0.record(stream)
-        pr.condense(keep_factors=True, store_fp32=True, store_df64=True, split_update=split, precond=pc)
+        pr.condense(precond=pc, **condense_flags(args.mode, split))
         g = pr.rhs()
         t1.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=args.mode, orth=args.orth)
+        x, rep, st = pr.solve(g, **solve_kw)
         t2.record(stream)
         torch.cuda.synchronize()
         pcs[pc] = {"condense_s": t0.elapsed_time(t1) / 1e3, "solve_s": t1.elapsed_time(t2) / 1e3,
                    "iterations": rep["iterations"], "rel_residual": rep["rel_residual"],
                    "converged": bool(rep["converged"])}
     pcs["note"] = ("d: D_f^-1 of Sec. 6.1 (the timed step above); face_schur: the inverted diagonal face blocks "
-                   "of S folded into the same stored rows (same apply cost), solve mode " + MODE_NAMES[args.mode])
+                   "of S folded into the same stored rows (same apply cost), the timed step's precision form")
     line["time_to_solve_by_preconditioner"] = pcs
 
     if not args.no_e2e:
+        # the whole step through the public end-to-end call on pinned host buffers, median of 3 calls
         fh = f.cpu().pin_memory()
+        host_kw = dict(outputs=True, restart=args.restart, mode=args.mode, orth=args.orth, basis=args.basis)
         torch.cuda.synchronize()
-        pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode, orth=args.orth)    # warm-up
+        pr.run_host(fh, **host_kw)    # warm-up
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, u, q, rep = pr.run_host(fh, outputs=True, restart=args.restart, mode=args.mode, orth=args.orth)
-        e2e_s = time.perf_counter() - t0
+        calls = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            x, u, q, rep = pr.run_host(fh, **host_kw)
+            calls.append((time.perf_counter() - t0, rep))
+        e2e_s, rep = sorted(calls, key=lambda c: c[0])[1]
         app_e2e = rep["iterations"] + rep["outer"]
         eu, es = aggregate(N_tr * app_e2e, e2e_s, world)
         line["e2e"] = {"value": eu / es / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": int(fh.numel() * 8),
                        "d2h_bytes_per_step": int((x.numel() + u.numel() + q.numel()) * 8), "seconds": e2e_s,
+                       "calls": [round(c[0], 4) for c in calls], "statistic": "median of 3 calls",
                        "call": "hdg_run_host (pinned host f in; x, u, q out)"}
     pr.close()
     del f
@@ -533,7 +593,7 @@ def bench_multi_rhs(stream, count=64):
     pr.condense(keep_factors=True, store_df64=True, split_update=True)
     g = pr.rhs()
     b.record(stream)
-    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1, maxit=40000)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000)
     c2.record(stream)
     u, q = pr.recover(x)
     d.record(stream)
@@ -544,11 +604,11 @@ def bench_multi_rhs(stream, count=64):
     p1.set_source(f[0])
     p1.condense(keep_factors=True, store_df64=True, split_update=True)
     g1 = p1.rhs()
-    p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=1)
+    p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
     e0, e1 = ev(), ev()
     torch.cuda.synchronize()
     e0.record(stream)
-    x1, rep1, st1 = p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=1)
+    x1, rep1, st1 = p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
     e1.record(stream)
     torch.cuda.synchronize()
     single_s = e0.elapsed_time(e1) / 1e3
@@ -593,7 +653,7 @@ def bench_levels_many_source(stream, count=64):
     pr.condense(**flags)
     g = pr.rhs()
     b.record(stream)
-    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1, maxit=40000)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000)
     c2.record(stream)
     u, q = pr.recover(x)
     d.record(stream)
@@ -661,12 +721,14 @@ def bench_levels_many_source(stream, count=64):
 
 
 def bench_mixed_precision_n256(stream):
-    """The large workload's element at n = 256 (131 072 macro-elements, N_tr = 4 902 400):
-    one condensation (split-FP32 elimination, FP64-accurate blocks; FP32 and split-FP32
-    copies of the preconditioned blocks), then the solve to 1e-10 with the FP64 operator,
-    the FP32 operator inside FP64 residual replacement and the split-FP32 operator (face-block
-    preconditioner), and the reduced-precision solutions' relative l2 differences from the
-    FP64 one (trace, u, q)."""
+    """The large workload's element at n = 256 (131 072 macro-elements, N_tr = 4 902 400),
+    face-block preconditioner, GMRES(80) to 1e-10, in the three precision forms: all-FP64
+    (FP64 elimination, blocks, operator, Krylov basis); FP32+IR (the same FP64 elimination,
+    the preconditioned blocks stored and applied in FP32 inside FP64 residual replacement, FP64
+    basis and orthogonalisation); split-FP32 (split-FP32 elimination, blocks and basis). Each
+    form's solution (trace, u, q) against the all-FP64 one (relative l2), and u against the
+    manufactured solution at the lattice nodes."""
+    import math
     import torch
     from paper_2302_10917_gb300 import Problem
     from paper_2302_10917_gb300 import workloads as wl
@@ -674,33 +736,41 @@ def bench_mixed_precision_n256(stream):
     pr = Problem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"], stream=stream)
     pr.set_source(wl.sin_sin_source(pr.quad_points(), cfg["kappa"], cfg["beta"]).contiguous())
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    a, b = ev(), ev()
-    torch.cuda.synchronize()
-    a.record(stream)
-    # factors not kept (131 072 local systems would take 169 GB): chunked condensation, the
-    # back-solve condenses each chunk again
-    pr.condense(keep_factors=False, store_fp32=True, store_df64=True, split_update=True, precond="face_schur")
-    b.record(stream)
-    torch.cuda.synchronize()
-    g = pr.rhs()
-    sols, out = {}, {"workload": f"n={cfg['n']} m={cfg['m']} p={cfg['p']} beta=50(cos 0.3, sin 0.3) kappa=1, "
-                                 "u = sin(pi x) sin(pi y); face-block preconditioner, GMRES(80), CGS",
-                     "N_tr": pr.info["N_tr"], "condense_s": a.elapsed_time(b) / 1e3, "modes": {}}
-    for mode in (0, 1, 2):
+    xy = _lattice_nodes(cfg["n"], cfg["m"], cfg["p"], "cuda")
+    u_ex = torch.sin(math.pi * xy[..., 0]) * torch.sin(math.pi * xy[..., 1])
+    del xy
+    out = {"workload": f"n={cfg['n']} m={cfg['m']} p={cfg['p']} beta=50(cos 0.3, sin 0.3) kappa=1, "
+                       "u = sin(pi x) sin(pi y); face-block preconditioner, GMRES(80), orth 2",
+           "N_tr": pr.info["N_tr"], "forms": {}}
+    sols = {}
+    for name, (mode, basis, spl) in FORMS.items():
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        # factors not kept (131 072 local systems would take 169 GB): chunked condensation, the
+        # back-solve condenses each chunk again
+        pr.condense(keep_factors=False, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=spl,
+                    precond="face_schur")
+        b.record(stream)
+        g = pr.rhs()
+        pr.autotune(mode=mode, restart=80, basis=basis)
         t0, t1 = ev(), ev()
         torch.cuda.synchronize()
         t0.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=80, maxit=60000, mode=mode, orth=1)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, maxit=60000, mode=mode, orth=2, basis=basis)
         t1.record(stream)
         torch.cuda.synchronize()
         u, q = pr.recover(x)
-        sols[mode] = (x, u, q)
-        out["modes"][MODE_NAMES[mode]] = {"seconds": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
-                                          "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"])}
+        sols[name] = (x, u, q)
+        out["forms"][name] = {"dtype": FORM_DTYPES[(mode, basis, spl)], "condense_s": a.elapsed_time(b) / 1e3,
+                              "solve_s": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
+                              "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"]),
+                              "max_nodal_error_u": float((u - u_ex).abs().max())}
     rel = lambda a, b: float((a - b).norm() / b.norm())
-    for mode in (1, 2):
-        out["modes"][MODE_NAMES[mode]]["rel_l2_vs_fp64"] = {
-            name: rel(sols[mode][k], sols[0][k]) for k, name in enumerate(("trace", "u", "q"))}
+    for name in sols:
+        if name != "fp64":
+            out["forms"][name]["rel_l2_vs_fp64"] = {
+                k: rel(sols[name][i], sols["fp64"][i]) for i, k in enumerate(("trace", "u", "q"))}
     pr.close()
     return out
 
@@ -741,7 +811,7 @@ def bench_macro_vs_standard(stream):
         pr.set_source(f)
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
         g = pr.rhs()
-        pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1)      # warm-up (graph capture)
+        pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1)      # warm-up (graph capture)
         a, b, c2 = ev(), ev(), ev()
         torch.cuda.synchronize()
         a.record(stream)
@@ -749,7 +819,7 @@ def bench_macro_vs_standard(stream):
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
         g = pr.rhs()
         b.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=1)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
         c2.record(stream)
         u, q = pr.recover(x)
         torch.cuda.synchronize()
@@ -780,7 +850,7 @@ def bench_supg_layer(stream):
         gD = wl.tanh_layer_exact(pr.bnd_quad_points(), kap).contiguous()
         pr.set_source(f, gD)
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
-        x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, mode=2, orth=1, maxit=40000, check=False)
+        x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000, check=False)
         u, q = pr.recover(x)
         out["supg" if supg else "plain"] = {"u_min": float(u.min()), "u_max": float(u.max()),
                                             "overshoot": float(max(u.max() - 1.0, -u.min(), 0.0)),
@@ -803,7 +873,7 @@ def bench_gradient(stream):
     kobs = torch.from_numpy(wl.grf_kappa(n, 1001)).cuda()
     pr = Problem(n, m, p, beta=beta, kappa=kap.cpu().numpy(), stream=stream)
     f = wl.sin_sin_source(pr.quad_points(), 1.0, beta).contiguous()
-    opts = dict(tol=1e-10, restart=128, mode=2, split_update=True, orth=1, precond="face_schur", maxit=60000)
+    opts = dict(tol=1e-10, restart=128, mode=2, split_update=True, orth=2, basis=1, precond="face_schur", maxit=60000)
     with torch.no_grad():
         u_obs = solve_u(pr, kobs, f, **opts).clone()      # also the warm-up (graph capture)
     times = []

@@ -145,12 +145,18 @@ typedef struct {
 } hdg_info_t;
 
 /* Solve options. Every restart cycle starts from the true FP64 residual
- * g - S x (the stopping test) and builds the Krylov basis in split-FP32
- * ("double-float", 48-bit significand) arithmetic; mode selects the
- * preconditioned Arnoldi operator: 0 = FP64 blocks, FP64 arithmetic;
- * 1 = FP32 blocks (requires HDG_STORE_FP32), i.e. FP32 inside FP64 iterative
- * refinement; 2 = split-FP32 blocks on the FP32 pipe (requires
- * HDG_STORE_DF64). */
+ * g - S x (the stopping test). mode selects the preconditioned Arnoldi
+ * operator: 0 = FP64 blocks, FP64 arithmetic; 1 = FP32 blocks (requires
+ * HDG_STORE_FP32), i.e. FP32 inside FP64 iterative refinement; 2 = split-FP32
+ * blocks on the FP32 pipe (requires HDG_STORE_DF64). basis selects the
+ * storage and arithmetic of the Krylov basis and its orthogonalisation:
+ * HDG_BASIS_FP64 (0, the default) = FP64 vectors, FP64 dot products and
+ * updates; HDG_BASIS_DF64 (1) = split-FP32 ("double-float", two FP32 words,
+ * 48-bit significand, FP32 exponent range) on the FP32 pipe. The pipelined
+ * apply shape (hdg_set_apply_shape bulk_warps) runs with HDG_BASIS_DF64 only;
+ * with FP64 vectors mode 2 uses the one-thread-per-row apply. */
+#define HDG_BASIS_FP64 0
+#define HDG_BASIS_DF64 1
 typedef struct {
   double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
   int maxit;             /* maximum number of operator applications inside GMRES */
@@ -162,7 +168,9 @@ typedef struct {
                             orthogonality faster, which the restart from the true residual bounds);
                             2 = as 1, with a second projection in the steps where ||w - V V^T w||^2 <
                             ||w||^2 / 2 (Kahan-Parlett "twice is enough"; decided on the device, two
-                            passes in the other steps) */
+                            passes in the other steps); 3 = as 2 with the second projection only where
+                            ||w - V V^T w||^2 < 1e-6 ||w||^2 (more than six digits cancelled) */
+  int basis;             /* HDG_BASIS_FP64 or HDG_BASIS_DF64 (see above) */
 } hdg_solve_opts;
 
 typedef struct {
@@ -259,7 +267,12 @@ hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
  * vectors (x and y [N_tr][2] FP32: entry i is x[i][0] + x[i][1]), with the
  * launch shape that solve uses (hdg_autotune's choice or hdg_set_apply_shape's);
  * with the pipelined shape it synchronises the stream to read that kernel's
- * timeout flag (HDG_ERR_TIMEOUT if a bounded wait gave up). */
+ * timeout flag (HDG_ERR_TIMEOUT if a bounded wait gave up).
+ * prec = 33 (nrhs = 1, or a level mesh; precond = 1, HDG_STORE_FP32): the
+ * FP32 blocks on FP64 vectors (x, y FP64; products and sums in FP32), the
+ * Arnoldi operator of mode 1 with HDG_BASIS_FP64.
+ * With FP64 vectors, prec = 64 and prec = 48 are the Arnoldi operators of
+ * modes 0 and 2 with HDG_BASIS_FP64 (same kernels, same bits). */
 hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int prec, int precond);
 
 /* Launch-shape override (no counterpart in the paper; project-written).
@@ -295,8 +308,9 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double*
 hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
 
 /* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to
- * the device, condenses (factors kept; for opts->mode 1 or 2 also the FP32
- * or split-FP32 blocks, with split-FP32 panel updates), assembles g, solves
+ * the device, condenses (factors kept; for opts->mode 1 also the FP32 blocks
+ * after FP64 elimination, for mode 2 the split-FP32 blocks after split-FP32
+ * elimination), assembles g, solves
  * from x = 0, recovers u and q and copies x, u, q back (each output may be
  * NULL to skip its copy). Synchronous. Same layouts as above. */
 hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_qp_host,

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmehdg.so")
 HDG_OK, HDG_ERR_ARG, HDG_ERR_STATE, HDG_ERR_CUDA, HDG_ERR_OOM = 0, 1, 2, 3, 4
 HDG_ERR_SINGULAR, HDG_ERR_NOCONV, HDG_ERR_TIMEOUT = 5, 6, 7
 HDG_STORE_FP32, HDG_KEEP_FACTORS, HDG_STORE_DF64, HDG_SPLIT_UPDATE, HDG_PRECOND_FACE_SCHUR = 1, 2, 4, 8, 16
+BASIS_FP64, BASIS_DF64 = 0, 1   # hdg_solve_opts.basis: FP64 or split-FP32 Krylov basis
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_CUDA", 4: "HDG_ERR_OOM",
                 5: "HDG_ERR_SINGULAR", 6: "HDG_ERR_NOCONV", 7: "HDG_ERR_TIMEOUT"}
 
@@ -53,7 +54,7 @@ OFF_SOURCE, OFF_DIRICHLET_POINTS, OFF_LATTICE, OFF_TRACE, OFF_SCHUR, OFF_DIRICHL
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
-                ("mode", ctypes.c_int), ("orth", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("orth", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -283,20 +284,21 @@ class Problem:
     def apply(self, x, precond=False, prec=64, out=None):
         """x: [N_tr] or [nrhs, N_tr] (multi-RHS apply); prec = 49: x [N_tr, 2] FP32 split pairs
         (the split-FP32 solve's own operator and launch shape), y likewise."""
-        dt = torch.float32 if prec in (32, 49) else torch.float64
+        dt = torch.float32 if prec in (32, 49) else torch.float64   # 64, 48, 33: FP64 vectors
         x = x.to(self.device, dt).contiguous()
         nrhs = 1 if x.dim() == 1 or prec == 49 else x.shape[0]
         y = out if out is not None else torch.empty_like(x)
         self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), nrhs, prec, 1 if precond else 0))
         return y
 
-    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0):
+    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0, basis=BASIS_FP64):
         """g: [N_tr], or [nrhs, N_tr] (independent systems solved in lockstep: one multi-RHS
-        apply and batched vector kernels per Arnoldi step; the report is the worst column's)."""
+        apply and batched vector kernels per Arnoldi step; the report is the worst column's).
+        basis: BASIS_FP64 (FP64 Krylov basis and orthogonalisation) or BASIS_DF64 (split-FP32)."""
         g = g.to(self.device, torch.float64).contiguous()
         nrhs = 1 if g.dim() == 1 else g.shape[0]
         x = torch.zeros_like(g) if x0 is None else x0.to(self.device, torch.float64).clone()
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth, basis=basis)
         r = SolveReport()
         st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), nrhs, ctypes.byref(o), ctypes.byref(r))
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
@@ -307,10 +309,10 @@ class Problem:
         """hdg_set_apply_shape: the apply's launch shape inside solves of this mode."""
         self._check(self.lib.hdg_set_apply_shape(self.h, mode, edges_per_block, bulk_warps))
 
-    def autotune(self, mode=0, restart=80):
+    def autotune(self, mode=0, restart=80, basis=BASIS_FP64):
         """hdg_autotune: time candidate launch shapes of the GMRES kernels for this mode and
         problem size, keep the fastest; returns the report as a dict."""
-        o = SolveOpts(tol=1e-10, maxit=1, restart=restart, mode=mode, orth=0)
+        o = SolveOpts(tol=1e-10, maxit=1, restart=restart, mode=mode, orth=0, basis=basis)
         r = TuneReport()
         self._check(self.lib.hdg_autotune(self.h, ctypes.byref(o), ctypes.byref(r)))
         return r.as_dict()
@@ -347,13 +349,14 @@ class Problem:
         library's fixed scratch array (no device allocation inside the call)."""
         self._check(self.lib.hdg_condense_static(self.h, e0, count, _ptr(S_out), _ptr(g_out)))
 
-    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True, mode=0, orth=0):
+    def run_host(self, f_host, gD_host=None, tol=1e-10, maxit=20000, restart=50, outputs=True, mode=0, orth=0,
+                 basis=BASIS_FP64):
         """End-to-end call on host (ideally pinned) tensors; returns (x, u, q, report)."""
         N, Q, N_tr = self.info["N"], self.info["Q"], self.info["N_tr"]
         x = torch.empty(N_tr, dtype=torch.float64, pin_memory=True) if outputs else None
         u = torch.empty(N, Q, dtype=torch.float64, pin_memory=True) if outputs else None
         q = torch.empty(N, 2, Q, dtype=torch.float64, pin_memory=True) if outputs else None
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth, basis=basis)
         r = SolveReport()
         st = self.lib.hdg_run_host(self.h, _ptr(f_host), _ptr(gD_host), ctypes.byref(o), _ptr(x), _ptr(u),
                                    _ptr(q), ctypes.byref(r))
@@ -392,13 +395,13 @@ class Problem:
         self._check(self.lib.hdg_gradient(self.h, *[_ptr(t) for t in args], _ptr(dk), _ptr(df)))
         return dk, df
 
-    def adjoint(self, r, x, u, tol=1e-10, maxit=20000, restart=80, mode=0, want_df=True, orth=0):
+    def adjoint(self, r, x, u, tol=1e-10, maxit=20000, restart=80, mode=0, want_df=True, orth=0, basis=BASIS_FP64):
         """dJ/dkappa [N] and dJ/df [N, n_qp] for dJ/du = r [N, Q], at the forward solution
         (x, u) of the current condensation (factors kept). Returns (dkappa, df, report)."""
         g = self.adjoint_rhs(r)
         self.transpose()
         try:
-            nu, rep, st = self.solve(g, tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth)
+            nu, rep, st = self.solve(g, tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth, basis=basis)
         finally:
             self.transpose()
         if st != HDG_OK:
@@ -428,15 +431,16 @@ class HDGSolve(torch.autograd.Function):
         opts = dict(opts or {})
         tol, restart, mode = opts.get("tol", 1e-10), opts.get("restart", 80), opts.get("mode", 0)
         split, orth = opts.get("split_update", False), opts.get("orth", 0)
-        precond = opts.get("precond", "d")
+        precond, basis = opts.get("precond", "d"), opts.get("basis", BASIS_FP64)
         kappa_d, f_d = kappa.detach(), f.detach()
         HDGSolve._prepare(problem, kappa_d, f_d, gD, mode, split, precond)
         x, rep, st = problem.solve(problem.rhs(), tol=tol, restart=restart, mode=mode,
-                                   maxit=opts.get("maxit", 20000), orth=orth)
+                                   maxit=opts.get("maxit", 20000), orth=orth, basis=basis)
         if st != HDG_OK:
             raise HDGError(st, f"forward solve did not converge: {rep}")
         u, _ = problem.recover(x)
-        ctx.problem, ctx.version, ctx.opts = problem, problem.version, (tol, restart, mode, split, orth, precond)
+        ctx.problem, ctx.version = problem, problem.version
+        ctx.opts = (tol, restart, mode, split, orth, precond, basis)
         ctx.gD = gD
         ctx.save_for_backward(x, u, kappa_d, f_d)
         return u
@@ -445,11 +449,11 @@ class HDGSolve(torch.autograd.Function):
     def backward(ctx, grad_u):
         pr = ctx.problem
         x, u, kappa, f = ctx.saved_tensors
-        tol, restart, mode, split, orth, precond = ctx.opts
+        tol, restart, mode, split, orth, precond, basis = ctx.opts
         if pr.version != ctx.version:
             HDGSolve._prepare(pr, kappa, f, ctx.gD, mode, split, precond)
         dk, df, _ = pr.adjoint(grad_u, x, u, tol=tol, restart=restart, mode=mode,
-                               want_df=ctx.needs_input_grad[1], orth=orth)
+                               want_df=ctx.needs_input_grad[1], orth=orth, basis=basis)
         return (dk if ctx.needs_input_grad[0] else None), df, None, None, None
 
 

@@ -543,11 +543,12 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     } else if (prec == 48) {
       if (!L.d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
       e = launch_level_apply(c, 1, 0, L.d_Stdf, x, y, nrhs, n, precond_scale(c), nullptr, c->stream);
-    } else if (prec == 32) {
+    } else if (prec == 32 || prec == 33) {
       if (!L.d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
-      e = launch_level_apply(c, 2, 2, L.d_St32, x, y, nrhs, n, precond_scale(c), nullptr, c->stream);
+      const int vt = prec == 32 ? 2 : 0;
+      e = launch_level_apply(c, 2, vt, L.d_St32, x, y, nrhs, n, precond_scale(c), nullptr, c->stream);
     } else {
-      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
+      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48, 33 or 32");
     }
     c->launches += 2;
     return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
@@ -565,7 +566,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
       if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
       e = launch_apply_mrhs(2, 2, P, c->d_St32, x, y, nrhs, P.N_tr, precond_scale(c), c->stream);
     } else {
-      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
+      return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32 for several columns");
     }
     c->launches += 1;
     return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply (multi-RHS)");
@@ -576,11 +577,15 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   } else if (prec == 48) {
     if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
     e = launch_apply_df(c->prm, c->d_Stdf, (const double*)x, (double*)y, precond_scale(c), nullptr, c->stream);
+  } else if (prec == 33) {
+    // FP32 blocks on FP64 vectors: the Arnoldi operator of mode 1 with the FP64 basis
+    if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
+    e = launch_apply_vdf(2, c->prm, c->d_St32, x, y, precond_scale(c), nullptr, c->stream, 0, 0);
   } else if (prec == 32) {
     if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
     e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, precond_scale(c), nullptr, c->stream);
   } else {
-    return set_err(c, HDG_ERR_ARG, "prec must be 64, 48 or 32");
+    return set_err(c, HDG_ERR_ARG, "prec must be 64, 49, 48, 33 or 32");
   }
   c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
@@ -605,7 +610,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
-      o->orth < 0 || o->orth > 2)
+      o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_DF64)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
@@ -626,7 +631,8 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
   if (!c) return HDG_ERR_ARG;
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
-  if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2)
+  if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 || o->basis < HDG_BASIS_FP64 ||
+      o->basis > HDG_BASIS_DF64)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
@@ -727,8 +733,9 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
     cleanup();
     return cuda_err(c, e, "hdg_run_host upload");
   }
-  // the blocks the requested solve mode needs, split-FP32 panel updates for modes 1 and 2
-  const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? (HDG_STORE_FP32 | HDG_SPLIT_UPDATE) : 0u) |
+  // the blocks the requested solve mode needs; FP64 local factorisations except with the split-FP32
+  // operator (mode 2), whose condensation eliminates in split-FP32 arithmetic too
+  const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? HDG_STORE_FP32 : 0u) |
                           (o->mode == 2 ? (HDG_STORE_DF64 | HDG_SPLIT_UPDATE) : 0u);
   if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, cflags)) == HDG_OK &&
       (s = hdg_rhs(c, dgv)) == HDG_OK) {

@@ -92,87 +92,57 @@ __global__ void __launch_bounds__(256) apply_kernel(Params P, const T* __restric
   y[(size_t)f * P1 + s] = TX(r);
 }
 
-// ---------------------------------------------------------------------------
-// Split-FP32 ("double-float") variant. GB300 issues FP64 FMAs at 1/63 of the
-// FP32 rate, so the FP64 apply above is bound by the FP64 pipe, not by HBM.
-// Here each block entry is stored as an unevaluated sum hi + lo of two FP32
-// numbers (hi = fl32(s), lo = fl32(s - hi); 48 significant bits, same 8 bytes
-// per entry), x is split the same way on the fly, and every product is
+// Split-FP32 ("double-float") arithmetic: GB300 issues FP64 FMAs at 1/63 of
+// the FP32 rate, so the FP64 apply is bound by the FP64 pipe, not by HBM.
+// With split-FP32 blocks each entry is stored as an unevaluated sum hi + lo
+// of two FP32 numbers (hi = fl32(s), lo = fl32(s - hi); 48 significant bits,
+// same 8 bytes per entry), x is split the same way, and every product is
 // accumulated with error-free transformations (Dekker's product via FMA,
-// Knuth's two-sum) on the FP32 pipe; the two FP32 words are combined in FP64
-// once per output.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) apply_df_kernel(Params P, const float2* __restrict__ S,
-                                                       const double* __restrict__ x, double* __restrict__ y,
-                                                       const double* __restrict__ escale, int epb,
-                                                       const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  extern __shared__ unsigned char sraw[];
-  float2* xs = reinterpret_cast<float2*>(sraw);   // [epb][2][n_t] (hi, lo)
-  const int nt = P.n_t, P1 = P.P1, PP = P.P;
-  const int f0 = blockIdx.x * epb;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < epb * 2 * nt; idx += blockDim.x) {
-    const int le = idx / (2 * nt);
-    const int rem = idx - le * 2 * nt;
-    const int sd = rem / nt, c = rem - sd * nt;
-    const int f = f0 + le;
-    double v = 0.0;
-    if (f < P.n_int) {
-      int e[2], k[2], fl[2];
-      double len;
-      edge_sides(f, P.n, e, k, fl, &len);
-      int code[3], flip[3];
-      elem_edges(e[sd], P.n, code, flip);
-      const int kk = c / P1, t = c - kk * P1;
-      if (code[kk] >= 0) v = x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
-    }
-    const float hi = (float)v;
-    xs[idx] = make_float2(hi, (float)(v - (double)hi));
+// Knuth's two-sum) on the FP32 pipe.
+// Vector element types of the edge-centric apply below: VT = 0 FP64 vectors
+// (the FP64 Krylov basis), VT = 1 split-FP32 pairs (the split-FP32 basis).
+// A gathered entry is converted once to the block type's accumulation type
+// (BT = 0: double, 1: split pair, 2: float).
+template <int BT>
+struct VAcc;
+template <>
+struct VAcc<0> { using T = double; };
+template <>
+struct VAcc<1> { using T = float2; };
+template <>
+struct VAcc<2> { using T = float; };
+
+template <int BT, int VT>
+__device__ __forceinline__ typename VAcc<BT>::T vgather(const void* x, size_t i) {
+  if constexpr (VT == 0) {
+    const double v = static_cast<const double*>(x)[i];
+    if constexpr (BT == 0) return v;
+    else if constexpr (BT == 1) return df_from(v);
+    else return (float)v;
+  } else {
+    const float2 v = static_cast<const float2*>(x)[i];
+    if constexpr (BT == 0) return df_to(v);
+    else if constexpr (BT == 1) return v;
+    else return v.x;
   }
-  __syncthreads();
-  const int le = tid / P1, s = tid - le * P1;
-  const int f = f0 + le;
-  if (le >= epb || f >= P.n_int) return;
-  int e[2], k[2], fl[2];
-  double len;
-  edge_sides(f, P.n, e, k, fl, &len);
-  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll
-  for (int sd = 0; sd < 2; ++sd) {
-    const int t = fl[sd] ? PP - s : s;
-    const float2* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + t;
-    const float2* xv = xs + (le * 2 + sd) * nt;
-    int j = 0;
-    for (; j + 8 <= nt; j += 8) {
-      float2 sv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        df_fma(h0, l0, sv[u], xv[j + u]);
-        df_fma(h1, l1, sv[u + 1], xv[j + u + 1]);
-      }
-    }
-    for (; j < nt; ++j) {
-      df_fma(h0, l0, base[(size_t)j * P1], xv[j]);
-    }
-  }
-  double r = ((double)h0 + (double)h1) + ((double)l0 + (double)l1);
-  if (escale) r *= escale[f];
-  y[(size_t)f * P1 + s] = r;
 }
 
-// The same edge-centric apply on split-FP32 vectors (Krylov basis storage):
-// BT = 0: FP64 blocks, FP64 accumulation; BT = 1: split-FP32 blocks and
-// accumulation on the FP32 pipe; BT = 2: FP32 blocks, FP32 accumulation.
 template <int BT>
+__device__ __forceinline__ typename VAcc<BT>::T vzero() {
+  if constexpr (BT == 1) return make_float2(0.f, 0.f);
+  else return typename VAcc<BT>::T(0);
+}
+
+// The same edge-centric apply on Krylov-basis vectors: BT = 0: FP64 blocks,
+// FP64 accumulation; BT = 1: split-FP32 blocks and accumulation on the FP32
+// pipe; BT = 2: FP32 blocks, FP32 accumulation. VT: vector type (above).
+template <int BT, int VT>
 __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __restrict__ Sv,
-                                                        const float2* __restrict__ x, float2* __restrict__ y,
+                                                        const void* __restrict__ x, void* __restrict__ y,
                                                         const double* __restrict__ escale, int epb,
                                                         const int* __restrict__ stop) {
   if (stop && *stop) return;
-  using XT = typename std::conditional<BT == 0, double, typename std::conditional<BT == 1, float2, float>::type>::type;
+  using XT = typename VAcc<BT>::T;
   extern __shared__ unsigned char sraw[];
   XT* xs = reinterpret_cast<XT*>(sraw);   // [epb][2][n_t]
   const int nt = P.n_t, P1 = P.P1, PP = P.P;
@@ -183,7 +153,7 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
     const int rem = idx - le * 2 * nt;
     const int sd = rem / nt, c = rem - sd * nt;
     const int f = f0 + le;
-    float2 v = make_float2(0.f, 0.f);
+    XT v = vzero<BT>();
     if (f < P.n_int) {
       int e[2], k[2], fl[2];
       double len;
@@ -191,11 +161,9 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
       int code[3], flip[3];
       elem_edges(e[sd], P.n, code, flip);
       const int kk = c / P1, t = c - kk * P1;
-      if (code[kk] >= 0) v = x[(size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+      if (code[kk] >= 0) v = vgather<BT, VT>(x, (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t));
     }
-    if constexpr (BT == 0) xs[idx] = df_to(v);
-    else if constexpr (BT == 1) xs[idx] = v;
-    else xs[idx] = v.x;
+    xs[idx] = v;
   }
   __syncthreads();
   const int le = tid / P1, s = tid - le * P1;
@@ -204,7 +172,6 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
   int e[2], k[2], fl[2];
   double len;
   edge_sides(f, P.n, e, k, fl, &len);
-  float2 out;
   // row t_side of each side's row-block (the edge dof s in the element's orientation)
   const int t0 = fl[0] ? PP - s : s, t1 = fl[1] ? PP - s : s;
   if constexpr (BT == 1) {
@@ -247,7 +214,9 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
       h0 = ph;
       l0 = pl;
     }
-    out = df_norm(h0, l0);
+    const float2 out = df_norm(h0, l0);
+    if constexpr (VT == 1) static_cast<float2*>(y)[(size_t)f * P1 + s] = out;
+    else static_cast<double*>(y)[(size_t)f * P1 + s] = df_to(out);
   } else if constexpr (BT == 2) {
     // both sides' terms as one sequence q = 0 .. 2 n_t - 1; loads of the next
     // batch of G2 are issued before the arithmetic of the current one (4-byte
@@ -279,32 +248,44 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
     }
     float r = acc0 + acc1;
     if (escale) r *= (float)escale[f];
-    out = make_float2(r, 0.f);
+    if constexpr (VT == 1) static_cast<float2*>(y)[(size_t)f * P1 + s] = make_float2(r, 0.f);
+    else static_cast<double*>(y)[(size_t)f * P1 + s] = (double)r;
   } else {
+    // FP64: both sides' terms as one sequence q = 0 .. 2 n_t - 1 with the
+    // next batch of G0 loads issued before the FMAs of the current one and
+    // two accumulator chains; the only FP64 work besides the 2 n_t FMAs is
+    // one add and the face scale. (The FP64 pipe, 2 FMA/clock/SM on GB300,
+    // is the bound: one FMA per 8-byte block entry.)
+    constexpr int G0 = 8;
+    const int nq = 2 * nt;
     const double* S = static_cast<const double*>(Sv);
+    const double* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
+    const double* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
+    const double* xv = xs + le * 2 * nt;
     double acc0 = 0.0, acc1 = 0.0;
+    double cur[G0], nxt[G0];
 #pragma unroll
-    for (int sd = 0; sd < 2; ++sd) {
-      const double* base = S + ((size_t)e[sd] * 3 + k[sd]) * (size_t)nt * P1 + (sd ? t1 : t0);
-      const XT* xv = xs + (le * 2 + sd) * nt;
-      int j = 0;
-      for (; j + 8 <= nt; j += 8) {
-        double sv[8];
+    for (int u = 0; u < G0; ++u) cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : 0.0;
+    for (int q0 = 0; q0 < nq; q0 += G0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sv[u] = base[(size_t)(j + u) * P1];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          acc0 += sv[u] * xv[j + u];
-          acc1 += sv[u + 1] * xv[j + u + 1];
-        }
+      for (int u = 0; u < G0; ++u) {
+        const int q = q0 + G0 + u;
+        nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : 0.0;
       }
-      for (; j < nt; ++j) acc0 += base[(size_t)j * P1] * xv[j];
+#pragma unroll
+      for (int u = 0; u < G0; u += 2) {
+        const int q = q0 + u;
+        if (q < nq) acc0 = fma(cur[u], xv[q], acc0);
+        if (q + 1 < nq) acc1 = fma(cur[u + 1], xv[q + 1], acc1);
+      }
+#pragma unroll
+      for (int u = 0; u < G0; ++u) cur[u] = nxt[u];
     }
     double r = acc0 + acc1;
     if (escale) r *= escale[f];
-    out = df_from(r);
+    if constexpr (VT == 1) static_cast<float2*>(y)[(size_t)f * P1 + s] = df_from(r);
+    else static_cast<double*>(y)[(size_t)f * P1 + s] = r;
   }
-  y[(size_t)f * P1 + s] = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -662,20 +643,22 @@ cudaError_t apply_bulk_take_error(cudaStream_t st, int* err) {
   return e;
 }
 
-cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
-                             const double* escale, const int* stop, cudaStream_t st, int epb) {
-  // epb < 0: the pipelined bulk-copy apply with -epb consumer warps per edge (split-FP32 blocks only)
-  if (epb < 0 && bt == 1)
-    return launch_apply_bulk(P, static_cast<const float2*>(S), x, y, escale, stop, st, -epb);
+cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void* x, void* y,
+                             const double* escale, const int* stop, cudaStream_t st, int epb, int vt) {
+  // epb < 0: the pipelined bulk-copy apply with -epb consumer warps per edge (split-FP32 blocks and vectors)
+  if (epb < 0 && bt == 1 && vt == 1)
+    return launch_apply_bulk(P, static_cast<const float2*>(S), static_cast<const float2*>(x), static_cast<float2*>(y),
+                             escale, stop, st, -epb);
   // epb edges per block, one thread per (edge, trace position): at most 512 threads
   if (epb <= 0 || epb * P.P1 > 512) epb = apply_edges_per_block(P);
   const int threads = (epb * P.P1 + 31) / 32 * 32;
   const int grid = (P.n_int + epb - 1) / epb;
   const size_t el = bt == 0 ? sizeof(double) : (bt == 1 ? sizeof(float2) : sizeof(float));
   const size_t sm = (size_t)epb * 2 * P.n_t * el;
-  if (bt == 0) apply_vdf_kernel<0><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
-  else if (bt == 1) apply_vdf_kernel<1><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
-  else apply_vdf_kernel<2><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
+#define VDF_CASE(B, V) \
+  if (bt == B && vt == V) apply_vdf_kernel<B, V><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
+  VDF_CASE(0, 0) VDF_CASE(1, 0) VDF_CASE(2, 0) VDF_CASE(0, 1) VDF_CASE(1, 1) VDF_CASE(2, 1)
+#undef VDF_CASE
   return cudaGetLastError();
 }
 
@@ -689,22 +672,16 @@ __global__ void split_df_kernel(const double* __restrict__ a, float2* __restrict
 }
 
 
+// FP64 vectors: the Arnoldi operators of the FP64-basis solve (and the true
+// residual), with the default edges per block
 cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
-                           const int* stop, cudaStream_t st) {
-  const int epb = apply_edges_per_block(P);
-  const int grid = (P.n_int + epb - 1) / epb;
-  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(double);
-  apply_kernel<double, double, double><<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
-  return cudaGetLastError();
+                           const int* stop, cudaStream_t st, int epb) {
+  return launch_apply_vdf(0, P, S, x, y, escale, stop, st, epb, 0);
 }
 
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st) {
-  const int epb = apply_edges_per_block(P);
-  const int grid = (P.n_int + epb - 1) / epb;
-  const size_t sm = (size_t)epb * 2 * P.n_t * sizeof(float2);
-  apply_df_kernel<<<grid, 256, sm, st>>>(P, S, x, y, escale, epb, stop);
-  return cudaGetLastError();
+  return launch_apply_vdf(1, P, S, x, y, escale, stop, st, 0, 0);
 }
 
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st) {

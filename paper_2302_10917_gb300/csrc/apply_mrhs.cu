@@ -252,26 +252,155 @@ __global__ void mrhs_edge_sum_kernel(Params P, const float2* __restrict__ Z, int
   }
 }
 
-// Element-centric multi-RHS apply on split vectors; Z: [N][nrhs][n_t] pairs.
-cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
-                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st, const int* cmap) {
-  if (nrhs < 1 || nrhs > HDG_MAX_RHS) return cudaErrorInvalidValue;
-  const size_t sm = (size_t)P.n_t * mrhs_row(nrhs) * sizeof(float2);
+// The same two kernels on FP64 vectors (the batched solve with the FP64
+// Krylov basis): products in the block type's arithmetic (BT = 0: FP64
+// fused multiply-adds, 1: split-FP32, 2: FP32), Z and the two-side sum in FP64.
+template <int BT>
+struct MrhsAccD;
+template <>
+struct MrhsAccD<0> { using T = double; };
+template <>
+struct MrhsAccD<1> { using T = float2; };
+template <>
+struct MrhsAccD<2> { using T = float; };
+
+template <int BT>
+__global__ void __launch_bounds__(256) mrhs_element_d_kernel(Params P, const void* __restrict__ Sv,
+                                                             const double* __restrict__ x, int nrhs, int64_t vstride,
+                                                             double* __restrict__ Z, const int* __restrict__ cmap) {
+  using A = typename MrhsAccD<BT>::T;
+  extern __shared__ unsigned char xraw[];
+  A* xs = reinterpret_cast<A*>(xraw);          // [n_t][NR1]
+  const int nt = P.n_t, P1 = P.P1, PP = P.P, NR1 = mrhs_row(nrhs);
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x;
+  int code[3], flip[3];
+  elem_edges(e, P.n, code, flip);
+  for (int idx = tid; idx < nt * (NR1 - 1); idx += blockDim.x) {
+    const int r = idx / nt, c = idx - r * nt;
+    const int kk = c / P1, t = c - kk * P1;
+    double v = 0.0;
+    if (r < nrhs && code[kk] >= 0)
+      v = x[(size_t)(cmap ? cmap[r] : r) * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
+    if constexpr (BT == 0) xs[c * NR1 + r] = v;
+    else if constexpr (BT == 1) xs[c * NR1 + r] = df_from(v);
+    else xs[c * NR1 + r] = (float)v;
+  }
+  __syncthreads();
+  const int groups = (nrhs + RPT - 1) / RPT;
+  const size_t sb = (size_t)e * 3 * nt * P1;
+  for (int item = tid; item < nt * groups; item += blockDim.x) {
+    const int row = item % nt, grp = item / nt;
+    const int k = row / P1, t = row - k * P1;
+    const int r0 = grp * RPT;
+    const size_t rb = sb + (size_t)k * nt * P1 + t;     // S_e(row, c) = S[e][k][c][t]
+    double out[RPT];
+    if constexpr (BT == 0) {
+      const double* S = static_cast<const double*>(Sv);
+      double acc[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = 0.0;
+      for (int c = 0; c < nt; ++c) {
+        const double bv = S[rb + (size_t)c * P1];
+        const double* xr = xs + c * NR1 + r0;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) acc[u] = fma(bv, xr[u], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) out[u] = acc[u];
+    } else if constexpr (BT == 1) {
+      const float2* S = static_cast<const float2*>(Sv);
+      float h[RPT], l[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) { h[u] = 0.f; l[u] = 0.f; }
+      for (int c = 0; c < nt; ++c) {
+        const float2 bv = S[rb + (size_t)c * P1];
+        const float2* xr = xs + c * NR1 + r0;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) df_fma(h[u], l[u], bv, xr[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) out[u] = df_to(df_norm(h[u], l[u]));
+    } else {
+      const float* S = static_cast<const float*>(Sv);
+      float acc[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = 0.f;
+      for (int c = 0; c < nt; ++c) {
+        const float bv = S[rb + (size_t)c * P1];
+        const float* xr = xs + c * NR1 + r0;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) acc[u] = fmaf(bv, xr[u], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) out[u] = (double)acc[u];
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int r = r0 + u;
+      if (r < nrhs) Z[((size_t)e * nrhs + r) * nt + row] = out[u];
+    }
+  }
+}
+
+__global__ void mrhs_edge_sum_d_kernel(Params P, const double* __restrict__ Z, int nrhs, int64_t vstride,
+                                       const double* __restrict__ escale, double* __restrict__ y,
+                                       const int* __restrict__ cmap) {
+  const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  const int64_t per = (int64_t)P.n_int * P1;
+  const int64_t total = per * nrhs;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / per);
+    const int64_t fs = idx - (int64_t)r * per;
+    const int f = (int)(fs / P1), s = (int)(fs - (int64_t)f * P1);
+    int e[2], k[2], fl[2];
+    double len;
+    edge_sides(f, P.n, e, k, fl, &len);
+    double v = 0.0;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const int t = fl[sd] ? PP - s : s;
+      v += Z[((size_t)e[sd] * nrhs + r) * nt + k[sd] * P1 + t];
+    }
+    if (escale) v *= escale[f];
+    y[(size_t)(cmap ? cmap[r] : r) * vstride + fs] = v;
+  }
+}
+
+// Element-centric multi-RHS apply; Z: [N][nrhs][n_t] (split pairs for split
+// vectors, FP64 for FP64 vectors). vt: 0 FP64 / 1 split-FP32 vectors.
+cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const void* x, void* y, int nrhs,
+                                 int64_t vstride, const double* escale, void* Z, cudaStream_t st, const int* cmap,
+                                 int vt) {
+  if (nrhs < 1 || nrhs > HDG_MAX_RHS || bt < 0 || bt > 2) return cudaErrorInvalidValue;
+  const size_t el = (vt == 0 && bt == 2) ? sizeof(float) : 8;
+  const size_t sm = (size_t)P.n_t * mrhs_row(nrhs) * el;
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t err;
-  if (bt == 0) {
-    err = cudaFuncSetAttribute(mrhs_element_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<0><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
-  } else if (bt == 1) {
-    err = cudaFuncSetAttribute(mrhs_element_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<1><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
+  cudaError_t err = cudaSuccess;
+  auto run = [&](auto kern, auto xp, auto zp) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (err == cudaSuccess) kern<<<P.N, 256, sm, st>>>(P, S, xp, nrhs, vstride, zp, cmap);
+  };
+  const float2* xf = static_cast<const float2*>(x);
+  float2* zf = static_cast<float2*>(Z);
+  const double* xd = static_cast<const double*>(x);
+  double* zd = static_cast<double*>(Z);
+  if (vt == 1) {
+    if (bt == 0) run(mrhs_element_kernel<0>, xf, zf);
+    else if (bt == 1) run(mrhs_element_kernel<1>, xf, zf);
+    else run(mrhs_element_kernel<2>, xf, zf);
   } else {
-    err = cudaFuncSetAttribute(mrhs_element_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err == cudaSuccess) mrhs_element_kernel<2><<<P.N, 256, sm, st>>>(P, S, x, nrhs, vstride, Z, cmap);
+    if (bt == 0) run(mrhs_element_d_kernel<0>, xd, zd);
+    else if (bt == 1) run(mrhs_element_d_kernel<1>, xd, zd);
+    else run(mrhs_element_d_kernel<2>, xd, zd);
   }
   if (err != cudaSuccess) return err;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  mrhs_edge_sum_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, Z, nrhs, vstride, escale, y, cmap);
+  if (vt == 1)
+    mrhs_edge_sum_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, zf, nrhs, vstride, escale, static_cast<float2*>(y), cmap);
+  else
+    mrhs_edge_sum_d_kernel<<<4 * 152 * 8, 256, 0, st>>>(P, zd, nrhs, vstride, escale, static_cast<double*>(y), cmap);
   return cudaGetLastError();
 }
 

@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(KT, 4) df_mdot_kernel(const float4* __restrict
 // whether a second pass is needed (Kahan-Parlett: ||w - V h||^2 < ||w||^2 / 2,
 // i.e. more than half of w lay in the basis and the Pythagorean norm has lost
 // digits): then it stores h, clears F_P2 and leaves the rotations to the second
-// pass. stopslot: the flag that makes the launch return at once.
+// pass; 3 as 2 with the threshold 1e-6 ||w||^2. stopslot: the flag that makes
+// the launch return at once.
 // Grid (column groups, instances), 1024 threads: block k sums columns
 // 32 k .. 32 k + 31 of the partial rows (warp w the rows w, w + 32, ..., then
 // the 32 warps' sums in order) into sm[htmp + col]; the last block of an
@@ -251,8 +252,12 @@ __global__ void __launch_bounds__(1024) reduce2_givens_kernel(const double* part
   double hh = 0.0;
   for (int i = 0; i < nw; ++i) hh += red[i];
   const double d = vals[nv] - hh;
-  if (add == 2) {
-    if (!(d >= 0.5 * vals[nv])) {   // second pass needed (also for a non-finite estimate)
+  if (add >= 2) {
+    // add = 2: Kahan-Parlett threshold 1/2; add = 3: only where the single projection cancelled
+    // more than six decimal digits of ||w||^2 (the new vector then loses orthogonality to
+    // about eps / 1e-3 = 1e-13 in FP64, harmless for GMRES, whose restarts use the true residual)
+    const double eta = add == 2 ? 0.5 : 1e-6;
+    if (!(d >= eta * vals[nv])) {   // second pass needed (also for a non-finite estimate)
       flags[F_P2] = 0;
       return;
     }
@@ -357,6 +362,169 @@ __global__ void __launch_bounds__(KT) df_xupdate_kernel(const float2* __restrict
     float ah = 0.f, al = 0.f;
     for (int i = 0; i < nv; ++i) df_fma(ah, al, cf[i], V[(size_t)i * ldv + idx]);
     x[idx] += df_to(make_float2(ah, al));
+  }
+}
+
+// ------------------------------------------------------ FP64 vector kernels
+// The FP64 Krylov basis (HDG_BASIS_FP64): the same passes as the split-FP32
+// kernels above, on FP64 entries with FP64 fused multiply-adds; rows have the
+// same even length, so a thread moves an element pair with one 16-byte load.
+// On GB300 these are bound by the FP64 pipe (one FMA per 8-byte basis entry
+// against 2 FMA/clock/SM), not by HBM.
+template <int NV>
+__device__ __forceinline__ void d_block_reduce(double (&h)[NV], int nv, double* red, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int g = 0; g < NV; ++g) {
+    double v = h[g];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid * NV + g] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NV && (int)threadIdx.x < nv) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) s += red[w2 * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Products of NG basis vectors with w over the pairs [lo, hi) (FP64 FMAs; NG is
+// the number of columns the block really has, so a partial last group costs
+// only its own FMAs: these passes are bound by the FP64 pipe).
+template <int NG>
+__device__ __forceinline__ void d_mdot_body(const double2* __restrict__ V, int64_t vstr, int g0, int nv,
+                                            const double2* __restrict__ w, int64_t lo, int64_t hi, double (&h)[VG]) {
+  for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    double2 a[NG];
+    const double2 wa = w[p];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) a[g] = g0 + g < nv ? V[(size_t)(g0 + g) * vstr + p] : wa;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) h[g] = fma(a[g].y, wa.y, fma(a[g].x, wa.x, h[g]));
+  }
+}
+
+// part[b * ncol + i] = sum over pair chunk b of V_i . w (FP64); block
+// numbering, columns and stop flags as in df_mdot_kernel.
+__global__ void __launch_bounds__(KT, 4) d_mdot_kernel(const double2* __restrict__ V, int64_t np, int nv, int ncol,
+                                                       const double2* __restrict__ w, double* part, const int* stop,
+                                                       Batch bt) {
+  const int rb = blockIdx.z;
+  if (stop && stop[rb * bt.rflag + F_STOP]) return;
+  V += rb * bt.rv;
+  w += rb * bt.rw;
+  part += rb * bt.rpart;
+  __shared__ double red[(KT / 32) * VG];
+  const unsigned k = blockIdx.y * gridDim.x + blockIdx.x;
+  const int64_t cb = k / gridDim.y;
+  const int g0 = (int)(k % gridDim.y) * VG;
+  const int64_t chunk = (np + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = cb * chunk;
+  const int64_t hi = lo + chunk < np ? lo + chunk : np;
+  double h[VG];
+#pragma unroll
+  for (int g = 0; g < VG; ++g) h[g] = 0.0;
+  switch (ncol - g0 < VG ? ncol - g0 : VG) {   // uniform over the block
+    case 1: d_mdot_body<1>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 2: d_mdot_body<2>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 3: d_mdot_body<3>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 4: d_mdot_body<4>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 5: d_mdot_body<5>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 6: d_mdot_body<6>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    case 7: d_mdot_body<7>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+    default: d_mdot_body<VG>(V, bt.vstr, g0, nv, w, lo, hi, h); break;
+  }
+  d_block_reduce<VG>(h, ncol - g0, red, part + (size_t)cb * ncol + g0);
+}
+
+// the last R (< 8) columns of an update: a -= sum cf_u v_u.x, b likewise
+template <int R>
+__device__ __forceinline__ void d_update_tail(double& a, double& b, const double* cf, const double2 (&v)[8]) {
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    a = fma(cf[u], v[u].x, a);
+    b = fma(cf[u], v[u].y, b);
+  }
+}
+
+// out = (w - sum_i coef_i V_i) * scale in FP64 (scale = sm[scale_off], or 1
+// when scale_off < 0); out may be w. Loads of the next group of 8 basis
+// vectors go out before the FMAs of the current one; rows walked last to
+// first (the multi-dot's most recent rows are still in L2).
+__global__ void __launch_bounds__(KT) d_update_kernel(const double2* __restrict__ V, int64_t np, int nv,
+                                                      const double* __restrict__ coef, const double2* w,
+                                                      const double* sm, int scale_off, double2* out,
+                                                      const int* stop, Batch bt, int64_t rout) {
+  const int rb = gridDim.y - 1 - blockIdx.y;
+  if (stop && stop[rb * bt.rflag + F_STOP]) return;
+  V += rb * bt.rv;
+  coef += rb * bt.rsm;
+  w += rb * bt.rw;
+  if (sm) sm += rb * bt.rsm;
+  out += rb * rout;
+  __shared__ double cf[144];
+  for (int i = threadIdx.x; i < 144; i += blockDim.x) cf[i] = i < nv ? -coef[i] : 0.0;
+  __syncthreads();
+  const bool scaled = scale_off >= 0;
+  const double inv = scaled ? sm[scale_off] : 1.0;
+  const double2 z2 = make_double2(0.0, 0.0);
+  for (int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pf < np; pf += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = np - 1 - pf;
+    const double2 wv = w[p];
+    double a = wv.x, b = wv.y;
+    double2 v[8], nx[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = u < nv ? V[(size_t)u * bt.vstr + p] : z2;
+    int i0 = 0;
+    for (; i0 + 8 <= nv; i0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) nx[u] = i0 + 8 + u < nv ? V[(size_t)(i0 + 8 + u) * bt.vstr + p] : z2;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a = fma(cf[i0 + u], v[u].x, a);
+        b = fma(cf[i0 + u], v[u].y, b);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = nx[u];
+    }
+    switch (nv - i0) {   // the partial last group: only its own FMAs
+      case 1: d_update_tail<1>(a, b, cf + i0, v); break;
+      case 2: d_update_tail<2>(a, b, cf + i0, v); break;
+      case 3: d_update_tail<3>(a, b, cf + i0, v); break;
+      case 4: d_update_tail<4>(a, b, cf + i0, v); break;
+      case 5: d_update_tail<5>(a, b, cf + i0, v); break;
+      case 6: d_update_tail<6>(a, b, cf + i0, v); break;
+      case 7: d_update_tail<7>(a, b, cf + i0, v); break;
+      default: break;
+    }
+    if (scaled) {
+      a *= inv;
+      b *= inv;
+    }
+    out[p] = make_double2(a, b);
+  }
+}
+
+// out = a * sm[off] (FP64 basis: the first vector of a cycle)
+__global__ void __launch_bounds__(KT) to_d_kernel(const double* a, const double* sm, int off, double* out, int64_t n,
+                                                  const int* stop) {
+  if (stop && stop[F_STOP]) return;
+  const double f = sm[off];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    out[idx] = a[idx] * f;
+}
+
+// x += sum_i y_i V_i (FP64 basis, row length ldv)
+__global__ void __launch_bounds__(KT) d_xupdate_kernel(const double* __restrict__ V, int64_t n, int64_t ldv, int nv,
+                                                       const double* __restrict__ y, double* x) {
+  __shared__ double cf[130];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = y[i];
+  __syncthreads();
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(cf[i], V[(size_t)i * ldv + idx], a);
+    x[idx] += a;
   }
 }
 
@@ -489,14 +657,47 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 // Multi-dot over nv basis vectors (ncol = nv + 1 appends ||w||^2): about kgd
 // blocks over all groups of VG vectors (at least one per SM along x), fewer
 // for short vectors. Returns the number of partial rows (blocks along x).
-static int launch_mdot(const float4* V4, int64_t np, int nv, int ncol, const float4* w4, double* part,
-                       const int* fl, cudaStream_t st, int kgd, const Batch& bt, int nb = 1) {
+// f64: FP64 basis (double pairs), else split-FP32 pairs.
+static int launch_mdot(const void* V4, int64_t np, int nv, int ncol, const void* w4, double* part,
+                       const int* fl, cudaStream_t st, int kgd, const Batch& bt, int nb = 1, bool f64 = false) {
   const int gy = (ncol + VG - 1) / VG;
   int64_t gx = kgd / gy > 152 ? kgd / gy : 152;
   const int64_t need = (np + KT - 1) / KT;
   if (gx > need) gx = need > 1 ? need : 1;
-  df_mdot_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)nb), KT, 0, st>>>(V4, np, nv, ncol, w4, part, fl, bt);
+  const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nb);
+  if (f64)
+    d_mdot_kernel<<<grid, KT, 0, st>>>(static_cast<const double2*>(V4), np, nv, ncol, static_cast<const double2*>(w4),
+                                       part, fl, bt);
+  else
+    df_mdot_kernel<<<grid, KT, 0, st>>>(static_cast<const float4*>(V4), np, nv, ncol, static_cast<const float4*>(w4),
+                                        part, fl, bt);
   return (int)gx;
+}
+
+// out = (w - sum_i coef_i V_i) * scale over the basis of either type
+static void launch_update(bool f64, dim3 grid, cudaStream_t st, const void* V4, int64_t np, int nv, const double* coef,
+                          const void* w4, const double* sm, int scale_off, void* out, const int* stop, const Batch& bt,
+                          int64_t rout) {
+  if (f64)
+    d_update_kernel<<<grid, KT, 0, st>>>(static_cast<const double2*>(V4), np, nv, coef, static_cast<const double2*>(w4),
+                                         sm, scale_off, static_cast<double2*>(out), stop, bt, rout);
+  else
+    df_update_kernel<<<grid, KT, 0, st>>>(static_cast<const float4*>(V4), np, nv, coef, static_cast<const float4*>(w4),
+                                          sm, scale_off, static_cast<float4*>(out), stop, bt, rout);
+}
+
+// first basis vector of a cycle: V0 = a * sm[off]
+static void launch_first(bool f64, cudaStream_t st, const double* a, const double* sm, int off, void* V0, int64_t n,
+                         const int* stop) {
+  if (f64) to_d_kernel<<<KG, KT, 0, st>>>(a, sm, off, static_cast<double*>(V0), n, stop);
+  else to_df_kernel<<<KG, KT, 0, st>>>(a, sm, off, static_cast<float2*>(V0), n, stop);
+}
+
+// x += sum_i y_i V_i
+static void launch_xupdate(bool f64, cudaStream_t st, const void* V, int64_t n, int64_t ldv, int nv, const double* y,
+                           double* x) {
+  if (f64) d_xupdate_kernel<<<KG, KT, 0, st>>>(static_cast<const double*>(V), n, ldv, nv, y, x);
+  else df_xupdate_kernel<<<KG, KT, 0, st>>>(static_cast<const float2*>(V), n, ldv, nv, y, x);
 }
 
 // The operator of the condensed system: the uniform-level kernels, or the
@@ -524,6 +725,20 @@ static cudaError_t op_dinv(hdg_ctx* c, const double* y, double* z, cudaStream_t 
   return launch_face_dinv(c->prm, c->dt.Ghinv, c->d_escale, y, z, st);
 }
 
+// Cycle length of restarted GMRES. GMRES(K) can stagnate on a non-normal
+// operator: the cycle's minimal-residual polynomial stops reducing the true
+// residual and every later cycle repeats it (on the banded-level workload one
+// column of 64 stays at 0.21, and which column is trapped changes with
+// rounding alone). When a cycle cuts the true residual by less than 1 %, the
+// next cycles get a different length: K - d, K - 2d, ... (d = K/8), back to K
+// below K/2 (varying the restart length, after Baker, Jessup and Kolev 2009).
+// A cycle shorter than K runs step by step instead of as the captured graph.
+static int next_cycle_length(int cur, int K, bool stalled) {
+  if (!stalled) return cur;
+  const int d = std::max(1, K / 8), lo = std::max(1, (K + 1) / 2);
+  return cur - d >= lo ? cur - d : K;
+}
+
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep) {
   const Params& P = c->prm;
   const int K = o.restart;
@@ -534,12 +749,16 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   SmallLayout L(K);
   double* sm = c->d_small;
   int* fl = c->d_flag;
-  float2* V = c->d_V;
-  float2* w = c->d_w;
+  // basis entries: FP64, or split-FP32 pairs (8 bytes either way)
+  const bool f64b = o.basis == HDG_BASIS_FP64;
+  const int vt = f64b ? 0 : 1;
+  const size_t esz = 8;
+  char* V = reinterpret_cast<char*>(c->d_V);
+  void* w = c->d_w;
   const int64_t ldv = n + (n & 1), np = ldv / 2;   // basis row length (even) and element pairs
   const Batch one{np, 0, 0, 0, 0, 0};
-  const float4* V4 = reinterpret_cast<const float4*>(V);
-  float4* w4 = reinterpret_cast<float4*>(w);
+  const void* V4 = V;
+  void* w4 = w;
   double* t = c->d_r;           // true residual g - S x (FP64)
   double* r0 = c->d_r + n;      // S x, then D^-1 t
   double* part = c->d_part;
@@ -552,11 +771,12 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   // update needs no more than one pass of KT pairs per block
   const int kgd = c->tune_kgd > 0 ? c->tune_kgd : KGD;
   const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
-  const int epb = c->tune_epb[bt];
+  // the pipelined shape runs on split-FP32 vectors only
+  const int epb = (f64b && c->tune_epb[bt] < 0) ? 0 : c->tune_epb[bt];
   const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
   // the pipelined apply's timeout flag, read once the solve has synchronised
   auto bulk_wait_gave_up = [&]() -> bool {
-    if (!(epb < 0 && bt == 1)) return false;
+    if (!(epb < 0 && bt == 1 && !f64b)) return false;
     int err = 0;
     return !cu.ok(apply_bulk_take_error(st, &err)) || err != 0;
   };
@@ -573,8 +793,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     rep.converged = 1;
     return cu.err == cudaSuccess ? HDG_OK : fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
   }
-  int its = 0;
-  double rel = 1.0;
+  int its = 0, klen = K;
+  double rel = 1.0, prev_rel = 0.0;
   while (true) {
     // true residual with the unpreconditioned FP64 operator (the stopping test)
     {
@@ -594,15 +814,17 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       return bulk_wait_gave_up() ? fail(c, HDG_ERR_TIMEOUT, "pipelined apply: a bounded copy wait gave up") : HDG_OK;
     }
     if (its >= o.maxit) break;
+    klen = next_cycle_length(klen, K, prev_rel > 0.0 && rel > 0.99 * prev_rel);
+    prev_rel = rel;
     // r0 = D^-1 t; V0 = r0 / beta; the cycle aims at the reduction the true residual still needs
     cu.ok(op_dinv(c, t, r0, st));
     const double factor = 0.5 * o.tol / rel;
     cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &factor, sizeof(double), cudaMemcpyHostToDevice, st));
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, r0, 0.0, r0, r0, n, part);
     cycle_init_kernel<<<1, 256, 0, st>>>(sm, L, fl, part, KG);
-    to_df_kernel<<<KG, KT, 0, st>>>(r0, sm, L.sc + 4, V, n, fl);
+    launch_first(f64b, st, r0, sm, L.sc + 4, V, n, fl);
     LAUNCHED(4);
-    const int jmax = std::min(K, o.maxit - its);
+    const int jmax = std::min(klen, o.maxit - its);
     std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
     // one Arnoldi step j on stream s (timed phases only when profiling, i.e. not captured)
     // (ev: event quadruple of a captured, timed step: apply begin/end, vector work begin/end)
@@ -612,40 +834,40 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        if (c->lv) cu.ok(launch_level_apply(c, bt, 1, Sop, V + (size_t)j * ldv, w, 1, ldv, precond_scale(c), fl, s));
-        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv, w, precond_scale(c), fl, s, epb));
+        if (c->lv) cu.ok(launch_level_apply(c, bt, vt, Sop, V + (size_t)j * ldv * esz, w, 1, ldv, precond_scale(c), fl, s));
+        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv * esz, w, precond_scale(c), fl, s, epb, vt));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
         cu.ok(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
       }
       ProfScope po(c, timed ? HDG_PROF_ORTHO : -1);
-      float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * ldv);
+      void* Vn = V + (size_t)(j + 1) * ldv * esz;
       if (o.orth == 0) {
         // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
         // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
         // the norm from ||w'||^2 - ||h2||^2
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd, one);
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd, one, 1, f64b);
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
-        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
+        launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_STOP);
       } else if (o.orth == 1) {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one, F_STOP);
       } else {
         // as orth = 1, plus a second projection (w' = w - V h; h2 = V^T w', ||w'||^2) only
         // when the first pass finds ||w - V h||^2 < ||w||^2 / 2; the second-pass kernels
         // are always launched and return at once when flag F_P2 says it is not needed
-        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one);
-        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 2, one, F_STOP);
-        df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, one, 0);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, s, kgd, one);
+        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, o.orth, one, F_STOP);
+        launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, one, 0);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, s, kgd, one, 1, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_P2);
       }
-      df_update_kernel<<<gu, KT, 0, s>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
+      launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     };
     const int per_step = o.orth == 1 ? 4 : 6;
@@ -656,7 +878,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       // turns the steps after convergence into immediate returns. With
       // profiling on, the capture carries an event quadruple per step.
       const int timed = c->prof_on ? 1 : 0;
-      const std::vector<intptr_t> key = {K, bt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
+      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
                                          (intptr_t)np, kgd, kgu, epb, c->lv ? c->lv->rb : 0};
       if (timed && (int)c->gm_ev.size() < 4 * K) {
@@ -720,7 +942,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     rep.restarts += 1;
     if (jused == 0) break;
     lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
-    df_xupdate_kernel<<<KG, KT, 0, st>>>(V, n, ldv, jused, sm + L.y, x);
+    launch_xupdate(f64b, st, V, n, ldv, jused, sm + L.y, x);
     LAUNCHED(2);
   }
   rep.converged = 0;
@@ -739,9 +961,11 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   const Batch one{np, 0, 0, 0, 0, 0};
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
   const void* Sop = op_blocks(c, o.mode);
-  float2* V = c->d_V;
-  const float4* V4 = reinterpret_cast<const float4*>(V);
-  float4* w4 = reinterpret_cast<float4*>(c->d_w);
+  const bool f64b = o.basis == HDG_BASIS_FP64;
+  const int vt = f64b ? 0 : 1;
+  char* V = reinterpret_cast<char*>(c->d_V);
+  const void* V4 = V;
+  void* w4 = c->d_w;
   // scratch: the update writes basis vector nv (contents of the basis are not
   // kept across solves); no stop flag, so every candidate does its full work
   const int nv = K / 2 > 1 ? K / 2 : 1;
@@ -771,7 +995,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
     if (!cu.ok(level_ensure_z(c, 1))) return fail(c, HDG_ERR_OOM, "element-side buffer");
     for (int rb : {128, 256, 512}) {
       c->lv->rb = rb;
-      const double t = time_it([&] { cu.ok(launch_level_apply(c, bt, 1, Sop, V, c->d_w, 1, ldv, precond_scale(c),
+      const double t = time_it([&] { cu.ok(launch_level_apply(c, bt, vt, Sop, V, c->d_w, 1, ldv, precond_scale(c),
                                                               nullptr, st)); });
       if (rb == 256) def_apply = t;
       if (t < best_apply) { best_apply = t; best_rb = rb; }
@@ -782,17 +1006,17 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
     if (c->lv) break;
     const int epb = threads / P.P1 > 0 ? threads / P.P1 : 1;
     if (epb * P.P1 > 512) continue;
-    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, epb)); });
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, epb, vt)); });
     if (epb == def_epb) def_apply = t;
     if (t < best_apply) { best_apply = t; best_epb = epb; }
   }
   if (def_apply == 0.0 && !c->lv)
-    def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb)); });
+    def_apply = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, def_epb, vt)); });
   // split-FP32 blocks: the pipelined bulk-copy apply with 1 .. 3 consumer warps per edge
   double best_bulk = 0.0;
-  for (int q = 1; q <= 3 && bt == 1 && !c->lv; ++q) {
+  for (int q = 1; q <= 3 && bt == 1 && !c->lv && !f64b; ++q) {
     if (!apply_bulk_available(P, q)) continue;
-    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -q)); });
+    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -q, 1)); });
     int err = 0;
     if (!cu.ok(apply_bulk_take_error(st, &err)) || err)
       return fail(c, HDG_ERR_TIMEOUT, "autotune: pipelined apply: a bounded copy wait gave up");
@@ -804,18 +1028,18 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   int best_kgd = KGD;
   double best_mdot = 1e30, def_mdot = 0.0;
   for (int kgd : {608, 1216, 2432}) {
-    const double t = time_it([&] { launch_mdot(V4, np, nv, nv + 1, w4, c->d_part, nullptr, st, kgd, one); });
+    const double t = time_it([&] { launch_mdot(V4, np, nv, nv + 1, w4, c->d_part, nullptr, st, kgd, one, 1, f64b); });
     if (kgd == KGD) def_mdot = t;
     if (t < best_mdot) { best_mdot = t; best_kgd = kgd; }
   }
   // streaming-update blocks
   int best_kgu = KGU;
   double best_upd = 1e30, def_upd = 0.0;
-  float4* out = reinterpret_cast<float4*>(V + (size_t)nv * ldv);
+  void* out = V + (size_t)nv * ldv * 8;
   for (int kgu : {608, 1216, 2432, 4864}) {
     const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
     const double t = time_it([&] {
-      df_update_kernel<<<gu, KT, 0, st>>>(V4, np, nv, coef, w4, nullptr, -1, out, nullptr, one, 0);
+      launch_update(f64b, dim3(gu), st, V4, np, nv, coef, w4, nullptr, -1, out, nullptr, one, 0);
       cu.ok(cudaGetLastError());
     });
     if (kgu == KGU) def_upd = t;
@@ -901,9 +1125,12 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
   const int64_t ldv = n + (n & 1), np = ldv / 2;
   const int64_t rpart = (int64_t)(KG > KGD_MAX ? KG : KGD_MAX) * (K + 2);
   const Batch bt{(int64_t)nb * np, np, np, rpart, L.total, 4};
-  float2* V = c->d_Vb;
-  const float4* V4 = reinterpret_cast<const float4*>(V);
-  float4* w4 = reinterpret_cast<float4*>(c->d_wb);
+  const bool f64b = o.basis == HDG_BASIS_FP64;
+  const int vt = f64b ? 0 : 1;
+  const size_t esz = 8;   // basis entries: FP64 or split-FP32 pairs
+  char* V = reinterpret_cast<char*>(c->d_Vb);
+  const void* V4 = V;
+  void* w4 = c->d_wb;
   double* t = c->d_rb;                 // [nb][n] true residuals
   double* r0 = c->d_rb + (size_t)nb * n;   // [nb][n] S x, then D^-1 t
   double* part = c->d_partb;
@@ -917,7 +1144,8 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
   const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
   const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
   rep = hdg_solve_report{};
-  std::vector<double> host(nb), gnorm(nb), rel(nb, 1.0);
+  std::vector<double> host(nb), gnorm(nb), rel(nb, 1.0), prev_rel(nb, 0.0);
+  int klen = K;
   std::vector<int> done(nb, 0), its(nb, 0), hfl(4 * nb);
   int* d_done = reinterpret_cast<int*>(scal + nb);   // [nb] converged flags (device copy)
   auto norms = [&](const double* vec, int64_t stride, double a, const double* y2, double bcoef, double* outv) {
@@ -964,6 +1192,12 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       return HDG_OK;
     }
     if (maxits >= o.maxit) break;
+    bool stalled = false;
+    for (int r = 0; r < nb; ++r) {
+      if (!done[r] && prev_rel[r] > 0.0 && rel[r] > 0.99 * prev_rel[r]) stalled = true;
+      prev_rel[r] = rel[r];
+    }
+    klen = next_cycle_length(klen, K, stalled);
     // cycle start for the instances still running: r0 = D^-1 t, V_0 = r0 / ||r0||
     std::vector<double> factor(nb, 0.0);
     for (int r = 0; r < nb; ++r) factor[r] = done[r] ? 1.0 : 0.5 * o.tol / rel[r];
@@ -991,47 +1225,47 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       cu.ok(op_dinv(c, tr, rr, st));
       axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, rr, 0.0, rr, rr, n, pr);
       cycle_init_kernel<<<1, 256, 0, st>>>(smr, L, flr, pr, KG);
-      to_df_kernel<<<KG, KT, 0, st>>>(rr, smr, L.sc + 4, V + (size_t)r * ldv, n, flr);
+      launch_first(f64b, st, rr, smr, L.sc + 4, V + (size_t)r * ldv * esz, n, flr);
       c->launches += 4;
     }
-    const int jmax = std::min(K, o.maxit - maxits);
+    const int jmax = std::min(klen, o.maxit - maxits);
     for (int j = 0; j < jmax; ++j) {
       const int nv = j + 1;
       {
         ProfScope ps(c, phase);
         if (c->lv)
-          cu.ok(launch_level_apply(c, btype, 1, Sop, V + (size_t)j * nb * ldv, c->d_wb, na, ldv, precond_scale(c),
-                                   nullptr, st, cmap));
+          cu.ok(launch_level_apply(c, btype, vt, Sop, V + (size_t)j * nb * ldv * esz, c->d_wb, na, ldv,
+                                   precond_scale(c), nullptr, st, cmap));
         else
-          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv, c->d_wb, na, ldv, precond_scale(c),
-                                     c->d_Zb, st, cmap));
+          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv * esz, c->d_wb, na, ldv,
+                                     precond_scale(c), c->d_Zb, st, cmap, vt));
         c->launches += 1;
       }
       ProfScope po(c, HDG_PROF_ORTHO);
-      float4* Vn = reinterpret_cast<float4*>(V + (size_t)(j + 1) * nb * ldv);
+      void* Vn = V + (size_t)(j + 1) * nb * ldv * esz;
       if (o.orth == 0) {
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, st, kgd, bt, nb);
+        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, st, kgd, bt, nb, f64b);
         for (int r = 0; r < nb; ++r)
           mdot_reduce_kernel<<<nv, 128, 0, st>>>(part + (size_t)r * rpart, G, nv, nv,
                                                  sm + (size_t)r * L.total + L.H + (size_t)j * (K + 1),
                                                  sm + (size_t)r * L.total + L.htmp, 0, fl + 4 * r, nullptr);
-        df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, bt, np);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
+        launch_update(f64b, dim3(gu, nb), st, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, bt, np);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_STOP);
         c->launches += 4 + nb;
       } else if (o.orth == 1) {
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
+        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 0, bt, F_STOP);
         c->launches += 2;
       } else {
-        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb);
-        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 2, bt, F_STOP);
-        df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, bt, np);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, st, kgd, bt, nb);
+        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, st, kgd, bt, nb, f64b);
+        reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, o.orth, bt, F_STOP);
+        launch_update(f64b, dim3(gu, nb), st, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, bt, np);
+        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, st, kgd, bt, nb, f64b);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, nb), 1024, 0, st>>>(part, G, nv, sm, L, fl, j, 1, bt, F_P2);
         c->launches += 5;
       }
-      df_update_kernel<<<dim3(gu, nb), KT, 0, st>>>(V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, bt, np);
+      launch_update(f64b, dim3(gu, nb), st, V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, bt, np);
       c->launches += 2;
     }
     cu.ok(cudaGetLastError());
@@ -1048,8 +1282,7 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       any = 1;
       double* smr = sm + (size_t)r * L.total;
       lsq_kernel<<<1, 32, 0, st>>>(smr, L, fl + 4 * r);
-      df_xupdate_kernel<<<KG, KT, 0, st>>>(V + (size_t)r * ldv, n, (int64_t)nb * ldv, jused, smr + L.y,
-                                           x + (size_t)r * n);
+      launch_xupdate(f64b, st, V + (size_t)r * ldv * esz, n, (int64_t)nb * ldv, jused, smr + L.y, x + (size_t)r * n);
       c->launches += 2;
     }
     if (!any) break;

@@ -34,13 +34,14 @@ cudaError_t launch_get_schur(const Params& P, const double* S, int64_t e0, int64
                              cudaStream_t st);
 
 cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
-                           const int* stop, cudaStream_t st);
+                           const int* stop, cudaStream_t st, int epb = 0);
 cudaError_t launch_apply32(const Params& P, const float* S, const float* x, float* y, const double* escale,
                            const int* stop, cudaStream_t st);
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st);
-cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const float2* x, float2* y,
-                             const double* escale, const int* stop, cudaStream_t st, int epb = 0);
+// bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks; vt: 0 FP64 / 1 split-FP32 vectors
+cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void* x, void* y,
+                             const double* escale, const int* stop, cudaStream_t st, int epb = 0, int vt = 1);
 int apply_edges_per_block(const Params& P);
 // Pipelined bulk-copy apply of split-FP32 blocks (q = 1 .. 3 consumer warps
 // per edge); whether it applies to this problem shape; its timeout flag (read
@@ -53,9 +54,10 @@ cudaError_t apply_bulk_take_error(cudaStream_t st, int* err);
 cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
                               int64_t vstride, const double* escale, cudaStream_t st);
 // cmap (optional): compute only the nrhs columns cmap[0 .. nrhs-1] of x and y
-cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const float2* x, float2* y, int nrhs,
-                                 int64_t vstride, const double* escale, float2* Z, cudaStream_t st,
-                                 const int* cmap = nullptr);
+// vt: 0 FP64 / 1 split-FP32 vectors (Z of the same entry type)
+cudaError_t launch_apply_mrhs_el(int bt, const Params& P, const void* S, const void* x, void* y, int nrhs,
+                                 int64_t vstride, const double* escale, void* Z, cudaStream_t st,
+                                 const int* cmap = nullptr, int vt = 1);
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st);
 cudaError_t launch_assemble_rhs(const Params& P, const double* gel, double* g, cudaStream_t st);
 cudaError_t launch_face_dinv(const Params& P, const double* Ghinv, const double* escale, const double* y, double* z,

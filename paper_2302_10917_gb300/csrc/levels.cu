@@ -980,7 +980,7 @@ cudaError_t launch_level_apply(hdg_ctx* c, int bt, int vt, const void* S, const 
   void* z = L.d_z;
 #define LV_CASE(B, V) \
   if (bt == B && vt == V) return lv_apply_r<B, V>(L, S, x, y, nrhs, vstride, escale, stop, z, st, cmap);
-  LV_CASE(0, 0) LV_CASE(0, 1) LV_CASE(1, 0) LV_CASE(1, 1) LV_CASE(2, 1) LV_CASE(2, 2)
+  LV_CASE(0, 0) LV_CASE(0, 1) LV_CASE(1, 0) LV_CASE(1, 1) LV_CASE(2, 0) LV_CASE(2, 1) LV_CASE(2, 2)
 #undef LV_CASE
   return cudaErrorInvalidValue;
 }

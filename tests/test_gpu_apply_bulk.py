@@ -20,6 +20,7 @@ import torch
 
 from oracle.hdg import HDGProblem
 from oracle.precond import face_block_inverse
+from paper_2302_10917_gb300 import BASIS_DF64
 from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -124,10 +125,10 @@ def test_solve_with_the_pipelined_apply(case):
     _set_shape(gpu, 0, 2)
     try:
         x_dir = np.linalg.solve(ora.assemble_S(case["S_el"]), case["g"])
-        x, rep, st = gpu.solve(gpu.rhs(), tol=1e-12, restart=40, mode=2, orth=1)
+        x, rep, st = gpu.solve(gpu.rhs(), tol=1e-12, restart=40, mode=2, orth=1, basis=BASIS_DF64)
         assert st == 0 and rep["converged"] == 1, rep
         assert rel(x.cpu().numpy(), x_dir) < 1e-8
-        x2, _, _ = gpu.solve(gpu.rhs(), tol=1e-12, restart=40, mode=2, orth=1)
+        x2, _, _ = gpu.solve(gpu.rhs(), tol=1e-12, restart=40, mode=2, orth=1, basis=BASIS_DF64)
         assert torch.equal(x, x2)
     finally:
         gpu.set_apply_shape(2)
@@ -242,8 +243,11 @@ def test_shape_errors_and_autotune_report():
         x = split(np.ones(gpu.info["N_tr"]))
         with pytest.raises(HDGError):
             gpu.apply(x, precond=False, prec=49)
+        # the pipelined shape is a candidate with the split-FP32 basis only
+        assert gpu.autotune(mode=2, restart=20)["apply_bulk"] == 0
         for mode in (0, 1, 2):
-            rep = gpu.autotune(mode=mode, restart=20)
+            basis = BASIS_DF64 if mode == 2 else 0
+            rep = gpu.autotune(mode=mode, restart=20, basis=basis)
             if mode == 2:
                 assert rep["apply_bulk_ms"] > 0 and rep["apply_bulk"] in (0, 1, 2, 3)
                 if rep["apply_bulk"]:
@@ -251,7 +255,7 @@ def test_shape_errors_and_autotune_report():
                     assert rep["apply_threads"] % 32 == 0
             else:
                 assert rep["apply_bulk"] == 0 and rep["apply_bulk_ms"] == 0
-            x_s, r, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=20, mode=mode)
+            x_s, r, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=20, mode=mode, basis=basis)
             assert st == 0 and r["converged"] == 1
     finally:
         gpu.close()

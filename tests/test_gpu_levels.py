@@ -110,23 +110,25 @@ def test_schur_blocks_and_rhs_match_the_oracle(case):
     assert np.array_equal(part, S[off[3]:off[7]])
 
 
-@pytest.mark.parametrize("prec", [64, 48, 32])
+@pytest.mark.parametrize("prec", [64, 48, 33, 32])
 def test_apply_matches_the_oracle(case, prec):
     ora, gpu = case["ora"], case["gpu"]
     Sg = ora.assemble_S(case["S"])
     x = case["rng"].standard_normal(ora.N_tr)
-    tol = 1e-6 if prec == 32 else 1e-12
+    tol = 1e-6 if prec in (32, 33) else 1e-12
     yp = gpu.apply(torch.from_numpy(x), precond=True, prec=prec).double().cpu().numpy()
     assert rel(yp, ora.apply_Dinv(Sg @ x)) < tol
     if prec == 64:
         assert rel(gpu.apply(torch.from_numpy(x)).cpu().numpy(), Sg @ x) < 1e-12
 
 
+@pytest.mark.parametrize("basis", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_solve_and_recover_match_the_oracle(case, mode):
+def test_solve_and_recover_match_the_oracle(case, mode, basis):
+    """Every operator precision with the FP64 (basis 0) and split-FP32 (1) Krylov basis."""
     ora, gpu = case["ora"], case["gpu"]
     x_dir = np.linalg.solve(ora.assemble_S(case["S"]), case["g"])
-    x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60, mode=mode, maxit=20000)
+    x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60, mode=mode, maxit=20000, basis=basis)
     assert st == 0, rep
     assert rel(x.cpu().numpy(), x_dir) < 1e-9
     u, q = gpu.recover(x)

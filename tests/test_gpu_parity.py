@@ -15,6 +15,7 @@ import torch
 
 from oracle.hdg import HDGProblem
 from oracle.problems import polynomial, random_polynomial
+from paper_2302_10917_gb300 import BASIS_DF64, BASIS_FP64
 from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -141,6 +142,16 @@ def test_fp32_preconditioned_apply(case):
     assert rel(z32, z_ora) < 5e-5
 
 
+def test_fp32_blocks_on_fp64_vectors_apply(case):
+    """prec = 33: the FP32 blocks on FP64 vectors, the Arnoldi operator of mode 1 with the
+    FP64 Krylov basis (the mixed-precision form): FP32 products and sums, FP64 in and out."""
+    ora, gpu, S_el = case["ora"], case["gpu"], case["S_el"]
+    x = case["rng"].standard_normal(ora.mesh.N_tr)
+    z_ora = ora.apply_Dinv(ora.apply_S(S_el, x))
+    z33 = gpu.apply(torch.from_numpy(x), precond=True, prec=33).cpu().numpy()
+    assert rel(z33, z_ora) < 5e-5
+
+
 def test_split_fp32_preconditioned_apply(case):
     """Blocks stored as FP32 hi/lo pairs, products on the FP32 pipe: FP64-level agreement."""
     ora, gpu, S_el = case["ora"], case["gpu"], case["S_el"]
@@ -160,6 +171,8 @@ def test_recover_from_same_trace(case):
 
 
 def test_gmres_solution_matches_direct_solve(case):
+    """The all-FP64 solve (FP64 blocks, FP64 Krylov basis and orthogonalisation, the
+    default options) against the oracle's direct solve of the assembled S."""
     ora, gpu = case["ora"], case["gpu"]
     S = ora.assemble_S(case["S_el"])
     x_dir = np.linalg.solve(S, case["g"])
@@ -176,50 +189,56 @@ def test_gmres_solution_matches_direct_solve(case):
     assert rel(q_g.cpu().numpy(), q_o) < 1e-7
 
 
-def test_gmres_split_fp32_apply_mode(case):
-    """mode 2: FP64 GMRES with the split-FP32 preconditioned apply; the FP64 residual decides."""
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+def test_gmres_split_fp32_apply_mode(case, basis):
+    """mode 2: GMRES with the split-FP32 preconditioned apply; the FP64 residual decides."""
     ora, gpu = case["ora"], case["gpu"]
     S = ora.assemble_S(case["S_el"])
     x_dir = np.linalg.solve(S, case["g"])
-    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=2)
+    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=2, basis=basis)
     assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10
     x_gpu = x_gpu.cpu().numpy()
     assert np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) <= 1.01e-10
     assert rel(x_gpu, x_dir) < 1e-8
 
 
-def test_gmres_fp32_iterative_refinement_mode(case):
-    """mode 1: FP32 blocks inside FP64 iterative refinement still reach the FP64 residual."""
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+def test_gmres_fp32_iterative_refinement_mode(case, basis):
+    """mode 1: FP32 blocks inside FP64 iterative refinement still reach the FP64 residual
+    (with BASIS_FP64: the mixed-precision form with FP64 orthogonalisation)."""
     ora, gpu = case["ora"], case["gpu"]
     S = ora.assemble_S(case["S_el"])
     x_dir = np.linalg.solve(S, case["g"])
-    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=20000, mode=1)
+    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=20000, mode=1, basis=basis)
     assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10 and rep["outer"] >= 1
     x_gpu = x_gpu.cpu().numpy()
     assert np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) <= 1.01e-10
     assert rel(x_gpu, x_dir) < 1e-8
 
 
-@pytest.mark.parametrize("orth", [1, 2])
-def test_gmres_single_projection_variants(case, orth):
-    """orth = 1 (one projection, norm from Pythagoras) and orth = 2 (a second projection
-    where the first removed more than half of the new vector): same solution, same residual."""
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+@pytest.mark.parametrize("orth", [1, 2, 3])
+def test_gmres_single_projection_variants(case, orth, basis):
+    """orth = 1 (one projection, norm from Pythagoras), orth = 2 (a second projection
+    where the first removed more than half of the new vector) and orth = 3 (a second
+    projection where the first cancelled more than six digits): same solution, same residual."""
     ora, gpu = case["ora"], case["gpu"]
     S = ora.assemble_S(case["S_el"])
     x_dir = np.linalg.solve(S, case["g"])
     for mode in (0, 2):
-        x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth)
+        x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth, basis=basis)
         assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10, (mode, rep)
         x_gpu = x_gpu.cpu().numpy()
         assert abs(np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) - rep["rel_residual"]) < 1e-12
         assert rel(x_gpu, x_dir) < 1e-8
 
 
-def test_solve_is_bitwise_reproducible(case):
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+def test_solve_is_bitwise_reproducible(case, basis):
     gpu = case["gpu"]
     g = gpu.rhs()
-    x1, r1, _ = gpu.solve(g, tol=1e-10, restart=20, maxit=3000)
-    x2, r2, _ = gpu.solve(g, tol=1e-10, restart=20, maxit=3000)
+    x1, r1, _ = gpu.solve(g, tol=1e-10, restart=20, maxit=3000, basis=basis)
+    x2, r2, _ = gpu.solve(g, tol=1e-10, restart=20, maxit=3000, basis=basis)
     assert torch.equal(x1, x2) and r1 == r2
 
 
