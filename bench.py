@@ -72,6 +72,9 @@ def parse_args(argv=None):
                     help="skip the many-source and gradient measurements that follow the main line")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the whole-step comparison of the precision forms and preconditioners")
+    ap.add_argument("--no-keep-factors", action="store_true",
+                    help="do not keep the factored local systems (the back-solve condenses again; small device "
+                         "footprint for profiler captures)")
     ap.add_argument("--n", type=int, default=0,
                     help="macro squares per side instead of the workload's (small cases for profiler captures)")
     return ap.parse_args(argv)
@@ -183,7 +186,7 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_sample(cfg_name, n_cond, n_apply_elems, applies_per_step):
+def oracle_sample(cfg_name, n_cond, n_apply_elems, applies_per_step, seed=0):
     """Time the oracle on a bounded sample of the workload, extrapolate one step.
 
     The oracle condenses n_cond sampled macro-elements (dense LU of the full
@@ -197,7 +200,7 @@ def oracle_sample(cfg_name, n_cond, n_apply_elems, applies_per_step):
     cfg = wl.CONFIGS[cfg_name]
     ora = HDGProblem(cfg["n"], cfg["m"], cfg["p"], beta=cfg["beta"], kappa=cfg["kappa"])
     msh = ora.mesh
-    rng = np.random.default_rng([wl.MASTER_SEED, 99])
+    rng = np.random.default_rng([wl.MASTER_SEED, 99, seed])
     els = rng.choice(msh.N, size=n_cond + 1, replace=False)
     # one untimed element first: the oracle builds its quadrature and basis caches on first use
     ora.condense_element(int(els[-1]))
@@ -231,29 +234,73 @@ def oracle_sample(cfg_name, n_cond, n_apply_elems, applies_per_step):
 def oracle_sample_one_thread(cfg_name, n_cond, n_apply_elems, applies_per_step):
     """oracle_sample in a fresh interpreter whose BLAS / OpenMP pools have one thread
     (so the reported core count is the one used); raises if the child fails."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
     code = ("import json, bench; print(json.dumps(bench.oracle_sample(%r, %d, %d, %d)))"
             % (cfg_name, n_cond, n_apply_elems, applies_per_step))
-    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                         timeout=600)
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=_one_thread_env(), capture_output=True,
+                         text=True, timeout=600)
     if res.returncode != 0:
         raise RuntimeError(res.stderr[-400:])
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
+def _one_thread_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                CUDA_VISIBLE_DEVICES="")
+
+
+def oracle_sample_all_cores(cfg_name, cores, n_cond, n_apply_elems, applies_per_step):
+    """The oracle sample on every host core at once: `cores` single-threaded interpreters, each
+    on its own seeded element sample, started together. Their per-element times under full load
+    give the oracle's throughput on the whole host: one step = N (t_cond + applies t_apply +
+    t_recover) / cores."""
+    code = ("import json, sys, bench; print(json.dumps(bench.oracle_sample(%r, %d, %d, %d, int(sys.argv[1]))))"
+            % (cfg_name, n_cond, n_apply_elems, applies_per_step))
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(i + 1)], cwd=ROOT, env=_one_thread_env(),
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for i in range(cores)]
+    outs = []
+    for pr_ in procs:
+        out, err = pr_.communicate(timeout=900)
+        if pr_.returncode != 0:
+            raise RuntimeError(err[-400:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    mean = lambda k: statistics.mean(o[k] for o in outs)
+    N, N_tr = outs[0]["N"], outs[0]["N_tr"]
+    step_s = N * (mean("t_condense_elem_s") + applies_per_step * mean("t_apply_elem_s") +
+                  mean("t_recover_elem_s")) / cores
+    return {"step_s": step_s, "value": N_tr * applies_per_step / step_s / 1e9, "N": N}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(cfg_name, applies_per_step):
-    """Run the oracle sample in a fresh single-threaded interpreter."""
+    """The oracle on the host: in a fresh single-threaded interpreter, and on every core at once."""
     try:
         r = oracle_sample_one_thread(cfg_name, CPU_SAMPLE_COND, CPU_SAMPLE_APPLY, applies_per_step)
     except (RuntimeError, subprocess.TimeoutExpired, ValueError, IndexError) as exc:
         return {"value": None, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "error": str(exc)[-400:]}
-    return {"value": r["value"], "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (numpy, 1 thread) condensing {CPU_SAMPLE_COND} sampled macro-elements (dense LU "
-                       f"of the 975x975 local system each), {CPU_SAMPLE_APPLY} element-wise Schur applies and "
-                       f"{CPU_SAMPLE_COND} element back-solves, extrapolated to one step: 32768 condensations + "
-                       f"{applies_per_step} applies of all elements + 32768 back-solves"),
-            "step_s_extrapolated": r["step_s"]}
+    out = {"value": r["value"], "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+           "sample": (f"oracle (numpy, 1 thread) condensing {CPU_SAMPLE_COND} sampled macro-elements (dense LU "
+                      f"of the 975x975 local system each), {CPU_SAMPLE_APPLY} element-wise Schur applies and "
+                      f"{CPU_SAMPLE_COND} element back-solves, extrapolated to one step: 32768 condensations + "
+                      f"{applies_per_step} applies of all elements + 32768 back-solves"),
+           "step_s_extrapolated": r["step_s"]}
+    cores = host_cores()
+    nc, na = max(2, CPU_SAMPLE_COND // 4), max(5000, CPU_SAMPLE_APPLY // 4)
+    try:
+        ra = oracle_sample_all_cores(cfg_name, cores, nc, na, applies_per_step)
+        out["all_cores"] = {"value": ra["value"], "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+                            "sample": (f"{cores} single-threaded oracle processes at once, each condensing {nc} "
+                                       f"sampled macro-elements, {na} element-wise applies and {nc} back-solves; "
+                                       "one step extrapolated from their per-element times under full load"),
+                            "step_s_extrapolated": ra["step_s"]}
+    except (RuntimeError, subprocess.TimeoutExpired, ValueError, IndexError, OSError) as exc:
+        out["all_cores"] = {"value": None, "cores": cores, "error": str(exc)[-400:]}
+    return out
 
 
 # ---------------------------------------------------------------- reference
@@ -322,7 +369,8 @@ def run_ours(args):
 
     def condense_flags(mode, split_update):
         # only the blocks the solve mode needs
-        return dict(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split_update)
+        return dict(keep_factors=not args.no_keep_factors, store_fp32=(mode == 1), store_df64=(mode == 2),
+                    split_update=split_update)
 
     def step(rec=None, mode=args.mode, basis=args.basis, split_update=split, precond="d"):
         marks = [ev() for _ in range(4)] if rec is not None else None
@@ -420,6 +468,10 @@ def run_ours(args):
                            "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
                            "hbm_frac_at_fp64_peak": fp64_ceiling / hbm_peak}
     rc = rooflines["condense"]
+    # one condensation per step (several launches when the factors are not kept: chunks)
+    cond_ms = prof["condense"][1] / max(1, args.steps)
+    rc["avg_launch_ms"] = cond_ms
+    rc["note"] = "per condensation of all elements (launches per step: %d)" % (prof["condense"][0] // max(1, args.steps))
     if split:
         rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=DF_PEAK_TFLOPS, unit="TFLOP/s",
                   algorithmic_per_launch=cond_flops,
@@ -593,7 +645,7 @@ def bench_multi_rhs(stream, count=64):
     pr.condense(keep_factors=True, store_df64=True, split_update=True)
     g = pr.rhs()
     b.record(stream)
-    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=3, basis=1, maxit=40000)
     c2.record(stream)
     u, q = pr.recover(x)
     d.record(stream)
@@ -604,11 +656,11 @@ def bench_multi_rhs(stream, count=64):
     p1.set_source(f[0])
     p1.condense(keep_factors=True, store_df64=True, split_update=True)
     g1 = p1.rhs()
-    p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
+    p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=3, basis=1)
     e0, e1 = ev(), ev()
     torch.cuda.synchronize()
     e0.record(stream)
-    x1, rep1, st1 = p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
+    x1, rep1, st1 = p1.solve(g1, tol=1e-10, restart=80, mode=2, orth=3, basis=1)
     e1.record(stream)
     torch.cuda.synchronize()
     single_s = e0.elapsed_time(e1) / 1e3
@@ -653,7 +705,7 @@ def bench_levels_many_source(stream, count=64):
     pr.condense(**flags)
     g = pr.rhs()
     b.record(stream)
-    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=3, basis=1, maxit=40000)
     c2.record(stream)
     u, q = pr.recover(x)
     d.record(stream)
@@ -794,8 +846,8 @@ def _lattice_nodes(n, m, p, device):
 
 
 def bench_macro_vs_standard(stream):
-    """The paper's comparison (Sec. 4, Tables 8 and 10) in 2D: the same 65 536 sub-triangles
-    of degree 3 as n = 32 macro-squares with m = 8 (macro-element HDG) and as n = 256 squares
+    """The paper's comparison with standard HDG (Sec. 5.3; Tables 8 and 10 of Sec. 6.3-6.4) in 2D:
+    the same 65 536 sub-triangles of degree 3 as n = 32 macro-squares with m = 8 (macro-element HDG) and as n = 256 squares
     with m = 1 (standard HDG), beta = 50 (cos 0.3, sin 0.3), kappa = 1, u = sin(pi x) sin(pi y);
     GMRES(80), split-FP32 operator, to 1e-10."""
     import math
@@ -811,7 +863,7 @@ def bench_macro_vs_standard(stream):
         pr.set_source(f)
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
         g = pr.rhs()
-        pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1)      # warm-up (graph capture)
+        pr.solve(g, tol=1e-10, restart=80, mode=2, orth=3, basis=1)      # warm-up (graph capture)
         a, b, c2 = ev(), ev(), ev()
         torch.cuda.synchronize()
         a.record(stream)
@@ -819,7 +871,7 @@ def bench_macro_vs_standard(stream):
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
         g = pr.rhs()
         b.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=2, basis=1)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, mode=2, orth=3, basis=1)
         c2.record(stream)
         u, q = pr.recover(x)
         torch.cuda.synchronize()
@@ -850,7 +902,7 @@ def bench_supg_layer(stream):
         gD = wl.tanh_layer_exact(pr.bnd_quad_points(), kap).contiguous()
         pr.set_source(f, gD)
         pr.condense(keep_factors=True, store_df64=True, split_update=True)
-        x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, mode=2, orth=2, basis=1, maxit=40000, check=False)
+        x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, mode=2, orth=3, basis=1, maxit=40000, check=False)
         u, q = pr.recover(x)
         out["supg" if supg else "plain"] = {"u_min": float(u.min()), "u_max": float(u.max()),
                                             "overshoot": float(max(u.max() - 1.0, -u.min(), 0.0)),
@@ -861,7 +913,7 @@ def bench_supg_layer(stream):
     return out
 
 
-def bench_gradient(stream):
+def bench_gradient(stream, fd_directions=20):
     """Adjoint gradient of J = 1/2 |u - u_obs|^2 (nodal) with respect to the per-element
     diffusivities and the source, n=256, m=4, p=2, beta=(1,0.5), kappa_e = exp(GRF); forward
     and adjoint GMRES(128) with the face blocks of S (with D^-1 the solve stalls at this size)."""
@@ -873,7 +925,7 @@ def bench_gradient(stream):
     kobs = torch.from_numpy(wl.grf_kappa(n, 1001)).cuda()
     pr = Problem(n, m, p, beta=beta, kappa=kap.cpu().numpy(), stream=stream)
     f = wl.sin_sin_source(pr.quad_points(), 1.0, beta).contiguous()
-    opts = dict(tol=1e-10, restart=128, mode=2, split_update=True, orth=2, basis=1, precond="face_schur", maxit=60000)
+    opts = dict(tol=1e-10, restart=128, mode=2, split_update=True, orth=3, basis=1, precond="face_schur", maxit=60000)
     with torch.no_grad():
         u_obs = solve_u(pr, kobs, f, **opts).clone()      # also the warm-up (graph capture)
     times = []
@@ -892,8 +944,50 @@ def bench_gradient(stream):
                        "J = 1/2 |u - u_obs|^2 nodal; face-block preconditioner", "N_tr": pr.info["N_tr"],
            "forward_s": times[-1][0], "backward_s": times[-1][1], "J": float(J.detach()),
            "grad_kappa_norm": float(k.grad.norm()), "grad_f_norm": float(ff.grad.norm())}
+    if fd_directions > 0:
+        out["finite_differences"] = gradient_fd_check(pr, kap, f, u_obs, k.grad, ff.grad, opts, fd_directions)
     pr.close()
     return out
+
+
+def gradient_fd_check(pr, kap, f, u_obs, gk, gf, opts, count, h=1e-3):
+    """Central differences of J along `count` seeded directions (d_kappa, d_f) at once:
+    kappa_e (1 + h z_e) and f + h |f|_max w, J(+) - J(-) over 2h against the adjoint
+    gradient's dJ/dkappa . (kappa z) + dJ/df . (|f|_max w). Each perturbed solve starts from
+    the unperturbed trace solution (same solve options as the gradient)."""
+    import torch
+    from paper_2302_10917_gb300 import workloads as wl
+    fmax = float(f.abs().max())
+    Z = torch.from_numpy(wl.random_directions(count, tuple(kap.shape), seed=5)).cuda()
+    Wd = torch.from_numpy(wl.random_directions(count, tuple(f.shape), seed=6)).cuda()
+    sk = dict(tol=opts["tol"], restart=opts["restart"], mode=opts["mode"], orth=opts["orth"],
+              basis=opts["basis"], maxit=opts["maxit"])
+
+    def J_of(kk, fv, x0):
+        pr.set_kappa(kk)
+        pr.set_source(fv)
+        pr.condense(keep_factors=True, store_df64=opts["mode"] == 2, store_fp32=opts["mode"] == 1,
+                    split_update=opts["split_update"], precond=opts["precond"])
+        x, rep, st = pr.solve(pr.rhs(), x0=x0, **sk)
+        if st != 0:
+            raise RuntimeError(f"finite-difference solve did not converge: {rep}")
+        u, _ = pr.recover(x)
+        return 0.5 * float(((u - u_obs) ** 2).sum()), x
+
+    t0 = time.perf_counter()
+    _, x_base = J_of(kap, f, None)
+    devs, rows = [], []
+    for i in range(count):
+        dk, df = kap * Z[i], fmax * Wd[i]
+        jp, _ = J_of(kap + h * dk, f + h * df, x_base)
+        jm, _ = J_of(kap - h * dk, f - h * df, x_base)
+        fd = (jp - jm) / (2.0 * h)
+        ad = float((gk * dk).sum() + (gf * df).sum())
+        devs.append(abs(fd - ad) / abs(ad))
+        rows.append({"fd": fd, "adjoint": ad})
+    return {"directions": count, "h": h, "max_rel_deviation": max(devs), "median_rel_deviation":
+            statistics.median(devs), "seconds": time.perf_counter() - t0, "first": rows[:3],
+            "directions_def": "kappa_e (1 + h z_e), f + h |f|_max w; z, w seeded standard normal"}
 
 
 def main(argv=None):

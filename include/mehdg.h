@@ -60,7 +60,7 @@
  * Nothing here falls back to the CPU: without a usable sm_103a device every
  * entry point that launches work returns HDG_ERR_CUDA.
  *
- * Level meshes (Sec. 5.3, local adaptive refinement; hdg_mesh_desc.level)
+ * Level meshes (Sec. 4.2, local adaptive refinement; hdg_mesh_desc.level)
  * ------------------------------------------------------------------------
  * Element e carries its own level r_e (0 <= r_e <= 4, m_e = 2^r_e and the
  * level-m_e lattice inside); interior edge f carries the level R_f =
@@ -142,6 +142,9 @@ typedef struct {
   int64_t n_bqp_total;   /* Dirichlet-data points per right-hand side */
   int64_t n_u_total;     /* lattice values of u per right-hand side */
   int64_t n_s_total;     /* Schur-block entries */
+  int64_t bounds_error;  /* library built with -DHDG_BOUNDS_CHECK: site code of the first device index check
+                            that failed since hdg_create (the access it guarded was skipped), 0 if none;
+                            always 0 in the regular build */
 } hdg_info_t;
 
 /* Solve options. Every restart cycle starts from the true FP64 residual
@@ -203,7 +206,8 @@ typedef struct {
  * Errors: HDG_ERR_ARG for an invalid descriptor, HDG_ERR_CUDA/OOM. */
 hdg_status hdg_create(const hdg_mesh_desc* desc, void* stream, hdg_ctx** out);
 
-/* Sizes of the problem and the context's device memory (host struct). */
+/* Sizes of the problem and the context's device memory (host struct).
+ * Synchronises the context's stream (it reads the bounds-check word). */
 hdg_status hdg_info(const hdg_ctx* ctx, hdg_info_t* out);
 
 /* Prefix sums of a ragged layout (host array, count + 1 entries): which =
@@ -288,6 +292,19 @@ hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int
  * HDG_ERR_ARG for a shape that does not apply (the context is unchanged). */
 hdg_status hdg_set_apply_shape(hdg_ctx* ctx, int mode, int edges_per_block, int bulk_warps);
 
+/* Bounded device waits (no counterpart in the paper; project-written). The
+ * pipelined apply (hdg_set_apply_shape bulk_warps) waits on shared-memory
+ * barriers for its bulk copies; every such wait gives up after wait_cycles
+ * SM clock cycles (0 restores the built-in limit of 2e9 cycles, about one
+ * second), records the failure, lets the copies it issued land (bounded again)
+ * and returns, and the entry point that launched it reports HDG_ERR_TIMEOUT;
+ * the context stays usable. skip_copy_edge >= 0 is a test hook for exactly
+ * that path: the row-block copies of that interior edge are not issued, so
+ * the waits for them run out; -1 (the state after hdg_create) issues every
+ * copy. Applies from the next launch; no device work. HDG_ERR_ARG for
+ * wait_cycles < 0 or skip_copy_edge outside -1 .. interior edges - 1. */
+hdg_status hdg_set_wait_hooks(hdg_ctx* ctx, int64_t wait_cycles, int64_t skip_copy_edge);
+
 /* Solve S x = g (Eq. global_problem) with restarted GMRES, left-
  * preconditioned by D^-1 (Sec. 6.1). x_dev holds the initial guess on entry
  * and the solution on exit ([N_tr] FP64). report may be NULL.
@@ -325,17 +342,19 @@ hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_
  * It condenses elements e0 .. e0+count-1 exactly like hdg_condense, but the
  * local factorisations use a fixed scratch array compiled into the library
  * (MEHDG_STATIC_SCRATCH_BYTES, held on every GPU that loads the library until
- * the process exits) and the results go to caller buffers: S_dev receives
- * S_e row-major [count][n_t][n_t] (same layout as hdg_get_schur) and g_dev,
- * if not NULL, the element right-hand sides -C_e A_e^-1 R_e - S_e g^_e
- * [count][n_t]. Requires hdg_set_source; needs no hdg_condense and does not
- * change the context's stored blocks. count is limited to
- * MEHDG_STATIC_SCRATCH_BYTES / ((Q + n_t) * ld * 8) elements (ld = Q + n_t + 1
- * rounded up to a multiple of 4); a larger count returns HDG_ERR_ARG with the
- * limit in the message. The first call on a device looks up the scratch
- * array's device address (once per device), so make that first call before
- * any stream capture. Every call shares the array and leaves its contents
- * behind; calls that overlap on the GPU race on it. Synchronous (it reads a
+ * the process exits; hdg_create loads it on its device, so it is set aside
+ * when a context is created, not at the first call) and the results go to
+ * caller buffers: S_dev receives S_e row-major [count][n_t][n_t] (same layout
+ * as hdg_get_schur) and g_dev, if not NULL, the element right-hand sides
+ * -C_e A_e^-1 R_e - S_e g^_e of every source of hdg_set_source,
+ * [nrhs][count][n_t]. Requires hdg_set_source; needs no hdg_condense and does
+ * not change the context's stored blocks. count is limited to
+ * MEHDG_STATIC_SCRATCH_BYTES / ((Q + n_t) * ld * 8) elements (ld = Q + n_t +
+ * nrhs rounded up to a multiple of 4); a larger count returns HDG_ERR_ARG
+ * with the limit in the message. Each call looks up the array's device
+ * address in the current context (no allocation); do not call it inside a
+ * stream capture. Every call shares the array and leaves its contents behind;
+ * calls that overlap on the GPU race on it. Synchronous (it reads a
  * zero-pivot flag back): HDG_ERR_SINGULAR if a local pivot is zero. */
 #define MEHDG_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 hdg_status hdg_condense_static(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev, double* g_dev);

@@ -18,7 +18,7 @@ It is a slow, literal restatement of the paper's discrete problem:
 * GMRES (Section 6.1) and the local back-solve Eq. (local_matrix_problem);
 * the counting formulas of Section 5 (Tables 1-2);
 * macro-elements of uneven refinement level with faces at the finer side's
-  level (Section 5.3, ``levels.py``);
+  level (Section 4.2, ``levels.py``);
 * the face-block preconditioner (the inverted diagonal face blocks of the
   condensed operator, not in the paper; ``precond.py``).
 

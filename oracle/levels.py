@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Sec. 5.3 (local adaptive refinement): every macro-element K carries its own
+Sec. 4.2 (local adaptive refinement): every macro-element K carries its own
 level r_K, i.e. m_K = 2^r_K sub-edges per macro-edge and the C0 lattice of
 that level inside. The trace space of a macro-face F is refined to its finer
 side, level R_F = max(r+, r-), so that it holds the trace of either side

@@ -25,7 +25,7 @@ EXPORTED = ["hdg_create", "hdg_info", "hdg_quad_points", "hdg_bnd_quad_points", 
             "hdg_condense", "hdg_rhs", "hdg_apply", "hdg_solve", "hdg_recover", "hdg_get_schur",
             "hdg_run_host", "hdg_profile", "hdg_profile_read", "hdg_condense_static", "hdg_set_kappa",
             "hdg_transpose", "hdg_adjoint_rhs", "hdg_adjoint_recover", "hdg_gradient", "hdg_autotune",
-            "hdg_set_apply_shape",
+            "hdg_set_apply_shape", "hdg_set_wait_hooks",
             "hdg_offsets", "hdg_last_error",
             "hdg_destroy"]
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
@@ -45,7 +45,7 @@ class Info(ctypes.Structure):
                 ("n_bnd_edges", ctypes.c_int64), ("n_qp", ctypes.c_int64), ("n_bqp", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_int64), ("levels", ctypes.c_int64),
                 ("n_qp_total", ctypes.c_int64), ("n_bqp_total", ctypes.c_int64), ("n_u_total", ctypes.c_int64),
-                ("n_s_total", ctypes.c_int64)]
+                ("n_s_total", ctypes.c_int64), ("bounds_error", ctypes.c_int64)]
 
 
 # ragged-layout tables of hdg_offsets
@@ -118,6 +118,7 @@ def load_library(path=LIB_PATH):
     lib.hdg_gradient.argtypes = [vp, dp, dp, dp, dp, dp, dp]
     lib.hdg_autotune.argtypes = [vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(TuneReport)]
     lib.hdg_set_apply_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.hdg_set_wait_hooks.argtypes = [vp, i64, i64]
     lib.hdg_profile.argtypes = [vp, ctypes.c_int]
     lib.hdg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     lib.hdg_last_error.argtypes = [vp]
@@ -139,7 +140,7 @@ class Problem:
     """One macro-element HDG problem on the structured unit-square mesh (one GPU).
 
     levels: None (every element of level m), or N per-element refinement levels r_e in 0..4
-    (m_e = 2^r_e; faces at the finer side's level, Sec. 5.3). On such a level mesh every
+    (m_e = 2^r_e; faces at the finer side's level, Sec. 4.2). On such a level mesh every
     per-element array is ragged (flat, element-ordered; offsets())."""
 
     def __init__(self, n, m, p, beta=(0.0, 0.0), kappa=1.0, tau_len=1.0, device="cuda:0", stream=None,
@@ -196,6 +197,13 @@ class Problem:
         info = Info()
         self._check(self.lib.hdg_info(self.h, ctypes.byref(info)))
         return info.launches
+
+    def bounds_error(self):
+        """Site code of the first failed device index check since hdg_create (a library built
+        with -DHDG_BOUNDS_CHECK), 0 if none; always 0 with the regular build."""
+        info = Info()
+        self._check(self.lib.hdg_info(self.h, ctypes.byref(info)))
+        return info.bounds_error
 
     def profile(self, enable=True):
         """Start (clears totals) or stop per-phase CUDA-event timing in the library."""
@@ -304,6 +312,11 @@ class Problem:
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):
             self._check(st)
         return x, r.as_dict(), st
+
+    def set_wait_hooks(self, wait_cycles=0, skip_copy_edge=-1):
+        """hdg_set_wait_hooks: the limit of the pipelined apply's bounded waits and its
+        copy-skip test hook."""
+        self._check(self.lib.hdg_set_wait_hooks(self.h, int(wait_cycles), int(skip_copy_edge)))
 
     def set_apply_shape(self, mode, edges_per_block=0, bulk_warps=0):
         """hdg_set_apply_shape: the apply's launch shape inside solves of this mode."""

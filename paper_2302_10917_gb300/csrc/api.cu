@@ -6,7 +6,19 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <nvtx3/nvToolsExt.h>
 #include "launch.h"
+
+// Tracing: every phase entry point is an NVTX range (header-only NVTX; the
+// calls do nothing unless a profiler or tracing tool is attached).
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace mehdg;
 
@@ -211,6 +223,11 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
     *out = c;
     return set_err(c, HDG_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
   }
+  // the bounds-checked build's error word (one int; zero in the regular build)
+  if ((e = dev_alloc(c, &c->d_oob, 1)) != cudaSuccess || (e = cudaMemset(c->d_oob, 0, sizeof(int))) != cudaSuccess) {
+    *out = c;
+    return cuda_err(c, e, "bounds word");
+  }
   if (d->level) {
     // per-element refinement levels: kappa here, everything else in the level mesh
     *out = c;
@@ -233,6 +250,7 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   }
   const RefTables& T = c->ref;
   Params& P = c->prm;
+  P.oob = c->d_oob;
   P.n = d->n; P.m = d->m; P.p = d->p; P.P = T.P; P.P1 = T.P1; P.Q = T.Q; P.n_t = T.n_t;
   P.N = (int)N;
   P.n_int = (int)n_int;
@@ -265,6 +283,8 @@ hdg_status hdg_create(const hdg_mesh_desc* d, void* stream, hdg_ctx** out) {
   if ((e = cudaMemsetAsync(c->d_ghat, 0, (size_t)P.n_bnd * P.P1 * 8, c->stream)) != cudaSuccess)
     return cuda_err(c, e, "ghat");
   c->alloc_nrhs = 1;
+  // hdg_condense_static's scratch array exists from here on (its module is loaded now, not at its first call)
+  if ((e = static_scratch_prepare()) != cudaSuccess) return cuda_err(c, e, "static scratch array");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_err(c, e, "create");
   return HDG_OK;
 }
@@ -294,6 +314,15 @@ hdg_status hdg_info(const hdg_ctx* c, hdg_info_t* out) {
     out->n_bqp_total = (int64_t)P.n_bnd * P.n_bqp;
     out->n_u_total = (int64_t)P.N * P.Q;
     out->n_s_total = (int64_t)P.N * P.n_t * P.n_t;
+  }
+  out->bounds_error = 0;
+  if (c->d_oob) {
+    // the first failing index check of the bounds-checked build (synchronises the stream)
+    int code = 0;
+    if (cudaMemcpyAsync(&code, c->d_oob, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return HDG_ERR_CUDA;
+    out->bounds_error = code;
   }
   return HDG_OK;
 }
@@ -361,6 +390,7 @@ hdg_status hdg_bnd_quad_points(const hdg_ctx* cc, double* xy) {
 }
 
 hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, int nrhs) {
+  NvtxRange nvtx_range("hdg_set_source");
   if (!c) return HDG_ERR_ARG;
   if (!c->d_tables) return set_err(c, HDG_ERR_STATE, "context not initialised");
   if (!f_qp || nrhs < 1 || nrhs > HDG_MAX_RHS)
@@ -408,6 +438,7 @@ hdg_status hdg_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp, i
 }
 
 hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
+  NvtxRange nvtx_range("hdg_condense");
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
   if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE | HDG_PRECOND_FACE_SCHUR))
@@ -513,6 +544,7 @@ hdg_status hdg_rhs(hdg_ctx* c, double* g) {
 }
 
 hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int precond) {
+  NvtxRange nvtx_range("hdg_apply");
   if (!c) return HDG_ERR_ARG;
   if (!x || !y || x == y || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad x/y or nrhs");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_apply before hdg_condense");
@@ -523,8 +555,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     if (c->lv || nrhs != 1) return set_err(c, HDG_ERR_ARG, "prec 49 is the one-column operator of a uniform mesh");
     if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
     const int epb = c->tune_epb[1];
-    e = launch_apply_vdf(1, c->prm, c->d_Stdf, static_cast<const float2*>(x), static_cast<float2*>(y), precond_scale(c),
-                         nullptr, c->stream, epb);
+    e = launch_apply_vdf(1, c->prm, c->d_Stdf, x, y, precond_scale(c), nullptr, c->stream, epb, 1, &c->bulk_hooks);
     c->launches += 1;
     if (e == cudaSuccess && epb < 0) {
       int err = 0;
@@ -591,6 +622,15 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
 }
 
+hdg_status hdg_set_wait_hooks(hdg_ctx* c, int64_t wait_cycles, int64_t skip_copy_edge) {
+  if (!c) return HDG_ERR_ARG;
+  if (wait_cycles < 0 || skip_copy_edge < -1 || skip_copy_edge >= c->prm.n_int)
+    return set_err(c, HDG_ERR_ARG, "wait_cycles >= 0 and -1 <= skip_copy_edge < interior edges");
+  c->bulk_hooks.wait_cycles = (long long)wait_cycles;
+  c->bulk_hooks.skip_edge = (int)skip_copy_edge;
+  return HDG_OK;
+}
+
 hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bulk_warps) {
   if (!c) return HDG_ERR_ARG;
   if (mode < 0 || mode > 2 || edges_per_block < 0 || bulk_warps < 0 || (edges_per_block > 0 && bulk_warps > 0))
@@ -606,6 +646,7 @@ hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bu
 
 hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg_solve_opts* o,
                      hdg_solve_report* rep) {
+  NvtxRange nvtx_range("hdg_solve");
   if (!c) return HDG_ERR_ARG;
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
@@ -628,6 +669,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
 }
 
 hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* rep) {
+  NvtxRange nvtx_range("hdg_autotune");
   if (!c) return HDG_ERR_ARG;
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
@@ -643,6 +685,7 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
 }
 
 hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nrhs) {
+  NvtxRange nvtx_range("hdg_recover");
   if (!c) return HDG_ERR_ARG;
   if (!x || !u || !q) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_recover before hdg_condense");
@@ -709,6 +752,7 @@ hdg_status hdg_get_schur(hdg_ctx* c, int64_t e0, int64_t count, double* S) {
 
 hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host, const hdg_solve_opts* o,
                         double* x_host, double* u_host, double* q_host, hdg_solve_report* rep) {
+  NvtxRange nvtx_range("hdg_run_host");
   if (!c) return HDG_ERR_ARG;
   if (!f_host || !o) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->lv) return set_err(c, HDG_ERR_ARG, "hdg_run_host: not available on a level mesh");

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
       int code[3], flip[3];
       elem_edges(e[sd], P.n, code, flip);
       const int kk = c / P1, t = c - kk * P1;
-      if (code[kk] >= 0) v = vgather<BT, VT>(x, (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t));
+      const size_t xi = (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t);
+      if (code[kk] >= 0 && HDG_INB(xi, P.N_tr, P.oob, 1)) v = vgather<BT, VT>(x, xi);
     }
     xs[idx] = v;
   }
@@ -174,6 +175,9 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
   edge_sides(f, P.n, e, k, fl, &len);
   // row t_side of each side's row-block (the edge dof s in the element's orientation)
   const int t0 = fl[0] ? PP - s : s, t1 = fl[1] ? PP - s : s;
+  if (!HDG_INB((int64_t)e[0] * 3 + k[0], 3LL * P.N, P.oob, 2) || !HDG_INB((int64_t)e[1] * 3 + k[1], 3LL * P.N, P.oob, 2) ||
+      !HDG_INB(t0, P1, P.oob, 2) || !HDG_INB(t1, P1, P.oob, 2) || !HDG_INB((int64_t)f * P1 + s, P.N_tr, P.oob, 3))
+    return;
   if constexpr (BT == 1) {
     const float2* S = static_cast<const float2*>(Sv);
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
@@ -262,7 +266,9 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
     const double* b0 = S + ((size_t)e[0] * 3 + k[0]) * (size_t)nt * P1 + t0;
     const double* b1 = S + ((size_t)e[1] * 3 + k[1]) * (size_t)nt * P1 + t1 - (size_t)nt * P1;
     const double* xv = xs + le * 2 * nt;
-    double acc0 = 0.0, acc1 = 0.0;
+    // four accumulator chains: a DFMA's result returns through the short scoreboard
+    // after a long latency, and two chains per thread left the FP64 pipe idle ~20 %
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     double cur[G0], nxt[G0];
 #pragma unroll
     for (int u = 0; u < G0; ++u) cur[u] = u < nq ? (u < nt ? b0 : b1)[(size_t)u * P1] : 0.0;
@@ -273,15 +279,14 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
         nxt[u] = q < nq ? (q < nt ? b0 : b1)[(size_t)q * P1] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < G0; u += 2) {
+      for (int u = 0; u < G0; ++u) {
         const int q = q0 + u;
-        if (q < nq) acc0 = fma(cur[u], xv[q], acc0);
-        if (q + 1 < nq) acc1 = fma(cur[u + 1], xv[q + 1], acc1);
+        if (q < nq) acc[u & 3] = fma(cur[u], xv[q], acc[u & 3]);
       }
 #pragma unroll
       for (int u = 0; u < G0; ++u) cur[u] = nxt[u];
     }
-    double r = acc0 + acc1;
+    double r = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     if (escale) r *= escale[f];
     if constexpr (VT == 1) static_cast<float2*>(y)[(size_t)f * P1 + s] = df_from(r);
     else static_cast<double*>(y)[(size_t)f * P1 + s] = r;
@@ -323,6 +328,8 @@ struct BulkShape {
   int q;       // consumer warps per slot
   int cpw;     // columns per consumer warp
   int seg;     // bytes of one side's segment in a slot (multiple of 16)
+  long long wait_cycles;   // limit of every mbarrier wait (clock64 cycles)
+  int skip_edge;           // test hook: the interior edge whose copy is not issued (-1: none)
 };
 
 namespace {
@@ -349,11 +356,12 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 }
 // true once the phase of this parity has completed; false after the cycle limit
 // or once another warp of the CTA has given up (abort flag)
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, const volatile int* abort_flag,
+                                                  long long limit) {
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
     if (abort_flag && *abort_flag) return false;
-    if (clock64() - t0 > ABK_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -401,23 +409,29 @@ __global__ void __launch_bounds__(32 * ABK_MAX_WARPS) apply_bulk_kernel(
     if (lane == 0) {
       for (int i = 0; i < nE; ++i) {
         const int c = i % NC, u = i / NC;
-        if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[c]), (uint32_t)((u - 1) & 1), abort_flag)) {
+        if (u > 0 && !mbar_wait_bounded(smem_addr(&empty[c]), (uint32_t)((u - 1) & 1), abort_flag, B.wait_cycles)) {
           *abort_flag = 1;
           break;
         }
         const int f = (int)blockIdx.x + i * G;
+        // test hook: this edge's copy is never issued, so its consumers' bounded wait runs out
+        if (f == B.skip_edge) continue;
         int e[2], k[2], fl[2];
         double len;
         edge_sides(f, P.n, e, k, fl, &len);
         const uint32_t bar = smem_addr(&full[c]);
         const char* src[2];
         uint32_t sz[2];
+        bool in_range = true;
         for (int sd = 0; sd < 2; ++sd) {
           const size_t off = ((size_t)e[sd] * 3 + k[sd]) * blk_bytes;
           const size_t a0 = off & ~(size_t)15;
           src[sd] = reinterpret_cast<const char*>(S) + a0;
           sz[sd] = (uint32_t)(((off - a0) + blk_bytes + 15) & ~(size_t)15);
+          // the array carries 16 bytes of slack past its 3 N row-blocks
+          in_range = in_range && HDG_INB(a0 + sz[sd] - 1, 3 * (size_t)P.N * blk_bytes + 16, P.oob, 4);
         }
+        if (!in_range) continue;   // (bounds-checked build) its consumers' bounded wait gives up
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_tx(bar, sz[0] + sz[1]);
         for (int sd = 0; sd < 2; ++sd)
@@ -469,7 +483,8 @@ __global__ void __launch_bounds__(32 * ABK_MAX_WARPS) apply_bulk_kernel(
       const int i = c + kq * NC;
       if (kq + 1 < nk) gather(i + NC);   // loads in flight during the products below
       // every lane polls; the warp goes on only if all lanes saw the copy land (a uniform decision)
-      if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)(kq & 1), abort_flag))) {
+      if (!__all_sync(0xffffffffu,
+                      mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)(kq & 1), abort_flag, B.wait_cycles))) {
         if (lane == 0) *abort_flag = 1;
         break;
       }
@@ -510,8 +525,8 @@ __global__ void __launch_bounds__(32 * ABK_MAX_WARPS) apply_bulk_kernel(
           red[pq * 32 + lane] = make_float2(h0, l0);
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_addr(&parts[c]));
-        } else if (!__all_sync(0xffffffffu,
-                               mbar_wait_bounded(smem_addr(&parts[c]), (uint32_t)(kq & 1), abort_flag))) {
+        } else if (!__all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&parts[c]), (uint32_t)(kq & 1), abort_flag,
+                                                              B.wait_cycles))) {
           if (lane == 0) *abort_flag = 1;
           break;
         } else {
@@ -546,7 +561,7 @@ __global__ void __launch_bounds__(32 * ABK_MAX_WARPS) apply_bulk_kernel(
       atomicExch(&apply_bulk_wait_error, 1);
       for (int c = 0; c < NC; ++c)
         if (s_issued[c] > s_done[c])
-          mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)((s_issued[c] - 1) & 1), nullptr);
+          mbar_wait_bounded(smem_addr(&full[c]), (uint32_t)((s_issued[c] - 1) & 1), nullptr, B.wait_cycles);
     }
     __syncthreads();
   }
@@ -620,8 +635,10 @@ bool apply_bulk_available(const Params& P, int q) {
 }
 
 cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x, float2* y, const double* escale,
-                              const int* stop, cudaStream_t st, int q) {
+                              const int* stop, cudaStream_t st, int q, long long wait_cycles, int skip_edge) {
   BulkShape B;
+  B.wait_cycles = wait_cycles > 0 ? wait_cycles : ABK_WAIT_CYCLES;
+  B.skip_edge = skip_edge;
   size_t smem, max_dyn;
   int sms;
   cudaError_t e = bulk_limits(&sms, &max_dyn);
@@ -644,11 +661,12 @@ cudaError_t apply_bulk_take_error(cudaStream_t st, int* err) {
 }
 
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void* x, void* y,
-                             const double* escale, const int* stop, cudaStream_t st, int epb, int vt) {
+                             const double* escale, const int* stop, cudaStream_t st, int epb, int vt,
+                             const BulkHooks* hk) {
   // epb < 0: the pipelined bulk-copy apply with -epb consumer warps per edge (split-FP32 blocks and vectors)
   if (epb < 0 && bt == 1 && vt == 1)
     return launch_apply_bulk(P, static_cast<const float2*>(S), static_cast<const float2*>(x), static_cast<float2*>(y),
-                             escale, stop, st, -epb);
+                             escale, stop, st, -epb, hk ? hk->wait_cycles : 0, hk ? hk->skip_edge : -1);
   // epb edges per block, one thread per (edge, trace position): at most 512 threads
   if (epb <= 0 || epb * P.P1 > 512) epb = apply_edges_per_block(P);
   const int threads = (epb * P.P1 + 31) / 32 * 32;
@@ -676,12 +694,12 @@ __global__ void split_df_kernel(const double* __restrict__ a, float2* __restrict
 // residual), with the default edges per block
 cudaError_t launch_apply64(const Params& P, const double* S, const double* x, double* y, const double* escale,
                            const int* stop, cudaStream_t st, int epb) {
-  return launch_apply_vdf(0, P, S, x, y, escale, stop, st, epb, 0);
+  return launch_apply_vdf(0, P, S, x, y, escale, stop, st, epb, 0, nullptr);
 }
 
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st) {
-  return launch_apply_vdf(1, P, S, x, y, escale, stop, st, 0, 0);
+  return launch_apply_vdf(1, P, S, x, y, escale, stop, st, 0, 0, nullptr);
 }
 
 cudaError_t launch_split_df(const double* a, float2* out, int64_t n, cudaStream_t st) {

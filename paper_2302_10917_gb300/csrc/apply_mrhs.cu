@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) mrhs_element_kernel(Params P, const void*
     const int r = idx / nt, c = idx - r * nt;
     const int kk = c / P1, t = c - kk * P1;
     float2 v = make_float2(0.f, 0.f);
-    if (r < nrhs && code[kk] >= 0)
+    if (r < nrhs && code[kk] >= 0 && HDG_INB((size_t)code[kk] * P1 + (flip[kk] ? PP - t : t), P.N_tr, P.oob, 5))
       v = x[(size_t)(cmap ? cmap[r] : r) * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
     xs2[c * NR1 + r] = v;
   }
@@ -239,6 +239,7 @@ __global__ void mrhs_edge_sum_kernel(Params P, const float2* __restrict__ Z, int
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       const int t = fl[sd] ? PP - s : s;
+      if (!HDG_INB((int64_t)e[sd] * 3 + k[sd], 3LL * P.N, P.oob, 6) || !HDG_INB(t, P1, P.oob, 6)) continue;
       const float2 z = Z[((size_t)e[sd] * nrhs + r) * nt + k[sd] * P1 + t];
       df_add(h, l, z.x, z.y);
     }
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(256) mrhs_element_d_kernel(Params P, const voi
     const int r = idx / nt, c = idx - r * nt;
     const int kk = c / P1, t = c - kk * P1;
     double v = 0.0;
-    if (r < nrhs && code[kk] >= 0)
+    if (r < nrhs && code[kk] >= 0 && HDG_INB((size_t)code[kk] * P1 + (flip[kk] ? PP - t : t), P.N_tr, P.oob, 5))
       v = x[(size_t)(cmap ? cmap[r] : r) * vstride + (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t)];
     if constexpr (BT == 0) xs[c * NR1 + r] = v;
     else if constexpr (BT == 1) xs[c * NR1 + r] = df_from(v);
@@ -361,6 +362,7 @@ __global__ void mrhs_edge_sum_d_kernel(Params P, const double* __restrict__ Z, i
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       const int t = fl[sd] ? PP - s : s;
+      if (!HDG_INB((int64_t)e[sd] * 3 + k[sd], 3LL * P.N, P.oob, 6) || !HDG_INB(t, P1, P.oob, 6)) continue;
       v += Z[((size_t)e[sd] * nrhs + r) * nt + k[sd] * P1 + t];
     }
     if (escale) v *= escale[f];

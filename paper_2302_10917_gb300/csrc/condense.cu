@@ -321,15 +321,20 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
 #pragma unroll
         for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? Us[c * ld + j] : 0.0;
         const int r0 = jb + rt * RT;
-        const int r1 = min(r0 + RT, R);
-        for (int r = r0; r < r1; ++r) {
-          double* wp = W + (size_t)r * ld + j;
-          const double* l = Ls + (r - j0) * LDP;
-          double acc = *wp;
+        const int nr = min(RT, R - r0);
+        // the tile's rows as RT independent FMA chains (each row keeps its order c = 0 .. NB-1):
+        // one chain per thread left the FP64 pipe waiting on DFMA results
+        double acc[RT];
 #pragma unroll
-          for (int c = 0; c < NB; ++c) acc -= l[c] * u[c];
-          *wp = acc;
-        }
+        for (int rr = 0; rr < RT; ++rr) acc[rr] = rr < nr ? W[(size_t)(r0 + rr) * ld + j] : 0.0;
+        const double* l = Ls + (r0 - j0) * LDP;
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+#pragma unroll
+          for (int rr = 0; rr < RT; ++rr) acc[rr] -= l[(rr < nr ? rr : 0) * LDP + c] * u[c];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr)
+          if (rr < nr) W[(size_t)(r0 + rr) * ld + j] = acc[rr];
       }
     }
     __syncthreads();
@@ -733,8 +738,11 @@ __global__ void __launch_bounds__(128) recover_kernel(RecArgs a) {
     const int s = flip[k] ? P.P - t : t;
     double v = 0.0;
     if (a.xel) v = a.xel[(size_t)eb * nt + c];
-    else if (code[k] >= 0) v = a.x[(size_t)code[k] * P1 + s];
-    else if (a.ghat) v = a.ghat[(size_t)(-1 - code[k]) * P1 + s];
+    else if (code[k] >= 0) {
+      if (HDG_INB((size_t)code[k] * P1 + s, P.N_tr, P.oob, 9)) v = a.x[(size_t)code[k] * P1 + s];
+    } else if (a.ghat) {
+      v = a.ghat[(size_t)(-1 - code[k]) * P1 + s];
+    }
     xe[c] = v;
   }
   __syncthreads();

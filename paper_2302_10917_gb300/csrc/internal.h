@@ -50,7 +50,7 @@ struct RefTables {
 // Builds the tables of level (m, p). Throws std::runtime_error on failure.
 void build_reference_tables(int m, int p, RefTables& T);
 
-// Trace tables of the face levels of a level mesh (Sec. 5.3), one host array:
+// Trace tables of the face levels of a level mesh (Sec. 4.2), one host array:
 // Gh_R (trace mass on [0,1] with 2^R sub-intervals) at G_off[R], its inverse at
 // Gi_off[R], and for r < R the transfer T_rR ((2^r p + 1) x (2^R p + 1),
 // row-major) at T_off[r][R] (-1 where not defined).
@@ -87,7 +87,24 @@ struct Params {
   int supg;              // 1: SUPG terms in the u-equations (Sec. 3.4)
   int R, Cc, ld;         // bordered local system: rows, used columns, leading dimension
   int nrhs;              // right-hand sides (source columns of the bordered system)
+  int* oob;              // bounds-checked build: first failing index check (site code), else unused
 };
+
+// Index checks of the bounds-checked build (-DHDG_BOUNDS_CHECK): an index
+// outside [0, n) records its site code in *oob (the first one wins), and the
+// access it guards is skipped; no trap, so the context stays usable and the
+// host reads the code (hdg_info bounds_error). In the regular build every
+// check is the constant true and costs nothing.
+#if defined(HDG_BOUNDS_CHECK) && defined(__CUDACC__)
+__device__ __forceinline__ bool hdg_in_bounds(long long i, long long n, int* oob, int site) {
+  if (i >= 0 && i < n) return true;
+  if (oob) atomicCAS(oob, 0, site);
+  return false;
+}
+#define HDG_INB(i, n, oob, site) hdg_in_bounds((long long)(i), (long long)(n), (oob), (site))
+#else
+#define HDG_INB(i, n, oob, site) true
+#endif
 
 // By-value view of a level mesh for kernels (device pointers).
 // Element-side rows: the n_t,e trace dofs of every element, elements in
@@ -96,6 +113,8 @@ struct Params {
 struct LevelDev {
   int N, n, n_int, p;
   int64_t N_tr, nz;
+  int64_t ns;                 // lifted Schur-block entries
+  int* oob;                   // bounds-checked build: see HDG_INB
   const int64_t* eoff;        // [n_int + 1] first trace dof of every interior edge
   const int* dof_edge;        // [N_tr] interior edge of every trace dof
   const int* ez;              // [n_int][2] element-side row of dof 0 of the face block on each side
@@ -280,6 +299,16 @@ struct LevelMesh {
 // ---------------------------------------------------------------------------
 // Context (opaque to callers).
 // ---------------------------------------------------------------------------
+namespace mehdg {
+// Wait limit of the pipelined apply's mbarrier waits (clock64 cycles; 0: the built-in
+// limit of about one second) and a test hook: the interior edge whose bulk copy is not
+// issued (-1: none), which makes the waiting consumers give up (HDG_ERR_TIMEOUT).
+struct BulkHooks {
+  long long wait_cycles = 0;
+  int skip_edge = -1;
+};
+}  // namespace mehdg
+
 struct hdg_ctx {
   mehdg::Params prm;
   mehdg::RefTables ref;
@@ -290,6 +319,7 @@ struct hdg_ctx {
   unsigned flags = 0;
   void* d_tables = nullptr;
   double* d_kappa = nullptr;      // [N]
+  int* d_oob = nullptr;           // bounds-checked build: first failing index check (site code)
   const double* f_qp = nullptr;   // caller-owned
   const double* gD_qp = nullptr;  // caller-owned or null
   double* d_ghat = nullptr;       // [n_bnd][P1]
@@ -332,6 +362,7 @@ struct hdg_ctx {
   int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)
   int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)
+  mehdg::BulkHooks bulk_hooks;    // pipelined apply: wait limit and the copy-skip test hook
   int tune_kgd = 0;               // multi-dot blocks over all vector groups
   int tune_kgu = 0;               // streaming-update blocks
   cudaGraphExec_t gm_exec = nullptr;   // captured GMRES cycle (one restart cycle of Arnoldi steps)

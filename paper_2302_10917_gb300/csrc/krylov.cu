@@ -438,9 +438,9 @@ __global__ void __launch_bounds__(KT, 4) d_mdot_kernel(const double2* __restrict
   d_block_reduce<VG>(h, ncol - g0, red, part + (size_t)cb * ncol + g0);
 }
 
-// the last R (< 8) columns of an update: a -= sum cf_u v_u.x, b likewise
+// the last R (< 4) columns of an update: a -= sum cf_u v_u.x, b likewise
 template <int R>
-__device__ __forceinline__ void d_update_tail(double& a, double& b, const double* cf, const double2 (&v)[8]) {
+__device__ __forceinline__ void d_update_tail(double& a, double& b, const double* cf, const double2 (&v)[4]) {
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     a = fma(cf[u], v[u].x, a);
@@ -472,32 +472,34 @@ __global__ void __launch_bounds__(KT) d_update_kernel(const double2* __restrict_
   for (int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pf < np; pf += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = np - 1 - pf;
     const double2 wv = w[p];
-    double a = wv.x, b = wv.y;
-    double2 v[8], nx[8];
+    // two chains per entry (even and odd basis vectors): four DFMA chains per thread;
+    // groups of 4 basis vectors, the next group's loads issued before this group's FMAs
+    double a = wv.x, b = wv.y, a1 = 0.0, b1 = 0.0;
+    double2 v[4], nx[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = u < nv ? V[(size_t)u * bt.vstr + p] : z2;
+    for (int u = 0; u < 4; ++u) v[u] = u < nv ? V[(size_t)u * bt.vstr + p] : z2;
     int i0 = 0;
-    for (; i0 + 8 <= nv; i0 += 8) {
+    for (; i0 + 4 <= nv; i0 += 4) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) nx[u] = i0 + 8 + u < nv ? V[(size_t)(i0 + 8 + u) * bt.vstr + p] : z2;
+      for (int u = 0; u < 4; ++u) nx[u] = i0 + 4 + u < nv ? V[(size_t)(i0 + 4 + u) * bt.vstr + p] : z2;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 4; u += 2) {
         a = fma(cf[i0 + u], v[u].x, a);
         b = fma(cf[i0 + u], v[u].y, b);
+        a1 = fma(cf[i0 + u + 1], v[u + 1].x, a1);
+        b1 = fma(cf[i0 + u + 1], v[u + 1].y, b1);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = nx[u];
+      for (int u = 0; u < 4; ++u) v[u] = nx[u];
     }
     switch (nv - i0) {   // the partial last group: only its own FMAs
       case 1: d_update_tail<1>(a, b, cf + i0, v); break;
       case 2: d_update_tail<2>(a, b, cf + i0, v); break;
       case 3: d_update_tail<3>(a, b, cf + i0, v); break;
-      case 4: d_update_tail<4>(a, b, cf + i0, v); break;
-      case 5: d_update_tail<5>(a, b, cf + i0, v); break;
-      case 6: d_update_tail<6>(a, b, cf + i0, v); break;
-      case 7: d_update_tail<7>(a, b, cf + i0, v); break;
       default: break;
     }
+    a += a1;
+    b += b1;
     if (scaled) {
       a *= inv;
       b *= inv;
@@ -835,7 +837,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       {
         ProfScope ps(c, timed ? phase : -1);
         if (c->lv) cu.ok(launch_level_apply(c, bt, vt, Sop, V + (size_t)j * ldv * esz, w, 1, ldv, precond_scale(c), fl, s));
-        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv * esz, w, precond_scale(c), fl, s, epb, vt));
+        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv * esz, w, precond_scale(c), fl, s, epb, vt,
+                                    &c->bulk_hooks));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -878,7 +881,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       // turns the steps after convergence into immediate returns. With
       // profiling on, the capture carries an event quadruple per step.
       const int timed = c->prof_on ? 1 : 0;
-      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
+      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, (intptr_t)c->bulk_hooks.wait_cycles,
+                                         c->bulk_hooks.skip_edge, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
                                          (intptr_t)np, kgd, kgu, epb, c->lv ? c->lv->rb : 0};
       if (timed && (int)c->gm_ev.size() < 4 * K) {
@@ -1016,7 +1020,9 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   double best_bulk = 0.0;
   for (int q = 1; q <= 3 && bt == 1 && !c->lv && !f64b; ++q) {
     if (!apply_bulk_available(P, q)) continue;
-    const double t = time_it([&] { cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -q, 1)); });
+    const double t = time_it([&] {
+      cu.ok(launch_apply_vdf(bt, P, Sop, V, c->d_w, precond_scale(c), nullptr, st, -q, 1, &c->bulk_hooks));
+    });
     int err = 0;
     if (!cu.ok(apply_bulk_take_error(st, &err)) || err)
       return fail(c, HDG_ERR_TIMEOUT, "autotune: pipelined apply: a bounded copy wait gave up");

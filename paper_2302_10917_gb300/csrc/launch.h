@@ -39,9 +39,11 @@ cudaError_t launch_apply32(const Params& P, const float* S, const float* x, floa
                            const int* stop, cudaStream_t st);
 cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, double* y, const double* escale,
                             const int* stop, cudaStream_t st);
-// bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks; vt: 0 FP64 / 1 split-FP32 vectors
+// bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks; vt: 0 FP64 / 1 split-FP32 vectors; hk: the pipelined
+// apply's wait limit and test hook (null: defaults)
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void* x, void* y,
-                             const double* escale, const int* stop, cudaStream_t st, int epb = 0, int vt = 1);
+                             const double* escale, const int* stop, cudaStream_t st, int epb = 0, int vt = 1,
+                             const BulkHooks* hk = nullptr);
 int apply_edges_per_block(const Params& P);
 // Pipelined bulk-copy apply of split-FP32 blocks (q = 1 .. 3 consumer warps
 // per edge); whether it applies to this problem shape; its timeout flag (read
@@ -49,7 +51,8 @@ int apply_edges_per_block(const Params& P);
 bool apply_bulk_available(const Params& P, int q);
 int apply_bulk_threads(const Params& P, int q);   // threads per CTA of that shape (0: not available)
 cudaError_t launch_apply_bulk(const Params& P, const float2* S, const float2* x, float2* y, const double* escale,
-                              const int* stop, cudaStream_t st, int q);
+                              const int* stop, cudaStream_t st, int q, long long wait_cycles = 0,
+                              int skip_edge = -1);
 cudaError_t apply_bulk_take_error(cudaStream_t st, int* err);
 cudaError_t launch_apply_mrhs(int bt, int vt, const Params& P, const void* S, const void* x, void* y, int nrhs,
                               int64_t vstride, const double* escale, cudaStream_t st);
@@ -109,6 +112,8 @@ cudaError_t launch_gradient(const Params& P, const DevTables& dt, const double* 
                             const double* u, const double* mu, const double* nu, double* dkappa, double* df,
                             cudaStream_t st);
 
+// Loads the no-allocation entry point's scratch array on the current device (static_scratch.cu).
+cudaError_t static_scratch_prepare();
 // Restarted GMRES on the condensed system (krylov.cu).
 hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_opts& o, hdg_solve_report& rep);
 // nrhs independent instances in lockstep: one multi-RHS apply and batched

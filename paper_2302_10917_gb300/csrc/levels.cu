@@ -1,4 +1,4 @@
-// Macro-elements of uneven refinement level (Sec. 5.3, local adaptive
+// Macro-elements of uneven refinement level (Sec. 4.2, local adaptive
 // refinement): element e carries its own level r_e (m_e = 2^r_e sub-edges per
 // macro-edge, the level-r_e C0 lattice inside), and the trace space of a face
 // is refined to its finer side, R_F = max(r+, r-) (a boundary face has its
@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(LV_RB_MAX) lv_elem_kernel(LevelDev L, const vo
     const int rr = (int)(i % RPT);
     const int d = L.xmap[row];
     Acc v = lv_zero<BT>();
-    if (d >= 0 && c0 + rr < nrhs) v = lv_load<BT, VT>(xv, (size_t)(cmap ? cmap[c0 + rr] : c0 + rr) * vstride + d);
+    if (d >= 0 && c0 + rr < nrhs && HDG_INB(d, L.N_tr, L.oob, 11))
+      v = lv_load<BT, VT>(xv, (size_t)(cmap ? cmap[c0 + rr] : c0 + rr) * vstride + d);
     xs[i] = v;
   }
   __syncthreads();
@@ -264,6 +265,10 @@ __global__ void __launch_bounds__(LV_RB_MAX) lv_elem_kernel(LevelDev L, const vo
   const int ap = L.row_ap[z];
   const int nt = L.ap_nt[ap];
   const int a = (int)(z - L.ap_zoff[ap]);
+  // the row's entries S[soff + a + c nt], c < nt, inside the blocks and its output inside z
+  if (!HDG_INB(L.ap_soff[ap] + a + (int64_t)(nt - 1) * nt, L.ns, L.oob, 12) || !HDG_INB(a, nt, L.oob, 12) ||
+      !HDG_INB((int64_t)(L.ap_zoff[ap] - xb + nt - 1) * RPT, (int64_t)(xn) * RPT, L.oob, 13))
+    return;
   const ST* sp = S + L.ap_soff[ap] + a;
   const Acc* xe = xs + (L.ap_zoff[ap] - xb) * RPT;
   if constexpr (BT == 1) {
@@ -334,6 +339,8 @@ __global__ void lv_face_kernel(LevelDev L, const void* __restrict__ zv, void* __
     const int s = (int)(i - b0), Pf = (int)(L.eoff[f + 1] - b0) - 1;
     const int fl = L.eflip[f];
     const int t0 = (fl & 1) ? Pf - s : s, t1 = (fl & 2) ? Pf - s : s;
+    if (!HDG_INB((int64_t)L.ez[2 * f] + t0, L.nz, L.oob, 14) || !HDG_INB((int64_t)L.ez[2 * f + 1] + t1, L.nz, L.oob, 14))
+      continue;
     const Acc a0 = zb[(size_t)r * L.nz + L.ez[2 * f] + t0];
     const Acc a1 = zb[(size_t)r * L.nz + L.ez[2 * f + 1] + t1];
     const size_t o = (size_t)(cmap ? cmap[r] : r) * vstride + i;
@@ -639,7 +646,7 @@ hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d) {
   if ((e = cudaMemcpyAsync(L.d_mem, host.data(), total, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return lv_cuda(c, e, "level mesh upload");
-  dv.N = N; dv.n = n; dv.n_int = n_int; dv.p = p; dv.N_tr = N_tr; dv.nz = z;
+  dv.N = N; dv.n = n; dv.n_int = n_int; dv.p = p; dv.N_tr = N_tr; dv.nz = z; dv.ns = L.ns; dv.oob = c->d_oob;
   for (int R = 0; R <= kMaxLevel; ++R) {
     dv.G_off[R] = L.lt.G_off[R];
     dv.Gi_off[R] = L.lt.Gi_off[R];
@@ -677,6 +684,7 @@ hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d) {
       return lv_err(c, HDG_ERR_ARG, ex.what());
     }
     B.prm = level_params(d, B.ref, N, n_int);
+    B.prm.oob = c->d_oob;
     const size_t lift = ((size_t)std::max(B.prm.n_t * B.prm.n_t, B.max_nt * B.max_nt) + (size_t)B.prm.n_t * B.max_nt) * 8;
     if (lift > kLvMaxSmem) return lv_err(c, HDG_ERR_ARG, "level " + std::to_string(r) + ": lifted blocks exceed shared memory");
     size_t tb = 0;
@@ -694,6 +702,7 @@ hdg_status level_create(hdg_ctx* c, const hdg_mesh_desc* d) {
   const RefTables& Tm = L.bins.back().ref;
   Params& P = c->prm;
   P = level_params(d, Tm, N, n_int);
+  P.oob = c->d_oob;
   P.N_tr = (int)N_tr;
   P.n_t = L.max_nt;
   P.n_qp = 0;

@@ -418,7 +418,7 @@ namespace mehdg {
 // level-R nodes. T_rR maps a level-R trace to the coefficients of its L2
 // projection onto the level-r space, and the coarse side's face couplings
 // to a level-R face are its own-level couplings times T_rR (the coarse
-// basis restricted to the edge lies in the level-r trace space, Sec. 5.3).
+// basis restricted to the edge lies in the level-r trace space, Sec. 4.2).
 void build_level_tables(int p, LevelTables& L) {
   L.p = p;
   std::vector<double> gx, gw;

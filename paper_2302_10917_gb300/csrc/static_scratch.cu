@@ -14,7 +14,6 @@
 // plus a one-word status flag. All calls share it and it keeps the contents of
 // the last call, so calls whose work overlaps on the GPU (two streams, two
 // host threads on one device) race on it and must be serialised by the caller.
-#include <mutex>
 #include <string>
 #include "launch.h"
 
@@ -26,30 +25,20 @@ static __device__ __align__(256) int g_static_flag[1];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-bool g_setup_done[kMaxDevices] = {};
-double* g_scratch_ptr[kMaxDevices] = {};
-int* g_flag_ptr[kMaxDevices] = {};
-
-// Device addresses of the scratch symbols for the current device (looked up
-// once per device; host code may not use the symbols' names as addresses).
-cudaError_t static_scratch_setup(int dev, double** scratch, int** flag) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_setup_done[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    void* q = nullptr;
-    e = cudaGetSymbolAddress(&q, g_static_flag);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-    g_flag_ptr[dev] = static_cast<int*>(q);
-    g_setup_done[dev] = true;
-  }
-  *scratch = g_scratch_ptr[dev];
-  *flag = g_flag_ptr[dev];
+// Device addresses of the scratch symbols in the current context. In host code
+// the symbols' names are host-side stand-ins, not device addresses, so every
+// call asks the runtime (cheap once the module is loaded). Nothing is cached:
+// an address kept from an earlier context (before a device reset) would point
+// into freed memory.
+cudaError_t static_scratch_lookup(double** scratch, int** flag) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  void* q = nullptr;
+  e = cudaGetSymbolAddress(&q, g_static_flag);
+  if (e != cudaSuccess) return e;
+  *scratch = static_cast<double*>(p);
+  *flag = static_cast<int*>(q);
   return cudaSuccess;
 }
 
@@ -74,20 +63,34 @@ __global__ void static_extract_kernel(Params P, const double* __restrict__ ws, i
   if (!g_out) return;
   int code[3], flip[3];
   elem_edges(e, P.n, code, flip);
-  for (int r = threadIdx.x; r < nt; r += blockDim.x) {
-    double acc = W[(size_t)(Q + r) * ld + Q + nt];
+  // source s: load column Q + n_t + s, Dirichlet lift of source s, out [nrhs][count][n_t]
+  for (int idx = threadIdx.x; idx < P.nrhs * nt; idx += blockDim.x) {
+    const int s = idx / nt, r = idx - s * nt;
+    double acc = W[(size_t)(Q + r) * ld + Q + nt + s];
     if (ghat) {
+      const double* gs = ghat + (size_t)s * P.n_bnd * P1;
       for (int k = 0; k < 3; ++k) {
         if (code[k] >= 0) continue;
-        const double* gb = ghat + (size_t)(-1 - code[k]) * P1;
+        const double* gb = gs + (size_t)(-1 - code[k]) * P1;
         for (int t = 0; t < P1; ++t) acc -= W[(size_t)(Q + r) * ld + Q + k * P1 + t] * gb[flip[k] ? P.P - t : t];
       }
     }
-    g_out[(size_t)b * nt + r] = acc;
+    g_out[((size_t)s * count + b) * nt + r] = acc;
   }
 }
 
 }  // namespace
+
+// Loads the module that holds the scratch array on the current device, so that
+// its MEHDG_STATIC_SCRATCH_BYTES are set aside when a context is created rather
+// than at the first hdg_condense_static call (under lazy module loading the
+// array comes into being when the module is first used). Called by hdg_create.
+cudaError_t static_scratch_prepare() {
+  double* s = nullptr;
+  int* f = nullptr;
+  return static_scratch_lookup(&s, &f);
+}
+
 }  // namespace mehdg
 
 using namespace mehdg;
@@ -115,11 +118,9 @@ extern "C" hdg_status hdg_condense_static(hdg_ctx* c, int64_t e0, int64_t count,
              std::to_string(MEHDG_STATIC_SCRATCH_BYTES / slot_bytes) + " elements of this size per call)";
     return HDG_ERR_ARG;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
   double* scratch = nullptr;
   int* flag = nullptr;
-  if (e == cudaSuccess) e = static_scratch_setup(dev, &scratch, &flag);
+  cudaError_t e = static_scratch_lookup(&scratch, &flag);
   if (e != cudaSuccess) {
     c->err = std::string("hdg_condense_static set-up: ") + cudaGetErrorString(e);
     return HDG_ERR_CUDA;

@@ -122,3 +122,10 @@ def bump_centres(count, seed):
 def random_vector(n, seed):
     g = np.random.default_rng([MASTER_SEED, 29, int(seed)])
     return g.standard_normal(n)
+
+
+def random_directions(count, shape, seed):
+    """count seeded standard-normal directions of the given shape: [count, *shape]
+    (the perturbation directions of the finite-difference gradient checks)."""
+    g = np.random.default_rng([MASTER_SEED, 67, int(seed)])
+    return g.standard_normal((count, *shape))

@@ -1,4 +1,4 @@
-"""Level meshes on the GPU (Sec. 5.3): per-element refinement levels, faces at
+"""Level meshes on the GPU (Sec. 4.2): per-element refinement levels, faces at
 the finer side's level, against the level-mesh oracle (oracle/levels.py).
 
 The oracle integrates the coarse side's face couplings on the fine sub-edges;

@@ -3,13 +3,13 @@ blocks of every element (FP64 and split-FP32 condensation), right-hand sides
 with the SUPG load, the solution against the oracle's direct solve, and
 polynomial exactness (the SUPG residual vanishes for the exact solution).
 
-Tolerance of the Schur blocks and right-hand sides: 2e-10 relative (1e-12 without SUPG). The
+Tolerance of the Schur blocks and right-hand sides: 5e-11 relative (1e-12 without SUPG). The
 consistency term -tau_s kappa (a . grad w, Lap u) of the SUPG residual lowers
 the smallest singular value of A_u: at m = 8, p = 3, beta = 50, kappa ~ 1 the
 measured cond(A_u) grows from 1.2e2 to 5.6e4 and that of the oracle's full
 3Q system from 1.2e5 to 3.5e8, so the two LU factorisations (different
 formulations, pivot orders and rounding) legitimately differ by up to about
-cond x 1e-16; measured 2.3e-11. The polynomial-exactness test below pins the
+cond x 1e-16; measured 2.3e-11 (the bound keeps 2x slack). The polynomial-exactness test below pins the
 SUPG terms independently of that conditioning.
 """
 import math
@@ -53,9 +53,9 @@ def test_supg_condensation_rhs_and_solve(cid, n, m, p, beta, kscale, split):
     pr.condense(keep_factors=True, store_df64=True, split_update=split)
     S = pr.schur().cpu().numpy()
     for e in range(S.shape[0]):
-        assert rel(S[e], S_el[e]) < 2e-10, e
+        assert rel(S[e], S_el[e]) < 5e-11, e
     gv = pr.rhs()
-    assert rel(gv.cpu().numpy(), g_ora) < 2e-10        # -C A^-1 R: the same conditioning as S
+    assert rel(gv.cpu().numpy(), g_ora) < 5e-11        # -C A^-1 R: the same conditioning as S
     Sa = ora.assemble_S(S_el)
     x, rep, st = pr.solve(gv, tol=1e-11, restart=60, mode=2, orth=1, maxit=40000)
     assert st == 0, (rep, np.linalg.cond(Sa))

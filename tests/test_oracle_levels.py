@@ -1,5 +1,5 @@
 """Pins of the level-mesh oracle (oracle/levels.py): macro-elements of uneven
-refinement level with faces at the finer side's level (Sec. 5.3).
+refinement level with faces at the finer side's level (Sec. 4.2).
 
 Each test targets a mistake the non-conforming coupling could plausibly
 contain: a fine sub-edge integrated against the wrong coarse sub-triangle, a
