@@ -64,8 +64,9 @@ def parse_args(argv=None):
                     help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes), "
                          "2 CGS with a second projection where more than half of the vector lay in the basis, "
                          "3 the same where the single projection cancelled more than six digits")
-    ap.add_argument("--split", action="store_true",
-                    help="split-FP32 elimination in the condensation (default: FP64 local factorisations)")
+    ap.add_argument("--elim", default="tc", choices=["tc", "fp64", "split"],
+                    help="local factorisation: tc = FP64 panels with the trailing updates as exact slice products "
+                         "on the tensor cores (FP64-accurate), fp64 = FP64 FMAs throughout, split = split-FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -334,13 +335,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def tc_slice_flops(Q, R, Cc, b=32, m_tile=128, n_tile=32, products=28):
+    """bf16 flops the tensor-core condensation issues per element: every 32-column panel,
+    every 128-row x 32-column tile of the trailing block, 28 slice products of K = 32."""
+    flops, j0 = 0, 0
+    while j0 < Q:
+        nb = min(b, Q - j0)
+        jb = j0 + nb
+        tiles = -(-(R - jb) // m_tile) * -(-(Cc - jb) // n_tile)
+        flops += tiles * products * 2 * m_tile * n_tile * b
+        j0 += b
+    return flops
+
+
 # ---------------------------------------------------------------------- ours
 MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64"}
-# precision forms of one step: (Arnoldi operator mode, Krylov basis, split-FP32 elimination)
-FORMS = {"fp64": (0, 0, False), "fp32_ir": (1, 0, False), "df64": (2, 1, True)}
-FORM_DTYPES = {(0, 0, False): "f64",
-               (1, 0, False): "f32 blocks (FP32 operator) + f64 factorisation, orthogonalisation and refinement",
-               (2, 1, True): "df64 (f32x2) elimination, blocks and Krylov basis + f64 residual"}
+# precision forms of one step: (Arnoldi operator mode, Krylov basis, local factorisation)
+FORMS = {"fp64": (0, 0, "tc"), "fp64_dfma": (0, 0, "fp64"), "fp32_ir": (1, 0, "tc"), "df64": (2, 1, "split")}
+FORM_DTYPES = {(0, 0, "tc"): "f64 (tensor-core trailing updates by exact 8-bit slices, FP64-accurate)",
+               (0, 0, "fp64"): "f64 (FP64 FMAs throughout)",
+               (1, 0, "tc"): "f32 blocks (FP32 operator) + f64 factorisation, orthogonalisation and refinement",
+               (2, 1, "split"): "df64 (f32x2) elimination, blocks and Krylov basis + f64 residual"}
 
 
 def run_ours(args):
@@ -365,19 +380,20 @@ def run_ours(args):
     f = wl.sin_sin_source(xy, cfg["kappa"], cfg["beta"]).contiguous()
     del xy
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    split = args.split
+    split = args.elim == "split"
+    tc = args.elim == "tc"
 
-    def condense_flags(mode, split_update):
+    def condense_flags(mode, elim):
         # only the blocks the solve mode needs
         return dict(keep_factors=not args.no_keep_factors, store_fp32=(mode == 1), store_df64=(mode == 2),
-                    split_update=split_update)
+                    split_update=elim == "split", tc_update=elim == "tc")
 
-    def step(rec=None, mode=args.mode, basis=args.basis, split_update=split, precond="d"):
+    def step(rec=None, mode=args.mode, basis=args.basis, elim=args.elim, precond="d"):
         marks = [ev() for _ in range(4)] if rec is not None else None
         if marks:
             marks[0].record(stream)
         pr.set_source(f)
-        pr.condense(precond=precond, **condense_flags(mode, split_update))
+        pr.condense(precond=precond, **condense_flags(mode, elim))
         g = pr.rhs()
         if marks:
             marks[1].record(stream)
@@ -452,6 +468,8 @@ def run_ours(args):
                   "launches": prof["apply32" if args.mode == 1 else "apply"][0],
                   "avg_launch_ms": avg("apply32" if args.mode == 1 else "apply")},
         "condense": {"kernel": ("condense_df_kernel (split-FP32 formation + bordered LU + Schur)" if split
+                                else "condense_tc_kernel (FP64 formation, 32-column FP64 panels, trailing updates "
+                                     "as exact 8-bit slice products on the tensor cores)" if tc
                                 else "condense_kernel (FP64 formation + bordered LU + Schur)"),
                      "bound": "alu", "launches": prof["condense"][0], "avg_launch_ms": avg("condense")},
     }
@@ -480,8 +498,17 @@ def run_ours(args):
     else:
         rc.update(achieved=cond_flops / (rc["avg_launch_ms"] / 1e3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                   algorithmic_per_launch=cond_flops,
-                  peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)")
+                  peak_source="FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
+                  note_flops="FP64-equivalent flops of the dense bordered LU")
     rc["frac"] = rc["achieved"] / rc["peak"]
+    if tc:
+        # the slice products issued on the tensor cores (bf16, dense) against the measured bf16 peak
+        tflop = N * tc_slice_flops(Q, R, Cc) / (rc["avg_launch_ms"] / 1e3) / 1e12
+        bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        rc["tensor_pipe"] = {"achieved": tflop, "peak": bf16_peak, "unit": "TFLOP/s (bf16 slice products)",
+                             "frac": tflop / bf16_peak,
+                             "peak_source": "measured cuBLAS bf16, sustained" if "bf16_tflops_sustained" in peaks
+                             else "fallback 1.7 PFLOP/s"}
     # Krylov vector passes: algorithmic bytes of every Arnoldi step of the timed solves
     # (CGS: multi-dot over nv + 1 vectors, update reading nv + 1 and writing 1; CGS2 (and the
     #  second projection of orth = 2, counted as not taken): two multi-dots and two updates)
@@ -516,14 +543,16 @@ def run_ours(args):
     roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
     all_fp64 = args.mode == 0 and args.basis == 0 and not split
-    dtype = "f64" if all_fp64 else FORM_DTYPES.get((args.mode, args.basis, split), "mixed")
+    dtype = "f64" if all_fp64 else FORM_DTYPES.get((args.mode, args.basis, args.elim), "mixed")
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("GMRES(restart)", f"GMRES({args.restart})").replace(
                            "128x128 macro grid (32768", f"{cfg['n']}x{cfg['n']} macro grid ({N}"),
                        "N_tr": N_tr, "macro_elements": N, "solve_mode": MODE_NAMES[args.mode],
-                       "local_factorisation": "split-FP32" if split else "FP64",
+                       "local_factorisation": {"split": "split-FP32", "fp64": "FP64 FMAs",
+                                               "tc": "FP64 panels + tensor-core trailing updates by exact 8-bit "
+                                                     "slices (FP64-accurate)"}[args.elim],
                        "krylov_basis": ["FP64", "split-FP32"][args.basis],
                        "orthogonalisation": ["CGS2", "CGS, Pythagorean norm",
                                              "CGS + second projection where ||w - V h||^2 < ||w||^2 / 2",
@@ -542,21 +571,21 @@ def run_ours(args):
     # (condensation + rhs + GMRES to 1e-10 + back-solve), each with its own autotuned shapes,
     # and each result's relative l2 distance from the all-FP64 step's x, u and q.
     if not args.no_forms:
-        _, x64, u64, q64 = step(mode=0, basis=0, split_update=False)
+        _, x64, u64, q64 = step(mode=0, basis=0, elim="fp64")
         torch.cuda.synchronize()
     forms = {}
-    for name, (mode, basis, spl) in ({} if args.no_forms else FORMS).items():
-        step(mode=mode, basis=basis, split_update=spl)
+    for name, (mode, basis, elim) in ({} if args.no_forms else FORMS).items():
+        step(mode=mode, basis=basis, elim=elim)
         pr.autotune(mode=mode, restart=args.restart, basis=basis)
         recf = []
         for _ in range(2):
-            rep_f, xf, uf, qf = step(recf, mode=mode, basis=basis, split_update=spl)
+            rep_f, xf, uf, qf = step(recf, mode=mode, basis=basis, elim=elim)
         torch.cuda.synchronize()
         cs = [m[0].elapsed_time(m[1]) / 1e3 for m, _ in recf]
         ss = [m[1].elapsed_time(m[2]) / 1e3 for m, _ in recf]
         rs = [m[2].elapsed_time(m[3]) / 1e3 for m, _ in recf]
         dist = lambda a, b: float((a - b).norm() / b.norm())
-        forms[name] = {"dtype": FORM_DTYPES[(mode, basis, spl)],
+        forms[name] = {"dtype": FORM_DTYPES[(mode, basis, elim)],
                        "step_s": statistics.median([c + s2 + r2 for c, s2, r2 in zip(cs, ss, rs)]),
                        "condense_s": statistics.median(cs), "solve_s": statistics.median(ss),
                        "recover_s": statistics.median(rs), "iterations": rep_f["iterations"],
@@ -571,13 +600,13 @@ def run_ours(args):
     pcs = {}
     solve_kw = dict(tol=1e-10, restart=args.restart, maxit=60000, mode=args.mode, orth=args.orth, basis=args.basis)
     for pc in () if args.no_forms else ("d", "face_schur"):
-        pr.condense(precond=pc, **condense_flags(args.mode, split))
+        pr.condense(precond=pc, **condense_flags(args.mode, args.elim))
         g = pr.rhs()
         pr.solve(g, **solve_kw)
         t0, t1, t2 = ev(), ev(), ev()
         torch.cuda.synchronize()
         t0.record(stream)
-        pr.condense(precond=pc, **condense_flags(args.mode, split))
+        pr.condense(precond=pc, **condense_flags(args.mode, args.elim))
         g = pr.rhs()
         t1.record(stream)
         x, rep, st = pr.solve(g, **solve_kw)
@@ -792,16 +821,19 @@ def bench_mixed_precision_n256(stream):
     u_ex = torch.sin(math.pi * xy[..., 0]) * torch.sin(math.pi * xy[..., 1])
     del xy
     out = {"workload": f"n={cfg['n']} m={cfg['m']} p={cfg['p']} beta=50(cos 0.3, sin 0.3) kappa=1, "
-                       "u = sin(pi x) sin(pi y); face-block preconditioner, GMRES(80), orth 2",
+                       "u = sin(pi x) sin(pi y); face-block preconditioner, GMRES(80), orth 3",
            "N_tr": pr.info["N_tr"], "forms": {}}
     sols = {}
-    for name, (mode, basis, spl) in FORMS.items():
+    for name, (mode, basis, elim) in FORMS.items():
+        if name == "fp64_dfma":
+            continue
         a, b = ev(), ev()
         torch.cuda.synchronize()
         a.record(stream)
         # factors not kept (131 072 local systems would take 169 GB): chunked condensation, the
         # back-solve condenses each chunk again
-        pr.condense(keep_factors=False, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=spl,
+        pr.condense(keep_factors=False, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=elim == "split",
+                    tc_update=elim == "tc",
                     precond="face_schur")
         b.record(stream)
         g = pr.rhs()
@@ -809,12 +841,12 @@ def bench_mixed_precision_n256(stream):
         t0, t1 = ev(), ev()
         torch.cuda.synchronize()
         t0.record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=80, maxit=60000, mode=mode, orth=2, basis=basis)
+        x, rep, st = pr.solve(g, tol=1e-10, restart=80, maxit=60000, mode=mode, orth=3, basis=basis)
         t1.record(stream)
         torch.cuda.synchronize()
         u, q = pr.recover(x)
         sols[name] = (x, u, q)
-        out["forms"][name] = {"dtype": FORM_DTYPES[(mode, basis, spl)], "condense_s": a.elapsed_time(b) / 1e3,
+        out["forms"][name] = {"dtype": FORM_DTYPES[(mode, basis, elim)], "condense_s": a.elapsed_time(b) / 1e3,
                               "solve_s": t0.elapsed_time(t1) / 1e3, "iterations": rep["iterations"],
                               "rel_residual": rep["rel_residual"], "converged": bool(rep["converged"]),
                               "max_nodal_error_u": float((u - u_ex).abs().max())}

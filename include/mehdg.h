@@ -191,6 +191,14 @@ typedef struct {
 #define HDG_STORE_DF64 4u      /* also keep the preconditioned blocks as FP32 hi/lo pairs (8 bytes per entry) */
 #define HDG_SPLIT_UPDATE 8u    /* eliminate in split-FP32 arithmetic on the FP32 pipe (formation, pivot search,
                                   panel, triangular solves and trailing updates); the stored entries are FP64 */
+#define HDG_TC_UPDATE 32u     /* FP64-accurate elimination with the trailing updates on the tensor cores: 32-column
+                                  panels (pivot search, panel LU, U12 = L11^-1 A12) in FP64, and A22 -= L21 U12
+                                  as exact products of 8-bit slices of the power-of-two-scaled rows of L21 and
+                                  columns of U12 (seven slices each, 28 bf16 tcgen05 products per panel and tile,
+                                  FP32 level sums exact below 2^24) combined in FP64; the dropped parts are below
+                                  2^-50 of the row and column scales, under the FP64 rounding of the same dot
+                                  product. Excludes HDG_SPLIT_UPDATE. HDG_ERR_TIMEOUT if a tensor-core wait
+                                  gives up. No counterpart in the paper (its local solver is LAPACK LU). */
 #define HDG_PRECOND_FACE_SCHUR 16u  /* precondition with the inverted diagonal face blocks of the condensed
                                        operator, S_ff = sum over both sides of S_e's face rows and columns,
                                        instead of D_f of Sec. 6.1 (folded into the stored preconditioned rows

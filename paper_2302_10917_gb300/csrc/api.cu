@@ -441,10 +441,13 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   NvtxRange nvtx_range("hdg_condense");
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
-  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE | HDG_PRECOND_FACE_SCHUR))
+  if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE | HDG_PRECOND_FACE_SCHUR |
+                HDG_TC_UPDATE))
     return set_err(c, HDG_ERR_ARG, "unknown flags");
+  if ((flags & HDG_SPLIT_UPDATE) && (flags & HDG_TC_UPDATE))
+    return set_err(c, HDG_ERR_ARG, "HDG_SPLIT_UPDATE and HDG_TC_UPDATE exclude each other");
   if (c->lv) return level_condense(c, flags);
-  const int split = (flags & HDG_SPLIT_UPDATE) ? 1 : 0;
+  const int split = update_kind(flags);
   const Params& P = c->prm;
   cudaError_t e;
   const size_t sblk = (size_t)P.N * 3 * P.n_t * P.P1;
@@ -526,7 +529,11 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_err(c, e, "condense");
   c->flags = flags;
   for (int64_t i = 0; i < P.N; ++i)
-    if (info[i]) {
+    if (info[i] < 0) {
+      c->state = 1;
+      return set_err(c, HDG_ERR_TIMEOUT, "condensation: the tensor-core update of element " + std::to_string(i) +
+                                             " did not complete within the bounded wait");
+    } else if (info[i]) {
       c->state = 1;
       return set_err(c, HDG_ERR_SINGULAR, "zero pivot in column " + std::to_string(info[i] - 1) + " of element " +
                                                 std::to_string(i));
@@ -722,7 +729,7 @@ hdg_status hdg_recover(hdg_ctx* c, const double* x, double* u, double* q, int nr
     for (int64_t e0 = 0; e0 < P.N; e0 += c->ws_slots) {
       const int64_t cnt = std::min<int64_t>(c->ws_slots, P.N - e0);
       e = launch_condense(P, c->dt, c->d_kappa, c->f_qp, gh, c->d_ws, e0, cnt, 0, 0, nullptr, nullptr, nullptr,
-                          nullptr, nullptr, c->stream, (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
+                          nullptr, nullptr, c->stream, update_kind(c->flags));
       if (e != cudaSuccess) return cuda_err(c, e, "refactor");
       c->launches += 1;
       if (nrhs > 1) {

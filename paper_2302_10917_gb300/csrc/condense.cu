@@ -48,7 +48,8 @@ struct CondArgs {
   float* St32;
   double* gel;
   int* info;
-  int split_update;       // 1: condense_df_kernel (split-FP32 elimination on the FP32 pipe)
+  int split_update;       // 1: condense_df_kernel (split-FP32 elimination on the FP32 pipe),
+                          // 2: condense_tc_kernel (FP64 panels, trailing updates on the tensor cores)
   int* piv;               // [N][Q] pivot row of every column (factors kept), or null
   // one refinement level of a level mesh: the launch covers slots e0.. of the
   // element list elist (outputs, workspace, info and pivots by slot; geometry,
@@ -107,22 +108,14 @@ __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   }
 }
 
-__global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
+// Forms element e's bordered system in W (rows R, leading dimension ld; FP64):
+// [A_u B_u F; C_u D_u 0] from the reference tables and the element's geometry,
+// kappa, tau and source (the load columns use proj as shared scratch). Block-wide;
+// ends with a barrier.
+__device__ void form_system(const CondArgs& a, int e, double* W, double* proj) {
   const Params& P = a.prm;
-  const int eb = (int)(a.e0 + blockIdx.x);
-  if (eb >= a.nslots) return;
-  const int e = a.elist ? a.elist[eb] : eb;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, Cc = P.Cc, ld = P.ld;
-  double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)R * ld;
-
-  extern __shared__ double smem[];
-  double* Ls = smem;                       // [R][LDP]
-  double* Us = smem + (size_t)R * LDP;     // [NB][ld]
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  __shared__ int piv_s[NB];
-
+  const int Q = P.Q, nt = P.n_t, P1 = P.P1, R = P.R, ld = P.ld;
   // ---------------------------------------------------------- element data
   ElemGeom g;
   elem_geom(e, P.n, g);
@@ -198,7 +191,7 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
   __syncthreads();
   // load columns Q + n_t + r: per sub-triangle projections of source r (in
   // the panel area, free before the LU starts), summed per lattice node
-  load_columns(a, e, g.detJ, Ls, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = v; }, ts, bxi,
+  load_columns(a, e, g.detJ, proj, [&](int i, int r, double v) { W[(size_t)i * ld + Q + nt + r] = v; }, ts, bxi,
                beta_);
   // tau E: E = sum_k L_k Pi_k^T Gh Pi_k (edge by edge: corner nodes are shared)
   for (int k = 0; k < 3; ++k) {
@@ -210,108 +203,148 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
     __syncthreads();
   }
 
+}
+
+// One panel of the bordered LU (columns j0 .. j0 + nb - 1, nb = min(NBW, Q - j0)):
+// the panel rows j0 .. R - 1 in shared memory (Ls, row stride NBW + 1), partial
+// pivoting over the u-rows, the factored panel written back to W, then the row
+// interchanges and U12 = L11^-1 A12 on the columns right of the panel (one column
+// per thread; also kept in Us, row stride ld, when KEEP_U). Returns nb; ends with a
+// barrier when columns remain right of the panel.
+template <int NBW, bool KEEP_U>
+__device__ int factor_panel(const CondArgs& a, double* W, double* Ls, double* Us, int j0, int eb, int* piv_s,
+                            double* red_v, int* red_i, int& singular_col) {
+  const Params& P = a.prm;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Q = P.Q, R = P.R, Cc = P.Cc, ld = P.ld;
+  constexpr int LDPW = NBW + 1;
+  const int nb = min(NBW, Q - j0);
+  const int rows = R - j0;
+  for (int idx = tid; idx < rows * NBW; idx += nthr) {
+    const int r = idx / NBW, c = idx - r * NBW;
+    Ls[r * LDPW + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    // pivot: largest |a| among u-rows j0+c .. Q-1 (first one on ties)
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < Q - j0; r += nthr) {
+      const double v = fabs(Ls[r * LDPW + c]);
+      if (v > best) { best = v; bi = r; }
+    }
+    warp_argmax(best, bi);
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid < 32) {
+      const int nw = nthr >> 5;
+      double v = tid < nw ? red_v[tid] : -1.0;
+      int ii = tid < nw ? red_i[tid] : 0x7fffffff;
+      warp_argmax(v, ii);
+      if (tid == 0) piv_s[c] = ii;
+    }
+    __syncthreads();
+    const int pr = piv_s[c];
+    if (a.piv) {
+      // kept factors: record the interchange and apply it to the columns of
+      // the earlier panels too, so that rows 0..Q-1 hold P A_u = L U
+      if (tid == 0) a.piv[(size_t)eb * Q + j0 + c] = j0 + pr;
+      if (pr != c)
+        for (int cc = tid; cc < j0; cc += nthr) {
+          double* x0 = W + (size_t)(j0 + c) * ld + cc;
+          double* x1 = W + (size_t)(j0 + pr) * ld + cc;
+          const double t0 = *x0;
+          *x0 = *x1;
+          *x1 = t0;
+        }
+    }
+    if (pr != c) {
+      for (int cc = tid; cc < nb; cc += nthr) {
+        const double t0 = Ls[c * LDPW + cc];
+        Ls[c * LDPW + cc] = Ls[pr * LDPW + cc];
+        Ls[pr * LDPW + cc] = t0;
+      }
+      __syncthreads();
+    }
+    const double d = Ls[c * LDPW + c];
+    if (d == 0.0 && singular_col < 0) singular_col = j0 + c;
+    const double inv = (d != 0.0) ? 1.0 / d : 0.0;
+    for (int r = c + 1 + tid; r < rows; r += nthr) Ls[r * LDPW + c] *= inv;
+    __syncthreads();
+    const int nrem = nb - c - 1;
+    if (nrem > 0) {
+      const int nr = rows - c - 1;
+      for (int idx = tid; idx < nr * nrem; idx += nthr) {
+        const int r = c + 1 + idx / nrem, cc = c + 1 + idx % nrem;
+        Ls[r * LDPW + cc] -= Ls[r * LDPW + c] * Ls[c * LDPW + cc];
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < rows * nb; idx += nthr) {
+    const int r = idx / nb, c = idx - r * nb;
+    W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDPW + c];
+  }
+  const int jb = j0 + nb, ncol = Cc - jb;
+  if (ncol > 0) {
+    // row interchanges and U12 = L11^-1 A12, one column per thread
+    for (int j = jb + tid; j < Cc; j += nthr) {
+      double u[NBW];
+      for (int c = 0; c < nb; ++c) {
+        const int pr = piv_s[c];
+        if (pr != c) {
+          double* x0 = W + (size_t)(j0 + c) * ld + j;
+          double* x1 = W + (size_t)(j0 + pr) * ld + j;
+          const double t0 = *x0;
+          *x0 = *x1;
+          *x1 = t0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NBW; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : 0.0;
+#pragma unroll
+      for (int c = 1; c < NBW; ++c) {
+        if (c < nb) {
+          double s = u[c];
+#pragma unroll
+          for (int t = 0; t < c; ++t) s -= Ls[c * LDPW + t] * u[t];
+          u[c] = s;
+        }
+      }
+      for (int c = 0; c < nb; ++c) {
+        W[(size_t)(j0 + c) * ld + j] = u[c];
+        if (KEEP_U) Us[c * ld + j] = u[c];
+      }
+    }
+    __syncthreads();
+  }
+  return nb;
+}
+
+__global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
+  const Params& P = a.prm;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int Q = P.Q, R = P.R, Cc = P.Cc, ld = P.ld;
+  double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)R * ld;
+
+  extern __shared__ double smem[];
+  double* Ls = smem;                       // [R][LDP]
+  double* Us = smem + (size_t)R * LDP;     // [NB][ld]
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int piv_s[NB];
+
+  form_system(a, e, W, Ls);
+
   // ------------------------------------------------------- blocked LU, Q pivots
   int singular_col = -1;
   for (int j0 = 0; j0 < Q; j0 += NB) {
-    const int nb = min(NB, Q - j0);
-    const int rows = R - j0;
-    for (int idx = tid; idx < rows * NB; idx += nthr) {
-      const int r = idx / NB, c = idx - r * NB;
-      Ls[r * LDP + c] = (c < nb) ? W[(size_t)(j0 + r) * ld + j0 + c] : 0.0;
-    }
-    __syncthreads();
-    for (int c = 0; c < nb; ++c) {
-      // pivot: largest |a| among u-rows j0+c .. Q-1 (first one on ties)
-      double best = -1.0;
-      int bi = c;
-      for (int r = c + tid; r < Q - j0; r += nthr) {
-        const double v = fabs(Ls[r * LDP + c]);
-        if (v > best) { best = v; bi = r; }
-      }
-      warp_argmax(best, bi);
-      if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-      __syncthreads();
-      if (tid < 32) {
-        const int nw = nthr >> 5;
-        double v = tid < nw ? red_v[tid] : -1.0;
-        int ii = tid < nw ? red_i[tid] : 0x7fffffff;
-        warp_argmax(v, ii);
-        if (tid == 0) piv_s[c] = ii;
-      }
-      __syncthreads();
-      const int pr = piv_s[c];
-      if (a.piv) {
-        // kept factors: record the interchange and apply it to the columns of
-        // the earlier panels too, so that rows 0..Q-1 hold P A_u = L U
-        if (tid == 0) a.piv[(size_t)eb * Q + j0 + c] = j0 + pr;
-        if (pr != c)
-          for (int cc = tid; cc < j0; cc += nthr) {
-            double* x0 = W + (size_t)(j0 + c) * ld + cc;
-            double* x1 = W + (size_t)(j0 + pr) * ld + cc;
-            const double t0 = *x0;
-            *x0 = *x1;
-            *x1 = t0;
-          }
-      }
-      if (pr != c) {
-        for (int cc = tid; cc < nb; cc += nthr) {
-          const double t0 = Ls[c * LDP + cc];
-          Ls[c * LDP + cc] = Ls[pr * LDP + cc];
-          Ls[pr * LDP + cc] = t0;
-        }
-        __syncthreads();
-      }
-      const double d = Ls[c * LDP + c];
-      if (d == 0.0 && singular_col < 0) singular_col = j0 + c;
-      const double inv = (d != 0.0) ? 1.0 / d : 0.0;
-      for (int r = c + 1 + tid; r < rows; r += nthr) Ls[r * LDP + c] *= inv;
-      __syncthreads();
-      const int nrem = nb - c - 1;
-      if (nrem > 0) {
-        const int nr = rows - c - 1;
-        for (int idx = tid; idx < nr * nrem; idx += nthr) {
-          const int r = c + 1 + idx / nrem, cc = c + 1 + idx % nrem;
-          Ls[r * LDP + cc] -= Ls[r * LDP + c] * Ls[c * LDP + cc];
-        }
-        __syncthreads();
-      }
-    }
-    for (int idx = tid; idx < rows * nb; idx += nthr) {
-      const int r = idx / nb, c = idx - r * nb;
-      W[(size_t)(j0 + r) * ld + j0 + c] = Ls[r * LDP + c];
-    }
+    const int nb = factor_panel<NB, true>(a, W, Ls, Us, j0, eb, piv_s, red_v, red_i, singular_col);
     const int jb = j0 + nb, ncol = Cc - jb;
     if (ncol > 0) {
-      // row interchanges and U12 = L11^-1 A12, one column per thread
-      for (int j = jb + tid; j < Cc; j += nthr) {
-        double u[NB];
-        for (int c = 0; c < nb; ++c) {
-          const int pr = piv_s[c];
-          if (pr != c) {
-            double* x0 = W + (size_t)(j0 + c) * ld + j;
-            double* x1 = W + (size_t)(j0 + pr) * ld + j;
-            const double t0 = *x0;
-            *x0 = *x1;
-            *x1 = t0;
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < NB; ++c) u[c] = (c < nb) ? W[(size_t)(j0 + c) * ld + j] : 0.0;
-#pragma unroll
-        for (int c = 1; c < NB; ++c) {
-          if (c < nb) {
-            double s = u[c];
-#pragma unroll
-            for (int t = 0; t < c; ++t) s -= Ls[c * LDP + t] * u[t];
-            u[c] = s;
-          }
-        }
-        for (int c = 0; c < nb; ++c) {
-          W[(size_t)(j0 + c) * ld + j] = u[c];
-          Us[c * ld + j] = u[c];
-        }
-      }
-      __syncthreads();
       // trailing update A22 -= L21 U12 (rows jb..R-1, columns jb..Cc-1)
       const int nrow = R - jb;
       const int ntile = (nrow + RT - 1) / RT;
@@ -345,6 +378,337 @@ __global__ void __launch_bounds__(256) condense_kernel(CondArgs a) {
 
 // S_e, its preconditioned copies and the element right-hand side from the
 // factored bordered system (FP64 entries).
+// ------------------------------------------------ tensor-core trailing updates
+// condense_tc_kernel eliminates with 32-column panels: pivot search, panel LU
+// and U12 = L11^-1 A12 in FP64 as above, and the trailing update
+// A22 -= L21 U12 on the tensor cores, FP64-accurate through exact slices
+// (Ozaki's splitting of floating-point matrix products into error-free partial
+// products, carried out here with integer bit operations):
+//  * every row r of L21 is scaled by 2^-e_r (2^e_r above the row's largest
+//    magnitude), every column c of U12 by 2^-f_c, and each scaled entry, a
+//    fixed-point number below 1, is cut into 7 slices of 8 bits,
+//    x = sum_i s_i 2^-8(i+1) + (less than 2^-56), |s_i| <= 255 (bf16-exact);
+//  * the slice products with i + j = t are summed into one FP32 accumulator per
+//    level t = 0..6 in tensor memory (tcgen05.mma kind::f16, M = 128, N = 32,
+//    K = 16): products below 2^16, K = 32 of them per pair, at most 7 pairs,
+//    so every level sum is an integer below 2^24 and exact;
+//  * the levels are combined as 2^(e_r + f_c - 16) (A_0 + 2^-8 A_1 + 2^-16 A_2
+//    + 2^-24 A_3 + 2^-32 (A_4 + 2^-8 A_5 + 2^-16 A_6)), the first four terms
+//    exactly in FP64, the last three in FP32, and subtracted from A22 in FP64.
+// The dropped parts (slice truncation, levels above 6, the FP32 tail) are below
+// 2^-50 of 2^(e_r + f_c) per entry, under the FP64 rounding bound of a 32-term
+// dot product. FP64 work per trailing entry and panel: 5 FMAs instead of 32.
+constexpr int TCB = 32;                   // panel width = K of the slice products
+constexpr int TC_SLICES = 7;
+constexpr int TC_LEVELS = 7;              // t = i + j <= 6
+constexpr int TC_M = 128, TC_N = 32;      // row tile (MMA M) and column tile (MMA N)
+constexpr int TC_TMEM_COLS = 256;         // 7 levels x 32 columns, rounded to a power of two
+constexpr int TC_EXP_NONE = -4000;        // a row or column without a normal entry
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;
+constexpr size_t TC_A_BYTES = (size_t)TC_SLICES * TC_M * TCB * 2;
+constexpr size_t TC_B_BYTES = (size_t)TC_SLICES * TC_N * TCB * 2;
+
+size_t condense_tc_smem_bytes(const Params& P) {
+  const size_t panel = (size_t)P.R * (TCB + 1) * sizeof(double);
+  const size_t slices = TC_A_BYTES + TC_B_BYTES;
+  return panel > slices ? panel : slices;
+}
+
+namespace {
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// element offset of (row, k) in a K-major slice plane without swizzle: 8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 bytes apart, 8-row groups
+// 4 x 128 bytes apart (K = 32)
+__device__ __forceinline__ int tc_kmaj(int row, int k) {
+  return (((row >> 3) * (TCB / 8) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// shared-memory matrix descriptor (no swizzle): start, leading (K) and stride (8-row) byte offsets
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// 2^e above |x|max for a row or column (TC_EXP_NONE without a normal entry)
+__device__ __forceinline__ int tc_exp_above(double mx) {
+  const int E = (int)((__double_as_longlong(mx) >> 52) & 0x7FF);
+  return E == 0 ? TC_EXP_NONE : E - 1023 + 1;
+}
+
+// bf16 bits of sign * n for an integer 0 <= n <= 255 (exact)
+__device__ __forceinline__ uint16_t tc_bf16_int(uint32_t n, uint32_t sgn) {
+  if (n == 0) return 0;
+  const int p = 31 - __clz(n);
+  return (uint16_t)((sgn << 15) | ((uint32_t)(127 + p) << 7) | ((n << (7 - p)) & 0x7Fu));
+}
+
+// the 7 slices of v 2^-e (|v| < 2^e) into planes dst[i * plane]
+__device__ __forceinline__ void tc_slice(double v, int e, uint16_t* dst, int plane) {
+  uint64_t F = 0;
+  uint32_t sgn = 0;
+  if (e != TC_EXP_NONE) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    sgn = (uint32_t)(b >> 63);
+    if (E != 0) {
+      const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = (E - 1023) + 4 - e;   // F = |v| 2^(56 - e) = M 2^sh, sh <= 3
+      F = sh >= 0 ? (M << sh) : (-sh < 64 ? (M >> -sh) : 0ull);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TC_SLICES; ++i) dst[i * plane] = tc_bf16_int((uint32_t)(F >> (48 - 8 * i)) & 0xFFu, sgn);
+}
+
+// exact FP64 value of an FP32 integer below 2^24 (bit conversion on the integer pipe)
+__device__ __forceinline__ double tc_f2d(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if ((b & 0x7FFFFFFFu) == 0) return 0.0;
+  const uint64_t r = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(((b >> 23) & 0xFFu) + 896u) << 52) |
+                     ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)r);
+}
+
+// FP64 value of any FP32 number by bit conversion (normal numbers exactly; zero and FP32
+// subnormals, below 2^-126, give 0)
+__device__ __forceinline__ double tc_f2d_any(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if ((b & 0x7F800000u) == 0) return 0.0;
+  const uint64_t r = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(((b >> 23) & 0xFFu) + 896u) << 52) |
+                     ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)r);
+}
+
+// 2^E as a double
+__device__ __forceinline__ double tc_pow2(int E) {
+  if (E >= -1022 && E <= 1023) return __longlong_as_double((long long)((uint64_t)(E + 1023) << 52));
+  return scalbn(1.0, E);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+}  // namespace
+
+// A22 -= L21 U12 for the panel j0 .. j0 + nb - 1 on the tensor cores: 128-row
+// tiles (A slices made once per tile) times 32-column tiles (B slices per
+// tile), 28 slice products of K = 32 (56 MMAs of K = 16) into 7 level
+// accumulators, then the FP64 epilogue (8 warps: TMEM lane quarter w % 4,
+// column half w / 4). Returns false if the MMAs did not complete within the
+// bounded wait (the caller then stops).
+__device__ bool tc_trailing_update(const CondArgs& a, double* W, int j0, int nb, uint16_t* As, uint16_t* Bs,
+                                   int* er_s, int* ec_s, uint32_t tmem, uint64_t* mbar, uint32_t& phase,
+                                   int* s_fail) {
+  const Params& P = a.prm;
+  const int R = P.R, Cc = P.Cc, ld = P.ld, jb = j0 + nb;
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  // kind::f16 instruction descriptor: D FP32, A and B bf16, both K-major, N = 32, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  constexpr int APL = TC_M * TCB, BPL = TC_N * TCB;   // elements per slice plane
+  for (int r0 = jb; r0 < R; r0 += TC_M) {
+    const int mr = min(TC_M, R - r0);
+    if (tid < TC_M) {
+      double mx = 0.0;
+      if (tid < mr)
+        for (int c = 0; c < nb; ++c) mx = fmax(mx, fabs(W[(size_t)(r0 + tid) * ld + j0 + c]));
+      er_s[tid] = tid < mr ? tc_exp_above(mx) : TC_EXP_NONE;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < TC_M * TCB; idx += nthr) {
+      const int i = idx / TCB, k = idx - i * TCB;
+      const double v = (i < mr && k < nb) ? W[(size_t)(r0 + i) * ld + j0 + k] : 0.0;
+      tc_slice(v, er_s[i], As + tc_kmaj(i, k), APL);
+    }
+    for (int c0 = jb; c0 < Cc; c0 += TC_N) {
+      const int nc = min(TC_N, Cc - c0);
+      if (tid < TC_N) {
+        double mx = 0.0;
+        if (tid < nc)
+          for (int k = 0; k < nb; ++k) mx = fmax(mx, fabs(W[(size_t)(j0 + k) * ld + c0 + tid]));
+        ec_s[tid] = tid < nc ? tc_exp_above(mx) : TC_EXP_NONE;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < TC_N * TCB; idx += nthr) {
+        const int j = idx / TCB, k = idx - j * TCB;
+        const double v = (j < nc && k < nb) ? W[(size_t)(j0 + k) * ld + c0 + j] : 0.0;
+        tc_slice(v, ec_s[j], Bs + tc_kmaj(j, k), BPL);
+      }
+      // the slices (generic-proxy stores) become visible to the tensor cores' async proxy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t a0 = tc_smem(As), b0 = tc_smem(Bs);
+#pragma unroll 1
+        for (int t = 0; t < TC_LEVELS; ++t)
+#pragma unroll 1
+          for (int i = 0; i <= t; ++i) {
+            const int j = t - i;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {   // K = 32 as two K = 16 halves (two core matrices each)
+              const uint64_t ad = tc_desc(a0 + (uint32_t)(i * APL * 2 + h * 256), 128, 4 * 128);
+              const uint64_t bd = tc_desc(b0 + (uint32_t)(j * BPL * 2 + h * 256), 128, 4 * 128);
+              tc_mma(tmem + (uint32_t)(t * TC_N), ad, bd, idesc, (i > 0 || h > 0) ? 1u : 0u);
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_smem(mbar))
+                     : "memory");
+      }
+      // this thread's 16 entries of A22 (row i of the tile, column half hh), loaded while the MMAs run
+      const int g = warp & 3, hh = warp >> 2;
+      const int i = g * 32 + lane;
+      const bool row_live = i < mr && er_s[i] != TC_EXP_NONE;
+      double* row = W + (size_t)(r0 + (i < mr ? i : 0)) * ld + c0 + hh * 16;
+      const int ncq = max(0, min(16, nc - hh * 16));   // live columns of this half
+      double wv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) wv[q] = (row_live && q < ncq) ? row[q] : 0.0;
+      const bool ok = tc_wait(tc_smem(mbar), phase);
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) atomicExch(s_fail, 1);
+      __syncthreads();
+      if (*s_fail) return false;
+      // epilogue: levels 6..4 in FP32, 3..0 exactly in FP64 (every lane loads: tcgen05.ld is warp-wide)
+      const uint32_t tl = tmem + ((uint32_t)(g * 32) << 16) + (uint32_t)(hh * 16);
+      float lv[16], tail[16];
+      tc_ld16(tl + 6 * TC_N, tail);
+      tc_ld16(tl + 5 * TC_N, lv);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) tail[q] = fmaf(tail[q], 0.00390625f, lv[q]);
+      tc_ld16(tl + 4 * TC_N, lv);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) tail[q] = fmaf(tail[q], 0.00390625f, lv[q]);
+      // FP64 work only in warps with a live row and only on live columns (both warp-uniform
+      // tests: the FP64 pipe spends a warp instruction's time whatever its active lanes)
+      const bool warp_live = __any_sync(0xffffffffu, row_live);
+      double sum[16];
+      tc_ld16(tl + 0 * TC_N, lv);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sum[q] = tc_f2d(lv[q]);
+#pragma unroll
+      for (int t = 1; t < 4; ++t) {
+        tc_ld16(tl + t * TC_N, lv);
+        const double w8 = t == 1 ? 0.00390625 : (t == 2 ? 1.52587890625e-05 : 5.9604644775390625e-08);
+        if (warp_live) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < ncq) sum[q] = fma(tc_f2d(lv[q]), w8, sum[q]);
+        }
+      }
+      if (warp_live) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q < ncq) {
+            const int jc = hh * 16 + q;
+            const double s = fma(tc_f2d_any(tail[q]), 2.3283064365386963e-10, sum[q]);   // 2^-32
+            const double upd = fma(-tc_pow2(er_s[i] + ec_s[jc] - 16), s, wv[q]);
+            if (row_live && ec_s[jc] != TC_EXP_NONE) row[q] = upd;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+// The bordered LU of condense_kernel with 32-column panels and the trailing
+// updates on the tensor cores (tc_trailing_update); same inputs, outputs and
+// workspace layout. One CTA of 256 threads per element, two per SM (the panel
+// and the slice planes share the dynamic shared memory; 256 TMEM columns each).
+__global__ void __launch_bounds__(256, 2) condense_tc_kernel(CondArgs a) {
+  const Params& P = a.prm;
+  const int eb = (int)(a.e0 + blockIdx.x);
+  if (eb >= a.nslots) return;
+  const int e = a.elist ? a.elist[eb] : eb;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Q = P.Q, R = P.R, Cc = P.Cc, ld = P.ld;
+  double* W = a.ws + (size_t)(a.slot_is_element ? eb : blockIdx.x) * (size_t)R * ld;
+
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  double* Ls = reinterpret_cast<double*>(tsm);                               // [R][TCB + 1] (panel phase)
+  uint16_t* As = reinterpret_cast<uint16_t*>(tsm);                           // [7][128 x 32] (update phase)
+  uint16_t* Bs = reinterpret_cast<uint16_t*>(tsm + TC_A_BYTES);              // [7][32 x 32]
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int piv_s[TCB];
+  __shared__ int er_s[TC_M], ec_s[TC_N];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_s;
+  __shared__ int s_fail;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_s)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_s;
+
+  form_system(a, e, W, Ls);
+
+  int singular_col = -1;
+  uint32_t phase = 0;
+  for (int j0 = 0; j0 < Q; j0 += TCB) {
+    const int nb = factor_panel<TCB, false>(a, W, Ls, nullptr, j0, eb, piv_s, red_v, red_i, singular_col);
+    if (Cc - (j0 + nb) > 0 && !tc_trailing_update(a, W, j0, nb, As, Bs, er_s, ec_s, tmem, &mbar, phase, &s_fail))
+      break;
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  // info: 0 fine, c + 1 zero pivot in column c, -1 the tensor cores did not finish within the bounded wait
+  if (tid == 0 && a.info) a.info[eb] = s_fail ? -1 : (singular_col >= 0 ? singular_col + 1 : 0);
+  if (a.write_outputs && !s_fail) condense_outputs(a, W, e, eb);
+}
+
 __device__ void condense_outputs(const CondArgs& a, const double* W, int e, int eb) {
   const Params& P = a.prm;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -940,7 +1304,13 @@ static cudaError_t launch_condense_args(CondArgs& a, int64_t count, cudaStream_t
   const Params& P = a.prm;
   const int split_update = a.split_update;
   const size_t sm = condense_smem_bytes(P);
-  if (split_update) {
+  if (split_update == 2) {
+    const size_t smt = condense_tc_smem_bytes(P);
+    if (smt > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t err = cudaFuncSetAttribute(condense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+    if (err != cudaSuccess) return err;
+    condense_tc_kernel<<<(unsigned)count, 256, smt, st>>>(a);
+  } else if (split_update) {
     cudaError_t err = cudaFuncSetAttribute(condense_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (err != cudaSuccess) return err;
     condense_df_kernel<<<(unsigned)count, 256, sm, st>>>(a);

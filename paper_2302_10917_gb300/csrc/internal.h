@@ -7,6 +7,12 @@
 #include <vector>
 #include "../../include/mehdg.h"
 
+// Kind of elimination requested by hdg_condense's flags: 0 FP64 (DFMA), 1 split-FP32,
+// 2 FP64 panels with the trailing updates on the tensor cores.
+inline int update_kind(unsigned flags) {
+  return (flags & HDG_SPLIT_UPDATE) ? 1 : ((flags & HDG_TC_UPDATE) ? 2 : 0);
+}
+
 namespace mehdg {
 
 // ---------------------------------------------------------------------------

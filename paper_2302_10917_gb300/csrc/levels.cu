@@ -796,7 +796,7 @@ hdg_status level_set_source(hdg_ctx* c, const double* f_qp, const double* gD_qp,
 
 hdg_status level_condense(hdg_ctx* c, unsigned flags) {
   LevelMesh& L = *c->lv;
-  const int split = (flags & HDG_SPLIT_UPDATE) ? 1 : 0;
+  const int split = update_kind(flags);
   const int keep = (flags & HDG_KEEP_FACTORS) ? 1 : 0;
   const int nrhs = c->prm.nrhs;
   cudaError_t e;
@@ -889,7 +889,11 @@ hdg_status level_condense(hdg_ctx* c, unsigned flags) {
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
       return lv_cuda(c, e, "condense");
     for (int i = 0; i < B.count; ++i)
-      if (info[i]) {
+      if (info[i] < 0) {
+        c->state = 1;
+        return lv_err(c, HDG_ERR_TIMEOUT, "condensation: the tensor-core update of element " + std::to_string(el[i]) +
+                                              " did not complete within the bounded wait");
+      } else if (info[i]) {
         c->state = 1;
         return lv_err(c, HDG_ERR_SINGULAR, "zero pivot in column " + std::to_string(info[i] - 1) + " of element " +
                                                std::to_string(el[i]));
@@ -929,7 +933,7 @@ hdg_status level_recover(hdg_ctx* c, const double* x, double* u, double* q, int 
         if (!keep) {
           e = launch_condense_bin(P, B.dt, c->d_kappa, c->f_qp, L.d_qoff, L.qoff.back(), gh, B.d_ws, B.d_elist,
                                   B.count, e0, cnt, 0, 0, nullptr, nullptr, nullptr, c->stream,
-                                  (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
+                                  update_kind(c->flags));
           c->launches += 1;
           if (e != cudaSuccess) return lv_cuda(c, e, "refactor");
         }
@@ -945,7 +949,7 @@ hdg_status level_recover(hdg_ctx* c, const double* x, double* u, double* q, int 
       const int64_t cnt = keep ? B.count : std::min<int64_t>(B.ws_slots, B.count - e0);
       if (!keep) {
         e = launch_condense_bin(P, B.dt, c->d_kappa, c->f_qp, L.d_qoff, L.qoff.back(), gh, B.d_ws, B.d_elist, B.count,
-                                e0, cnt, 0, 0, nullptr, nullptr, nullptr, c->stream, (c->flags & HDG_SPLIT_UPDATE) ? 1 : 0);
+                                e0, cnt, 0, 0, nullptr, nullptr, nullptr, c->stream, update_kind(c->flags));
         c->launches += 1;
         if (e != cudaSuccess) return lv_cuda(c, e, "refactor");
       }

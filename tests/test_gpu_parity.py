@@ -99,6 +99,28 @@ def test_split_fp32_panel_updates_keep_fp64_parity(case):
     gpu2.close()
 
 
+def test_tensor_core_updates_keep_fp64_parity(case):
+    """HDG_TC_UPDATE: 32-column FP64 panels, trailing updates as exact 8-bit slice products on
+    the tensor cores: Schur blocks, right-hand side and back-solve at the FP64 bounds."""
+    ora = case["ora"]
+    gpu2 = _lib_problem(case["n"], case["m"], case["p"], tuple(ora.beta), ora.kappa)
+    gpu2.set_source(torch.from_numpy(case["f"]), torch.from_numpy(case["gD"]))
+    gpu2.condense(keep_factors=True, tc_update=True)
+    S_gpu = gpu2.schur().cpu().numpy()
+    for e in range(S_gpu.shape[0]):
+        assert rel(S_gpu[e], case["S_el"][e]) < 1e-12, e
+    assert rel(gpu2.rhs().cpu().numpy(), case["g"]) < 1e-12
+    x = np.linalg.solve(ora.assemble_S(case["S_el"]), case["g"])
+    u_o, q_o = ora.recover(x, case["f"], case["ghat"])
+    u_g, q_g = gpu2.recover(torch.from_numpy(x))
+    assert rel(u_g.cpu().numpy(), u_o) < 1e-11 and rel(q_g.cpu().numpy(), q_o) < 1e-11
+    # without kept factors the back-solve condenses again with the same kernel
+    gpu2.condense(keep_factors=False, tc_update=True)
+    u_g, q_g = gpu2.recover(torch.from_numpy(x))
+    assert rel(u_g.cpu().numpy(), u_o) < 1e-11 and rel(q_g.cpu().numpy(), q_o) < 1e-11
+    gpu2.close()
+
+
 def test_condensed_rhs_matches(case):
     assert rel(case["gpu"].rhs().cpu().numpy(), case["g"]) < 1e-12
 
