@@ -36,12 +36,12 @@ WORKLOAD = ("2D steady advection-diffusion, 128x128 macro grid (32768 macro-tria
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12     # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # split-FP32 multiply-add (Dekker product + two-sum accumulation): 1 FMUL + 3 FFMA + 8 FADD
 DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
-# DRAM bytes (read + write) of one apply_vdf_kernel<1> launch per interior edge, from an ncu
-# capture at n = 64, m = 8, p = 3 (376.57 MB for 12 160 edges, 128-thread blocks); the traffic
-# scales with the edges. Only valid for that kernel and element (m = 8, p = 3).
-APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.57e6 / 12160
-# the same for apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors); None until captured
-APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3 = None
+# DRAM bytes (read + write) of one apply_vdf_kernel<1,1> launch per interior edge, from an ncu
+# capture at n = 64, m = 8, p = 3 (376.20 MB for 12 160 edges); the traffic scales with the
+# edges. Only valid for that kernel and element (m = 8, p = 3).
+APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.20e6 / 12160
+# the same for apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors): 376.72 MB for 12 160 edges at n = 64
+APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3 = 376.72e6 / 12160
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
@@ -76,6 +76,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-keep-factors", action="store_true",
                     help="do not keep the factored local systems (the back-solve condenses again; small device "
                          "footprint for profiler captures)")
+    ap.add_argument("--bulk-warps", type=int, default=0,
+                    help="with --mode 2 --basis 1: the pipelined bulk-copy apply with this many consumer warps per "
+                         "edge instead of the autotuned shape")
+    ap.add_argument("--maxit", type=int, default=60000,
+                    help="GMRES operator applications per solve; a value below what the solve needs (one restart "
+                         "cycle for a profiler's launch list) lets the step end unconverged: not a benchmark line")
     ap.add_argument("--n", type=int, default=0,
                     help="macro squares per side instead of the workload's (small cases for profiler captures)")
     return ap.parse_args(argv)
@@ -397,9 +403,10 @@ def run_ours(args):
         g = pr.rhs()
         if marks:
             marks[1].record(stream)
-        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=60000, mode=mode, orth=args.orth, basis=basis)
-        if st != 0:
-            raise RuntimeError(f"solve did not converge: {rep}")
+        x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=args.maxit, mode=mode, orth=args.orth,
+                              basis=basis, check=False)
+        if st != 0 and not (st == 6 and args.maxit < 60000):   # 6: HDG_ERR_NOCONV
+            raise RuntimeError(f"solve did not converge: {rep} (status {st})")
         if marks:
             marks[2].record(stream)
         u, q = pr.recover(x)
@@ -411,6 +418,9 @@ def run_ours(args):
     # the project's launch-shape autotuner runs once per problem (outside the timed region)
     step()
     tune = pr.autotune(mode=args.mode, restart=args.restart, basis=args.basis)
+    if args.bulk_warps:
+        pr.set_apply_shape(2, bulk_warps=args.bulk_warps)
+        tune["apply_bulk"] = args.bulk_warps
     for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
@@ -535,7 +545,7 @@ def run_ours(args):
                                                            else kname][1])
     roof = dict(rooflines[dom])
     roof["traffic"] = None
-    traffic_per_edge = {(0, 0): APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3}
+    traffic_per_edge = {(0, 0): APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3, (2, 1): APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3}
     if dom == "apply" and (cfg["m"], cfg["p"]) == (8, 3) and (args.mode, args.basis) in traffic_per_edge \
             and not tune.get("apply_bulk") and traffic_per_edge[(args.mode, args.basis)]:
         roof["traffic"] = traffic_per_edge[(args.mode, args.basis)] * n_int

@@ -110,6 +110,29 @@ def test_schur_blocks_and_rhs_match_the_oracle(case):
     assert np.array_equal(part, S[off[3]:off[7]])
 
 
+def test_tensor_core_elimination_on_level_meshes(case):
+    """HDG_TC_UPDATE on every level bin: lifted Schur blocks, right-hand side and back-solve
+    at the FP64 bounds."""
+    from paper_2302_10917_gb300 import OFF_SCHUR, Problem
+    ora = case["ora"]
+    pr = Problem(ora.n, 1, ora.p, beta=tuple(ora.beta), kappa=ora.kappa, levels=case["lev"])
+    try:
+        pr.set_source(torch.from_numpy(case["f"]), torch.from_numpy(case["gD"]))
+        pr.condense(keep_factors=True, tc_update=True)
+        S = pr.schur().cpu().numpy()
+        off = pr.offsets(OFF_SCHUR).numpy()
+        for e in range(ora.N):
+            nt = ora.n_t(e)
+            assert rel(S[off[e]:off[e + 1]].reshape(nt, nt), case["S"][e]) < 1e-12, e
+        assert rel(pr.rhs().cpu().numpy(), case["g"]) < 1e-12
+        x_dir = np.linalg.solve(ora.assemble_S(case["S"]), case["g"])
+        u, q = pr.recover(torch.from_numpy(x_dir))
+        u_o, q_o = ora.recover(x_dir, case["f"], case["gh"])
+        assert rel(u.cpu().numpy(), u_o) < 1e-11 and rel(q.cpu().numpy(), q_o) < 1e-11
+    finally:
+        pr.close()
+
+
 @pytest.mark.parametrize("prec", [64, 48, 33, 32])
 def test_apply_matches_the_oracle(case, prec):
     ora, gpu = case["ora"], case["gpu"]
