@@ -333,8 +333,8 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double*
 hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
 
 /* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to
- * the device, condenses (factors kept; for opts->mode 1 also the FP32 blocks
- * after FP64 elimination, for mode 2 the split-FP32 blocks after split-FP32
+ * the device, condenses (factors kept; modes 0 and 1 with HDG_TC_UPDATE, mode 1
+ * also keeping the FP32 blocks; mode 2 the split-FP32 blocks after split-FP32
  * elimination), assembles g, solves
  * from x = 0, recovers u and q and copies x, u, q back (each output may be
  * NULL to skip its copy). Synchronous. Same layouts as above. */

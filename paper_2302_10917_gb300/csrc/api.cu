@@ -784,10 +784,11 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
     cleanup();
     return cuda_err(c, e, "hdg_run_host upload");
   }
-  // the blocks the requested solve mode needs; FP64 local factorisations except with the split-FP32
-  // operator (mode 2), whose condensation eliminates in split-FP32 arithmetic too
+  // the blocks the requested solve mode needs; FP64-accurate local factorisations (FP64 panels,
+  // trailing updates on the tensor cores) except with the split-FP32 operator (mode 2), whose
+  // condensation eliminates in split-FP32 arithmetic too
   const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? HDG_STORE_FP32 : 0u) |
-                          (o->mode == 2 ? (HDG_STORE_DF64 | HDG_SPLIT_UPDATE) : 0u);
+                          (o->mode == 2 ? (HDG_STORE_DF64 | HDG_SPLIT_UPDATE) : HDG_TC_UPDATE);
   if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, cflags)) == HDG_OK &&
       (s = hdg_rhs(c, dgv)) == HDG_OK) {
     s = hdg_solve(c, dgv, dx, 1, o, rep);

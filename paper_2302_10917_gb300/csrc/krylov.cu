@@ -663,7 +663,9 @@ static double read_scalar(hdg_ctx* c, const double* p, Cu& cu) {
 static int launch_mdot(const void* V4, int64_t np, int nv, int ncol, const void* w4, double* part,
                        const int* fl, cudaStream_t st, int kgd, const Batch& bt, int nb = 1, bool f64 = false) {
   const int gy = (ncol + VG - 1) / VG;
-  int64_t gx = kgd / gy > 152 ? kgd / gy : 152;
+  // about kgd blocks over all groups: whole waves of the resident blocks (4 per SM), not a
+  // partly filled last wave
+  int64_t gx = kgd / gy > 0 ? kgd / gy : 1;
   const int64_t need = (np + KT - 1) / KT;
   if (gx > need) gx = need > 1 ? need : 1;
   const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nb);
