@@ -64,6 +64,8 @@ def parse_args(argv=None):
                     help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes), "
                          "2 CGS with a second projection where more than half of the vector lay in the basis, "
                          "3 the same where the single projection cancelled more than six digits")
+    ap.add_argument("--augment", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="augmented restarts: corrections of earlier cycles in each cycle's search space (LGMRES)")
     ap.add_argument("--elim", default="tc", choices=["tc", "fp64", "split"],
                     help="local factorisation: tc = FP64 panels with the trailing updates as exact slice products "
                          "on the tensor cores (FP64-accurate), fp64 = FP64 FMAs throughout, split = split-FP32")
@@ -404,7 +406,7 @@ def run_ours(args):
         if marks:
             marks[1].record(stream)
         x, rep, st = pr.solve(g, tol=1e-10, restart=args.restart, maxit=args.maxit, mode=mode, orth=args.orth,
-                              basis=basis, check=False)
+                              basis=basis, check=False, augment=args.augment)
         if st != 0 and not (st == 6 and args.maxit < 60000):   # 6: HDG_ERR_NOCONV
             raise RuntimeError(f"solve did not converge: {rep} (status {st})")
         if marks:

@@ -160,6 +160,7 @@ typedef struct {
  * with FP64 vectors mode 2 uses the one-thread-per-row apply. */
 #define HDG_BASIS_FP64 0
 #define HDG_BASIS_DF64 1
+#define HDG_MAX_AUGMENT 3
 typedef struct {
   double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
   int maxit;             /* maximum number of operator applications inside GMRES */
@@ -174,6 +175,12 @@ typedef struct {
                             passes in the other steps); 3 = as 2 with the second projection only where
                             ||w - V V^T w||^2 < 1e-6 ||w||^2 (more than six digits cancelled) */
   int basis;             /* HDG_BASIS_FP64 or HDG_BASIS_DF64 (see above) */
+  int augment;           /* 0 .. HDG_MAX_AUGMENT, below restart: augmented restarts (LGMRES, Baker, Jessup
+                            and Manteuffel 2005): the last `augment` steps of every restart cycle take the
+                            normalised corrections x_new - x_old of the previous cycles as their operator
+                            inputs instead of new Krylov vectors (flexible Arnoldi, the images orthogonalised
+                            into the same basis), which counters the stagnation of restarted GMRES; 0 = plain
+                            GMRES(restart) */
 } hdg_solve_opts;
 
 typedef struct {

@@ -55,7 +55,7 @@ OFF_SOURCE, OFF_DIRICHLET_POINTS, OFF_LATTICE, OFF_TRACE, OFF_SCHUR, OFF_DIRICHL
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
-                ("mode", ctypes.c_int), ("orth", ctypes.c_int), ("basis", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("orth", ctypes.c_int), ("basis", ctypes.c_int), ("augment", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -303,14 +303,17 @@ class Problem:
         self._check(self.lib.hdg_apply(self.h, _ptr(x), _ptr(y), nrhs, prec, 1 if precond else 0))
         return y
 
-    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0, basis=BASIS_FP64):
+    def solve(self, g, x0=None, tol=1e-10, maxit=20000, restart=50, mode=0, check=True, orth=0, basis=BASIS_FP64,
+              augment=0):
         """g: [N_tr], or [nrhs, N_tr] (independent systems solved in lockstep: one multi-RHS
         apply and batched vector kernels per Arnoldi step; the report is the worst column's).
-        basis: BASIS_FP64 (FP64 Krylov basis and orthogonalisation) or BASIS_DF64 (split-FP32)."""
+        basis: BASIS_FP64 (FP64 Krylov basis and orthogonalisation) or BASIS_DF64 (split-FP32).
+        augment: 0..3 corrections of earlier restart cycles added to each cycle's search space
+        (augmented restarts, LGMRES)."""
         g = g.to(self.device, torch.float64).contiguous()
         nrhs = 1 if g.dim() == 1 else g.shape[0]
         x = torch.zeros_like(g) if x0 is None else x0.to(self.device, torch.float64).clone()
-        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth, basis=basis)
+        o = SolveOpts(tol=tol, maxit=maxit, restart=restart, mode=mode, orth=orth, basis=basis, augment=augment)
         r = SolveReport()
         st = self.lib.hdg_solve(self.h, _ptr(g), _ptr(x), nrhs, ctypes.byref(o), ctypes.byref(r))
         if check and st not in (HDG_OK, HDG_ERR_NOCONV):

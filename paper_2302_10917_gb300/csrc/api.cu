@@ -658,7 +658,8 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
-      o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_DF64)
+      o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_DF64 || o->augment < 0 ||
+      o->augment > HDG_MAX_AUGMENT || o->augment >= o->restart)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
@@ -933,7 +934,8 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
   cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_Pinv); cudaFree(c->d_cmapb);
-  if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
+  cudaFree(c->d_aug); cudaFree(c->d_augb);
+  for (auto& g : c->gm_cache) cudaGraphExecDestroy(g.second);
   for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;

@@ -354,6 +354,7 @@ struct hdg_ctx {
   double* d_part = nullptr;       // reduction partials
   double* d_small = nullptr;      // Hessenberg, Givens, scalars
   int* d_flag = nullptr;
+  void* d_aug = nullptr;          // [3][ldv] augmentation vectors of the restarted GMRES (basis format)
   int krylov_restart = 0;
   // batched (several right-hand sides) Krylov workspace, sized for (restart, nrhs)
   float2* d_Vb = nullptr;         // [restart + 1][nrhs][ldv] split-FP32 pairs
@@ -365,14 +366,16 @@ struct hdg_ctx {
   double* d_scalb = nullptr;      // [nrhs] gathered scalars
   int* d_cmapb = nullptr;         // [nrhs] columns still iterating in the current restart cycle
   float2* d_Zb = nullptr;         // [N][nrhs][n_t] element products of the multi-RHS apply
+  void* d_augb = nullptr;         // [3][nrhs][ldv] augmentation vectors of the batched GMRES
   int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)
   int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)
   mehdg::BulkHooks bulk_hooks;    // pipelined apply: wait limit and the copy-skip test hook
   int tune_kgd = 0;               // multi-dot blocks over all vector groups
   int tune_kgu = 0;               // streaming-update blocks
-  cudaGraphExec_t gm_exec = nullptr;   // captured GMRES cycle (one restart cycle of Arnoldi steps)
-  std::vector<intptr_t> gm_key;        // configuration the capture is valid for
+  // captured GMRES cycles (one restart cycle of Arnoldi steps each), with the configuration each
+  // capture is valid for; the most recently used first, at most kGraphCache of them
+  std::vector<std::pair<std::vector<intptr_t>, cudaGraphExec_t>> gm_cache;
   cudaStream_t cap_stream = nullptr;   // private stream used only for the capture
   std::vector<cudaEvent_t> gm_ev;      // per-step event quadruples of a timed capture
   mehdg::LevelMesh* lv = nullptr;     // per-element refinement levels (null: one level m)

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <type_traits>
 #include "df64.h"
 #include "launch.h"
 
@@ -542,6 +543,68 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
   return s;
 }
 
+// ------------------------------------------------------- augmented restarts
+// LGMRES (Baker, Jessup and Manteuffel, 2005): the last steps of a restart
+// cycle take the normalised corrections of the previous cycles, z_i, as their
+// operator inputs instead of new Krylov vectors (flexible Arnoldi: the images
+// A z_i are orthogonalised into the same basis V), so the cycle's search space
+// is span(V_0..V_{m-1}) + span(z_0..z_{nz-1}) and the correction is
+// c = sum_{i<nv} y_i V_i + sum_{i<nzu} y_{m+i} z_i. x += c; c is kept in r0 and
+// its squared norm's block partials in part, for the next z.
+template <typename T>
+__device__ __forceinline__ double basis_entry(const T* V, size_t i);
+template <>
+__device__ __forceinline__ double basis_entry<double>(const double* V, size_t i) { return V[i]; }
+template <>
+__device__ __forceinline__ double basis_entry<float2>(const float2* V, size_t i) { return df_to(V[i]); }
+
+template <typename T>
+__global__ void __launch_bounds__(KT) aug_correction_kernel(const T* __restrict__ V, const T* __restrict__ Z,
+                                                            int64_t n, int64_t vstr, int nv, int nzu, int m,
+                                                            const double* __restrict__ y, double* x, double* c,
+                                                            double* part) {
+  __shared__ double cf[136];
+  __shared__ double red[KT / 32];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = y[i];
+  for (int i = threadIdx.x; i < nzu; i += blockDim.x) cf[nv + i] = y[m + i];
+  __syncthreads();
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double ss = 0.0;
+  for (int64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(cf[i], basis_entry(V, (size_t)i * vstr + idx), a);
+    for (int i = 0; i < nzu; ++i) a = fma(cf[nv + i], basis_entry(Z, (size_t)i * vstr + idx), a);
+    c[idx] = a;
+    x[idx] += a;
+    ss = fma(a, a, ss);
+  }
+  const double s = block_sum(ss, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// z = c / ||c|| in the basis format (||c||^2 summed from G partials in block order);
+// a zero correction leaves z = 0
+template <typename T>
+__global__ void __launch_bounds__(KT) aug_store_kernel(const double* __restrict__ c, const double* __restrict__ part,
+                                                       int G, T* z, int64_t n) {
+  __shared__ double red[KT / 32];
+  __shared__ double s_inv;
+  double s0 = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s0 += part[b];
+  const double nrm2 = block_sum_all(s0, red);
+  if (threadIdx.x == 0) s_inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  __syncthreads();
+  const double inv = s_inv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const double v = c[idx] * inv;
+    if constexpr (std::is_same<T, double>::value) z[idx] = v;
+    else z[idx] = df_from(v);
+  }
+}
+
+
 // out[i] = sum_b part[b * nv + i] in block order (block i sums vector i);
 // mode 0: H column := s, mode 1: H column += s; htmp receives s.
 // Column i = nv of a ncol = nv + 1 layout is ||w||^2 and goes to *wnorm2.
@@ -625,7 +688,9 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   cudaFree(c->d_flag);
   cudaFree(c->d_w);
   cudaFree(c->d_r);
+  cudaFree(c->d_aug);
   c->d_V = nullptr; c->d_part = nullptr; c->d_small = nullptr; c->d_flag = nullptr; c->d_w = nullptr; c->d_r = nullptr;
+  c->d_aug = nullptr;
   c->krylov_restart = 0;
   const size_t n = (size_t)c->prm.N_tr;
   const size_t ldv = n + (n & 1);   // even row length: 16-byte element pairs, zero padding
@@ -636,6 +701,8 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   if ((e = cudaMemset(c->d_V, 0, (size_t)(K + 1) * ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMemset(c->d_w, 0, ldv * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_r, 2 * n * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_aug, (size_t)HDG_MAX_AUGMENT * ldv * 8)) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_aug, 0, (size_t)HDG_MAX_AUGMENT * ldv * 8)) != cudaSuccess) return e;
   // partial rows of a multi-dot: kgd / gy per group (at most KGD_MAX over all
   // groups) or 152 per group, each row (K + 2) columns at most
   if ((e = cudaMalloc(&c->d_part, (size_t)(KG > KGD_MAX ? KG : KGD_MAX) * (K + 2) * sizeof(double))) != cudaSuccess)
@@ -798,6 +865,9 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     return cu.err == cudaSuccess ? HDG_OK : fail(c, HDG_ERR_CUDA, cudaGetErrorString(cu.err));
   }
   int its = 0, klen = K;
+  // augmented restarts: nz stored corrections (ring of o.augment slots, zslot the oldest once full)
+  char* Zr = reinterpret_cast<char*>(c->d_aug);
+  int nz = 0, zslot = 0;
   double rel = 1.0, prev_rel = 0.0;
   while (true) {
     // true residual with the unpreconditioned FP64 operator (the stopping test)
@@ -829,6 +899,9 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     launch_first(f64b, st, r0, sm, L.sc + 4, V, n, fl);
     LAUNCHED(4);
     const int jmax = std::min(klen, o.maxit - its);
+    // steps m .. jmax-1 take the stored corrections as operator inputs (at least one Krylov step)
+    const int nzc = std::min(nz, std::max(0, jmax - 1));
+    const int m = jmax - nzc;
     std::vector<size_t> mark(jmax + 1, 0);   // profiling entries recorded before Arnoldi step j
     // one Arnoldi step j on stream s (timed phases only when profiling, i.e. not captured)
     // (ev: event quadruple of a captured, timed step: apply begin/end, vector work begin/end)
@@ -838,9 +911,9 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        if (c->lv) cu.ok(launch_level_apply(c, bt, vt, Sop, V + (size_t)j * ldv * esz, w, 1, ldv, precond_scale(c), fl, s));
-        else cu.ok(launch_apply_vdf(bt, P, Sop, V + (size_t)j * ldv * esz, w, precond_scale(c), fl, s, epb, vt,
-                                    &c->bulk_hooks));
+        const void* in = j < m ? (const void*)(V + (size_t)j * ldv * esz) : (const void*)(Zr + (size_t)(j - m) * ldv * esz);
+        if (c->lv) cu.ok(launch_level_apply(c, bt, vt, Sop, in, w, 1, ldv, precond_scale(c), fl, s));
+        else cu.ok(launch_apply_vdf(bt, P, Sop, in, w, precond_scale(c), fl, s, epb, vt, &c->bulk_hooks));
       }
       if (ev) {
         cu.ok(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
@@ -883,7 +956,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       // turns the steps after convergence into immediate returns. With
       // profiling on, the capture carries an event quadruple per step.
       const int timed = c->prof_on ? 1 : 0;
-      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, (intptr_t)c->bulk_hooks.wait_cycles,
+      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, m, (intptr_t)Zr, (intptr_t)c->bulk_hooks.wait_cycles,
                                          c->bulk_hooks.skip_edge, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
                                          (intptr_t)np, kgd, kgu, epb, c->lv ? c->lv->rb : 0};
@@ -893,25 +966,39 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
           if (!cu.ok(cudaEventCreate(&ev))) break;
           c->gm_ev.push_back(ev);
         }
-        c->gm_key.clear();   // event handles are part of a timed capture
+        for (auto& gc : c->gm_cache) cudaGraphExecDestroy(gc.second);   // event handles are part of a timed capture
+        c->gm_cache.clear();
       }
-      if (!c->gm_exec || c->gm_key != key) {
-        if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
-        c->gm_exec = nullptr;
+      // (augmented restarts use up to HDG_MAX_AUGMENT + 1 cycle shapes per solve: a small cache)
+      constexpr size_t kGraphCache = 6;
+      size_t hit = c->gm_cache.size();
+      for (size_t i = 0; i < c->gm_cache.size(); ++i)
+        if (c->gm_cache[i].first == key) hit = i;
+      if (hit == c->gm_cache.size()) {
+        if (c->gm_cache.size() >= kGraphCache) {
+          cudaGraphExecDestroy(c->gm_cache.back().second);
+          c->gm_cache.pop_back();
+        }
         if (!c->cap_stream) cu.ok(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
         if (cu.ok(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal))) {
           for (int j = 0; j < K; ++j) enqueue_step(j, c->cap_stream, false, timed ? &c->gm_ev[4 * j] : nullptr);
           cu.ok(cudaStreamEndCapture(c->cap_stream, &graph));
         }
         if (graph) {
-          cu.ok(cudaGraphInstantiate(&c->gm_exec, graph, 0));
+          cu.ok(cudaGraphInstantiate(&exec, graph, 0));
           cudaGraphDestroy(graph);
         }
-        if (cu.err != cudaSuccess) return fail(c, HDG_ERR_CUDA, std::string("GMRES cycle capture: ") + cudaGetErrorString(cu.err));
-        c->gm_key = key;
+        if (cu.err != cudaSuccess) {
+          if (exec) cudaGraphExecDestroy(exec);
+          return fail(c, HDG_ERR_CUDA, std::string("GMRES cycle capture: ") + cudaGetErrorString(cu.err));
+        }
+        c->gm_cache.insert(c->gm_cache.begin(), {key, exec});
+      } else if (hit > 0) {
+        std::rotate(c->gm_cache.begin(), c->gm_cache.begin() + hit, c->gm_cache.begin() + hit + 1);
       }
-      cu.ok(cudaGraphLaunch(c->gm_exec, st));
+      cu.ok(cudaGraphLaunch(c->gm_cache.front().second, st));
       LAUNCHED(per_step * K);
     } else {
       for (int j = 0; j < jmax; ++j) {
@@ -948,8 +1035,29 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     rep.restarts += 1;
     if (jused == 0) break;
     lsq_kernel<<<1, 32, 0, st>>>(sm, L, fl);
-    launch_xupdate(f64b, st, V, n, ldv, jused, sm + L.y, x);
-    LAUNCHED(2);
+    if (o.augment > 0) {
+      // x += c = V y + Z y (the cycle's correction), then c / ||c|| becomes a stored correction
+      const int nvv = std::min(jused, m), nzu = std::max(0, jused - m);
+      const int slot = nz < o.augment ? nz : zslot;
+      void* zdst = Zr + (size_t)slot * ldv * esz;
+      if (f64b) {
+        aug_correction_kernel<double><<<KG, KT, 0, st>>>(reinterpret_cast<const double*>(V),
+                                                         reinterpret_cast<const double*>(Zr), n, ldv, nvv, nzu, m,
+                                                         sm + L.y, x, r0, part);
+        aug_store_kernel<double><<<KG, KT, 0, st>>>(r0, part, KG, static_cast<double*>(zdst), n);
+      } else {
+        aug_correction_kernel<float2><<<KG, KT, 0, st>>>(reinterpret_cast<const float2*>(V),
+                                                         reinterpret_cast<const float2*>(Zr), n, ldv, nvv, nzu, m,
+                                                         sm + L.y, x, r0, part);
+        aug_store_kernel<float2><<<KG, KT, 0, st>>>(r0, part, KG, static_cast<float2*>(zdst), n);
+      }
+      if (nz < o.augment) ++nz;
+      else zslot = (zslot + 1) % o.augment;
+      LAUNCHED(3);
+    } else {
+      launch_xupdate(f64b, st, V, n, ldv, jused, sm + L.y, x);
+      LAUNCHED(2);
+    }
   }
   rep.converged = 0;
   if (bulk_wait_gave_up()) return fail(c, HDG_ERR_TIMEOUT, "pipelined apply: a bounded copy wait gave up");
@@ -1095,9 +1203,9 @@ __global__ void set_cycle_kernel(int* flags, int rflag, const int* done, double*
 static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   if (c->kb_restart == K && c->kb_nrhs == nb && c->d_Vb) return cudaSuccess;
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
-  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_cmapb);
+  cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_cmapb); cudaFree(c->d_augb);
   c->d_Vb = nullptr; c->d_wb = nullptr; c->d_rb = nullptr; c->d_partb = nullptr; c->d_smallb = nullptr;
-  c->d_flagb = nullptr; c->d_scalb = nullptr; c->d_Zb = nullptr; c->d_cmapb = nullptr;
+  c->d_flagb = nullptr; c->d_scalb = nullptr; c->d_Zb = nullptr; c->d_cmapb = nullptr; c->d_augb = nullptr;
   c->kb_restart = c->kb_nrhs = 0;
   const size_t n = (size_t)c->prm.N_tr, ldv = n + (n & 1);
   SmallLayout L(K);
@@ -1115,6 +1223,8 @@ static cudaError_t ensure_krylov_batched(hdg_ctx* c, int K, int nb) {
   const size_t nzb = c->lv ? 1 : (size_t)c->prm.N * nb * c->prm.n_t;   // level meshes use their own buffer
   if ((e = cudaMalloc(&c->d_Zb, nzb * sizeof(float2))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_cmapb, (size_t)nb * sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_augb, (size_t)HDG_MAX_AUGMENT * nb * ldv * 8)) != cudaSuccess) return e;
+  if ((e = cudaMemset(c->d_augb, 0, (size_t)HDG_MAX_AUGMENT * nb * ldv * 8)) != cudaSuccess) return e;
   c->kb_restart = K;
   c->kb_nrhs = nb;
   return cudaSuccess;
@@ -1154,6 +1264,9 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
   rep = hdg_solve_report{};
   std::vector<double> host(nb), gnorm(nb), rel(nb, 1.0), prev_rel(nb, 0.0);
   int klen = K;
+  // augmented restarts: per column nz stored corrections ([slot][column][ldv]), as in gmres_solve
+  char* Zr = reinterpret_cast<char*>(c->d_augb);
+  int nz = 0, zslot = 0;
   std::vector<int> done(nb, 0), its(nb, 0), hfl(4 * nb);
   int* d_done = reinterpret_cast<int*>(scal + nb);   // [nb] converged flags (device copy)
   auto norms = [&](const double* vec, int64_t stride, double a, const double* y2, double bcoef, double* outv) {
@@ -1237,16 +1350,18 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       c->launches += 4;
     }
     const int jmax = std::min(klen, o.maxit - maxits);
+    const int nzc = std::min(nz, std::max(0, jmax - 1));
+    const int m = jmax - nzc;
     for (int j = 0; j < jmax; ++j) {
       const int nv = j + 1;
       {
         ProfScope ps(c, phase);
+        const void* in = j < m ? (const void*)(V + (size_t)j * nb * ldv * esz)
+                               : (const void*)(Zr + (size_t)(j - m) * nb * ldv * esz);
         if (c->lv)
-          cu.ok(launch_level_apply(c, btype, vt, Sop, V + (size_t)j * nb * ldv * esz, c->d_wb, na, ldv,
-                                   precond_scale(c), nullptr, st, cmap));
+          cu.ok(launch_level_apply(c, btype, vt, Sop, in, c->d_wb, na, ldv, precond_scale(c), nullptr, st, cmap));
         else
-          cu.ok(launch_apply_mrhs_el(btype, P, Sop, V + (size_t)j * nb * ldv * esz, c->d_wb, na, ldv,
-                                     precond_scale(c), c->d_Zb, st, cmap, vt));
+          cu.ok(launch_apply_mrhs_el(btype, P, Sop, in, c->d_wb, na, ldv, precond_scale(c), c->d_Zb, st, cmap, vt));
         c->launches += 1;
       }
       ProfScope po(c, HDG_PROF_ORTHO);
@@ -1290,8 +1405,35 @@ hdg_status gmres_solve_batched(hdg_ctx* c, const double* g, double* x, int nb, c
       any = 1;
       double* smr = sm + (size_t)r * L.total;
       lsq_kernel<<<1, 32, 0, st>>>(smr, L, fl + 4 * r);
-      launch_xupdate(f64b, st, V + (size_t)r * ldv * esz, n, (int64_t)nb * ldv, jused, smr + L.y, x + (size_t)r * n);
-      c->launches += 2;
+      if (o.augment > 0) {
+        const int nvv = std::min(jused, m), nzu = std::max(0, jused - m);
+        const int slot = nz < o.augment ? nz : zslot;
+        const int64_t vs = (int64_t)nb * ldv;
+        char* vcol = V + (size_t)r * ldv * esz;
+        char* zcol = Zr + (size_t)r * ldv * esz;
+        void* zdst = zcol + (size_t)slot * vs * esz;
+        double* cr = r0 + (size_t)r * n;
+        double* pr = part + (size_t)r * rpart;
+        if (f64b) {
+          aug_correction_kernel<double><<<KG, KT, 0, st>>>(reinterpret_cast<const double*>(vcol),
+                                                           reinterpret_cast<const double*>(zcol), n, vs, nvv, nzu, m,
+                                                           smr + L.y, x + (size_t)r * n, cr, pr);
+          aug_store_kernel<double><<<KG, KT, 0, st>>>(cr, pr, KG, static_cast<double*>(zdst), n);
+        } else {
+          aug_correction_kernel<float2><<<KG, KT, 0, st>>>(reinterpret_cast<const float2*>(vcol),
+                                                           reinterpret_cast<const float2*>(zcol), n, vs, nvv, nzu, m,
+                                                           smr + L.y, x + (size_t)r * n, cr, pr);
+          aug_store_kernel<float2><<<KG, KT, 0, st>>>(cr, pr, KG, static_cast<float2*>(zdst), n);
+        }
+        c->launches += 3;
+      } else {
+        launch_xupdate(f64b, st, V + (size_t)r * ldv * esz, n, (int64_t)nb * ldv, jused, smr + L.y, x + (size_t)r * n);
+        c->launches += 2;
+      }
+    }
+    if (o.augment > 0 && any) {
+      if (nz < o.augment) ++nz;
+      else zslot = (zslot + 1) % o.augment;
     }
     if (!any) break;
   }

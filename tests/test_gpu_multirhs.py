@@ -79,12 +79,15 @@ def test_multi_rhs_apply_matches_oracle(mcase, k):
     assert rel(y32, ref_p) < 5e-5
 
 
-@pytest.mark.parametrize("mode,orth,basis", [(2, 1, 1), (0, 0, 0), (1, 1, 0), (2, 2, 0), (1, 1, 1), (0, 2, 1)])
-def test_batched_solve_and_recover_match_oracle(mcase, mode, orth, basis):
-    """Lockstep batched GMRES on every column; basis 0: FP64 Krylov basis, 1: split-FP32."""
+@pytest.mark.parametrize("mode,orth,basis,augment", [(2, 1, 1, 0), (0, 0, 0, 0), (1, 1, 0, 0), (2, 2, 0, 0),
+                                                      (1, 1, 1, 0), (0, 2, 1, 0), (0, 3, 0, 2), (2, 3, 1, 3)])
+def test_batched_solve_and_recover_match_oracle(mcase, mode, orth, basis, augment):
+    """Lockstep batched GMRES on every column; basis 0: FP64 Krylov basis, 1: split-FP32;
+    augment > 0: augmented restarts (LGMRES)."""
     ora, pr, S, nrhs = mcase["ora"], mcase["pr"], mcase["S"], mcase["nrhs"]
     g = pr.rhs()
-    x, rep, st = pr.solve(g, tol=1e-10, restart=30, mode=mode, orth=orth, basis=basis)
+    x, rep, st = pr.solve(g, tol=1e-10, restart=30 if augment == 0 else 8, mode=mode, orth=orth, basis=basis,
+                          augment=augment)
     assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10
     xs = x.cpu().numpy()
     for r in range(nrhs):

@@ -255,6 +255,26 @@ def test_gmres_single_projection_variants(case, orth, basis):
         assert rel(x_gpu, x_dir) < 1e-8
 
 
+@pytest.mark.parametrize("augment", [1, 3])
+@pytest.mark.parametrize("mode,basis", [(0, BASIS_FP64), (1, BASIS_FP64), (2, BASIS_DF64)])
+def test_gmres_with_augmented_restarts(case, mode, basis, augment):
+    """Augmented restarts (LGMRES): the last steps of each cycle run on the corrections of the
+    previous cycles; the solution still matches the direct solve and the reported residual is
+    the true one (restart 10 forces many cycles)."""
+    ora, gpu = case["ora"], case["gpu"]
+    S = ora.assemble_S(case["S_el"])
+    x_dir = np.linalg.solve(S, case["g"])
+    x_gpu, rep, st = gpu.solve(gpu.rhs(), tol=1e-10, restart=10, maxit=20000, mode=mode, orth=3, basis=basis,
+                               augment=augment)
+    assert st == 0 and rep["converged"] == 1 and rep["rel_residual"] <= 1e-10, rep
+    x_gpu = x_gpu.cpu().numpy()
+    assert abs(np.linalg.norm(case["g"] - S @ x_gpu) / np.linalg.norm(case["g"]) - rep["rel_residual"]) < 1e-12
+    assert rel(x_gpu, x_dir) < 1e-8
+    x2, rep2, _ = gpu.solve(gpu.rhs(), tol=1e-10, restart=10, maxit=20000, mode=mode, orth=3, basis=basis,
+                            augment=augment)
+    assert torch.equal(torch.from_numpy(x_gpu).cuda(), x2) and rep == rep2
+
+
 @pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
 def test_solve_is_bitwise_reproducible(case, basis):
     gpu = case["gpu"]
