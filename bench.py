@@ -42,6 +42,8 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.20e6 / 12160
 # the same for apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors): 376.72 MB for 12 160 edges at n = 64
 APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3 = 376.72e6 / 12160
+# the same for apply_fix_kernel (fixed-point rows, FP64 vectors): 376.25 + 4.75 MB for 12 160 edges at n = 64
+APPLY_FIX_TRAFFIC_PER_EDGE_M8P3 = 381.00e6 / 12160
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
@@ -56,8 +58,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="n128_m8_p3")
     ap.add_argument("--restart", type=int, default=80)
-    ap.add_argument("--mode", type=int, default=0, choices=[0, 1, 2],
-                    help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32")
+    ap.add_argument("--mode", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32, "
+                         "3 fixed-point rows with exact integer products (FP64-accurate)")
     ap.add_argument("--basis", type=int, default=0, choices=[0, 1],
                     help="Krylov basis and orthogonalisation: 0 FP64, 1 split FP32")
     ap.add_argument("--orth", type=int, default=3, choices=[0, 1, 2, 3],
@@ -357,10 +360,13 @@ def tc_slice_flops(Q, R, Cc, b=32, m_tile=128, n_tile=32, products=28):
 
 
 # ---------------------------------------------------------------------- ours
-MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64"}
+MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64", 3: "fp64_fixed"}
 # precision forms of one step: (Arnoldi operator mode, Krylov basis, local factorisation)
-FORMS = {"fp64": (0, 0, "tc"), "fp64_dfma": (0, 0, "fp64"), "fp32_ir": (1, 0, "tc"), "df64": (2, 1, "split")}
+FORMS = {"fp64": (0, 0, "tc"), "fp64_fixed": (3, 0, "tc"), "fp64_dfma": (0, 0, "fp64"), "fp32_ir": (1, 0, "tc"),
+         "df64": (2, 1, "split")}
 FORM_DTYPES = {(0, 0, "tc"): "f64 (tensor-core trailing updates by exact 8-bit slices, FP64-accurate)",
+               (3, 0, "tc"): "f64 (trace apply on 56-bit fixed-point rows with exact integer products, one FP64 "
+                             "rounding per element side; tensor-core trailing updates by exact 8-bit slices)",
                (0, 0, "fp64"): "f64 (FP64 FMAs throughout)",
                (1, 0, "tc"): "f32 blocks (FP32 operator) + f64 factorisation, orthogonalisation and refinement",
                (2, 1, "split"): "df64 (f32x2) elimination, blocks and Krylov basis + f64 residual"}
@@ -394,7 +400,7 @@ def run_ours(args):
     def condense_flags(mode, elim):
         # only the blocks the solve mode needs
         return dict(keep_factors=not args.no_keep_factors, store_fp32=(mode == 1), store_df64=(mode == 2),
-                    split_update=elim == "split", tc_update=elim == "tc")
+                    store_fix=(mode == 3), split_update=elim == "split", tc_update=elim == "tc")
 
     def step(rec=None, mode=args.mode, basis=args.basis, elim=args.elim, precond="d"):
         marks = [ev() for _ in range(4)] if rec is not None else None
@@ -470,6 +476,7 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     apply_kernels = {0: "apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors)",
+                     3: "apply_fix_kernel (56-bit fixed-point rows, exact int64 products, FP64 vectors)",
                      1: "apply_vdf_kernel<2,%d> (FP32 blocks)" % (1 - args.basis),
                      2: "apply_vdf_kernel<1,%d> (split-FP32 blocks)" % (1 - args.basis)}
     rooflines = {
@@ -487,7 +494,9 @@ def run_ours(args):
     }
     ra = rooflines["apply"]
     # FP32 blocks move 4 bytes per entry; the vectors are 8 bytes per entry in either basis
-    bpl = apply_bytes - (4.0 * 2 * P1 * n_t * n_int if args.mode == 1 else 0.0)
+    # (fixed-point rows: 8 bytes per entry plus a 4-byte scale per row of each side)
+    bpl = apply_bytes - (4.0 * 2 * P1 * n_t * n_int if args.mode == 1 else 0.0) + \
+        (4.0 * 2 * P1 * n_int if args.mode == 3 else 0.0)
     ra.update(achieved=bpl / (ra["avg_launch_ms"] / 1e3) / 1e9, peak=hbm_peak, unit="GB/s",
               algorithmic_per_launch=bpl, peak_source=hbm_src)
     ra["frac"] = ra["achieved"] / ra["peak"]
@@ -547,14 +556,15 @@ def run_ours(args):
                                                            else kname][1])
     roof = dict(rooflines[dom])
     roof["traffic"] = None
-    traffic_per_edge = {(0, 0): APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3, (2, 1): APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3}
+    traffic_per_edge = {(0, 0): APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3, (2, 1): APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3,
+                        (3, 0): APPLY_FIX_TRAFFIC_PER_EDGE_M8P3}
     if dom == "apply" and (cfg["m"], cfg["p"]) == (8, 3) and (args.mode, args.basis) in traffic_per_edge \
             and not tune.get("apply_bulk") and traffic_per_edge[(args.mode, args.basis)]:
         roof["traffic"] = traffic_per_edge[(args.mode, args.basis)] * n_int
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 64, scaled by interior edges"
     roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
-    all_fp64 = args.mode == 0 and args.basis == 0 and not split
+    all_fp64 = args.mode in (0, 3) and args.basis == 0 and not split
     dtype = "f64" if all_fp64 else FORM_DTYPES.get((args.mode, args.basis, args.elim), "mixed")
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
@@ -565,6 +575,10 @@ def run_ours(args):
                        "local_factorisation": {"split": "split-FP32", "fp64": "FP64 FMAs",
                                                "tc": "FP64 panels + tensor-core trailing updates by exact 8-bit "
                                                      "slices (FP64-accurate)"}[args.elim],
+                       "trace_apply": {0: "FP64 blocks, FP64 FMAs", 1: "FP32 blocks, FP32 FMAs",
+                                       2: "split-FP32 blocks on the FP32 pipe",
+                                       3: "56-bit fixed-point rows, exact int64 products, one FP64 rounding per "
+                                          "element side"}[args.mode],
                        "krylov_basis": ["FP64", "split-FP32"][args.basis],
                        "orthogonalisation": ["CGS2", "CGS, Pythagorean norm",
                                              "CGS + second projection where ||w - V h||^2 < ||w||^2 / 2",
@@ -844,9 +858,8 @@ def bench_mixed_precision_n256(stream):
         a.record(stream)
         # factors not kept (131 072 local systems would take 169 GB): chunked condensation, the
         # back-solve condenses each chunk again
-        pr.condense(keep_factors=False, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=elim == "split",
-                    tc_update=elim == "tc",
-                    precond="face_schur")
+        pr.condense(keep_factors=False, store_fp32=(mode == 1), store_df64=(mode == 2), store_fix=(mode == 3),
+                    split_update=elim == "split", tc_update=elim == "tc", precond="face_schur")
         b.record(stream)
         g = pr.rhs()
         pr.autotune(mode=mode, restart=80, basis=basis)
@@ -1011,7 +1024,7 @@ def gradient_fd_check(pr, kap, f, u_obs, gk, gf, opts, count, h=1e-3):
         pr.set_kappa(kk)
         pr.set_source(fv)
         pr.condense(keep_factors=True, store_df64=opts["mode"] == 2, store_fp32=opts["mode"] == 1,
-                    split_update=opts["split_update"], precond=opts["precond"])
+                    store_fix=opts["mode"] == 3, split_update=opts["split_update"], precond=opts["precond"])
         x, rep, st = pr.solve(pr.rhs(), x0=x0, **sk)
         if st != 0:
             raise RuntimeError(f"finite-difference solve did not converge: {rep}")

@@ -151,7 +151,10 @@ typedef struct {
  * g - S x (the stopping test). mode selects the preconditioned Arnoldi
  * operator: 0 = FP64 blocks, FP64 arithmetic; 1 = FP32 blocks (requires
  * HDG_STORE_FP32), i.e. FP32 inside FP64 iterative refinement; 2 = split-FP32
- * blocks on the FP32 pipe (requires HDG_STORE_DF64). basis selects the
+ * blocks on the FP32 pipe (requires HDG_STORE_DF64); 3 = fixed-point blocks
+ * (requires HDG_STORE_FIX64, one right-hand side, a uniform mesh and
+ * HDG_BASIS_FP64): the FP64 products carried out exactly in integer
+ * arithmetic, one FP64 rounding per element side. basis selects the
  * storage and arithmetic of the Krylov basis and its orthogonalisation:
  * HDG_BASIS_FP64 (0, the default) = FP64 vectors, FP64 dot products and
  * updates; HDG_BASIS_DF64 (1) = split-FP32 ("double-float", two FP32 words,
@@ -206,6 +209,14 @@ typedef struct {
                                   2^-50 of the row and column scales, under the FP64 rounding of the same dot
                                   product. Excludes HDG_SPLIT_UPDATE. HDG_ERR_TIMEOUT if a tensor-core wait
                                   gives up. No counterpart in the paper (its local solver is LAPACK LU). */
+#define HDG_STORE_FIX64 64u   /* also keep the preconditioned blocks as fixed-point numbers (uniform mesh, n_t <= 240):
+                                  every row (element, edge, trace position) scaled by the power of two of its largest
+                                  entry's exponent and rounded to 56 bits (|v| <= 2^55, error <= 2^-56 of the row's
+                                  largest magnitude), stored as a signed high and a 28-bit low 32-bit limb (8 bytes
+                                  per entry, the FP64 layout) plus one int32 scale per row. The apply (prec = 56,
+                                  mode 3) scales each gathered element trace vector the same way and sums the limb
+                                  products exactly in 64-bit integers (no FP64 FMAs), rounding once to FP64 per
+                                  element side. Kept through hdg_transpose. No counterpart in the paper. */
 #define HDG_PRECOND_FACE_SCHUR 16u  /* precondition with the inverted diagonal face blocks of the condensed
                                        operator, S_ff = sum over both sides of S_e's face rows and columns,
                                        instead of D_f of Sec. 6.1 (folded into the stored preconditioned rows
@@ -287,6 +298,11 @@ hdg_status hdg_rhs(hdg_ctx* ctx, double* g_dev);
  * launch shape that solve uses (hdg_autotune's choice or hdg_set_apply_shape's);
  * with the pipelined shape it synchronises the stream to read that kernel's
  * timeout flag (HDG_ERR_TIMEOUT if a bounded wait gave up).
+ * prec = 56 (uniform mesh, nrhs = 1, precond = 1, HDG_STORE_FIX64): the
+ * fixed-point blocks on FP64 vectors, the Arnoldi operator of mode 3: each
+ * side's dot product exact in integers from the 56-bit fixed-point row and
+ * trace vector, rounded once to FP64; the two sides added and the face scale
+ * applied in FP64.
  * prec = 33 (nrhs = 1, or a level mesh; precond = 1, HDG_STORE_FP32): the
  * FP32 blocks on FP64 vectors (x, y FP64; products and sums in FP32), the
  * Arnoldi operator of mode 1 with HDG_BASIS_FP64.
@@ -296,7 +312,7 @@ hdg_status hdg_apply(hdg_ctx* ctx, const void* x_dev, void* y_dev, int nrhs, int
 
 /* Launch-shape override (no counterpart in the paper; project-written).
  * Sets the launch shape of the trace-operator apply inside hdg_solve for one
- * mode (0 FP64, 1 FP32 + refinement, 2 split-FP32), as hdg_autotune would:
+ * mode (0 FP64, 1 FP32 + refinement, 2 split-FP32, 3 fixed-point), as hdg_autotune would:
  * edges_per_block > 0 (with edges_per_block (m p + 1) <= 512) for the
  * one-thread-per-row apply, or bulk_warps = 1 .. 3 (mode 2 only) for the
  * pipelined apply with that many consumer warps per edge; both 0 restores

@@ -18,6 +18,7 @@ HDG_OK, HDG_ERR_ARG, HDG_ERR_STATE, HDG_ERR_CUDA, HDG_ERR_OOM = 0, 1, 2, 3, 4
 HDG_ERR_SINGULAR, HDG_ERR_NOCONV, HDG_ERR_TIMEOUT = 5, 6, 7
 HDG_STORE_FP32, HDG_KEEP_FACTORS, HDG_STORE_DF64, HDG_SPLIT_UPDATE, HDG_PRECOND_FACE_SCHUR = 1, 2, 4, 8, 16
 HDG_TC_UPDATE = 32
+HDG_STORE_FIX64 = 64
 BASIS_FP64, BASIS_DF64 = 0, 1   # hdg_solve_opts.basis: FP64 or split-FP32 Krylov basis
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_CUDA", 4: "HDG_ERR_OOM",
                 5: "HDG_ERR_SINGULAR", 6: "HDG_ERR_NOCONV", 7: "HDG_ERR_TIMEOUT"}
@@ -274,15 +275,17 @@ class Problem:
         self._check(self.lib.hdg_set_source(self.h, _ptr(f_qp), _ptr(gD_qp), nrhs))
 
     def condense(self, store_fp32=False, keep_factors=True, store_df64=False, split_update=False, precond="d",
-                 tc_update=False):
+                 tc_update=False, store_fix=False):
         """precond: "d" (D_f^-1 of Sec. 6.1) or "face_schur" (the inverted diagonal face blocks of S).
         split_update: split-FP32 elimination; tc_update: FP64 elimination with the trailing
-        updates on the tensor cores (exact 8-bit slices)."""
+        updates on the tensor cores (exact 8-bit slices); store_fix: also keep the
+        preconditioned blocks as 56-bit fixed-point rows (mode 3, apply prec 56)."""
         if precond not in ("d", "face_schur"):
             raise ValueError("precond must be 'd' or 'face_schur'")
         flags = ((HDG_STORE_FP32 if store_fp32 else 0) | (HDG_KEEP_FACTORS if keep_factors else 0)
                  | (HDG_STORE_DF64 if store_df64 else 0) | (HDG_SPLIT_UPDATE if split_update else 0)
-                 | (HDG_PRECOND_FACE_SCHUR if precond == "face_schur" else 0) | (HDG_TC_UPDATE if tc_update else 0))
+                 | (HDG_PRECOND_FACE_SCHUR if precond == "face_schur" else 0) | (HDG_TC_UPDATE if tc_update else 0)
+                 | (HDG_STORE_FIX64 if store_fix else 0))
         self._check(self.lib.hdg_condense(self.h, flags))
         self.version += 1
 
@@ -296,7 +299,7 @@ class Problem:
     def apply(self, x, precond=False, prec=64, out=None):
         """x: [N_tr] or [nrhs, N_tr] (multi-RHS apply); prec = 49: x [N_tr, 2] FP32 split pairs
         (the split-FP32 solve's own operator and launch shape), y likewise."""
-        dt = torch.float32 if prec in (32, 49) else torch.float64   # 64, 48, 33: FP64 vectors
+        dt = torch.float32 if prec in (32, 49) else torch.float64   # 64, 56, 48, 33: FP64 vectors
         x = x.to(self.device, dt).contiguous()
         nrhs = 1 if x.dim() == 1 or prec == 49 else x.shape[0]
         y = out if out is not None else torch.empty_like(x)
@@ -444,7 +447,7 @@ class HDGSolve(torch.autograd.Function):
         problem.set_kappa(kappa)
         problem.set_source(f, gD)
         problem.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split,
-                         precond=precond)
+                         precond=precond, store_fix=(mode == 3))
 
     @staticmethod
     def forward(ctx, kappa, f, problem, gD, opts):

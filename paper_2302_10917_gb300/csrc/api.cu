@@ -442,8 +442,10 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if (!c) return HDG_ERR_ARG;
   if (c->state < 1) return set_err(c, HDG_ERR_STATE, "hdg_condense before hdg_set_source");
   if (flags & ~(HDG_STORE_FP32 | HDG_KEEP_FACTORS | HDG_STORE_DF64 | HDG_SPLIT_UPDATE | HDG_PRECOND_FACE_SCHUR |
-                HDG_TC_UPDATE))
+                HDG_TC_UPDATE | HDG_STORE_FIX64))
     return set_err(c, HDG_ERR_ARG, "unknown flags");
+  if ((flags & HDG_STORE_FIX64) && (c->lv || !fix_supported(c->prm)))
+    return set_err(c, HDG_ERR_ARG, "HDG_STORE_FIX64 needs a uniform mesh with at most 240 trace dofs per element");
   if ((flags & HDG_SPLIT_UPDATE) && (flags & HDG_TC_UPDATE))
     return set_err(c, HDG_ERR_ARG, "HDG_SPLIT_UPDATE and HDG_TC_UPDATE exclude each other");
   if (c->lv) return level_condense(c, flags);
@@ -461,6 +463,10 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
   if ((flags & HDG_STORE_DF64) && !c->d_Stdf && (e = dev_alloc(c, &c->d_Stdf, sblk + 2)) != cudaSuccess)
     return cuda_err(c, e, "split-FP32 S blocks");
   if (!(flags & HDG_STORE_DF64)) dev_free(c, c->d_Stdf, sblk + 2);
+  const size_t fixb = fix_blocks_bytes(P);
+  if ((flags & HDG_STORE_FIX64) && !c->d_Sfix && (e = dev_alloc(c, &c->d_Sfix, fixb)) != cudaSuccess)
+    return cuda_err(c, e, "fixed-point S blocks");
+  if (!(flags & HDG_STORE_FIX64)) dev_free(c, c->d_Sfix, fixb);
   if (!c->d_gel && (e = dev_alloc(c, &c->d_gel, (size_t)P.nrhs * P.N * P.n_t)) != cudaSuccess) return cuda_err(c, e, "gel");
   if (!c->d_g && (e = dev_alloc(c, &c->d_g, (size_t)P.nrhs * P.N_tr)) != cudaSuccess) return cuda_err(c, e, "g");
   if (!c->d_info && (e = dev_alloc(c, &c->d_info, (size_t)P.N)) != cudaSuccess) return cuda_err(c, e, "info");
@@ -516,6 +522,11 @@ hdg_status hdg_condense(hdg_ctx* c, unsigned flags) {
     c->launches += 1;
     if ((e = launch_split_df(c->d_St, c->d_Stdf, (int64_t)sblk, c->stream)) != cudaSuccess)
       return cuda_err(c, e, "split");
+  }
+  if (flags & HDG_STORE_FIX64) {
+    c->launches += 1;
+    if ((e = launch_fix_convert(P, c->d_St, c->d_Sfix, c->stream)) != cudaSuccess)
+      return cuda_err(c, e, "fixed-point blocks");
   }
   for (int r = 0; r < P.nrhs; ++r) {
     c->launches += 1;
@@ -615,6 +626,11 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
   } else if (prec == 48) {
     if (!c->d_Stdf || !precond) return set_err(c, HDG_ERR_ARG, "split-FP32 apply needs HDG_STORE_DF64 and precond = 1");
     e = launch_apply_df(c->prm, c->d_Stdf, (const double*)x, (double*)y, precond_scale(c), nullptr, c->stream);
+  } else if (prec == 56) {
+    // fixed-point blocks on FP64 vectors: the Arnoldi operator of mode 3
+    if (!c->d_Sfix || !precond) return set_err(c, HDG_ERR_ARG, "fixed-point apply needs HDG_STORE_FIX64 and precond = 1");
+    e = launch_apply_fix(c->prm, c->d_Sfix, (const double*)x, (double*)y, precond_scale(c), nullptr, c->stream,
+                         c->tune_epb[3]);
   } else if (prec == 33) {
     // FP32 blocks on FP64 vectors: the Arnoldi operator of mode 1 with the FP64 basis
     if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
@@ -623,7 +639,7 @@ hdg_status hdg_apply(hdg_ctx* c, const void* x, void* y, int nrhs, int prec, int
     if (!c->d_St32 || !precond) return set_err(c, HDG_ERR_ARG, "FP32 apply needs HDG_STORE_FP32 and precond = 1");
     e = launch_apply32(c->prm, c->d_St32, (const float*)x, (float*)y, precond_scale(c), nullptr, c->stream);
   } else {
-    return set_err(c, HDG_ERR_ARG, "prec must be 64, 49, 48, 33 or 32");
+    return set_err(c, HDG_ERR_ARG, "prec must be 64, 56, 49, 48, 33 or 32");
   }
   c->launches += 1;
   return e == cudaSuccess ? HDG_OK : cuda_err(c, e, "hdg_apply");
@@ -640,10 +656,10 @@ hdg_status hdg_set_wait_hooks(hdg_ctx* c, int64_t wait_cycles, int64_t skip_copy
 
 hdg_status hdg_set_apply_shape(hdg_ctx* c, int mode, int edges_per_block, int bulk_warps) {
   if (!c) return HDG_ERR_ARG;
-  if (mode < 0 || mode > 2 || edges_per_block < 0 || bulk_warps < 0 || (edges_per_block > 0 && bulk_warps > 0))
-    return set_err(c, HDG_ERR_ARG, "mode 0..2 and at most one of edges_per_block, bulk_warps");
+  if (mode < 0 || mode > 3 || edges_per_block < 0 || bulk_warps < 0 || (edges_per_block > 0 && bulk_warps > 0))
+    return set_err(c, HDG_ERR_ARG, "mode 0..3 and at most one of edges_per_block, bulk_warps");
   if (c->lv) return set_err(c, HDG_ERR_ARG, "a level mesh has no per-edge apply shape");
-  const int bt = mode == 0 ? 0 : (mode == 2 ? 1 : 2);
+  const int bt = mode == 0 ? 0 : (mode == 2 ? 1 : (mode == 3 ? 3 : 2));
   if (edges_per_block * c->prm.P1 > 512) return set_err(c, HDG_ERR_ARG, "edges_per_block * (m p + 1) above 512");
   if (bulk_warps > 0 && (bt != 1 || !apply_bulk_available(c->prm, bulk_warps)))
     return set_err(c, HDG_ERR_ARG, "the pipelined apply needs mode 2 and a shape that fits shared memory");
@@ -657,7 +673,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!c) return HDG_ERR_ARG;
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
-  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 ||
+  if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 3 ||
       o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_DF64 || o->augment < 0 ||
       o->augment > HDG_MAX_AUGMENT || o->augment >= o->restart)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
@@ -666,6 +682,8 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)
   if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  if (o->mode == 3 && (!c->d_Sfix || nrhs != 1 || o->basis != HDG_BASIS_FP64))
+    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64, one right-hand side and the FP64 basis");
   if (c->lv) {
     const cudaError_t e = level_ensure_z(c, nrhs);
     if (e != cudaSuccess) return cuda_err(c, e, "element-side buffer");
@@ -681,13 +699,15 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
   if (!c) return HDG_ERR_ARG;
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
-  if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 2 || o->basis < HDG_BASIS_FP64 ||
+  if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 3 || o->basis < HDG_BASIS_FP64 ||
       o->basis > HDG_BASIS_DF64)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
   if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
+  if (o->mode == 3 && (!c->d_Sfix || o->basis != HDG_BASIS_FP64))
+    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64 and the FP64 basis");
   *rep = hdg_tune_report{};
   return autotune(c, *o, *rep);
 }
@@ -788,7 +808,7 @@ hdg_status hdg_run_host(hdg_ctx* c, const double* f_host, const double* gD_host,
   // the blocks the requested solve mode needs; FP64-accurate local factorisations (FP64 panels,
   // trailing updates on the tensor cores) except with the split-FP32 operator (mode 2), whose
   // condensation eliminates in split-FP32 arithmetic too
-  const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? HDG_STORE_FP32 : 0u) |
+  const unsigned cflags = HDG_KEEP_FACTORS | (o->mode == 1 ? HDG_STORE_FP32 : 0u) | (o->mode == 3 ? HDG_STORE_FIX64 : 0u) |
                           (o->mode == 2 ? (HDG_STORE_DF64 | HDG_SPLIT_UPDATE) : HDG_TC_UPDATE);
   if ((s = hdg_set_source(c, df, dg, 1)) == HDG_OK && (s = hdg_condense(c, cflags)) == HDG_OK &&
       (s = hdg_rhs(c, dgv)) == HDG_OK) {
@@ -851,6 +871,12 @@ hdg_status hdg_transpose(hdg_ctx* c) {
       e = launch_split_df(c->d_St, c->d_Stdf, (int64_t)c->prm.N * 3 * c->prm.n_t * c->prm.P1, c->stream);
     c->launches += 2;
     if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose (face blocks)");
+  }
+  if (c->d_Sfix) {
+    // the fixed-point copy follows the transposed rows
+    e = launch_fix_convert(c->prm, c->d_St, c->d_Sfix, c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_err(c, e, "hdg_transpose (fixed-point blocks)");
   }
   return HDG_OK;
 }
@@ -929,7 +955,7 @@ void hdg_destroy(hdg_ctx* c) {
     c->d_tables = nullptr;
   }
   cudaFree(c->d_tables); cudaFree(c->d_kappa); cudaFree(c->d_ghat); cudaFree(c->d_S); cudaFree(c->d_St);
-  cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
+  cudaFree(c->d_St32); cudaFree(c->d_Stdf); cudaFree(c->d_Sfix); cudaFree(c->d_gel); cudaFree(c->d_g); cudaFree(c->d_ws); cudaFree(c->d_info);
   cudaFree(c->d_escale); cudaFree(c->d_V); cudaFree(c->d_w); cudaFree(c->d_r); cudaFree(c->d_part);
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);

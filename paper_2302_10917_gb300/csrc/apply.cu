@@ -20,6 +20,7 @@
 // memory, consumed by warps), which the launch-shape autotuner times beside
 // this one.
 #include "internal.h"
+#include "launch.h"
 #include "df64.h"
 #include <type_traits>
 #include <algorithm>
@@ -667,6 +668,11 @@ cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void*
   if (epb < 0 && bt == 1 && vt == 1)
     return launch_apply_bulk(P, static_cast<const float2*>(S), static_cast<const float2*>(x), static_cast<float2*>(y),
                              escale, stop, st, -epb, hk ? hk->wait_cycles : 0, hk ? hk->skip_edge : -1);
+  // bt = 3: fixed-point blocks (exact integer products) on FP64 vectors
+  if (bt == 3) {
+    if (vt != 0) return cudaErrorInvalidValue;
+    return launch_apply_fix(P, S, static_cast<const double*>(x), static_cast<double*>(y), escale, stop, st, epb);
+  }
   // epb edges per block, one thread per (edge, trace position): at most 512 threads
   if (epb <= 0 || epb * P.P1 > 512) epb = apply_edges_per_block(P);
   const int threads = (epb * P.P1 + 31) / 32 * 32;

@@ -333,6 +333,7 @@ struct hdg_ctx {
   double* d_St = nullptr;         // [N][3][n_t][P1]  Gh^-1 S_e (preconditioned rows)
   float* d_St32 = nullptr;        // FP32 copy of d_St
   float2* d_Stdf = nullptr;       // d_St as FP32 (hi, lo) pairs
+  char* d_Sfix = nullptr;         // d_St as fixed-point limbs and row scales (HDG_STORE_FIX64)
   double* d_gel = nullptr;        // [N][n_t] element right-hand sides
   double* d_g = nullptr;          // [N_tr] assembled right-hand side
   double* d_ws = nullptr;         // factored bordered systems [slots][R][ld]
@@ -369,7 +370,7 @@ struct hdg_ctx {
   void* d_augb = nullptr;         // [3][nrhs][ldv] augmentation vectors of the batched GMRES
   int kb_restart = 0, kb_nrhs = 0;
   // launch shapes chosen by hdg_autotune (0: built-in defaults)
-  int tune_epb[3] = {0, 0, 0};    // apply edges per block, per block type (FP64, split, FP32)
+  int tune_epb[4] = {0, 0, 0, 0}; // apply edges per block, per block type (FP64, split, FP32, fixed-point)
   mehdg::BulkHooks bulk_hooks;    // pipelined apply: wait limit and the copy-skip test hook
   int tune_kgd = 0;               // multi-dot blocks over all vector groups
   int tune_kgu = 0;               // streaming-update blocks

@@ -776,6 +776,7 @@ static void launch_xupdate(bool f64, cudaStream_t st, const void* V, int64_t n, 
 static const void* op_blocks(hdg_ctx* c, int mode) {
   if (c->lv)
     return mode == 0 ? (const void*)c->lv->d_St : (mode == 2 ? (const void*)c->lv->d_Stdf : (const void*)c->lv->d_St32);
+  if (mode == 3) return c->d_Sfix;
   return mode == 0 ? (const void*)c->d_St : (mode == 2 ? (const void*)c->d_Stdf : (const void*)c->d_St32);
 }
 
@@ -835,7 +836,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   double* part = c->d_part;
   rep = hdg_solve_report{};
   // Arnoldi operator D^-1 S on split-FP32 vectors
-  const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
+  const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : (o.mode == 3 ? 3 : 2));
   const void* Sop = op_blocks(c, o.mode);
   const int phase = o.mode == 1 ? HDG_PROF_APPLY32 : HDG_PROF_APPLY;
   // launch shapes: the autotuner's choices, else the defaults; the streaming
@@ -1073,7 +1074,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   cudaStream_t st = c->stream;
   const int64_t n = P.N_tr, ldv = n + (n & 1), np = ldv / 2;
   const Batch one{np, 0, 0, 0, 0, 0};
-  const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : 2);
+  const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : (o.mode == 3 ? 3 : 2));
   const void* Sop = op_blocks(c, o.mode);
   const bool f64b = o.basis == HDG_BASIS_FP64;
   const int vt = f64b ? 0 : 1;

@@ -41,6 +41,13 @@ cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, d
                             const int* stop, cudaStream_t st);
 // bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks; vt: 0 FP64 / 1 split-FP32 vectors; hk: the pipelined
 // apply's wait limit and test hook (null: defaults)
+// Fixed-point apply (FP64 products exact in integer arithmetic): block conversion and apply.
+// fix points to limbs [N][3][n_t][P1] int2 followed by row scales [N][3][P1] int32.
+size_t fix_blocks_bytes(const Params& P);
+bool fix_supported(const Params& P);
+cudaError_t launch_fix_convert(const Params& P, const double* S, void* fix, cudaStream_t st);
+cudaError_t launch_apply_fix(const Params& P, const void* fix, const double* x, double* y, const double* escale,
+                             const int* stop, cudaStream_t st, int epb);
 cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void* x, void* y,
                              const double* escale, const int* stop, cudaStream_t st, int epb = 0, int vt = 1,
                              const BulkHooks* hk = nullptr);

@@ -236,7 +236,7 @@ def test_shape_errors_and_autotune_report():
     try:
         gpu.set_source(wl.sin_sin_source(gpu.quad_points(), 1.0, (1.0, 0.5)))
         gpu.condense(keep_factors=True, store_df64=True, store_fp32=True)
-        for args in ((0, 0, 1), (1, 0, 2), (2, 1, 1), (3, 0, 0), (2, -1, 0), (2, 0, -1), (2, 100, 0), (2, 0, 4)):
+        for args in ((0, 0, 1), (1, 0, 2), (2, 1, 1), (3, 0, 1), (4, 0, 0), (2, -1, 0), (2, 0, -1), (2, 100, 0), (2, 0, 4)):
             with pytest.raises(HDGError) as ei:
                 gpu.set_apply_shape(*args)
             assert ei.value.status == HDG_ERR_ARG, args
