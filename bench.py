@@ -61,8 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--mode", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Arnoldi operator of the timed solve: 0 FP64, 1 FP32 (+FP64 refinement), 2 split FP32, "
                          "3 fixed-point rows with exact integer products (FP64-accurate)")
-    ap.add_argument("--basis", type=int, default=0, choices=[0, 1],
-                    help="Krylov basis and orthogonalisation: 0 FP64, 1 split FP32")
+    ap.add_argument("--basis", type=int, default=0, choices=[0, 1, 2],
+                    help="Krylov basis and orthogonalisation: 0 FP64, 1 split FP32, 2 fixed-point chunks with "
+                         "exact integer products (FP64-accurate)")
     ap.add_argument("--orth", type=int, default=3, choices=[0, 1, 2, 3],
                     help="Arnoldi orthogonalisation: 0 CGS2 (four passes), 1 CGS with Pythagorean norm (two passes), "
                          "2 CGS with a second projection where more than half of the vector lay in the basis, "
@@ -542,7 +543,12 @@ def run_ours(args):
             for j in range(max(jused, 0)):
                 nv = j + 1
                 steps_bytes += ((4 * nv + 6) if args.orth == 0 else (2 * nv + 3)) * 8.0 * N_tr
-    vk = "d_mdot_kernel + d_update_kernel" if args.basis == 0 else "df_mdot_kernel + df_update_kernel"
+                if args.basis == 2:
+                    # the new vector is also written in FP64 (the operator's input); chunk scales are
+                    # 4 bytes per 2048 entries and vector read
+                    steps_bytes += 8.0 * N_tr + ((2 * nv + 1) * 4.0 * N_tr / 2048)
+    vk = {0: "d_mdot_kernel + d_update_kernel", 1: "df_mdot_kernel + df_update_kernel",
+          2: "fx_mdot_kernel + fx_combine_kernel (fixed-point chunks, exact int64 products)"}[args.basis]
     rooflines["ortho"] = {"kernel": vk + " (+ reduce2_givens_kernel)",
                           "bound": "hbm", "launches": prof["ortho"][0], "avg_launch_ms": avg("ortho"),
                           "achieved": steps_bytes / (prof["ortho"][1] / 1e3) / 1e9 if prof["ortho"][1] else 0.0,
@@ -564,7 +570,7 @@ def run_ours(args):
         roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 64, scaled by interior edges"
     roof_other = {k: v for k, v in rooflines.items() if k != dom}
 
-    all_fp64 = args.mode in (0, 3) and args.basis == 0 and not split
+    all_fp64 = args.mode in (0, 3) and args.basis in (0, 2) and not split
     dtype = "f64" if all_fp64 else FORM_DTYPES.get((args.mode, args.basis, args.elim), "mixed")
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
@@ -579,7 +585,8 @@ def run_ours(args):
                                        2: "split-FP32 blocks on the FP32 pipe",
                                        3: "56-bit fixed-point rows, exact int64 products, one FP64 rounding per "
                                           "element side"}[args.mode],
-                       "krylov_basis": ["FP64", "split-FP32"][args.basis],
+                       "krylov_basis": ["FP64", "split-FP32",
+                                        "fixed-point chunks of 2048 entries (56-bit, exact int64 products)"][args.basis],
                        "orthogonalisation": ["CGS2", "CGS, Pythagorean norm",
                                              "CGS + second projection where ||w - V h||^2 < ||w||^2 / 2",
                                              "CGS + second projection where ||w - V h||^2 < 1e-6 ||w||^2"][args.orth],

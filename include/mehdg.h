@@ -158,11 +158,19 @@ typedef struct {
  * storage and arithmetic of the Krylov basis and its orthogonalisation:
  * HDG_BASIS_FP64 (0, the default) = FP64 vectors, FP64 dot products and
  * updates; HDG_BASIS_DF64 (1) = split-FP32 ("double-float", two FP32 words,
- * 48-bit significand, FP32 exponent range) on the FP32 pipe. The pipelined
+ * 48-bit significand, FP32 exponent range) on the FP32 pipe; HDG_BASIS_FIX
+ * (2; one right-hand side, no augmented restarts) = FP64-accurate fixed-point
+ * vectors: each chunk of 2048 entries of a basis vector held as 56-bit
+ * integers at the scale of its largest entry (8 bytes per entry plus one int32
+ * per chunk), the products of the multi-dot and the updates summed exactly in
+ * 64-bit integers and rounded once per chunk and vector (multi-dot) or per
+ * entry (updates), the operator applied to an FP64 copy of the newest vector;
+ * no FP64 FMA per entry and vector. The pipelined
  * apply shape (hdg_set_apply_shape bulk_warps) runs with HDG_BASIS_DF64 only;
  * with FP64 vectors mode 2 uses the one-thread-per-row apply. */
 #define HDG_BASIS_FP64 0
 #define HDG_BASIS_DF64 1
+#define HDG_BASIS_FIX 2
 #define HDG_MAX_AUGMENT 3
 typedef struct {
   double tol;            /* true relative residual ||g - S x|| / ||g|| to reach, > 0 */
@@ -177,7 +185,7 @@ typedef struct {
                             ||w||^2 / 2 (Kahan-Parlett "twice is enough"; decided on the device, two
                             passes in the other steps); 3 = as 2 with the second projection only where
                             ||w - V V^T w||^2 < 1e-6 ||w||^2 (more than six digits cancelled) */
-  int basis;             /* HDG_BASIS_FP64 or HDG_BASIS_DF64 (see above) */
+  int basis;             /* HDG_BASIS_FP64, HDG_BASIS_DF64 or HDG_BASIS_FIX (see above) */
   int augment;           /* 0 .. HDG_MAX_AUGMENT, below restart: augmented restarts (LGMRES, Baker, Jessup
                             and Manteuffel 2005): the last `augment` steps of every restart cycle take the
                             normalised corrections x_new - x_old of the previous cycles as their operator

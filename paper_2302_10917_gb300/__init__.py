@@ -19,7 +19,7 @@ HDG_ERR_SINGULAR, HDG_ERR_NOCONV, HDG_ERR_TIMEOUT = 5, 6, 7
 HDG_STORE_FP32, HDG_KEEP_FACTORS, HDG_STORE_DF64, HDG_SPLIT_UPDATE, HDG_PRECOND_FACE_SCHUR = 1, 2, 4, 8, 16
 HDG_TC_UPDATE = 32
 HDG_STORE_FIX64 = 64
-BASIS_FP64, BASIS_DF64 = 0, 1   # hdg_solve_opts.basis: FP64 or split-FP32 Krylov basis
+BASIS_FP64, BASIS_DF64, BASIS_FIX = 0, 1, 2   # hdg_solve_opts.basis: FP64, split-FP32 or fixed-point Krylov basis
 STATUS_NAMES = {0: "HDG_OK", 1: "HDG_ERR_ARG", 2: "HDG_ERR_STATE", 3: "HDG_ERR_CUDA", 4: "HDG_ERR_OOM",
                 5: "HDG_ERR_SINGULAR", 6: "HDG_ERR_NOCONV", 7: "HDG_ERR_TIMEOUT"}
 
@@ -310,7 +310,10 @@ class Problem:
               augment=0):
         """g: [N_tr], or [nrhs, N_tr] (independent systems solved in lockstep: one multi-RHS
         apply and batched vector kernels per Arnoldi step; the report is the worst column's).
-        basis: BASIS_FP64 (FP64 Krylov basis and orthogonalisation) or BASIS_DF64 (split-FP32).
+        mode: Arnoldi operator, 0 FP64 blocks, 1 FP32 blocks (FP64 refinement), 2 split-FP32 blocks,
+        3 fixed-point rows with exact integer products (condense(store_fix=True)).
+        basis: BASIS_FP64 (FP64 Krylov basis and orthogonalisation), BASIS_DF64 (split-FP32) or
+        BASIS_FIX (fixed-point chunks, products exact in integers; one right-hand side).
         augment: 0..3 corrections of earlier restart cycles added to each cycle's search space
         (augmented restarts, LGMRES)."""
         g = g.to(self.device, torch.float64).contiguous()

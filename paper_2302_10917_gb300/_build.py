@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmehdg.so")
 LIB_BOUNDS_CHECK = os.path.join(HERE, "libmehdg_bc.so")
-SOURCES = ["reference.cpp", "condense.cu", "apply.cu", "apply_fix.cu", "krylov.cu", "api.cu", "static_scratch.cu", "adjoint.cu", "apply_mrhs.cu", "levels.cu", "precond.cu"]
+SOURCES = ["reference.cpp", "condense.cu", "apply.cu", "apply_fix.cu", "krylov.cu", "krylov_fix.cu", "api.cu", "static_scratch.cu", "adjoint.cu", "apply_mrhs.cu", "levels.cu", "precond.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -674,7 +674,7 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (!g || !x || !o || nrhs < 1 || nrhs > HDG_MAX_RHS) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_solve before hdg_condense");
   if (!(o->tol > 0.0) || o->maxit < 1 || o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 3 ||
-      o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_DF64 || o->augment < 0 ||
+      o->orth < 0 || o->orth > 3 || o->basis < HDG_BASIS_FP64 || o->basis > HDG_BASIS_FIX || o->augment < 0 ||
       o->augment > HDG_MAX_AUGMENT || o->augment >= o->restart)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
@@ -682,8 +682,10 @@ hdg_status hdg_solve(hdg_ctx* c, const double* g, double* x, int nrhs, const hdg
   if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   // (the profiling phase of the FP32 inner operator is HDG_PROF_APPLY32)
   if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
-  if (o->mode == 3 && (!c->d_Sfix || nrhs != 1 || o->basis != HDG_BASIS_FP64))
-    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64, one right-hand side and the FP64 basis");
+  if (o->mode == 3 && (!c->d_Sfix || nrhs != 1 || o->basis == HDG_BASIS_DF64))
+    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64, one right-hand side and FP64 vectors");
+  if (o->basis == HDG_BASIS_FIX && (nrhs != 1 || o->augment > 0))
+    return set_err(c, HDG_ERR_ARG, "the fixed-point basis takes one right-hand side and no augmented restarts");
   if (c->lv) {
     const cudaError_t e = level_ensure_z(c, nrhs);
     if (e != cudaSuccess) return cuda_err(c, e, "element-side buffer");
@@ -700,14 +702,14 @@ hdg_status hdg_autotune(hdg_ctx* c, const hdg_solve_opts* o, hdg_tune_report* re
   if (!o || !rep) return set_err(c, HDG_ERR_ARG, "bad arguments");
   if (c->state < 2) return set_err(c, HDG_ERR_STATE, "hdg_autotune before hdg_condense");
   if (o->restart < 1 || o->restart > 128 || o->mode < 0 || o->mode > 3 || o->basis < HDG_BASIS_FP64 ||
-      o->basis > HDG_BASIS_DF64)
+      o->basis > HDG_BASIS_FIX)
     return set_err(c, HDG_ERR_ARG, "bad solve options");
   const bool has32 = c->lv ? c->lv->d_St32 != nullptr : c->d_St32 != nullptr;
   const bool hasdf = c->lv ? c->lv->d_Stdf != nullptr : c->d_Stdf != nullptr;
   if (o->mode == 1 && !has32) return set_err(c, HDG_ERR_ARG, "mode 1 needs HDG_STORE_FP32");
   if (o->mode == 2 && !hasdf) return set_err(c, HDG_ERR_ARG, "mode 2 needs HDG_STORE_DF64");
-  if (o->mode == 3 && (!c->d_Sfix || o->basis != HDG_BASIS_FP64))
-    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64 and the FP64 basis");
+  if (o->mode == 3 && (!c->d_Sfix || o->basis == HDG_BASIS_DF64))
+    return set_err(c, HDG_ERR_ARG, "mode 3 needs HDG_STORE_FIX64 and FP64 vectors");
   *rep = hdg_tune_report{};
   return autotune(c, *o, *rep);
 }
@@ -960,7 +962,7 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_small); cudaFree(c->d_flag); cudaFree(c->d_piv); cudaFree(c->d_gadj); cudaFree(c->d_bad);
   cudaFree(c->d_Vb); cudaFree(c->d_wb); cudaFree(c->d_rb); cudaFree(c->d_partb); cudaFree(c->d_smallb);
   cudaFree(c->d_flagb); cudaFree(c->d_scalb); cudaFree(c->d_Zb); cudaFree(c->d_Pinv); cudaFree(c->d_cmapb);
-  cudaFree(c->d_aug); cudaFree(c->d_augb);
+  cudaFree(c->d_aug); cudaFree(c->d_augb); cudaFree(c->d_Vs); cudaFree(c->d_vin);
   for (auto& g : c->gm_cache) cudaGraphExecDestroy(g.second);
   for (cudaEvent_t ev : c->gm_ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

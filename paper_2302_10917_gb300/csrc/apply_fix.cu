@@ -26,12 +26,12 @@
 // below 2^64; n_t is limited to FIX_MAX_NT accordingly.
 #include "internal.h"
 #include "launch.h"
+#include "fixpoint.h"
 #include <algorithm>
 
 namespace mehdg {
 
 constexpr int FIX_MAX_NT = 240;
-constexpr int FIX_LO_BITS = 28;
 constexpr int FIX_GATHER = (FIX_MAX_NT + 31) / 32;   // trace values per lane in the gather
 constexpr int FIX_G = 8;    // row entries per load group
 
@@ -41,51 +41,6 @@ constexpr int FIX_G = 8;    // row entries per load group
 __host__ __device__ inline int fix_ntp(int nt) { return (nt + FIX_G - 1) / FIX_G * FIX_G; }
 __host__ __device__ inline size_t fix_tab_offset(int epb, int nt) {
   return ((size_t)epb * 2 * fix_ntp(nt) * 8 + (size_t)epb * 2 * 4 + 15) / 16 * 16;
-}
-
-// v as a fixed-point number at scale 2^(1077 - Eb), where Eb (>= 1) is the
-// largest biased exponent of the set v belongs to: |result| <= 2^55, rounded to
-// nearest (ties away from zero) on the magnitude. Integer operations only.
-__device__ __forceinline__ int2 fix_limbs(unsigned long long bits, int Eb) {
-  int eb = (int)((bits >> 52) & 0x7ff);
-  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
-  if (eb == 0) eb = 1;
-  else m |= 1ull << 52;
-  const int sh = eb - Eb + 2;   // <= 2 since eb <= Eb
-  unsigned long long a;
-  if (sh >= 0) {
-    a = m << sh;
-  } else {
-    const int r = -sh;
-    a = r > 54 ? 0ull : (m + (1ull << (r - 1))) >> r;
-  }
-  const long long v = (bits >> 63) ? -(long long)a : (long long)a;
-  return make_int2((int)(v & ((1ll << FIX_LO_BITS) - 1)), (int)(v >> FIX_LO_BITS));
-}
-
-__device__ __forceinline__ int fix_exp_field(unsigned long long bits) {
-  const int eb = (int)((bits >> 52) & 0x7ff);
-  return eb == 0 ? 1 : eb;
-}
-
-// (hh 2^56 + (m0 + m1) 2^28 + ll) 2^(Er + Ex - 2154), rounded once to FP64
-// (round to nearest even: the top 64 bits of the normalised magnitude with a
-// sticky bit for the rest go through one correctly rounded conversion).
-__device__ __forceinline__ double fix_result(long long hh, long long m0, long long m1, unsigned long long ll, int Er,
-                                             int Ex) {
-  if (Er == 2047 || Ex == 2047) return __longlong_as_double(0x7FF8000000000000ll);   // Inf or NaN input
-  __int128 t = ((__int128)hh << 56) + (((__int128)m0 + (__int128)m1) << 28) + (__int128)ll;
-  const bool neg = t < 0;
-  unsigned __int128 a = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  if (a == 0) return 0.0;
-  const unsigned long long ahi = (unsigned long long)(a >> 64), alo = (unsigned long long)a;
-  const int lz = ahi ? __clzll(ahi) : 64 + __clzll(alo);
-  const unsigned __int128 n = a << lz;
-  unsigned long long top = (unsigned long long)(n >> 64);
-  if ((unsigned long long)n != 0ull) top |= 1ull;
-  const double d = __ull2double_rn(top);
-  const double r = scalbn(d, 64 - lz + Er + Ex - 2154);
-  return neg ? -r : r;
 }
 
 // Rows (e, k, t) of the FP64 blocks -> limbs and row scales; one thread per row.

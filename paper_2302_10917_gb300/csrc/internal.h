@@ -334,6 +334,8 @@ struct hdg_ctx {
   float* d_St32 = nullptr;        // FP32 copy of d_St
   float2* d_Stdf = nullptr;       // d_St as FP32 (hi, lo) pairs
   char* d_Sfix = nullptr;         // d_St as fixed-point limbs and row scales (HDG_STORE_FIX64)
+  int* d_Vs = nullptr;            // chunk scales of the fixed-point Krylov basis [restart + 1][chunks]
+  double* d_vin = nullptr;        // the newest fixed-point basis vector in FP64 (the operator's input)
   double* d_gel = nullptr;        // [N][n_t] element right-hand sides
   double* d_g = nullptr;          // [N_tr] assembled right-hand side
   double* d_ws = nullptr;         // factored bordered systems [slots][R][ld]

@@ -689,8 +689,10 @@ static cudaError_t ensure_krylov(hdg_ctx* c, int K) {
   cudaFree(c->d_w);
   cudaFree(c->d_r);
   cudaFree(c->d_aug);
+  cudaFree(c->d_Vs);
+  cudaFree(c->d_vin);
   c->d_V = nullptr; c->d_part = nullptr; c->d_small = nullptr; c->d_flag = nullptr; c->d_w = nullptr; c->d_r = nullptr;
-  c->d_aug = nullptr;
+  c->d_aug = nullptr; c->d_Vs = nullptr; c->d_vin = nullptr;
   c->krylov_restart = 0;
   const size_t n = (size_t)c->prm.N_tr;
   const size_t ldv = n + (n & 1);   // even row length: 16-byte element pairs, zero padding
@@ -821,13 +823,22 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   SmallLayout L(K);
   double* sm = c->d_small;
   int* fl = c->d_flag;
-  // basis entries: FP64, or split-FP32 pairs (8 bytes either way)
+  // basis entries: FP64, split-FP32 pairs or fixed-point limbs (8 bytes each); the operator
+  // reads FP64 vectors except with the split-FP32 basis
   const bool f64b = o.basis == HDG_BASIS_FP64;
-  const int vt = f64b ? 0 : 1;
+  const bool fixb = o.basis == HDG_BASIS_FIX;
+  const int vt = o.basis == HDG_BASIS_DF64 ? 1 : 0;
   const size_t esz = 8;
   char* V = reinterpret_cast<char*>(c->d_V);
   void* w = c->d_w;
   const int64_t ldv = n + (n & 1), np = ldv / 2;   // basis row length (even) and element pairs
+  // fixed-point basis: chunk scales and the FP64 copy of the newest vector
+  const int64_t nch = fx_chunks(n);
+  if (fixb && !c->d_Vs) {
+    if (!cu.ok(cudaMalloc(&c->d_Vs, (size_t)(K + 1) * nch * sizeof(int))) ||
+        !cu.ok(cudaMalloc(&c->d_vin, (size_t)ldv * sizeof(double))))
+      return fail(c, HDG_ERR_OOM, std::string("fixed-point basis: ") + cudaGetErrorString(cu.err));
+  }
   const Batch one{np, 0, 0, 0, 0, 0};
   const void* V4 = V;
   void* w4 = w;
@@ -844,11 +855,11 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
   const int kgd = c->tune_kgd > 0 ? c->tune_kgd : KGD;
   const int kgu = c->tune_kgu > 0 ? c->tune_kgu : KGU;
   // the pipelined shape runs on split-FP32 vectors only
-  const int epb = (f64b && c->tune_epb[bt] < 0) ? 0 : c->tune_epb[bt];
+  const int epb = (vt == 0 && c->tune_epb[bt] < 0) ? 0 : c->tune_epb[bt];
   const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
   // the pipelined apply's timeout flag, read once the solve has synchronised
   auto bulk_wait_gave_up = [&]() -> bool {
-    if (!(epb < 0 && bt == 1 && !f64b)) return false;
+    if (!(epb < 0 && bt == 1 && vt == 1)) return false;
     int err = 0;
     return !cu.ok(apply_bulk_take_error(st, &err)) || err != 0;
   };
@@ -897,7 +908,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
     cu.ok(cudaMemcpyAsync(sm + L.sc + 2, &factor, sizeof(double), cudaMemcpyHostToDevice, st));
     axpby_norm_kernel<<<KG, KT, 0, st>>>(1.0, r0, 0.0, r0, r0, n, part);
     cycle_init_kernel<<<1, 256, 0, st>>>(sm, L, fl, part, KG);
-    launch_first(f64b, st, r0, sm, L.sc + 4, V, n, fl);
+    if (fixb) launch_fx_combine(V, c->d_Vs, ldv, n, 0, nullptr, 0.0, r0, 1.0, sm, L.sc + 4, c->d_vin, V, c->d_Vs, fl, st);
+    else launch_first(f64b, st, r0, sm, L.sc + 4, V, n, fl);
     LAUNCHED(4);
     const int jmax = std::min(klen, o.maxit - its);
     // steps m .. jmax-1 take the stored corrections as operator inputs (at least one Krylov step)
@@ -912,7 +924,9 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
       {
         ProfScope ps(c, timed ? phase : -1);
-        const void* in = j < m ? (const void*)(V + (size_t)j * ldv * esz) : (const void*)(Zr + (size_t)(j - m) * ldv * esz);
+        const void* in = fixb ? (const void*)c->d_vin
+                              : (j < m ? (const void*)(V + (size_t)j * ldv * esz)
+                                       : (const void*)(Zr + (size_t)(j - m) * ldv * esz));
         if (c->lv) cu.ok(launch_level_apply(c, bt, vt, Sop, in, w, 1, ldv, precond_scale(c), fl, s));
         else cu.ok(launch_apply_vdf(bt, P, Sop, in, w, precond_scale(c), fl, s, epb, vt, &c->bulk_hooks));
       }
@@ -922,31 +936,49 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       }
       ProfScope po(c, timed ? HDG_PROF_ORTHO : -1);
       void* Vn = V + (size_t)(j + 1) * ldv * esz;
+      // the basis passes of either representation: multi-dot (ncol = nv, or nv + 1 with
+      // ||w||^2), w -= V htmp, and V_{j+1} = (w - V htmp) * sm[sc + 4]
+      auto mdot = [&](int ncol, const int* flag) -> int {
+        if (fixb) return launch_fx_mdot(V, c->d_Vs, ldv, n, nv, ncol, static_cast<const double*>(w), part, flag, s);
+        return launch_mdot(V4, np, nv, ncol, w4, part, flag, s, kgd, one, 1, f64b);
+      };
+      auto update_w = [&](const int* flag) {
+        if (fixb)
+          launch_fx_combine(V, c->d_Vs, ldv, n, nv, sm + L.htmp, -1.0, static_cast<const double*>(w), 1.0, sm, -1,
+                            static_cast<double*>(w), nullptr, nullptr, flag, s);
+        else launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, flag, one, 0);
+      };
+      auto update_v = [&]() {
+        if (fixb)
+          launch_fx_combine(V, c->d_Vs, ldv, n, nv, sm + L.htmp, -1.0, static_cast<const double*>(w), 1.0, sm,
+                            L.sc + 4, c->d_vin, Vn, c->d_Vs + (size_t)(j + 1) * nch, fl, s);
+        else launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
+      };
       if (o.orth == 0) {
         // CGS2 in four passes over the basis: (1) h1 = V^T w; (2) w' = w - V h1;
         // (3) h2 = V^T w' and ||w'||^2; (4) V_{j+1} = (w' - V h2) / ||w' - V h2||,
         // the norm from ||w'||^2 - ||h2||^2
-        int G = launch_mdot(V4, np, nv, nv, w4, part, fl, s, kgd, one, 1, f64b);
+        int G = mdot(nv, fl);
         mdot_reduce_kernel<<<nv, 128, 0, s>>>(part, G, nv, nv, Hcol, sm + L.htmp, 0, fl, nullptr);
-        launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl, one, 0);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
+        update_w(fl);
+        G = mdot(nv + 1, fl);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_STOP);
       } else if (o.orth == 1) {
         // classical Gram-Schmidt, one projection in two passes: (1) h = V^T w and
         // ||w||^2; (2) V_{j+1} = (w - V h) / ||w - V h||, the norm from ||w||^2 - ||h||^2
-        const int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
+        const int G = mdot(nv + 1, fl);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 0, one, F_STOP);
       } else {
         // as orth = 1, plus a second projection (w' = w - V h; h2 = V^T w', ||w'||^2) only
         // when the first pass finds ||w - V h||^2 < ||w||^2 / 2; the second-pass kernels
         // are always launched and return at once when flag F_P2 says it is not needed
-        int G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl, s, kgd, one, 1, f64b);
+        int G = mdot(nv + 1, fl);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, o.orth, one, F_STOP);
-        launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, -1, w4, fl + F_P2, one, 0);
-        G = launch_mdot(V4, np, nv, nv + 1, w4, part, fl + F_P2, s, kgd, one, 1, f64b);
+        update_w(fl + F_P2);
+        G = mdot(nv + 1, fl + F_P2);
         reduce2_givens_kernel<<<dim3((nv + 32) / 32, 1), 1024, 0, s>>>(part, G, nv, sm, L, fl, j, 1, one, F_P2);
       }
-      launch_update(f64b, dim3(gu), s, V4, np, nv, sm + L.htmp, w4, sm, L.sc + 4, Vn, fl, one, 0);
+      update_v();
       if (ev) cu.ok(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     };
     const int per_step = o.orth == 1 ? 4 : 6;
@@ -957,7 +989,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       // turns the steps after convergence into immediate returns. With
       // profiling on, the capture carries an event quadruple per step.
       const int timed = c->prof_on ? 1 : 0;
-      const std::vector<intptr_t> key = {K, bt, vt, o.orth, timed, m, (intptr_t)Zr, (intptr_t)c->bulk_hooks.wait_cycles,
+      const std::vector<intptr_t> key = {K, bt, vt, o.basis, o.orth, timed, m, (intptr_t)Zr, (intptr_t)c->bulk_hooks.wait_cycles,
                                          c->bulk_hooks.skip_edge, (intptr_t)Sop, (intptr_t)V, (intptr_t)w,
                                          (intptr_t)part, (intptr_t)sm, (intptr_t)fl, (intptr_t)precond_scale(c),
                                          (intptr_t)np, kgd, kgu, epb, c->lv ? c->lv->rb : 0};
@@ -1056,7 +1088,8 @@ hdg_status gmres_solve(hdg_ctx* c, const double* g, double* x, const hdg_solve_o
       else zslot = (zslot + 1) % o.augment;
       LAUNCHED(3);
     } else {
-      launch_xupdate(f64b, st, V, n, ldv, jused, sm + L.y, x);
+      if (fixb) launch_fx_combine(V, c->d_Vs, ldv, n, jused, sm + L.y, 1.0, x, 1.0, sm, -1, x, nullptr, nullptr, nullptr, st);
+      else launch_xupdate(f64b, st, V, n, ldv, jused, sm + L.y, x);
       LAUNCHED(2);
     }
   }
@@ -1076,7 +1109,8 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   const Batch one{np, 0, 0, 0, 0, 0};
   const int bt = o.mode == 0 ? 0 : (o.mode == 2 ? 1 : (o.mode == 3 ? 3 : 2));
   const void* Sop = op_blocks(c, o.mode);
-  const bool f64b = o.basis == HDG_BASIS_FP64;
+  // (the fixed-point basis runs its operator on FP64 vectors: tuned as the FP64 basis)
+  const bool f64b = o.basis != HDG_BASIS_DF64;
   const int vt = f64b ? 0 : 1;
   char* V = reinterpret_cast<char*>(c->d_V);
   const void* V4 = V;

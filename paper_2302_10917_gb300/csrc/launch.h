@@ -41,6 +41,13 @@ cudaError_t launch_apply_df(const Params& P, const float2* S, const double* x, d
                             const int* stop, cudaStream_t st);
 // bt: 0 FP64 / 1 split-FP32 / 2 FP32 blocks; vt: 0 FP64 / 1 split-FP32 vectors; hk: the pipelined
 // apply's wait limit and test hook (null: defaults)
+// Fixed-point Krylov basis: limbs [vectors][ldv] int2, chunk scales [vectors][fx_chunks(n)] int32.
+int64_t fx_chunks(int64_t n);
+int launch_fx_mdot(const void* V, const int* Vs, int64_t ldv, int64_t n, int nv, int ncol, const double* w,
+                   double* part, const int* stop, cudaStream_t st);
+void launch_fx_combine(const void* V, const int* Vs, int64_t ldv, int64_t n, int nv, const double* coef, double csign,
+                       const double* base, double bcoef, const double* sm, int scale_off, double* out_d, void* out_l,
+                       int* out_s, const int* stop, cudaStream_t st);
 // Fixed-point apply (FP64 products exact in integer arithmetic): block conversion and apply.
 // fix points to limbs [N][3][n_t][P1] int2 followed by row scales [N][3][P1] int32.
 size_t fix_blocks_bytes(const Params& P);

@@ -140,6 +140,43 @@ def test_fixed_operator_solve_matches_direct_solve(case):
     assert abs(rep3["iterations"] - rep0["iterations"]) <= max(2, rep0["iterations"] // 10)
 
 
+@pytest.mark.parametrize("orth", [0, 1, 3])
+def test_fixed_point_basis_solve_matches_direct_solve(case, orth):
+    """The fixed-point Krylov basis (chunks of 56-bit integers, products exact in integers)
+    with the fixed-point and the FP64 operators, every orthogonalisation: against the oracle's
+    direct solve, the true residual reported, bitwise reproducible, and (with the second
+    projections) the iteration count of the FP64 basis within 20 % (the count of a
+    restarted GMRES follows rounding)."""
+    from paper_2302_10917_gb300 import BASIS_FIX
+    ora, gpu = case["ora"], case["gpu"]
+    S = ora.assemble_S(case["S_el"])
+    x_dir = np.linalg.solve(S, case["g"])
+    g_gpu = gpu.rhs()
+    for mode in (3, 0):
+        x2, rep2, st = gpu.solve(g_gpu, tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth, basis=BASIS_FIX)
+        assert st == 0 and rep2["converged"] == 1 and rep2["rel_residual"] <= 1e-10
+        xn = x2.cpu().numpy()
+        assert abs(np.linalg.norm(case["g"] - S @ xn) / np.linalg.norm(case["g"]) - rep2["rel_residual"]) < 1e-12
+        assert rel(xn, x_dir) < 1e-8
+        x2b, rep2b, _ = gpu.solve(g_gpu, tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth, basis=BASIS_FIX)
+        assert torch.equal(x2, x2b) and rep2 == rep2b
+        if orth != 1:   # (the single projection's Pythagorean norm makes the count follow the rounding)
+            _, rep0, _ = gpu.solve(g_gpu, tol=1e-10, restart=30, maxit=5000, mode=mode, orth=orth)
+            assert abs(rep2["iterations"] - rep0["iterations"]) <= max(6, rep0["iterations"] // 5)
+
+
+def test_fixed_point_basis_is_scale_invariant(case):
+    """Power-of-two scaling of the right-hand side scales the fixed-point basis solve's
+    iterate exactly (every chunk scale and coefficient scale moves by the same power)."""
+    from paper_2302_10917_gb300 import BASIS_FIX
+    gpu = case["gpu"]
+    g = gpu.rhs()
+    x1, r1, _ = gpu.solve(g, tol=1e-10, restart=30, maxit=5000, mode=3, orth=1, basis=BASIS_FIX)
+    x2, r2, _ = gpu.solve(g * 2.0 ** 37, tol=1e-10, restart=30, maxit=5000, mode=3, orth=1, basis=BASIS_FIX)
+    assert r1["iterations"] == r2["iterations"]
+    assert torch.equal(x2, x1 * 2.0 ** 37)
+
+
 def test_fixed_point_argument_errors():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -160,7 +197,11 @@ def test_fixed_point_argument_errors():
     g2 = torch.stack([gpu.rhs(), gpu.rhs()])
     _, _, st = gpu.solve(g2, mode=3, check=False)        # one right-hand side only
     assert st == HDG_ERR_ARG
-    _, _, st = gpu.solve(gpu.rhs(), mode=3, basis=1, check=False)   # FP64 basis only
+    _, _, st = gpu.solve(gpu.rhs(), mode=3, basis=1, check=False)   # FP64 vectors only
+    assert st == HDG_ERR_ARG
+    _, _, st = gpu.solve(g2, basis=2, check=False)                  # the fixed-point basis: one column
+    assert st == HDG_ERR_ARG
+    _, _, st = gpu.solve(gpu.rhs(), basis=2, augment=1, restart=10, check=False)   # and no augmentation
     assert st == HDG_ERR_ARG
     gpu.close()
     lv = Problem(4, 1, 1, beta=(1.0, 0.0), kappa=1.0, levels=np.zeros(32, dtype=np.int32))

@@ -145,15 +145,15 @@ def test_apply_matches_the_oracle(case, prec):
         assert rel(gpu.apply(torch.from_numpy(x)).cpu().numpy(), Sg @ x) < 1e-12
 
 
-@pytest.mark.parametrize("basis", [0, 1])
+@pytest.mark.parametrize("basis", [0, 1, 2])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_solve_and_recover_match_the_oracle(case, mode, basis):
-    """Every operator precision with the FP64 (basis 0) and split-FP32 (1) Krylov basis, and
-    augmented restarts with the FP64 basis."""
+    """Every operator precision with the FP64 (basis 0), split-FP32 (1) and fixed-point (2)
+    Krylov basis, and augmented restarts with the FP64 basis."""
     ora, gpu = case["ora"], case["gpu"]
     x_dir = np.linalg.solve(ora.assemble_S(case["S"]), case["g"])
-    x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=60 if basis == 1 else 12, mode=mode, maxit=20000,
-                           basis=basis, augment=0 if basis == 1 else 2)
+    x, rep, st = gpu.solve(gpu.rhs(), tol=1e-13, restart=12 if basis == 0 else 60, mode=mode, maxit=20000,
+                           basis=basis, augment=2 if basis == 0 else 0)
     assert st == 0, rep
     assert rel(x.cpu().numpy(), x_dir) < 1e-9
     u, q = gpu.recover(x)

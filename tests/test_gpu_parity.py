@@ -15,7 +15,7 @@ import torch
 
 from oracle.hdg import HDGProblem
 from oracle.problems import polynomial, random_polynomial
-from paper_2302_10917_gb300 import BASIS_DF64, BASIS_FP64
+from paper_2302_10917_gb300 import BASIS_DF64, BASIS_FIX, BASIS_FP64
 from paper_2302_10917_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -211,7 +211,7 @@ def test_gmres_solution_matches_direct_solve(case):
     assert rel(q_g.cpu().numpy(), q_o) < 1e-7
 
 
-@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64, BASIS_FIX])
 def test_gmres_split_fp32_apply_mode(case, basis):
     """mode 2: GMRES with the split-FP32 preconditioned apply; the FP64 residual decides."""
     ora, gpu = case["ora"], case["gpu"]
@@ -224,7 +224,7 @@ def test_gmres_split_fp32_apply_mode(case, basis):
     assert rel(x_gpu, x_dir) < 1e-8
 
 
-@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64, BASIS_FIX])
 def test_gmres_fp32_iterative_refinement_mode(case, basis):
     """mode 1: FP32 blocks inside FP64 iterative refinement still reach the FP64 residual
     (with BASIS_FP64: the mixed-precision form with FP64 orthogonalisation)."""
@@ -238,7 +238,7 @@ def test_gmres_fp32_iterative_refinement_mode(case, basis):
     assert rel(x_gpu, x_dir) < 1e-8
 
 
-@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64, BASIS_FIX])
 @pytest.mark.parametrize("orth", [1, 2, 3])
 def test_gmres_single_projection_variants(case, orth, basis):
     """orth = 1 (one projection, norm from Pythagoras), orth = 2 (a second projection
@@ -275,7 +275,7 @@ def test_gmres_with_augmented_restarts(case, mode, basis, augment):
     assert torch.equal(torch.from_numpy(x_gpu).cuda(), x2) and rep == rep2
 
 
-@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64])
+@pytest.mark.parametrize("basis", [BASIS_FP64, BASIS_DF64, BASIS_FIX])
 def test_solve_is_bitwise_reproducible(case, basis):
     gpu = case["gpu"]
     g = gpu.rhs()
