@@ -134,6 +134,11 @@ __device__ __forceinline__ typename VAcc<BT>::T vzero() {
   else return typename VAcc<BT>::T(0);
 }
 
+// byte offset of the per-vector edge table behind the gathered traces (16-byte aligned)
+__host__ __device__ inline size_t vdf_tab_offset(int epb, int nt, size_t el) {
+  return ((size_t)epb * 2 * nt * el + 15) / 16 * 16;
+}
+
 // The same edge-centric apply on Krylov-basis vectors: BT = 0: FP64 blocks,
 // FP64 accumulation; BT = 1: split-FP32 blocks and accumulation on the FP32
 // pipe; BT = 2: FP32 blocks, FP32 accumulation. VT: vector type (above).
@@ -145,27 +150,41 @@ __global__ void __launch_bounds__(512) apply_vdf_kernel(Params P, const void* __
   if (stop && *stop) return;
   using XT = typename VAcc<BT>::T;
   extern __shared__ unsigned char sraw[];
-  XT* xs = reinterpret_cast<XT*>(sraw);   // [epb][2][n_t]
   const int nt = P.n_t, P1 = P.P1, PP = P.P;
+  XT* xs = reinterpret_cast<XT*>(sraw);                                        // [epb][2][n_t]
+  int4* tab = reinterpret_cast<int4*>(sraw + vdf_tab_offset(epb, nt, sizeof(XT)));   // [epb][2]
   const int f0 = blockIdx.x * epb;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < epb * 2 * nt; idx += blockDim.x) {
-    const int le = idx / (2 * nt);
-    const int rem = idx - le * 2 * nt;
-    const int sd = rem / nt, c = rem - sd * nt;
-    const int f = f0 + le;
-    XT v = vzero<BT>();
+  // the three edges (code, orientation) of each side's element, once per vector; then
+  // one warp per vector gathers its n_t trace values
+  for (int i = tid; i < 2 * epb; i += blockDim.x) {
+    const int f = f0 + (i >> 1);
+    int4 te = make_int4(-1, -1, -1, 0);
     if (f < P.n_int) {
       int e[2], k[2], fl[2];
       double len;
       edge_sides(f, P.n, e, k, fl, &len);
       int code[3], flip[3];
-      elem_edges(e[sd], P.n, code, flip);
-      const int kk = c / P1, t = c - kk * P1;
-      const size_t xi = (size_t)code[kk] * P1 + (flip[kk] ? PP - t : t);
-      if (code[kk] >= 0 && HDG_INB(xi, P.N_tr, P.oob, 1)) v = vgather<BT, VT>(x, xi);
+      elem_edges(e[i & 1], P.n, code, flip);
+      te = make_int4(code[0], code[1], code[2], flip[0] | (flip[1] << 1) | (flip[2] << 2));
     }
-    xs[idx] = v;
+    tab[i] = te;
+  }
+  __syncthreads();
+  {
+    const int lane = tid & 31, nw = blockDim.x >> 5;
+    for (int vi = tid >> 5; vi < 2 * epb; vi += nw) {
+      const int4 te = tab[vi];
+      for (int c = lane; c < nt; c += 32) {
+        const int kk = c < P1 ? 0 : (c < 2 * P1 ? 1 : 2);
+        const int t = c - kk * P1;
+        const int code = kk == 0 ? te.x : (kk == 1 ? te.y : te.z);
+        const size_t xi = (size_t)code * P1 + (((te.w >> kk) & 1) ? PP - t : t);
+        XT v = vzero<BT>();
+        if (code >= 0 && HDG_INB(xi, P.N_tr, P.oob, 1)) v = vgather<BT, VT>(x, xi);
+        xs[vi * nt + c] = v;
+      }
+    }
   }
   __syncthreads();
   const int le = tid / P1, s = tid - le * P1;
@@ -678,7 +697,7 @@ cudaError_t launch_apply_vdf(int bt, const Params& P, const void* S, const void*
   const int threads = (epb * P.P1 + 31) / 32 * 32;
   const int grid = (P.n_int + epb - 1) / epb;
   const size_t el = bt == 0 ? sizeof(double) : (bt == 1 ? sizeof(float2) : sizeof(float));
-  const size_t sm = (size_t)epb * 2 * P.n_t * el;
+  const size_t sm = vdf_tab_offset(epb, P.n_t, el) + (size_t)epb * 2 * sizeof(int4);
 #define VDF_CASE(B, V) \
   if (bt == B && vt == V) apply_vdf_kernel<B, V><<<grid, threads, sm, st>>>(P, S, x, y, escale, epb, stop);
   VDF_CASE(0, 0) VDF_CASE(1, 0) VDF_CASE(2, 0) VDF_CASE(0, 1) VDF_CASE(1, 1) VDF_CASE(2, 1)
