@@ -364,9 +364,9 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* x_dev, double* u_dev, double*
 hdg_status hdg_get_schur(hdg_ctx* ctx, int64_t e0, int64_t count, double* S_dev);
 
 /* End-to-end pipeline on HOST buffers: copies f (and g_D, may be NULL) to
- * the device, condenses (factors kept; modes 0 and 1 with HDG_TC_UPDATE, mode 1
- * also keeping the FP32 blocks; mode 2 the split-FP32 blocks after split-FP32
- * elimination), assembles g, solves
+ * the device, condenses (factors kept; modes 0, 1 and 3 with HDG_TC_UPDATE, mode 1
+ * also keeping the FP32 blocks, mode 3 the fixed-point blocks; mode 2 the
+ * split-FP32 blocks after split-FP32 elimination), assembles g, solves
  * from x = 0, recovers u and q and copies x, u, q back (each output may be
  * NULL to skip its copy). Synchronous. Same layouts as above. */
 hdg_status hdg_run_host(hdg_ctx* ctx, const double* f_qp_host, const double* gD_qp_host,
