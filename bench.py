@@ -625,6 +625,8 @@ def run_ours(args):
                        "rel_residual": rep_f["rel_residual"], "converged": bool(rep_f["converged"]),
                        "rel_l2_vs_fp64_step": {"trace": dist(xf, x64), "u": dist(uf, u64), "q": dist(qf, q64)}}
     if not args.no_forms:
+        # back to the timed step's blocks and launch shapes (the last form kept other blocks)
+        pr.condense(**condense_flags(args.mode, args.elim))
         pr.autotune(mode=args.mode, restart=args.restart, basis=args.basis)
         del x64, u64, q64
         line["forms"] = forms
