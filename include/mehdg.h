@@ -219,7 +219,7 @@ typedef struct {
                                   gives up. No counterpart in the paper (its local solver is LAPACK LU). */
 #define HDG_STORE_FIX64 64u   /* also keep the preconditioned blocks as fixed-point numbers (uniform mesh, n_t <= 240):
                                   every row (element, edge, trace position) scaled by the power of two of its largest
-                                  entry's exponent and rounded to 56 bits (|v| <= 2^55, error <= 2^-56 of the row's
+                                  entry's exponent and rounded to 56 bits (|v| <= 2^55, error <= 2^-55 of the row's
                                   largest magnitude), stored as a signed high and a 28-bit low 32-bit limb (8 bytes
                                   per entry, the FP64 layout) plus one int32 scale per row. The apply (prec = 56,
                                   mode 3) scales each gathered element trace vector the same way and sums the limb

@@ -13,7 +13,7 @@
 // scale are then added and multiplied in FP64 as in the FP64 apply.
 //
 // Accuracy: the only errors besides the final roundings are the fixed-point
-// roundings of the inputs, at most 2^-56 of the row's (vector's) largest
+// roundings of the inputs, at most 2^-55 of the row's (vector's) largest
 // magnitude per entry, so |y - y_exact| <= 2^-55 (max|s| sum|x| + max|x| sum|s|)
 // per side plus one FP64 rounding of the result, against the FP64 FMA chain's
 // bound of about n_t 2^-53 sum |s||x|.

@@ -16,9 +16,9 @@
 // Besides the limbs, the update that writes a new basis vector also writes it
 // in FP64 (the operator's input).
 //
-// Accuracy: storage rounds each entry to 2^-56 of its chunk's largest
+// Accuracy: storage rounds each entry to 2^-55 of its chunk's largest
 // magnitude; sums are exact until one final FP64 rounding; the coefficient
-// scaling rounds each h_i 2^s_i to 2^-56 of the largest of them. Accumulator
+// scaling rounds each h_i 2^s_i to 2^-55 of the largest of them. Accumulator
 // bounds: per dot product sum at most 16 terms per thread (a warp's 512 summed
 // exactly in 128 bits), per update sum at most 128 terms, inside 2^63
 // (|hi| <= 2^27, 0 <= lo < 2^28).
