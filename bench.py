@@ -42,8 +42,8 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 APPLY_VDF1_TRAFFIC_PER_EDGE_M8P3 = 376.20e6 / 12160
 # the same for apply_vdf_kernel<0,0> (FP64 blocks, FP64 vectors): 376.72 MB for 12 160 edges at n = 64
 APPLY_VDF00_TRAFFIC_PER_EDGE_M8P3 = 376.72e6 / 12160
-# the same for apply_fix_kernel (fixed-point rows, FP64 vectors): 376.25 + 4.75 MB for 12 160 edges at n = 64
-APPLY_FIX_TRAFFIC_PER_EDGE_M8P3 = 381.00e6 / 12160
+# the same for apply_fix_kernel (fixed-point rows, FP64 vectors): 376.25 + 4.69 MB for 12 160 edges at n = 64
+APPLY_FIX_TRAFFIC_PER_EDGE_M8P3 = 380.94e6 / 12160
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SAMPLE_COND, CPU_SAMPLE_APPLY = 40, 100000     # about 12 s of single-thread oracle work
 # trace-operator applications per step of the GPU path (GMRES(80) Arnoldi steps + 1 per restart)
