@@ -67,7 +67,6 @@ struct Batch {
 constexpr int KGU = 1216;     // blocks of the streaming update kernel, 8 per SM
 constexpr int KGD = 1216;     // blocks (over all vector groups) of the multi-dot, 8 per SM
 constexpr int KGD_MAX = 2432; // largest multi-dot block count the autotuner tries
-constexpr int KGU_MAX = 4864; // largest streaming-update block count the autotuner tries
 
 // ------------------------------------------------------------ FP64 helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -1187,7 +1186,7 @@ hdg_status autotune(hdg_ctx* c, const hdg_solve_opts& o, hdg_tune_report& rep) {
   int best_kgu = KGU;
   double best_upd = 1e30, def_upd = 0.0;
   void* out = V + (size_t)nv * ldv * 8;
-  for (int kgu : {608, 1216, 2432, 4864}) {
+  for (int kgu : {608, 1216, 2432, 4864}) {   // (the streaming update's candidate block counts)
     const int gu = (int)std::min<int64_t>(kgu, std::max<int64_t>(1, (np + KT - 1) / KT));
     const double t = time_it([&] {
       launch_update(f64b, dim3(gu), st, V4, np, nv, coef, w4, nullptr, -1, out, nullptr, one, 0);
