@@ -100,3 +100,18 @@ def test_reference_arm_runs_on_rank_zero_only():
     res = _run_reference({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert res.returncode == 0, res.stderr[-500:]
     assert not [ln for ln in res.stdout.splitlines() if ln.strip().startswith("{")]
+
+
+def test_precision_forms_are_labelled_and_the_defaults_are_the_fp64_step():
+    """Every precision form the benchmark line reports has its label, every solve mode a
+    name, and the default options are the FP64 step (fixed-point operator, FP64 basis,
+    tensor-core elimination) on the large workload."""
+    for name, key in bench.FORMS.items():
+        assert key in bench.FORM_DTYPES, name
+        assert key[0] in bench.MODE_NAMES
+    assert bench.FORM_DTYPES[bench.FORMS["fp64_fixed"]].startswith("f64")
+    assert bench.FORM_DTYPES[bench.FORMS["fp64"]].startswith("f64")
+    args = bench.parse_args([])
+    assert (args.mode, args.basis, args.elim, args.gpus) == (3, 0, "tc", 1)
+    assert args.warmup >= 3 and args.config == "n128_m8_p3"
+    assert bench.parse_args(["--mode", "0", "--basis", "2"]).basis == 2
