@@ -363,11 +363,13 @@ def tc_slice_flops(Q, R, Cc, b=32, m_tile=128, n_tile=32, products=28):
 # ---------------------------------------------------------------------- ours
 MODE_NAMES = {0: "fp64", 1: "fp32_ir", 2: "df64", 3: "fp64_fixed"}
 # precision forms of one step: (Arnoldi operator mode, Krylov basis, local factorisation)
-FORMS = {"fp64": (0, 0, "tc"), "fp64_fixed": (3, 0, "tc"), "fp64_dfma": (0, 0, "fp64"), "fp32_ir": (1, 0, "tc"),
-         "df64": (2, 1, "split")}
+FORMS = {"fp64": (0, 0, "tc"), "fp64_fixed": (3, 0, "tc"), "fp64_fixed_basis": (3, 2, "tc"),
+         "fp64_dfma": (0, 0, "fp64"), "fp32_ir": (1, 0, "tc"), "df64": (2, 1, "split")}
 FORM_DTYPES = {(0, 0, "tc"): "f64 (tensor-core trailing updates by exact 8-bit slices, FP64-accurate)",
                (3, 0, "tc"): "f64 (trace apply on 56-bit fixed-point rows with exact integer products, one FP64 "
                              "rounding per element side; tensor-core trailing updates by exact 8-bit slices)",
+               (3, 2, "tc"): "f64 (as fp64_fixed, and the Krylov basis in 56-bit fixed-point chunks with exact "
+                             "integer products in the multi-dot and the updates)",
                (0, 0, "fp64"): "f64 (FP64 FMAs throughout)",
                (1, 0, "tc"): "f32 blocks (FP32 operator) + f64 factorisation, orthogonalisation and refinement",
                (2, 1, "split"): "df64 (f32x2) elimination, blocks and Krylov basis + f64 residual"}

@@ -57,7 +57,7 @@ __device__ __forceinline__ int block_max_i(int v, int* red) {
 // lane 0 rounds once; the rounding and the warp sum are spread over FXM_E entries.
 constexpr int FXM_T = 64;                 // threads per multi-dot block (one chunk)
 constexpr int FXM_E = FXC / FXM_T;        // entries per thread
-__global__ void __launch_bounds__(FXM_T, 10) fx_mdot_kernel(const int2* __restrict__ V, const int* __restrict__ Vs,
+__global__ void __launch_bounds__(FXM_T, 16) fx_mdot_kernel(const int2* __restrict__ V, const int* __restrict__ Vs,
                                                             int nch, int64_t ldv, int64_t n, int nv, int ncol,
                                                             const double* __restrict__ w, double* part,
                                                             const int* stop) {
@@ -65,18 +65,20 @@ __global__ void __launch_bounds__(FXM_T, 10) fx_mdot_kernel(const int2* __restri
   constexpr int NW = FXM_T / 32;
   __shared__ double acc[FX_VG][NW];
   __shared__ int red[NW];
+  __shared__ int2 wls[FXC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int g0 = blockIdx.y * FX_VG, g1 = min(ncol, g0 + FX_VG);
   for (int i = threadIdx.x; i < FX_VG * NW; i += FXM_T) (&acc[0][0])[i] = 0.0;
   for (int c = blockIdx.x; c < nch; c += gridDim.x) {
     const int64_t e0 = (int64_t)c * FXC + threadIdx.x;
-    int2 wl[FXM_E];
+    // this thread's limbs of w for the chunk, kept in shared memory (entry-major,
+    // thread-minor: conflict-free) to leave the registers to the loads in flight
     int eb = 1;
 #pragma unroll
     for (int k = 0; k < FXM_E; ++k) {
       const int64_t e = e0 + k * FXM_T;
       const unsigned long long b = e < n ? (unsigned long long)__double_as_longlong(w[e]) : 0ull;
-      wl[k] = make_int2((int)(unsigned)b, (int)(unsigned)(b >> 32));   // the bits, for now
+      wls[k * FXM_T + threadIdx.x] = make_int2((int)(unsigned)b, (int)(unsigned)(b >> 32));   // the bits, for now
       eb = max(eb, fix_exp_field(b));
     }
     eb = __reduce_max_sync(0xffffffffu, eb);
@@ -87,8 +89,10 @@ __global__ void __launch_bounds__(FXM_T, 10) fx_mdot_kernel(const int2* __restri
 #pragma unroll
     for (int q = 1; q < NW; ++q) Ew = max(Ew, red[q]);
 #pragma unroll
-    for (int k = 0; k < FXM_E; ++k)
-      wl[k] = fix_limbs(((unsigned long long)(unsigned)wl[k].y << 32) | (unsigned)wl[k].x, Ew);
+    for (int k = 0; k < FXM_E; ++k) {
+      const int2 b = wls[k * FXM_T + threadIdx.x];
+      wls[k * FXM_T + threadIdx.x] = fix_limbs(((unsigned long long)(unsigned)b.y << 32) | (unsigned)b.x, Ew);
+    }
     // (16 loads of a vector in flight per thread; column nv is w itself)
     for (int i = g0; i < g1; ++i) {
       long long hh = 0, m0 = 0, m1 = 0;
@@ -102,10 +106,13 @@ __global__ void __launch_bounds__(FXM_T, 10) fx_mdot_kernel(const int2* __restri
           v[k] = e < n ? vp[e] : make_int2(0, 0);
         }
 #pragma unroll
-        for (int k = 0; k < FXM_E; ++k) fix_mac(hh, m0, m1, ll, v[k], wl[k]);
+        for (int k = 0; k < FXM_E; ++k) fix_mac(hh, m0, m1, ll, v[k], wls[k * FXM_T + threadIdx.x]);
       } else {
 #pragma unroll
-        for (int k = 0; k < FXM_E; ++k) fix_mac(hh, m0, m1, ll, wl[k], wl[k]);
+        for (int k = 0; k < FXM_E; ++k) {
+          const int2 b = wls[k * FXM_T + threadIdx.x];
+          fix_mac(hh, m0, m1, ll, b, b);
+        }
       }
       // the warp's products share one scale: summed exactly across the warp (|sum| < 2^120),
       // rounded once by lane 0
