@@ -1,4 +1,4 @@
-"""The three precision forms of the whole path against the FP64 oracle.
+"""The precision forms of the whole path against the FP64 oracle.
 
 The large workload's element (m = 8, p = 3, beta = 50 (cos 0.3, sin 0.3),
 kappa = 1, sin-sin source) on a small macro mesh. The oracle condenses every
@@ -6,6 +6,10 @@ element from the literal 3Q x 3Q system of Eq. (D) and solves the assembled
 trace system (Eq. global_problem) directly; each GPU form condenses, solves to
 a 1e-10 true residual and back-solves:
   fp64     FP64 elimination, blocks, operator, Krylov basis and orthogonalisation;
+  fp64_tc_fixed      the benchmark's step: FP64 panels with the trailing updates
+           on the tensor cores (exact slices), the operator's products exact in
+           integers (56-bit fixed-point rows), FP64 basis;
+  fp64_tc_fixed_basis  as fp64_tc_fixed, with the fixed-point Krylov basis;
   fp32_ir  FP64 elimination, the preconditioned blocks stored and applied in
            FP32 inside FP64 residual replacement, FP64 basis;
   df64     split-FP32 elimination, blocks, operator and basis.
@@ -23,7 +27,8 @@ from oracle.problems import sin_sin
 
 pytestmark = pytest.mark.gpu
 
-FORMS = {"fp64": (0, 0, False), "fp32_ir": (1, 0, False), "df64": (2, 1, True)}
+FORMS = {"fp64": (0, 0, False), "fp64_tc_fixed": (3, 0, "tc"), "fp64_tc_fixed_basis": (3, 2, "tc"),
+         "fp32_ir": (1, 0, False), "df64": (2, 1, True)}
 
 
 def rel(a, b):
@@ -54,7 +59,8 @@ def test_form_matches_the_oracle(oracle_solution, form):
     pr = Problem(o["n"], o["m"], o["p"], beta=o["beta"], kappa=o["kappa"])
     try:
         pr.set_source(torch.from_numpy(o["f"]))
-        pr.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), split_update=split)
+        pr.condense(keep_factors=True, store_fp32=(mode == 1), store_df64=(mode == 2), store_fix=(mode == 3),
+                    split_update=split is True, tc_update=split == "tc")
         x, rep, st = pr.solve(pr.rhs(), tol=1e-10, restart=80, maxit=20000, mode=mode, orth=2, basis=basis)
         assert st == 0 and rep["converged"] == 1, rep
         u, q = pr.recover(x)
